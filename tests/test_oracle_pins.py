@@ -1,0 +1,282 @@
+"""Pins of the CPU oracle to things other than itself (no GPU).
+
+* the paper's worked example (Sec. 4.1): printed hit points, boolean result,
+  leaf order, leaf and internal boxes;
+* the canopy surface of Sec. 4.1.5 (counts follow from our patch geometry);
+* closed forms of axis-aligned cases (t, u, v known by hand);
+* a closed box: convexity fixes every crossing count;
+* exact rational orientation predicates (a different formula: signed
+  volumes instead of Moller's cross/dot products) on near-boundary pairs;
+* the degenerate cases the method has (edge, vertex, end point, parallel,
+  zero-area triangle, zero-length segment).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from golden_io import load
+
+MISS, HIT, AMB = oracle.PAIR_MISS, oracle.PAIR_HIT, oracle.PAIR_AMBIGUOUS
+
+
+# ------------------------------------------------------------ worked example
+def test_case_study1_boolean_and_hit_points():
+    g = load("case_study1_sec4_1.txt")
+    r = oracle.query(g["vertices"], g["triangles"], g["ray_from"], g["ray_to"])
+    assert r["hit"].tolist() == g["boolean"].tolist()
+    assert r["amb_hit"].sum() == 0 and r["amb_count"].sum() == 0
+    for ray, tri, point in g["hitpoint"]:
+        assert r["near_tri"][ray] == tri
+        s, e = g["ray_from"][ray].astype(np.float64), g["ray_to"][ray].astype(np.float64)
+        p = s + float(r["near_t"][ray]) * (e - s)
+        # the printed points carry 2 decimals; FP32 vertices round at ~1e-7
+        np.testing.assert_allclose(p, point, atol=2e-6)
+        assert r["count"][ray] == 1
+
+
+def test_case_study1_leaf_order_and_boxes():
+    g = load("case_study1_sec4_1.txt")
+    b = oracle.build_all(g["vertices"], g["triangles"], bits=30)
+    assert b["perm"].tolist() == g["leaf_order"].tolist()
+    b63 = oracle.build_all(g["vertices"], g["triangles"], bits=63)
+    assert b63["perm"].tolist() == g["leaf_order"].tolist()
+    n = len(b["perm"])
+    for leaf, box in g["leaf_box"].items():
+        got = b["box"][n - 1 + leaf]
+        np.testing.assert_allclose(got[[0, 3, 1, 4, 2, 5]], box, atol=1e-6)
+    ranges = {(int(a), int(c)): i for i, (a, c) in enumerate(zip(b["range_lo"], b["range_hi"]))}
+    assert set(ranges) == set(g["internal_box"])
+    for rng, box in g["internal_box"].items():
+        got = b["box"][ranges[rng]]
+        np.testing.assert_allclose(got[[0, 3, 1, 4, 2, 5]], box, atol=1e-6)
+    # root covers all leaves (Sec. 4.2: bounds reach the top of the tree)
+    assert ranges[(0, 3)] == 0
+
+
+def test_canopy_counts():
+    g = load("canopy_sec4_1_5.txt")
+    r = oracle.query(g["vertices"], g["triangles"], g["ray_from"], g["ray_to"])
+    assert r["count"].tolist() == g["count"].tolist()
+    assert r["amb_count"].sum() == 0
+    assert r["hit"].tolist() == (g["count"] > 0).astype(int).tolist()
+
+
+# ------------------------------------------------------------ closed forms
+TRI = ([0, 0, 0], [1, 0, 0], [0, 1, 0])
+
+
+@pytest.mark.parametrize("x,y,z0,z1", [(0.25, 0.25, -1, 3), (0.1, 0.6, -2, 0.5), (0.7, 0.2, 1, -1)])
+def test_axis_aligned_closed_form(x, y, z0, z1):
+    cls, q = oracle.classify_pair([x, y, z0], [x, y, z1], *TRI)
+    assert cls == HIT
+    t = -z0 / (z1 - z0)
+    assert q["t"] == pytest.approx(t, abs=1e-12)
+    x64, y64 = float(np.float32(x)), float(np.float32(y))
+    assert q["u"] == pytest.approx(x64, abs=1e-12)   # weight of b = x
+    assert q["v"] == pytest.approx(y64, abs=1e-12)   # weight of c = y
+    assert q["w"] == pytest.approx(1 - x64 - y64, abs=1e-12)
+
+
+@pytest.mark.parametrize("name,s,e,expect", [
+    ("edge u=0 side", [0.0, 0.5, -1], [0.0, 0.5, 1], AMB),
+    ("edge v=0 side", [0.5, 0.0, -1], [0.5, 0.0, 1], AMB),
+    ("hypotenuse", [0.5, 0.5, -1], [0.5, 0.5, 1], AMB),
+    ("vertex", [0.0, 0.0, -1], [0.0, 0.0, 1], AMB),
+    ("vertex b", [1.0, 0.0, -1], [1.0, 0.0, 1], AMB),
+    ("start on face t=0", [0.25, 0.25, 0], [0.25, 0.25, 1], AMB),
+    ("end on face t=1", [0.25, 0.25, -1], [0.25, 0.25, 0], AMB),
+    ("in-plane through face", [0.1, 0.1, 0], [0.3, 0.3, 0], AMB),
+    ("in-plane far away", [2.0, 2.0, 0], [3.0, 3.0, 0], MISS),
+    ("parallel above", [0.2, 0.2, 0.5], [0.4, 0.2, 0.5], MISS),
+    ("outside footprint", [2.0, 2.0, -1], [2.0, 2.0, 1], MISS),
+    ("stops short", [0.25, 0.25, 0.5], [0.25, 0.25, 1], MISS),
+    ("just inside edge", [0.5, 1e-3, -1], [0.5, 1e-3, 1], HIT),
+    ("just outside edge", [0.5, -1e-3, -1], [0.5, -1e-3, 1], MISS),
+    ("zero-length on face", [0.25, 0.25, 0], [0.25, 0.25, 0], MISS),
+])
+def test_degenerate_and_boundary_cases(name, s, e, expect):
+    cls, _ = oracle.classify_pair(s, e, *TRI)
+    assert cls == expect, name
+
+
+def test_zero_area_triangle_never_hits():
+    a, b = [0, 0, 0], [1, 0, 0]
+    c = [2, 0, 0]                       # collinear: the normal is exactly zero
+    cls, _ = oracle.classify_pair([0.5, 0, -1], [0.5, 0, 1], a, b, c)
+    assert cls == MISS
+
+
+def test_nearly_parallel_uses_distance():
+    # direction tilted by 1e-8 rad out of the plane z = 0, 0.1 above it: the
+    # distance 0.1 >> tau |d| so it is a decisive miss, though det_rel < tau
+    cls, q = oracle.classify_pair([-1, 0.2, 0.1], [1, 0.2, 0.1 + 2e-8], *TRI)
+    assert abs(q["det_rel"]) <= oracle.TAU and q["dist"] > 0.09 and cls == MISS
+    # the same segment 1e-9 above the face is within the band: ambiguous
+    cls, q = oracle.classify_pair([-1, 0.2, 0.0], [1, 0.2, 2e-8], *TRI)
+    assert cls == AMB
+
+
+# ------------------------------------------------------------ closed box
+def _cube():
+    V = np.array([[x, y, z] for z in (0, 1) for y in (0, 1) for x in (0, 1)], np.float32)
+    q = [(0, 1, 3, 2), (4, 5, 7, 6), (0, 1, 5, 4), (2, 3, 7, 6), (0, 2, 6, 4), (1, 3, 7, 5)]
+    T = []
+    for a, b, c, d in q:
+        T += [(a, b, c), (a, c, d)]
+    return V, np.array(T, np.int32)
+
+
+def test_closed_box_crossing_parity():
+    V, T = _cube()
+    rng = np.random.default_rng(7)
+    n = 4000
+    F = rng.uniform(-1, 2, (n, 3)).astype(np.float32)
+    E = rng.uniform(-1, 2, (n, 3)).astype(np.float32)
+    inside = lambda P: np.all((P > 0) & (P < 1), axis=1)
+    # force a quarter of the segments to start inside
+    F[: n // 4] = rng.uniform(0.05, 0.95, (n // 4, 3)).astype(np.float32)
+    r = oracle.query(V, T, F, E)
+    ok = r["amb_count"] == 0
+    assert ok.mean() > 0.95
+    fi, ei = inside(F), inside(E)
+    cnt = r["count"]
+    # a convex closed surface: through-segments cross 0 or 2 times, a segment
+    # with exactly one end inside crosses once, both inside: never
+    both_out = ok & ~fi & ~ei
+    one_in = ok & (fi ^ ei)
+    both_in = ok & fi & ei
+    assert set(np.unique(cnt[both_out])) <= {0, 2}
+    assert np.all(cnt[one_in] == 1)
+    assert np.all(cnt[both_in] == 0)
+    assert np.all(r["hit"][ok] == (cnt[ok] > 0))
+    assert both_out.sum() > 500 and one_in.sum() > 500
+
+
+# ------------------------------------------------------------ exact predicates
+def _F(x):
+    return [Fraction(float(v)) for v in x]
+
+
+def _orient(a, b, c, d):
+    ab = [b[i] - a[i] for i in range(3)]
+    ac = [c[i] - a[i] for i in range(3)]
+    ad = [d[i] - a[i] for i in range(3)]
+    return (ab[0] * (ac[1] * ad[2] - ac[2] * ad[1]) - ab[1] * (ac[0] * ad[2] - ac[2] * ad[0])
+            + ab[2] * (ac[0] * ad[1] - ac[1] * ad[0]))
+
+
+def _exact_class(s, e, a, b, c, tau=Fraction(1, 10 ** 6)):
+    """Exact classification from signed volumes.  Returns (cls, guard) where
+    guard is False when a margin sits so near a threshold that FP64 rounding
+    could flip it, or when the pair is on the nearly-parallel branch (there
+    the threshold is an irrational distance and is not checked here)."""
+    s, e, a, b, c = map(_F, (s, e, a, b, c))
+    d = [e[i] - s[i] for i in range(3)]
+    e1 = [b[i] - a[i] for i in range(3)]
+    e2 = [c[i] - a[i] for i in range(3)]
+    n = [e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]]
+    dot = lambda x, y: sum(x[i] * y[i] for i in range(3))
+    det = -dot(d, n)                                      # e1 . (d x e2)
+    den2 = dot(d, d) * dot(e1, e1) * dot(e2, e2)
+    # nearly parallel (|det_rel| <= tau, with a relative guard of 1e-6 so that
+    # FP64 rounding of det_rel cannot cross the threshold): not checked here
+    if det == 0 or det * det <= tau * tau * den2 * (1 + Fraction(1, 10 ** 6)):
+        return None, False
+    # plane side of the end points: t = S_s / (S_s - S_e)
+    Ss, Se = _orient(a, b, c, s), _orient(a, b, c, e)
+    t = Ss / (Ss - Se)
+    # barycentric weights of the line's plane point, from the volumes spanned
+    # by the segment and each edge: weight of a ~ (s,e,b,c), b ~ (s,e,c,a),
+    # c ~ (s,e,a,b)
+    Oa, Ob, Oc = _orient(s, e, b, c), _orient(s, e, c, a), _orient(s, e, a, b)
+    tot = Oa + Ob + Oc
+    w, u, v = Oa / tot, Ob / tot, Oc / tot
+    marg = min(abs(x - y) for x in (u, v, w, t) for y in (tau, -tau))
+    marg = min(marg, abs(t - (1 - tau)), abs(t - (1 + tau)))
+    guard = marg > Fraction(1, 10 ** 12)
+    if u > tau and v > tau and w > tau and tau < t < 1 - tau:
+        return HIT, guard
+    if u < -tau or v < -tau or w < -tau or t < -tau or t > 1 + tau:
+        return MISS, guard
+    return AMB, guard
+
+
+def _near_boundary_pairs(rng, n):
+    """Triangles of random shape and size; segments aimed at a point of the
+    triangle's edge, vertex or interior, displaced by 1e-9..1e-3 of the size,
+    with random length and a random split of the segment at that point."""
+    out = []
+    for _ in range(n):
+        a = rng.uniform(-1, 1, 3); b = a + rng.uniform(-0.3, 0.3, 3); c = a + rng.uniform(-0.3, 0.3, 3)
+        kind = rng.integers(0, 4)
+        lam = rng.uniform()
+        if kind == 0:
+            p = a + lam * (b - a)
+        elif kind == 1:
+            p = (a, b, c)[rng.integers(0, 3)].copy()
+        elif kind == 2:
+            r1, r2 = rng.uniform(size=2)
+            if r1 + r2 > 1:
+                r1, r2 = 1 - r1, 1 - r2
+            p = a + r1 * (b - a) + r2 * (c - a)
+        else:
+            p = b + lam * (c - b)
+        p = p + rng.normal(size=3) * 10.0 ** rng.uniform(-9, -3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        L = rng.uniform(0.01, 2.0)
+        f = rng.choice([rng.uniform(), 0.0, 1.0, rng.uniform(-1e-6, 1e-6), 1 + rng.uniform(-1e-6, 1e-6)])
+        s = p - f * L * d
+        e = p + (1 - f) * L * d
+        out.append([x.astype(np.float32) for x in (s, e, a, b, c)])
+    return out
+
+
+def test_oracle_matches_exact_predicates():
+    rng = np.random.default_rng(11)
+    checked = {HIT: 0, MISS: 0, AMB: 0}
+    for s, e, a, b, c in _near_boundary_pairs(rng, 3000):
+        exact, guard = _exact_class(s, e, a, b, c)
+        cls, _ = oracle.classify_pair(s, e, a, b, c)
+        if exact is None:
+            # nearly parallel: a decisive hit would contradict the definition
+            assert cls != HIT
+            continue
+        if guard:
+            assert cls == exact
+            checked[exact] += 1
+    assert min(checked.values()) > 100, checked
+
+
+def test_query_aggregates_pairs():
+    """The per-ray answer is the aggregate of the per-pair classes."""
+    g = load("canopy_sec4_1_5.txt")
+    rng = np.random.default_rng(3)
+    F = rng.uniform([11.8, 1.8, 0.5], [13.2, 3.2, 2.0], (300, 3)).astype(np.float32)
+    E = rng.uniform([11.8, 1.8, 0.5], [13.2, 3.2, 2.0], (300, 3)).astype(np.float32)
+    r = oracle.query(g["vertices"], g["triangles"], F, E)
+    V, T = g["vertices"], g["triangles"]
+    for i in range(len(F)):
+        cls = [oracle.classify_pair(F[i], E[i], *V[T[j]])[0] for j in range(len(T))]
+        nh, na = cls.count(HIT), cls.count(AMB)
+        assert r["amb_count"][i] == (na > 0)
+        assert r["amb_hit"][i] == (nh == 0 and na > 0)
+        if na == 0:
+            assert r["count"][i] == nh and r["hit"][i] == (nh > 0)
+
+
+def test_shared_edge_counted_once_on_ambiguous_ray():
+    """Reading of "unique intersections" (Sec. 1): a segment through the
+    shared edge of two triangles is one crossing point (parity unpinned)."""
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], np.float32)
+    T = np.array([[0, 1, 2], [1, 3, 2]], np.int32)
+    r = oracle.query(V, T, [[0.5, 0.5, -1]], [[0.5, 0.5, 1]])
+    assert r["amb_count"][0] == 1 and r["count"][0] == 1 and r["hit"][0] == 1
+
+
+def test_bad_index_rejected():
+    V = np.zeros((3, 3), np.float32)
+    with pytest.raises(ValueError):
+        oracle.query(V, [[0, 1, 3]], [[0, 0, 0]], [[0, 0, 1]])
