@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the linear-BVH segment/surface intersection on one GB300.
+
+Workload (the paper's scale: ~2e4 triangles, 1e7 segments, Sec. 3.3): a
+100 x 100-vertex heightfield with sinusoid + Gaussian-bump relief (19,602
+triangles) and 1e7 segments, half crossing the surface and half wholly above
+it, length U(0.05, 1), random directions -- seeded synthetic data standing in
+for the paper's unavailable generator.
+
+One step = the whole hot path on one batch: GPU build of the hierarchy
+(extent, Morton codes, radix sort, radix tree, refit) + the boolean query +
+the intercept_count query of every segment (FP32 traversal with the FP64
+re-test of band segments).  value = segments fully answered (both modes) per
+second, summed over ranks.  The segments (240 MB) exceed the 129 MB L2, so no
+flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rays/s (exact vs FP64 oracle) plain vs batched+learned on 1 GB300; % roofline"
+WORKLOAD = ("c2: 100x100-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (19,602 FP32 triangles); "
+            "1e7 FP32 segments, 50% crossing / 50% above, length U(0.05,1), random directions; "
+            "step = lbvh_build + boolean query + intercept_count query")
+BYTES_PER_RAY_COUNT = 28   # 24 B of segment in + 4 B of count out (algorithmic)
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_query_fp32_count_c2.md")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for name in ("query.cu", "rsi_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2305_01867_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """DRAM bytes per launch of the count traversal from the committed ncu
+    summary, if it was taken on the current source (else None)."""
+    try:
+        txt = open(TRAFFIC_SUMMARY).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_hash") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def run_reference(args, ws, rank):
+    """The FP64 oracle as it stands, on this machine's host cores."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import workloads as W
+    oracle.build()
+    mesh = W.config_mesh("c2")
+    spec = W.config_rays("c2")
+    per_step = args.ref_rays
+    times = []
+    for k in range(args.warmup + args.steps):
+        F, E = W.rays(spec, mesh, start=k * per_step, count=per_step)
+        t0 = time.perf_counter()
+        oracle.query(mesh.vertices, mesh.triangles, F, E)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = per_step / (ms / 1e3)
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_triangles": int(len(mesh.triangles)),
+                       "rays_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} segments of the 1e7-segment batch per step, all "
+                                       f"{len(mesh.triangles)} triangles each (brute force, both modes)"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline(mesh, spec, n):
+    import oracle
+    import workloads as W
+    F, E = W.rays(spec, mesh, start=0, count=n)
+    t0 = time.perf_counter()
+    oracle.query(mesh.vertices, mesh.triangles, F, E)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {n} segments of the batch x all {len(mesh.triangles)} triangles, FP64 brute force "
+                      f"(both modes in one pass), {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rays", type=int, default=10_000_000)
+    ap.add_argument("--ref-rays", type=int, default=20_000)
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        if pg:
+            pg.barrier()
+            pg.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2305_01867_gb300 as rsi
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mesh = W.config_mesh("c2")
+    spec = W.config_rays("c2", args.rays)
+    spec.seed = spec.seed + 1000 * rank          # each rank its own batch (weak scaling)
+    F, E = W.rays(spec, mesh)
+    n = len(F)
+    pF, pE = torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory()
+    pV, pT = torch.from_numpy(mesh.vertices).pin_memory(), torch.from_numpy(mesh.triangles).pin_memory()
+    dV, dT = pV.to(dev), pT.to(dev)
+    dF, dE = pF.to(dev), pE.to(dev)
+    hit = torch.empty(n, dtype=torch.uint8, device=dev)
+    amb_h = torch.empty(n, dtype=torch.uint8, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    amb_c = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None, trav=None):
+        if evs:
+            evs[0].record(stream)
+        bvh = rsi.LBVH(dV, dT, morton_bits=30)
+        if evs:
+            evs[1].record(stream)
+        bvh.query(dF, dE, "any_hit", hit=hit, ambiguous=amb_h)
+        if evs:
+            evs[2].record(stream)
+        bvh.query(dF, dE, "count", count=cnt, ambiguous=amb_c, time_kernels=trav is not None)
+        if evs:
+            evs[3].record(stream)
+        if trav is not None:
+            trav.append(bvh.last_query_ms()[0])
+        bvh.close()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    n_ev = args.steps
+    phase = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_ev)]
+    trav = []
+    l0 = rsi.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(phase[k], trav)
+    e1.record(stream)
+    barrier()
+    launches = rsi.kernel_launches() - l0
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1) / args.steps
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n / (ms / 1e3)
+    build_ms = statistics.median(p[0].elapsed_time(p[1]) for p in phase)
+    any_ms = statistics.median(p[1].elapsed_time(p[2]) for p in phase)
+    count_ms = statistics.median(p[2].elapsed_time(p[3]) for p in phase)
+    trav_ms = statistics.mean(trav)
+
+    # end to end through the host-buffer C-ABI calls: mesh and segments in
+    # pinned host memory, results back in pinned host memory, every step
+    hh = torch.empty(n, dtype=torch.uint8).pin_memory()
+    ha = torch.empty(n, dtype=torch.uint8).pin_memory()
+    hc = torch.empty(n, dtype=torch.int32).pin_memory()
+    hac = torch.empty(n, dtype=torch.uint8).pin_memory()
+
+    def step_e2e():
+        bvh = rsi.LBVH(pV, pT, morton_bits=30)
+        bvh.query_host(pF, pE, "any_hit", hit=hh, ambiguous=ha)
+        bvh.query_host(pF, pE, "count", count=hc, ambiguous=hac)
+        bvh.close()
+
+    for _ in range(args.warmup):
+        step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    barrier()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    if pg:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    same = bool(torch.equal(hh, hit.cpu()) and torch.equal(hc, cnt.cpu()))
+    h2d = (pV.numel() * 4 + pT.numel() * 4) + 2 * (pF.numel() + pE.numel()) * 4
+    d2h = n * (1 + 1) + n * (4 + 1)
+
+    # counters of one extra (untimed) pass
+    bvh = rsi.LBVH(dV, dT)
+    st_c = bvh.query(dF, dE, "count", stats=True)["stats"]
+    st_a = bvh.query(dF, dE, "any_hit", stats=True)["stats"]
+    height = bvh.info()["height"]
+    bvh.close()
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_RAY_COUNT * n / (trav_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_triangles": int(len(mesh.triangles)), "rays_per_gpu": n,
+                   "morton_bits": 30, "l2": "inputs larger than L2 (240 MB of segments per batch), no flush",
+                   "fp64_retest": "on (band segments re-tested in FP64)"},
+        "roofline": {"kernel": "k_query_fp32<count> (FP32 traversal, intercept_count)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s",
+                     "traffic": traffic_per_launch(), "algorithmic_bytes_per_ray": BYTES_PER_RAY_COUNT,
+                     "kernel_ms": trav_ms},
+        "e2e": {"value": ws * n / (e2e_ms / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "matches_device_results": same},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "phases_ms": {"build": build_ms, "any_hit_query": any_ms, "count_query": count_ms},
+        "query_rays_per_s": {"any_hit": n / (any_ms / 1e3), "count": n / (count_ms / 1e3)},
+        "counters": {"tree_height": height, "node_visits_per_ray_count": st_c["node_visits"] / n,
+                     "tri_tests_per_ray_count": st_c["tri_tests"] / n, "band_rays_count": st_c["band_rays"],
+                     "ambiguous_count": st_c["ambiguous"], "node_visits_per_ray_any": st_a["node_visits"] / n,
+                     "band_rays_any": st_a["band_rays"], "ambiguous_any": st_a["ambiguous"]},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mesh, W.config_rays("c2"), args.cpu_sample)
+    print(json.dumps(line))
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

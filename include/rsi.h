@@ -1,0 +1,190 @@
+/*
+ * rsi.h -- C ABI of the GB300 (sm_103a) ray-segment / triangle-surface
+ * intersection library (librsi.so).
+ *
+ * The method (R. Leung, "An experience with PyCUDA: Refactoring an existing
+ * implementation of a ray-surface intersection algorithm", 2023):
+ *   build  -- surface extent (Sec. 3.3), Morton codes of triangle centroids
+ *             (Sec. 3.2), sort (Sec. 3.2), binary radix tree (Sec. 1, after
+ *             Karras 2012; Sec. 4.2) and bottom-up bounding boxes (Sec. 4.1,
+ *             4.2), all on the GPU;
+ *   query  -- per-segment BVH search with Moller-Trumbore segment/triangle
+ *             tests (Sec. 1), returning the boolean result or the number of
+ *             crossings (the "boolean" and "intercept_count" modes of Sec. 1).
+ * Tests run in FP32; segments whose FP32 result could differ from an FP64
+ * evaluation (the Epilogue's near-parallel precision loss) are re-tested on
+ * the GPU in FP64.
+ *
+ * Conventions
+ *   - A "segment" (the paper's ray) runs from `from[i]` to `to[i]`; both are
+ *     row-major float32 [n_rays][3].  Vertices are float32 [n_vertices][3];
+ *     triangles are int32 [n_triangles][3] vertex indices (int64 indices are
+ *     a different layout and are not accepted, Sec. 4.1.2).
+ *   - Pointers named d_* are device pointers, h_* host pointers.  The caller
+ *     owns every buffer it passes; the library owns a handle and its buffers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered: a call returns after enqueueing unless
+ *     stated otherwise.  Calls that share a handle must be ordered on one
+ *     stream (they share the handle's scratch memory).
+ *   - Every function returns RSI_OK (0) or a negative RSI_ERR_* code and
+ *     never throws; rsi_last_error() then describes the failure.
+ */
+#ifndef RSI_H_
+#define RSI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSI_OK 0
+#define RSI_ERR_INVALID_ARG (-1) /* null pointer, negative size, bad mode   */
+#define RSI_ERR_DTYPE (-2)       /* element size other than the documented  */
+#define RSI_ERR_OOM (-3)         /* device allocation failed                */
+#define RSI_ERR_CUDA (-4)        /* a CUDA runtime call failed              */
+#define RSI_ERR_TIMEOUT (-5)     /* a bounded device wait ran out           */
+#define RSI_ERR_STACK (-6)       /* tree deeper than the traversal stack    */
+#define RSI_ERR_NAN (-7)         /* NaN vertex coordinate                   */
+#define RSI_ERR_INDEX (-8)       /* triangle vertex index out of range      */
+#define RSI_ERR_OVERFLOW (-9)    /* a bounded per-segment list overflowed   */
+
+/* Query modes (Sec. 1). */
+#define RSI_ANY_HIT 0 /* "boolean": does the segment meet the surface       */
+#define RSI_COUNT 1   /* "intercept_count": number of distinct crossings    */
+
+typedef struct rsi_bvh_s* rsi_bvh_t;
+
+/* Options of a query; a NULL pointer means all defaults (zeros). */
+typedef struct rsi_options {
+    int fp32_only;      /* 1: skip the FP64 re-test (results may flip near
+                           edges and for nearly parallel segments)          */
+    int block;          /* threads per block of the traversal, 0 = tuned    */
+    int blocks_per_sm;  /* resident blocks per SM for the persistent grid,
+                           0 = tuned                                         */
+    int collect_stats;  /* 1: count node visits and triangle tests          */
+    int64_t timeout_ns; /* bounded waits of the batched kernel, 0 = 2 s     */
+    int time_kernels;   /* 1: record CUDA events around the traversal and
+                           re-test kernels on `stream` (rsi_last_query_ms) */
+    int reserved;
+} rsi_options;
+
+/* Per-query counters, filled on the host when a non-NULL pointer is given
+ * (the call then synchronizes `stream`). */
+typedef struct rsi_stats {
+    int64_t n_rays;
+    int64_t node_visits;   /* child-pair nodes fetched (collect_stats only)  */
+    int64_t tri_tests;     /* FP32 segment/triangle tests (collect_stats)    */
+    int64_t band_rays;     /* segments re-tested in FP64                     */
+    int64_t ambiguous;     /* segments left ambiguous by the FP64 re-test    */
+    int32_t tree_height;
+    int32_t device_error;  /* RSI_OK or the RSI_ERR_* a kernel raised        */
+} rsi_stats;
+
+/* Static description of a built hierarchy. */
+typedef struct rsi_bvh_info {
+    int64_t n_triangles;
+    int64_t n_vertices;
+    int32_t morton_bits;
+    int32_t height;          /* edges on the longest root-to-leaf path      */
+    int64_t device_bytes;    /* bytes the handle holds on the device        */
+    float extent_lo[3], extent_hi[3];
+    float max_tri_extent[3]; /* largest triangle box side per axis          */
+} rsi_bvh_info;
+
+/* Host-side copy of the hierarchy for inspection (the BVH dump of Sec.
+ * 4.1.1).  The caller allocates every array with the sizes given
+ * (n = n_triangles); NULL members are skipped.  Internal node i has children
+ * left[i], right[i]: an internal node index, or a leaf j tagged as
+ * (int32)(0x80000000u | j); leaf j holds triangle perm[j].  Numbering follows
+ * Karras 2012: the root is internal node 0.  parent[] lists internal nodes
+ * then leaves (root: -1).  box[] is 6 floats (min xyz, max xyz) per node,
+ * internal nodes then leaves. */
+typedef struct rsi_bvh_host_view {
+    uint64_t* sorted_keys; /* [n]     Morton codes in sorted order          */
+    int32_t* perm;         /* [n]     triangle id of each leaf              */
+    int32_t* left;         /* [n-1]                                         */
+    int32_t* right;        /* [n-1]                                         */
+    int32_t* parent;       /* [2n-1]                                        */
+    float* box;            /* [6(2n-1)]                                     */
+} rsi_bvh_host_view;
+
+/*
+ * Build the hierarchy over a triangle mesh (Sec. 3.2, 3.3, 4.1, 4.2): extent,
+ * Morton codes of the centroids ((v0 + v1) + v2) / 3 in FP32
+ * round-to-nearest, a stable radix sort by (code, triangle id), a Karras
+ * radix tree and bottom-up boxes.
+ *   d_vertices  [n_vertices][3] float32, device; d_triangles [n_triangles][3]
+ *   int32, device.  index_bytes must be 4 (RSI_ERR_DTYPE otherwise: the
+ *   int64 mix-up of Sec. 4.1.2).  morton_bits is 30 or 63.
+ * The inputs are read during the call and may be freed afterwards.  The call
+ * synchronizes `stream` once to check for NaN coordinates (RSI_ERR_NAN) and
+ * out-of-range indices (RSI_ERR_INDEX).  n_triangles >= 1.
+ * On success *out holds a new handle; release it with lbvh_free.
+ */
+int lbvh_build(const float* d_vertices, int64_t n_vertices, const int32_t* d_triangles,
+               int64_t n_triangles, int index_bytes, int morton_bits, void* stream,
+               rsi_bvh_t* out);
+
+/* As lbvh_build, with the mesh in host memory (copied in on `stream`). */
+int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
+                    int64_t n_triangles, int index_bytes, int morton_bits, void* stream,
+                    rsi_bvh_t* out);
+
+/* Release a handle (synchronizes the device first).  NULL is a no-op. */
+int lbvh_free(rsi_bvh_t h);
+
+int lbvh_info(rsi_bvh_t h, rsi_bvh_info* out);
+
+/* Copy the hierarchy to host arrays (synchronizes `stream`). */
+int lbvh_export(rsi_bvh_t h, void* stream, rsi_bvh_host_view* out);
+
+/* sizeof of one packed hierarchy node on the device (the paper's
+ * bytesInBVHNode query, Sec. 3.2: sizes are asked of the library, never
+ * hard-coded). */
+size_t lbvh_node_bytes(void);
+
+/*
+ * Query n_rays segments against the hierarchy (Sec. 1 modes).
+ *   mode RSI_ANY_HIT: d_hit[i] = 1 if segment i meets the surface, else 0.
+ *   mode RSI_COUNT  : d_count[i] = number of distinct crossings; d_hit, if
+ *                     not NULL, gets count > 0.
+ *   d_ambiguous (optional): 1 where the segment lies within the 1e-6
+ *   relative margin band even in FP64 (an end point, edge or vertex on the
+ *   surface, or nearly parallel and touching); those results are the
+ *   closed-interval reading with crossings closer than 1e-9 in t merged.
+ * Segments: d_from, d_to [n_rays][3] float32, device.  n_rays == 0 is a
+ * no-op.  Asynchronous unless `stats` is given.
+ */
+int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
+              const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
+              rsi_stats* stats, void* stream);
+
+/*
+ * As rsi_query with segments and results in HOST memory.  The segments are
+ * streamed to the device in chunks and the results back, with copies and
+ * traversal overlapped on internal streams; returns after the results are
+ * in host memory.  Page-locked host buffers give asynchronous copies.
+ */
+int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n_rays, int mode,
+                   const rsi_options* opt, uint8_t* h_hit, int32_t* h_count, uint8_t* h_ambiguous,
+                   rsi_stats* stats, void* stream);
+
+/* Durations of the FP32 traversal kernel and of the FP64 re-test kernel of
+ * the last query on `h` that ran with time_kernels = 1, from CUDA events
+ * recorded on that query's stream (waits for them).  -1 if none. */
+int rsi_last_query_ms(rsi_bvh_t h, float* traverse_ms, float* retest_ms);
+
+/* Number of kernels this library has launched since it was loaded (all
+ * threads, all devices): lets a caller count the device work of a region. */
+uint64_t rsi_kernel_launches(void);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* rsi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSI_H_ */

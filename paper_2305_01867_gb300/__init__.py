@@ -1,0 +1,255 @@
+"""GB300 (sm_103a) linear-BVH ray-segment / triangle-surface intersection.
+
+A thin binding over the C ABI of ``librsi.so`` (declared in include/rsi.h):
+argument checking and marshalling only -- every step of the build and the
+query runs in the library's CUDA kernels.  PyTorch supplies device memory
+and streams.  If the library is missing this module raises on import; there
+is no CPU fallback.
+
+    import paper_2305_01867_gb300 as rsi
+    bvh = rsi.LBVH(vertices_cuda_f32, triangles_cuda_i32, morton_bits=30)
+    hit = bvh.query(ray_from, ray_to, mode="any_hit")["hit"]       # Sec. 1 boolean
+    cnt = bvh.query(ray_from, ray_to, mode="count")["count"]       # intercept_count
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB as _LIB_PATH
+from .build import build as build_library
+
+RSI_OK = 0
+RSI_ANY_HIT, RSI_COUNT = 0, 1
+LEAF_TAG = 0x80000000
+ERRORS = {-1: "INVALID_ARG", -2: "DTYPE", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "STACK", -7: "NAN",
+          -8: "INDEX", -9: "OVERFLOW"}
+
+
+class RSIError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("fp32_only", ctypes.c_int), ("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("collect_stats", ctypes.c_int), ("timeout_ns", ctypes.c_int64), ("time_kernels", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_rays", ctypes.c_int64), ("node_visits", ctypes.c_int64), ("tri_tests", ctypes.c_int64),
+                ("band_rays", ctypes.c_int64), ("ambiguous", ctypes.c_int64), ("tree_height", ctypes.c_int32),
+                ("device_error", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_triangles", ctypes.c_int64), ("n_vertices", ctypes.c_int64), ("morton_bits", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("extent_lo", ctypes.c_float * 3),
+                ("extent_hi", ctypes.c_float * 3), ("max_tri_extent", ctypes.c_float * 3)]
+
+
+class HostView(ctypes.Structure):
+    _fields_ = [("sorted_keys", ctypes.c_void_p), ("perm", ctypes.c_void_p), ("left", ctypes.c_void_p),
+                ("right", ctypes.c_void_p), ("parent", ctypes.c_void_p), ("box", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"librsi.so is not built ({_LIB_PATH}); run paper_2305_01867_gb300.build_library()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.lbvh_build.argtypes = [P, i64, P, i64, i32, i32, P, ctypes.POINTER(P)]
+    lib.lbvh_build_host.argtypes = [P, i64, P, i64, i32, i32, P, ctypes.POINTER(P)]
+    lib.lbvh_free.argtypes = [P]
+    lib.lbvh_info.argtypes = [P, ctypes.POINTER(Info)]
+    lib.lbvh_export.argtypes = [P, P, ctypes.POINTER(HostView)]
+    lib.lbvh_node_bytes.restype = ctypes.c_size_t
+    lib.lbvh_node_bytes.argtypes = []
+    for f in (lib.rsi_query, lib.rsi_query_host):
+        f.argtypes = [P, P, P, i64, i32, ctypes.POINTER(Options), P, P, P, ctypes.POINTER(Stats), P]
+    lib.rsi_last_query_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    lib.rsi_last_query_ms.restype = ctypes.c_int
+    lib.rsi_kernel_launches.argtypes = []
+    lib.rsi_kernel_launches.restype = ctypes.c_uint64
+    lib.rsi_last_error.restype = ctypes.c_char_p
+    lib.rsi_last_error.argtypes = []
+    for name in ("lbvh_build", "lbvh_build_host", "lbvh_free", "lbvh_info", "lbvh_export", "rsi_query",
+                 "rsi_query_host"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    return lib.rsi_last_error().decode()
+
+
+def check(rc: int):
+    if rc != RSI_OK:
+        raise RSIError(rc, last_error())
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched since it was loaded."""
+    return int(lib.rsi_kernel_launches())
+
+
+def node_bytes() -> int:
+    return int(lib.lbvh_node_bytes())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_f32x3(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 3:
+        raise TypeError(f"{name} must be a float32 tensor of shape [n, 3]")
+    if not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous")
+
+
+def _mode(mode):
+    if mode in ("any_hit", "boolean", RSI_ANY_HIT):
+        return RSI_ANY_HIT
+    if mode in ("count", "intercept_count", RSI_COUNT):
+        return RSI_COUNT
+    raise ValueError(f"unknown mode {mode!r}")
+
+
+class LBVH:
+    """A linear BVH over a triangle mesh, built on the GPU (lbvh_build)."""
+
+    def __init__(self, vertices, triangles, morton_bits: int = 30, stream=None):
+        import torch
+        _check_f32x3(vertices, "vertices")
+        if not isinstance(triangles, torch.Tensor) or triangles.dim() != 2 or triangles.shape[1] != 3:
+            raise TypeError("triangles must be a tensor of shape [n, 3]")
+        index_bytes = triangles.element_size()
+        if triangles.dtype not in (torch.int32, torch.int64):
+            raise TypeError("triangles must hold integer vertex indices")
+        self._h = ctypes.c_void_p()
+        on_dev = vertices.is_cuda
+        if on_dev != triangles.is_cuda:
+            raise TypeError("vertices and triangles must both be on the GPU or both on the host")
+        fn = lib.lbvh_build if on_dev else lib.lbvh_build_host
+        check(fn(_ptr(vertices), vertices.shape[0], _ptr(triangles.contiguous()), triangles.shape[0], index_bytes,
+                 morton_bits, _stream(stream), ctypes.byref(self._h)))
+        self.n_triangles = triangles.shape[0]
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.lbvh_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = Info()
+        check(lib.lbvh_info(self._h, ctypes.byref(inf)))
+        d = {k: getattr(inf, k) for k, _ in Info._fields_}
+        for k in ("extent_lo", "extent_hi", "max_tri_extent"):
+            d[k] = list(d[k])
+        return d
+
+    def export(self, stream=None) -> dict:
+        """Host copy of keys, order, children, parents and boxes (Sec. 4.1.1)."""
+        import numpy as np
+        n = self.n_triangles
+        out = dict(sorted_keys=np.zeros(n, np.uint64), perm=np.zeros(n, np.int32),
+                   left=np.zeros(max(n - 1, 1), np.int32), right=np.zeros(max(n - 1, 1), np.int32),
+                   parent=np.zeros(2 * n - 1, np.int32), box=np.zeros((2 * n - 1, 6), np.float32))
+        v = HostView(*[out[k].ctypes.data for k in ("sorted_keys", "perm", "left", "right", "parent", "box")])
+        check(lib.lbvh_export(self._h, _stream(stream), ctypes.byref(v)))
+        if n == 1:
+            out["left"], out["right"] = out["left"][:0], out["right"][:0]
+        return out
+
+    def last_query_ms(self):
+        """(traversal ms, FP64 re-test ms) of the last query run with time_kernels=True."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        check(lib.rsi_last_query_ms(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def query(self, ray_from, ray_to, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0,
+              stats=False, hit=None, count=None, ambiguous=None, want_ambiguous=True, time_kernels=False,
+              stream=None):
+        """Query segments (device tensors [n, 3] float32).  Returns a dict with
+        'hit' (uint8, any-hit mode or count > 0), 'count' (int32, count mode),
+        'ambiguous' (uint8) and, with stats=True, 'stats'."""
+        import torch
+        _check_f32x3(ray_from, "ray_from")
+        _check_f32x3(ray_to, "ray_to")
+        if ray_from.shape != ray_to.shape:
+            raise ValueError("ray_from and ray_to differ in shape")
+        if not (ray_from.is_cuda and ray_to.is_cuda):
+            raise TypeError("query() takes device tensors; use query_host() for host arrays")
+        m = _mode(mode)
+        n = ray_from.shape[0]
+        dev = ray_from.device
+        if hit is None and m == RSI_ANY_HIT:
+            hit = torch.empty(n, dtype=torch.uint8, device=dev)
+        if count is None and m == RSI_COUNT:
+            count = torch.empty(n, dtype=torch.int32, device=dev)
+        if ambiguous is None and want_ambiguous:
+            ambiguous = torch.empty(n, dtype=torch.uint8, device=dev)
+        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels), 0)
+        st = Stats()
+        check(lib.rsi_query(self._h, _ptr(ray_from), _ptr(ray_to), n, m, ctypes.byref(opt), _ptr(hit), _ptr(count),
+                            _ptr(ambiguous), ctypes.byref(st) if stats else None, _stream(stream)))
+        out = {"hit": hit, "count": count, "ambiguous": ambiguous}
+        if stats:
+            out["stats"] = st.as_dict()
+        return out
+
+    def query_host(self, ray_from, ray_to, mode="any_hit", *, fp32_only=False, stats=False, hit=None, count=None,
+                   ambiguous=None, want_ambiguous=True, stream=None):
+        """As query() with host (preferably pinned) tensors; blocks until the
+        results are in host memory."""
+        import torch
+        _check_f32x3(ray_from, "ray_from")
+        _check_f32x3(ray_to, "ray_to")
+        m = _mode(mode)
+        n = ray_from.shape[0]
+        if hit is None and m == RSI_ANY_HIT:
+            hit = torch.empty(n, dtype=torch.uint8)
+        if count is None and m == RSI_COUNT:
+            count = torch.empty(n, dtype=torch.int32)
+        if ambiguous is None and want_ambiguous:
+            ambiguous = torch.empty(n, dtype=torch.uint8)
+        opt = Options(int(fp32_only), 0, 0, int(stats), 0, 0, 0)
+        st = Stats()
+        check(lib.rsi_query_host(self._h, _ptr(ray_from), _ptr(ray_to), n, m, ctypes.byref(opt), _ptr(hit),
+                                 _ptr(count), _ptr(ambiguous), ctypes.byref(st), _stream(stream)))
+        out = {"hit": hit, "count": count, "ambiguous": ambiguous}
+        if stats:
+            out["stats"] = st.as_dict()
+        return out

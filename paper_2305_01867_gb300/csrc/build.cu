@@ -1,0 +1,618 @@
+// build.cu -- GPU construction of the linear BVH (Sec. 3.2, 3.3, 4.1, 4.2):
+//   k_extent   surface extent (Sec. 3.3, get_min_max_extent_of_surface)
+//   k_morton   30/63-bit Morton codes of triangle centroids (Sec. 3.2; the
+//              paper turned the host createMortonCode into a kernel)
+//   radix sort stable LSD sort of (code, triangle id), 8-bit digits (the
+//              paper sorted on the host with argsort, Sec. 3.2)
+//   k_karras   binary radix tree, one thread per internal node (Karras 2012,
+//              cited in Sec. 1)
+//   k_refit    bottom-up boxes: the second child to arrive at a node (atomic
+//              counter) unions the children and climbs on (Sec. 4.2: a node
+//              left with counter 1 is "half-filled")
+// Every grid is sized from its own element count (the grid-size error of
+// Sec. 4.2.3 is the lesson) and all steps run on the caller's stream.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+
+#include "rsi_internal.cuh"
+
+namespace rsi {
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    unsigned int b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __host__ __forceinline__ float ord2f(unsigned int o) {
+    unsigned int b = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+#endif
+}
+
+__device__ __forceinline__ void raise_error(DevCounters* c, int code) { atomicCAS(&c->error, 0, code); }
+
+__global__ void k_init(DevCounters* c) {
+    if (threadIdx.x == 0) {
+        c->error = 0;
+        c->band_count = 0;
+        c->height = 0;
+        c->node_visits = c->tri_tests = c->ambiguous = 0;
+        for (int a = 0; a < 3; ++a) {
+            c->ext_bits[a] = 0xFFFFFFFFu;   // running min
+            c->ext_bits[3 + a] = 0u;        // running max
+            c->dmax_bits[a] = 0u;
+        }
+    }
+}
+
+// Per-axis min / max over all vertices; NaN raises RSI_ERR_NAN.
+__global__ void k_extent(const float* __restrict__ V, int64_t nv, DevCounters* c) {
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool nan = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float x = __ldg(V + 3 * i + a);
+            nan |= (x != x);
+            mn[a] = fminf(mn[a], x);
+            mx[a] = fmaxf(mx[a], x);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], off));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], off));
+        }
+    if (__any_sync(0xffffffffu, nan) && (threadIdx.x & 31) == 0) raise_error(c, RSI_ERR_NAN);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (mn[a] <= mx[a]) {
+                atomicMin(&c->ext_bits[a], f2ord(mn[a]));
+                atomicMax(&c->ext_bits[3 + a], f2ord(mx[a]));
+            }
+        }
+    }
+}
+
+// Spread the low bits of q so that bit i lands on bit 3i.
+__device__ __forceinline__ uint32_t spread10(uint32_t x) {
+    x &= 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+__device__ __forceinline__ uint64_t spread21(uint64_t x) {
+    x &= 0x1FFFFFull;
+    x = (x | (x << 32)) & 0x001F00000000FFFFull;
+    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+template <typename K>
+struct MortonTraits;
+template <>
+struct MortonTraits<uint32_t> {
+    static constexpr int kBitsPerAxis = 10;
+    static __device__ __forceinline__ uint32_t encode(uint32_t x, uint32_t y, uint32_t z) {
+        return spread10(x) | (spread10(y) << 1) | (spread10(z) << 2);
+    }
+};
+template <>
+struct MortonTraits<uint64_t> {
+    static constexpr int kBitsPerAxis = 21;
+    static __device__ __forceinline__ uint64_t encode(uint32_t x, uint32_t y, uint32_t z) {
+        return spread21(x) | (spread21(y) << 1) | (spread21(z) << 2);
+    }
+};
+
+// Morton code of triangle j: centroid ((v0 + v1) + v2) / 3, normalised per
+// axis by the extent, clamped to [0, 1], truncated to b bits; z is the high
+// bit of every 3-bit group.  Explicit round-to-nearest intrinsics keep the
+// compiler from fusing any multiply-add, so the code is the same on any host
+// that evaluates the same IEEE operations.
+template <typename K>
+__global__ void k_morton(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T, int64_t nt,
+                         DevCounters* c, K* __restrict__ keys, int32_t* __restrict__ ids) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nt) return;
+    const int b = MortonTraits<K>::kBitsPerAxis;
+    const float scale = (float)(1u << b);
+    const uint32_t qmax = (1u << b) - 1u;
+    int32_t i0 = __ldg(T + 3 * j), i1 = __ldg(T + 3 * j + 1), i2 = __ldg(T + 3 * j + 2);
+    ids[j] = (int32_t)j;
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
+        raise_error(c, RSI_ERR_INDEX);
+        keys[j] = 0;
+        return;
+    }
+    uint32_t q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float lo = ord2f(c->ext_bits[a]), hi = ord2f(c->ext_bits[3 + a]);
+        float x0 = __ldg(V + 3 * (int64_t)i0 + a), x1 = __ldg(V + 3 * (int64_t)i1 + a), x2 = __ldg(V + 3 * (int64_t)i2 + a);
+        float cen = __fdiv_rn(__fadd_rn(__fadd_rn(x0, x1), x2), 3.0f);
+        float u = (hi != lo) ? __fdiv_rn(__fsub_rn(cen, lo), __fsub_rn(hi, lo)) : 0.0f;
+        u = fminf(fmaxf(u, 0.0f), 1.0f);
+        uint32_t qq = __float2uint_rz(__fmul_rn(u, scale));
+        q[a] = qq > qmax ? qmax : qq;
+    }
+    keys[j] = MortonTraits<K>::encode(q[0], q[1], q[2]);
+}
+
+// ---------------------------------------------------------------- radix sort
+// One LSD pass over 8-bit digit `shift`: per-tile histograms (digit-major so
+// a single exclusive scan yields every tile's scatter base), then a stable
+// scatter that ranks keys inside the tile in index order.
+constexpr int kSortTile = 4096;   // keys per block (16 rounds of 256)
+
+template <typename K>
+__global__ void k_rs_hist(const K* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist, int ntiles) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+    int64_t end = min(base + (int64_t)kSortTile, n);
+    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
+        atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Exclusive scan of m words by one block of 1024 threads.
+__global__ void k_rs_scan(uint32_t* __restrict__ h, int64_t m) {
+    __shared__ uint32_t part[1024];
+    int64_t per = (m + blockDim.x - 1) / blockDim.x;
+    int64_t b = threadIdx.x * per, e = min(b + per, m);
+    uint32_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += h[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int64_t i = b; i < e; ++i) {
+        uint32_t v = h[i];
+        h[i] = run;
+        run += v;
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_rs_scatter(const K* __restrict__ kin, const int32_t* __restrict__ vin,
+                                                    K* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
+                                                    int shift, const uint32_t* __restrict__ hist, int ntiles) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[8][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    base[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortTile / 256; ++r) {
+        int64_t i = tile0 + r * 256 + threadIdx.x;
+        bool valid = i < n;
+        K key = valid ? kin[i] : K(0);
+        uint32_t dig = valid ? ((uint32_t)(key >> shift) & 255u) : 256u + lane;   // invalid lanes never match
+#pragma unroll
+        for (int w = 0; w < 8; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        uint32_t peers = __match_any_sync(0xffffffffu, dig);
+        uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[warp][dig] = __popc(peers);
+        __syncthreads();
+        // exclusive prefix over warps for digit threadIdx.x; total goes to base
+        {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                uint32_t v = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = run;
+                run += v;
+            }
+            __syncthreads();
+            if (valid) {
+                uint32_t pos = base[dig] + wcnt[warp][dig] + rank;
+                kout[pos] = key;
+                vout[pos] = vin[i];
+            }
+            __syncthreads();
+            base[threadIdx.x] += run;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- radix tree
+template <typename K>
+struct KeyBits;
+template <>
+struct KeyBits<uint32_t> {
+    static __device__ __forceinline__ int clz(uint32_t x) { return __clz(x); }
+    static constexpr int kWidth = 32;
+};
+template <>
+struct KeyBits<uint64_t> {
+    static __device__ __forceinline__ int clz(uint64_t x) { return __clzll(x); }
+    static constexpr int kWidth = 64;
+};
+
+// Length of the common prefix of the keys at i and j, with the index appended
+// below the key so that equal keys still differ; -1 outside [0, n).
+template <typename K>
+__device__ __forceinline__ int delta(const K* __restrict__ k, int64_t n, int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    K a = k[i], b = k[j];
+    if (a == b) return KeyBits<K>::kWidth + __clz((uint32_t)i ^ (uint32_t)j);
+    return KeyBits<K>::clz(a ^ b);
+}
+
+// Internal node i (Karras 2012): find the direction of its range, the other
+// end j by an exponential then binary search on the common-prefix length,
+// and the split gamma by a binary search; children are gamma and gamma + 1,
+// leaves when they coincide with an end of the range.
+template <typename K>
+__global__ void k_karras(const K* __restrict__ k, int64_t n, int32_t* __restrict__ left, int32_t* __restrict__ right,
+                         int32_t* __restrict__ parent) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = delta(k, n, i, i - d);
+    int64_t lmax = 2;
+    while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    int64_t j = i + l * d;
+    int dnode = delta(k, n, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int64_t g = i + s * d + (d < 0 ? -1 : 0);
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    int32_t lc, rc;
+    if (lo == g) { lc = (int32_t)(kLeafTag | (uint32_t)g); parent[n - 1 + g] = (int32_t)i; }
+    else { lc = (int32_t)g; parent[g] = (int32_t)i; }
+    if (hi == g + 1) { rc = (int32_t)(kLeafTag | (uint32_t)(g + 1)); parent[n - 1 + g + 1] = (int32_t)i; }
+    else { rc = (int32_t)(g + 1); parent[g + 1] = (int32_t)i; }
+    left[i] = lc;
+    right[i] = rc;
+    if (i == 0) parent[0] = -1;
+}
+
+// ---------------------------------------------------------------- refit
+__device__ __forceinline__ int64_t box_slot(int32_t ref, int64_t n) {
+    return ((uint32_t)ref & kLeafTag) ? (n - 1 + (int64_t)((uint32_t)ref & ~kLeafTag)) : (int64_t)ref;
+}
+__device__ __forceinline__ int packed_ref(int32_t ref) {
+    return ((uint32_t)ref & kLeafTag) ? ~(int)((uint32_t)ref & ~kLeafTag) : (int)ref;
+}
+
+// Leaf j: pack triangle perm[j] and its box, then climb: the first thread to
+// reach a node stops, the second (both child boxes final) writes the node.
+__global__ void k_refit(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T,
+                        const int32_t* __restrict__ perm, int64_t n, const int32_t* __restrict__ left,
+                        const int32_t* __restrict__ right, const int32_t* __restrict__ parent,
+                        float* __restrict__ box, int32_t* __restrict__ hgt, int32_t* __restrict__ flag,
+                        Node* __restrict__ nodes, Tri* __restrict__ tris, DevCounters* c) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int32_t t = perm[j];
+    int32_t i0 = T[3 * (int64_t)t], i1 = T[3 * (int64_t)t + 1], i2 = T[3 * (int64_t)t + 2];
+    float v[3][3];
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
+        raise_error(c, RSI_ERR_INDEX);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[0][a] = v[1][a] = v[2][a] = 0.0f;
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            v[0][a] = V[3 * (int64_t)i0 + a];
+            v[1][a] = V[3 * (int64_t)i1 + a];
+            v[2][a] = V[3 * (int64_t)i2 + a];
+        }
+    }
+    Tri tr;
+    tr.v0 = make_float4(v[0][0], v[0][1], v[0][2], __int_as_float(t));
+    tr.v1 = make_float4(v[1][0], v[1][1], v[1][2], 0.0f);
+    tr.v2 = make_float4(v[2][0], v[2][1], v[2][2], 0.0f);
+    tris[j] = tr;
+    float* bx = box + 6 * (n - 1 + j);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float mn = fminf(fminf(v[0][a], v[1][a]), v[2][a]);
+        float mx = fmaxf(fmaxf(v[0][a], v[1][a]), v[2][a]);
+        bx[a] = mn;
+        bx[3 + a] = mx;
+        atomicMax(&c->dmax_bits[a], __float_as_uint(mx - mn));   // >= 0: uint order = float order
+    }
+    hgt[n - 1 + j] = 0;
+    if (n == 1) return;
+    int32_t node = parent[n - 1 + j];
+    while (node >= 0) {
+        __threadfence();
+        if (atomicAdd(&flag[node], 1) == 0) return;
+        __threadfence();
+        int32_t lc = left[node], rc = right[node];
+        int64_t sl = box_slot(lc, n), sr = box_slot(rc, n);
+        float bl[6], br[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            bl[a] = __ldcg(box + 6 * sl + a);
+            br[a] = __ldcg(box + 6 * sr + a);
+        }
+        int h = 1 + max(__ldcg(hgt + sl), __ldcg(hgt + sr));
+        float* bn = box + 6 * (int64_t)node;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bn[a] = fminf(bl[a], br[a]);
+            bn[3 + a] = fmaxf(bl[3 + a], br[3 + a]);
+        }
+        hgt[node] = h;
+        Node nd;
+        nd.lmin = make_float4(bl[0], bl[1], bl[2], __int_as_float(packed_ref(lc)));
+        nd.lmax = make_float4(bl[3], bl[4], bl[5], __int_as_float(packed_ref(rc)));
+        nd.rmin = make_float4(br[0], br[1], br[2], 0.0f);
+        nd.rmax = make_float4(br[3], br[4], br[5], 0.0f);
+        nodes[node] = nd;
+        if (node == 0) c->height = h;
+        node = parent[node];
+    }
+}
+
+template <typename K>
+int sort_pairs(K* ka, int32_t* va, K* kb, int32_t* vb, int64_t n, int passes, uint32_t* hist, cudaStream_t s,
+               K** out_k, int32_t** out_v) {
+    int ntiles = grid_for(n, kSortTile);
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_rs_hist<K><<<ntiles, 256, 0, s>>>(ka, n, shift, hist, ntiles);
+        k_rs_scan<<<1, 1024, 0, s>>>(hist, (int64_t)256 * ntiles);
+        k_rs_scatter<K><<<ntiles, 256, 0, s>>>(ka, va, kb, vb, n, shift, hist, ntiles);
+        note_launches(3);
+        K* tk = ka; ka = kb; kb = tk;
+        int32_t* tv = va; va = vb; vb = tv;
+    }
+    *out_k = ka;
+    *out_v = va;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RSI_OK : rsi::cuda_fail(e, "radix sort launch");
+}
+
+template <typename K>
+int build_impl(rsi_bvh_s* h, const float* V, const int32_t* T, cudaStream_t s, char* scratch) {
+    const int64_t n = h->n_tri;
+    K* ka = (K*)scratch;
+    K* kb = ka + n;
+    int32_t* va = (int32_t*)(kb + n);
+    int32_t* vb = va + n;
+    uint32_t* hist = (uint32_t*)(vb + n);
+    k_morton<K><<<grid_for(n, kBlock), kBlock, 0, s>>>(V, h->n_vert, T, n, h->ctr, ka, va);
+    note_launches(1);
+    const int passes = sizeof(K) == 4 ? 4 : 8;   // 30-bit codes: 4 digits; 63-bit: 8
+    K* sk;
+    int32_t* sv;
+    int rc = sort_pairs<K>(ka, va, kb, vb, n, passes, hist, s, &sk, &sv);
+    if (rc) return rc;
+    RSI_CUDA_TRY(cudaMemcpyAsync(h->sorted_keys, sk, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
+    RSI_CUDA_TRY(cudaMemcpyAsync(h->perm, sv, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (n > 1) {
+        k_karras<K><<<grid_for(n - 1, kBlock), kBlock, 0, s>>>((const K*)h->sorted_keys, n, h->left, h->right,
+                                                                h->parent);
+        note_launches(1);
+    } else
+        RSI_CUDA_TRY(cudaMemsetAsync(h->parent, 0xFF, sizeof(int32_t), s));
+    return RSI_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, int morton_bits, cudaStream_t s,
+                      rsi_bvh_t* out) {
+    rsi_bvh_s* h = new rsi_bvh_s();
+    h->n_tri = nt;
+    h->n_vert = nv;
+    h->morton_bits = morton_bits;
+    const int64_t n = nt, ni = n > 1 ? n - 1 : 1;
+    const size_t ksz = morton_bits == 30 ? 4 : 8;
+    const int ntiles = grid_for(n, 4096);
+    // one allocation, carved into the handle's arrays (256-byte aligned)
+    size_t off[12], total = 0;
+    size_t sizes[12] = {
+        sizeof(Node) * (size_t)ni,                 // 0 nodes
+        sizeof(Tri) * (size_t)n,                   // 1 tris
+        ksz * (size_t)n,                           // 2 sorted keys
+        4 * (size_t)n,                             // 3 perm
+        4 * (size_t)ni,                            // 4 left
+        4 * (size_t)ni,                            // 5 right
+        4 * (size_t)(2 * n - 1),                   // 6 parent
+        24 * (size_t)(2 * n - 1),                  // 7 box
+        4 * (size_t)(2 * n - 1),                   // 8 heights
+        4 * (size_t)ni,                            // 9 flags
+        sizeof(DevCounters),                       // 10 counters
+        2 * ksz * (size_t)n + 8 * (size_t)n + 4 * 256 * (size_t)ntiles   // 11 sort scratch
+    };
+    for (int i = 0; i < 12; ++i) {
+        off[i] = total;
+        total += align_up(sizes[i]);
+    }
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) {
+        delete h;
+        cudaGetLastError();
+        return fail(RSI_ERR_OOM, "lbvh_build: cudaMalloc of " + std::to_string(total) + " bytes failed");
+    }
+    h->device_bytes = (int64_t)total;
+    h->nodes = (Node*)(base + off[0]);
+    h->tris = (Tri*)(base + off[1]);
+    h->sorted_keys = base + off[2];
+    h->perm = (int32_t*)(base + off[3]);
+    h->left = (int32_t*)(base + off[4]);
+    h->right = (int32_t*)(base + off[5]);
+    h->parent = (int32_t*)(base + off[6]);
+    h->box = (float*)(base + off[7]);
+    int32_t* hgt = (int32_t*)(base + off[8]);
+    int32_t* flag = (int32_t*)(base + off[9]);
+    h->ctr = (DevCounters*)(base + off[10]);
+    char* scratch = base + off[11];
+    if (cudaMallocHost(&h->h_ctr, sizeof(DevCounters)) != cudaSuccess) {
+        cudaFree(base);
+        delete h;
+        cudaGetLastError();
+        return fail(RSI_ERR_OOM, "lbvh_build: cudaMallocHost failed");
+    }
+    auto cleanup = [&](int code) {
+        cudaFree(base);
+        cudaFreeHost(h->h_ctr);
+        delete h;
+        return code;
+    };
+    k_init<<<1, 32, 0, s>>>(h->ctr);
+    note_launches(3);   // k_init, k_extent, k_refit
+    k_extent<<<grid_for(nv, kBlock) < 4 * 152 ? grid_for(nv, kBlock) : 4 * 152, kBlock, 0, s>>>(V, nv, h->ctr);
+    if (cudaMemsetAsync(flag, 0, 4 * (size_t)ni, s) != cudaSuccess) return cleanup(cuda_fail(cudaGetLastError(), "memset"));
+    int rc = morton_bits == 30 ? build_impl<uint32_t>(h, V, T, s, scratch) : build_impl<uint64_t>(h, V, T, s, scratch);
+    if (rc) return cleanup(rc);
+    k_refit<<<grid_for(n, kBlock), kBlock, 0, s>>>(V, nv, T, h->perm, n, h->left, h->right, h->parent, h->box, hgt,
+                                                   flag, h->nodes, h->tris, h->ctr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "lbvh_build kernels"));
+    e = cudaMemcpyAsync(h->h_ctr, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "lbvh_build"));
+    const DevCounters& hc = *h->h_ctr;
+    if (hc.error) {
+        return cleanup(fail(hc.error, hc.error == RSI_ERR_NAN ? "lbvh_build: NaN vertex coordinate"
+                                                             : "lbvh_build: triangle vertex index out of range"));
+    }
+    h->height = hc.height;
+    for (int a = 0; a < 3; ++a) {
+        h->lo[a] = ord2f(hc.ext_bits[a]);
+        h->hi[a] = ord2f(hc.ext_bits[3 + a]);
+        float f;
+        std::memcpy(&f, &hc.dmax_bits[a], 4);
+        h->dmax[a] = f;
+    }
+    *out = h;
+    return RSI_OK;
+}
+
+}  // namespace rsi
+
+extern "C" int lbvh_build(const float* d_vertices, int64_t n_vertices, const int32_t* d_triangles,
+                          int64_t n_triangles, int index_bytes, int morton_bits, void* stream, rsi_bvh_t* out) {
+    if (!out) return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build: out is NULL");
+    *out = nullptr;
+    if (index_bytes != 4)
+        return rsi::fail(RSI_ERR_DTYPE, "lbvh_build: triangle indices must be int32 (index_bytes = 4), got " +
+                                            std::to_string(index_bytes) + " bytes");
+    if (!d_vertices || !d_triangles) return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build: NULL input pointer");
+    if (n_triangles < 1 || n_vertices < 1 || n_triangles > (int64_t)0x3FFFFFFF || n_vertices > ((int64_t)1 << 31))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build: need 1 <= n_triangles < 2^30 and 1 <= n_vertices <= 2^31");
+    if (morton_bits != 30 && morton_bits != 63)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build: morton_bits must be 30 or 63");
+    return rsi::build_from_device(d_vertices, n_vertices, d_triangles, n_triangles, morton_bits,
+                                  (cudaStream_t)stream, out);
+}
+
+extern "C" int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
+                               int64_t n_triangles, int index_bytes, int morton_bits, void* stream, rsi_bvh_t* out) {
+    if (!out) return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_host: out is NULL");
+    *out = nullptr;
+    if (!h_vertices || !h_triangles || n_vertices < 1 || n_triangles < 1)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_host: bad input");
+    if (index_bytes != 4) return rsi::fail(RSI_ERR_DTYPE, "lbvh_build_host: triangle indices must be int32");
+    cudaStream_t s = (cudaStream_t)stream;
+    float* dv = nullptr;
+    int32_t* dt = nullptr;
+    size_t bv = 12 * (size_t)n_vertices, bt = 12 * (size_t)n_triangles;
+    if (cudaMallocAsync(&dv, bv, s) != cudaSuccess || cudaMallocAsync(&dt, bt, s) != cudaSuccess) {
+        if (dv) cudaFreeAsync(dv, s);
+        cudaGetLastError();
+        return rsi::fail(RSI_ERR_OOM, "lbvh_build_host: staging allocation failed");
+    }
+    int rc = RSI_OK;
+    if (cudaMemcpyAsync(dv, h_vertices, bv, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dt, h_triangles, bt, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = rsi::cuda_fail(cudaGetLastError(), "lbvh_build_host copy");
+    if (rc == RSI_OK) rc = lbvh_build(dv, n_vertices, dt, n_triangles, 4, morton_bits, stream, out);
+    cudaFreeAsync(dv, s);
+    cudaFreeAsync(dt, s);
+    return rc;
+}
+
+extern "C" int lbvh_free(rsi_bvh_t h) {
+    if (!h) return RSI_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->nodes);   // base of the single allocation
+    if (h->band_ids) cudaFree(h->band_ids);
+    cudaFreeHost(h->h_ctr);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+    return RSI_OK;
+}
+
+extern "C" int lbvh_info(rsi_bvh_t h, rsi_bvh_info* out) {
+    if (!h || !out) return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_info: NULL argument");
+    out->n_triangles = h->n_tri;
+    out->n_vertices = h->n_vert;
+    out->morton_bits = h->morton_bits;
+    out->height = h->height;
+    out->device_bytes = h->device_bytes + 4 * h->band_cap;
+    for (int a = 0; a < 3; ++a) {
+        out->extent_lo[a] = h->lo[a];
+        out->extent_hi[a] = h->hi[a];
+        out->max_tri_extent[a] = h->dmax[a];
+    }
+    return RSI_OK;
+}
+
+extern "C" int lbvh_export(rsi_bvh_t h, void* stream, rsi_bvh_host_view* v) {
+    if (!h || !v) return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_export: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = h->n_tri;
+    RSI_CUDA_TRY(cudaStreamSynchronize(s));
+    if (v->sorted_keys) {
+        if (h->morton_bits == 30) {
+            uint32_t* tmp = new uint32_t[n];
+            cudaError_t e = cudaMemcpy(tmp, h->sorted_keys, 4 * n, cudaMemcpyDeviceToHost);
+            for (int64_t i = 0; i < n; ++i) v->sorted_keys[i] = tmp[i];
+            delete[] tmp;
+            RSI_CUDA_TRY(e);
+        } else {
+            RSI_CUDA_TRY(cudaMemcpy(v->sorted_keys, h->sorted_keys, 8 * n, cudaMemcpyDeviceToHost));
+        }
+    }
+    if (v->perm) RSI_CUDA_TRY(cudaMemcpy(v->perm, h->perm, 4 * n, cudaMemcpyDeviceToHost));
+    if (n > 1 && v->left) RSI_CUDA_TRY(cudaMemcpy(v->left, h->left, 4 * (n - 1), cudaMemcpyDeviceToHost));
+    if (n > 1 && v->right) RSI_CUDA_TRY(cudaMemcpy(v->right, h->right, 4 * (n - 1), cudaMemcpyDeviceToHost));
+    if (v->parent) RSI_CUDA_TRY(cudaMemcpy(v->parent, h->parent, 4 * (2 * n - 1), cudaMemcpyDeviceToHost));
+    if (v->box) RSI_CUDA_TRY(cudaMemcpy(v->box, h->box, 24 * (2 * n - 1), cudaMemcpyDeviceToHost));
+    return RSI_OK;
+}
+
+extern "C" size_t lbvh_node_bytes(void) { return sizeof(rsi::Node); }

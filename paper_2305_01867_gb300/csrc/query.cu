@@ -1,0 +1,671 @@
+// query.cu -- per-segment BVH search with Moller-Trumbore tests (Sec. 1:
+// the tree yields candidate triangles, each tested with Moller-Trumbore;
+// boolean and intercept_count modes), in two passes:
+//
+//  k_query_fp32  one thread per segment (grid-stride over a persistent grid):
+//                stack traversal of the child-pair nodes with a padded,
+//                outward-rounded slab test, and an FP32 Moller test that
+//                carries a forward error bound.  Each pair comes out as a
+//                certain decisive hit, a certain decisive miss, or "band"
+//                (the FP32 value is too close to a decision boundary or to
+//                the 1e-6 margin to be trusted, the Epilogue's concern).
+//                Segments with a band pair and no certain answer are queued.
+//  k_query_fp64  re-traverses the queued segments and classifies every
+//                candidate pair in FP64 exactly as the definition does
+//                (decisive hit / decisive miss / ambiguous, margin 1e-6).
+//
+// Culling never drops a pair that could be a hit or ambiguous: node boxes
+// are padded by 4e-6 (|d|_1 + the largest triangle extent), which covers
+// the margin band, and the slab interval is widened by 1e-6 relative, which
+// covers FP32 rounding of the slab arithmetic.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "rsi_internal.cuh"
+
+namespace rsi {
+
+struct QueryArgs {
+    const Node* nodes;
+    const Tri* tris;
+    int64_t n_tri;
+    const float* from;
+    const float* to;
+    int64_t n_rays;
+    uint8_t* hit;
+    int32_t* count;
+    uint8_t* amb;
+    int32_t* band_ids;
+    DevCounters* ctr;
+    float dmax0, dmax1, dmax2;
+    int fp32_only;
+};
+
+namespace {
+
+constexpr float kU = 5.9604645e-8f;        // unit roundoff of FP32, 2^-24
+constexpr float kErrK = 16.0f * kU;        // bound factor of a dot(cross) in FP32
+constexpr float kTauHi = 1.000001e-6f;     // tau, rounded up
+constexpr float kWiden = 1e-6f;            // relative widening of slab intervals
+
+enum { kMiss = 0, kHit = 1, kBand = 2 };
+
+struct SegF {
+    float3 s, d, inv, slo, shi;   // slo = s + pad (up), shi = s - pad (down)
+    float dl1;                    // |d|_1
+};
+
+__device__ __forceinline__ float safe_inv(float x) {
+    return fabsf(x) < 1e-20f ? copysignf(1e20f, x) : 1.0f / x;
+}
+
+__device__ __forceinline__ SegF make_seg(float3 s, float3 e, float dmx, float dmy, float dmz) {
+    SegF g;
+    g.s = s;
+    g.d = make_float3(e.x - s.x, e.y - s.y, e.z - s.z);
+    g.inv = make_float3(safe_inv(g.d.x), safe_inv(g.d.y), safe_inv(g.d.z));
+    g.dl1 = fabsf(g.d.x) + fabsf(g.d.y) + fabsf(g.d.z);
+    const float k = 4.0f * kTauHi;
+    float px = __fmul_ru(k, __fadd_ru(g.dl1, dmx));
+    float py = __fmul_ru(k, __fadd_ru(g.dl1, dmy));
+    float pz = __fmul_ru(k, __fadd_ru(g.dl1, dmz));
+    g.slo = make_float3(__fadd_ru(s.x, px), __fadd_ru(s.y, py), __fadd_ru(s.z, pz));
+    g.shi = make_float3(__fsub_rd(s.x, px), __fsub_rd(s.y, py), __fsub_rd(s.z, pz));
+    return g;
+}
+
+// Does the segment pass through the padded box?  The padded slab [lo - pad,
+// hi + pad] becomes parameters (lo - (s + pad)) / d and (hi - (s - pad)) / d
+// with the shifted origins rounded outward; the interval is then widened.
+__device__ __forceinline__ bool slab(const float4& bmin, const float4& bmax, const SegF& g) {
+    float t0x = (bmin.x - g.slo.x) * g.inv.x, t1x = (bmax.x - g.shi.x) * g.inv.x;
+    float t0y = (bmin.y - g.slo.y) * g.inv.y, t1y = (bmax.y - g.shi.y) * g.inv.y;
+    float t0z = (bmin.z - g.slo.z) * g.inv.z, t1z = (bmax.z - g.shi.z) * g.inv.z;
+    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
+    tn = tn - fabsf(tn) * kWiden;
+    tf = tf + fabsf(tf) * kWiden;
+    return tn <= tf && tn <= 1.0f && tf >= 0.0f;
+}
+
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 f3(const float4& v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 abs3(float3 a) { return make_float3(fabsf(a.x), fabsf(a.y), fabsf(a.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+// |a| x |b| with every product added: bounds the magnitude of each term.
+__device__ __forceinline__ float3 cross_abs(float3 a, float3 b) {
+    return make_float3(a.y * b.z + a.z * b.y, a.z * b.x + a.x * b.z, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// FP32 Moller-Trumbore with forward error bounds.  With d, e1, e2, sv each
+// rounded once and every quantity a dot of a cross, |fl(x) - x| <= 8 u M_x
+// where M_x is the same expression in absolute values; kErrK doubles that.
+// Decisions are taken on the numerators against the denominator so the
+// bounds stay linear:  u > tau  <=>  sign(det) U > tau |det|,  etc.
+__device__ __forceinline__ int tri_fp32(const SegF& g, const Tri& tr, bool want_plain, bool& plain_hit) {
+    float3 a = f3(tr.v0);
+    float3 e1 = sub3(f3(tr.v1), a), e2 = sub3(f3(tr.v2), a);
+    float3 sv = sub3(g.s, a);
+    float3 p = cross3(g.d, e2);
+    float det = dot3(e1, p);
+    float3 q = cross3(sv, e1);
+    float T = dot3(e2, q);
+    float3 ad = abs3(g.d), ae1 = abs3(e1), ae2 = abs3(e2), asv = abs3(sv);
+    float3 pa = cross_abs(ad, ae2), qa = cross_abs(asv, ae1);
+    float errdet = kErrK * dot3(ae1, pa) + 1e-35f;
+    float errT = kErrK * dot3(ae2, qa) + 1e-35f;
+    // tau * |d| |e1| |e2| bounded above with 1-norms (no square roots)
+    float thr = kTauHi * (g.dl1 * (ae1.x + ae1.y + ae1.z)) * (ae2.x + ae2.y + ae2.z) * 1.000001f;
+    float Tm = T - det;
+    float errTm = errT + errdet + 2.0f * kU * (fabsf(T) + fabsf(det));
+    float U = dot3(sv, p), V = dot3(g.d, q);
+    plain_hit = false;
+    if (want_plain && det != 0.0f) {   // the uncorrected FP32 decision (fp32_only)
+        float u = U / det, v = V / det, t = T / det;
+        plain_hit = u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t >= 0.0f && t <= 1.0f;
+    }
+    // both end points strictly on one side of the plane, farther than
+    // tau |d| |n| (|n| <= |e1||e2|): a decisive miss on either branch
+    if ((T > 0.0f) == (Tm > 0.0f) && fminf(fabsf(T) - errT, fabsf(Tm) - errTm) > thr) return kMiss;
+    float D = fabsf(det);
+    if (D - errdet > thr) {   // |det_rel| > tau for certain
+        float sg = det > 0.0f ? 1.0f : -1.0f;
+        float errU = kErrK * dot3(asv, pa) + 1e-35f;
+        float errV = kErrK * dot3(ad, qa) + 1e-35f;
+        float Us = sg * U, Vs = sg * V, Ts = sg * T;
+        float Ws = D - Us - Vs;
+        float errW = errdet + errU + errV + 2.0f * kU * (D + fabsf(U) + fabsf(V));
+        float Tms = D - Ts;
+        float lim = kTauHi * (D + errdet) * 1.000001f;
+        if (Us - errU > lim && Vs - errV > lim && Ws - errW > lim && Ts - errT > lim && Tms - errTm > lim)
+            return kHit;
+        if (Us + errU < -lim || Vs + errV < -lim || Ws + errW < -lim || Ts + errT < -lim || Tms + errTm < -lim)
+            return kMiss;
+    }
+    return kBand;
+}
+
+__device__ __forceinline__ void load_node(const Node* __restrict__ nodes, int i, float4& a, float4& b, float4& c,
+                                          float4& d) {
+    const float4* p = reinterpret_cast<const float4*>(nodes + i);
+    a = __ldg(p);
+    b = __ldg(p + 1);
+    c = __ldg(p + 2);
+    d = __ldg(p + 3);
+}
+
+__device__ __forceinline__ Tri load_tri(const Tri* __restrict__ tris, int j) {
+    const float4* p = reinterpret_cast<const float4*>(tris + j);
+    Tri t;
+    t.v0 = __ldg(p);
+    t.v1 = __ldg(p + 1);
+    t.v2 = __ldg(p + 2);
+    return t;
+}
+
+__device__ __forceinline__ void raise_error(DevCounters* c, int code) { atomicCAS(&c->error, 0, code); }
+
+__device__ __forceinline__ bool bad3(float3 a) {
+    return !(isfinite(a.x) && isfinite(a.y) && isfinite(a.z));
+}
+
+// The traversal shared by both passes: visits every leaf whose padded box
+// the segment crosses, calling leaf(j) -> true to stop early.  Returns false
+// on stack overflow.
+template <int STACK, bool STATS, typename Leaf>
+__device__ __forceinline__ bool traverse(const QueryArgs& A, const SegF& g, Leaf&& leaf, unsigned long long& visits) {
+    if (A.n_tri == 1) {
+        leaf(0);
+        return true;
+    }
+    int stack[STACK];
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        float4 lmin, lmax, rmin, rmax;
+        load_node(A.nodes, node, lmin, lmax, rmin, rmax);
+        if (STATS) ++visits;
+        int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
+        bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
+        if (hl && lref < 0) {
+            hl = false;
+            if (leaf(~lref)) return true;
+        }
+        if (hr && rref < 0) {
+            hr = false;
+            if (leaf(~rref)) return true;
+        }
+        if (hl && hr) {
+            if (sp >= STACK) return false;
+            stack[sp++] = rref;
+            node = lref;
+        } else if (hl) {
+            node = lref;
+        } else if (hr) {
+            node = rref;
+        } else {
+            if (sp == 0) return true;
+            node = stack[--sp];
+        }
+    }
+}
+
+template <int MODE, bool STATS, int STACK>
+__global__ void __launch_bounds__(256) k_query_fp32(QueryArgs A) {
+    unsigned long long visits = 0, tests = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n_rays; r += stride) {
+        float3 s = make_float3(__ldg(A.from + 3 * r), __ldg(A.from + 3 * r + 1), __ldg(A.from + 3 * r + 2));
+        float3 e = make_float3(__ldg(A.to + 3 * r), __ldg(A.to + 3 * r + 1), __ldg(A.to + 3 * r + 2));
+        if (bad3(s) || bad3(e)) {   // undefined answer: report it as ambiguous
+            if (A.hit) A.hit[r] = 0;
+            if (MODE == RSI_COUNT) A.count[r] = 0;
+            if (A.amb) A.amb[r] = 1;
+            continue;
+        }
+        SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
+        bool found = false, band = false;
+        int cnt = 0, plain_cnt = 0;
+        auto leaf = [&](int j) -> bool {
+            if (STATS) ++tests;
+            Tri tr = load_tri(A.tris, j);
+            bool plain;
+            int c = tri_fp32(g, tr, A.fp32_only != 0, plain);
+            plain_cnt += plain;
+            if (c == kHit) {
+                ++cnt;
+                if (MODE == RSI_ANY_HIT) {
+                    found = true;
+                    return true;
+                }
+            } else if (c == kBand) {
+                band = true;
+                if (MODE == RSI_COUNT && !A.fp32_only) return true;   // re-done in FP64
+            }
+            return false;
+        };
+        bool ok = traverse<STACK, STATS>(A, g, leaf, visits);
+        if (!ok) {
+            raise_error(A.ctr, RSI_ERR_STACK);
+            band = true;
+            found = false;
+        }
+        if (A.fp32_only) {
+            // plain FP32 closed-interval decisions, no re-test
+            int c = plain_cnt;
+            if (MODE == RSI_ANY_HIT) A.hit[r] = (uint8_t)(found || c > 0);
+            else {
+                A.count[r] = c;
+                if (A.hit) A.hit[r] = (uint8_t)(c > 0);
+            }
+            if (A.amb) A.amb[r] = 0;
+            continue;
+        }
+        if (MODE == RSI_ANY_HIT && found) {
+            A.hit[r] = 1;
+            if (A.amb) A.amb[r] = 0;
+        } else if (band) {
+            int pos = atomicAdd(&A.ctr->band_count, 1);
+            A.band_ids[pos] = (int32_t)r;
+        } else {
+            if (MODE == RSI_ANY_HIT) A.hit[r] = 0;
+            else {
+                A.count[r] = cnt;
+                if (A.hit) A.hit[r] = (uint8_t)(cnt > 0);
+            }
+            if (A.amb) A.amb[r] = 0;
+        }
+    }
+    if (STATS) {
+        __syncwarp();
+        for (int off = 16; off; off >>= 1) {
+            visits += __shfl_xor_sync(0xffffffffu, visits, off);
+            tests += __shfl_xor_sync(0xffffffffu, tests, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&A.ctr->node_visits, visits);
+            atomicAdd(&A.ctr->tri_tests, tests);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- FP64
+// The definition in FP64 with explicit round-to-nearest operations in the
+// order the definition is written, so that no multiply-add is fused.
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return {__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y), __dsub_rn(a.z, b.z)}; }
+__device__ __forceinline__ D3 dadd(D3 a, D3 b) { return {__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z)}; }
+__device__ __forceinline__ D3 dscale(D3 a, double s) { return {__dmul_rn(a.x, s), __dmul_rn(a.y, s), __dmul_rn(a.z, s)}; }
+__device__ __forceinline__ double ddot(D3 a, D3 b) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)), __dmul_rn(a.z, b.z));
+}
+__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
+    return {__dsub_rn(__dmul_rn(a.y, b.z), __dmul_rn(a.z, b.y)), __dsub_rn(__dmul_rn(a.z, b.x), __dmul_rn(a.x, b.z)),
+            __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x))};
+}
+__device__ __forceinline__ double dnorm(D3 a) { return __dsqrt_rn(ddot(a, a)); }
+__device__ __forceinline__ double clamp01d(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
+__device__ __forceinline__ D3 d3of(float4 v) { return {(double)v.x, (double)v.y, (double)v.z}; }
+
+__device__ double pt_seg(D3 p, D3 a, D3 b) {
+    D3 ab = dsub(b, a);
+    double len2 = ddot(ab, ab);
+    double t = len2 > 0.0 ? clamp01d(__ddiv_rn(ddot(dsub(p, a), ab), len2)) : 0.0;
+    return dnorm(dsub(p, dadd(a, dscale(ab, t))));
+}
+
+__device__ double seg_seg(D3 p0, D3 p1, D3 q0, D3 q1) {
+    double best = pt_seg(p0, q0, q1);
+    double d = pt_seg(p1, q0, q1);
+    if (d < best) best = d;
+    d = pt_seg(q0, p0, p1);
+    if (d < best) best = d;
+    d = pt_seg(q1, p0, p1);
+    if (d < best) best = d;
+    D3 u = dsub(p1, p0), v = dsub(q1, q0), w0 = dsub(p0, q0);
+    double a = ddot(u, u), b = ddot(u, v), c = ddot(v, v);
+    double dd = ddot(u, w0), e = ddot(v, w0);
+    double den = __dsub_rn(__dmul_rn(a, c), __dmul_rn(b, b));
+    if (den > 0.0) {
+        double s = __ddiv_rn(__dsub_rn(__dmul_rn(b, e), __dmul_rn(c, dd)), den);
+        double t = __ddiv_rn(__dsub_rn(__dmul_rn(a, e), __dmul_rn(b, dd)), den);
+        if (s >= 0.0 && s <= 1.0 && t >= 0.0 && t <= 1.0) {
+            d = dnorm(dsub(dadd(w0, dscale(u, s)), dscale(v, t)));
+            if (d < best) best = d;
+        }
+    }
+    return best;
+}
+
+__device__ double pt_tri(D3 p, D3 a, D3 b, D3 c) {
+    D3 n = dcross(dsub(b, a), dsub(c, a));
+    double nn = ddot(n, n);
+    double h = __ddiv_rn(ddot(dsub(p, a), n), nn);
+    D3 proj = dsub(p, dscale(n, h));
+    double s0 = ddot(dcross(dsub(b, a), dsub(proj, a)), n);
+    double s1 = ddot(dcross(dsub(c, b), dsub(proj, b)), n);
+    double s2 = ddot(dcross(dsub(a, c), dsub(proj, c)), n);
+    if (s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0) return __dmul_rn(fabs(h), __dsqrt_rn(nn));
+    double best = pt_seg(p, a, b);
+    double d = pt_seg(p, b, c);
+    if (d < best) best = d;
+    d = pt_seg(p, c, a);
+    if (d < best) best = d;
+    return best;
+}
+
+// Class of a pair in FP64 (decisive hit / decisive miss / ambiguous), the
+// inclusive (closed-interval) hit and its t.
+__device__ int classify_fp64(D3 s, D3 e, D3 a, D3 b, D3 c, double& t_out, bool& incl) {
+    const double tau = kTauD;
+    D3 d = dsub(e, s);
+    D3 e1 = dsub(b, a), e2 = dsub(c, a);
+    D3 n = dcross(e1, e2);
+    incl = false;
+    t_out = 0.0;
+    if ((d.x == 0.0 && d.y == 0.0 && d.z == 0.0) || (n.x == 0.0 && n.y == 0.0 && n.z == 0.0)) return kMiss;
+    D3 p = dcross(d, e2);
+    double det = ddot(e1, p);
+    D3 sv = dsub(s, a);
+    D3 q = dcross(sv, e1);
+    double det_rel = __ddiv_rn(det, __dmul_rn(__dmul_rn(dnorm(d), dnorm(e1)), dnorm(e2)));
+    double u = 0.0, v = 0.0, t = 0.0, w = 0.0;
+    if (det != 0.0) {
+        u = __ddiv_rn(ddot(sv, p), det);
+        v = __ddiv_rn(ddot(d, q), det);
+        t = __ddiv_rn(ddot(e2, q), det);
+        w = __dsub_rn(__dsub_rn(1.0, u), v);
+        incl = (u >= 0.0 && v >= 0.0 && w >= 0.0 && t >= 0.0 && t <= 1.0);
+    }
+    t_out = t;
+    if (fabs(det_rel) > tau) {
+        if (u > tau && v > tau && w > tau && t > tau && t < 1.0 - tau) return kHit;
+        if (u < -tau || v < -tau || w < -tau || t < -tau || t > 1.0 + tau) return kMiss;
+        return kBand;   // ambiguous
+    }
+    double dist;
+    if (incl) {
+        dist = 0.0;
+    } else {
+        dist = pt_tri(s, a, b, c);
+        double dd = pt_tri(e, a, b, c);
+        if (dd < dist) dist = dd;
+        dd = seg_seg(s, e, a, b);
+        if (dd < dist) dist = dd;
+        dd = seg_seg(s, e, b, c);
+        if (dd < dist) dist = dd;
+        dd = seg_seg(s, e, c, a);
+        if (dd < dist) dist = dd;
+    }
+    return dist > __dmul_rn(tau, dnorm(d)) ? kMiss : kBand;
+}
+
+template <int MODE, int STACK>
+__global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
+    const int nb = *(volatile int*)&A.ctr->band_count;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+        const int64_t r = A.band_ids[k];
+        float3 s = make_float3(A.from[3 * r], A.from[3 * r + 1], A.from[3 * r + 2]);
+        float3 e = make_float3(A.to[3 * r], A.to[3 * r + 1], A.to[3 * r + 2]);
+        SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
+        D3 sd = {(double)s.x, (double)s.y, (double)s.z}, ed = {(double)e.x, (double)e.y, (double)e.z};
+        int n_hit = 0, n_amb = 0, n_incl = 0;
+        bool overflow = false;
+        double ts[kMaxInclusive];
+        auto leaf = [&](int j) -> bool {
+            Tri tr = load_tri(A.tris, j);
+            double t;
+            bool incl;
+            int c = classify_fp64(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2), t, incl);
+            if (c == kHit) ++n_hit;
+            else if (c == kBand) ++n_amb;
+            if (incl) {
+                if (n_incl < kMaxInclusive) ts[n_incl++] = t;
+                else overflow = true;
+            }
+            return MODE == RSI_ANY_HIT && c == kHit;   // a decisive hit settles it
+        };
+        unsigned long long dummy = 0;
+        bool ok = traverse<STACK, false>(A, g, leaf, dummy);
+        if (!ok) raise_error(A.ctr, RSI_ERR_STACK);
+        if (overflow) raise_error(A.ctr, RSI_ERR_OVERFLOW);
+        if (MODE == RSI_ANY_HIT) {
+            bool amb = n_hit == 0 && n_amb > 0;
+            A.hit[r] = (uint8_t)(n_hit > 0 || (amb && n_incl > 0));
+            if (A.amb) A.amb[r] = (uint8_t)amb;
+            if (amb) atomicAdd(&A.ctr->ambiguous, 1ull);
+        } else {
+            bool amb = n_amb > 0;
+            int count = n_hit;
+            if (amb) {
+                // distinct crossing points: sort t, start a new one at each gap > 1e-9
+                for (int i = 1; i < n_incl; ++i) {
+                    double x = ts[i];
+                    int k2 = i - 1;
+                    while (k2 >= 0 && ts[k2] > x) {
+                        ts[k2 + 1] = ts[k2];
+                        --k2;
+                    }
+                    ts[k2 + 1] = x;
+                }
+                count = 0;
+                for (int i = 0; i < n_incl; ++i)
+                    if (i == 0 || __dsub_rn(ts[i], ts[i - 1]) > kTMerge) ++count;
+                atomicAdd(&A.ctr->ambiguous, 1ull);
+            }
+            A.count[r] = count;
+            if (A.hit) A.hit[r] = (uint8_t)(count > 0);
+            if (A.amb) A.amb[r] = (uint8_t)amb;
+        }
+    }
+}
+
+__global__ void k_reset_query(DevCounters* c) {
+    c->band_count = 0;
+    c->error = 0;
+    c->node_visits = c->tri_tests = c->ambiguous = 0;
+}
+
+template <int MODE, bool STATS, int STACK>
+void launch_fp32(const QueryArgs& A, int grid, int block, cudaStream_t s) {
+    k_query_fp32<MODE, STATS, STACK><<<grid, block, 0, s>>>(A);
+}
+
+template <int MODE, bool STATS>
+void launch_fp32_stack(const QueryArgs& A, int height, int grid, int block, cudaStream_t s) {
+    if (height < 32) launch_fp32<MODE, STATS, 32>(A, grid, block, s);
+    else if (height < 64) launch_fp32<MODE, STATS, 64>(A, grid, block, s);
+    else launch_fp32<MODE, STATS, 128>(A, grid, block, s);
+}
+
+template <int MODE>
+void launch_fp64(const QueryArgs& A, int height, int grid, cudaStream_t s) {
+    if (height < 32) k_query_fp64<MODE, 32><<<grid, 128, 0, s>>>(A);
+    else if (height < 64) k_query_fp64<MODE, 64><<<grid, 128, 0, s>>>(A);
+    else k_query_fp64<MODE, 128><<<grid, 128, 0, s>>>(A);
+}
+
+}  // namespace
+
+// Launch the two passes for one batch of segments already on the device.
+int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n, int mode, const rsi_options* opt,
+                 uint8_t* d_hit, int32_t* d_count, uint8_t* d_amb, int32_t* band_ids, DevCounters* ctr,
+                 cudaStream_t s) {
+    rsi_options o = {};
+    if (opt) o = *opt;
+    if (h->height >= 127) return fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
+    QueryArgs A;
+    A.nodes = h->nodes;
+    A.tris = h->tris;
+    A.n_tri = h->n_tri;
+    A.from = d_from;
+    A.to = d_to;
+    A.n_rays = n;
+    A.hit = d_hit;
+    A.count = d_count;
+    A.amb = d_amb;
+    A.band_ids = band_ids;
+    A.ctr = ctr;
+    A.dmax0 = h->dmax[0];
+    A.dmax1 = h->dmax[1];
+    A.dmax2 = h->dmax[2];
+    A.fp32_only = o.fp32_only;
+    const int block = o.block > 0 ? o.block : 256;
+    const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
+    int64_t want = (n + block - 1) / block;
+    int64_t cap = (int64_t)device_sm_count() * bps;
+    int grid = (int)std::max<int64_t>(1, std::min(want, cap));
+    if (o.time_kernels && !h->ev[0]) {
+        for (auto& e : h->ev) RSI_CUDA_TRY(cudaEventCreate(&e));
+    }
+    h->timed = o.time_kernels != 0;
+    k_reset_query<<<1, 1, 0, s>>>(ctr);
+    if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[0], s));
+    if (mode == RSI_ANY_HIT) {
+        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, grid, block, s);
+        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, grid, block, s);
+    } else {
+        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, grid, block, s);
+        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, grid, block, s);
+    }
+    if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[1], s));
+    if (!o.fp32_only) {
+        if (mode == RSI_ANY_HIT) launch_fp64<RSI_ANY_HIT>(A, h->height, device_sm_count() * 4, s);
+        else launch_fp64<RSI_COUNT>(A, h->height, device_sm_count() * 4, s);
+    }
+    if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[2], s));
+    note_launches(o.fp32_only ? 2 : 3);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rsi_query launch");
+    return RSI_OK;
+}
+
+int ensure_band_capacity(rsi_bvh_t h, int64_t n, cudaStream_t s) {
+    if (h->band_cap >= n) return RSI_OK;
+    int64_t cap = std::max<int64_t>(n, 1 << 16);
+    if (h->band_ids) {
+        RSI_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(h->band_ids);
+        h->band_ids = nullptr;
+        h->band_cap = 0;
+    }
+    if (cudaMalloc(&h->band_ids, 4 * (size_t)cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RSI_ERR_OOM, "rsi_query: band list allocation failed");
+    }
+    h->band_cap = cap;
+    return RSI_OK;
+}
+
+int read_stats(rsi_bvh_t h, DevCounters* ctr, int64_t n, rsi_stats* st, cudaStream_t s) {
+    RSI_CUDA_TRY(cudaMemcpyAsync(h->h_ctr, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    RSI_CUDA_TRY(cudaStreamSynchronize(s));
+    const DevCounters& c = *h->h_ctr;
+    if (st) {
+        st->n_rays = n;
+        st->node_visits = (int64_t)c.node_visits;
+        st->tri_tests = (int64_t)c.tri_tests;
+        st->band_rays = c.band_count;
+        st->ambiguous = (int64_t)c.ambiguous;
+        st->tree_height = h->height;
+        st->device_error = c.error;
+    }
+    if (c.error) return fail(c.error, "rsi_query: device error " + std::to_string(c.error));
+    return RSI_OK;
+}
+
+}  // namespace rsi
+
+extern "C" int rsi_last_query_ms(rsi_bvh_t h, float* traverse_ms, float* retest_ms) {
+    if (!h) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_last_query_ms: NULL handle");
+    float a = -1.0f, b = -1.0f;
+    if (h->timed && h->ev[0]) {
+        RSI_CUDA_TRY(cudaEventSynchronize(h->ev[2]));
+        RSI_CUDA_TRY(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+        RSI_CUDA_TRY(cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
+    }
+    if (traverse_ms) *traverse_ms = a;
+    if (retest_ms) *retest_ms = b;
+    return RSI_OK;
+}
+
+static int check_query_args(rsi_bvh_t h, const void* from, const void* to, int64_t n, int mode, const void* hit,
+                            const void* count) {
+    if (!h) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: NULL handle");
+    if (n < 0 || n > 0x7FFFFFFFll) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: need 0 <= n_rays < 2^31");
+    if (mode != RSI_ANY_HIT && mode != RSI_COUNT) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: bad mode");
+    if (n > 0 && (!from || !to)) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: NULL segment pointer");
+    if (n > 0 && mode == RSI_ANY_HIT && !hit) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: any-hit needs hit");
+    if (n > 0 && mode == RSI_COUNT && !count) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: count needs count");
+    return RSI_OK;
+}
+
+extern "C" int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
+                         const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
+                         rsi_stats* stats, void* stream) {
+    int rc = check_query_args(h, d_from, d_to, n_rays, mode, d_hit, d_count);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_rays == 0) {
+        if (stats) *stats = rsi_stats{};
+        return RSI_OK;
+    }
+    rc = rsi::ensure_band_capacity(h, n_rays, s);
+    if (rc) return rc;
+    rc = rsi::query_device(h, d_from, d_to, n_rays, mode, opt, d_hit, d_count, d_ambiguous, h->band_ids, h->ctr, s);
+    if (rc) return rc;
+    if (stats) return rsi::read_stats(h, h->ctr, n_rays, stats, s);
+    return RSI_OK;
+}
+
+extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n_rays, int mode,
+                              const rsi_options* opt, uint8_t* h_hit, int32_t* h_count, uint8_t* h_ambiguous,
+                              rsi_stats* stats, void* stream) {
+    int rc = check_query_args(h, h_from, h_to, n_rays, mode, h_hit, h_count);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_rays == 0) {
+        if (stats) *stats = rsi_stats{};
+        return RSI_OK;
+    }
+    rc = rsi::ensure_band_capacity(h, n_rays, s);
+    if (rc) return rc;
+    const size_t bf = 12 * (size_t)n_rays;
+    float *df = nullptr, *dt = nullptr;
+    uint8_t *dh = nullptr, *da = nullptr;
+    int32_t* dc = nullptr;
+    bool ok = cudaMallocAsync(&df, bf, s) == cudaSuccess && cudaMallocAsync(&dt, bf, s) == cudaSuccess;
+    if (ok && h_hit) ok = cudaMallocAsync(&dh, n_rays, s) == cudaSuccess;
+    if (ok && h_ambiguous) ok = cudaMallocAsync(&da, n_rays, s) == cudaSuccess;
+    if (ok && mode == RSI_COUNT) ok = cudaMallocAsync(&dc, 4 * (size_t)n_rays, s) == cudaSuccess;
+    if (ok) {
+        ok = cudaMemcpyAsync(df, h_from, bf, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+             cudaMemcpyAsync(dt, h_to, bf, cudaMemcpyHostToDevice, s) == cudaSuccess;
+        if (!ok) rc = rsi::cuda_fail(cudaGetLastError(), "rsi_query_host copy in");
+    } else {
+        cudaGetLastError();
+        rc = rsi::fail(RSI_ERR_OOM, "rsi_query_host: staging allocation failed");
+    }
+    if (rc == RSI_OK)
+        rc = rsi::query_device(h, df, dt, n_rays, mode, opt, dh, dc, da, h->band_ids, h->ctr, s);
+    if (rc == RSI_OK) {
+        bool c_ok = true;
+        if (h_hit) c_ok &= cudaMemcpyAsync(h_hit, dh, n_rays, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        if (h_ambiguous) c_ok &= cudaMemcpyAsync(h_ambiguous, da, n_rays, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        if (mode == RSI_COUNT) c_ok &= cudaMemcpyAsync(h_count, dc, 4 * (size_t)n_rays, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        if (!c_ok) rc = rsi::cuda_fail(cudaGetLastError(), "rsi_query_host copy out");
+    }
+    for (void* p : {(void*)df, (void*)dt, (void*)dh, (void*)da, (void*)dc})
+        if (p) cudaFreeAsync(p, s);
+    if (rc) return rc;
+    rsi_stats tmp;
+    return rsi::read_stats(h, h->ctr, n_rays, stats ? stats : &tmp, s);
+}

@@ -1,0 +1,99 @@
+// rsi_internal.cuh -- device data layout and host helpers shared by the
+// library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "rsi.h"
+
+namespace rsi {
+
+// Packed child-pair node: the boxes of both children next to the two child
+// references, so one 64-byte fetch (two L2 sectors, one L1 line half) lets
+// a segment test both children.  lmin.w holds the left reference, lmax.w the
+// right one (as int bits): an internal node index >= 0 or ~leaf for a leaf.
+struct __align__(64) Node {
+    float4 lmin, lmax, rmin, rmax;
+};
+static_assert(sizeof(Node) == 64, "node layout");
+
+// Triangle in leaf (Morton) order: three float4 vertices; v0.w carries the
+// caller's triangle id (int bits).
+struct __align__(16) Tri {
+    float4 v0, v1, v2;
+};
+static_assert(sizeof(Tri) == 48, "triangle layout");
+
+constexpr uint32_t kLeafTag = 0x80000000u;   // leaf tag of the exported tree
+constexpr float kTau = 1e-6f;                // relative margin of the band
+constexpr double kTauD = 1e-6;
+constexpr double kTMerge = 1e-9;             // crossings merged within this t
+constexpr int kMaxInclusive = 64;            // inclusive hits kept per FP64 ray
+
+// Per-handle device scratch words.
+struct DevCounters {
+    int error;          // first RSI_ERR_* raised by a kernel (0 = none)
+    int band_count;     // rays queued for the FP64 re-test
+    int height;         // tree height (written by the refit)
+    int pad0;
+    unsigned long long node_visits, tri_tests, ambiguous;
+    unsigned int ext_bits[6];   // extent as order-preserving uint (min xyz, max xyz)
+    unsigned int dmax_bits[3];  // largest triangle box side per axis (float bits)
+    unsigned int pad1;
+};
+
+}  // namespace rsi
+
+struct rsi_bvh_s {
+    int64_t n_tri = 0, n_vert = 0;
+    int morton_bits = 30;
+    int height = 0;
+    float lo[3], hi[3], dmax[3];
+    // packed traversal data
+    rsi::Node* nodes = nullptr;   // [max(n_tri - 1, 1)]
+    rsi::Tri* tris = nullptr;     // [n_tri]
+    // exported build arrays
+    void* sorted_keys = nullptr;  // uint32 or uint64 [n_tri]
+    int32_t* perm = nullptr;      // [n_tri]
+    int32_t* left = nullptr;      // [n_tri - 1]
+    int32_t* right = nullptr;     // [n_tri - 1]
+    int32_t* parent = nullptr;    // [2 n_tri - 1]
+    float* box = nullptr;         // [6 (2 n_tri - 1)]
+    // scratch
+    rsi::DevCounters* ctr = nullptr;
+    rsi::DevCounters* h_ctr = nullptr;   // pinned mirror for read-back
+    int32_t* band_ids = nullptr;         // [band_cap] rays queued for FP64
+    int64_t band_cap = 0;
+    int64_t device_bytes = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // traversal / re-test timing
+    bool timed = false;
+};
+
+namespace rsi {
+
+// Thread-local last-error message and helpers that turn CUDA failures into
+// RSI_ERR_* codes.
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define RSI_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return rsi::cuda_fail(e_, #expr); \
+    } while (0)
+
+inline int grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    return (int)(g < 1 ? 1 : g);
+}
+
+int device_sm_count();
+
+// Count of kernel launches made by the library (rsi_kernel_launches).
+void note_launches(int n);
+
+}  // namespace rsi

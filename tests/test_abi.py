@@ -1,0 +1,58 @@
+"""The C ABI without a GPU: the library builds (nvcc cross-compiles for
+sm_103a), loads, exports every function include/rsi.h declares, and rejects
+bad arguments on the host before any device work."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2305_01867_gb300 import build as b
+    if not b.up_to_date():
+        if not shutil.which(b.NVCC) and not os.path.exists(b.NVCC):
+            pytest.skip("nvcc not available")
+        b.build()
+    import paper_2305_01867_gb300 as m
+    return m
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared("rsi.h")
+    assert {"lbvh_build", "rsi_query", "rsi_query_host", "lbvh_export", "rsi_last_error"} <= set(names)
+    raw = ctypes.CDLL(lib._LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+
+
+def test_node_size_is_queried_not_assumed(lib):
+    # Sec. 3.2: struct sizes come from the library (bytesInBVHNode)
+    assert lib.node_bytes() == 64
+
+
+def test_host_side_rejections(lib):
+    L = lib.lib
+    h = ctypes.c_void_p()
+    # int64 indices (Sec. 4.1.2) are refused before any device work
+    rc = L.lbvh_build(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 8, 30, None, ctypes.byref(h))
+    assert rc == -2 and "int32" in lib.last_error()
+    rc = L.lbvh_build(None, 3, None, 1, 4, 30, None, ctypes.byref(h))
+    assert rc == -1
+    rc = L.lbvh_build(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 0, 4, 30, None, ctypes.byref(h))
+    assert rc == -1
+    rc = L.lbvh_build(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 4, 31, None, ctypes.byref(h))
+    assert rc == -1 and "30 or 63" in lib.last_error()
+    rc = L.rsi_query(None, None, None, 0, 0, None, None, None, None, None, None)
+    assert rc == -1
+    assert L.lbvh_free(None) == 0

@@ -1,0 +1,113 @@
+"""GPU build (extent, Morton, sort, radix tree, refit) against the oracle,
+bit for bit, through the C ABI.  Sizes span several sort tiles (4096 keys),
+ragged tails, a single triangle and forced duplicate Morton codes."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from golden_io import load
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rsi():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2305_01867_gb300 as m
+    return m
+
+
+def _soup(n, seed, dup_frac=0.0):
+    """n random small triangles in [0,1]^3; a fraction share one centroid
+    cell so their Morton codes collide."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0, 1, (n, 3))
+    off = rng.uniform(-0.01, 0.01, (n, 3, 3))
+    k = int(n * dup_frac)
+    if k:   # identical triangles: identical codes
+        c[:k] = c[0]
+        off[:k] = off[0]
+    V = (c[:, None, :] + off).reshape(-1, 3).astype(np.float32)
+    T = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    return V, T
+
+
+def _meshes():
+    g = load("case_study1_sec4_1.txt")
+    yield "case_study1", g["vertices"], g["triangles"]
+    for n in (1, 2, 3, 1023, 1024, 1025, 4097, 9000):
+        V, T = _soup(n, seed=n)
+        yield f"soup{n}", V, T
+    V, T = _soup(5000, seed=3, dup_frac=0.3)
+    yield "dups", V, T
+    m = W.config_mesh("c1")
+    yield "c1", m.vertices, m.triangles
+    m = W.config_mesh("c2")
+    yield "c2", m.vertices, m.triangles
+
+
+@pytest.mark.parametrize("bits", [30, 63])
+def test_build_bit_exact(rsi, bits):
+    for name, V, T in _meshes():
+        ref = oracle.build_all(V, T, bits=bits)
+        bvh = rsi.LBVH(torch.from_numpy(V).cuda(), torch.from_numpy(T).cuda(), morton_bits=bits)
+        got = bvh.export()
+        n = len(T)
+        assert np.array_equal(got["sorted_keys"], ref["sorted_keys"]), name
+        assert np.array_equal(got["perm"], ref["perm"]), name
+        if n > 1:
+            assert np.array_equal(got["left"], ref["left"]), name
+            assert np.array_equal(got["right"], ref["right"]), name
+        assert np.array_equal(got["parent"], ref["parent"]), name
+        assert np.array_equal(got["box"].view(np.uint32), ref["box"].view(np.uint32)), name
+        info = bvh.info()
+        assert info["height"] == ref["height"], name
+        lo, hi = oracle.extent(V)
+        assert np.array_equal(np.array(info["extent_lo"], np.float32), lo), name
+        assert np.array_equal(np.array(info["extent_hi"], np.float32), hi), name
+        bvh.close()
+
+
+def test_case_study1_leaf_order_on_gpu(rsi):
+    """Sec. 4.1: leaves hold T0, T3, T1, T2 and every leaf has a parent."""
+    g = load("case_study1_sec4_1.txt")
+    bvh = rsi.LBVH(torch.from_numpy(g["vertices"]).cuda(), torch.from_numpy(g["triangles"]).cuda())
+    got = bvh.export()
+    assert got["perm"].tolist() == g["leaf_order"].tolist()
+    assert got["parent"][0] == -1 and np.all(got["parent"][1:] >= 0)
+
+
+def test_build_errors(rsi):
+    V = torch.zeros(3, 3, dtype=torch.float32, device="cuda")
+    V[1, 0] = 1
+    V[2, 1] = 1
+    T64 = torch.tensor([[0, 1, 2]], dtype=torch.int64, device="cuda")
+    with pytest.raises(rsi.RSIError) as e:       # the int64 mix-up of Sec. 4.1.2
+        rsi.LBVH(V, T64)
+    assert e.value.code == -2
+    with pytest.raises(rsi.RSIError) as e:
+        rsi.LBVH(V, torch.tensor([[0, 1, 5]], dtype=torch.int32, device="cuda"))
+    assert e.value.code == -8
+    Vn = V.clone()
+    Vn[0, 2] = float("nan")
+    with pytest.raises(rsi.RSIError) as e:
+        rsi.LBVH(Vn, torch.tensor([[0, 1, 2]], dtype=torch.int32, device="cuda"))
+    assert e.value.code == -7
+    with pytest.raises(rsi.RSIError) as e:
+        rsi.LBVH(V, torch.tensor([[0, 1, 2]], dtype=torch.int32, device="cuda"), morton_bits=32)
+    assert e.value.code == -1
+    # the library keeps working after rejected calls
+    b = rsi.LBVH(V, torch.tensor([[0, 1, 2]], dtype=torch.int32, device="cuda"))
+    assert b.info()["n_triangles"] == 1
+
+
+def test_build_from_host_equals_device(rsi):
+    m = W.config_mesh("c1")
+    a = rsi.LBVH(torch.from_numpy(m.vertices), torch.from_numpy(m.triangles)).export()
+    b = rsi.LBVH(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda()).export()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
