@@ -60,7 +60,8 @@ typedef struct rsi_bvh_s* rsi_bvh_t;
 typedef struct rsi_options {
     int fp32_only;      /* 1: skip the FP64 re-test (results may flip near
                            edges and for nearly parallel segments)          */
-    int block;          /* threads per block of the traversal, 0 = tuned    */
+    int block;          /* threads per block of the traversal: a multiple
+                           of 32 in [32, 256]; 0 = tuned                    */
     int blocks_per_sm;  /* resident blocks per SM for the persistent grid,
                            0 = tuned                                         */
     int collect_stats;  /* 1: count node visits and triangle tests          */

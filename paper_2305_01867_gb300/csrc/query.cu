@@ -518,6 +518,9 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     A.dmax1 = h->dmax[1];
     A.dmax2 = h->dmax[2];
     A.fp32_only = o.fp32_only;
+    if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
+        return fail(RSI_ERR_INVALID_ARG, "rsi_query: block must be a multiple of 32 in [32, 256]");
+    if (o.blocks_per_sm < 0) return fail(RSI_ERR_INVALID_ARG, "rsi_query: blocks_per_sm < 0");
     const int block = o.block > 0 ? o.block : 256;
     const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
     int64_t want = (n + block - 1) / block;

@@ -19,7 +19,8 @@ def _declared(header):
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2305_01867_gb300 import build as b
+    import __graft_entry__
+    b = __graft_entry__._builder()
     if not b.up_to_date():
         if not shutil.which(b.NVCC) and not os.path.exists(b.NVCC):
             pytest.skip("nvcc not available")

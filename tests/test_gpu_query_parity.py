@@ -32,7 +32,7 @@ def _dev(a):
 def _gpu_both(rsi, bvh, F, E, **kw):
     dF, dE = _dev(F), _dev(E)
     a = bvh.query(dF, dE, "any_hit", **kw)
-    c = bvh.query(dF, dE, "count", **kw)
+    c = bvh.query(dF, dE, "count", hit=torch.empty(len(F), dtype=torch.uint8, device="cuda"), **kw)
     torch.cuda.synchronize()
     return dict(hit=a["hit"].cpu().numpy(), amb_hit=a["ambiguous"].cpu().numpy(),
                 count=c["count"].cpu().numpy(), amb_count=c["ambiguous"].cpu().numpy(),
@@ -143,7 +143,7 @@ def test_c2_full_size_sampled(rsi):
     ref = oracle.query(mesh.vertices, mesh.triangles, F[idx], E[idx])
     _compare(got, ref, idx)
     # the other half of the workload: segments above the surface never hit
-    above = F[:, 2].astype(np.float64) + E[:, 2] > 2 * mesh.z_max
+    above = np.minimum(F[:, 2], E[:, 2]) > mesh.z_max
     assert got["hit"][above].sum() == 0 and got["count"][above].sum() == 0
 
 
@@ -195,7 +195,7 @@ def test_stats_and_host_path(rsi):
     assert e["hit"].numel() == 0
 
 
-@pytest.mark.parametrize("block,bps", [(64, 2), (128, 16), (512, 1)])
+@pytest.mark.parametrize("block,bps", [(64, 2), (128, 16), (256, 1), (32, 64)])
 def test_launch_shapes_agree(rsi, block, bps):
     mesh = W.config_mesh("c1")
     F, E = W.rays(W.config_rays("c1", 30011), mesh)
@@ -203,3 +203,13 @@ def test_launch_shapes_agree(rsi, block, bps):
     base = bvh.query(_dev(F), _dev(E), "count")["count"].cpu().numpy()
     other = bvh.query(_dev(F), _dev(E), "count", block=block, blocks_per_sm=bps)["count"].cpu().numpy()
     assert np.array_equal(base, other)
+
+
+def test_bad_launch_shape_rejected(rsi):
+    mesh = W.config_mesh("c1")
+    F, E = W.rays(W.config_rays("c1", 100), mesh)
+    bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles))
+    for block in (512, 48, 1024):
+        with pytest.raises(rsi.RSIError) as e:
+            bvh.query(_dev(F), _dev(E), "any_hit", block=block)
+        assert e.value.code == -1
