@@ -172,6 +172,33 @@ int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t 
                    const rsi_options* opt, uint8_t* h_hit, int32_t* h_count, uint8_t* h_ambiguous,
                    rsi_stats* stats, void* stream);
 
+/*
+ * Query without any device allocation.  The paper has no counterpart: this
+ * is for callers that cannot allocate device memory while they query -- for
+ * example a plugin whose host application owns all device memory through
+ * its own allocator, or a real-time loop that must not pay for (or risk the
+ * failure of) a cudaMalloc.  The hierarchy must already be built.
+ *
+ * Same arguments and results as rsi_query, except that no statistics are
+ * returned and opt->time_kernels is ignored.  The per-call scratch (the
+ * queue of segments re-tested in FP64 and the call's counters) lives in one
+ * fixed device array of 256 B + 4 B x RSI_NOALLOC_MAX_RAYS (about 8 MiB)
+ * that every GPU which loads the library keeps until the process exits.
+ * n_rays above RSI_NOALLOC_MAX_RAYS is rejected with RSI_ERR_INVALID_ARG;
+ * split larger batches into several calls.
+ *
+ * The first call on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the one array: each call
+ * clears the counters it needs, but calls whose work overlaps on the GPU
+ * (different streams, or different threads without ordering) race on it and
+ * must be serialized by the caller.  Device-side errors are not reported.
+ */
+#define RSI_NOALLOC_MAX_RAYS (1 << 21)
+int rsi_query_noalloc(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
+                      const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
+                      void* stream);
+
 /* Durations of the FP32 traversal kernel and of the FP64 re-test kernel of
  * the last query on `h` that ran with time_kernels = 1, from CUDA events
  * recorded on that query's stream (waits for them).  -1 if none. */

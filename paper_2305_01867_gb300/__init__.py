@@ -21,6 +21,7 @@ from .build import build as build_library
 
 RSI_OK = 0
 RSI_ANY_HIT, RSI_COUNT = 0, 1
+NOALLOC_MAX_RAYS = 1 << 21   # RSI_NOALLOC_MAX_RAYS of include/rsi.h
 LEAF_TAG = 0x80000000
 ERRORS = {-1: "INVALID_ARG", -2: "DTYPE", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "STACK", -7: "NAN",
           -8: "INDEX", -9: "OVERFLOW"}
@@ -72,6 +73,8 @@ def _load():
     lib.lbvh_node_bytes.argtypes = []
     for f in (lib.rsi_query, lib.rsi_query_host):
         f.argtypes = [P, P, P, i64, i32, ctypes.POINTER(Options), P, P, P, ctypes.POINTER(Stats), P]
+    lib.rsi_query_noalloc.argtypes = [P, P, P, i64, i32, ctypes.POINTER(Options), P, P, P, P]
+    lib.rsi_query_noalloc.restype = ctypes.c_int
     lib.rsi_last_query_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     lib.rsi_last_query_ms.restype = ctypes.c_int
     lib.rsi_kernel_launches.argtypes = []

@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "rsi_internal.cuh"
@@ -671,4 +672,60 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
     if (rc) return rc;
     rsi_stats tmp;
     return rsi::read_stats(h, h->ctr, n_rays, stats ? stats : &tmp, s);
+}
+
+// ---------------------------------------------------------------- no-alloc
+// rsi_query_noalloc: the same two passes with their scratch (counters, then
+// the FP64 queue) in this file-scope array instead of handle memory.
+namespace {
+
+constexpr size_t kNoallocHeader = 256;
+constexpr size_t kNoallocBytes = kNoallocHeader + 4 * (size_t)RSI_NOALLOC_MAX_RAYS;
+static_assert(sizeof(rsi::DevCounters) <= kNoallocHeader, "counters fit the header");
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (host code only sees a host-side stand-in for the symbol).
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    RSI_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_noalloc: device id >= 64");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return rsi::cuda_fail(e, "rsi_query_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return RSI_OK;
+}
+
+}  // namespace
+
+extern "C" int rsi_query_noalloc(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
+                                 const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
+                                 void* stream) {
+    int rc = check_query_args(h, d_from, d_to, n_rays, mode, d_hit, d_count);
+    if (rc) return rc;
+    if (n_rays > (int64_t)RSI_NOALLOC_MAX_RAYS)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_noalloc: n_rays " + std::to_string(n_rays) +
+                                                  " exceeds RSI_NOALLOC_MAX_RAYS (" +
+                                                  std::to_string(RSI_NOALLOC_MAX_RAYS) + "); split the batch");
+    if (n_rays == 0) return RSI_OK;
+    void* base = nullptr;
+    rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    rsi_options o = {};
+    if (opt) o = *opt;
+    o.time_kernels = 0;
+    o.collect_stats = 0;
+    auto* ctr = reinterpret_cast<rsi::DevCounters*>(base);
+    auto* band = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(base) + kNoallocHeader);
+    return rsi::query_device(h, d_from, d_to, n_rays, mode, &o, d_hit, d_count, d_ambiguous, band, ctr,
+                             (cudaStream_t)stream);
 }
