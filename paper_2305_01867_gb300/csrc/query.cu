@@ -2,7 +2,7 @@
 // the tree yields candidate triangles, each tested with Moller-Trumbore;
 // boolean and intercept_count modes), in two passes:
 //
-//  k_query_fp32  one thread per segment (grid-stride over a persistent grid):
+//  k_query_fp32  one lane per segment in a warp-coherent persistent loop:
 //                stack traversal of the child-pair nodes with a padded,
 //                outward-rounded slab test, and an FP32 Moller test that
 //                carries a forward error bound.  Each pair comes out as a
@@ -10,9 +10,10 @@
 //                (the FP32 value is too close to a decision boundary or to
 //                the 1e-6 margin to be trusted, the Epilogue's concern).
 //                Segments with a band pair and no certain answer are queued.
-//  k_query_fp64  re-traverses the queued segments and classifies every
-//                candidate pair in FP64 exactly as the definition does
-//                (decisive hit / decisive miss / ambiguous, margin 1e-6).
+//  k_query_fp64  one warp per queued segment: re-traverses it, and classifies
+//                the candidate pairs 32 at a time in FP64 with the outcome
+//                the definition gives (decisive hit / decisive miss /
+//                ambiguous, margin 1e-6).
 //
 // Culling never drops a pair that could be a hit or ambiguous: node boxes
 // are padded by 4e-6 (|d|_1 + the largest triangle extent), which covers
@@ -176,126 +177,6 @@ __device__ __forceinline__ bool bad3(float3 a) {
     return !(isfinite(a.x) && isfinite(a.y) && isfinite(a.z));
 }
 
-// The traversal shared by both passes: visits every leaf whose padded box
-// the segment crosses, calling leaf(j) -> true to stop early.  Returns false
-// on stack overflow.
-template <int STACK, bool STATS, typename Leaf>
-__device__ __forceinline__ bool traverse(const QueryArgs& A, const SegF& g, Leaf&& leaf, unsigned long long& visits) {
-    if (A.n_tri == 1) {
-        leaf(0);
-        return true;
-    }
-    int stack[STACK];
-    int sp = 0;
-    int node = 0;
-    while (true) {
-        float4 lmin, lmax, rmin, rmax;
-        load_node(A.nodes, node, lmin, lmax, rmin, rmax);
-        if (STATS) ++visits;
-        int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
-        bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
-        if (hl && lref < 0) {
-            hl = false;
-            if (leaf(~lref)) return true;
-        }
-        if (hr && rref < 0) {
-            hr = false;
-            if (leaf(~rref)) return true;
-        }
-        if (hl && hr) {
-            if (sp >= STACK) return false;
-            stack[sp++] = rref;
-            node = lref;
-        } else if (hl) {
-            node = lref;
-        } else if (hr) {
-            node = rref;
-        } else {
-            if (sp == 0) return true;
-            node = stack[--sp];
-        }
-    }
-}
-
-template <int MODE, bool STATS, int STACK>
-__global__ void __launch_bounds__(256) k_query_fp32(QueryArgs A) {
-    unsigned long long visits = 0, tests = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n_rays; r += stride) {
-        float3 s = make_float3(__ldg(A.from + 3 * r), __ldg(A.from + 3 * r + 1), __ldg(A.from + 3 * r + 2));
-        float3 e = make_float3(__ldg(A.to + 3 * r), __ldg(A.to + 3 * r + 1), __ldg(A.to + 3 * r + 2));
-        if (bad3(s) || bad3(e)) {   // undefined answer: report it as ambiguous
-            if (A.hit) A.hit[r] = 0;
-            if (MODE == RSI_COUNT) A.count[r] = 0;
-            if (A.amb) A.amb[r] = 1;
-            continue;
-        }
-        SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
-        bool found = false, band = false;
-        int cnt = 0, plain_cnt = 0;
-        auto leaf = [&](int j) -> bool {
-            if (STATS) ++tests;
-            Tri tr = load_tri(A.tris, j);
-            bool plain;
-            int c = tri_fp32(g, tr, A.fp32_only != 0, plain);
-            plain_cnt += plain;
-            if (c == kHit) {
-                ++cnt;
-                if (MODE == RSI_ANY_HIT) {
-                    found = true;
-                    return true;
-                }
-            } else if (c == kBand) {
-                band = true;
-                if (MODE == RSI_COUNT && !A.fp32_only) return true;   // re-done in FP64
-            }
-            return false;
-        };
-        bool ok = traverse<STACK, STATS>(A, g, leaf, visits);
-        if (!ok) {
-            raise_error(A.ctr, RSI_ERR_STACK);
-            band = true;
-            found = false;
-        }
-        if (A.fp32_only) {
-            // plain FP32 closed-interval decisions, no re-test
-            int c = plain_cnt;
-            if (MODE == RSI_ANY_HIT) A.hit[r] = (uint8_t)(found || c > 0);
-            else {
-                A.count[r] = c;
-                if (A.hit) A.hit[r] = (uint8_t)(c > 0);
-            }
-            if (A.amb) A.amb[r] = 0;
-            continue;
-        }
-        if (MODE == RSI_ANY_HIT && found) {
-            A.hit[r] = 1;
-            if (A.amb) A.amb[r] = 0;
-        } else if (band) {
-            int pos = atomicAdd(&A.ctr->band_count, 1);
-            A.band_ids[pos] = (int32_t)r;
-        } else {
-            if (MODE == RSI_ANY_HIT) A.hit[r] = 0;
-            else {
-                A.count[r] = cnt;
-                if (A.hit) A.hit[r] = (uint8_t)(cnt > 0);
-            }
-            if (A.amb) A.amb[r] = 0;
-        }
-    }
-    if (STATS) {
-        __syncwarp();
-        for (int off = 16; off; off >>= 1) {
-            visits += __shfl_xor_sync(0xffffffffu, visits, off);
-            tests += __shfl_xor_sync(0xffffffffu, tests, off);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&A.ctr->node_visits, visits);
-            atomicAdd(&A.ctr->tri_tests, tests);
-        }
-    }
-}
-
 // ---------------------------------------------------------------- FP64
 // The definition in FP64 with explicit round-to-nearest operations in the
 // order the definition is written, so that no multiply-add is fused.
@@ -409,68 +290,371 @@ __device__ int classify_fp64(D3 s, D3 e, D3 a, D3 b, D3 c, double& t_out, bool& 
     return dist > __dmul_rn(tau, dnorm(d)) ? kMiss : kBand;
 }
 
+constexpr int kWarpChunk = 64;   // segments a warp takes per atomic
+constexpr int kRefillMin = 4;    // refill once this many lanes of a warp are idle
+
+// Warp-coherent persistent traversal.  Every iteration, each active lane
+// processes exactly one node (both child boxes, leaf children tested in
+// place), so the lanes of a warp stay in step; lanes whose segment is done
+// are refilled together from a per-warp chunk of segment indices taken with
+// one atomic.  A segment with a band pair and no certain answer is queued
+// for k_query_fp64 (count mode stops at the first band pair).
+template <int MODE, bool STATS, int STACK>
+__global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int n_rays = (int)A.n_rays;
+    unsigned long long visits = 0, tests = 0;
+    int wbase = 0, wend = 0;     // warp-uniform chunk [wbase, wend)
+    bool exhausted = false;      // warp-uniform
+    int ray = -1;
+    SegF g;
+    int node = 0, sp = 0;
+    int stack[STACK];
+    int cnt = 0, plain_cnt = 0;
+    bool found = false, band = false;
+    while (true) {
+        unsigned idle = __ballot_sync(kFull, ray < 0);
+        if (!exhausted && (__popc(idle) >= kRefillMin || idle == kFull)) {
+            while (idle) {
+                if (wbase >= wend) {
+                    unsigned long long b = 0;
+                    if (lane == 0) b = atomicAdd(&A.ctr->next_ray, (unsigned long long)kWarpChunk);
+                    b = __shfl_sync(kFull, b, 0);
+                    if (b >= (unsigned long long)n_rays) {
+                        exhausted = true;
+                        break;
+                    }
+                    wbase = (int)b;
+                    wend = min(wbase + kWarpChunk, n_rays);
+                }
+                const int take = min(__popc(idle), wend - wbase);
+                bool mine = false;
+                if ((idle >> lane) & 1u) {
+                    const int rank = __popc(idle & lt);
+                    if (rank < take) {
+                        ray = wbase + rank;
+                        mine = true;
+                    }
+                }
+                wbase += take;
+                if (mine) {
+                    const int64_t r = ray;
+                    float3 s = make_float3(__ldg(A.from + 3 * r), __ldg(A.from + 3 * r + 1), __ldg(A.from + 3 * r + 2));
+                    float3 e = make_float3(__ldg(A.to + 3 * r), __ldg(A.to + 3 * r + 1), __ldg(A.to + 3 * r + 2));
+                    if (bad3(s) || bad3(e)) {   // undefined answer: reported as ambiguous
+                        if (A.hit) A.hit[r] = 0;
+                        if (MODE == RSI_COUNT) A.count[r] = 0;
+                        if (A.amb) A.amb[r] = 1;
+                        ray = -1;
+                    } else {
+                        g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
+                        node = 0;
+                        sp = 0;
+                        cnt = plain_cnt = 0;
+                        found = band = false;
+                    }
+                }
+                idle = __ballot_sync(kFull, ray < 0);
+            }
+        }
+        if (__ballot_sync(kFull, ray >= 0) == 0) {
+            if (exhausted) break;
+            continue;
+        }
+        if (ray < 0) continue;
+        auto leaf = [&](int j) -> bool {
+            if (STATS) ++tests;
+            Tri tr = load_tri(A.tris, j);
+            bool plain;
+            int c = tri_fp32(g, tr, A.fp32_only != 0, plain);
+            plain_cnt += plain;
+            if (c == kBand && !A.fp32_only) {   // settled by the FP64 pass
+                band = true;
+                if (MODE == RSI_COUNT) return true;
+            }
+            if (c == kHit) {
+                ++cnt;
+                if (MODE == RSI_ANY_HIT) {
+                    found = true;
+                    return true;
+                }
+            }
+            return false;
+        };
+        bool done = false;
+        if (A.n_tri == 1) {
+            leaf(0);
+            done = true;
+        } else {
+            float4 lmin, lmax, rmin, rmax;
+            load_node(A.nodes, node, lmin, lmax, rmin, rmax);
+            if (STATS) ++visits;
+            const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
+            bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
+            if (hl && lref < 0) {
+                hl = false;
+                done = leaf(~lref);
+            }
+            if (!done && hr && rref < 0) {
+                hr = false;
+                done = leaf(~rref);
+            }
+            if (!done) {
+                if (hl && hr) {
+                    if (sp < STACK) {
+                        stack[sp++] = rref;
+                        node = lref;
+                    } else {   // cannot happen with STACK > tree height; queued
+                        raise_error(A.ctr, RSI_ERR_STACK);
+                        band = true;
+                        found = false;
+                        done = true;
+                    }
+                } else if (hl) {
+                    node = lref;
+                } else if (hr) {
+                    node = rref;
+                } else if (sp > 0) {
+                    node = stack[--sp];
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (done) {
+            const int64_t r = ray;
+            if (A.fp32_only) {   // plain FP32 closed-interval decisions, no re-test
+                if (MODE == RSI_ANY_HIT) A.hit[r] = (uint8_t)(found || plain_cnt > 0);
+                else {
+                    A.count[r] = plain_cnt;
+                    if (A.hit) A.hit[r] = (uint8_t)(plain_cnt > 0);
+                }
+                if (A.amb) A.amb[r] = 0;
+            } else if (MODE == RSI_ANY_HIT && found) {
+                A.hit[r] = 1;
+                if (A.amb) A.amb[r] = 0;
+            } else if (band) {
+                int pos = atomicAdd(&A.ctr->band_count, 1);
+                A.band_ids[pos] = ray;
+            } else {
+                if (MODE == RSI_ANY_HIT) A.hit[r] = 0;
+                else {
+                    A.count[r] = cnt;
+                    if (A.hit) A.hit[r] = (uint8_t)(cnt > 0);
+                }
+                if (A.amb) A.amb[r] = 0;
+            }
+            ray = -1;
+        }
+    }
+    if (STATS) {
+        for (int off = 16; off; off >>= 1) {
+            visits += __shfl_xor_sync(kFull, visits, off);
+            tests += __shfl_xor_sync(kFull, tests, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&A.ctr->node_visits, visits);
+            atomicAdd(&A.ctr->tri_tests, tests);
+        }
+    }
+}
+
+// Certain decisions in FP64 without square roots or divisions: the FP32 test
+// above in double precision, with the bound factor 32 u (u = 2^-53) and a
+// 1e-9 relative slack on tau, so that a certain answer is also the answer
+// the definition's own FP64 rounding gives.  kBand = undecided.
+__device__ __forceinline__ int tri_certain64(D3 s, D3 e, D3 a, D3 b, D3 c) {
+    const double u = 1.1102230246251565e-16, K = 32.0 * u, tau = kTauD * (1.0 + 1e-9);
+    const double dx = e.x - s.x, dy = e.y - s.y, dz = e.z - s.z;
+    const double e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+    const double e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+    const double sx = s.x - a.x, sy = s.y - a.y, sz = s.z - a.z;
+    const double px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
+    const double qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+    const double det = e1x * px + e1y * py + e1z * pz;
+    const double T = e2x * qx + e2y * qy + e2z * qz;
+    const double U = sx * px + sy * py + sz * pz, V = dx * qx + dy * qy + dz * qz;
+    const double adx = fabs(dx), ady = fabs(dy), adz = fabs(dz);
+    const double a1x = fabs(e1x), a1y = fabs(e1y), a1z = fabs(e1z);
+    const double a2x = fabs(e2x), a2y = fabs(e2y), a2z = fabs(e2z);
+    const double asx = fabs(sx), asy = fabs(sy), asz = fabs(sz);
+    const double pax = ady * a2z + adz * a2y, pay = adz * a2x + adx * a2z, paz = adx * a2y + ady * a2x;
+    const double qax = asy * a1z + asz * a1y, qay = asz * a1x + asx * a1z, qaz = asx * a1y + asy * a1x;
+    const double errdet = K * (a1x * pax + a1y * pay + a1z * paz) + 1e-300;
+    const double errT = K * (a2x * qax + a2y * qay + a2z * qaz) + 1e-300;
+    const double thr = tau * ((adx + ady + adz) * (a1x + a1y + a1z)) * (a2x + a2y + a2z);
+    const double Tm = T - det;
+    const double errTm = errT + errdet + 4.0 * u * (fabs(T) + fabs(det));
+    if ((T > 0.0) == (Tm > 0.0) && fmin(fabs(T) - errT, fabs(Tm) - errTm) > thr) return kMiss;
+    const double D = fabs(det);
+    if (D - errdet > thr) {
+        const double sg = det > 0.0 ? 1.0 : -1.0;
+        const double errU = K * (asx * pax + asy * pay + asz * paz) + 1e-300;
+        const double errV = K * (adx * qax + ady * qay + adz * qaz) + 1e-300;
+        const double Us = sg * U, Vs = sg * V, Ts = sg * T;
+        const double Ws = D - Us - Vs;
+        const double errW = errdet + errU + errV + 4.0 * u * (D + fabs(U) + fabs(V));
+        const double Tms = D - Ts;
+        const double lim = tau * (D + errdet);
+        if (Us - errU > lim && Vs - errV > lim && Ws - errW > lim && Ts - errT > lim && Tms - errTm > lim)
+            return kHit;
+        if (Us + errU < -lim || Vs + errV < -lim || Ws + errW < -lim || Ts + errT < -lim || Tms + errTm < -lim)
+            return kMiss;
+    }
+    return kBand;
+}
+
+// t of the definition with its own operations (so that crossings merge
+// exactly as the definition merges them).
+__device__ __forceinline__ double t_of_definition(D3 s, D3 e, D3 a, D3 b, D3 c) {
+    D3 d = dsub(e, s);
+    D3 e1 = dsub(b, a), e2 = dsub(c, a);
+    D3 p = dcross(d, e2);
+    double det = ddot(e1, p);
+    D3 q = dcross(dsub(s, a), e1);
+    return __ddiv_rn(ddot(e2, q), det);
+}
+
+// The queued segments, one warp each: lane 0 walks the tree and keeps the
+// leaves the FP32 test does not reject for certain (up to 32 at a time);
+// the lanes then classify those pairs side by side in FP64 -- a certain
+// decision from the numerators where possible, the definition itself
+// otherwise -- and the warp combines the classes.  A decisive hit ends a
+// boolean query; otherwise the closed-interval answer of an ambiguous
+// segment counts distinct crossings (t merged within 1e-9).
 template <int MODE, int STACK>
 __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
+    constexpr int kWarps = 4;
+    __shared__ double s_t[kWarps][kMaxInclusive];
+    __shared__ int s_cand[kWarps][32];
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int nb = *(volatile int*)&A.ctr->band_count;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    for (int k = blockIdx.x * kWarps + w; k < nb; k += gridDim.x * kWarps) {
         const int64_t r = A.band_ids[k];
-        float3 s = make_float3(A.from[3 * r], A.from[3 * r + 1], A.from[3 * r + 2]);
-        float3 e = make_float3(A.to[3 * r], A.to[3 * r + 1], A.to[3 * r + 2]);
-        SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
-        D3 sd = {(double)s.x, (double)s.y, (double)s.z}, ed = {(double)e.x, (double)e.y, (double)e.z};
+        const float3 s = make_float3(A.from[3 * r], A.from[3 * r + 1], A.from[3 * r + 2]);
+        const float3 e = make_float3(A.to[3 * r], A.to[3 * r + 1], A.to[3 * r + 2]);
+        const SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
+        const D3 sd = {(double)s.x, (double)s.y, (double)s.z}, ed = {(double)e.x, (double)e.y, (double)e.z};
         int n_hit = 0, n_amb = 0, n_incl = 0;
         bool overflow = false;
-        double ts[kMaxInclusive];
-        auto leaf = [&](int j) -> bool {
-            Tri tr = load_tri(A.tris, j);
-            double t;
-            bool incl;
-            int c = classify_fp64(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2), t, incl);
-            if (c == kHit) ++n_hit;
-            else if (c == kBand) ++n_amb;
+        int node = 0, sp = 0;
+        int stack[STACK];
+        bool trav_done = false;
+        while (true) {
+            int nc = 0;
+            if (lane == 0) {
+                if (A.n_tri == 1) {
+                    s_cand[w][nc++] = 0;
+                    trav_done = true;
+                }
+                while (!trav_done && nc <= 30) {
+                    float4 lmin, lmax, rmin, rmax;
+                    load_node(A.nodes, node, lmin, lmax, rmin, rmax);
+                    const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
+                    bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
+                    bool plain;
+                    if (hl && lref < 0) {
+                        hl = false;
+                        if (tri_fp32(g, load_tri(A.tris, ~lref), false, plain) != kMiss) s_cand[w][nc++] = ~lref;
+                    }
+                    if (hr && rref < 0) {
+                        hr = false;
+                        if (tri_fp32(g, load_tri(A.tris, ~rref), false, plain) != kMiss) s_cand[w][nc++] = ~rref;
+                    }
+                    if (hl && hr) {
+                        if (sp < STACK) {
+                            stack[sp++] = rref;
+                            node = lref;
+                        } else {
+                            raise_error(A.ctr, RSI_ERR_STACK);
+                            trav_done = true;
+                        }
+                    } else if (hl) {
+                        node = lref;
+                    } else if (hr) {
+                        node = rref;
+                    } else if (sp > 0) {
+                        node = stack[--sp];
+                    } else {
+                        trav_done = true;
+                    }
+                }
+            }
+            nc = __shfl_sync(kFull, nc, 0);
+            trav_done = __shfl_sync(kFull, trav_done ? 1 : 0, 0) != 0;
+            __syncwarp();
+            int cls = -1;
+            bool incl = false;
+            double t = 0.0;
+            if (lane < nc) {
+                const Tri tr = load_tri(A.tris, s_cand[w][lane]);
+                const D3 a = d3of(tr.v0), b = d3of(tr.v1), c = d3of(tr.v2);
+                cls = tri_certain64(sd, ed, a, b, c);
+                if (cls == kHit) {
+                    incl = true;
+                    t = t_of_definition(sd, ed, a, b, c);
+                } else if (cls == kBand) {
+                    cls = classify_fp64(sd, ed, a, b, c, t, incl);
+                }
+            }
+            const unsigned mh = __ballot_sync(kFull, cls == kHit);
+            const unsigned ma = __ballot_sync(kFull, cls == kBand);
+            const unsigned mi = __ballot_sync(kFull, incl);
             if (incl) {
-                if (n_incl < kMaxInclusive) ts[n_incl++] = t;
+                const int pos = n_incl + __popc(mi & lt);
+                if (pos < kMaxInclusive) s_t[w][pos] = t;
                 else overflow = true;
             }
-            return MODE == RSI_ANY_HIT && c == kHit;   // a decisive hit settles it
-        };
-        unsigned long long dummy = 0;
-        bool ok = traverse<STACK, false>(A, g, leaf, dummy);
-        if (!ok) raise_error(A.ctr, RSI_ERR_STACK);
-        if (overflow) raise_error(A.ctr, RSI_ERR_OVERFLOW);
-        if (MODE == RSI_ANY_HIT) {
-            bool amb = n_hit == 0 && n_amb > 0;
-            A.hit[r] = (uint8_t)(n_hit > 0 || (amb && n_incl > 0));
-            if (A.amb) A.amb[r] = (uint8_t)amb;
-            if (amb) atomicAdd(&A.ctr->ambiguous, 1ull);
-        } else {
-            bool amb = n_amb > 0;
-            int count = n_hit;
-            if (amb) {
-                // distinct crossing points: sort t, start a new one at each gap > 1e-9
-                for (int i = 1; i < n_incl; ++i) {
-                    double x = ts[i];
-                    int k2 = i - 1;
-                    while (k2 >= 0 && ts[k2] > x) {
-                        ts[k2 + 1] = ts[k2];
-                        --k2;
-                    }
-                    ts[k2 + 1] = x;
-                }
-                count = 0;
-                for (int i = 0; i < n_incl; ++i)
-                    if (i == 0 || __dsub_rn(ts[i], ts[i - 1]) > kTMerge) ++count;
-                atomicAdd(&A.ctr->ambiguous, 1ull);
-            }
-            A.count[r] = count;
-            if (A.hit) A.hit[r] = (uint8_t)(count > 0);
-            if (A.amb) A.amb[r] = (uint8_t)amb;
+            n_hit += __popc(mh);
+            n_amb += __popc(ma);
+            n_incl += __popc(mi);
+            overflow = __any_sync(kFull, overflow);
+            __syncwarp();
+            if ((MODE == RSI_ANY_HIT && mh) || trav_done) break;
         }
+        if (lane == 0) {
+            if (overflow) raise_error(A.ctr, RSI_ERR_OVERFLOW);
+            const int m = min(n_incl, kMaxInclusive);
+            if (MODE == RSI_ANY_HIT) {
+                const bool amb = n_hit == 0 && n_amb > 0;
+                A.hit[r] = (uint8_t)(n_hit > 0 || (amb && n_incl > 0));
+                if (A.amb) A.amb[r] = (uint8_t)amb;
+                if (amb) atomicAdd(&A.ctr->ambiguous, 1ull);
+            } else {
+                const bool amb = n_amb > 0;
+                int count = n_hit;
+                if (amb) {
+                    double* ts = s_t[w];
+                    for (int i = 1; i < m; ++i) {   // insertion sort of the crossing parameters
+                        const double x = ts[i];
+                        int k2 = i - 1;
+                        while (k2 >= 0 && ts[k2] > x) {
+                            ts[k2 + 1] = ts[k2];
+                            --k2;
+                        }
+                        ts[k2 + 1] = x;
+                    }
+                    count = 0;
+                    for (int i = 0; i < m; ++i)
+                        if (i == 0 || __dsub_rn(ts[i], ts[i - 1]) > kTMerge) ++count;
+                    atomicAdd(&A.ctr->ambiguous, 1ull);
+                }
+                A.count[r] = count;
+                if (A.hit) A.hit[r] = (uint8_t)(count > 0);
+                if (A.amb) A.amb[r] = (uint8_t)amb;
+            }
+        }
+        __syncwarp();
     }
 }
 
 __global__ void k_reset_query(DevCounters* c) {
     c->band_count = 0;
+    c->next_ray = 0;
     c->error = 0;
     c->node_visits = c->tri_tests = c->ambiguous = 0;
 }
