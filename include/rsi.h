@@ -68,7 +68,10 @@ typedef struct rsi_options {
     int64_t timeout_ns; /* bounded waits of the batched kernel, 0 = 2 s     */
     int time_kernels;   /* 1: record CUDA events around the traversal and
                            re-test kernels on `stream` (rsi_last_query_ms) */
-    int reserved;
+    int ray_sort_tile;  /* 0: segments traversed in input order; 256..8192:
+                           each tile of this many segments is first grouped
+                           by a coarse Morton cell of the segment midpoints
+                           (better warp coherence; results are unchanged)  */
 } rsi_options;
 
 /* Per-query counters, filled on the host when a non-NULL pointer is given
@@ -180,7 +183,7 @@ int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t 
  * failure of) a cudaMalloc.  The hierarchy must already be built.
  *
  * Same arguments and results as rsi_query, except that no statistics are
- * returned and opt->time_kernels is ignored.  The per-call scratch (the
+ * returned and opt->time_kernels and opt->ray_sort_tile are ignored.  The per-call scratch (the
  * queue of segments re-tested in FP64 and the call's counters) lives in one
  * fixed device array of 256 B + 4 B x RSI_NOALLOC_MAX_RAYS (about 8 MiB)
  * that every GPU which loads the library keeps until the process exits.

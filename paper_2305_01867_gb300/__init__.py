@@ -36,7 +36,7 @@ class RSIError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("fp32_only", ctypes.c_int), ("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("collect_stats", ctypes.c_int), ("timeout_ns", ctypes.c_int64), ("time_kernels", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("ray_sort_tile", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -204,7 +204,7 @@ class LBVH:
 
     def query(self, ray_from, ray_to, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0,
               stats=False, hit=None, count=None, ambiguous=None, want_ambiguous=True, time_kernels=False,
-              stream=None):
+              ray_sort_tile=0, stream=None):
         """Query segments (device tensors [n, 3] float32).  Returns a dict with
         'hit' (uint8, any-hit mode or count > 0), 'count' (int32, count mode),
         'ambiguous' (uint8) and, with stats=True, 'stats'."""
@@ -224,7 +224,8 @@ class LBVH:
             count = torch.empty(n, dtype=torch.int32, device=dev)
         if ambiguous is None and want_ambiguous:
             ambiguous = torch.empty(n, dtype=torch.uint8, device=dev)
-        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels), 0)
+        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels),
+                      int(ray_sort_tile))
         st = Stats()
         check(lib.rsi_query(self._h, _ptr(ray_from), _ptr(ray_to), n, m, ctypes.byref(opt), _ptr(hit), _ptr(count),
                             _ptr(ambiguous), ctypes.byref(st) if stats else None, _stream(stream)))

@@ -41,6 +41,7 @@ struct QueryArgs {
     int32_t* count;
     uint8_t* amb;
     int32_t* band_ids;
+    const int32_t* perm;   // traversal order of the segments, or NULL
     DevCounters* ctr;
     float dmax0, dmax1, dmax2;
     int fp32_only;
@@ -293,12 +294,21 @@ __device__ int classify_fp64(D3 s, D3 e, D3 a, D3 b, D3 c, double& t_out, bool& 
 constexpr int kWarpChunk = 64;   // segments a warp takes per atomic
 constexpr int kRefillMin = 4;    // refill once this many lanes of a warp are idle
 
-// Warp-coherent persistent traversal.  Every iteration, each active lane
-// processes exactly one node (both child boxes, leaf children tested in
-// place), so the lanes of a warp stay in step; lanes whose segment is done
-// are refilled together from a per-warp chunk of segment indices taken with
-// one atomic.  A segment with a band pair and no certain answer is queued
-// for k_query_fp64 (count mode stops at the first band pair).
+constexpr int kLeafMin = 12;     // run the triangle tests once this many lanes hold one
+constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^30)
+
+// Warp-coherent persistent traversal with deferred leaf tests.  Each lane
+// holds its next reference (internal node >= 0, leaf ~j < 0, or kDone) and a
+// one-entry leaf slot.  Every iteration a lane whose next reference is an
+// internal node fetches it and tests both child boxes (the nearer-listed hit
+// child becomes next, the other is pushed; leaves travel as references too);
+// a lane whose next reference is a leaf parks it in its slot if the slot is
+// free.  The warp runs the triangle tests of all parked leaves together once
+// kLeafMin lanes hold one or no lane can move on without it, so node work and
+// triangle work both run with most lanes active.  Lanes whose segment is done
+// are refilled together from a per-warp chunk of segment indices (one atomic
+// per chunk).  A segment with a band pair and no certain answer is queued for
+// k_query_fp64 (count mode stops at the first band pair).
 template <int MODE, bool STATS, int STACK>
 __global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
     const unsigned kFull = 0xffffffffu;
@@ -310,10 +320,10 @@ __global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
     bool exhausted = false;      // warp-uniform
     int ray = -1;
     SegF g;
-    int node = 0, sp = 0;
+    int next = kDone, slot = -1, sp = 0;
     int stack[STACK];
     int cnt = 0, plain_cnt = 0;
-    bool found = false, band = false;
+    bool found = false, band = false, stop = false;
     while (true) {
         unsigned idle = __ballot_sync(kFull, ray < 0);
         if (!exhausted && (__popc(idle) >= kRefillMin || idle == kFull)) {
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
                 if ((idle >> lane) & 1u) {
                     const int rank = __popc(idle & lt);
                     if (rank < take) {
-                        ray = wbase + rank;
+                        ray = A.perm ? __ldg(A.perm + wbase + rank) : wbase + rank;
                         mine = true;
                     }
                 }
@@ -350,80 +360,75 @@ __global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
                         ray = -1;
                     } else {
                         g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
-                        node = 0;
+                        next = A.n_tri == 1 ? ~0 : 0;
+                        slot = -1;
                         sp = 0;
                         cnt = plain_cnt = 0;
-                        found = band = false;
+                        found = band = stop = false;
                     }
                 }
                 idle = __ballot_sync(kFull, ray < 0);
             }
         }
-        if (__ballot_sync(kFull, ray >= 0) == 0) {
+        const bool active = ray >= 0;
+        const unsigned act = __ballot_sync(kFull, active);
+        if (act == 0) {
             if (exhausted) break;
             continue;
         }
-        if (ray < 0) continue;
-        auto leaf = [&](int j) -> bool {
-            if (STATS) ++tests;
-            Tri tr = load_tri(A.tris, j);
-            bool plain;
-            int c = tri_fp32(g, tr, A.fp32_only != 0, plain);
-            plain_cnt += plain;
-            if (c == kBand && !A.fp32_only) {   // settled by the FP64 pass
-                band = true;
-                if (MODE == RSI_COUNT) return true;
-            }
-            if (c == kHit) {
-                ++cnt;
-                if (MODE == RSI_ANY_HIT) {
-                    found = true;
-                    return true;
-                }
-            }
-            return false;
-        };
-        bool done = false;
-        if (A.n_tri == 1) {
-            leaf(0);
-            done = true;
-        } else {
+        // node step
+        if (active && next != kDone && next >= 0) {
             float4 lmin, lmax, rmin, rmax;
-            load_node(A.nodes, node, lmin, lmax, rmin, rmax);
+            load_node(A.nodes, next, lmin, lmax, rmin, rmax);
             if (STATS) ++visits;
             const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
-            bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
-            if (hl && lref < 0) {
-                hl = false;
-                done = leaf(~lref);
-            }
-            if (!done && hr && rref < 0) {
-                hr = false;
-                done = leaf(~rref);
-            }
-            if (!done) {
-                if (hl && hr) {
-                    if (sp < STACK) {
-                        stack[sp++] = rref;
-                        node = lref;
-                    } else {   // cannot happen with STACK > tree height; queued
-                        raise_error(A.ctr, RSI_ERR_STACK);
-                        band = true;
-                        found = false;
-                        done = true;
-                    }
-                } else if (hl) {
-                    node = lref;
-                } else if (hr) {
-                    node = rref;
-                } else if (sp > 0) {
-                    node = stack[--sp];
-                } else {
-                    done = true;
+            const bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
+            if (hl && hr) {
+                if (sp < STACK) {
+                    stack[sp++] = rref;
+                    next = lref;
+                } else {   // cannot happen with STACK > tree height; queued
+                    raise_error(A.ctr, RSI_ERR_STACK);
+                    band = true;
+                    stop = true;
                 }
+            } else if (hl) {
+                next = lref;
+            } else if (hr) {
+                next = rref;
+            } else {
+                next = sp > 0 ? stack[--sp] : kDone;
             }
         }
-        if (done) {
+        // park a leaf reference
+        if (active && !stop && next < 0 && slot < 0) {
+            slot = ~next;
+            next = sp > 0 ? stack[--sp] : kDone;
+        }
+        // leaf phase: all parked leaves of the warp at once
+        const unsigned pend = __ballot_sync(kFull, active && slot >= 0);
+        const unsigned moving = __ballot_sync(kFull, active && !stop && next != kDone && (next >= 0 || slot < 0));
+        if (pend && (__popc(pend) >= kLeafMin || moving == 0)) {
+            if (slot >= 0) {
+                if (STATS) ++tests;
+                const Tri tr = load_tri(A.tris, slot);
+                bool plain;
+                int c = tri_fp32(g, tr, A.fp32_only != 0, plain);
+                plain_cnt += plain;
+                if (c == kBand && !A.fp32_only) {   // settled by the FP64 pass
+                    band = true;
+                    if (MODE == RSI_COUNT) stop = true;
+                } else if (c == kHit) {
+                    ++cnt;
+                    if (MODE == RSI_ANY_HIT) {
+                        found = true;
+                        stop = true;
+                    }
+                }
+                slot = -1;
+            }
+        }
+        if (active && (stop || (next == kDone && slot < 0))) {
             const int64_t r = ray;
             if (A.fp32_only) {   // plain FP32 closed-interval decisions, no re-test
                 if (MODE == RSI_ANY_HIT) A.hit[r] = (uint8_t)(found || plain_cnt > 0);
@@ -652,6 +657,71 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
     }
 }
 
+// In-tile reordering of segments for warp coherence: a counting sort of each
+// tile by the top 10 bits of the 30-bit Morton code of the segment midpoint
+// (normalised by the mesh extent).  perm[base .. base + m) becomes a
+// permutation of the tile's indices; order inside a cell is arbitrary, which
+// is harmless because every segment's answer is independent of the order.
+constexpr int kSortBins = 1024;
+constexpr int kMaxSortTile = 8192;
+
+__device__ __forceinline__ uint32_t spread10q(uint32_t x) {
+    x &= 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__global__ void __launch_bounds__(256) k_ray_tile_sort(const float* __restrict__ from, const float* __restrict__ to,
+                                                       int n, int tile, float lox, float loy, float loz, float sx,
+                                                       float sy, float sz, int32_t* __restrict__ perm) {
+    __shared__ int cnt[kSortBins];
+    __shared__ unsigned short key[kMaxSortTile];
+    __shared__ int wsum[8];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kSortBins; i += 256) cnt[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * tile;
+    const int m = (int)min((int64_t)tile, (int64_t)n - base);
+    for (int i = tid; i < m; i += 256) {
+        const int64_t r = base + i;
+        float mx = 0.5f * (from[3 * r] + to[3 * r]);
+        float my = 0.5f * (from[3 * r + 1] + to[3 * r + 1]);
+        float mz = 0.5f * (from[3 * r + 2] + to[3 * r + 2]);
+        uint32_t qx = (uint32_t)fminf(fmaxf((mx - lox) * sx, 0.0f), 1023.0f);
+        uint32_t qy = (uint32_t)fminf(fmaxf((my - loy) * sy, 0.0f), 1023.0f);
+        uint32_t qz = (uint32_t)fminf(fmaxf((mz - loz) * sz, 0.0f), 1023.0f);   // NaN -> 0
+        uint32_t k = (spread10q(qx) | (spread10q(qy) << 1) | (spread10q(qz) << 2)) >> 20;
+        key[i] = (unsigned short)k;
+        atomicAdd(&cnt[k], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the 1024 bins: 4 per thread, then across warps
+    int v0 = cnt[4 * tid], v1 = cnt[4 * tid + 1], v2 = cnt[4 * tid + 2], v3 = cnt[4 * tid + 3];
+    int tot = v0 + v1 + v2 + v3, inc = tot;
+    const int lane = tid & 31, w = tid >> 5;
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int wpre = 0;
+    for (int j = 0; j < w; ++j) wpre += wsum[j];
+    int ex = wpre + inc - tot;
+    cnt[4 * tid] = ex;
+    cnt[4 * tid + 1] = ex + v0;
+    cnt[4 * tid + 2] = ex + v0 + v1;
+    cnt[4 * tid + 3] = ex + v0 + v1 + v2;
+    __syncthreads();
+    for (int i = tid; i < m; i += 256) {
+        int pos = atomicAdd(&cnt[key[i]], 1);
+        perm[base + pos] = (int32_t)(base + i);
+    }
+}
+
 __global__ void k_reset_query(DevCounters* c) {
     c->band_count = 0;
     c->next_ray = 0;
@@ -682,8 +752,8 @@ void launch_fp64(const QueryArgs& A, int height, int grid, cudaStream_t s) {
 
 // Launch the two passes for one batch of segments already on the device.
 int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n, int mode, const rsi_options* opt,
-                 uint8_t* d_hit, int32_t* d_count, uint8_t* d_amb, int32_t* band_ids, DevCounters* ctr,
-                 cudaStream_t s) {
+                 uint8_t* d_hit, int32_t* d_count, uint8_t* d_amb, int32_t* band_ids, int32_t* perm_scratch,
+                 DevCounters* ctr, cudaStream_t s) {
     rsi_options o = {};
     if (opt) o = *opt;
     if (h->height >= 127) return fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
@@ -698,6 +768,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     A.count = d_count;
     A.amb = d_amb;
     A.band_ids = band_ids;
+    A.perm = nullptr;
     A.ctr = ctr;
     A.dmax0 = h->dmax[0];
     A.dmax1 = h->dmax[1];
@@ -715,6 +786,18 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
         for (auto& e : h->ev) RSI_CUDA_TRY(cudaEventCreate(&e));
     }
     h->timed = o.time_kernels != 0;
+    if (o.ray_sort_tile != 0) {
+        if (o.ray_sort_tile < 256 || o.ray_sort_tile > kMaxSortTile)
+            return fail(RSI_ERR_INVALID_ARG, "rsi_query: ray_sort_tile must be 0 or in [256, 8192]");
+        if (!perm_scratch) return fail(RSI_ERR_INVALID_ARG, "rsi_query: ray_sort_tile needs scratch");
+        float sc[3];
+        for (int a = 0; a < 3; ++a) sc[a] = h->hi[a] > h->lo[a] ? 1024.0f / (h->hi[a] - h->lo[a]) : 0.0f;
+        k_ray_tile_sort<<<grid_for(n, o.ray_sort_tile), 256, 0, s>>>(d_from, d_to, (int)n, o.ray_sort_tile, h->lo[0],
+                                                                     h->lo[1], h->lo[2], sc[0], sc[1], sc[2],
+                                                                     perm_scratch);
+        note_launches(1);
+        A.perm = perm_scratch;
+    }
     k_reset_query<<<1, 1, 0, s>>>(ctr);
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[0], s));
     if (mode == RSI_ANY_HIT) {
@@ -745,7 +828,7 @@ int ensure_band_capacity(rsi_bvh_t h, int64_t n, cudaStream_t s) {
         h->band_ids = nullptr;
         h->band_cap = 0;
     }
-    if (cudaMalloc(&h->band_ids, 4 * (size_t)cap) != cudaSuccess) {
+    if (cudaMalloc(&h->band_ids, 8 * (size_t)cap) != cudaSuccess) {   // band list, then permutation
         cudaGetLastError();
         return fail(RSI_ERR_OOM, "rsi_query: band list allocation failed");
     }
@@ -808,7 +891,8 @@ extern "C" int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, in
     }
     rc = rsi::ensure_band_capacity(h, n_rays, s);
     if (rc) return rc;
-    rc = rsi::query_device(h, d_from, d_to, n_rays, mode, opt, d_hit, d_count, d_ambiguous, h->band_ids, h->ctr, s);
+    rc = rsi::query_device(h, d_from, d_to, n_rays, mode, opt, d_hit, d_count, d_ambiguous, h->band_ids,
+                           h->band_ids + h->band_cap, h->ctr, s);
     if (rc) return rc;
     if (stats) return rsi::read_stats(h, h->ctr, n_rays, stats, s);
     return RSI_OK;
@@ -843,7 +927,8 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
         rc = rsi::fail(RSI_ERR_OOM, "rsi_query_host: staging allocation failed");
     }
     if (rc == RSI_OK)
-        rc = rsi::query_device(h, df, dt, n_rays, mode, opt, dh, dc, da, h->band_ids, h->ctr, s);
+        rc = rsi::query_device(h, df, dt, n_rays, mode, opt, dh, dc, da, h->band_ids, h->band_ids + h->band_cap,
+                               h->ctr, s);
     if (rc == RSI_OK) {
         bool c_ok = true;
         if (h_hit) c_ok &= cudaMemcpyAsync(h_hit, dh, n_rays, cudaMemcpyDeviceToHost, s) == cudaSuccess;
@@ -908,8 +993,9 @@ extern "C" int rsi_query_noalloc(rsi_bvh_t h, const float* d_from, const float* 
     if (opt) o = *opt;
     o.time_kernels = 0;
     o.collect_stats = 0;
+    o.ray_sort_tile = 0;
     auto* ctr = reinterpret_cast<rsi::DevCounters*>(base);
     auto* band = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(base) + kNoallocHeader);
-    return rsi::query_device(h, d_from, d_to, n_rays, mode, &o, d_hit, d_count, d_ambiguous, band, ctr,
+    return rsi::query_device(h, d_from, d_to, n_rays, mode, &o, d_hit, d_count, d_ambiguous, band, nullptr, ctr,
                              (cudaStream_t)stream);
 }

@@ -213,3 +213,19 @@ def test_bad_launch_shape_rejected(rsi):
         with pytest.raises(rsi.RSIError) as e:
             bvh.query(_dev(F), _dev(E), "any_hit", block=block)
         assert e.value.code == -1
+
+
+@pytest.mark.parametrize("tile", [256, 1000, 4096, 8192])
+def test_ray_sort_tile_changes_nothing(rsi, tile):
+    """Reordering segments inside tiles before traversal leaves every answer
+    unchanged (ragged last tile included)."""
+    mesh = W.config_mesh("c2")
+    F, E = W.rays(W.config_rays("c2", 200_003), mesh)
+    bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles))
+    dF, dE = _dev(F), _dev(E)
+    for mode, key in (("any_hit", "hit"), ("count", "count")):
+        a = bvh.query(dF, dE, mode)
+        b = bvh.query(dF, dE, mode, ray_sort_tile=tile)
+        assert torch.equal(a[key], b[key]) and torch.equal(a["ambiguous"], b["ambiguous"])
+    with pytest.raises(rsi.RSIError):
+        bvh.query(dF, dE, "any_hit", ray_sort_tile=100)
