@@ -182,6 +182,55 @@ def cpu_baseline(mesh, spec, n):
                       f"(both modes in one pass), {dt:.1f} s"}
 
 
+def measure_batched(rsi, torch, dev, c4, args):
+    """64 independent heightfields with log-uniform triangle counts in
+    [1e3, 1e5] and segment counts in [1e4, 1e7]: one graph-launched
+    persistent traversal over all of them (rsi_query_batched), against the
+    same work issued as 64 separate rsi_query calls."""
+    jobs, rays = c4
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    bvhs = [rsi.LBVH(torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.triangles).to(dev)) for m, _ in jobs]
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    items = [(b, torch.from_numpy(F).to(dev), torch.from_numpy(E).to(dev)) for b, (F, E) in zip(bvhs, rays)]
+    total = sum(int(f.shape[0]) for _, f, _ in items)
+    steps = max(3, min(args.steps, 10))
+    out = {"n_meshes": len(jobs), "triangles": int(sum(len(m.triangles) for m, _ in jobs)), "rays": total,
+           "build_all_ms": build_ms, "steps": steps}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    for mode in ("any_hit", "count"):
+        plan = rsi.BatchPlan(items, mode)
+        ms = timed(plan.run)
+        outs = {}
+
+        def sequential():
+            for i, (b, f, t) in enumerate(items):
+                key = "hit" if mode == "any_hit" else "count"
+                buf = plan.hit[i] if mode == "any_hit" else plan.count[i]
+                outs[i] = b.query(f, t, mode, **{key: buf}, ambiguous=plan.ambiguous[i])
+        ms_seq = timed(sequential)
+        st = plan.stats()
+        out[mode] = {"rays_per_s": total / (ms / 1e3), "ms": ms, "sequential_rays_per_s": total / (ms_seq / 1e3),
+                     "sequential_ms": ms_seq, "band_rays": st["band_rays"], "ambiguous": st["ambiguous"]}
+        plan.close()
+    for b in bvhs:
+        b.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,6 +241,7 @@ def main():
     ap.add_argument("--ref-rays", type=int, default=20_000)
     ap.add_argument("--cpu-sample", type=int, default=600_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local, pg = dist_setup(args)
@@ -208,12 +258,16 @@ def main():
     import paper_2305_01867_gb300 as rsi
     import workloads as W
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     mesh = W.config_mesh("c2")
     spec = W.config_rays("c2", args.rays)
     spec.seed = spec.seed + 1000 * rank          # each rank its own batch (weak scaling)
     F, E = W.rays(spec, mesh)
+    c4 = None
+    if not args.no_batched and rank == 0:
+        jobs = W.batched_meshes(n_meshes=64, seed=4)
+        c4 = (jobs, W.rays_many(jobs))           # process pool before any GPU call
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     n = len(F)
     pF, pE = torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory()
     pV, pT = torch.from_numpy(mesh.vertices).pin_memory(), torch.from_numpy(mesh.triangles).pin_memory()
@@ -340,6 +394,8 @@ def main():
                      "ambiguous_count": st_c["ambiguous"], "node_visits_per_ray_any": st_a["node_visits"] / n,
                      "band_rays_any": st_a["band_rays"], "ambiguous_any": st_a["ambiguous"]},
     }
+    if c4 is not None:
+        line["batched_c4"] = measure_batched(rsi, torch, dev, c4, args)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mesh, W.config_rays("c2"), args.cpu_sample)
     print(json.dumps(line))

@@ -65,7 +65,9 @@ typedef struct rsi_options {
     int blocks_per_sm;  /* resident blocks per SM for the persistent grid,
                            0 = tuned                                         */
     int collect_stats;  /* 1: count node visits and triangle tests          */
-    int64_t timeout_ns; /* bounded waits of the batched kernel, 0 = 2 s     */
+    int64_t timeout_ns; /* batched plans: > 0 bounds the device waits of a
+                           streaming plan (0 = 2 s); < 0 makes the plan
+                           streaming with a |timeout_ns| bound             */
     int time_kernels;   /* 1: record CUDA events around the traversal and
                            re-test kernels on `stream` (rsi_last_query_ms) */
     int ray_sort_tile;  /* 0: segments traversed in input order; 256..8192:
@@ -201,6 +203,57 @@ int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t 
 int rsi_query_noalloc(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
                       const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
                       void* stream);
+
+/*
+ * Batched queries: many independent meshes, each with its own segments.
+ * Each segment gets the boolean or intercept_count answer of Sec. 1 against
+ * its own mesh, exactly as rsi_query would give it; batching (one persistent
+ * launch over all batches, a device work queue, a CUDA graph) has no
+ * counterpart in the paper.
+ *   bvh       built hierarchy (must outlive the plan)
+ *   d_from/d_to/n_rays, d_hit/d_count/d_ambiguous: as in rsi_query, device.
+ */
+typedef struct rsi_ray_batch {
+    rsi_bvh_t bvh;
+    const float* d_from;
+    const float* d_to;
+    int64_t n_rays;
+    uint8_t* d_hit;
+    int32_t* d_count;
+    uint8_t* d_ambiguous;
+} rsi_ray_batch;
+
+typedef struct rsi_batch_s* rsi_batch_t;
+
+/* Plan a batched query: validates the batches, uploads a descriptor table
+ * (total segments < 2^31), and captures reset + traversal + FP64 pass into a
+ * CUDA graph.  The buffers named in `batches` are fixed for the plan's life.
+ * opt->timeout_ns < 0 selects streaming: the work queue starts empty and the
+ * caller makes segments available with rsi_batch_post (|timeout_ns| bounds
+ * each wait of the kernel for a post, then RSI_ERR_TIMEOUT is raised and the
+ * unposted segments are left untouched).  opt->ray_sort_tile is ignored.
+ * Synchronizes `stream`. */
+int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int mode, const rsi_options* opt,
+                     void* stream, rsi_batch_t* out);
+
+/* Replay the plan on `stream` (one graph launch, asynchronous). */
+int rsi_query_batched(rsi_batch_t plan, void* stream);
+
+/* Streaming plans only: segments [0, n_ready) of the concatenated batches
+ * (batch 0's, then batch 1's, ...) are now in device memory.  Call after
+ * rsi_query_batched for the run being fed, on a stream other than the one
+ * running the plan, after the copies of those segments on that stream
+ * (stream order makes them visible first; the post also waits for the run's
+ * queue reset, not for the run).  Counts must not decrease; at most 256
+ * posts per plan may be pending. */
+int rsi_batch_post(rsi_batch_t plan, int64_t n_ready, void* stream);
+
+/* Counters of the plan's last run (synchronizes `stream`); returns the
+ * device error (e.g. RSI_ERR_TIMEOUT) if a kernel raised one. */
+int rsi_batch_stats(rsi_batch_t plan, rsi_stats* out, void* stream);
+
+/* Release a plan (synchronizes the device first).  NULL is a no-op. */
+int rsi_batch_free(rsi_batch_t plan);
 
 /* Durations of the FP32 traversal kernel and of the FP64 re-test kernel of
  * the last query on `h` that ran with time_kernels = 1, from CUDA events

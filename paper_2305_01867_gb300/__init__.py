@@ -59,6 +59,12 @@ class HostView(ctypes.Structure):
                 ("right", ctypes.c_void_p), ("parent", ctypes.c_void_p), ("box", ctypes.c_void_p)]
 
 
+class RayBatch(ctypes.Structure):
+    _fields_ = [("bvh", ctypes.c_void_p), ("d_from", ctypes.c_void_p), ("d_to", ctypes.c_void_p),
+                ("n_rays", ctypes.c_int64), ("d_hit", ctypes.c_void_p), ("d_count", ctypes.c_void_p),
+                ("d_ambiguous", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"librsi.so is not built ({_LIB_PATH}); run paper_2305_01867_gb300.build_library()")
@@ -79,6 +85,14 @@ def _load():
     lib.rsi_last_query_ms.restype = ctypes.c_int
     lib.rsi_kernel_launches.argtypes = []
     lib.rsi_kernel_launches.restype = ctypes.c_uint64
+    lib.rsi_batch_create.argtypes = [ctypes.POINTER(RayBatch), i32, i32, ctypes.POINTER(Options), P,
+                                     ctypes.POINTER(P)]
+    lib.rsi_query_batched.argtypes = [P, P]
+    lib.rsi_batch_post.argtypes = [P, i64, P]
+    lib.rsi_batch_stats.argtypes = [P, ctypes.POINTER(Stats), P]
+    lib.rsi_batch_free.argtypes = [P]
+    for name in ("rsi_batch_create", "rsi_query_batched", "rsi_batch_post", "rsi_batch_stats", "rsi_batch_free"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.rsi_last_error.restype = ctypes.c_char_p
     lib.rsi_last_error.argtypes = []
     for name in ("lbvh_build", "lbvh_build_host", "lbvh_free", "lbvh_info", "lbvh_export", "rsi_query",
@@ -257,3 +271,62 @@ class LBVH:
         if stats:
             out["stats"] = st.as_dict()
         return out
+
+
+class BatchPlan:
+    """Many (hierarchy, segments) pairs answered by one graph-launched
+    persistent traversal (rsi_batch_create / rsi_query_batched).
+
+    items: list of (LBVH, ray_from, ray_to) with device tensors.  Outputs
+    are allocated here: .hit / .count / .ambiguous are lists of tensors.
+    stream_timeout_ns > 0 makes a streaming plan fed by post()."""
+
+    def __init__(self, items, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0, stats=False,
+                 stream_timeout_ns=0, stream=None):
+        import torch
+        m = _mode(mode)
+        self.mode = m
+        self.items = items
+        self.hit, self.count, self.ambiguous = [], [], []
+        arr = (RayBatch * len(items))()
+        for i, (bvh, f, t) in enumerate(items):
+            _check_f32x3(f, "ray_from")
+            _check_f32x3(t, "ray_to")
+            n = f.shape[0]
+            h = torch.empty(n, dtype=torch.uint8, device=f.device) if m == RSI_ANY_HIT else None
+            c = torch.empty(n, dtype=torch.int32, device=f.device) if m == RSI_COUNT else None
+            a = torch.empty(n, dtype=torch.uint8, device=f.device)
+            self.hit.append(h)
+            self.count.append(c)
+            self.ambiguous.append(a)
+            arr[i] = RayBatch(bvh.handle.value, f.data_ptr(), t.data_ptr(), n, h.data_ptr() if h is not None else None,
+                              c.data_ptr() if c is not None else None, a.data_ptr())
+        timeout = -int(stream_timeout_ns) if stream_timeout_ns else 0
+        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), timeout, 0, 0)
+        self._p = ctypes.c_void_p()
+        check(lib.rsi_batch_create(arr, len(items), m, ctypes.byref(opt), _stream(stream), ctypes.byref(self._p)))
+        self.total = sum(int(f.shape[0]) for _, f, _ in items)
+
+    def run(self, stream=None):
+        check(lib.rsi_query_batched(self._p, _stream(stream)))
+
+    def post(self, n_ready, stream=None):
+        check(lib.rsi_batch_post(self._p, int(n_ready), _stream(stream)))
+
+    def stats(self, stream=None, raise_on_error=True):
+        st = Stats()
+        rc = lib.rsi_batch_stats(self._p, ctypes.byref(st), _stream(stream))
+        if raise_on_error:
+            check(rc)
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_p", None) and self._p.value:
+            lib.rsi_batch_free(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "rsi_internal.cuh"
 
@@ -45,6 +46,30 @@ struct QueryArgs {
     DevCounters* ctr;
     float dmax0, dmax1, dmax2;
     int fp32_only;
+};
+
+// One (hierarchy, segment batch, outputs) triple of a batched query.
+struct BatchDesc {
+    const Node* nodes;
+    const Tri* tris;
+    const float* from;
+    const float* to;
+    uint8_t* hit;
+    int32_t* count;
+    uint8_t* amb;
+    int n_tri;
+    int n_rays;
+    int ray_begin;   // first global segment index of this batch
+    float dmax0, dmax1, dmax2;
+};
+
+struct BatchArgs {
+    const BatchDesc* desc;
+    const int* begins;   // [n_batches + 1] prefix of the batch sizes
+    int n_batches;
+    int total;
+    long long timeout_ns;
+    int streamed;        // 1: segments become available as the host posts them
 };
 
 namespace {
@@ -294,6 +319,45 @@ __device__ int classify_fp64(D3 s, D3 e, D3 a, D3 b, D3 c, double& t_out, bool& 
 constexpr int kWarpChunk = 64;   // segments a warp takes per atomic
 constexpr int kRefillMin = 4;    // refill once this many lanes of a warp are idle
 
+// Batch holding global segment index gi: the last b with begins[b] <= gi.
+__device__ __forceinline__ int find_batch(const BatchArgs& B, int gi) {
+    int lo = 0, hi = B.n_batches - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(B.begins + mid) <= gi) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait (lane 0) until the host has posted segments up to `need`;
+// false when the budget ran out (RSI_ERR_TIMEOUT is raised) or another warp
+// already timed out.
+__device__ __noinline__ bool wait_ready(DevCounters* c, unsigned long long need, long long budget_ns) {
+    const unsigned long long t0 = global_ns();
+    while (ld_acquire_u64(&c->ready) < need) {
+        if (*(volatile int*)&c->error == RSI_ERR_TIMEOUT) return false;
+        if ((long long)(global_ns() - t0) > budget_ns) {
+            atomicCAS(&c->error, 0, RSI_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(1000);
+    }
+    return true;
+}
+
 constexpr int kLeafMin = 12;     // run the triangle tests once this many lanes hold one
 constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^30)
 
@@ -309,12 +373,16 @@ constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^
 // are refilled together from a per-warp chunk of segment indices (one atomic
 // per chunk).  A segment with a band pair and no certain answer is queued for
 // k_query_fp64 (count mode stops at the first band pair).
-template <int MODE, bool STATS, int STACK>
-__global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
+template <int MODE, bool STATS, int STACK, bool BATCHED>
+__global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A, BatchArgs B) {
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int n_rays = (int)A.n_rays;
+    const int n_rays = BATCHED ? B.total : (int)A.n_rays;
+    // BATCHED: the lane's batch and its hierarchy (uniform kernel arguments otherwise)
+    int l_batch = 0, l_ntri = 0;
+    const Node* l_nodes = nullptr;
+    const Tri* l_tris = nullptr;
     unsigned long long visits = 0, tests = 0;
     int wbase = 0, wend = 0;     // warp-uniform chunk [wbase, wend)
     bool exhausted = false;      // warp-uniform
@@ -338,29 +406,60 @@ __global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
                     }
                     wbase = (int)b;
                     wend = min(wbase + kWarpChunk, n_rays);
+                    if (BATCHED && B.streamed) {   // device work queue fed by the host
+                        bool ok = true;
+                        if (lane == 0) ok = wait_ready(A.ctr, (unsigned long long)wend, B.timeout_ns);
+                        if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) {
+                            exhausted = true;
+                            break;
+                        }
+                    }
                 }
                 const int take = min(__popc(idle), wend - wbase);
                 bool mine = false;
                 if ((idle >> lane) & 1u) {
                     const int rank = __popc(idle & lt);
                     if (rank < take) {
-                        ray = A.perm ? __ldg(A.perm + wbase + rank) : wbase + rank;
+                        if (BATCHED) {
+                            const int gi = wbase + rank;
+                            l_batch = find_batch(B, gi);
+                            ray = gi - __ldg(B.begins + l_batch);
+                        } else {
+                            ray = A.perm ? __ldg(A.perm + wbase + rank) : wbase + rank;
+                        }
                         mine = true;
                     }
                 }
                 wbase += take;
                 if (mine) {
                     const int64_t r = ray;
-                    float3 s = make_float3(__ldg(A.from + 3 * r), __ldg(A.from + 3 * r + 1), __ldg(A.from + 3 * r + 2));
-                    float3 e = make_float3(__ldg(A.to + 3 * r), __ldg(A.to + 3 * r + 1), __ldg(A.to + 3 * r + 2));
+                    const float* from = A.from;
+                    const float* to = A.to;
+                    float dm0 = A.dmax0, dm1 = A.dmax1, dm2 = A.dmax2;
+                    if (BATCHED) {
+                        const BatchDesc& bd = B.desc[l_batch];
+                        from = bd.from;
+                        to = bd.to;
+                        dm0 = bd.dmax0;
+                        dm1 = bd.dmax1;
+                        dm2 = bd.dmax2;
+                        l_nodes = bd.nodes;
+                        l_tris = bd.tris;
+                        l_ntri = bd.n_tri;
+                    }
+                    float3 s = make_float3(__ldg(from + 3 * r), __ldg(from + 3 * r + 1), __ldg(from + 3 * r + 2));
+                    float3 e = make_float3(__ldg(to + 3 * r), __ldg(to + 3 * r + 1), __ldg(to + 3 * r + 2));
                     if (bad3(s) || bad3(e)) {   // undefined answer: reported as ambiguous
-                        if (A.hit) A.hit[r] = 0;
-                        if (MODE == RSI_COUNT) A.count[r] = 0;
-                        if (A.amb) A.amb[r] = 1;
+                        uint8_t* hit = BATCHED ? B.desc[l_batch].hit : A.hit;
+                        int32_t* count = BATCHED ? B.desc[l_batch].count : A.count;
+                        uint8_t* amb = BATCHED ? B.desc[l_batch].amb : A.amb;
+                        if (hit) hit[r] = 0;
+                        if (MODE == RSI_COUNT) count[r] = 0;
+                        if (amb) amb[r] = 1;
                         ray = -1;
                     } else {
-                        g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
-                        next = A.n_tri == 1 ? ~0 : 0;
+                        g = make_seg(s, e, dm0, dm1, dm2);
+                        next = (BATCHED ? l_ntri : A.n_tri) == 1 ? ~0 : 0;
                         slot = -1;
                         sp = 0;
                         cnt = plain_cnt = 0;
@@ -379,7 +478,7 @@ __global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
         // node step
         if (active && next != kDone && next >= 0) {
             float4 lmin, lmax, rmin, rmax;
-            load_node(A.nodes, next, lmin, lmax, rmin, rmax);
+            load_node(BATCHED ? l_nodes : A.nodes, next, lmin, lmax, rmin, rmax);
             if (STATS) ++visits;
             const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
             const bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
@@ -411,7 +510,7 @@ __global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
         if (pend && (__popc(pend) >= kLeafMin || moving == 0)) {
             if (slot >= 0) {
                 if (STATS) ++tests;
-                const Tri tr = load_tri(A.tris, slot);
+                const Tri tr = load_tri(BATCHED ? l_tris : A.tris, slot);
                 bool plain;
                 int c = tri_fp32(g, tr, A.fp32_only != 0, plain);
                 plain_cnt += plain;
@@ -430,26 +529,29 @@ __global__ void __launch_bounds__(256, 4) k_query_fp32(QueryArgs A) {
         }
         if (active && (stop || (next == kDone && slot < 0))) {
             const int64_t r = ray;
+            uint8_t* hit = BATCHED ? B.desc[l_batch].hit : A.hit;
+            int32_t* count = BATCHED ? B.desc[l_batch].count : A.count;
+            uint8_t* amb = BATCHED ? B.desc[l_batch].amb : A.amb;
             if (A.fp32_only) {   // plain FP32 closed-interval decisions, no re-test
-                if (MODE == RSI_ANY_HIT) A.hit[r] = (uint8_t)(found || plain_cnt > 0);
+                if (MODE == RSI_ANY_HIT) hit[r] = (uint8_t)(found || plain_cnt > 0);
                 else {
-                    A.count[r] = plain_cnt;
-                    if (A.hit) A.hit[r] = (uint8_t)(plain_cnt > 0);
+                    count[r] = plain_cnt;
+                    if (hit) hit[r] = (uint8_t)(plain_cnt > 0);
                 }
-                if (A.amb) A.amb[r] = 0;
+                if (amb) amb[r] = 0;
             } else if (MODE == RSI_ANY_HIT && found) {
-                A.hit[r] = 1;
-                if (A.amb) A.amb[r] = 0;
+                hit[r] = 1;
+                if (amb) amb[r] = 0;
             } else if (band) {
                 int pos = atomicAdd(&A.ctr->band_count, 1);
-                A.band_ids[pos] = ray;
+                A.band_ids[pos] = BATCHED ? ray + __ldg(B.begins + l_batch) : ray;
             } else {
-                if (MODE == RSI_ANY_HIT) A.hit[r] = 0;
+                if (MODE == RSI_ANY_HIT) hit[r] = 0;
                 else {
-                    A.count[r] = cnt;
-                    if (A.hit) A.hit[r] = (uint8_t)(cnt > 0);
+                    count[r] = cnt;
+                    if (hit) hit[r] = (uint8_t)(cnt > 0);
                 }
-                if (A.amb) A.amb[r] = 0;
+                if (amb) amb[r] = 0;
             }
             ray = -1;
         }
@@ -529,8 +631,8 @@ __device__ __forceinline__ double t_of_definition(D3 s, D3 e, D3 a, D3 b, D3 c) 
 // otherwise -- and the warp combines the classes.  A decisive hit ends a
 // boolean query; otherwise the closed-interval answer of an ambiguous
 // segment counts distinct crossings (t merged within 1e-9).
-template <int MODE, int STACK>
-__global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
+template <int MODE, int STACK, bool BATCHED>
+__global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B) {
     constexpr int kWarps = 4;
     __shared__ double s_t[kWarps][kMaxInclusive];
     __shared__ int s_cand[kWarps][32];
@@ -539,10 +641,27 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
     const unsigned lt = (1u << lane) - 1u;
     const int nb = *(volatile int*)&A.ctr->band_count;
     for (int k = blockIdx.x * kWarps + w; k < nb; k += gridDim.x * kWarps) {
-        const int64_t r = A.band_ids[k];
-        const float3 s = make_float3(A.from[3 * r], A.from[3 * r + 1], A.from[3 * r + 2]);
-        const float3 e = make_float3(A.to[3 * r], A.to[3 * r + 1], A.to[3 * r + 2]);
-        const SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
+        QueryArgs Q = A;   // this segment's hierarchy and outputs
+        int64_t r = A.band_ids[k];
+        if (BATCHED) {
+            const int b = find_batch(B, (int)r);
+            const BatchDesc& bd = B.desc[b];
+            r -= __ldg(B.begins + b);
+            Q.nodes = bd.nodes;
+            Q.tris = bd.tris;
+            Q.n_tri = bd.n_tri;
+            Q.from = bd.from;
+            Q.to = bd.to;
+            Q.hit = bd.hit;
+            Q.count = bd.count;
+            Q.amb = bd.amb;
+            Q.dmax0 = bd.dmax0;
+            Q.dmax1 = bd.dmax1;
+            Q.dmax2 = bd.dmax2;
+        }
+        const float3 s = make_float3(Q.from[3 * r], Q.from[3 * r + 1], Q.from[3 * r + 2]);
+        const float3 e = make_float3(Q.to[3 * r], Q.to[3 * r + 1], Q.to[3 * r + 2]);
+        const SegF g = make_seg(s, e, Q.dmax0, Q.dmax1, Q.dmax2);
         const D3 sd = {(double)s.x, (double)s.y, (double)s.z}, ed = {(double)e.x, (double)e.y, (double)e.z};
         int n_hit = 0, n_amb = 0, n_incl = 0;
         bool overflow = false;
@@ -552,23 +671,23 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
         while (true) {
             int nc = 0;
             if (lane == 0) {
-                if (A.n_tri == 1) {
+                if (Q.n_tri == 1) {
                     s_cand[w][nc++] = 0;
                     trav_done = true;
                 }
                 while (!trav_done && nc <= 30) {
                     float4 lmin, lmax, rmin, rmax;
-                    load_node(A.nodes, node, lmin, lmax, rmin, rmax);
+                    load_node(Q.nodes, node, lmin, lmax, rmin, rmax);
                     const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
                     bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
                     bool plain;
                     if (hl && lref < 0) {
                         hl = false;
-                        if (tri_fp32(g, load_tri(A.tris, ~lref), false, plain) != kMiss) s_cand[w][nc++] = ~lref;
+                        if (tri_fp32(g, load_tri(Q.tris, ~lref), false, plain) != kMiss) s_cand[w][nc++] = ~lref;
                     }
                     if (hr && rref < 0) {
                         hr = false;
-                        if (tri_fp32(g, load_tri(A.tris, ~rref), false, plain) != kMiss) s_cand[w][nc++] = ~rref;
+                        if (tri_fp32(g, load_tri(Q.tris, ~rref), false, plain) != kMiss) s_cand[w][nc++] = ~rref;
                     }
                     if (hl && hr) {
                         if (sp < STACK) {
@@ -596,7 +715,7 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
             bool incl = false;
             double t = 0.0;
             if (lane < nc) {
-                const Tri tr = load_tri(A.tris, s_cand[w][lane]);
+                const Tri tr = load_tri(Q.tris, s_cand[w][lane]);
                 const D3 a = d3of(tr.v0), b = d3of(tr.v1), c = d3of(tr.v2);
                 cls = tri_certain64(sd, ed, a, b, c);
                 if (cls == kHit) {
@@ -626,8 +745,8 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
             const int m = min(n_incl, kMaxInclusive);
             if (MODE == RSI_ANY_HIT) {
                 const bool amb = n_hit == 0 && n_amb > 0;
-                A.hit[r] = (uint8_t)(n_hit > 0 || (amb && n_incl > 0));
-                if (A.amb) A.amb[r] = (uint8_t)amb;
+                Q.hit[r] = (uint8_t)(n_hit > 0 || (amb && n_incl > 0));
+                if (Q.amb) Q.amb[r] = (uint8_t)amb;
                 if (amb) atomicAdd(&A.ctr->ambiguous, 1ull);
             } else {
                 const bool amb = n_amb > 0;
@@ -648,9 +767,9 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A) {
                         if (i == 0 || __dsub_rn(ts[i], ts[i - 1]) > kTMerge) ++count;
                     atomicAdd(&A.ctr->ambiguous, 1ull);
                 }
-                A.count[r] = count;
-                if (A.hit) A.hit[r] = (uint8_t)(count > 0);
-                if (A.amb) A.amb[r] = (uint8_t)amb;
+                Q.count[r] = count;
+                if (Q.hit) Q.hit[r] = (uint8_t)(count > 0);
+                if (Q.amb) Q.amb[r] = (uint8_t)amb;
             }
         }
         __syncwarp();
@@ -722,30 +841,32 @@ __global__ void __launch_bounds__(256) k_ray_tile_sort(const float* __restrict__
     }
 }
 
-__global__ void k_reset_query(DevCounters* c) {
+__global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->band_count = 0;
     c->next_ray = 0;
+    if (ready != ~0ull) c->ready = ready;   // ~0: a streaming plan, fed by posts
     c->error = 0;
     c->node_visits = c->tri_tests = c->ambiguous = 0;
 }
 
-template <int MODE, bool STATS, int STACK>
-void launch_fp32(const QueryArgs& A, int grid, int block, cudaStream_t s) {
-    k_query_fp32<MODE, STATS, STACK><<<grid, block, 0, s>>>(A);
+template <int MODE, bool STATS, int STACK, bool BATCHED>
+void launch_fp32(const QueryArgs& A, const BatchArgs& B, int grid, int block, cudaStream_t s) {
+    k_query_fp32<MODE, STATS, STACK, BATCHED><<<grid, block, 0, s>>>(A, B);
 }
 
-template <int MODE, bool STATS>
-void launch_fp32_stack(const QueryArgs& A, int height, int grid, int block, cudaStream_t s) {
-    if (height < 32) launch_fp32<MODE, STATS, 32>(A, grid, block, s);
-    else if (height < 64) launch_fp32<MODE, STATS, 64>(A, grid, block, s);
-    else launch_fp32<MODE, STATS, 128>(A, grid, block, s);
+template <int MODE, bool STATS, bool BATCHED = false>
+void launch_fp32_stack(const QueryArgs& A, int height, int grid, int block, cudaStream_t s,
+                       const BatchArgs& B = BatchArgs{}) {
+    if (height < 32) launch_fp32<MODE, STATS, 32, BATCHED>(A, B, grid, block, s);
+    else if (height < 64) launch_fp32<MODE, STATS, 64, BATCHED>(A, B, grid, block, s);
+    else launch_fp32<MODE, STATS, 128, BATCHED>(A, B, grid, block, s);
 }
 
-template <int MODE>
-void launch_fp64(const QueryArgs& A, int height, int grid, cudaStream_t s) {
-    if (height < 32) k_query_fp64<MODE, 32><<<grid, 128, 0, s>>>(A);
-    else if (height < 64) k_query_fp64<MODE, 64><<<grid, 128, 0, s>>>(A);
-    else k_query_fp64<MODE, 128><<<grid, 128, 0, s>>>(A);
+template <int MODE, bool BATCHED = false>
+void launch_fp64(const QueryArgs& A, int height, int grid, cudaStream_t s, const BatchArgs& B = BatchArgs{}) {
+    if (height < 32) k_query_fp64<MODE, 32, BATCHED><<<grid, 128, 0, s>>>(A, B);
+    else if (height < 64) k_query_fp64<MODE, 64, BATCHED><<<grid, 128, 0, s>>>(A, B);
+    else k_query_fp64<MODE, 128, BATCHED><<<grid, 128, 0, s>>>(A, B);
 }
 
 }  // namespace
@@ -798,7 +919,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
         note_launches(1);
         A.perm = perm_scratch;
     }
-    k_reset_query<<<1, 1, 0, s>>>(ctr);
+    k_reset_query<<<1, 1, 0, s>>>(ctr, (unsigned long long)n);
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[0], s));
     if (mode == RSI_ANY_HIT) {
         if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, grid, block, s);
@@ -941,6 +1062,219 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
     if (rc) return rc;
     rsi_stats tmp;
     return rsi::read_stats(h, h->ctr, n_rays, stats ? stats : &tmp, s);
+}
+
+// ---------------------------------------------------------------- batched
+using namespace rsi;   // the kernels and launchers above
+
+// Many independent (hierarchy, segment batch) pairs answered by one
+// persistent traversal launch over the concatenated segment index space,
+// followed by one FP64 pass; the three kernels are captured once into a CUDA
+// graph and replayed by rsi_query_batched.
+struct rsi_batch_s {
+    int mode = 0;
+    rsi_options opt{};
+    int n_batches = 0;
+    int total = 0;
+    int height = 0;
+    char* dev = nullptr;
+    rsi::DevCounters* ctr = nullptr;
+    int* begins = nullptr;
+    rsi::BatchDesc* desc = nullptr;
+    int32_t* band = nullptr;
+    rsi::DevCounters* h_ctr = nullptr;
+    unsigned long long* h_post = nullptr;   // pinned ring of posted counts
+    cudaEvent_t post_ev[256] = {};
+    cudaEvent_t reset_ev = nullptr;   // streaming: the queue was emptied on the launch stream
+    bool streamed = false;
+    int post_idx = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void batch_destroy(rsi_batch_s* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaEvent_t e : b->post_ev)
+        if (e) cudaEventDestroy(e);
+    if (b->reset_ev) cudaEventDestroy(b->reset_ev);
+    if (b->dev) cudaFree(b->dev);
+    if (b->h_ctr) cudaFreeHost(b->h_ctr);
+    if (b->h_post) cudaFreeHost(b->h_post);
+    delete b;
+}
+
+template <int MODE>
+void launch_batched(rsi_batch_s* b, const QueryArgs& A, const BatchArgs& B, cudaStream_t s) {
+    const int block = b->opt.block > 0 ? b->opt.block : 256;
+    const int bps = b->opt.blocks_per_sm > 0 ? b->opt.blocks_per_sm : 3;
+    int64_t want = ((int64_t)b->total + block - 1) / block;
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)rsi::device_sm_count() * bps));
+    if (b->opt.collect_stats) launch_fp32_stack<MODE, true, true>(A, b->height, grid, block, s, B);
+    else launch_fp32_stack<MODE, false, true>(A, b->height, grid, block, s, B);
+    if (!b->opt.fp32_only) launch_fp64<MODE, true>(A, b->height, rsi::device_sm_count() * 4, s, B);
+}
+
+}  // namespace
+
+extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int mode, const rsi_options* opt,
+                                void* stream, rsi_batch_t* out) {
+    if (!out) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: out is NULL");
+    *out = nullptr;
+    if (!batches || n_batches < 1) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: need >= 1 batch");
+    if (mode != RSI_ANY_HIT && mode != RSI_COUNT) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: bad mode");
+    rsi_options o = {};
+    if (opt) o = *opt;
+    if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: block must be a multiple of 32 in [32, 256]");
+    if (o.blocks_per_sm < 0) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: blocks_per_sm < 0");
+    std::vector<int> begins(n_batches + 1, 0);
+    std::vector<rsi::BatchDesc> desc(n_batches);
+    int height = 0;
+    int64_t total = 0;
+    for (int i = 0; i < n_batches; ++i) {
+        const rsi_ray_batch& rb = batches[i];
+        if (!rb.bvh) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: batch " + std::to_string(i) + " has no hierarchy");
+        if (rb.n_rays < 0) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: negative n_rays");
+        if (rb.n_rays > 0 && (!rb.d_from || !rb.d_to || (mode == RSI_ANY_HIT && !rb.d_hit) ||
+                              (mode == RSI_COUNT && !rb.d_count)))
+            return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: batch " + std::to_string(i) + " lacks a buffer");
+        if (rb.bvh->height >= 127) return rsi::fail(RSI_ERR_STACK, "rsi_batch_create: tree too deep");
+        begins[i] = (int)total;
+        total += rb.n_rays;
+        if (total > 0x7FFFFFFFll) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: more than 2^31 segments");
+        height = std::max(height, rb.bvh->height);
+        rsi::BatchDesc& d = desc[i];
+        d.nodes = rb.bvh->nodes;
+        d.tris = rb.bvh->tris;
+        d.from = rb.d_from;
+        d.to = rb.d_to;
+        d.hit = rb.d_hit;
+        d.count = rb.d_count;
+        d.amb = rb.d_ambiguous;
+        d.n_tri = (int)rb.bvh->n_tri;
+        d.n_rays = (int)rb.n_rays;
+        d.ray_begin = begins[i];
+        d.dmax0 = rb.bvh->dmax[0];
+        d.dmax1 = rb.bvh->dmax[1];
+        d.dmax2 = rb.bvh->dmax[2];
+    }
+    begins[n_batches] = (int)total;
+    auto* b = new rsi_batch_s();
+    b->mode = mode;
+    b->opt = o;
+    b->n_batches = n_batches;
+    b->total = (int)total;
+    b->height = height;
+    const size_t off_begins = 256, off_desc = off_begins + ((4 * (size_t)(n_batches + 1) + 255) & ~(size_t)255);
+    const size_t off_band = off_desc + ((sizeof(rsi::BatchDesc) * (size_t)n_batches + 255) & ~(size_t)255);
+    const size_t bytes = off_band + 4 * (size_t)std::max<int64_t>(total, 1);
+    if (cudaMalloc(&b->dev, bytes) != cudaSuccess || cudaMallocHost(&b->h_ctr, sizeof(rsi::DevCounters)) != cudaSuccess ||
+        cudaMallocHost(&b->h_post, 256 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        batch_destroy(b);
+        return rsi::fail(RSI_ERR_OOM, "rsi_batch_create: allocation failed");
+    }
+    b->ctr = reinterpret_cast<rsi::DevCounters*>(b->dev);
+    b->begins = reinterpret_cast<int*>(b->dev + off_begins);
+    b->desc = reinterpret_cast<rsi::BatchDesc*>(b->dev + off_desc);
+    b->band = reinterpret_cast<int32_t*>(b->dev + off_band);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(b->begins, begins.data(), 4 * begins.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->desc, desc.data(), sizeof(rsi::BatchDesc) * desc.size(),
+                                              cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ctr, 0, sizeof(rsi::DevCounters), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int i = 0; e == cudaSuccess && i < 256; ++i) e = cudaEventCreateWithFlags(&b->post_ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->reset_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        int rc = rsi::cuda_fail(e, "rsi_batch_create");
+        batch_destroy(b);
+        return rc;
+    }
+    // capture reset -> traversal -> FP64 pass into a graph
+    QueryArgs A{};
+    A.band_ids = b->band;
+    A.ctr = b->ctr;
+    A.fp32_only = o.fp32_only;
+    BatchArgs B{b->desc, b->begins, n_batches, (int)total, o.timeout_ns > 0 ? (long long)o.timeout_ns : 2000000000ll,
+                0};
+    const bool streamed = o.timeout_ns < 0;
+    if (streamed) B.timeout_ns = -(long long)o.timeout_ns;
+    B.streamed = streamed ? 1 : 0;
+    b->streamed = streamed;
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        k_reset_query<<<1, 1, 0, b->cap>>>(b->ctr, streamed ? ~0ull : (unsigned long long)total);
+        if (mode == RSI_ANY_HIT) launch_batched<RSI_ANY_HIT>(b, A, B, b->cap);
+        else launch_batched<RSI_COUNT>(b, A, B, b->cap);
+        cudaError_t le = cudaGetLastError();
+        e = cudaStreamEndCapture(b->cap, &b->graph);
+        if (e == cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        int rc = rsi::cuda_fail(e, "rsi_batch_create: graph capture");
+        batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return RSI_OK;
+}
+
+extern "C" int rsi_query_batched(rsi_batch_t b, void* stream) {
+    if (!b) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_batched: NULL plan");
+    if (b->streamed) {   // empty the queue before any post of this run can land
+        RSI_CUDA_TRY(cudaMemsetAsync(&b->ctr->ready, 0, sizeof(unsigned long long), (cudaStream_t)stream));
+        RSI_CUDA_TRY(cudaEventRecord(b->reset_ev, (cudaStream_t)stream));
+    }
+    RSI_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    rsi::note_launches(b->opt.fp32_only ? 2 : 3);
+    return RSI_OK;
+}
+
+extern "C" int rsi_batch_post(rsi_batch_t b, int64_t n_ready, void* stream) {
+    if (!b) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_post: NULL plan");
+    if (!b->streamed) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_post: the plan is not streaming");
+    if (n_ready < 0 || n_ready > b->total) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_post: n_ready out of range");
+    const int k = b->post_idx++ & 255;
+    RSI_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, b->reset_ev, 0));
+    RSI_CUDA_TRY(cudaEventSynchronize(b->post_ev[k]));   // the slot's previous copy has run
+    b->h_post[k] = (unsigned long long)n_ready;
+    RSI_CUDA_TRY(cudaMemcpyAsync(&b->ctr->ready, &b->h_post[k], sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                                 (cudaStream_t)stream));
+    RSI_CUDA_TRY(cudaEventRecord(b->post_ev[k], (cudaStream_t)stream));
+    return RSI_OK;
+}
+
+extern "C" int rsi_batch_stats(rsi_batch_t b, rsi_stats* st, void* stream) {
+    if (!b || !st) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_stats: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    RSI_CUDA_TRY(cudaMemcpyAsync(b->h_ctr, b->ctr, sizeof(rsi::DevCounters), cudaMemcpyDeviceToHost, s));
+    RSI_CUDA_TRY(cudaStreamSynchronize(s));
+    const rsi::DevCounters& c = *b->h_ctr;
+    st->n_rays = b->total;
+    st->node_visits = (int64_t)c.node_visits;
+    st->tri_tests = (int64_t)c.tri_tests;
+    st->band_rays = c.band_count;
+    st->ambiguous = (int64_t)c.ambiguous;
+    st->tree_height = b->height;
+    st->device_error = c.error;
+    if (c.error) return rsi::fail(c.error, "rsi_query_batched: device error " + std::to_string(c.error));
+    return RSI_OK;
+}
+
+extern "C" int rsi_batch_free(rsi_batch_t b) {
+    if (!b) return RSI_OK;
+    cudaDeviceSynchronize();
+    batch_destroy(b);
+    return RSI_OK;
 }
 
 // ---------------------------------------------------------------- no-alloc

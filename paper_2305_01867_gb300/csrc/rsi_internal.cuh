@@ -41,6 +41,7 @@ struct DevCounters {
     int pad0;
     unsigned long long node_visits, tri_tests, ambiguous;
     unsigned long long next_ray;   // work counter of the persistent traversal
+    unsigned long long ready;      // segments available to the work queue
     unsigned int ext_bits[6];   // extent as order-preserving uint (min xyz, max xyz)
     unsigned int dmax_bits[3];  // largest triangle box side per axis (float bits)
     unsigned int pad1;

@@ -228,6 +228,34 @@ def rays(spec: RaySpec, mesh: Mesh, start: int = 0, count: int | None = None, ou
     return F, E
 
 
+def _chunk_task(args):
+    spec, mesh, c = args
+    return ray_chunk(spec, mesh, c)
+
+
+def rays_many(jobs, workers: int | None = None):
+    """Several whole batches [(mesh, spec), ...] generated chunk by chunk in
+    a pool of spawned processes (start it before the process touches a GPU).
+    Returns [(from, to), ...] in job order, identical to rays()."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    tasks = [(spec, mesh, c) for mesh, spec in jobs for c in range((spec.n + CHUNK - 1) // CHUNK)]
+    workers = workers or min(32, os.cpu_count() or 1)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_chunk_task, tasks, chunksize=1))
+    out, k = [], 0
+    for mesh, spec in jobs:
+        nc = (spec.n + CHUNK - 1) // CHUNK
+        fs = [parts[k + i][0] for i in range(nc)]
+        ts = [parts[k + i][1] for i in range(nc)]
+        k += nc
+        F = np.concatenate(fs) if fs else np.zeros((0, 3), np.float32)
+        E = np.concatenate(ts) if ts else np.zeros((0, 3), np.float32)
+        out.append((F, E))
+    return out
+
+
 def rays_at(spec: RaySpec, mesh: Mesh, idx: np.ndarray):
     """Rows idx (any order) of the batch, regenerating only their chunks."""
     idx = np.asarray(idx, np.int64)
