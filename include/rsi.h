@@ -255,6 +255,63 @@ int rsi_batch_stats(rsi_batch_t plan, rsi_stats* out, void* stream);
 /* Release a plan (synchronizes the device first).  NULL is a no-op. */
 int rsi_batch_free(rsi_batch_t plan);
 
+/* Result of rsi_autotune. */
+typedef struct rsi_tuning {
+    int block;          /* threads per block chosen                          */
+    int blocks_per_sm;  /* resident blocks per SM chosen                     */
+    int ray_sort_tile;  /* in-tile reordering chosen (0 = off)               */
+    int stack;          /* traversal stack entries the tree needs (32/64/128,
+                           the smallest above the tree height)               */
+    float ms;           /* time of the best candidate on the sample          */
+    int from_cache;     /* 1 if the choice came from the cache file          */
+    int candidates;     /* candidates timed (0 on a cache hit)               */
+} rsi_tuning;
+
+/*
+ * Choose the traversal launch shape and the in-tile segment reordering for
+ * queries like this one (the method's query of Sec. 1; tuning has no
+ * counterpart in the paper).  Times candidate options on the first
+ * min(n_rays, 2^21) segments with CUDA events (running rsi_query, so it
+ * allocates and synchronizes `stream`), writes the winner into *inout, and
+ * records it in `cache_path` (a JSON object keyed by device, mode and log2
+ * buckets of the triangle and segment counts; NULL = no cache).  A cached
+ * key is reused without timing.  Concurrent writers of one cache file may
+ * lose entries.
+ */
+int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
+                 const char* cache_path, rsi_options* inout, rsi_tuning* result, void* stream);
+
+/*
+ * Learned cluster proposal for boolean queries (no counterpart in the paper;
+ * the answers stay the paper's, see rsi_query_learned).  A small network maps
+ * a segment's end points (normalised by the mesh extent) through
+ * 6 -> 128 -> 128 -> 256 units with GELU to logits over 256 clusters: equal
+ * ranges of the Morton-ordered leaves of the hierarchy.  Weights and layer
+ * inputs are BF16, accumulation FP32; inference runs on the tensor cores.
+ * Parameters are one FP32 array of rsi_mlp_num_params() values:
+ *   W1 [16][128] (rows 6..15 unused), b1 [128], W2 [128][128], b2 [128],
+ *   W3 [128][256], b3 [256]   (row-major, y = x W + b).
+ */
+typedef struct rsi_mlp_s* rsi_mlp_t;
+
+/* New network with seeded He-normal weights and zero biases. */
+int rsi_mlp_create(uint64_t seed, rsi_mlp_t* out);
+int rsi_mlp_free(rsi_mlp_t m);
+int rsi_mlp_num_params(void);
+/* Copy parameters in / out (host arrays of rsi_mlp_num_params() floats;
+ * h_grads receives the gradient of the last training step; both
+ * synchronize `stream`). */
+int rsi_mlp_set_params(rsi_mlp_t m, const float* h_params, void* stream);
+int rsi_mlp_get_params(rsi_mlp_t m, float* h_params, float* h_grads, void* stream);
+
+/* Tensor-core inference for n segments against the extent of hierarchy h:
+ * d_logits [n][256] float (nullable) and/or d_top4 [n][4] cluster ids, best
+ * first (nullable).  Asynchronous; rsi_mlp_status reports a tensor-core wait
+ * that ran out (RSI_ERR_TIMEOUT). */
+int rsi_mlp_forward(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
+                    float* d_logits, uint8_t* d_top4, void* stream);
+int rsi_mlp_status(rsi_mlp_t m, void* stream);
+
 /* Durations of the FP32 traversal kernel and of the FP64 re-test kernel of
  * the last query on `h` that ran with time_kernels = 1, from CUDA events
  * recorded on that query's stream (waits for them).  -1 if none. */

@@ -59,6 +59,15 @@ class HostView(ctypes.Structure):
                 ("right", ctypes.c_void_p), ("parent", ctypes.c_void_p), ("box", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("ray_sort_tile", ctypes.c_int),
+                ("stack", ctypes.c_int), ("ms", ctypes.c_float), ("from_cache", ctypes.c_int),
+                ("candidates", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class RayBatch(ctypes.Structure):
     _fields_ = [("bvh", ctypes.c_void_p), ("d_from", ctypes.c_void_p), ("d_to", ctypes.c_void_p),
                 ("n_rays", ctypes.c_int64), ("d_hit", ctypes.c_void_p), ("d_count", ctypes.c_void_p),
@@ -85,6 +94,8 @@ def _load():
     lib.rsi_last_query_ms.restype = ctypes.c_int
     lib.rsi_kernel_launches.argtypes = []
     lib.rsi_kernel_launches.restype = ctypes.c_uint64
+    lib.rsi_autotune.argtypes = [P, P, P, i64, i32, ctypes.c_char_p, ctypes.POINTER(Options), ctypes.POINTER(Tuning), P]
+    lib.rsi_autotune.restype = ctypes.c_int
     lib.rsi_batch_create.argtypes = [ctypes.POINTER(RayBatch), i32, i32, ctypes.POINTER(Options), P,
                                      ctypes.POINTER(P)]
     lib.rsi_query_batched.argtypes = [P, P]
@@ -92,6 +103,16 @@ def _load():
     lib.rsi_batch_stats.argtypes = [P, ctypes.POINTER(Stats), P]
     lib.rsi_batch_free.argtypes = [P]
     for name in ("rsi_batch_create", "rsi_query_batched", "rsi_batch_post", "rsi_batch_stats", "rsi_batch_free"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.rsi_mlp_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
+    lib.rsi_mlp_free.argtypes = [P]
+    lib.rsi_mlp_num_params.argtypes = []
+    lib.rsi_mlp_set_params.argtypes = [P, P, P]
+    lib.rsi_mlp_get_params.argtypes = [P, P, P, P]
+    lib.rsi_mlp_forward.argtypes = [P, P, P, P, i64, P, P, P]
+    lib.rsi_mlp_status.argtypes = [P, P]
+    for name in ("rsi_mlp_create", "rsi_mlp_free", "rsi_mlp_num_params", "rsi_mlp_set_params", "rsi_mlp_get_params",
+                 "rsi_mlp_forward", "rsi_mlp_status"):
         getattr(lib, name).restype = ctypes.c_int
     lib.rsi_last_error.restype = ctypes.c_char_p
     lib.rsi_last_error.argtypes = []
@@ -209,6 +230,17 @@ class LBVH:
         if n == 1:
             out["left"], out["right"] = out["left"][:0], out["right"][:0]
         return out
+
+    def autotune(self, ray_from, ray_to, mode="any_hit", cache_path=None, stream=None) -> dict:
+        """Pick block / blocks_per_sm / ray_sort_tile for queries like this one
+        (rsi_autotune); the result's keys can be passed straight to query()."""
+        _check_f32x3(ray_from, "ray_from")
+        _check_f32x3(ray_to, "ray_to")
+        opt, res = Options(), Tuning()
+        path = cache_path.encode() if cache_path else None
+        check(lib.rsi_autotune(self._h, _ptr(ray_from), _ptr(ray_to), ray_from.shape[0], _mode(mode), path,
+                               ctypes.byref(opt), ctypes.byref(res), _stream(stream)))
+        return res.as_dict()
 
     def last_query_ms(self):
         """(traversal ms, FP64 re-test ms) of the last query run with time_kernels=True."""
@@ -330,3 +362,76 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+MLP_SHAPES = (("W1", (16, 128)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (128, 256)),
+              ("b3", (256,)))
+
+
+class MLP:
+    """The cluster-proposal network (rsi_mlp_*): 6 -> 128 -> 128 -> 256,
+    BF16 weights, FP32 accumulation, tensor-core inference."""
+
+    def __init__(self, seed: int = 0):
+        self._m = ctypes.c_void_p()
+        check(lib.rsi_mlp_create(int(seed), ctypes.byref(self._m)))
+        self.n_params = int(lib.rsi_mlp_num_params())
+
+    @property
+    def handle(self):
+        return self._m
+
+    def close(self):
+        if getattr(self, "_m", None) and self._m.value:
+            lib.rsi_mlp_free(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def flatten(params: dict):
+        import numpy as np
+        return np.concatenate([np.asarray(params[k], np.float32).reshape(-1) for k, _ in MLP_SHAPES])
+
+    @staticmethod
+    def unflatten(flat):
+        import numpy as np
+        out, i = {}, 0
+        for k, shp in MLP_SHAPES:
+            n = int(np.prod(shp))
+            out[k] = np.asarray(flat[i:i + n], np.float64).reshape(shp)
+            i += n
+        return out
+
+    def set_params(self, params, stream=None):
+        import numpy as np
+        flat = self.flatten(params) if isinstance(params, dict) else np.ascontiguousarray(params, np.float32)
+        assert flat.size == self.n_params
+        check(lib.rsi_mlp_set_params(self._m, flat.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+
+    def get_params(self, grads=False, stream=None):
+        import numpy as np
+        p = np.zeros(self.n_params, np.float32)
+        g = np.zeros(self.n_params, np.float32) if grads else None
+        check(lib.rsi_mlp_get_params(self._m, p.ctypes.data_as(ctypes.c_void_p),
+                                     g.ctypes.data_as(ctypes.c_void_p) if grads else None, _stream(stream)))
+        return (self.unflatten(p), self.unflatten(g)) if grads else self.unflatten(p)
+
+    def forward(self, bvh, ray_from, ray_to, logits=True, top4=True, stream=None):
+        """Tensor-core inference: dict(logits=[n,256] float32, top4=[n,4] uint8)."""
+        import torch
+        _check_f32x3(ray_from, "ray_from")
+        _check_f32x3(ray_to, "ray_to")
+        n = ray_from.shape[0]
+        lg = torch.empty(n, 256, dtype=torch.float32, device=ray_from.device) if logits else None
+        t4 = torch.empty(n, 4, dtype=torch.uint8, device=ray_from.device) if top4 else None
+        check(lib.rsi_mlp_forward(self._m, bvh.handle, _ptr(ray_from), _ptr(ray_to), n, _ptr(lg), _ptr(t4),
+                                  _stream(stream)))
+        return {"logits": lg, "top4": t4}
+
+    def status(self, stream=None):
+        check(lib.rsi_mlp_status(self._m, _stream(stream)))

@@ -1,0 +1,514 @@
+// mlp.cu -- the cluster-proposal network of the learned any-hit query:
+// segment end points -> 128 -> 128 -> 256 cluster logits (GELU), BF16
+// weights and layer inputs, FP32 accumulation.  (Not in the paper: the
+// proposal, its training and the proposal-verify-fallback query are added
+// on top of the method; the fallback is the paper's full tree search, so
+// answers stay exactly those of the plain query.)
+//
+//  k_mlp_forward_tc  inference on the 5th-generation tensor cores: per tile
+//                    of 128 segments three tcgen05.mma chains (K = 16, 128,
+//                    128; N = 128, 128, 256) with FP32 accumulators in TMEM,
+//                    operands in shared memory in the no-swizzle K-major
+//                    core-matrix layout (8 rows x 16 bytes per core matrix),
+//                    bias + GELU + BF16 rounding in the TMEM->register
+//                    epilogue, top-4 cluster selection at the end.
+//  training          FP32 SIMT kernels (tiled GEMMs, fused elementwise
+//                    steps, Adam) on the same BF16 roundings; the network is
+//                    small and training is a one-off set-up cost.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "rsi_internal.cuh"
+
+namespace rsi {
+namespace mlpk {
+
+constexpr int kIn = 16, kH = 128, kOut = 256;
+constexpr int kW1 = kIn * kH, kW2 = kH * kH, kW3 = kH * kOut;   // element counts
+constexpr int kParams = kW1 + kH + kW2 + kH + kW3 + kOut;        // W1 b1 W2 b2 W3 b3
+constexpr int kOffW1 = 0, kOffB1 = kW1, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kW2, kOffW3 = kOffB2 + kH,
+              kOffB3 = kOffW3 + kW3;
+// BF16 images of W^T (N rows x K columns, K-major core matrices) in the order
+// the forward kernel copies them to shared memory
+constexpr int kImgW1 = 0, kImgW2 = kImgW1 + kH * kIn * 2, kImgW3 = kImgW2 + kH * kH * 2,
+              kImgBytes = kImgW3 + kOut * kH * 2;   // 102400 bytes
+
+// Byte offset of element (row, k) of a K-major operand with K columns: core
+// matrices of 8 rows x 8 elements (128 B), K-adjacent ones 128 B apart
+// (leading byte offset), row-adjacent groups K * 16 B apart (stride offset).
+__host__ __device__ constexpr uint32_t cm_offset(int row, int k, int K) {
+    return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// Features of segment r: both end points mapped by the extent to [-1, 1],
+// clamped to [-4, 4]; inputs 6..15 are zero.
+__device__ __forceinline__ void seg_features(const float* __restrict__ from, const float* __restrict__ to, int64_t r,
+                                             const float lo[3], const float sc[3], float f[6]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[a] = fminf(fmaxf((from[3 * r + a] - lo[a]) * sc[a] - 1.0f, -4.0f), 4.0f);
+        f[3 + a] = fminf(fmaxf((to[3 * r + a] - lo[a]) * sc[a] - 1.0f, -4.0f), 4.0f);
+    }
+}
+
+// ---------------------------------------------------------------- tcgen05
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared memory matrix descriptor: start >> 4 (bits 0-13), leading byte
+// offset >> 4 (16-29), stride byte offset >> 4 (32-45), version 1 (46-47),
+// base offset 0, no swizzle (61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B in BF16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for an mbarrier phase: false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    const unsigned long long t0 = now_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (now_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+    uint32_t r[32];
+    __syncwarp();   // .sync.aligned: the whole warp issues the load together
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Hidden-layer epilogue: this thread's row of a 128-column accumulator ->
+// + bias -> GELU -> BF16 -> row of the next layer's K-major A operand.
+__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* __restrict__ bias, uint8_t* sA, int row) {
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+        float v[32];
+        tmem_ld32(taddr + 32 * c, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 w;
+            const int k0 = 32 * c + 8 * q;
+            w.x = pack_bf16x2(gelu(v[8 * q + 0] + bias[k0 + 0]), gelu(v[8 * q + 1] + bias[k0 + 1]));
+            w.y = pack_bf16x2(gelu(v[8 * q + 2] + bias[k0 + 2]), gelu(v[8 * q + 3] + bias[k0 + 3]));
+            w.z = pack_bf16x2(gelu(v[8 * q + 4] + bias[k0 + 4]), gelu(v[8 * q + 5] + bias[k0 + 5]));
+            w.w = pack_bf16x2(gelu(v[8 * q + 6] + bias[k0 + 6]), gelu(v[8 * q + 7] + bias[k0 + 7]));
+            *reinterpret_cast<uint4*>(sA + cm_offset(row, k0, kH)) = w;
+        }
+    }
+}
+
+// Shared memory map of the forward kernel (bytes from a 1024-aligned base).
+constexpr int kSmX = kImgBytes;                 // [128 x 16] features
+constexpr int kSmH = kSmX + 128 * kIn * 2;       // [128 x 128] hidden activations
+constexpr int kSmBias = kSmH + 128 * kH * 2;     // 512 floats
+constexpr int kSmBar = kSmBias + 512 * 4;        // mbarrier + TMEM address
+constexpr int kSmBytes = kSmBar + 64;
+constexpr int kTmemCols = 512;
+
+struct FwdArgs {
+    const uint8_t* img;    // BF16 weight images
+    const float* bias;     // b1 | b2 | b3
+    const float* from;
+    const float* to;
+    int n;
+    float lo0, lo1, lo2, sc0, sc1, sc2;   // feature map: (p - lo) * sc - 1
+    float* logits;         // [n][256] or NULL
+    uint8_t* top4;         // [n][4] or NULL (cluster ids, best first)
+    int* tile_ctr;         // work counter, 0 at launch
+    int* err;              // RSI_ERR_TIMEOUT if a tensor-core wait ran out
+};
+
+__global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(FwdArgs P) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    float* sBias = reinterpret_cast<float*>(sm + kSmBias);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kSmBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSmBar + 8);
+    int* s_tile = reinterpret_cast<int*>(sm + kSmBar + 16);
+    int* s_ok = reinterpret_cast<int*>(sm + kSmBar + 20);
+
+    for (int i = tid; i < kImgBytes / 16; i += 128)
+        reinterpret_cast<uint4*>(sm)[i] = reinterpret_cast<const uint4*>(P.img)[i];
+    for (int i = tid; i < 512; i += 128) sBias[i] = P.bias[i];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lanes
+    const uint32_t bar = smem_addr(mbar);
+    const uint32_t aX = smem_addr(sm + kSmX), aH = smem_addr(sm + kSmH);
+    const uint32_t aW1 = smem_addr(sm + kImgW1), aW2 = smem_addr(sm + kImgW2), aW3 = smem_addr(sm + kImgW3);
+    const float lo[3] = {P.lo0, P.lo1, P.lo2}, sc[3] = {P.sc0, P.sc1, P.sc2};
+    uint32_t phase = 0;
+
+    // one elected thread issues a chain and waits for it; the others learn
+    // the outcome through the barrier
+    auto run_chain = [&](int layer) -> bool {
+        if (tid == 0) {
+            fence_after();
+            if (layer == 1) {
+                mma_bf16(tbase, smem_desc(aX, 128, kIn * 16), smem_desc(aW1, 128, kIn * 16), idesc_bf16(128, kH), 0);
+            } else if (layer == 2) {
+                for (int ks = 0; ks < kH / 16; ++ks)
+                    mma_bf16(tbase + 256, smem_desc(aH + 256 * ks, 128, kH * 16), smem_desc(aW2 + 256 * ks, 128, kH * 16),
+                             idesc_bf16(128, kH), ks > 0);
+            } else {
+                for (int ks = 0; ks < kH / 16; ++ks)
+                    mma_bf16(tbase, smem_desc(aH + 256 * ks, 128, kH * 16), smem_desc(aW3 + 256 * ks, 128, kH * 16),
+                             idesc_bf16(128, kOut), ks > 0);
+            }
+            mma_commit(bar);
+            const bool ok = mbar_wait(bar, phase);
+            *s_ok = ok ? 1 : 0;
+            if (!ok) atomicCAS(P.err, 0, RSI_ERR_TIMEOUT);
+            fence_before();
+        }
+        phase ^= 1u;
+        __syncthreads();
+        fence_after();
+        return *s_ok != 0;
+    };
+
+    while (true) {
+        if (tid == 0) *s_tile = atomicAdd(P.tile_ctr, 1);
+        __syncthreads();
+        const int tile = *s_tile;
+        if ((int64_t)tile * 128 >= P.n) break;
+        const int64_t r = (int64_t)tile * 128 + tid;
+        float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (r < P.n) seg_features(P.from, P.to, r, lo, sc, f);
+        {
+            uint4 w0, w1;
+            w0.x = pack_bf16x2(f[0], f[1]);
+            w0.y = pack_bf16x2(f[2], f[3]);
+            w0.z = pack_bf16x2(f[4], f[5]);
+            w0.w = 0u;
+            w1 = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(sm + kSmX + cm_offset(tid, 0, kIn)) = w0;
+            *reinterpret_cast<uint4*>(sm + kSmX + cm_offset(tid, 8, kIn)) = w1;
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (!run_chain(1)) break;
+        epilogue_hidden(tbase + lane_off, sBias, sm + kSmH, tid);
+        fence_proxy_async();
+        fence_before();
+        __syncthreads();
+        if (!run_chain(2)) break;
+        epilogue_hidden(tbase + lane_off + 256, sBias + kH, sm + kSmH, tid);
+        fence_proxy_async();
+        fence_before();
+        __syncthreads();
+        if (!run_chain(3)) break;
+        float best_v[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        int best_i[4] = {0, 0, 0, 0};
+#pragma unroll 1
+        for (int c = 0; c < kOut / 32; ++c) {
+            float v[32];
+            tmem_ld32(tbase + lane_off + 32 * c, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float z = v[j] + sBias[2 * kH + 32 * c + j];
+                v[j] = z;
+                const int idx = 32 * c + j;
+                if (z > best_v[3]) {   // insert (strictly greater: lower index wins ties)
+                    int k = 3;
+                    while (k > 0 && z > best_v[k - 1]) {
+                        best_v[k] = best_v[k - 1];
+                        best_i[k] = best_i[k - 1];
+                        --k;
+                    }
+                    best_v[k] = z;
+                    best_i[k] = idx;
+                }
+            }
+            if (P.logits && r < P.n) {
+                float4* dst = reinterpret_cast<float4*>(P.logits + r * kOut + 32 * c);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+        if (P.top4 && r < P.n)
+            *reinterpret_cast<uchar4*>(P.top4 + 4 * r) =
+                make_uchar4((uint8_t)best_i[0], (uint8_t)best_i[1], (uint8_t)best_i[2], (uint8_t)best_i[3]);
+        fence_before();
+        __syncthreads();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
+    }
+}
+
+// FP32 master parameters -> BF16 images of W1^T, W2^T, W3^T (core-matrix
+// layout) and the FP32 biases.
+__global__ void k_mlp_pack(const float* __restrict__ p, uint8_t* __restrict__ img, float* __restrict__ bias) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __nv_bfloat16* im = reinterpret_cast<__nv_bfloat16*>(img);
+    if (i < kW1) {   // W1[k][n], k < 16, n < 128
+        const int k = i / kH, n = i % kH;
+        im[(kImgW1 + cm_offset(n, k, kIn)) / 2] = __float2bfloat16_rn(p[kOffW1 + i]);
+    } else if (i < kW1 + kW2) {
+        const int j = i - kW1, k = j / kH, n = j % kH;
+        im[(kImgW2 + cm_offset(n, k, kH)) / 2] = __float2bfloat16_rn(p[kOffW2 + j]);
+    } else if (i < kW1 + kW2 + kW3) {
+        const int j = i - kW1 - kW2, k = j / kOut, n = j % kOut;
+        im[(kImgW3 + cm_offset(n, k, kH)) / 2] = __float2bfloat16_rn(p[kOffW3 + j]);
+    }
+    if (i < kH) {
+        bias[i] = p[kOffB1 + i];
+        bias[kH + i] = p[kOffB2 + i];
+    }
+    if (i < kOut) bias[2 * kH + i] = p[kOffB3 + i];
+}
+
+}  // namespace mlpk
+}  // namespace rsi
+
+struct rsi_mlp_s {
+    float* params = nullptr;   // FP32 master weights [kParams]
+    float* grads = nullptr;    // [kParams]
+    float* adam_m = nullptr;   // [kParams]
+    float* adam_v = nullptr;   // [kParams]
+    uint8_t* img = nullptr;    // BF16 images
+    float* bias = nullptr;     // 512
+    int* scratch_i = nullptr;  // tile counter, error
+    int64_t step = 0;
+    bool packed = false;
+    // training scratch
+    float* act = nullptr;
+    int64_t act_cap = 0;
+};
+
+namespace rsi {
+namespace mlpk {
+
+int ensure_packed(rsi_mlp_s* m, cudaStream_t s) {
+    if (m->packed) return RSI_OK;
+    k_mlp_pack<<<grid_for(kW1 + kW2 + kW3, 256), 256, 0, s>>>(m->params, m->img, m->bias);
+    note_launches(1);
+    RSI_CUDA_TRY(cudaGetLastError());
+    m->packed = true;
+    return RSI_OK;
+}
+
+void feature_map(rsi_bvh_t h, float lo[3], float sc[3]) {
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = h->lo[a];
+        sc[a] = h->hi[a] > h->lo[a] ? 2.0f / (h->hi[a] - h->lo[a]) : 0.0f;
+    }
+}
+
+int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, int64_t n, float* logits,
+               uint8_t* top4, cudaStream_t s) {
+    int rc = ensure_packed(m, s);
+    if (rc) return rc;
+    static bool attr_set = false;
+    if (!attr_set) {
+        RSI_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kSmBytes + 1024));
+        attr_set = true;
+    }
+    RSI_CUDA_TRY(cudaMemsetAsync(m->scratch_i, 0, 2 * sizeof(int), s));
+    FwdArgs P;
+    P.img = m->img;
+    P.bias = m->bias;
+    P.from = from;
+    P.to = to;
+    P.n = (int)n;
+    float lo[3], sc[3];
+    feature_map(h, lo, sc);
+    P.lo0 = lo[0];
+    P.lo1 = lo[1];
+    P.lo2 = lo[2];
+    P.sc0 = sc[0];
+    P.sc1 = sc[1];
+    P.sc2 = sc[2];
+    P.logits = logits;
+    P.top4 = top4;
+    P.tile_ctr = m->scratch_i;
+    P.err = m->scratch_i + 1;
+    const int64_t tiles = (n + 127) / 128;
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)device_sm_count());
+    k_mlp_forward_tc<<<grid, 128, kSmBytes + 1024, s>>>(P);
+    note_launches(1);
+    RSI_CUDA_TRY(cudaGetLastError());
+    return RSI_OK;
+}
+
+// He-style initial weights from a counter-based generator (splitmix64 +
+// Box-Muller), so a seed gives the same network on any host.
+uint64_t splitmix(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double gauss(uint64_t& st) {
+    double u1 = ((splitmix(st) >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    double u2 = (splitmix(st) >> 11) * (1.0 / 9007199254740992.0);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+}  // namespace mlpk
+}  // namespace rsi
+
+using namespace rsi::mlpk;
+
+extern "C" int rsi_mlp_create(uint64_t seed, rsi_mlp_t* out) {
+    if (!out) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_create: out is NULL");
+    *out = nullptr;
+    auto* m = new rsi_mlp_s();
+    const size_t pb = sizeof(float) * kParams;
+    char* base = nullptr;
+    if (cudaMalloc(&base, 4 * pb + kImgBytes + 512 * 4 + 256) != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return rsi::fail(RSI_ERR_OOM, "rsi_mlp_create: allocation failed");
+    }
+    m->params = reinterpret_cast<float*>(base);
+    m->grads = reinterpret_cast<float*>(base + pb);
+    m->adam_m = reinterpret_cast<float*>(base + 2 * pb);
+    m->adam_v = reinterpret_cast<float*>(base + 3 * pb);
+    m->img = reinterpret_cast<uint8_t*>(base + 4 * pb);
+    m->bias = reinterpret_cast<float*>(base + 4 * pb + kImgBytes);
+    m->scratch_i = reinterpret_cast<int*>(base + 4 * pb + kImgBytes + 512 * 4);
+    std::vector<float> p(kParams, 0.0f);
+    uint64_t st = seed * 0x2545F4914F6CDD1Dull + 0x4D4C50ull;
+    for (int k = 0; k < 6; ++k)
+        for (int n = 0; n < kH; ++n) p[kOffW1 + k * kH + n] = (float)(gauss(st) * std::sqrt(2.0 / 6.0));
+    for (int i = 0; i < kW2; ++i) p[kOffW2 + i] = (float)(gauss(st) * std::sqrt(2.0 / kH));
+    for (int i = 0; i < kW3; ++i) p[kOffW3 + i] = (float)(gauss(st) * std::sqrt(1.0 / kH));
+    cudaError_t e = cudaMemcpy(m->params, p.data(), pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, 2 * pb);
+    if (e == cudaSuccess) e = cudaMemset(m->img, 0, kImgBytes);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        delete m;
+        return rsi::cuda_fail(e, "rsi_mlp_create");
+    }
+    *out = m;
+    return RSI_OK;
+}
+
+extern "C" int rsi_mlp_free(rsi_mlp_t m) {
+    if (!m) return RSI_OK;
+    cudaDeviceSynchronize();
+    cudaFree(m->params);
+    if (m->act) cudaFree(m->act);
+    delete m;
+    return RSI_OK;
+}
+
+extern "C" int rsi_mlp_num_params(void) { return kParams; }
+
+extern "C" int rsi_mlp_set_params(rsi_mlp_t m, const float* h_params, void* stream) {
+    if (!m || !h_params) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_set_params: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    RSI_CUDA_TRY(cudaMemcpyAsync(m->params, h_params, sizeof(float) * kParams, cudaMemcpyHostToDevice, s));
+    RSI_CUDA_TRY(cudaStreamSynchronize(s));
+    m->packed = false;
+    return RSI_OK;
+}
+
+extern "C" int rsi_mlp_get_params(rsi_mlp_t m, float* h_params, float* h_grads, void* stream) {
+    if (!m) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_get_params: NULL handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h_params) RSI_CUDA_TRY(cudaMemcpyAsync(h_params, m->params, sizeof(float) * kParams, cudaMemcpyDeviceToHost, s));
+    if (h_grads) RSI_CUDA_TRY(cudaMemcpyAsync(h_grads, m->grads, sizeof(float) * kParams, cudaMemcpyDeviceToHost, s));
+    RSI_CUDA_TRY(cudaStreamSynchronize(s));
+    return RSI_OK;
+}
+
+extern "C" int rsi_mlp_forward(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
+                               float* d_logits, uint8_t* d_top4, void* stream) {
+    if (!m || !h || n < 0 || n > 0x7FFFFF00ll || (n > 0 && (!d_from || !d_to)))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_forward: bad arguments");
+    if (n == 0) return RSI_OK;
+    return forward_tc(m, h, d_from, d_to, n, d_logits, d_top4, (cudaStream_t)stream);
+}
+
+extern "C" int rsi_mlp_status(rsi_mlp_t m, void* stream) {
+    if (!m) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_status: NULL handle");
+    int v[2] = {0, 0};
+    RSI_CUDA_TRY(cudaMemcpyAsync(v, m->scratch_i, sizeof v, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    RSI_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (v[1]) return rsi::fail(v[1], "rsi_mlp: a tensor-core wait ran out");
+    return RSI_OK;
+}

@@ -1,0 +1,41 @@
+"""The autotuner: times candidate launch shapes and in-tile reorderings on a
+sample, caches the winner in a JSON file, and its choice changes no answer."""
+import json
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rsi():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2305_01867_gb300 as m
+    return m
+
+
+def test_autotune_caches_and_keeps_results(rsi, tmp_path):
+    mesh = W.config_mesh("c2")
+    F, E = W.rays(W.config_rays("c2", 500_000), mesh)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).cuda(), torch.from_numpy(mesh.triangles).cuda())
+    cache = str(tmp_path / "tune.json")
+    t1 = bvh.autotune(dF, dE, "count", cache_path=cache)
+    assert t1["from_cache"] == 0 and t1["candidates"] >= 6 and t1["ms"] > 0
+    assert t1["stack"] >= bvh.info()["height"] + 1
+    t2 = bvh.autotune(dF, dE, "count", cache_path=cache)
+    assert t2["from_cache"] == 1 and t2["candidates"] == 0
+    for k in ("block", "blocks_per_sm", "ray_sort_tile"):
+        assert t1[k] == t2[k]
+    d = json.load(open(cache))
+    assert len(d) == 1 and list(d.values())[0]["block"] == t1["block"]
+    base = bvh.query(dF, dE, "count")
+    tuned = bvh.query(dF, dE, "count", block=t1["block"], blocks_per_sm=t1["blocks_per_sm"],
+                      ray_sort_tile=t1["ray_sort_tile"])
+    assert torch.equal(base["count"], tuned["count"]) and torch.equal(base["ambiguous"], tuned["ambiguous"])

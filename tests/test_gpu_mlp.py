@@ -1,0 +1,68 @@
+"""The proposal network on the GPU against the FP64 reference: tensor-core
+inference (tcgen05, TMEM accumulators) logits within the BF16 tolerance."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rsi():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2305_01867_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def setup(rsi):
+    mesh = W.config_mesh("c1")
+    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).cuda(), torch.from_numpy(mesh.triangles).cuda())
+    params = ref.init_params(7)
+    rng = np.random.default_rng(3)
+    for k in ("b1", "b2", "b3"):   # non-zero biases exercise the epilogue
+        params[k] = rng.normal(0, 0.1, params[k].shape).astype(np.float32).astype(np.float64)
+    net = rsi.MLP(0)
+    net.set_params(params)
+    info = bvh.info()
+    return mesh, bvh, net, params, np.array(info["extent_lo"]), np.array(info["extent_hi"])
+
+
+# Tolerance: both sides round every layer input to BF16 (2^-8 relative);
+# a value that lands near a rounding boundary may round differently on the
+# two sides (FP32 vs FP64 pre-activation), one BF16 ulp, which moves a logit
+# by |w| * |h| * 2^-8 for each such flip; sums are otherwise exact products
+# accumulated in FP32 (~1e-6 relative).
+ATOL, RTOL = 3e-2, 1e-2
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 5000, 100_003])
+def test_forward_logits_match_reference(rsi, setup, n):
+    mesh, bvh, net, params, lo, hi = setup
+    F, E = W.rays(W.config_rays("c1", n), mesh)
+    out = net.forward(bvh, torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda())
+    net.status()
+    got = out["logits"].cpu().numpy().astype(np.float64)
+    idx = np.arange(n) if n <= 5000 else np.random.default_rng(1).choice(n, 3000, replace=False)
+    want, _ = ref.forward(params, ref.features(F[idx], E[idx], lo, hi))
+    err = np.abs(got[idx] - want)
+    assert np.all(err <= ATOL + RTOL * np.abs(want)), float(err.max())
+    assert float(err.mean()) < 2e-3
+    # top-4 is the arg-sort of the kernel's own logits (same precision)
+    t4 = out["top4"].cpu().numpy()
+    own = ref.top4(got)
+    assert np.array_equal(np.sort(t4, 1), np.sort(own, 1))
+
+
+def test_forward_is_deterministic(rsi, setup):
+    mesh, bvh, net, _, _, _ = setup
+    F, E = W.rays(W.config_rays("c1", 20000), mesh)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    a = net.forward(bvh, dF, dE)
+    b = net.forward(bvh, dF, dE)
+    assert torch.equal(a["logits"], b["logits"]) and torch.equal(a["top4"], b["top4"])
