@@ -55,6 +55,7 @@ extern "C" {
 #define RSI_COUNT 1   /* "intercept_count": number of distinct crossings    */
 
 typedef struct rsi_bvh_s* rsi_bvh_t;
+typedef struct rsi_mlp_s* rsi_mlp_t;
 
 /* Options of a query; a NULL pointer means all defaults (zeros). */
 typedef struct rsi_options {
@@ -86,6 +87,8 @@ typedef struct rsi_stats {
     int64_t ambiguous;     /* segments left ambiguous by the FP64 re-test    */
     int32_t tree_height;
     int32_t device_error;  /* RSI_OK or the RSI_ERR_* a kernel raised        */
+    int64_t proposal_confirmed; /* learned query: hits settled by the proposal */
+    int64_t fallback_rays;      /* learned query: segments left to the tree   */
 } rsi_stats;
 
 /* Static description of a built hierarchy. */
@@ -292,8 +295,6 @@ int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_
  *   W1 [16][128] (rows 6..15 unused), b1 [128], W2 [128][128], b2 [128],
  *   W3 [128][256], b3 [256]   (row-major, y = x W + b).
  */
-typedef struct rsi_mlp_s* rsi_mlp_t;
-
 /* New network with seeded He-normal weights and zero biases. */
 int rsi_mlp_create(uint64_t seed, rsi_mlp_t* out);
 int rsi_mlp_free(rsi_mlp_t m);
@@ -311,6 +312,40 @@ int rsi_mlp_get_params(rsi_mlp_t m, float* h_params, float* h_grads, void* strea
 int rsi_mlp_forward(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
                     float* d_logits, uint8_t* d_top4, void* stream);
 int rsi_mlp_status(rsi_mlp_t m, void* stream);
+
+/* One training step on the GPU over a batch of n (1..65536) segments with
+ * multi-hot labels d_labels [n][8] uint32 (bit c of word c/32: the segment
+ * meets a triangle of cluster c, see rsi_cluster_labels): forward with the
+ * inference roundings, mean binary cross-entropy over n x 256 logits,
+ * backward (the BF16 roundings pass gradients unchanged), gradients kept for
+ * rsi_mlp_get_params, then an Adam step (b1 0.9, b2 0.999, eps 1e-8, rate
+ * lr) on the FP32 master weights if `apply`.  h_loss (nullable) gets the
+ * batch loss before the step (the call then synchronizes `stream`). */
+int rsi_mlp_train_step(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* d_to,
+                       const uint32_t* d_labels, int64_t n, float lr, int apply, float* h_loss, void* stream);
+int rsi_mlp_reset_optimizer(rsi_mlp_t m, void* stream);
+
+/*
+ * Training labels: d_labels [n][8] uint32, bit c set when segment i meets a
+ * triangle of cluster c (c = 256 * leaf / n_triangles) -- FP32 decisions,
+ * the plain closed-interval one inside the error band (labels need not be
+ * exact: they only steer the proposal).
+ */
+int rsi_cluster_labels(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n, uint32_t* d_labels,
+                       void* stream);
+
+/*
+ * Boolean query with the learned proposal (Sec. 1's boolean mode; the
+ * proposal has no counterpart in the paper): the network proposes 4 of the
+ * 256 clusters per segment (tensor cores); the triangles of those clusters
+ * are tested in FP32 and a certain decisive hit ends the segment with hit =
+ * 1; every other segment gets the plain query (tree search + FP64 re-test).
+ * d_hit / d_ambiguous are therefore identical to rsi_query's.  Scratch as
+ * rsi_query (plus 4 B per segment); asynchronous unless `stats`.
+ */
+int rsi_query_learned(rsi_bvh_t h, rsi_mlp_t m, const float* d_from, const float* d_to, int64_t n_rays,
+                      const rsi_options* opt, uint8_t* d_hit, uint8_t* d_ambiguous, rsi_stats* stats,
+                      void* stream);
 
 /* Durations of the FP32 traversal kernel and of the FP64 re-test kernel of
  * the last query on `h` that ran with time_kernels = 1, from CUDA events

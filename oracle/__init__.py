@@ -59,6 +59,8 @@ def _load():
         lib.oracle_refit.argtypes = [P, P, P, i64, P, P, P]
         lib.oracle_refit.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_pair_classes.argtypes = [P, i64, P, i64, P, P, i64, P]
+        lib.oracle_pair_classes.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -110,6 +112,17 @@ def query(vertices, triangles, ray_from, ray_to, nthreads: int = 0):
     if rc != 0:
         raise ValueError("oracle_query: bad arguments (triangle index out of range?)")
     return res
+
+
+def pair_classes(vertices, triangles, ray_from, ray_to):
+    """[n_rays, n_triangles] uint8 class of every pair (PAIR_MISS/HIT/AMBIGUOUS)."""
+    lib = _load()
+    V, T = _f32(vertices).reshape(-1, 3), _i32(triangles).reshape(-1, 3)
+    F, E = _f32(ray_from).reshape(-1, 3), _f32(ray_to).reshape(-1, 3)
+    out = np.zeros((F.shape[0], T.shape[0]), np.uint8)
+    if lib.oracle_pair_classes(_ptr(V), V.shape[0], _ptr(T), T.shape[0], _ptr(F), _ptr(E), F.shape[0], _ptr(out)) != 0:
+        raise ValueError("oracle_pair_classes: triangle index out of range")
+    return out
 
 
 def extent(vertices):

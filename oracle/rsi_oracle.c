@@ -287,6 +287,21 @@ int oracle_query(const float* V, int64_t nV, const int32_t* T, int64_t nT,
     return 0;
 }
 
+/* Class of every pair (ray-major, n_rays x n_triangles bytes): the input of
+ * per-triangle checks such as which triangles a segment meets. */
+int oracle_pair_classes(const float* V, int64_t nV, const int32_t* T, int64_t nT, const float* from,
+                        const float* to, int64_t nR, uint8_t* cls) {
+    for (int64_t j = 0; j < 3 * nT; ++j)
+        if (T[j] < 0 || (int64_t)T[j] >= nV) return -1;
+    for (int64_t r = 0; r < nR; ++r)
+        for (int64_t j = 0; j < nT; ++j) {
+            const int32_t* tri = T + 3 * j;
+            cls[r * nT + j] = (uint8_t)oracle_classify_pair(from + 3 * r, to + 3 * r, V + 3 * (int64_t)tri[0],
+                                                            V + 3 * (int64_t)tri[1], V + 3 * (int64_t)tri[2], NULL);
+        }
+    return 0;
+}
+
 /* Surface extent (Sec. 3.3, get_min_max_extent_of_surface): per-axis min and
  * max over all vertices.  Returns -1 if any coordinate is NaN. */
 int oracle_extent(const float* V, int64_t nV, float* lo, float* hi) {

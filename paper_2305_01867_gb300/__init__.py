@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n_rays", ctypes.c_int64), ("node_visits", ctypes.c_int64), ("tri_tests", ctypes.c_int64),
                 ("band_rays", ctypes.c_int64), ("ambiguous", ctypes.c_int64), ("tree_height", ctypes.c_int32),
-                ("device_error", ctypes.c_int32)]
+                ("device_error", ctypes.c_int32), ("proposal_confirmed", ctypes.c_int64),
+                ("fallback_rays", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -111,6 +112,12 @@ def _load():
     lib.rsi_mlp_get_params.argtypes = [P, P, P, P]
     lib.rsi_mlp_forward.argtypes = [P, P, P, P, i64, P, P, P]
     lib.rsi_mlp_status.argtypes = [P, P]
+    lib.rsi_mlp_train_step.argtypes = [P, P, P, P, P, i64, ctypes.c_float, i32, ctypes.POINTER(ctypes.c_float), P]
+    lib.rsi_mlp_reset_optimizer.argtypes = [P, P]
+    lib.rsi_cluster_labels.argtypes = [P, P, P, i64, P, P]
+    lib.rsi_query_learned.argtypes = [P, P, P, P, i64, ctypes.POINTER(Options), P, P, ctypes.POINTER(Stats), P]
+    for name in ("rsi_mlp_train_step", "rsi_mlp_reset_optimizer", "rsi_cluster_labels", "rsi_query_learned"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("rsi_mlp_create", "rsi_mlp_free", "rsi_mlp_num_params", "rsi_mlp_set_params", "rsi_mlp_get_params",
                  "rsi_mlp_forward", "rsi_mlp_status"):
         getattr(lib, name).restype = ctypes.c_int
@@ -435,3 +442,63 @@ class MLP:
 
     def status(self, stream=None):
         check(lib.rsi_mlp_status(self._m, _stream(stream)))
+
+    def train_step(self, bvh, ray_from, ray_to, labels, lr=1e-3, apply=True, want_loss=False, stream=None):
+        """One GPU training step on a batch (labels: [n, 8] int32 bit masks).
+        Returns the batch loss when want_loss (synchronizes)."""
+        loss = ctypes.c_float()
+        check(lib.rsi_mlp_train_step(self._m, bvh.handle, _ptr(ray_from), _ptr(ray_to), _ptr(labels),
+                                     ray_from.shape[0], float(lr), int(apply),
+                                     ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
+
+    def reset_optimizer(self, stream=None):
+        check(lib.rsi_mlp_reset_optimizer(self._m, _stream(stream)))
+
+    def fit(self, bvh, ray_from, ray_to, labels, epochs=1, batch=8192, lr=1e-3, stream=None):
+        """Minibatch training over the whole set (in order); returns the
+        per-epoch mean loss of the last batches."""
+        n = ray_from.shape[0]
+        losses = []
+        for _ in range(epochs):
+            last = []
+            for b0 in range(0, n, batch):
+                b1 = min(n, b0 + batch)
+                want = b0 + batch >= n or (b0 // batch) % 50 == 0
+                l = self.train_step(bvh, ray_from[b0:b1], ray_to[b0:b1], labels[b0:b1], lr=lr, want_loss=want,
+                                    stream=stream)
+                if want:
+                    last.append(l)
+            losses.append(float(sum(last) / len(last)))
+        return losses
+
+
+def cluster_labels(bvh, ray_from, ray_to, stream=None):
+    """[n, 8] int32 bit masks of the clusters each segment meets (rsi_cluster_labels)."""
+    import torch
+    n = ray_from.shape[0]
+    out = torch.empty(n, 8, dtype=torch.int32, device=ray_from.device)
+    check(lib.rsi_cluster_labels(bvh.handle, _ptr(ray_from), _ptr(ray_to), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def query_learned(bvh, net, ray_from, ray_to, stats=False, hit=None, ambiguous=None, stream=None, **opts):
+    """Boolean query with the learned proposal (rsi_query_learned); answers
+    identical to LBVH.query(..., "any_hit")."""
+    import torch
+    _check_f32x3(ray_from, "ray_from")
+    _check_f32x3(ray_to, "ray_to")
+    n = ray_from.shape[0]
+    if hit is None:
+        hit = torch.empty(n, dtype=torch.uint8, device=ray_from.device)
+    if ambiguous is None:
+        ambiguous = torch.empty(n, dtype=torch.uint8, device=ray_from.device)
+    opt = Options(int(opts.get("fp32_only", 0)), int(opts.get("block", 0)), int(opts.get("blocks_per_sm", 0)),
+                  int(stats), 0, 0, 0)
+    st = Stats()
+    check(lib.rsi_query_learned(bvh.handle, net.handle, _ptr(ray_from), _ptr(ray_to), n, ctypes.byref(opt),
+                                _ptr(hit), _ptr(ambiguous), ctypes.byref(st) if stats else None, _stream(stream)))
+    out = {"hit": hit, "ambiguous": ambiguous}
+    if stats:
+        out["stats"] = st.as_dict()
+    return out

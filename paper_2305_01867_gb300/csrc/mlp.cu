@@ -338,6 +338,122 @@ __global__ void k_mlp_pack(const float* __restrict__ p, uint8_t* __restrict__ im
     if (i < kOut) bias[2 * kH + i] = p[kOffB3 + i];
 }
 
+// ---------------------------------------------------------------- training
+// C[M][N] = op(A)[M][K] op(B)[K][N] in FP32; op(A)[m][k] = TA ? A[k][m] :
+// A[m][k] (row-major, leading dimension lda), likewise B.  64 x 64 tiles,
+// 256 threads, 4 x 4 outputs per thread.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm(const float* __restrict__ A, const float* __restrict__ B,
+                                              float* __restrict__ C, int M, int N, int K, int lda, int ldb, int ldc) {
+    __shared__ float As[16][64 + 4], Bs[16][64 + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+            const int kk = i / 64, mm = i % 64;
+            const int m = m0 + mm, k = k0 + kk, n = n0 + mm;
+            As[kk][mm] = (m < M && k < K) ? (TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k]) : 0.0f;
+            Bs[kk][mm] = (n < N && k < K) ? (TB ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n]) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty * 4 + i];
+                b[i] = Bs[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+            if (m < M && n < N) C[(int64_t)m * ldc + n] = acc[i][j];
+        }
+}
+
+// BF16-rounded copies of the weight matrices (the values the forward uses).
+__global__ void k_round_weights(const float* __restrict__ p, float* __restrict__ wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kW1) wb[i] = bf16r(p[kOffW1 + i]);
+    else if (i < kW1 + kW2) wb[i] = bf16r(p[kOffW2 + i - kW1]);
+    else if (i < kW1 + kW2 + kW3) wb[i] = bf16r(p[kOffW3 + i - kW1 - kW2]);
+}
+
+__global__ void k_train_features(const float* __restrict__ from, const float* __restrict__ to, int n, float lo0,
+                                 float lo1, float lo2, float sc0, float sc1, float sc2, float* __restrict__ x) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float lo[3] = {lo0, lo1, lo2}, sc[3] = {sc0, sc1, sc2};
+    float f[6];
+    seg_features(from, to, r, lo, sc, f);
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) x[(int64_t)r * kIn + k] = k < 6 ? bf16r(f[k]) : 0.0f;
+}
+
+// z += b (kept for the backward); a = BF16(GELU(z)).
+__global__ void k_bias_gelu(float* __restrict__ z, const float* __restrict__ b, float* __restrict__ a, int rows, int cols) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * cols) return;
+    const float v = z[i] + b[i % cols];
+    z[i] = v;
+    a[i] = bf16r(gelu(v));
+}
+
+// Mean BCE with logits over n x 256: dz = (sigmoid(z + b3) - y) / (n 256);
+// the loss sum goes to *loss.
+__global__ void k_bce(float* __restrict__ z, const float* __restrict__ b3, const uint32_t* __restrict__ labels, int n,
+                      float* __restrict__ loss) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (i < (int64_t)n * kOut) {
+        const int c = (int)(i % kOut);
+        const int64_t r = i / kOut;
+        const float v = z[i] + b3[c];
+        const float y = (float)((labels[r * 8 + (c >> 5)] >> (c & 31)) & 1u);
+        l = fmaxf(v, 0.0f) - v * y + log1pf(expf(-fabsf(v)));
+        z[i] = (1.0f / (1.0f + expf(-v)) - y) / ((float)n * kOut);
+    }
+    for (int off = 16; off; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, l);
+}
+
+// dz = da * GELU'(z)
+__global__ void k_gelu_back(const float* __restrict__ da, const float* __restrict__ z, float* __restrict__ dz, int64_t m) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) dz[i] = da[i] * gelu_grad(z[i]);
+}
+
+// g[c] = sum over rows of d[r][c]
+__global__ void k_colsum(const float* __restrict__ d, int rows, int cols, float* __restrict__ g) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.0f;
+    for (int r = 0; r < rows; ++r) s += d[(int64_t)r * cols + c];
+    g[c] = s;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
 }  // namespace mlpk
 }  // namespace rsi
 
@@ -354,6 +470,7 @@ struct rsi_mlp_s {
     // training scratch
     float* act = nullptr;
     int64_t act_cap = 0;
+    float* d_loss = nullptr;
 };
 
 namespace rsi {
@@ -409,6 +526,87 @@ int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, in
     k_mlp_forward_tc<<<grid, 128, kSmBytes + 1024, s>>>(P);
     note_launches(1);
     RSI_CUDA_TRY(cudaGetLastError());
+    return RSI_OK;
+}
+
+template <bool TA, bool TB>
+void gemm(const float* A, const float* B, float* C, int M, int N, int K, int lda, int ldb, int ldc, cudaStream_t s) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    k_gemm<TA, TB><<<grid, 256, 0, s>>>(A, B, C, M, N, K, lda, ldb, ldc);
+    note_launches(1);
+}
+
+// One training step on a batch of n <= 65536 segments: forward with the
+// BF16 roundings of the inference kernel, mean BCE, backward (roundings as
+// identity), gradients into m->grads, then Adam when `apply`.
+int train_step(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, const uint32_t* labels, int n, float lr,
+               int apply, float* h_loss, cudaStream_t s) {
+    const int64_t need = (int64_t)n * (kIn + 4 * kH + kOut + kH) + kW1 + kW2 + kW3 + 1;
+    if (m->act_cap < need) {
+        if (m->act) {
+            RSI_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(m->act);
+            m->act = nullptr;
+            m->act_cap = 0;
+        }
+        if (cudaMalloc(&m->act, sizeof(float) * need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RSI_ERR_OOM, "rsi_mlp_train_step: activation buffers");
+        }
+        m->act_cap = need;
+    }
+    float* x = m->act;                     // [n][16]
+    float* z1 = x + (int64_t)n * kIn;      // [n][128]
+    float* a1 = z1 + (int64_t)n * kH;
+    float* z2 = a1 + (int64_t)n * kH;
+    float* a2 = z2 + (int64_t)n * kH;
+    float* z3 = a2 + (int64_t)n * kH;      // [n][256], then dz3
+    float* da = z3 + (int64_t)n * kOut;    // [n][128]
+    float* wb = da + (int64_t)n * kH;      // BF16-rounded W1 | W2 | W3
+    float* loss = wb + kW1 + kW2 + kW3;
+    float *W1b = wb, *W2b = wb + kW1, *W3b = wb + kW1 + kW2;
+    float* g = m->grads;
+    float lo[3], sc[3];
+    feature_map(h, lo, sc);
+    k_round_weights<<<grid_for(kW1 + kW2 + kW3, 256), 256, 0, s>>>(m->params, wb);
+    k_train_features<<<grid_for(n, 256), 256, 0, s>>>(from, to, n, lo[0], lo[1], lo[2], sc[0], sc[1], sc[2], x);
+    note_launches(2);
+    gemm<false, false>(x, W1b, z1, n, kH, kIn, kIn, kH, kH, s);
+    k_bias_gelu<<<grid_for((int64_t)n * kH, 256), 256, 0, s>>>(z1, m->params + kOffB1, a1, n, kH);
+    gemm<false, false>(a1, W2b, z2, n, kH, kH, kH, kH, kH, s);
+    k_bias_gelu<<<grid_for((int64_t)n * kH, 256), 256, 0, s>>>(z2, m->params + kOffB2, a2, n, kH);
+    gemm<false, false>(a2, W3b, z3, n, kOut, kH, kH, kOut, kOut, s);
+    RSI_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), s));
+    k_bce<<<grid_for((int64_t)n * kOut, 256), 256, 0, s>>>(z3, m->params + kOffB3, labels, n, loss);
+    note_launches(3);
+    // backward: z3 now holds dz3
+    gemm<true, false>(a2, z3, g + kOffW3, kH, kOut, n, kH, kOut, kOut, s);          // a2^T dz3
+    k_colsum<<<1, kOut, 0, s>>>(z3, n, kOut, g + kOffB3);
+    gemm<false, true>(z3, W3b, da, n, kH, kOut, kOut, kOut, kH, s);                 // dz3 W3^T
+    k_gelu_back<<<grid_for((int64_t)n * kH, 256), 256, 0, s>>>(da, z2, z2, (int64_t)n * kH);   // z2 <- dz2
+    gemm<true, false>(a1, z2, g + kOffW2, kH, kH, n, kH, kH, kH, s);                // a1^T dz2
+    k_colsum<<<1, kH, 0, s>>>(z2, n, kH, g + kOffB2);
+    gemm<false, true>(z2, W2b, da, n, kH, kH, kH, kH, kH, s);                       // dz2 W2^T
+    k_gelu_back<<<grid_for((int64_t)n * kH, 256), 256, 0, s>>>(da, z1, z1, (int64_t)n * kH);   // z1 <- dz1
+    gemm<true, false>(x, z1, g + kOffW1, kIn, kH, n, kIn, kH, kH, s);               // x^T dz1
+    k_colsum<<<1, kH, 0, s>>>(z1, n, kH, g + kOffB1);
+    note_launches(5);
+    if (apply) {
+        ++m->step;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.0f - std::pow(b1, (float)m->step), c2 = 1.0f - std::pow(b2, (float)m->step);
+        k_adam<<<grid_for(kParams, 256), 256, 0, s>>>(m->params, g, m->adam_m, m->adam_v, kParams, lr, b1, b2, 1e-8f,
+                                                       c1, c2);
+        note_launches(1);
+        m->packed = false;
+    }
+    RSI_CUDA_TRY(cudaGetLastError());
+    if (h_loss) {
+        float l = 0.0f;
+        RSI_CUDA_TRY(cudaMemcpyAsync(&l, loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        RSI_CUDA_TRY(cudaStreamSynchronize(s));
+        *h_loss = l / ((float)n * kOut);
+    }
     return RSI_OK;
 }
 
@@ -510,5 +708,20 @@ extern "C" int rsi_mlp_status(rsi_mlp_t m, void* stream) {
     RSI_CUDA_TRY(cudaMemcpyAsync(v, m->scratch_i, sizeof v, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     RSI_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     if (v[1]) return rsi::fail(v[1], "rsi_mlp: a tensor-core wait ran out");
+    return RSI_OK;
+}
+
+extern "C" int rsi_mlp_train_step(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* d_to,
+                                  const uint32_t* d_labels, int64_t n, float lr, int apply, float* h_loss,
+                                  void* stream) {
+    if (!m || !h || !d_from || !d_to || !d_labels || n < 1 || n > 65536)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_train_step: need 1 <= n <= 65536 and all buffers");
+    return train_step(m, h, d_from, d_to, d_labels, (int)n, lr, apply, h_loss, (cudaStream_t)stream);
+}
+
+extern "C" int rsi_mlp_reset_optimizer(rsi_mlp_t m, void* stream) {
+    if (!m) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_reset_optimizer: NULL handle");
+    RSI_CUDA_TRY(cudaMemsetAsync(m->adam_m, 0, 2 * sizeof(float) * kParams, (cudaStream_t)stream));
+    m->step = 0;
     return RSI_OK;
 }

@@ -43,6 +43,7 @@ struct QueryArgs {
     uint8_t* amb;
     int32_t* band_ids;
     const int32_t* perm;   // traversal order of the segments, or NULL
+    const int* n_dev;      // number of segments read from device memory, or NULL
     DevCounters* ctr;
     float dmax0, dmax1, dmax2;
     int fp32_only;
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int n_rays = BATCHED ? B.total : (int)A.n_rays;
+    const int n_rays = BATCHED ? B.total : (A.n_dev ? *A.n_dev : (int)A.n_rays);
     // BATCHED: the lane's batch and its hierarchy (uniform kernel arguments otherwise)
     int l_batch = 0, l_ntri = 0;
     const Node* l_nodes = nullptr;
@@ -841,9 +842,112 @@ __global__ void __launch_bounds__(256) k_ray_tile_sort(const float* __restrict__
     }
 }
 
+// Cluster of leaf j: 256 equal ranges of the Morton-ordered leaves.
+__device__ __forceinline__ int leaf_cluster(int j, int64_t n_tri) { return (int)(((int64_t)j * 256) / n_tri); }
+__device__ __forceinline__ int cluster_begin(int c, int64_t n_tri) { return (int)(((int64_t)c * n_tri + 255) / 256); }
+
+// Multi-hot training labels: every leaf the segment's padded box search
+// reaches, tested in FP32 (certain hit, or the plain decision in the band).
+template <int STACK>
+__global__ void __launch_bounds__(128) k_cluster_labels(QueryArgs A, uint32_t* __restrict__ labels) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t bits[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const float3 s = make_float3(A.from[3 * r], A.from[3 * r + 1], A.from[3 * r + 2]);
+        const float3 e = make_float3(A.to[3 * r], A.to[3 * r + 1], A.to[3 * r + 2]);
+        if (!(bad3(s) || bad3(e))) {
+            const SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
+            auto leaf = [&](int j) {
+                bool plain;
+                const int c = tri_fp32(g, load_tri(A.tris, j), true, plain);
+                if (c == kHit || (c == kBand && plain)) {
+                    const int k = leaf_cluster(j, A.n_tri);
+                    bits[k >> 5] |= 1u << (k & 31);
+                }
+            };
+            if (A.n_tri == 1) {
+                leaf(0);
+            } else {
+                int stack[STACK];
+                int sp = 0, node = 0;
+                while (true) {
+                    float4 lmin, lmax, rmin, rmax;
+                    load_node(A.nodes, node, lmin, lmax, rmin, rmax);
+                    const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
+                    bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
+                    if (hl && lref < 0) {
+                        leaf(~lref);
+                        hl = false;
+                    }
+                    if (hr && rref < 0) {
+                        leaf(~rref);
+                        hr = false;
+                    }
+                    if (hl && hr && sp < STACK) {
+                        stack[sp++] = rref;
+                        node = lref;
+                    } else if (hl) {
+                        node = lref;
+                    } else if (hr) {
+                        node = rref;
+                    } else if (sp > 0) {
+                        node = stack[--sp];
+                    } else {
+                        break;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 8; ++w) labels[r * 8 + w] = bits[w];
+    }
+}
+
+// Proposal verification: the triangles of the 4 proposed clusters, best
+// first; an FP32-certain decisive hit settles the segment (hit = 1, not
+// ambiguous); the rest go to the fallback list in `order`.
+__global__ void __launch_bounds__(256) k_verify_proposals(QueryArgs A, const uint8_t* __restrict__ top4,
+                                                          int32_t* __restrict__ order) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool confirmed = false;
+    if (r < A.n_rays) {
+        const float3 s = make_float3(A.from[3 * r], A.from[3 * r + 1], A.from[3 * r + 2]);
+        const float3 e = make_float3(A.to[3 * r], A.to[3 * r + 1], A.to[3 * r + 2]);
+        if (!(bad3(s) || bad3(e))) {
+            const SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
+            const uchar4 p = *reinterpret_cast<const uchar4*>(top4 + 4 * r);
+            const int cl[4] = {p.x, p.y, p.z, p.w};
+            for (int q = 0; q < 4 && !confirmed; ++q) {
+                const int j1 = cluster_begin(cl[q] + 1, A.n_tri);
+                for (int j = cluster_begin(cl[q], A.n_tri); j < j1; ++j) {
+                    bool plain;
+                    if (tri_fp32(g, load_tri(A.tris, j), false, plain) == kHit) {
+                        confirmed = true;
+                        break;
+                    }
+                }
+            }
+        }
+        if (confirmed) {
+            A.hit[r] = 1;
+            if (A.amb) A.amb[r] = 0;
+        }
+    }
+    const bool left = r < A.n_rays && !confirmed;
+    const unsigned m = __ballot_sync(0xffffffffu, left);
+    const unsigned mc = __ballot_sync(0xffffffffu, confirmed);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(&A.ctr->n_fallback, __popc(m));
+    if (lane == 0 && mc) atomicAdd(&A.ctr->n_confirmed, __popc(mc));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (left) order[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)r;
+}
+
 __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->band_count = 0;
     c->next_ray = 0;
+    c->n_fallback = 0;
+    c->n_confirmed = 0;
     if (ready != ~0ull) c->ready = ready;   // ~0: a streaming plan, fed by posts
     c->error = 0;
     c->node_visits = c->tri_tests = c->ambiguous = 0;
@@ -874,7 +978,7 @@ void launch_fp64(const QueryArgs& A, int height, int grid, cudaStream_t s, const
 // Launch the two passes for one batch of segments already on the device.
 int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n, int mode, const rsi_options* opt,
                  uint8_t* d_hit, int32_t* d_count, uint8_t* d_amb, int32_t* band_ids, int32_t* perm_scratch,
-                 DevCounters* ctr, cudaStream_t s) {
+                 DevCounters* ctr, cudaStream_t s, const int32_t* order = nullptr, const int* n_dev = nullptr) {
     rsi_options o = {};
     if (opt) o = *opt;
     if (h->height >= 127) return fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
@@ -890,6 +994,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     A.amb = d_amb;
     A.band_ids = band_ids;
     A.perm = nullptr;
+    A.n_dev = nullptr;
     A.ctr = ctr;
     A.dmax0 = h->dmax[0];
     A.dmax1 = h->dmax[1];
@@ -919,7 +1024,12 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
         note_launches(1);
         A.perm = perm_scratch;
     }
-    k_reset_query<<<1, 1, 0, s>>>(ctr, (unsigned long long)n);
+    if (order) {   // learned path: the segments left by the proposal, counted on the device
+        A.perm = order;
+        A.n_dev = n_dev;
+    } else {
+        k_reset_query<<<1, 1, 0, s>>>(ctr, (unsigned long long)n);
+    }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[0], s));
     if (mode == RSI_ANY_HIT) {
         if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, grid, block, s);
@@ -949,7 +1059,7 @@ int ensure_band_capacity(rsi_bvh_t h, int64_t n, cudaStream_t s) {
         h->band_ids = nullptr;
         h->band_cap = 0;
     }
-    if (cudaMalloc(&h->band_ids, 8 * (size_t)cap) != cudaSuccess) {   // band list, then permutation
+    if (cudaMalloc(&h->band_ids, 12 * (size_t)cap) != cudaSuccess) {   // band list | order | proposals
         cudaGetLastError();
         return fail(RSI_ERR_OOM, "rsi_query: band list allocation failed");
     }
@@ -969,6 +1079,8 @@ int read_stats(rsi_bvh_t h, DevCounters* ctr, int64_t n, rsi_stats* st, cudaStre
         st->ambiguous = (int64_t)c.ambiguous;
         st->tree_height = h->height;
         st->device_error = c.error;
+        st->proposal_confirmed = c.n_confirmed;
+        st->fallback_rays = c.n_fallback;
     }
     if (c.error) return fail(c.error, "rsi_query: device error " + std::to_string(c.error));
     return RSI_OK;
@@ -1064,8 +1176,80 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
     return rsi::read_stats(h, h->ctr, n_rays, stats ? stats : &tmp, s);
 }
 
-// ---------------------------------------------------------------- batched
+// ---------------------------------------------------------------- learned
 using namespace rsi;   // the kernels and launchers above
+
+extern "C" int rsi_cluster_labels(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n, uint32_t* d_labels,
+                                  void* stream) {
+    if (!h || n < 0 || n > 0x7FFFFFFFll || (n > 0 && (!d_from || !d_to || !d_labels)))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_cluster_labels: bad arguments");
+    if (n == 0) return RSI_OK;
+    if (h->height >= 127) return rsi::fail(RSI_ERR_STACK, "rsi_cluster_labels: tree too deep");
+    QueryArgs A{};
+    A.nodes = h->nodes;
+    A.tris = h->tris;
+    A.n_tri = h->n_tri;
+    A.from = d_from;
+    A.to = d_to;
+    A.n_rays = n;
+    A.dmax0 = h->dmax[0];
+    A.dmax1 = h->dmax[1];
+    A.dmax2 = h->dmax[2];
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = rsi::device_sm_count() * 8;
+    if (h->height < 32) k_cluster_labels<32><<<grid, 128, 0, s>>>(A, d_labels);
+    else if (h->height < 64) k_cluster_labels<64><<<grid, 128, 0, s>>>(A, d_labels);
+    else k_cluster_labels<128><<<grid, 128, 0, s>>>(A, d_labels);
+    rsi::note_launches(1);
+    RSI_CUDA_TRY(cudaGetLastError());
+    return RSI_OK;
+}
+
+extern "C" int rsi_query_learned(rsi_bvh_t h, rsi_mlp_t m, const float* d_from, const float* d_to, int64_t n_rays,
+                                 const rsi_options* opt, uint8_t* d_hit, uint8_t* d_ambiguous, rsi_stats* stats,
+                                 void* stream) {
+    int rc = check_query_args(h, d_from, d_to, n_rays, RSI_ANY_HIT, d_hit, nullptr);
+    if (rc) return rc;
+    if (!m) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_learned: NULL network");
+    if (n_rays > 0x7FFFFF00ll) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_learned: too many segments");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_rays == 0) {
+        if (stats) *stats = rsi_stats{};
+        return RSI_OK;
+    }
+    rc = rsi::ensure_band_capacity(h, n_rays, s);
+    if (rc) return rc;
+    int32_t* order = h->band_ids + h->band_cap;
+    uint8_t* top4 = reinterpret_cast<uint8_t*>(h->band_ids + 2 * h->band_cap);
+    rc = rsi::mlpk::forward_tc(m, h, d_from, d_to, n_rays, nullptr, top4, s);
+    if (rc) return rc;
+    k_reset_query<<<1, 1, 0, s>>>(h->ctr, ~0ull);
+    QueryArgs A{};
+    A.nodes = h->nodes;
+    A.tris = h->tris;
+    A.n_tri = h->n_tri;
+    A.from = d_from;
+    A.to = d_to;
+    A.n_rays = n_rays;
+    A.hit = d_hit;
+    A.amb = d_ambiguous;
+    A.ctr = h->ctr;
+    A.dmax0 = h->dmax[0];
+    A.dmax1 = h->dmax[1];
+    A.dmax2 = h->dmax[2];
+    k_verify_proposals<<<rsi::grid_for(n_rays, 256), 256, 0, s>>>(A, top4, order);
+    rsi::note_launches(2);
+    rsi_options o = {};
+    if (opt) o = *opt;
+    o.ray_sort_tile = 0;
+    rc = rsi::query_device(h, d_from, d_to, n_rays, RSI_ANY_HIT, &o, d_hit, nullptr, d_ambiguous, h->band_ids, nullptr,
+                           h->ctr, s, order, &h->ctr->n_fallback);
+    if (rc) return rc;
+    if (stats) return rsi::read_stats(h, h->ctr, n_rays, stats, s);
+    return RSI_OK;
+}
+
+// ---------------------------------------------------------------- batched
 
 // Many independent (hierarchy, segment batch) pairs answered by one
 // persistent traversal launch over the concatenated segment index space,

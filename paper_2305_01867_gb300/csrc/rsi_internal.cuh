@@ -42,6 +42,8 @@ struct DevCounters {
     unsigned long long node_visits, tri_tests, ambiguous;
     unsigned long long next_ray;   // work counter of the persistent traversal
     unsigned long long ready;      // segments available to the work queue
+    int n_fallback;                // learned query: segments left to the tree search
+    int n_confirmed;               // learned query: hits confirmed by the proposal
     unsigned int ext_bits[6];   // extent as order-preserving uint (min xyz, max xyz)
     unsigned int dmax_bits[3];  // largest triangle box side per axis (float bits)
     unsigned int pad1;
@@ -97,5 +99,11 @@ int device_sm_count();
 
 // Count of kernel launches made by the library (rsi_kernel_launches).
 void note_launches(int n);
+
+namespace mlpk {
+// Tensor-core inference of the proposal network (mlp.cu).
+int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, int64_t n, float* logits,
+               uint8_t* top4, cudaStream_t s);
+}  // namespace mlpk
 
 }  // namespace rsi

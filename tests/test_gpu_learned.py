@@ -1,0 +1,156 @@
+"""The learned proposal on the GPU: training kernels against the FP64
+reference (gradients), Adam against its closed form, cluster labels against
+the oracle's pair classes, and the learned boolean query, whose answers must
+equal the plain query's exactly whatever the network proposes."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rsi():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2305_01867_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def c1(rsi):
+    mesh = W.config_mesh("c1")
+    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).cuda(), torch.from_numpy(mesh.triangles).cuda())
+    info = bvh.info()
+    return mesh, bvh, np.array(info["extent_lo"]), np.array(info["extent_hi"])
+
+
+def _labels_np(lab):
+    """[n, 8] int32 bit masks -> [n, 256] float multi-hot."""
+    u = lab.astype(np.int64) & 0xFFFFFFFF
+    bits = (u[:, :, None] >> np.arange(32)[None, None, :]) & 1
+    return bits.reshape(len(lab), 256).astype(np.float64)
+
+
+def _pack_labels(y):
+    """[n, 256] 0/1 -> [n, 8] int32 bit masks (bit c of word c / 32)."""
+    b = y.reshape(len(y), 8, 32).astype(np.uint64) << np.arange(32, dtype=np.uint64)[None, None, :]
+    return b.sum(2).astype(np.uint32).view(np.int32)
+
+
+def test_cluster_labels_match_oracle(rsi, c1):
+    mesh, bvh, _, _ = c1
+    F, E = W.rays(W.config_rays("c1", 300), mesh)
+    lab = rsi.cluster_labels(bvh, torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()).cpu().numpy()
+    cls = oracle.pair_classes(mesh.vertices, mesh.triangles, F, E)
+    perm = bvh.export()["perm"]
+    leaf_of = np.empty(len(perm), np.int64)
+    leaf_of[perm] = np.arange(len(perm))            # triangle -> leaf
+    clus = (leaf_of * 256) // len(perm)
+    got = _labels_np(lab)
+    checked = 0
+    for i in range(len(F)):
+        if np.any(cls[i] == oracle.PAIR_AMBIGUOUS):
+            continue
+        want = np.zeros(256)
+        want[np.unique(clus[cls[i] == oracle.PAIR_HIT])] = 1
+        assert np.array_equal(got[i], want), i
+        checked += 1
+    assert checked > 250
+
+
+def test_gradients_match_reference(rsi, c1):
+    mesh, bvh, lo, hi = c1
+    F, E = W.rays(W.config_rays("c1", 777), mesh)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    y = (np.random.default_rng(8).uniform(size=(len(F), 256)) < 0.03).astype(np.float64)
+    lab = torch.from_numpy(_pack_labels(y)).cuda()
+    params = ref.init_params(11)
+    rng = np.random.default_rng(4)
+    for k in ("b1", "b2", "b3"):
+        params[k] = rng.normal(0, 0.1, params[k].shape).astype(np.float32).astype(np.float64)
+    net = rsi.MLP(1)
+    net.set_params(params)
+    loss = net.train_step(bvh, dF, dE, lab, apply=False, want_loss=True)
+    _, g_gpu = net.get_params(grads=True)
+    x = ref.features(F, E, lo, hi)
+    logits, cache = ref.forward(params, x)
+    assert abs(loss - ref.bce_loss(logits, y)) < 1e-4 * max(1.0, abs(loss))
+    g_ref = ref.backward(params, cache, logits, y)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a, b = g_gpu[k], g_ref[k]
+        if k == "W1":
+            a, b = a[:6], b[:6]
+        # FP32 sums of the same BF16-rounded operands vs FP64; a BF16 rounding
+        # that lands differently on the two sides moves single terms by 2^-8
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel < 2e-2, (k, rel)
+    assert np.allclose(g_gpu["W1"][6:], 0.0)   # padded inputs carry no gradient
+
+
+def test_adam_step_closed_form(rsi, c1):
+    """From zero moments the first Adam step is -lr g / (|g| + eps)."""
+    mesh, bvh, _, _ = c1
+    F, E = W.rays(W.config_rays("c1", 2048), mesh)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    lab = rsi.cluster_labels(bvh, dF, dE)
+    net = rsi.MLP(2)
+    p0 = net.get_params()
+    net.reset_optimizer()
+    net.train_step(bvh, dF, dE, lab, lr=1e-2, apply=True)
+    p1, g = net.get_params(grads=True)
+    for k in p0:
+        step = p1[k] - p0[k]
+        want = -1e-2 * g[k] / (np.abs(g[k]) + 1e-8)
+        assert np.allclose(step, want, rtol=1e-4, atol=1e-7), k
+
+
+@pytest.fixture(scope="module")
+def trained(rsi, c1):
+    """A network trained briefly on 2e5 labelled segments of the c1 kind."""
+    mesh, bvh, _, _ = c1
+    F, E = W.rays(W.RaySpec("uniform_box", 200_000, seed=11), mesh)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    lab = rsi.cluster_labels(bvh, dF, dE)
+    net = rsi.MLP(3)
+    losses = net.fit(bvh, dF, dE, lab, epochs=4, batch=4096, lr=2e-3)
+    return net, losses
+
+
+def test_training_reduces_loss(rsi, trained):
+    net, losses = trained
+    assert losses[-1] < 0.5 * losses[0], losses
+
+
+@pytest.mark.parametrize("n", [1, 127, 129, 50_000])
+def test_learned_query_equals_plain(rsi, c1, trained, n):
+    mesh, bvh, _, _ = c1
+    F, E = W.rays(W.RaySpec("uniform_box", n, seed=12), mesh)
+    if n > 100:
+        F[7] = np.nan   # undefined segment: ambiguous, hit 0 on both paths
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    plain = bvh.query(dF, dE, "any_hit")
+    for net in (trained[0], rsi.MLP(99)):   # trained and untrained proposals
+        got = rsi.query_learned(bvh, net, dF, dE, stats=True)
+        assert torch.equal(got["hit"], plain["hit"]) and torch.equal(got["ambiguous"], plain["ambiguous"])
+        st = got["stats"]
+        assert st["proposal_confirmed"] + st["fallback_rays"] == n and st["device_error"] == 0
+
+
+def test_trained_proposal_gains(rsi, c1, trained):
+    """What the trained network buys: the share of hits it confirms without a
+    tree search, against an untrained network's."""
+    mesh, bvh, _, _ = c1
+    F, E = W.rays(W.RaySpec("uniform_box", 100_000, seed=13), mesh)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    hits = int(bvh.query(dF, dE, "any_hit")["hit"].sum())
+    good = rsi.query_learned(bvh, trained[0], dF, dE, stats=True)["stats"]["proposal_confirmed"]
+    rand = rsi.query_learned(bvh, rsi.MLP(98), dF, dE, stats=True)["stats"]["proposal_confirmed"]
+    # a short training run (about 200 steps) already settles several times
+    # more hits without a tree search than an untrained network does
+    assert good > 0.2 * hits and good > 5 * rand, (good, rand, hits)
