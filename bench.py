@@ -231,6 +231,74 @@ def measure_batched(rsi, torch, dev, c4, args):
     return out
 
 
+MLP_FLOP_PER_SEGMENT = 2 * (6 * 128 + 128 * 128 + 128 * 256)   # algorithmic (unpadded) multiply-adds x 2
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1900.0, 1700.0, "fallback"
+
+
+def measure_learned(rsi, torch, dev, c5, args):
+    """The c1 mesh: train the proposal network on labelled segments, then
+    time the boolean query over fresh segments with and without it (answers
+    identical by construction) and the tensor-core forward alone."""
+    mesh, ((Ft, Et), (Fe, Ee)) = c5
+    stream = torch.cuda.current_stream()
+    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).to(dev), torch.from_numpy(mesh.triangles).to(dev))
+    dFt, dEt = torch.from_numpy(Ft).to(dev), torch.from_numpy(Et).to(dev)
+    labels = rsi.cluster_labels(bvh, dFt, dEt)
+    net = rsi.MLP(5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.fit(bvh, dFt, dEt, labels, epochs=2, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del dFt, dEt, labels
+    dF, dE = torch.from_numpy(Fe).to(dev), torch.from_numpy(Ee).to(dev)
+    n = dF.shape[0]
+    hit = torch.empty(n, dtype=torch.uint8, device=dev)
+    amb = torch.empty(n, dtype=torch.uint8, device=dev)
+    steps = max(3, min(args.steps, 10))
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_plain = timed(lambda: bvh.query(dF, dE, "any_hit", hit=hit, ambiguous=amb))
+    plain_hit = hit.clone()
+    ms_learned = timed(lambda: rsi.query_learned(bvh, net, dF, dE, hit=hit, ambiguous=amb))
+    same = bool(torch.equal(hit, plain_hit))
+    st = rsi.query_learned(bvh, net, dF, dE, hit=hit, ambiguous=amb, stats=True)["stats"]
+    top4 = torch.empty(n, 4, dtype=torch.uint8, device=dev)
+    ms_fwd = timed(lambda: net.forward(bvh, dF, dE, logits=False, top4=True))
+    tflops = MLP_FLOP_PER_SEGMENT * n / (ms_fwd / 1e3) / 1e12
+    burst, sustained, kind = bf16_peak()
+    hits = int(plain_hit.sum())
+    bvh.close()
+    return {"train_segments": int(Ft.shape[0]), "epochs": 2, "batch": 8192, "train_s": train_s,
+            "loss_per_epoch": losses, "eval_segments": n, "steps": steps,
+            "plain_any_hit": {"ms": ms_plain, "rays_per_s": n / (ms_plain / 1e3)},
+            "learned_any_hit": {"ms": ms_learned, "rays_per_s": n / (ms_learned / 1e3), "matches_plain": same},
+            "proposal_confirmed": st["proposal_confirmed"], "hits": hits,
+            "confirmed_share_of_hits": st["proposal_confirmed"] / max(hits, 1), "fallback_rays": st["fallback_rays"],
+            "mlp_forward_tc": {"ms": ms_fwd, "tflops": tflops, "flop_per_segment": MLP_FLOP_PER_SEGMENT,
+                               "peak_tflops": sustained, "frac": tflops / sustained,
+                               "peak_source": f"{kind} bf16 sustained"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,6 +310,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=600_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-rays", type=int, default=100_000_000)
+    ap.add_argument("--train-rays", type=int, default=10_000_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local, pg = dist_setup(args)
@@ -266,6 +337,12 @@ def main():
     if not args.no_batched and rank == 0:
         jobs = W.batched_meshes(n_meshes=64, seed=4)
         c4 = (jobs, W.rays_many(jobs))           # process pool before any GPU call
+    c5 = None
+    if not args.no_learned and rank == 0:
+        m1 = W.config_mesh("c1")
+        jobs = [(m1, W.RaySpec("uniform_box", args.train_rays, seed=11)),
+                (m1, W.RaySpec("uniform_box", args.learned_rays, seed=12))]
+        c5 = (m1, W.rays_many(jobs))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = len(F)
@@ -396,6 +473,8 @@ def main():
     }
     if c4 is not None:
         line["batched_c4"] = measure_batched(rsi, torch, dev, c4, args)
+    if c5 is not None:
+        line["learned_c5"] = measure_learned(rsi, torch, dev, c5, args)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mesh, W.config_rays("c2"), args.cpu_sample)
     print(json.dumps(line))

@@ -313,6 +313,12 @@ int rsi_mlp_forward(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* 
                     float* d_logits, uint8_t* d_top4, void* stream);
 int rsi_mlp_status(rsi_mlp_t m, void* stream);
 
+/* The network's activation on n device floats z (for tests): d_erf gets the
+ * erf approximation the network uses (Abramowitz & Stegun 7.1.26, |error| <=
+ * 1.5e-7), d_erf_cuda CUDA's erff of the same z, d_gelu the GELU
+ * 0.5 z (1 + erf(z / sqrt 2)) the layers apply. */
+int rsi_mlp_activation(const float* d_z, int64_t n, float* d_erf, float* d_erf_cuda, float* d_gelu, void* stream);
+
 /* One training step on the GPU over a batch of n (1..65536) segments with
  * multi-hot labels d_labels [n][8] uint32 (bit c of word c/32: the segment
  * meets a triangle of cluster c, see rsi_cluster_labels): forward with the

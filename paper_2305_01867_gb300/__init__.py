@@ -112,6 +112,8 @@ def _load():
     lib.rsi_mlp_get_params.argtypes = [P, P, P, P]
     lib.rsi_mlp_forward.argtypes = [P, P, P, P, i64, P, P, P]
     lib.rsi_mlp_status.argtypes = [P, P]
+    lib.rsi_mlp_activation.argtypes = [P, i64, P, P, P, P]
+    lib.rsi_mlp_activation.restype = ctypes.c_int
     lib.rsi_mlp_train_step.argtypes = [P, P, P, P, P, i64, ctypes.c_float, i32, ctypes.POINTER(ctypes.c_float), P]
     lib.rsi_mlp_reset_optimizer.argtypes = [P, P]
     lib.rsi_cluster_labels.argtypes = [P, P, P, i64, P, P]
@@ -502,3 +504,12 @@ def query_learned(bvh, net, ray_from, ray_to, stats=False, hit=None, ambiguous=N
     if stats:
         out["stats"] = st.as_dict()
     return out
+
+
+def activation(z, stream=None):
+    """(erf by the network's approximation, CUDA erff, GELU) of a device
+    float32 vector (rsi_mlp_activation)."""
+    import torch
+    a, b, g = torch.empty_like(z), torch.empty_like(z), torch.empty_like(z)
+    check(lib.rsi_mlp_activation(_ptr(z), z.numel(), _ptr(a), _ptr(b), _ptr(g), _stream(stream)))
+    return a, b, g

@@ -46,9 +46,20 @@ __host__ __device__ constexpr uint32_t cm_offset(int row, int k, int K) {
     return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula
+// 7.1.26: erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2), t = 1 / (1 + p x),
+// x >= 0, |error| <= 1.5e-7 (far below the BF16 resolution of the layer
+// outputs); odd extension for x < 0.
+__device__ __forceinline__ float erf_as(float x) {
+    const float ax = fabsf(x);
+    const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    return copysignf(1.0f - poly * __expf(-ax * ax), x);
+}
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
+    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * __expf(-0.5f * z * z) * 0.3989422804014327f;
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -103,15 +114,17 @@ __device__ __forceinline__ unsigned long long now_ns() {
     return t;
 }
 
-// Bounded wait for an mbarrier phase: false after ~2 s.
+// Bounded wait for an mbarrier phase: the waiting thread is suspended by the
+// hardware between checks (suspend-time hint 1 ms) instead of spinning;
+// false after ~2 s.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     const unsigned long long t0 = now_ns();
     while (true) {
         uint32_t done;
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(mbar), "r"(phase)
+            : "r"(mbar), "r"(phase), "r"(1000000u)
             : "memory");
         if (done) return true;
         if (now_ns() - t0 > 2000000000ull) return false;
@@ -140,11 +153,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Hidden-layer epilogue: this thread's row of a 128-column accumulator ->
-// + bias -> GELU -> BF16 -> row of the next layer's K-major A operand.
-__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* __restrict__ bias, uint8_t* sA, int row) {
-#pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
+// Hidden-layer epilogue of one 32-column slice c of this thread's row:
+// + bias -> GELU -> BF16 -> the row of the next layer's K-major A operand.
+__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* __restrict__ bias, uint8_t* sA, int row,
+                                                int c) {
+    {
         float v[32];
         tmem_ld32(taddr + 32 * c, v);
 #pragma unroll
@@ -164,9 +177,11 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* __r
 constexpr int kSmX = kImgBytes;                 // [128 x 16] features
 constexpr int kSmH = kSmX + 128 * kIn * 2;       // [128 x 128] hidden activations
 constexpr int kSmBias = kSmH + 128 * kH * 2;     // 512 floats
-constexpr int kSmBar = kSmBias + 512 * 4;        // mbarrier + TMEM address
+constexpr int kSmTop = kSmBias + 512 * 4;        // [4 column groups][128 rows][4] top-4 keys
+constexpr int kSmBar = kSmTop + 4 * 128 * 4 * 4; // mbarrier + TMEM address + flags
 constexpr int kSmBytes = kSmBar + 64;
 constexpr int kTmemCols = 512;
+constexpr int kFwdThreads = 512;                 // 16 warps: 4 lane quarters x 4 column groups
 
 struct FwdArgs {
     const uint8_t* img;    // BF16 weight images
@@ -177,23 +192,49 @@ struct FwdArgs {
     float lo0, lo1, lo2, sc0, sc1, sc2;   // feature map: (p - lo) * sc - 1
     float* logits;         // [n][256] or NULL
     uint8_t* top4;         // [n][4] or NULL (cluster ids, best first)
-    int* tile_ctr;         // work counter, 0 at launch
     int* err;              // RSI_ERR_TIMEOUT if a tensor-core wait ran out
 };
 
-__global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(FwdArgs P) {
+// Top-4 selection on 32-bit keys: the order-preserving bits of the logit
+// with its low 8 bits replaced by 255 - cluster, so a larger key is a larger
+// logit (compared to 24 significant bits) and equal logits rank the lower
+// cluster first.  Insertion keeps t0 >= t1 >= t2 >= t3 with min/max only.
+__device__ __forceinline__ uint32_t logit_key(float z, int cluster) {
+    const uint32_t b = __float_as_uint(z);
+    const uint32_t o = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    return (o & 0xFFFFFF00u) | (uint32_t)(255 - cluster);
+}
+__device__ __forceinline__ void top4_insert(uint32_t k, uint32_t t[4]) {
+    t[3] = max(t[3], k);
+    uint32_t lo = min(t[2], t[3]);
+    t[2] = max(t[2], t[3]);
+    t[3] = lo;
+    lo = min(t[1], t[2]);
+    t[1] = max(t[1], t[2]);
+    t[2] = lo;
+    lo = min(t[0], t[1]);
+    t[0] = max(t[0], t[1]);
+    t[1] = lo;
+}
+
+// 16 warps per CTA: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows) and
+// column group w / 4, so every epilogue is split four ways by columns; the
+// four partial top-4 lists of a row are merged through shared memory.
+__global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_forward_tc(FwdArgs P) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, cg = warp >> 2;
+    const int row = quarter * 32 + lane;   // tile row of this thread in every epilogue
     float* sBias = reinterpret_cast<float*>(sm + kSmBias);
+    uint32_t* sTop = reinterpret_cast<uint32_t*>(sm + kSmTop);   // [4 groups][128 rows][4] keys
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kSmBar);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSmBar + 8);
-    int* s_tile = reinterpret_cast<int*>(sm + kSmBar + 16);
     int* s_ok = reinterpret_cast<int*>(sm + kSmBar + 20);
 
-    for (int i = tid; i < kImgBytes / 16; i += 128)
+    for (int i = tid; i < kImgBytes / 16; i += kFwdThreads)
         reinterpret_cast<uint4*>(sm)[i] = reinterpret_cast<const uint4*>(P.img)[i];
-    for (int i = tid; i < 512; i += 128) sBias[i] = P.bias[i];
+    for (int i = tid; i < 512; i += kFwdThreads) sBias[i] = P.bias[i];
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -209,7 +250,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(FwdArgs P) {
     __syncthreads();
     fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lanes
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;   // this warp's TMEM lanes
     const uint32_t bar = smem_addr(mbar);
     const uint32_t aX = smem_addr(sm + kSmX), aH = smem_addr(sm + kSmH);
     const uint32_t aW1 = smem_addr(sm + kImgW1), aW2 = smem_addr(sm + kImgW2), aW3 = smem_addr(sm + kImgW3);
@@ -244,58 +285,66 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(FwdArgs P) {
         return *s_ok != 0;
     };
 
-    while (true) {
-        if (tid == 0) *s_tile = atomicAdd(P.tile_ctr, 1);
-        __syncthreads();
-        const int tile = *s_tile;
-        if ((int64_t)tile * 128 >= P.n) break;
-        const int64_t r = (int64_t)tile * 128 + tid;
-        float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (r < P.n) seg_features(P.from, P.to, r, lo, sc, f);
-        {
-            uint4 w0, w1;
+    // static schedule: tile = blockIdx.x + k gridDim.x; the segments of the
+    // next tile are loaded into registers while this one is processed
+    const int64_t n_tiles = ((int64_t)P.n + 127) / 128;
+    float seg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto load_seg = [&](int64_t t) {
+        const int64_t r = t * 128 + tid;
+        if (tid < 128 && t < n_tiles && r < P.n) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                seg[a] = __ldg(P.from + 3 * r + a);
+                seg[3 + a] = __ldg(P.to + 3 * r + a);
+            }
+        }
+    };
+    load_seg(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        if (tid < 128) {
+            const int64_t r = tile * 128 + tid;
+            float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (r < P.n) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    f[a] = fminf(fmaxf((seg[a] - lo[a]) * sc[a] - 1.0f, -4.0f), 4.0f);
+                    f[3 + a] = fminf(fmaxf((seg[3 + a] - lo[a]) * sc[a] - 1.0f, -4.0f), 4.0f);
+                }
+            }
+            uint4 w0;
             w0.x = pack_bf16x2(f[0], f[1]);
             w0.y = pack_bf16x2(f[2], f[3]);
             w0.z = pack_bf16x2(f[4], f[5]);
             w0.w = 0u;
-            w1 = make_uint4(0u, 0u, 0u, 0u);
             *reinterpret_cast<uint4*>(sm + kSmX + cm_offset(tid, 0, kIn)) = w0;
-            *reinterpret_cast<uint4*>(sm + kSmX + cm_offset(tid, 8, kIn)) = w1;
+            *reinterpret_cast<uint4*>(sm + kSmX + cm_offset(tid, 8, kIn)) = make_uint4(0u, 0u, 0u, 0u);
         }
+        load_seg(tile + gridDim.x);
         fence_proxy_async();
         __syncthreads();
         if (!run_chain(1)) break;
-        epilogue_hidden(tbase + lane_off, sBias, sm + kSmH, tid);
+        epilogue_hidden(tbase + lane_off, sBias, sm + kSmH, row, cg);
         fence_proxy_async();
         fence_before();
         __syncthreads();
         if (!run_chain(2)) break;
-        epilogue_hidden(tbase + lane_off + 256, sBias + kH, sm + kSmH, tid);
+        epilogue_hidden(tbase + lane_off + 256, sBias + kH, sm + kSmH, row, cg);
         fence_proxy_async();
         fence_before();
         __syncthreads();
         if (!run_chain(3)) break;
-        float best_v[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        int best_i[4] = {0, 0, 0, 0};
+        const int64_t r = tile * 128 + row;
+        uint32_t ta[4] = {0u, 0u, 0u, 0u}, tb[4] = {0u, 0u, 0u, 0u};   // two streams for ILP
 #pragma unroll 1
-        for (int c = 0; c < kOut / 32; ++c) {
+        for (int c = 2 * cg; c < 2 * cg + 2; ++c) {   // this warp's 64 logits of the row
             float v[32];
             tmem_ld32(tbase + lane_off + 32 * c, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float z = v[j] + sBias[2 * kH + 32 * c + j];
-                v[j] = z;
-                const int idx = 32 * c + j;
-                if (z > best_v[3]) {   // insert (strictly greater: lower index wins ties)
-                    int k = 3;
-                    while (k > 0 && z > best_v[k - 1]) {
-                        best_v[k] = best_v[k - 1];
-                        best_i[k] = best_i[k - 1];
-                        --k;
-                    }
-                    best_v[k] = z;
-                    best_i[k] = idx;
-                }
+            for (int j = 0; j < 32; j += 2) {
+                v[j] += sBias[2 * kH + 32 * c + j];
+                v[j + 1] += sBias[2 * kH + 32 * c + j + 1];
+                top4_insert(logit_key(v[j], 32 * c + j), ta);
+                top4_insert(logit_key(v[j + 1], 32 * c + j + 1), tb);
             }
             if (P.logits && r < P.n) {
                 float4* dst = reinterpret_cast<float4*>(P.logits + r * kOut + 32 * c);
@@ -303,17 +352,42 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward_tc(FwdArgs P) {
                 for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
         }
-        if (P.top4 && r < P.n)
-            *reinterpret_cast<uchar4*>(P.top4 + 4 * r) =
-                make_uchar4((uint8_t)best_i[0], (uint8_t)best_i[1], (uint8_t)best_i[2], (uint8_t)best_i[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) top4_insert(tb[k], ta);
+        *reinterpret_cast<uint4*>(sTop + (cg * 128 + row) * 4) = make_uint4(ta[0], ta[1], ta[2], ta[3]);
         fence_before();
         __syncthreads();
+        if (cg == 0) {   // merge the other column groups' lists into this row's
+#pragma unroll
+            for (int g = 1; g < 4; ++g) {
+                const uint4 o = *reinterpret_cast<const uint4*>(sTop + (g * 128 + row) * 4);
+                top4_insert(o.x, ta);
+                top4_insert(o.y, ta);
+                top4_insert(o.z, ta);
+                top4_insert(o.w, ta);
+            }
+            if (P.top4 && r < P.n)
+                *reinterpret_cast<uchar4*>(P.top4 + 4 * r) =
+                    make_uchar4((uint8_t)(255u - (ta[0] & 255u)), (uint8_t)(255u - (ta[1] & 255u)),
+                                (uint8_t)(255u - (ta[2] & 255u)), (uint8_t)(255u - (ta[3] & 255u)));
+        }
     }
     __syncthreads();
     if (warp == 0) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
     }
+}
+
+// The network's activation pieces on a vector (tests): erf by the published
+// approximation, CUDA's erff beside it, and GELU.
+__global__ void k_activation(const float* __restrict__ z, int64_t n, float* __restrict__ erf_a,
+                             float* __restrict__ erf_cuda, float* __restrict__ g) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    erf_a[i] = erf_as(z[i]);
+    erf_cuda[i] = erff(z[i]);
+    g[i] = gelu(z[i]);
 }
 
 // FP32 master parameters -> BF16 images of W1^T, W2^T, W3^T (core-matrix
@@ -519,11 +593,10 @@ int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, in
     P.sc2 = sc[2];
     P.logits = logits;
     P.top4 = top4;
-    P.tile_ctr = m->scratch_i;
     P.err = m->scratch_i + 1;
     const int64_t tiles = (n + 127) / 128;
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)device_sm_count());
-    k_mlp_forward_tc<<<grid, 128, kSmBytes + 1024, s>>>(P);
+    k_mlp_forward_tc<<<grid, kFwdThreads, kSmBytes + 1024, s>>>(P);
     note_launches(1);
     RSI_CUDA_TRY(cudaGetLastError());
     return RSI_OK;
@@ -723,5 +796,16 @@ extern "C" int rsi_mlp_reset_optimizer(rsi_mlp_t m, void* stream) {
     if (!m) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_reset_optimizer: NULL handle");
     RSI_CUDA_TRY(cudaMemsetAsync(m->adam_m, 0, 2 * sizeof(float) * kParams, (cudaStream_t)stream));
     m->step = 0;
+    return RSI_OK;
+}
+
+extern "C" int rsi_mlp_activation(const float* d_z, int64_t n, float* d_erf, float* d_erf_cuda, float* d_gelu,
+                                  void* stream) {
+    if (n < 0 || (n > 0 && (!d_z || !d_erf || !d_erf_cuda || !d_gelu)))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_activation: bad arguments");
+    if (n == 0) return RSI_OK;
+    k_activation<<<rsi::grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(d_z, n, d_erf, d_erf_cuda, d_gelu);
+    rsi::note_launches(1);
+    RSI_CUDA_TRY(cudaGetLastError());
     return RSI_OK;
 }

@@ -33,6 +33,13 @@ def setup(rsi):
     return mesh, bvh, net, params, np.array(info["extent_lo"]), np.array(info["extent_hi"])
 
 
+def _top4_rule(logits):
+    b = logits.astype(np.float32).view(np.uint32).astype(np.uint64)
+    o = np.where(b & 0x80000000, (~b) & 0xFFFFFFFF, b | 0x80000000)
+    key = (o & 0xFFFFFF00) | (255 - np.arange(logits.shape[1], dtype=np.uint64))[None, :]
+    return np.argsort(-key.astype(np.int64), axis=1, kind="stable")[:, :4].astype(np.uint8)
+
+
 # Tolerance: both sides round every layer input to BF16 (2^-8 relative);
 # a value that lands near a rounding boundary may round differently on the
 # two sides (FP32 vs FP64 pre-activation), one BF16 ulp, which moves a logit
@@ -53,10 +60,11 @@ def test_forward_logits_match_reference(rsi, setup, n):
     err = np.abs(got[idx] - want)
     assert np.all(err <= ATOL + RTOL * np.abs(want)), float(err.max())
     assert float(err.mean()) < 2e-3
-    # top-4 is the arg-sort of the kernel's own logits (same precision)
+    # top-4 of the kernel's own logits under the proposal's rule: logits
+    # compared to 24 significant bits (order-preserving bits with the low 8
+    # replaced by 255 - cluster, so ties go to the lower cluster)
     t4 = out["top4"].cpu().numpy()
-    own = ref.top4(got)
-    assert np.array_equal(np.sort(t4, 1), np.sort(own, 1))
+    assert np.array_equal(t4, _top4_rule(out["logits"].cpu().numpy()))
 
 
 def test_forward_is_deterministic(rsi, setup):
@@ -66,3 +74,20 @@ def test_forward_is_deterministic(rsi, setup):
     a = net.forward(bvh, dF, dE)
     b = net.forward(bvh, dF, dE)
     assert torch.equal(a["logits"], b["logits"]) and torch.equal(a["top4"], b["top4"])
+
+
+def test_erf_approximation_against_cuda_and_bound(rsi):
+    """The network's erf (Abramowitz & Stegun 7.1.26) stays within its
+    published 1.5e-7 bound of the exact erf and close to CUDA's erff; GELU
+    built on it matches the FP64 GELU."""
+    import math
+    z = torch.linspace(-8, 8, 200_001, device="cuda")
+    a, b, g = rsi.activation(z)
+    zz = z.cpu().numpy().astype(np.float64)
+    exact = np.array([math.erf(v) for v in zz])
+    # published bound 1.5e-7 (exact arithmetic) plus the FP32 evaluation of
+    # 1 - poly exp(-x^2): a few units of 2^-24 near x = 0 where the two
+    # terms nearly cancel, and the fast exponential's relative error
+    assert np.abs(a.cpu().numpy() - exact).max() <= 1e-6
+    assert np.abs(a.cpu().numpy() - b.cpu().numpy()).max() <= 1e-6
+    assert np.allclose(g.cpu().numpy(), ref.gelu(zz), atol=1e-6, rtol=1e-6)
