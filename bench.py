@@ -136,6 +136,21 @@ def dist_setup(args):
     return ws, rank, local, pg
 
 
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Weak scaling: every rank answers its own batch of the same workload."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(pg, value: float, device) -> float:
+    """The slowest rank's time (the job finishes when it does)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, ws, rank):
     """The FP64 oracle as it stands, on this machine's host cores."""
     if rank != 0:
@@ -331,7 +346,7 @@ def main():
 
     mesh = W.config_mesh("c2")
     spec = W.config_rays("c2", args.rays)
-    spec.seed = spec.seed + 1000 * rank          # each rank its own batch (weak scaling)
+    spec.seed = rank_seed(spec.seed, rank)       # each rank its own batch (weak scaling)
     F, E = W.rays(spec, mesh)
     c4 = None
     if not args.no_batched and rank == 0:
@@ -394,11 +409,7 @@ def main():
     barrier()
     launches = rsi.kernel_launches() - l0
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1) / args.steps
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps, dev)
     value = ws * n / (ms / 1e3)
     build_ms = statistics.median(p[0].elapsed_time(p[1]) for p in phase)
     any_ms = statistics.median(p[1].elapsed_time(p[2]) for p in phase)
@@ -425,11 +436,7 @@ def main():
     for _ in range(args.steps):
         step_e2e()
     barrier()
-    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
-    if pg:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(pg, 1e3 * (time.perf_counter() - t0) / args.steps, dev)
     same = bool(torch.equal(hh, hit.cpu()) and torch.equal(hc, cnt.cpu()))
     h2d = (pV.numel() * 4 + pT.numel() * 4) + 2 * (pF.numel() + pE.numel()) * 4
     d2h = n * (1 + 1) + n * (4 + 1)

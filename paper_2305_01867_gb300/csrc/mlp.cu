@@ -416,19 +416,23 @@ __global__ void k_mlp_pack(const float* __restrict__ p, uint8_t* __restrict__ im
 // C[M][N] = op(A)[M][K] op(B)[K][N] in FP32; op(A)[m][k] = TA ? A[k][m] :
 // A[m][k] (row-major, leading dimension lda), likewise B.  64 x 64 tiles,
 // 256 threads, 4 x 4 outputs per thread.
+// blockIdx.z splits K into chunks of kchunk; with more than one chunk the
+// partial products are added into C (zeroed by the caller).
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm(const float* __restrict__ A, const float* __restrict__ B,
-                                              float* __restrict__ C, int M, int N, int K, int lda, int ldb, int ldc) {
+                                              float* __restrict__ C, int M, int N, int K, int lda, int ldb, int ldc,
+                                              int kchunk) {
     __shared__ float As[16][64 + 4], Bs[16][64 + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = kb; k0 < ke; k0 += 16) {
         for (int i = threadIdx.x; i < 16 * 64; i += 256) {
             const int kk = i / 64, mm = i % 64;
             const int m = m0 + mm, k = k0 + kk, n = n0 + mm;
-            As[kk][mm] = (m < M && k < K) ? (TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k]) : 0.0f;
-            Bs[kk][mm] = (n < N && k < K) ? (TB ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n]) : 0.0f;
+            As[kk][mm] = (m < M && k < ke) ? (TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k]) : 0.0f;
+            Bs[kk][mm] = (n < N && k < ke) ? (TB ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n]) : 0.0f;
         }
         __syncthreads();
 #pragma unroll
@@ -451,7 +455,10 @@ __global__ void __launch_bounds__(256) k_gemm(const float* __restrict__ A, const
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
-            if (m < M && n < N) C[(int64_t)m * ldc + n] = acc[i][j];
+            if (m < M && n < N) {
+                if (gridDim.z > 1) atomicAdd(C + (int64_t)m * ldc + n, acc[i][j]);
+                else C[(int64_t)m * ldc + n] = acc[i][j];
+            }
         }
 }
 
@@ -507,13 +514,14 @@ __global__ void k_gelu_back(const float* __restrict__ da, const float* __restric
     if (i < m) dz[i] = da[i] * gelu_grad(z[i]);
 }
 
-// g[c] = sum over rows of d[r][c]
+// g[c] += sum over a chunk of 256 rows of d[r][c] (g zeroed by the caller)
 __global__ void k_colsum(const float* __restrict__ d, int rows, int cols, float* __restrict__ g) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = threadIdx.x;
+    const int r0 = blockIdx.x * 256, r1 = min(rows, r0 + 256);
     if (c >= cols) return;
     float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += d[(int64_t)r * cols + c];
-    g[c] = s;
+    for (int r = r0; r < r1; ++r) s += d[(int64_t)r * cols + c];
+    atomicAdd(g + c, s);
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
@@ -602,11 +610,23 @@ int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, in
     return RSI_OK;
 }
 
+// C = op(A) op(B).  A long reduction (the batch, for weight gradients) is
+// split into chunks of 512 accumulated atomically so the grid fills the GPU.
 template <bool TA, bool TB>
-void gemm(const float* A, const float* B, float* C, int M, int N, int K, int lda, int ldb, int ldc, cudaStream_t s) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<TA, TB><<<grid, 256, 0, s>>>(A, B, C, M, N, K, lda, ldb, ldc);
+int gemm(const float* A, const float* B, float* C, int M, int N, int K, int lda, int ldb, int ldc, cudaStream_t s) {
+    const int chunks = K >= 2048 ? (K + 511) / 512 : 1;
+    if (chunks > 1) RSI_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * ldc, s));
+    dim3 grid((N + 63) / 64, (M + 63) / 64, chunks);
+    k_gemm<TA, TB><<<grid, 256, 0, s>>>(A, B, C, M, N, K, lda, ldb, ldc, chunks > 1 ? 512 : K);
     note_launches(1);
+    return RSI_OK;
+}
+
+int colsum(const float* d, int rows, int cols, float* g, cudaStream_t s) {
+    RSI_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(float) * cols, s));
+    k_colsum<<<(rows + 255) / 256, cols, 0, s>>>(d, rows, cols, g);
+    note_launches(1);
+    return RSI_OK;
 }
 
 // One training step on a batch of n <= 65536 segments: forward with the
@@ -654,16 +674,16 @@ int train_step(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, co
     note_launches(3);
     // backward: z3 now holds dz3
     gemm<true, false>(a2, z3, g + kOffW3, kH, kOut, n, kH, kOut, kOut, s);          // a2^T dz3
-    k_colsum<<<1, kOut, 0, s>>>(z3, n, kOut, g + kOffB3);
+    colsum(z3, n, kOut, g + kOffB3, s);
     gemm<false, true>(z3, W3b, da, n, kH, kOut, kOut, kOut, kH, s);                 // dz3 W3^T
     k_gelu_back<<<grid_for((int64_t)n * kH, 256), 256, 0, s>>>(da, z2, z2, (int64_t)n * kH);   // z2 <- dz2
     gemm<true, false>(a1, z2, g + kOffW2, kH, kH, n, kH, kH, kH, s);                // a1^T dz2
-    k_colsum<<<1, kH, 0, s>>>(z2, n, kH, g + kOffB2);
+    colsum(z2, n, kH, g + kOffB2, s);
     gemm<false, true>(z2, W2b, da, n, kH, kH, kH, kH, kH, s);                       // dz2 W2^T
     k_gelu_back<<<grid_for((int64_t)n * kH, 256), 256, 0, s>>>(da, z1, z1, (int64_t)n * kH);   // z1 <- dz1
     gemm<true, false>(x, z1, g + kOffW1, kIn, kH, n, kIn, kH, kH, s);               // x^T dz1
-    k_colsum<<<1, kH, 0, s>>>(z1, n, kH, g + kOffB1);
-    note_launches(5);
+    colsum(z1, n, kH, g + kOffB1, s);
+    note_launches(2);
     if (apply) {
         ++m->step;
         const float b1 = 0.9f, b2 = 0.999f;
