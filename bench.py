@@ -51,11 +51,11 @@ def peaks():
 
 
 def source_hash():
-    h = hashlib.sha256()
-    for name in ("query.cu", "rsi_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2305_01867_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
+    """Hash of the traversal kernels' source: the region between their
+    markers in query.cu (device code and the structures it reads)."""
+    q = open(os.path.join(ROOT, "paper_2305_01867_gb300", "csrc", "query.cu")).read()
+    b, e = q.index("// [traversal kernel: begin]"), q.index("// [traversal kernel: end]")
+    return hashlib.sha256(q[b:e].encode()).hexdigest()[:16]
 
 
 def traffic_per_launch():
@@ -392,10 +392,13 @@ def main():
         if pg:
             pg.barrier()
 
+    # the clock sampler starts (and its NVML set-up finishes) before the warm-up,
+    # so only its steady 50 ms sampling overlaps the timed region
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    time.sleep(0.5)
     for _ in range(args.warmup):
         step()
     barrier()
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     n_ev = args.steps
     phase = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_ev)]
     trav = []

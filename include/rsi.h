@@ -26,6 +26,9 @@
  *     stream).  Work is stream-ordered: a call returns after enqueueing unless
  *     stated otherwise.  Calls that share a handle must be ordered on one
  *     stream (they share the handle's scratch memory).
+ *   - Device memory of handles and their scratch comes from a private
+ *     stream-ordered pool per device: up to 4 GiB of freed blocks stay cached
+ *     for later handles, and frees do not synchronize the device.
  *   - Every function returns RSI_OK (0) or a negative RSI_ERR_* code and
  *     never throws; rsi_last_error() then describes the failure.
  */
@@ -172,9 +175,11 @@ int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_ray
 
 /*
  * As rsi_query with segments and results in HOST memory.  The segments are
- * streamed to the device in chunks and the results back, with copies and
- * traversal overlapped on internal streams; returns after the results are
- * in host memory.  Page-locked host buffers give asynchronous copies.
+ * streamed to the device in chunks of 2^21 and the results back, with copies
+ * and traversal overlapped on internal streams; returns after the results are
+ * in host memory.  Page-locked host buffers give asynchronous copies.  The
+ * staging is shared by all handles of a device: concurrent host-buffer
+ * queries on one device run one after the other.
  */
 int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n_rays, int mode,
                    const rsi_options* opt, uint8_t* h_hit, int32_t* h_count, uint8_t* h_ambiguous,

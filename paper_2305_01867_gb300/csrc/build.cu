@@ -459,12 +459,11 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
         total += align_up(sizes[i]);
     }
     char* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, total);
-    if (e != cudaSuccess) {
+    if (pool_alloc(reinterpret_cast<void**>(&base), total, s) != RSI_OK) {
         delete h;
-        cudaGetLastError();
-        return fail(RSI_ERR_OOM, "lbvh_build: cudaMalloc of " + std::to_string(total) + " bytes failed");
+        return RSI_ERR_OOM;
     }
+    cudaError_t e = cudaSuccess;
     h->device_bytes = (int64_t)total;
     h->nodes = (Node*)(base + off[0]);
     h->tris = (Tri*)(base + off[1]);
@@ -478,15 +477,9 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     int32_t* flag = (int32_t*)(base + off[9]);
     h->ctr = (DevCounters*)(base + off[10]);
     char* scratch = base + off[11];
-    if (cudaMallocHost(&h->h_ctr, sizeof(DevCounters)) != cudaSuccess) {
-        cudaFree(base);
-        delete h;
-        cudaGetLastError();
-        return fail(RSI_ERR_OOM, "lbvh_build: cudaMallocHost failed");
-    }
     auto cleanup = [&](int code) {
-        cudaFree(base);
-        cudaFreeHost(h->h_ctr);
+        cudaStreamSynchronize(s);
+        pool_free(base, s);
         delete h;
         return code;
     };
@@ -549,27 +542,26 @@ extern "C" int lbvh_build_host(const float* h_vertices, int64_t n_vertices, cons
     float* dv = nullptr;
     int32_t* dt = nullptr;
     size_t bv = 12 * (size_t)n_vertices, bt = 12 * (size_t)n_triangles;
-    if (cudaMallocAsync(&dv, bv, s) != cudaSuccess || cudaMallocAsync(&dt, bt, s) != cudaSuccess) {
-        if (dv) cudaFreeAsync(dv, s);
-        cudaGetLastError();
-        return rsi::fail(RSI_ERR_OOM, "lbvh_build_host: staging allocation failed");
+    if (rsi::pool_alloc(reinterpret_cast<void**>(&dv), bv, s) != RSI_OK ||
+        rsi::pool_alloc(reinterpret_cast<void**>(&dt), bt, s) != RSI_OK) {
+        rsi::pool_free(dv, s);
+        return RSI_ERR_OOM;
     }
     int rc = RSI_OK;
     if (cudaMemcpyAsync(dv, h_vertices, bv, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(dt, h_triangles, bt, cudaMemcpyHostToDevice, s) != cudaSuccess)
         rc = rsi::cuda_fail(cudaGetLastError(), "lbvh_build_host copy");
     if (rc == RSI_OK) rc = lbvh_build(dv, n_vertices, dt, n_triangles, 4, morton_bits, stream, out);
-    cudaFreeAsync(dv, s);
-    cudaFreeAsync(dt, s);
+    rsi::pool_free(dv, s);
+    rsi::pool_free(dt, s);
     return rc;
 }
 
 extern "C" int lbvh_free(rsi_bvh_t h) {
     if (!h) return RSI_OK;
     cudaDeviceSynchronize();
-    cudaFree(h->nodes);   // base of the single allocation
-    if (h->band_ids) cudaFree(h->band_ids);
-    cudaFreeHost(h->h_ctr);
+    rsi::pool_free(h->nodes, 0);   // base of the single allocation
+    rsi::pool_free(h->band_ids, 0);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     delete h;

@@ -2,6 +2,8 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstdint>
+#include <mutex>
 #include <string>
 
 #include "rsi_internal.cuh"
@@ -25,6 +27,47 @@ int cuda_fail(cudaError_t e, const char* what) {
 static std::atomic<unsigned long long> g_launches{0};
 
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+static std::mutex g_ctx_mu;
+static DeviceCtx* g_ctx[kMaxCtxDevices] = {};
+
+DeviceCtx* device_ctx() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxCtxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_ctx_mu);
+    if (!g_ctx[dev]) {
+        auto* c = new DeviceCtx();
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return nullptr;
+        }
+        uint64_t keep = 4ull << 30;   // up to 4 GiB of freed blocks stay cached for later handles
+        cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_ctx[dev] = c;
+    }
+    return g_ctx[dev];
+}
+
+int pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    DeviceCtx* c = device_ctx();
+    if (!c) return fail(RSI_ERR_CUDA, "no CUDA device context");
+    if (cudaMallocFromPoolAsync(p, bytes, c->pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(RSI_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    return RSI_OK;
+}
+
+void pool_free(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
 
 int device_sm_count() {
     int dev = 0, n = 0;

@@ -31,6 +31,7 @@
 
 namespace rsi {
 
+// [traversal kernel: begin] (device code of the traversal passes)
 struct QueryArgs {
     const Node* nodes;
     const Tri* tris;
@@ -777,6 +778,8 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B) {
     }
 }
 
+// [traversal kernel: end]
+
 // In-tile reordering of segments for warp coherence: a counting sort of each
 // tile by the top 10 bits of the 30-bit Morton code of the segment midpoint
 // (normalised by the mesh extent).  perm[base .. base + m) becomes a
@@ -1053,16 +1056,13 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
 int ensure_band_capacity(rsi_bvh_t h, int64_t n, cudaStream_t s) {
     if (h->band_cap >= n) return RSI_OK;
     int64_t cap = std::max<int64_t>(n, 1 << 16);
-    if (h->band_ids) {
-        RSI_CUDA_TRY(cudaStreamSynchronize(s));
-        cudaFree(h->band_ids);
+    if (h->band_ids) {   // stream-ordered: after the queries that used it on s
+        pool_free(h->band_ids, s);
         h->band_ids = nullptr;
         h->band_cap = 0;
     }
-    if (cudaMalloc(&h->band_ids, 12 * (size_t)cap) != cudaSuccess) {   // band list | order | proposals
-        cudaGetLastError();
-        return fail(RSI_ERR_OOM, "rsi_query: band list allocation failed");
-    }
+    if (pool_alloc(reinterpret_cast<void**>(&h->band_ids), 12 * (size_t)cap, s) != RSI_OK)   // band | order | proposals
+        return RSI_ERR_OOM;
     h->band_cap = cap;
     return RSI_OK;
 }
@@ -1131,6 +1131,55 @@ extern "C" int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, in
     return RSI_OK;
 }
 
+// Host-buffer query: segments streamed in chunks through two device staging
+// slots of the device context.  Copies in run on its st_in, the traversal on
+// the caller's stream, copies out on its st_out; events chain them so that chunk k's traversal
+// overlaps chunk k+1's copy in and chunk k-1's copy out, and a slot is
+// reused only after its previous chunk has left it.
+namespace {
+constexpr int64_t kHostChunk = 1 << 21;
+
+int host_setup(rsi::DeviceCtx* c, int64_t chunk, int64_t n_chunks) {
+    if (!c->st_in) {
+        RSI_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_in, cudaStreamNonBlocking));
+        RSI_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_out, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming));
+            RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_q[i], cudaEventDisableTiming));
+            RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming));
+        }
+    }
+    if (c->stage_chunk < chunk) {
+        if (c->stage) {
+            RSI_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(c->stage);
+            c->stage = nullptr;
+            c->stage_chunk = 0;
+        }
+        if (cudaMalloc(&c->stage, 2 * 32 * (size_t)chunk) != cudaSuccess) {   // 2 slots x (24 + 1 + 4 + 1) B
+            cudaGetLastError();
+            return rsi::fail(RSI_ERR_OOM, "rsi_query_host: staging allocation failed");
+        }
+        c->stage_chunk = chunk;
+    }
+    if (c->h_chunk_cap < n_chunks) {
+        if (c->h_chunk_ctr) {
+            RSI_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFreeHost(c->h_chunk_ctr);
+            c->h_chunk_ctr = nullptr;
+        }
+        const int64_t cap = std::max<int64_t>(n_chunks, 64);
+        if (cudaMallocHost(&c->h_chunk_ctr, sizeof(rsi::DevCounters) * (size_t)cap) != cudaSuccess) {
+            cudaGetLastError();
+            c->h_chunk_cap = 0;
+            return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
+        }
+        c->h_chunk_cap = cap;
+    }
+    return RSI_OK;
+}
+}  // namespace
+
 extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n_rays, int mode,
                               const rsi_options* opt, uint8_t* h_hit, int32_t* h_count, uint8_t* h_ambiguous,
                               rsi_stats* stats, void* stream) {
@@ -1141,39 +1190,66 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
         if (stats) *stats = rsi_stats{};
         return RSI_OK;
     }
-    rc = rsi::ensure_band_capacity(h, n_rays, s);
+    const int64_t chunk = std::min<int64_t>(n_rays, kHostChunk);
+    const int64_t n_chunks = (n_rays + chunk - 1) / chunk;
+    rc = rsi::ensure_band_capacity(h, chunk, s);
     if (rc) return rc;
-    const size_t bf = 12 * (size_t)n_rays;
-    float *df = nullptr, *dt = nullptr;
-    uint8_t *dh = nullptr, *da = nullptr;
-    int32_t* dc = nullptr;
-    bool ok = cudaMallocAsync(&df, bf, s) == cudaSuccess && cudaMallocAsync(&dt, bf, s) == cudaSuccess;
-    if (ok && h_hit) ok = cudaMallocAsync(&dh, n_rays, s) == cudaSuccess;
-    if (ok && h_ambiguous) ok = cudaMallocAsync(&da, n_rays, s) == cudaSuccess;
-    if (ok && mode == RSI_COUNT) ok = cudaMallocAsync(&dc, 4 * (size_t)n_rays, s) == cudaSuccess;
-    if (ok) {
-        ok = cudaMemcpyAsync(df, h_from, bf, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-             cudaMemcpyAsync(dt, h_to, bf, cudaMemcpyHostToDevice, s) == cudaSuccess;
-        if (!ok) rc = rsi::cuda_fail(cudaGetLastError(), "rsi_query_host copy in");
-    } else {
-        cudaGetLastError();
-        rc = rsi::fail(RSI_ERR_OOM, "rsi_query_host: staging allocation failed");
-    }
-    if (rc == RSI_OK)
-        rc = rsi::query_device(h, df, dt, n_rays, mode, opt, dh, dc, da, h->band_ids, h->band_ids + h->band_cap,
-                               h->ctr, s);
-    if (rc == RSI_OK) {
-        bool c_ok = true;
-        if (h_hit) c_ok &= cudaMemcpyAsync(h_hit, dh, n_rays, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-        if (h_ambiguous) c_ok &= cudaMemcpyAsync(h_ambiguous, da, n_rays, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-        if (mode == RSI_COUNT) c_ok &= cudaMemcpyAsync(h_count, dc, 4 * (size_t)n_rays, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-        if (!c_ok) rc = rsi::cuda_fail(cudaGetLastError(), "rsi_query_host copy out");
-    }
-    for (void* p : {(void*)df, (void*)dt, (void*)dh, (void*)da, (void*)dc})
-        if (p) cudaFreeAsync(p, s);
+    rsi::DeviceCtx* c = rsi::device_ctx();
+    if (!c) return rsi::fail(RSI_ERR_CUDA, "rsi_query_host: no device context");
+    std::lock_guard<std::mutex> lock(c->host_mu);   // one host-buffer query per device at a time
+    rc = host_setup(c, chunk, n_chunks);
     if (rc) return rc;
-    rsi_stats tmp;
-    return rsi::read_stats(h, h->ctr, n_rays, stats ? stats : &tmp, s);
+    for (int64_t k = 0; k < n_chunks && rc == RSI_OK; ++k) {
+        const int b = (int)(k & 1);
+        const int64_t r0 = k * chunk, m = std::min(chunk, n_rays - r0);
+        char* slot = c->stage + (size_t)b * 32 * (size_t)chunk;
+        float* df = reinterpret_cast<float*>(slot);
+        float* dt = df + 3 * chunk;
+        int32_t* dc = reinterpret_cast<int32_t*>(dt + 3 * chunk);
+        uint8_t* dh = reinterpret_cast<uint8_t*>(dc + chunk);
+        uint8_t* da = dh + chunk;
+        cudaError_t e = cudaStreamWaitEvent(c->st_in, c->ev_q[b], 0);   // slot's inputs no longer read
+        if (e == cudaSuccess) e = cudaMemcpyAsync(df, h_from + 3 * r0, 12 * (size_t)m, cudaMemcpyHostToDevice, c->st_in);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dt, h_to + 3 * r0, 12 * (size_t)m, cudaMemcpyHostToDevice, c->st_in);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_in[b], c->st_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_in[b], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_out[b], 0);   // slot's outputs copied out
+        if (e != cudaSuccess) {
+            rc = rsi::cuda_fail(e, "rsi_query_host copy in");
+            break;
+        }
+        rc = rsi::query_device(h, df, dt, m, mode, opt, h_hit ? dh : nullptr, mode == RSI_COUNT ? dc : nullptr,
+                               h_ambiguous ? da : nullptr, h->band_ids, h->band_ids + h->band_cap, h->ctr, s);
+        if (rc) break;
+        e = cudaMemcpyAsync(c->h_chunk_ctr + k, h->ctr, sizeof(rsi::DevCounters), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_q[b], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st_out, c->ev_q[b], 0);
+        if (e == cudaSuccess && h_hit) e = cudaMemcpyAsync(h_hit + r0, dh, (size_t)m, cudaMemcpyDeviceToHost, c->st_out);
+        if (e == cudaSuccess && h_ambiguous)
+            e = cudaMemcpyAsync(h_ambiguous + r0, da, (size_t)m, cudaMemcpyDeviceToHost, c->st_out);
+        if (e == cudaSuccess && mode == RSI_COUNT)
+            e = cudaMemcpyAsync(h_count + r0, dc, 4 * (size_t)m, cudaMemcpyDeviceToHost, c->st_out);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[b], c->st_out);
+        if (e != cudaSuccess) rc = rsi::cuda_fail(e, "rsi_query_host copy out");
+    }
+    cudaError_t e1 = cudaStreamSynchronize(c->st_out);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (rc) return rc;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return rsi::cuda_fail(e1 != cudaSuccess ? e1 : e2, "rsi_query_host");
+    rsi_stats acc{};
+    acc.n_rays = n_rays;
+    acc.tree_height = h->height;
+    for (int64_t k = 0; k < n_chunks; ++k) {
+        const rsi::DevCounters& kc = c->h_chunk_ctr[k];
+        acc.node_visits += (int64_t)kc.node_visits;
+        acc.tri_tests += (int64_t)kc.tri_tests;
+        acc.band_rays += kc.band_count;
+        acc.ambiguous += (int64_t)kc.ambiguous;
+        if (kc.error && !acc.device_error) acc.device_error = kc.error;
+    }
+    if (stats) *stats = acc;
+    if (acc.device_error) return rsi::fail(acc.device_error, "rsi_query_host: device error " + std::to_string(acc.device_error));
+    return RSI_OK;
 }
 
 // ---------------------------------------------------------------- learned

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 
 #include "rsi.h"
@@ -68,7 +69,8 @@ struct rsi_bvh_s {
     float* box = nullptr;         // [6 (2 n_tri - 1)]
     // scratch
     rsi::DevCounters* ctr = nullptr;
-    rsi::DevCounters* h_ctr = nullptr;   // pinned mirror for read-back
+    rsi::DevCounters h_ctr_store{};                // host copy for read-back
+    rsi::DevCounters* h_ctr = &h_ctr_store;
     int32_t* band_ids = nullptr;         // [band_cap] rays queued for FP64
     int64_t band_cap = 0;
     int64_t device_bytes = 0;
@@ -96,6 +98,25 @@ inline int grid_for(int64_t n, int block) {
 }
 
 int device_sm_count();
+
+// Per-device library context: a private stream-ordered memory pool (freed
+// blocks stay cached, frees do not synchronize the device) and the staging
+// of host-buffer queries, shared by all handles of the device and serialized
+// by `host_mu`.
+constexpr int kMaxCtxDevices = 64;
+struct DeviceCtx {
+    cudaMemPool_t pool = nullptr;
+    std::mutex host_mu;
+    char* stage = nullptr;                 // two slots of host-query staging
+    int64_t stage_chunk = 0;
+    cudaStream_t st_in = nullptr, st_out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_q[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    DevCounters* h_chunk_ctr = nullptr;    // pinned counters of every chunk of a call
+    int64_t h_chunk_cap = 0;
+};
+DeviceCtx* device_ctx();   // the current device's context (NULL without a device)
+int pool_alloc(void** p, size_t bytes, cudaStream_t s);
+void pool_free(void* p, cudaStream_t s);
 
 // Count of kernel launches made by the library (rsi_kernel_launches).
 void note_launches(int n);
