@@ -46,7 +46,7 @@ def _load():
         i64 = ctypes.c_int64
         lib.oracle_classify_pair.argtypes = [P, P, P, P, P, P]
         lib.oracle_classify_pair.restype = ctypes.c_int
-        lib.oracle_query.argtypes = [P, i64, P, i64, P, P, i64, P, P, P, P, P, P, ctypes.c_int]
+        lib.oracle_query.argtypes = [P, i64, P, i64, P, P, i64, P, P, P, P, P, P, P, P, ctypes.c_int]
         lib.oracle_query.restype = ctypes.c_int
         lib.oracle_extent.argtypes = [P, i64, P, P]
         lib.oracle_extent.restype = ctypes.c_int
@@ -95,8 +95,9 @@ def classify_pair(s, e, a, b, c):
 
 def query(vertices, triangles, ray_from, ray_to, nthreads: int = 0):
     """Brute force over all pairs (Sec. 1).  Returns a dict of per-ray arrays:
-    hit, amb_hit (boolean mode), count, amb_count (intercept_count mode),
-    near_tri, near_t (nearest inclusive hit)."""
+    hit, amb_hit (boolean mode), count, amb_count (intercept_count mode, and
+    the flag of the barycentric mode), near_tri, near_t, near_point,
+    near_dist (barycentric mode: nearest inclusive hit, -1 / NaN if none)."""
     lib = _load()
     V, T = _f32(vertices).reshape(-1, 3), _i32(triangles).reshape(-1, 3)
     F, E = _f32(ray_from).reshape(-1, 3), _f32(ray_to).reshape(-1, 3)
@@ -104,11 +105,12 @@ def query(vertices, triangles, ray_from, ray_to, nthreads: int = 0):
     assert E.shape[0] == n
     res = dict(hit=np.zeros(n, np.uint8), amb_hit=np.zeros(n, np.uint8),
                count=np.zeros(n, np.int32), amb_count=np.zeros(n, np.uint8),
-               near_tri=np.zeros(n, np.int32), near_t=np.zeros(n, np.float32))
+               near_tri=np.zeros(n, np.int32), near_t=np.zeros(n, np.float32),
+               near_point=np.zeros((n, 3), np.float32), near_dist=np.zeros(n, np.float32))
     rc = lib.oracle_query(_ptr(V), V.shape[0], _ptr(T), T.shape[0], _ptr(F), _ptr(E), n,
                           _ptr(res["hit"]), _ptr(res["amb_hit"]), _ptr(res["count"]),
                           _ptr(res["amb_count"]), _ptr(res["near_tri"]), _ptr(res["near_t"]),
-                          int(nthreads))
+                          _ptr(res["near_point"]), _ptr(res["near_dist"]), int(nthreads))
     if rc != 0:
         raise ValueError("oracle_query: bad arguments (triangle index out of range?)")
     return res

@@ -14,8 +14,9 @@
  *                            decisive-hit / decisive-miss / ambiguous.
  *   - oracle_query         : brute force over all N_r x N_t pairs (Sec. 1:
  *                            the exhaustive search the BVH accelerates), in the
- *                            three result forms of Sec. 1 (boolean and
- *                            intercept_count; barycentric = nearest hit).
+ *                            three result forms of Sec. 1 (boolean,
+ *                            intercept_count, and barycentric = the nearest
+ *                            hit's triangle, t, point and distance).
  *   - oracle_extent / oracle_morton : surface extent and 30/63-bit Morton
  *                            codes of triangle centroids (Sec. 3.2, Sec. 3.3).
  *   - oracle_sort          : stable sort of (key, triangle id) (Sec. 3.2).
@@ -203,7 +204,7 @@ typedef struct {
     int64_t nT, r0, r1;
     uint8_t *hit, *amb_hit, *amb_count;
     int32_t *count, *near_tri;
-    float* near_t;
+    float *near_t, *near_point, *near_dist;
 } query_job;
 
 /* Per ray, over every triangle (the exhaustive search of Sec. 1):
@@ -213,8 +214,13 @@ typedef struct {
  *  intercept_count: ambiguous iff some pair is ambiguous; count = number of
  *                   decisive hits, or on an ambiguous ray the number of
  *                   distinct inclusive crossing points (t merged within 1e-9).
- *  nearest hit    : smallest t over inclusive hits and its triangle (for the
- *                   barycentric mode), -1 when none. */
+ *  nearest hit    : the barycentric mode (Sec. 1: the intersecting triangle,
+ *                   the distance to and the location of the nearest
+ *                   intersecting point).  Smallest t over the inclusive hits
+ *                   (equal t: the lower triangle index), its triangle, the
+ *                   point s + t (e - s) and the distance t |e - s| from the
+ *                   start point; -1 / NaN when none.  The ray is flagged
+ *                   exactly as in intercept_count (some ambiguous pair). */
 static void* query_worker(void* arg) {
     query_job* J = (query_job*)arg;
     double* ts = (double*)malloc(sizeof(double) * (size_t)(J->nT > 0 ? J->nT : 1));
@@ -253,6 +259,14 @@ static void* query_worker(void* arg) {
         if (J->amb_count) J->amb_count[r] = (uint8_t)amb_count;
         if (J->near_tri) J->near_tri[r] = best_j;
         if (J->near_t) J->near_t[r] = best_j >= 0 ? (float)best_t : -1.0f;
+        vec3 sv = v_load(s), dv = v_sub(v_load(e), sv);
+        if (J->near_point) {
+            vec3 pt = v_add(sv, v_scale(dv, best_t));
+            J->near_point[3 * r + 0] = best_j >= 0 ? (float)pt.x : NAN;
+            J->near_point[3 * r + 1] = best_j >= 0 ? (float)pt.y : NAN;
+            J->near_point[3 * r + 2] = best_j >= 0 ? (float)pt.z : NAN;
+        }
+        if (J->near_dist) J->near_dist[r] = best_j >= 0 ? (float)(best_t * v_norm(dv)) : -1.0f;
     }
     free(ts);
     return NULL;
@@ -267,7 +281,7 @@ int oracle_num_threads(void) {
 int oracle_query(const float* V, int64_t nV, const int32_t* T, int64_t nT,
                  const float* from, const float* to, int64_t nR,
                  uint8_t* hit, uint8_t* amb_hit, int32_t* count, uint8_t* amb_count,
-                 int32_t* near_tri, float* near_t, int nthreads) {
+                 int32_t* near_tri, float* near_t, float* near_point, float* near_dist, int nthreads) {
     if (nV < 0 || nT < 0 || nR < 0) return -1;
     for (int64_t j = 0; j < 3 * nT; ++j)
         if (T[j] < 0 || (int64_t)T[j] >= nV) return -1;
@@ -277,7 +291,7 @@ int oracle_query(const float* V, int64_t nV, const int32_t* T, int64_t nT,
     query_job* jobs = (query_job*)malloc(sizeof(query_job) * (size_t)nthreads);
     for (int k = 0; k < nthreads; ++k) {
         query_job j = {V, from, to, T, nT, nR * k / nthreads, nR * (k + 1) / nthreads,
-                       hit, amb_hit, amb_count, count, near_tri, near_t};
+                       hit, amb_hit, amb_count, count, near_tri, near_t, near_point, near_dist};
         jobs[k] = j;
         pthread_create(&th[k], NULL, query_worker, &jobs[k]);
     }

@@ -33,6 +33,8 @@ def test_case_study1_boolean_and_hit_points():
         p = s + float(r["near_t"][ray]) * (e - s)
         # the printed points carry 2 decimals; FP32 vertices round at ~1e-7
         np.testing.assert_allclose(p, point, atol=2e-6)
+        np.testing.assert_allclose(r["near_point"][ray], point, atol=2e-6)
+        assert abs(r["near_dist"][ray] - np.linalg.norm(np.asarray(point) - s)) < 2e-6
         assert r["count"][ray] == 1
 
 
@@ -280,3 +282,76 @@ def test_bad_index_rejected():
     V = np.zeros((3, 3), np.float32)
     with pytest.raises(ValueError):
         oracle.query(V, [[0, 1, 3]], [[0, 0, 0]], [[0, 0, 1]])
+
+
+# ------------------------------------------------------------ nearest hit (barycentric mode)
+def _plates(zs):
+    """One right triangle [0,1]^2 (lower half) per height z, listed in the given order."""
+    V, T = [], []
+    for z in zs:
+        k = len(V)
+        V += [[0, 0, z], [1, 0, z], [0, 1, z]]
+        T.append([k, k + 1, k + 2])
+    return np.array(V, np.float32), np.array(T, np.int32)
+
+
+def test_nearest_of_stacked_plates():
+    """Three parallel plates listed out of order: the nearest crossing of a
+    vertical segment is the first plate met from the start point, in both
+    directions (Sec. 1, barycentric mode: triangle, distance, point)."""
+    V, T = _plates([0.5, 0.0, 0.25])
+    F = np.array([[0.25, 0.25, -1.0], [0.25, 0.25, 1.0], [0.25, 0.25, 0.75]], np.float32)
+    E = np.array([[0.25, 0.25, 1.0], [0.25, 0.25, -1.0], [0.25, 0.25, 2.0]], np.float32)
+    r = oracle.query(V, T, F, E)
+    assert r["near_tri"].tolist() == [1, 0, -1]
+    assert r["near_t"][:2].tolist() == [0.5, 0.25] and r["near_t"][2] == -1
+    np.testing.assert_array_equal(r["near_point"][:2], [[0.25, 0.25, 0.0], [0.25, 0.25, 0.5]])
+    assert np.isnan(r["near_point"][2]).all()
+    assert r["near_dist"].tolist() == [1.0, 0.5, -1.0]
+    assert r["count"].tolist() == [3, 3, 0] and r["amb_count"].sum() == 0
+
+
+def test_nearest_equal_t_takes_lower_index():
+    V, T = _plates([0.0, 0.3, 0.0, 0.0])     # plates 0, 2 and 3 coincide
+    r = oracle.query(V, T, [[0.2, 0.2, -1.0]], [[0.2, 0.2, 1.0]])
+    assert r["near_tri"][0] == 0 and r["near_t"][0] == 0.5
+
+
+def test_nearest_on_heightfield_closed_form():
+    """Vertical segments through a piecewise-linear surface cross it once:
+    the crossing is the plane of the triangle whose footprint holds (x, y),
+    found here by solving 2x2 systems (a different formula from Moller's)."""
+    rng = np.random.default_rng(5)
+    n = 6
+    xs = np.linspace(0.0, 1.0, n)
+    gx, gy = np.meshgrid(xs, xs, indexing="xy")
+    gz = rng.uniform(-0.2, 0.2, gx.shape)
+    V = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1).astype(np.float32)
+    T = []
+    for j in range(n - 1):
+        for i in range(n - 1):
+            a, b, c, d = j * n + i, j * n + i + 1, (j + 1) * n + i + 1, (j + 1) * n + i
+            T += [(a, b, c), (a, c, d)]
+    T = np.array(T, np.int32)
+    P = rng.uniform(0.01, 0.99, (300, 2))
+    F = np.c_[P, np.full(300, -1.0)].astype(np.float32)
+    E = np.c_[P, np.full(300, 1.0)].astype(np.float32)
+    r = oracle.query(V, T, F, E)
+    V64 = V.astype(np.float64)
+    for k in range(300):
+        x, y = float(F[k, 0]), float(F[k, 1])
+        want = None
+        for j, tri in enumerate(T):
+            a, b, c = V64[tri]
+            lam = np.linalg.solve(np.array([[b[0] - a[0], c[0] - a[0]], [b[1] - a[1], c[1] - a[1]]]),
+                                  np.array([x - a[0], y - a[1]]))
+            if lam.min() > 1e-6 and lam.sum() < 1 - 1e-6:   # strictly inside the footprint
+                z = a[2] + lam[0] * (b[2] - a[2]) + lam[1] * (c[2] - a[2])
+                want = (j, z)
+        if want is None:
+            continue    # on a footprint edge: ambiguous by construction
+        j, z = want
+        assert r["near_tri"][k] == j and r["amb_count"][k] == 0
+        assert abs(r["near_t"][k] - (z + 1.0) / 2.0) < 1e-6
+        np.testing.assert_allclose(r["near_point"][k], [x, y, z], atol=1e-6)
+        assert abs(r["near_dist"][k] - (z + 1.0)) < 1e-6
