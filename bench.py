@@ -246,6 +246,56 @@ def measure_batched(rsi, torch, dev, c4, args):
     return out
 
 
+def measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args):
+    """Barycentric mode on the same 1e7 segments: the device query
+    (rsi_query_nearest: nearest triangle, t, point, distance) and, in the
+    paper's end-to-end style (Sec. 3.3), host segments -> build -> nearest
+    query -> compacted (rays, distances, triangles, points) -> host."""
+    stream = torch.cuda.current_stream()
+    n = dF.shape[0]
+    steps = max(3, min(args.steps, 10))
+    bvh = rsi.LBVH(dV, dT)
+    for _ in range(args.warmup):
+        bvh.nearest(dF, dE)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    trav, fin = [], []
+    e0.record(stream)
+    for _ in range(steps):
+        r = bvh.nearest(dF, dE, time_kernels=True)
+        a, b = bvh.last_query_ms()
+        trav.append(a)
+        fin.append(b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = bvh.nearest(dF, dE, stats=True)["stats"]
+    hits = int((r["tri"] >= 0).sum())
+    bvh.close()
+
+    def paper_style():
+        b = rsi.LBVH(pV.to(dev, non_blocking=True), pT.to(dev, non_blocking=True))
+        rays, dist, tri, point = b.barycentric(pF.to(dev, non_blocking=True), pE.to(dev, non_blocking=True))
+        out = (rays.cpu(), dist.cpu(), tri.cpu(), point.cpu())
+        b.close()
+        return out
+
+    for _ in range(args.warmup):
+        paper_style()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        out = paper_style()
+    e2e = 1e3 * (time.perf_counter() - t0) / steps
+    assert out[0].shape[0] == hits
+    return {"rays": n, "steps": steps, "ms": ms, "rays_per_s": n / (ms / 1e3),
+            "traverse_ms": statistics.median(trav), "fp64_and_finish_ms": statistics.median(fin),
+            "hitting_rays": hits, "band_rays": st["band_rays"], "ambiguous": st["ambiguous"],
+            "paper_style_e2e_ms": e2e,
+            "paper_style_e2e": "pinned host segments and mesh -> build -> nearest -> compaction -> host "
+                               "(rays, distances, triangles, points)"}
+
+
 MLP_FLOP_PER_SEGMENT = 2 * (6 * 128 + 128 * 128 + 128 * 256)   # algorithmic (unpadded) multiply-adds x 2
 
 
@@ -326,6 +376,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-nearest", action="store_true")
     ap.add_argument("--learned-rays", type=int, default=100_000_000)
     ap.add_argument("--train-rays", type=int, default=10_000_000)
     args = ap.parse_args()
@@ -481,6 +532,8 @@ def main():
                      "ambiguous_count": st_c["ambiguous"], "node_visits_per_ray_any": st_a["node_visits"] / n,
                      "band_rays_any": st_a["band_rays"], "ambiguous_any": st_a["ambiguous"]},
     }
+    if not args.no_nearest:
+        line["barycentric_c2"] = measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args)
     if c4 is not None:
         line["batched_c4"] = measure_batched(rsi, torch, dev, c4, args)
     if c5 is not None:

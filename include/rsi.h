@@ -56,6 +56,7 @@ extern "C" {
 /* Query modes (Sec. 1). */
 #define RSI_ANY_HIT 0 /* "boolean": does the segment meet the surface       */
 #define RSI_COUNT 1   /* "intercept_count": number of distinct crossings    */
+#define RSI_NEAREST 2 /* "barycentric": nearest crossing (rsi_query_nearest) */
 
 typedef struct rsi_bvh_s* rsi_bvh_t;
 typedef struct rsi_mlp_s* rsi_mlp_t;
@@ -172,6 +173,47 @@ size_t lbvh_node_bytes(void);
 int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
               const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
               rsi_stats* stats, void* stream);
+
+/*
+ * Barycentric mode (Sec. 1: for each intersecting ray, the intersecting
+ * triangle and the distance to and location of the nearest intersecting
+ * point; Sec. 3.3 moves the distance and point computations onto the GPU).
+ * Per segment i, over the inclusive (closed-interval) crossings:
+ *   d_tri[i]   int32, required: index (into the caller's triangle array) of
+ *              the triangle of the smallest t (equal t: the lower index), or
+ *              -1 when the segment meets no triangle;
+ *   d_t[i]     float, optional: that t in [0, 1] (fraction of to - from),
+ *              evaluated by the Moller-Trumbore definition in FP64 and
+ *              rounded once; -1 when there is no hit;
+ *   d_point    float [n_rays][3], optional: from + t (to - from), FP64 then
+ *              rounded; NaN when there is no hit;
+ *   d_dist[i]  float, optional: t |to - from|, the distance from the start
+ *              point; -1 when there is no hit;
+ *   d_ambiguous[i] uint8, optional: 1 where some pair lies in the 1e-6
+ *              margin band in FP64 (as in RSI_COUNT); the result there is
+ *              the closed-interval reading.
+ * The search visits every pair like RSI_COUNT; segments whose nearest pair
+ * is not certain in FP32 are settled in FP64.  Device buffers; n_rays == 0
+ * is a no-op; asynchronous unless `stats` is given.  Errors as rsi_query.
+ */
+int rsi_query_nearest(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays,
+                      const rsi_options* opt, int32_t* d_tri, float* d_t, float* d_point, float* d_dist,
+                      uint8_t* d_ambiguous, rsi_stats* stats, void* stream);
+
+/*
+ * The paper's barycentric result form (Sec. 2.3: intersecting rays,
+ * distances, hit triangles, hit points): the segments with d_tri[i] >= 0,
+ * in increasing index order, gathered from rsi_query_nearest's outputs.
+ *   d_rays [n]: segment indices; d_tri_out [n]: triangle indices;
+ *   d_dist_out [n] from d_dist; d_point_out [n][3] from d_point.
+ * Every output is optional (NULL skips it) and must hold n_rays entries (the
+ * most there can be).  *n_hits (host) receives n.  Device buffers; returns
+ * after `stream` has finished the compaction.  RSI_ERR_INVALID_ARG when an
+ * output is asked for without its input, or n_rays is outside [0, 2^31).
+ */
+int rsi_nearest_compact(const int32_t* d_tri, const float* d_dist, const float* d_point, int64_t n_rays,
+                        int32_t* d_rays, int32_t* d_tri_out, float* d_dist_out, float* d_point_out,
+                        int64_t* n_hits, void* stream);
 
 /*
  * As rsi_query with segments and results in HOST memory.  The segments are
@@ -360,7 +402,9 @@ int rsi_query_learned(rsi_bvh_t h, rsi_mlp_t m, const float* d_from, const float
 
 /* Durations of the FP32 traversal kernel and of the FP64 re-test kernel of
  * the last query on `h` that ran with time_kernels = 1, from CUDA events
- * recorded on that query's stream (waits for them).  -1 if none. */
+ * recorded on that query's stream (waits for them); in the nearest mode the
+ * second figure includes the pass that writes t, points and distances.
+ * -1 if none. */
 int rsi_last_query_ms(rsi_bvh_t h, float* traverse_ms, float* retest_ms);
 
 /* Number of kernels this library has launched since it was loaded (all

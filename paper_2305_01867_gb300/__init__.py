@@ -20,7 +20,7 @@ from .build import LIB as _LIB_PATH
 from .build import build as build_library
 
 RSI_OK = 0
-RSI_ANY_HIT, RSI_COUNT = 0, 1
+RSI_ANY_HIT, RSI_COUNT, RSI_NEAREST = 0, 1, 2
 NOALLOC_MAX_RAYS = 1 << 21   # RSI_NOALLOC_MAX_RAYS of include/rsi.h
 LEAF_TAG = 0x80000000
 ERRORS = {-1: "INVALID_ARG", -2: "DTYPE", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "STACK", -7: "NAN",
@@ -90,6 +90,10 @@ def _load():
     for f in (lib.rsi_query, lib.rsi_query_host):
         f.argtypes = [P, P, P, i64, i32, ctypes.POINTER(Options), P, P, P, ctypes.POINTER(Stats), P]
     lib.rsi_query_noalloc.argtypes = [P, P, P, i64, i32, ctypes.POINTER(Options), P, P, P, P]
+    lib.rsi_query_nearest.argtypes = [P, P, P, i64, ctypes.POINTER(Options), P, P, P, P, P, ctypes.POINTER(Stats), P]
+    lib.rsi_query_nearest.restype = ctypes.c_int
+    lib.rsi_nearest_compact.argtypes = [P, P, P, i64, P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]
+    lib.rsi_nearest_compact.restype = ctypes.c_int
     lib.rsi_query_noalloc.restype = ctypes.c_int
     lib.rsi_last_query_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     lib.rsi_last_query_ms.restype = ctypes.c_int
@@ -312,6 +316,62 @@ class LBVH:
         if stats:
             out["stats"] = st.as_dict()
         return out
+
+
+    def nearest(self, ray_from, ray_to, *, fp32_only=False, block=0, blocks_per_sm=0, stats=False,
+                want_t=True, want_point=True, want_dist=True, want_ambiguous=True, time_kernels=False,
+                ray_sort_tile=0, stream=None):
+        """Barycentric mode per segment (rsi_query_nearest): 'tri' (int32, -1
+        when no hit), 't', 'point' [n, 3], 'dist' (float32), 'ambiguous'."""
+        import torch
+        _check_f32x3(ray_from, "ray_from")
+        _check_f32x3(ray_to, "ray_to")
+        if ray_from.shape != ray_to.shape:
+            raise ValueError("ray_from and ray_to differ in shape")
+        if not (ray_from.is_cuda and ray_to.is_cuda):
+            raise TypeError("nearest() takes device tensors")
+        n = ray_from.shape[0]
+        dev = ray_from.device
+        tri = torch.empty(n, dtype=torch.int32, device=dev)
+        t = torch.empty(n, dtype=torch.float32, device=dev) if want_t else None
+        point = torch.empty(n, 3, dtype=torch.float32, device=dev) if want_point else None
+        dist = torch.empty(n, dtype=torch.float32, device=dev) if want_dist else None
+        amb = torch.empty(n, dtype=torch.uint8, device=dev) if want_ambiguous else None
+        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels),
+                      int(ray_sort_tile))
+        st = Stats()
+        check(lib.rsi_query_nearest(self._h, _ptr(ray_from), _ptr(ray_to), n, ctypes.byref(opt), _ptr(tri), _ptr(t),
+                                    _ptr(point), _ptr(dist), _ptr(amb), ctypes.byref(st) if stats else None,
+                                    _stream(stream)))
+        out = {"tri": tri, "t": t, "point": point, "dist": dist, "ambiguous": amb}
+        if stats:
+            out["stats"] = st.as_dict()
+        return out
+
+    def barycentric(self, ray_from, ray_to, stream=None):
+        """The paper's barycentric result (Sec. 2.3): (intersecting_rays,
+        distances, hit_triangles, hit_points) for the segments that meet the
+        surface, in increasing segment order."""
+        r = self.nearest(ray_from, ray_to, want_t=False, want_ambiguous=False, stream=stream)
+        return compact_hits(r["tri"], r["dist"], r["point"], stream=stream)
+
+
+def compact_hits(tri, dist, point, stream=None):
+    """rsi_nearest_compact: (segment indices, distances, triangles, points)
+    of the entries with tri >= 0, in index order."""
+    import torch
+    n = tri.shape[0]
+    dev = tri.device
+    rays = torch.empty(n, dtype=torch.int32, device=dev)
+    tri_o = torch.empty(n, dtype=torch.int32, device=dev)
+    dist_o = torch.empty(n, dtype=torch.float32, device=dev) if dist is not None else None
+    point_o = torch.empty(n, 3, dtype=torch.float32, device=dev) if point is not None else None
+    k = ctypes.c_int64()
+    check(lib.rsi_nearest_compact(_ptr(tri), _ptr(dist), _ptr(point), n, _ptr(rays), _ptr(tri_o), _ptr(dist_o),
+                                  _ptr(point_o), ctypes.byref(k), _stream(stream)))
+    k = k.value
+    return (rays[:k], dist_o[:k] if dist_o is not None else None, tri_o[:k],
+            point_o[:k] if point_o is not None else None)
 
 
 class BatchPlan:

@@ -42,6 +42,7 @@ struct QueryArgs {
     uint8_t* hit;
     int32_t* count;
     uint8_t* amb;
+    int32_t* near;         // nearest mode: leaf of the nearest hit, -1 none (ids after k_nearest_finish)
     int32_t* band_ids;
     const int32_t* perm;   // traversal order of the segments, or NULL
     const int* n_dev;      // number of segments read from device memory, or NULL
@@ -138,7 +139,12 @@ __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a
 // where M_x is the same expression in absolute values; kErrK doubles that.
 // Decisions are taken on the numerators against the denominator so the
 // bounds stay linear:  u > tau  <=>  sign(det) U > tau |det|,  etc.
-__device__ __forceinline__ int tri_fp32(const SegF& g, const Tri& tr, bool want_plain, bool& plain_hit) {
+//
+// For a certain hit, `tlo`/`thi` (when given) receive bounds of the exact t
+// (numerator and denominator bounds divided with directed rounding), and
+// `tplain` the plain FP32 t of a plain hit.
+__device__ __forceinline__ int tri_fp32(const SegF& g, const Tri& tr, bool want_plain, bool& plain_hit,
+                                        float* tlo = nullptr, float* thi = nullptr, float* tplain = nullptr) {
     float3 a = f3(tr.v0);
     float3 e1 = sub3(f3(tr.v1), a), e2 = sub3(f3(tr.v2), a);
     float3 sv = sub3(g.s, a);
@@ -159,6 +165,7 @@ __device__ __forceinline__ int tri_fp32(const SegF& g, const Tri& tr, bool want_
     if (want_plain && det != 0.0f) {   // the uncorrected FP32 decision (fp32_only)
         float u = U / det, v = V / det, t = T / det;
         plain_hit = u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t >= 0.0f && t <= 1.0f;
+        if (tplain) *tplain = t;
     }
     // both end points strictly on one side of the plane, farther than
     // tau |d| |n| (|n| <= |e1||e2|): a decisive miss on either branch
@@ -173,8 +180,13 @@ __device__ __forceinline__ int tri_fp32(const SegF& g, const Tri& tr, bool want_
         float errW = errdet + errU + errV + 2.0f * kU * (D + fabsf(U) + fabsf(V));
         float Tms = D - Ts;
         float lim = kTauHi * (D + errdet) * 1.000001f;
-        if (Us - errU > lim && Vs - errV > lim && Ws - errW > lim && Ts - errT > lim && Tms - errTm > lim)
+        if (Us - errU > lim && Vs - errV > lim && Ws - errW > lim && Ts - errT > lim && Tms - errTm > lim) {
+            if (tlo) {   // 0 < Ts - errT <= Ts_exact, 0 < D - errdet <= D_exact
+                *tlo = __fdiv_rd(__fsub_rd(Ts, errT), __fadd_ru(D, errdet));
+                *thi = __fdiv_ru(__fadd_ru(Ts, errT), __fsub_rd(D, errdet));
+            }
             return kHit;
+        }
         if (Us + errU < -lim || Vs + errV < -lim || Ws + errW < -lim || Ts + errT < -lim || Tms + errTm < -lim)
             return kMiss;
     }
@@ -374,7 +386,10 @@ constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^
 // triangle work both run with most lanes active.  Lanes whose segment is done
 // are refilled together from a per-warp chunk of segment indices (one atomic
 // per chunk).  A segment with a band pair and no certain answer is queued for
-// k_query_fp64 (count mode stops at the first band pair).
+// k_query_fp64 (count and nearest modes stop at the first band pair).  The
+// nearest mode visits every pair like the count mode and keeps the certain
+// hit with the smallest upper bound on t; the answer is certain when every
+// other certain hit's lower bound lies above it, else the segment is queued.
 template <int MODE, bool STATS, int STACK, bool BATCHED>
 __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A, BatchArgs B) {
     const unsigned kFull = 0xffffffffu;
@@ -394,6 +409,10 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
     int stack[STACK];
     int cnt = 0, plain_cnt = 0;
     bool found = false, band = false, stop = false;
+    // nearest mode: best certain hit (leaf n1, t in [lo1, hi1]), smallest lower
+    // bound m2 of the other certain hits, and the plain FP32 nearest (fp32_only)
+    int n1 = -1, pbest = -1;
+    float lo1 = 0.0f, hi1 = 0.0f, m2 = 0.0f, pbt = 0.0f;
     while (true) {
         unsigned idle = __ballot_sync(kFull, ray < 0);
         if (!exhausted && (__popc(idle) >= kRefillMin || idle == kFull)) {
@@ -457,6 +476,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
                         uint8_t* amb = BATCHED ? B.desc[l_batch].amb : A.amb;
                         if (hit) hit[r] = 0;
                         if (MODE == RSI_COUNT) count[r] = 0;
+                        if (MODE == RSI_NEAREST) A.near[r] = -1;
                         if (amb) amb[r] = 1;
                         ray = -1;
                     } else {
@@ -466,6 +486,10 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
                         sp = 0;
                         cnt = plain_cnt = 0;
                         found = band = stop = false;
+                        if (MODE == RSI_NEAREST) {
+                            n1 = pbest = -1;
+                            lo1 = hi1 = m2 = pbt = __int_as_float(0x7f800000);
+                        }
                     }
                 }
                 idle = __ballot_sync(kFull, ray < 0);
@@ -514,16 +538,33 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
                 if (STATS) ++tests;
                 const Tri tr = load_tri(BATCHED ? l_tris : A.tris, slot);
                 bool plain;
-                int c = tri_fp32(g, tr, A.fp32_only != 0, plain);
+                float tlo, thi, tpl;
+                const bool near = MODE == RSI_NEAREST;
+                int c = tri_fp32(g, tr, A.fp32_only != 0, plain, near ? &tlo : nullptr, near ? &thi : nullptr,
+                                 near ? &tpl : nullptr);
                 plain_cnt += plain;
+                if (near && plain && tpl < pbt) {
+                    pbt = tpl;
+                    pbest = slot;
+                }
                 if (c == kBand && !A.fp32_only) {   // settled by the FP64 pass
                     band = true;
-                    if (MODE == RSI_COUNT) stop = true;
+                    if (MODE != RSI_ANY_HIT) stop = true;
                 } else if (c == kHit) {
                     ++cnt;
                     if (MODE == RSI_ANY_HIT) {
                         found = true;
                         stop = true;
+                    }
+                    if (near) {
+                        if (thi < hi1) {
+                            m2 = fminf(m2, lo1);
+                            n1 = slot;
+                            lo1 = tlo;
+                            hi1 = thi;
+                        } else {
+                            m2 = fminf(m2, tlo);
+                        }
                     }
                 }
                 slot = -1;
@@ -536,22 +577,26 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
             uint8_t* amb = BATCHED ? B.desc[l_batch].amb : A.amb;
             if (A.fp32_only) {   // plain FP32 closed-interval decisions, no re-test
                 if (MODE == RSI_ANY_HIT) hit[r] = (uint8_t)(found || plain_cnt > 0);
-                else {
+                else if (MODE == RSI_COUNT) {
                     count[r] = plain_cnt;
                     if (hit) hit[r] = (uint8_t)(plain_cnt > 0);
+                } else {
+                    A.near[r] = pbest;
                 }
                 if (amb) amb[r] = 0;
             } else if (MODE == RSI_ANY_HIT && found) {
                 hit[r] = 1;
                 if (amb) amb[r] = 0;
-            } else if (band) {
+            } else if (band || (MODE == RSI_NEAREST && n1 >= 0 && !(m2 > hi1))) {
                 int pos = atomicAdd(&A.ctr->band_count, 1);
                 A.band_ids[pos] = BATCHED ? ray + __ldg(B.begins + l_batch) : ray;
             } else {
                 if (MODE == RSI_ANY_HIT) hit[r] = 0;
-                else {
+                else if (MODE == RSI_COUNT) {
                     count[r] = cnt;
                     if (hit) hit[r] = (uint8_t)(cnt > 0);
+                } else {
+                    A.near[r] = n1;
                 }
                 if (amb) amb[r] = 0;
             }
@@ -632,7 +677,8 @@ __device__ __forceinline__ double t_of_definition(D3 s, D3 e, D3 a, D3 b, D3 c) 
 // decision from the numerators where possible, the definition itself
 // otherwise -- and the warp combines the classes.  A decisive hit ends a
 // boolean query; otherwise the closed-interval answer of an ambiguous
-// segment counts distinct crossings (t merged within 1e-9).
+// segment counts distinct crossings (t merged within 1e-9).  The nearest
+// mode keeps the inclusive hit of smallest (t, triangle id).
 template <int MODE, int STACK, bool BATCHED>
 __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B) {
     constexpr int kWarps = 4;
@@ -667,6 +713,8 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B) {
         const D3 sd = {(double)s.x, (double)s.y, (double)s.z}, ed = {(double)e.x, (double)e.y, (double)e.z};
         int n_hit = 0, n_amb = 0, n_incl = 0;
         bool overflow = false;
+        double best_t = __longlong_as_double(0x7ff0000000000000ll);   // nearest mode (lane 0)
+        int best_id = 0x7FFFFFFF, best_leaf = -1;
         int node = 0, sp = 0;
         int stack[STACK];
         bool trav_done = false;
@@ -713,11 +761,12 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B) {
             nc = __shfl_sync(kFull, nc, 0);
             trav_done = __shfl_sync(kFull, trav_done ? 1 : 0, 0) != 0;
             __syncwarp();
-            int cls = -1;
+            int cls = -1, my_id = 0x7FFFFFFF;
             bool incl = false;
             double t = 0.0;
             if (lane < nc) {
                 const Tri tr = load_tri(Q.tris, s_cand[w][lane]);
+                my_id = __float_as_int(tr.v0.w);
                 const D3 a = d3of(tr.v0), b = d3of(tr.v1), c = d3of(tr.v2);
                 cls = tri_certain64(sd, ed, a, b, c);
                 if (cls == kHit) {
@@ -730,10 +779,30 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B) {
             const unsigned mh = __ballot_sync(kFull, cls == kHit);
             const unsigned ma = __ballot_sync(kFull, cls == kBand);
             const unsigned mi = __ballot_sync(kFull, incl);
-            if (incl) {
+            if (MODE == RSI_COUNT && incl) {
                 const int pos = n_incl + __popc(mi & lt);
                 if (pos < kMaxInclusive) s_t[w][pos] = t;
                 else overflow = true;
+            }
+            if (MODE == RSI_NEAREST && mi) {   // warp minimum of (t, id) over the inclusive hits
+                double bt = incl ? t : __longlong_as_double(0x7ff0000000000000ll);
+                int bid = incl ? my_id : 0x7FFFFFFF;
+                int bl = incl ? s_cand[w][lane] : -1;
+                for (int off = 16; off; off >>= 1) {
+                    const double ot = __shfl_xor_sync(kFull, bt, off);
+                    const int oid = __shfl_xor_sync(kFull, bid, off);
+                    const int ol = __shfl_xor_sync(kFull, bl, off);
+                    if (ot < bt || (ot == bt && oid < bid)) {
+                        bt = ot;
+                        bid = oid;
+                        bl = ol;
+                    }
+                }
+                if (bt < best_t || (bt == best_t && bid < best_id)) {
+                    best_t = bt;
+                    best_id = bid;
+                    best_leaf = bl;
+                }
             }
             n_hit += __popc(mh);
             n_amb += __popc(ma);
@@ -750,6 +819,10 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B) {
                 Q.hit[r] = (uint8_t)(n_hit > 0 || (amb && n_incl > 0));
                 if (Q.amb) Q.amb[r] = (uint8_t)amb;
                 if (amb) atomicAdd(&A.ctr->ambiguous, 1ull);
+            } else if (MODE == RSI_NEAREST) {
+                Q.near[r] = best_leaf;
+                if (Q.amb) Q.amb[r] = (uint8_t)(n_amb > 0);
+                if (n_amb > 0) atomicAdd(&A.ctr->ambiguous, 1ull);
             } else {
                 const bool amb = n_amb > 0;
                 int count = n_hit;
@@ -779,6 +852,129 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B) {
 }
 
 // [traversal kernel: end]
+
+// Barycentric-mode results (Sec. 1: the intersecting triangle, the distance
+// to and the location of the nearest intersecting point) from the leaf the
+// passes chose: t by the definition's own FP64 operations, the point
+// s + t (e - s) and the distance t |e - s| from the start point, each rounded
+// once to FP32; the leaf is replaced by the caller's triangle index.  No hit:
+// triangle -1, t -1, distance -1, point NaN.
+__global__ void __launch_bounds__(256) k_nearest_finish(QueryArgs A, float* __restrict__ t_out,
+                                                        float* __restrict__ point, float* __restrict__ dist) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n_rays;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int j = A.near[r];
+        const float qnan = __int_as_float(0x7fc00000);
+        float tf = -1.0f, df = -1.0f, px = qnan, py = qnan, pz = qnan;
+        if (j >= A.n_tri) {   // no pass wrote this segment: reported, never dereferenced
+            raise_error(A.ctr, RSI_ERR_INDEX);
+            A.near[r] = j = -1;
+        }
+        if (j >= 0) {
+            const Tri tr = load_tri(A.tris, j);
+            const D3 sd = {(double)A.from[3 * r], (double)A.from[3 * r + 1], (double)A.from[3 * r + 2]};
+            const D3 ed = {(double)A.to[3 * r], (double)A.to[3 * r + 1], (double)A.to[3 * r + 2]};
+            const double t = t_of_definition(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2));
+            const D3 d = dsub(ed, sd);
+            const D3 p = dadd(sd, dscale(d, t));
+            tf = __double2float_rn(t);
+            px = __double2float_rn(p.x);
+            py = __double2float_rn(p.y);
+            pz = __double2float_rn(p.z);
+            df = __double2float_rn(__dmul_rn(t, dnorm(d)));
+            A.near[r] = __float_as_int(tr.v0.w);
+        }
+        if (t_out) t_out[r] = tf;
+        if (dist) dist[r] = df;
+        if (point) {
+            point[3 * r] = px;
+            point[3 * r + 1] = py;
+            point[3 * r + 2] = pz;
+        }
+    }
+}
+
+// Stream compaction of the hitting segments in index order (the paper's
+// barycentric result lists only the intersecting rays): per-tile counts, one
+// exclusive scan, and an ordered scatter.  Each thread owns 16 consecutive
+// segments of a 4096-segment tile.
+constexpr int kCompactPer = 16;
+constexpr int kCompactTile = 256 * kCompactPer;
+
+__device__ __forceinline__ int block_exclusive_scan256(int v, int* wsum, int& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int pre = 0;
+    total = 0;
+    for (int k = 0; k < 8; ++k) {
+        if (k < w) pre += wsum[k];
+        total += wsum[k];
+    }
+    __syncthreads();
+    return pre + inc - v;
+}
+
+__global__ void __launch_bounds__(256) k_compact_count(const int32_t* __restrict__ tri, int64_t n,
+                                                       int* __restrict__ tile_count) {
+    __shared__ int wsum[8];
+    const int64_t b0 = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPer;
+    int c = 0;
+    for (int k = 0; k < kCompactPer; ++k)
+        if (b0 + k < n && tri[b0 + k] >= 0) ++c;
+    int total;
+    block_exclusive_scan256(c, wsum, total);
+    if (threadIdx.x == 0) tile_count[blockIdx.x] = total;
+}
+
+// One block: tile counts -> exclusive offsets (in place), total in *n_out.
+__global__ void __launch_bounds__(256) k_compact_scan(int* __restrict__ tile_count, int n_tiles,
+                                                      long long* __restrict__ n_out) {
+    __shared__ int wsum[8];
+    int carry = 0;
+    for (int base = 0; base < n_tiles; base += 256) {
+        const int i = base + threadIdx.x;
+        const int v = i < n_tiles ? tile_count[i] : 0;
+        int total;
+        const int ex = block_exclusive_scan256(v, wsum, total);
+        if (i < n_tiles) tile_count[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) *n_out = carry;
+}
+
+__global__ void __launch_bounds__(256) k_compact_scatter(const int32_t* __restrict__ tri, const float* __restrict__ dist,
+                                                         const float* __restrict__ point, int64_t n,
+                                                         const int* __restrict__ tile_off, int32_t* __restrict__ rays,
+                                                         int32_t* __restrict__ tri_out, float* __restrict__ dist_out,
+                                                         float* __restrict__ point_out) {
+    __shared__ int wsum[8];
+    const int64_t b0 = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPer;
+    int c = 0;
+    for (int k = 0; k < kCompactPer; ++k)
+        if (b0 + k < n && tri[b0 + k] >= 0) ++c;
+    int total;
+    int pos = tile_off[blockIdx.x] + block_exclusive_scan256(c, wsum, total);
+    for (int k = 0; k < kCompactPer; ++k) {
+        const int64_t r = b0 + k;
+        if (r < n && tri[r] >= 0) {
+            if (rays) rays[pos] = (int32_t)r;
+            if (tri_out) tri_out[pos] = tri[r];
+            if (dist_out) dist_out[pos] = dist[r];
+            if (point_out) {
+                point_out[3 * (int64_t)pos] = point[3 * r];
+                point_out[3 * (int64_t)pos + 1] = point[3 * r + 1];
+                point_out[3 * (int64_t)pos + 2] = point[3 * r + 2];
+            }
+            ++pos;
+        }
+    }
+}
 
 // In-tile reordering of segments for warp coherence: a counting sort of each
 // tile by the top 10 bits of the 30-bit Morton code of the segment midpoint
@@ -979,9 +1175,17 @@ void launch_fp64(const QueryArgs& A, int height, int grid, cudaStream_t s, const
 }  // namespace
 
 // Launch the two passes for one batch of segments already on the device.
+struct NearestOut {
+    int32_t* tri;
+    float* t;
+    float* point;
+    float* dist;
+};
+
 int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n, int mode, const rsi_options* opt,
                  uint8_t* d_hit, int32_t* d_count, uint8_t* d_amb, int32_t* band_ids, int32_t* perm_scratch,
-                 DevCounters* ctr, cudaStream_t s, const int32_t* order = nullptr, const int* n_dev = nullptr) {
+                 DevCounters* ctr, cudaStream_t s, const int32_t* order = nullptr, const int* n_dev = nullptr,
+                 const NearestOut* nearest = nullptr) {
     rsi_options o = {};
     if (opt) o = *opt;
     if (h->height >= 127) return fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
@@ -995,6 +1199,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     A.hit = d_hit;
     A.count = d_count;
     A.amb = d_amb;
+    A.near = nearest ? nearest->tri : nullptr;
     A.band_ids = band_ids;
     A.perm = nullptr;
     A.n_dev = nullptr;
@@ -1037,14 +1242,23 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (mode == RSI_ANY_HIT) {
         if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, grid, block, s);
         else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, grid, block, s);
-    } else {
+    } else if (mode == RSI_COUNT) {
         if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, grid, block, s);
         else launch_fp32_stack<RSI_COUNT, false>(A, h->height, grid, block, s);
+    } else {
+        if (o.collect_stats) launch_fp32_stack<RSI_NEAREST, true>(A, h->height, grid, block, s);
+        else launch_fp32_stack<RSI_NEAREST, false>(A, h->height, grid, block, s);
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[1], s));
     if (!o.fp32_only) {
         if (mode == RSI_ANY_HIT) launch_fp64<RSI_ANY_HIT>(A, h->height, device_sm_count() * 4, s);
-        else launch_fp64<RSI_COUNT>(A, h->height, device_sm_count() * 4, s);
+        else if (mode == RSI_COUNT) launch_fp64<RSI_COUNT>(A, h->height, device_sm_count() * 4, s);
+        else launch_fp64<RSI_NEAREST>(A, h->height, device_sm_count() * 4, s);
+    }
+    if (mode == RSI_NEAREST) {
+        k_nearest_finish<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count() * 8)),
+                           256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist);
+        note_launches(1);
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[2], s));
     note_launches(o.fp32_only ? 2 : 3);
@@ -1128,6 +1342,58 @@ extern "C" int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, in
                            h->band_ids + h->band_cap, h->ctr, s);
     if (rc) return rc;
     if (stats) return rsi::read_stats(h, h->ctr, n_rays, stats, s);
+    return RSI_OK;
+}
+
+extern "C" int rsi_query_nearest(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays,
+                                 const rsi_options* opt, int32_t* d_tri, float* d_t, float* d_point, float* d_dist,
+                                 uint8_t* d_ambiguous, rsi_stats* stats, void* stream) {
+    if (!h) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_nearest: NULL handle");
+    if (n_rays < 0 || n_rays > 0x7FFFFFFFll)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_nearest: need 0 <= n_rays < 2^31");
+    if (n_rays > 0 && (!d_from || !d_to || !d_tri))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_nearest: NULL segment or triangle pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_rays == 0) {
+        if (stats) *stats = rsi_stats{};
+        return RSI_OK;
+    }
+    int rc = rsi::ensure_band_capacity(h, n_rays, s);
+    if (rc) return rc;
+    const rsi::NearestOut no = {d_tri, d_t, d_point, d_dist};
+    rc = rsi::query_device(h, d_from, d_to, n_rays, RSI_NEAREST, opt, nullptr, nullptr, d_ambiguous, h->band_ids,
+                           h->band_ids + h->band_cap, h->ctr, s, nullptr, nullptr, &no);
+    if (rc) return rc;
+    if (stats) return rsi::read_stats(h, h->ctr, n_rays, stats, s);
+    return RSI_OK;
+}
+
+extern "C" int rsi_nearest_compact(const int32_t* d_tri, const float* d_dist, const float* d_point, int64_t n_rays,
+                                   int32_t* d_rays, int32_t* d_tri_out, float* d_dist_out, float* d_point_out,
+                                   int64_t* n_hits, void* stream) {
+    if (!n_hits || n_rays < 0 || n_rays > 0x7FFFFFFFll || (n_rays > 0 && !d_tri) || (d_dist_out && !d_dist) ||
+        (d_point_out && !d_point))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_nearest_compact: bad arguments");
+    *n_hits = 0;
+    if (n_rays == 0) return RSI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n_tiles = (n_rays + rsi::kCompactTile - 1) / rsi::kCompactTile;
+    void* scratch = nullptr;   // [total (8 B)] [tile offsets]
+    if (rsi::pool_alloc(&scratch, 8 + 4 * (size_t)n_tiles, s) != RSI_OK) return RSI_ERR_OOM;
+    long long* d_total = reinterpret_cast<long long*>(scratch);
+    int* tiles = reinterpret_cast<int*>(d_total + 1);
+    rsi::k_compact_count<<<(int)n_tiles, 256, 0, s>>>(d_tri, n_rays, tiles);
+    rsi::k_compact_scan<<<1, 256, 0, s>>>(tiles, (int)n_tiles, d_total);
+    rsi::k_compact_scatter<<<(int)n_tiles, 256, 0, s>>>(d_tri, d_dist, d_point, n_rays, tiles, d_rays, d_tri_out,
+                                                        d_dist_out, d_point_out);
+    rsi::note_launches(3);
+    long long total = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, sizeof(total), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    rsi::pool_free(scratch, s);
+    if (e != cudaSuccess) return rsi::cuda_fail(e, "rsi_nearest_compact");
+    *n_hits = total;
     return RSI_OK;
 }
 

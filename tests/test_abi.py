@@ -57,3 +57,13 @@ def test_host_side_rejections(lib):
     rc = L.rsi_query(None, None, None, 0, 0, None, None, None, None, None, None)
     assert rc == -1
     assert L.lbvh_free(None) == 0
+    # barycentric mode: a handle is required; compaction checks its outputs
+    rc = L.rsi_query_nearest(None, None, None, 0, None, None, None, None, None, None, None, None)
+    assert rc == -1
+    k = ctypes.c_int64(7)
+    assert L.rsi_nearest_compact(None, None, None, 0, None, None, None, None, ctypes.byref(k), None) == 0
+    assert k.value == 0                        # nothing to compact: no device work
+    assert L.rsi_nearest_compact(None, None, None, 10, None, None, None, None, None, None) == -1
+    rc = L.rsi_nearest_compact(ctypes.c_void_p(16), None, None, 5, None, None, ctypes.c_void_p(16), None,
+                               ctypes.byref(k), None)
+    assert rc == -1                            # distances asked for without their input
