@@ -36,6 +36,8 @@ METRIC = "rays/s (exact vs FP64 oracle) plain vs batched+learned on 1 GB300; % r
 WORKLOAD = ("c2: 100x100-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (19,602 FP32 triangles); "
             "1e7 FP32 segments, 50% crossing / 50% above, length U(0.05,1), random directions; "
             "step = lbvh_build + boolean query + intercept_count query")
+W_DOC_PAPER = ("paper scale: 111x134-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (14,874 vertices, "
+               "29,260 triangles, the paper's counts); 1e7 segments, 50% crossing / 50% above")
 BYTES_PER_RAY_COUNT = 28   # 24 B of segment in + 4 B of count out (algorithmic)
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_query_fp32_count_c2.md")
 
@@ -296,6 +298,93 @@ def measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args):
                                "(rays, distances, triangles, points)"}
 
 
+def measure_builders(rsi, torch, dev, meshes, c4, reps=20):
+    """Build time of the two tree constructions (Karras radix tree + refit,
+    and the single bottom-up pass of Sec. 4.2 after Apetrei) on the c2 and
+    c3 meshes and on all 64 c4 meshes: wall-clock per lbvh_build call
+    (each call synchronizes its stream once), median over reps."""
+    def per_build(V, T, builder):
+        for _ in range(3):
+            rsi.LBVH(V, T, builder=builder).close()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b = rsi.LBVH(V, T, builder=builder)
+            ts.append(1e3 * (time.perf_counter() - t0))
+            b.close()
+        return statistics.median(ts)
+
+    out = {"reps": reps, "timing": "wall clock of one lbvh_build call (one stream synchronization inside)"}
+    for name, m in meshes:
+        V, T = torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.triangles).to(dev)
+        out[name] = {"triangles": int(len(m.triangles)),
+                     **{f"{b}_ms": per_build(V, T, b) for b in ("karras", "apetrei")}}
+    if c4 is not None:
+        jobs = [(torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.triangles).to(dev)) for m, _ in c4[0]]
+        tot = {}
+        for b in ("karras", "apetrei"):
+            tot[f"{b}_ms"] = sum(per_build(V, T, b) for V, T in jobs)
+        out["c4_all_64"] = {"triangles": int(sum(len(m.triangles) for m, _ in c4[0])), **tot}
+    return out
+
+
+# The paper's own timings for 1e7 rays on its 29,260-triangle surface (Sec. 4,
+# GPU not stated; the original CUDA program and the PyCUDA port), in ms.
+PAPER_MS = {"boolean": {"cuda": 300.166, "pycuda": 355.094},
+            "intercept_count": {"cuda": 334.192, "pycuda": 383.117},
+            "barycentric": {"cuda": 308.625, "pycuda": 909.376}}
+
+
+def measure_paper_scale(rsi, torch, dev, paper, args):
+    """End to end in the paper's style (Sec. 3.3, Sec. 4) at the paper's
+    scale: a surface with its vertex and triangle counts (111 x 134 grid,
+    29,260 triangles) and 1e7 segments, all in pinned host memory; one run =
+    build from host arrays + query + results back in host memory, per mode.
+    Set beside the paper's own timings (other hardware, context only)."""
+    mesh, (F, E) = paper
+    pV, pT = torch.from_numpy(mesh.vertices).pin_memory(), torch.from_numpy(mesh.triangles).pin_memory()
+    pF, pE = torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory()
+    n = pF.shape[0]
+    hh = torch.empty(n, dtype=torch.uint8).pin_memory()
+    hc = torch.empty(n, dtype=torch.int32).pin_memory()
+    ha = torch.empty(n, dtype=torch.uint8).pin_memory()
+    steps = max(3, min(args.steps, 10))
+
+    def boolean():
+        b = rsi.LBVH(pV, pT)
+        b.query_host(pF, pE, "any_hit", hit=hh, ambiguous=ha)
+        b.close()
+
+    def intercept_count():
+        b = rsi.LBVH(pV, pT)
+        b.query_host(pF, pE, "count", count=hc, ambiguous=ha)
+        b.close()
+
+    def barycentric():
+        b = rsi.LBVH(pV.to(dev, non_blocking=True), pT.to(dev, non_blocking=True))
+        out = [x.cpu() for x in b.barycentric(pF.to(dev, non_blocking=True), pE.to(dev, non_blocking=True))]
+        b.close()
+        return out
+
+    out = {"workload": W_DOC_PAPER, "rays": n, "triangles": int(len(mesh.triangles)), "steps": steps,
+           "timing": "wall clock, pinned host mesh and segments in, host results out, build included"}
+    for name, fn in (("boolean", boolean), ("intercept_count", intercept_count), ("barycentric", barycentric)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0) / steps
+        out[name] = {"ms": ms, "rays_per_s": n / (ms / 1e3), "paper_ms": PAPER_MS[name],
+                     "paper_rays_per_s_cuda": n / (PAPER_MS[name]["cuda"] / 1e3)}
+    out["hits"] = int(hh.sum())
+    out["crossings"] = int(hc.sum())
+    return out
+
+
 MLP_FLOP_PER_SEGMENT = 2 * (6 * 128 + 128 * 128 + 128 * 256)   # algorithmic (unpadded) multiply-adds x 2
 
 
@@ -377,6 +466,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-nearest", action="store_true")
+    ap.add_argument("--no-builders", action="store_true")
+    ap.add_argument("--no-paper-scale", action="store_true")
     ap.add_argument("--learned-rays", type=int, default=100_000_000)
     ap.add_argument("--train-rays", type=int, default=10_000_000)
     args = ap.parse_args()
@@ -403,6 +494,10 @@ def main():
     if not args.no_batched and rank == 0:
         jobs = W.batched_meshes(n_meshes=64, seed=4)
         c4 = (jobs, W.rays_many(jobs))           # process pool before any GPU call
+    paper = None
+    if not args.no_paper_scale and rank == 0:
+        pm = W.config_mesh("paper")
+        paper = (pm, W.rays_many([(pm, W.config_rays("paper"))])[0])
     c5 = None
     if not args.no_learned and rank == 0:
         m1 = W.config_mesh("c1")
@@ -500,6 +595,19 @@ def main():
     st_c = bvh.query(dF, dE, "count", stats=True)["stats"]
     st_a = bvh.query(dF, dE, "any_hit", stats=True)["stats"]
     height = bvh.info()["height"]
+    # traversal kernel time by node width (child-pair vs four-wide), same answers
+    widths = {}
+    for w in (2, 4):
+        st_w = bvh.query(dF, dE, "count", stats=True, node_width=w)["stats"]
+        per = {}
+        for mode in ("any_hit", "count"):
+            ts = []
+            for _ in range(5):
+                bvh.query(dF, dE, mode, hit=hit, count=cnt, ambiguous=amb_c, time_kernels=True, node_width=w)
+                ts.append(bvh.last_query_ms()[0])
+            per[f"{mode}_traverse_ms"] = statistics.median(ts[1:])
+        per["node_fetches_per_ray_count"] = st_w["node_visits"] / n
+        widths[str(w)] = per
     bvh.close()
 
     if rank != 0:
@@ -531,7 +639,13 @@ def main():
                      "tri_tests_per_ray_count": st_c["tri_tests"] / n, "band_rays_count": st_c["band_rays"],
                      "ambiguous_count": st_c["ambiguous"], "node_visits_per_ray_any": st_a["node_visits"] / n,
                      "band_rays_any": st_a["band_rays"], "ambiguous_any": st_a["ambiguous"]},
+        "node_width": widths,
     }
+    if not args.no_builders:
+        line["builders"] = measure_builders(rsi, torch, dev, [("c2", mesh), ("c3", W.config_mesh("c3"))],
+                                            c4, reps=max(5, min(args.steps, 20)))
+    if paper is not None:
+        line["paper_scale_e2e"] = measure_paper_scale(rsi, torch, dev, paper, args)
     if not args.no_nearest:
         line["barycentric_c2"] = measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args)
     if c4 is not None:

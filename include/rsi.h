@@ -79,13 +79,19 @@ typedef struct rsi_options {
                            each tile of this many segments is first grouped
                            by a coarse Morton cell of the segment midpoints
                            (better warp coherence; results are unchanged)  */
+    int node_width;     /* nodes the FP32 traversal fetches: 2 (or 0, the
+                           default) = child-pair nodes; 4 = four-wide nodes
+                           (up to four child boxes per 128-byte fetch; trees
+                           of height > 82 fall back to 2).  Results are the
+                           same either way.                                 */
 } rsi_options;
 
 /* Per-query counters, filled on the host when a non-NULL pointer is given
  * (the call then synchronizes `stream`). */
 typedef struct rsi_stats {
     int64_t n_rays;
-    int64_t node_visits;   /* child-pair nodes fetched (collect_stats only)  */
+    int64_t node_visits;   /* nodes fetched by the FP32 traversal, four-wide
+                              or child-pair (collect_stats only)            */
     int64_t tri_tests;     /* FP32 segment/triangle tests (collect_stats)    */
     int64_t band_rays;     /* segments re-tested in FP64                     */
     int64_t ambiguous;     /* segments left ambiguous by the FP64 re-test    */
@@ -139,6 +145,25 @@ typedef struct rsi_bvh_host_view {
 int lbvh_build(const float* d_vertices, int64_t n_vertices, const int32_t* d_triangles,
                int64_t n_triangles, int index_bytes, int morton_bits, void* stream,
                rsi_bvh_t* out);
+
+/* Tree construction of lbvh_build_ex. */
+#define RSI_TREE_KARRAS 0  /* radix tree top-down, one thread per internal node
+                              (Karras 2012), then a separate bottom-up refit */
+#define RSI_TREE_APETREI 1 /* one bottom-up pass that builds the tree and its
+                              boxes together (Apetrei 2014; the bottom-up
+                              construction of Sec. 4.2)                      */
+
+/*
+ * As lbvh_build, with the tree construction chosen by tree_builder
+ * (RSI_TREE_KARRAS or RSI_TREE_APETREI; anything else: RSI_ERR_INVALID_ARG).
+ * Both give the same hierarchy bit for bit -- the binary radix tree over the
+ * sorted (code, triangle id) pairs is unique -- in the same numbering
+ * (lbvh_export), so queries answer identically; only the build time differs.
+ * RSI_TREE_APETREI replaces the tree and refit kernels with one kernel.
+ */
+int lbvh_build_ex(const float* d_vertices, int64_t n_vertices, const int32_t* d_triangles,
+                  int64_t n_triangles, int index_bytes, int morton_bits, int tree_builder, void* stream,
+                  rsi_bvh_t* out);
 
 /* As lbvh_build, with the mesh in host memory (copied in on `stream`). */
 int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
@@ -315,10 +340,11 @@ typedef struct rsi_tuning {
     float ms;           /* time of the best candidate on the sample          */
     int from_cache;     /* 1 if the choice came from the cache file          */
     int candidates;     /* candidates timed (0 on a cache hit)               */
+    int node_width;     /* node width chosen (2 or 4, see rsi_options)       */
 } rsi_tuning;
 
 /*
- * Choose the traversal launch shape and the in-tile segment reordering for
+ * Choose the traversal launch shape, node width and the in-tile segment reordering for
  * queries like this one (the method's query of Sec. 1; tuning has no
  * counterpart in the paper).  Times candidate options on the first
  * min(n_rays, 2^21) segments with CUDA events (running rsi_query, so it

@@ -36,7 +36,7 @@ class RSIError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("fp32_only", ctypes.c_int), ("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("collect_stats", ctypes.c_int), ("timeout_ns", ctypes.c_int64), ("time_kernels", ctypes.c_int),
-                ("ray_sort_tile", ctypes.c_int)]
+                ("ray_sort_tile", ctypes.c_int), ("node_width", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -63,7 +63,7 @@ class HostView(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("ray_sort_tile", ctypes.c_int),
                 ("stack", ctypes.c_int), ("ms", ctypes.c_float), ("from_cache", ctypes.c_int),
-                ("candidates", ctypes.c_int)]
+                ("candidates", ctypes.c_int), ("node_width", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +82,8 @@ def _load():
     P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     lib.lbvh_build.argtypes = [P, i64, P, i64, i32, i32, P, ctypes.POINTER(P)]
     lib.lbvh_build_host.argtypes = [P, i64, P, i64, i32, i32, P, ctypes.POINTER(P)]
+    lib.lbvh_build_ex.argtypes = [P, i64, P, i64, i32, i32, i32, P, ctypes.POINTER(P)]
+    lib.lbvh_build_ex.restype = ctypes.c_int
     lib.lbvh_free.argtypes = [P]
     lib.lbvh_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.lbvh_export.argtypes = [P, P, ctypes.POINTER(HostView)]
@@ -182,10 +184,17 @@ def _mode(mode):
     raise ValueError(f"unknown mode {mode!r}")
 
 
-class LBVH:
-    """A linear BVH over a triangle mesh, built on the GPU (lbvh_build)."""
+_TREE_BUILDERS = {"karras": 0, "apetrei": 1}   # RSI_TREE_KARRAS, RSI_TREE_APETREI
 
-    def __init__(self, vertices, triangles, morton_bits: int = 30, stream=None):
+
+class LBVH:
+    """A linear BVH over a triangle mesh, built on the GPU (lbvh_build).
+
+    builder: "karras" (radix tree, then refit) or "apetrei" (one bottom-up
+    pass, lbvh_build_ex; device inputs only).  Both give the same hierarchy.
+    """
+
+    def __init__(self, vertices, triangles, morton_bits: int = 30, stream=None, builder: str = "karras"):
         import torch
         _check_f32x3(vertices, "vertices")
         if not isinstance(triangles, torch.Tensor) or triangles.dim() != 2 or triangles.shape[1] != 3:
@@ -197,9 +206,18 @@ class LBVH:
         on_dev = vertices.is_cuda
         if on_dev != triangles.is_cuda:
             raise TypeError("vertices and triangles must both be on the GPU or both on the host")
-        fn = lib.lbvh_build if on_dev else lib.lbvh_build_host
-        check(fn(_ptr(vertices), vertices.shape[0], _ptr(triangles.contiguous()), triangles.shape[0], index_bytes,
-                 morton_bits, _stream(stream), ctypes.byref(self._h)))
+        if builder not in _TREE_BUILDERS:
+            raise ValueError(f"unknown builder {builder!r} (karras or apetrei)")
+        if builder == "karras":
+            fn = lib.lbvh_build if on_dev else lib.lbvh_build_host
+            check(fn(_ptr(vertices), vertices.shape[0], _ptr(triangles.contiguous()), triangles.shape[0],
+                     index_bytes, morton_bits, _stream(stream), ctypes.byref(self._h)))
+        else:
+            if not on_dev:
+                raise TypeError("the apetrei builder takes device tensors")
+            check(lib.lbvh_build_ex(_ptr(vertices), vertices.shape[0], _ptr(triangles.contiguous()),
+                                    triangles.shape[0], index_bytes, morton_bits, _TREE_BUILDERS[builder],
+                                    _stream(stream), ctypes.byref(self._h)))
         self.n_triangles = triangles.shape[0]
 
     def close(self):
@@ -263,7 +281,7 @@ class LBVH:
 
     def query(self, ray_from, ray_to, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0,
               stats=False, hit=None, count=None, ambiguous=None, want_ambiguous=True, time_kernels=False,
-              ray_sort_tile=0, stream=None):
+              ray_sort_tile=0, node_width=0, stream=None):
         """Query segments (device tensors [n, 3] float32).  Returns a dict with
         'hit' (uint8, any-hit mode or count > 0), 'count' (int32, count mode),
         'ambiguous' (uint8) and, with stats=True, 'stats'."""
@@ -284,7 +302,7 @@ class LBVH:
         if ambiguous is None and want_ambiguous:
             ambiguous = torch.empty(n, dtype=torch.uint8, device=dev)
         opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels),
-                      int(ray_sort_tile))
+                      int(ray_sort_tile), int(node_width))
         st = Stats()
         check(lib.rsi_query(self._h, _ptr(ray_from), _ptr(ray_to), n, m, ctypes.byref(opt), _ptr(hit), _ptr(count),
                             _ptr(ambiguous), ctypes.byref(st) if stats else None, _stream(stream)))
@@ -320,7 +338,7 @@ class LBVH:
 
     def nearest(self, ray_from, ray_to, *, fp32_only=False, block=0, blocks_per_sm=0, stats=False,
                 want_t=True, want_point=True, want_dist=True, want_ambiguous=True, time_kernels=False,
-                ray_sort_tile=0, stream=None):
+                ray_sort_tile=0, node_width=0, stream=None):
         """Barycentric mode per segment (rsi_query_nearest): 'tri' (int32, -1
         when no hit), 't', 'point' [n, 3], 'dist' (float32), 'ambiguous'."""
         import torch
@@ -338,7 +356,7 @@ class LBVH:
         dist = torch.empty(n, dtype=torch.float32, device=dev) if want_dist else None
         amb = torch.empty(n, dtype=torch.uint8, device=dev) if want_ambiguous else None
         opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels),
-                      int(ray_sort_tile))
+                      int(ray_sort_tile), int(node_width))
         st = Stats()
         check(lib.rsi_query_nearest(self._h, _ptr(ray_from), _ptr(ray_to), n, ctypes.byref(opt), _ptr(tri), _ptr(t),
                                     _ptr(point), _ptr(dist), _ptr(amb), ctypes.byref(st) if stats else None,
@@ -383,7 +401,7 @@ class BatchPlan:
     stream_timeout_ns > 0 makes a streaming plan fed by post()."""
 
     def __init__(self, items, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0, stats=False,
-                 stream_timeout_ns=0, stream=None):
+                 stream_timeout_ns=0, node_width=0, stream=None):
         import torch
         m = _mode(mode)
         self.mode = m
@@ -403,7 +421,7 @@ class BatchPlan:
             arr[i] = RayBatch(bvh.handle.value, f.data_ptr(), t.data_ptr(), n, h.data_ptr() if h is not None else None,
                               c.data_ptr() if c is not None else None, a.data_ptr())
         timeout = -int(stream_timeout_ns) if stream_timeout_ns else 0
-        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), timeout, 0, 0)
+        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), timeout, 0, 0, int(node_width))
         self._p = ctypes.c_void_p()
         check(lib.rsi_batch_create(arr, len(items), m, ctypes.byref(opt), _stream(stream), ctypes.byref(self._p)))
         self.total = sum(int(f.shape[0]) for _, f, _ in items)
@@ -556,7 +574,7 @@ def query_learned(bvh, net, ray_from, ray_to, stats=False, hit=None, ambiguous=N
     if ambiguous is None:
         ambiguous = torch.empty(n, dtype=torch.uint8, device=ray_from.device)
     opt = Options(int(opts.get("fp32_only", 0)), int(opts.get("block", 0)), int(opts.get("blocks_per_sm", 0)),
-                  int(stats), 0, 0, 0)
+                  int(stats), 0, 0, 0, int(opts.get("node_width", 0)))
     st = Stats()
     check(lib.rsi_query_learned(bvh.handle, net.handle, _ptr(ray_from), _ptr(ray_to), n, ctypes.byref(opt),
                                 _ptr(hit), _ptr(ambiguous), ctypes.byref(st) if stats else None, _stream(stream)))

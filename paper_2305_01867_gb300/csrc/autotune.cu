@@ -1,8 +1,9 @@
 // autotune.cu -- picks the launch shape of the traversal (threads per block,
-// resident blocks per SM) and the in-tile segment reordering of a query by
+// resident blocks per SM), the node width it fetches (child-pair or
+// four-wide) and the in-tile segment reordering of a query by
 // timing candidates on a sample of its own segments with CUDA events, and
 // reports the traversal stack the tree needs (the smallest of 32 / 64 / 128
-// entries above the tree height).  Choices are cached in a JSON file keyed
+// entries that holds the chosen walk's worst case).  Choices are cached in a JSON file keyed
 // by device, mode and the sizes of the problem (log2 buckets).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -22,7 +23,7 @@
 namespace {
 
 struct Choice {
-    int block = 256, bps = 4, tile = 0, stack = 32;
+    int block = 256, bps = 4, tile = 0, stack = 32, width = 2;
     float ms = 0.0f;
 };
 
@@ -54,7 +55,7 @@ std::string tuning_key(int mode, int64_t n_tri, int64_t n_rays) {
 }
 
 // The cache holds one entry per line:  "key": {"block": B, "blocks_per_sm": S,
-// "ray_sort_tile": T, "stack": K, "ms": M},
+// "ray_sort_tile": T, "stack": K, "node_width": W, "ms": M},
 int field(const std::string& line, const char* name, int dflt) {
     std::string pat = std::string("\"") + name + "\":";
     size_t p = line.find(pat);
@@ -96,9 +97,11 @@ bool write_cache(const char* path, const std::map<std::string, std::string>& m) 
 }
 
 std::string encode(const Choice& c) {
-    char buf[160];
-    std::snprintf(buf, sizeof buf, "{\"block\": %d, \"blocks_per_sm\": %d, \"ray_sort_tile\": %d, \"stack\": %d, \"ms\": %.4f}",
-                  c.block, c.bps, c.tile, c.stack, c.ms);
+    char buf[200];
+    std::snprintf(buf, sizeof buf,
+                  "{\"block\": %d, \"blocks_per_sm\": %d, \"ray_sort_tile\": %d, \"stack\": %d, \"node_width\": %d, "
+                  "\"ms\": %.4f}",
+                  c.block, c.bps, c.tile, c.stack, c.width, c.ms);
     return buf;
 }
 
@@ -110,7 +113,13 @@ extern "C" int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to,
         return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_autotune: bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
     Choice best;
-    best.stack = h->height < 32 ? 32 : (h->height < 64 ? 64 : 128);
+    // stack entries of the walk: one per level (child-pair), three per
+    // four-wide level; the four-wide walk needs <= 128 (tree height <= 82)
+    auto stack_for = [&](int width) {
+        const int need = width == 4 ? 3 * ((h->height + 2) / 2) : h->height + 1;
+        return need <= 32 ? 32 : (need <= 64 ? 64 : 128);
+    };
+    const bool wide_ok = 3 * ((h->height + 2) / 2) <= 128;
     const std::string key = tuning_key(mode, h->n_tri, n_rays);
     auto cache = read_cache(cache_path);
     auto it = cache.find(key);
@@ -119,6 +128,8 @@ extern "C" int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to,
         best.block = field(it->second, "block", 256);
         best.bps = field(it->second, "blocks_per_sm", 4);
         best.tile = field(it->second, "ray_sort_tile", 0);
+        best.width = field(it->second, "node_width", 2);
+        if (best.width == 4 && !wide_ok) best.width = 2;
         from_cache = 1;
     } else {
         const int64_t n = std::min<int64_t>(n_rays, (int64_t)1 << 21);   // sample: the first 2M segments
@@ -135,14 +146,18 @@ extern "C" int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to,
         cudaEventCreate(&e1);
         const int shapes[][2] = {{256, 4}, {256, 3}, {256, 2}, {128, 8}, {128, 6}, {64, 16}};
         const int tiles[] = {0, 2048, 8192};
+        const int widths[] = {2, 4};
         float best_ms = INFINITY;
         int rc = RSI_OK;
         for (const auto& sh : shapes) {
-            for (int tile : tiles) {
+            for (int c = 0; c < 6; ++c) {
+                const int tile = tiles[c % 3], width = widths[c / 3];
+                if (width == 4 && !wide_ok) continue;
                 rsi_options o = *inout;
                 o.block = sh[0];
                 o.blocks_per_sm = sh[1];
                 o.ray_sort_tile = tile;
+                o.node_width = width;
                 o.time_kernels = 0;
                 o.collect_stats = 0;
                 float total = 0.0f;
@@ -164,6 +179,7 @@ extern "C" int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to,
                     best.block = sh[0];
                     best.bps = sh[1];
                     best.tile = tile;
+                    best.width = width;
                     best.ms = ms;
                 }
             }
@@ -174,12 +190,15 @@ extern "C" int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to,
         cudaFreeAsync(hit, s);
         cudaFreeAsync(cnt, s);
         if (rc != RSI_OK) return rc;
+        best.stack = stack_for(best.width);
         cache[key] = encode(best);
         if (!write_cache(cache_path, cache)) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_autotune: cannot write cache");
     }
     inout->block = best.block;
     inout->blocks_per_sm = best.bps;
     inout->ray_sort_tile = best.tile;
+    inout->node_width = best.width;
+    best.stack = stack_for(best.width);
     if (result) {
         result->block = best.block;
         result->blocks_per_sm = best.bps;
@@ -188,6 +207,7 @@ extern "C" int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to,
         result->ms = best.ms;
         result->from_cache = from_cache;
         result->candidates = candidates;
+        result->node_width = best.width;
     }
     return RSI_OK;
 }

@@ -9,6 +9,9 @@
 //   k_refit    bottom-up boxes: the second child to arrive at a node (atomic
 //              counter) unions the children and climbs on (Sec. 4.2: a node
 //              left with counter 1 is "half-filled")
+//   k_apetrei  the alternative single pass that builds the same tree and its
+//              boxes bottom-up at once (Apetrei 2014, the agglomerative build
+//              the paper's Sec. 4.2 follows), replacing k_karras + k_refit
 // Every grid is sized from its own element count (the grid-size error of
 // Sec. 4.2.3 is the lesson) and all steps run on the caller's stream.
 #include <cuda_runtime.h>
@@ -380,6 +383,175 @@ __global__ void k_refit(const float* __restrict__ V, int64_t nv, const int32_t* 
     }
 }
 
+// ---------------------------------------------------------------- 4-wide nodes
+// Binary node i at even depth becomes a four-wide node holding its children,
+// an internal child being replaced by that child's two children.  Child order
+// is leaf order (Morton order).  Odd-depth nodes get no four-wide node.
+__global__ void k_collapse4(const Node* __restrict__ nodes, const int32_t* __restrict__ parent, int64_t n,
+                            Node4* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int depth = 0;
+    for (int32_t p = (int32_t)i; p != 0; p = parent[p]) ++depth;
+    if (depth & 1) return;
+    float bx[6][4];
+    int rf[4];
+    int m = 0;
+    const Node nd = nodes[i];
+    const float4 side[2][2] = {{nd.lmin, nd.lmax}, {nd.rmin, nd.rmax}};
+    const int refs[2] = {__float_as_int(nd.lmin.w), __float_as_int(nd.lmax.w)};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (refs[c] < 0) {   // a leaf: kept as it is
+            bx[0][m] = side[c][0].x; bx[1][m] = side[c][1].x;
+            bx[2][m] = side[c][0].y; bx[3][m] = side[c][1].y;
+            bx[4][m] = side[c][0].z; bx[5][m] = side[c][1].z;
+            rf[m++] = refs[c];
+        } else {             // an internal node: its two children instead
+            const Node k = nodes[refs[c]];
+            const float4 ks[2][2] = {{k.lmin, k.lmax}, {k.rmin, k.rmax}};
+            const int krefs[2] = {__float_as_int(k.lmin.w), __float_as_int(k.lmax.w)};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                bx[0][m] = ks[e][0].x; bx[1][m] = ks[e][1].x;
+                bx[2][m] = ks[e][0].y; bx[3][m] = ks[e][1].y;
+                bx[4][m] = ks[e][0].z; bx[5][m] = ks[e][1].z;
+                rf[m++] = krefs[e];
+            }
+        }
+    }
+    for (int c = m; c < 4; ++c) {   // empty lanes: a NaN box (never passes a slab test) and kEmpty4
+        for (int a = 0; a < 6; ++a) bx[a][c] = __int_as_float(0x7fc00000);
+        rf[c] = kEmpty4;
+    }
+    Node4 o;
+    o.xlo = make_float4(bx[0][0], bx[0][1], bx[0][2], bx[0][3]);
+    o.xhi = make_float4(bx[1][0], bx[1][1], bx[1][2], bx[1][3]);
+    o.ylo = make_float4(bx[2][0], bx[2][1], bx[2][2], bx[2][3]);
+    o.yhi = make_float4(bx[3][0], bx[3][1], bx[3][2], bx[3][3]);
+    o.zlo = make_float4(bx[4][0], bx[4][1], bx[4][2], bx[4][3]);
+    o.zhi = make_float4(bx[5][0], bx[5][1], bx[5][2], bx[5][3]);
+    o.ref = make_int4(rf[0], rf[1], rf[2], rf[3]);
+    o.pad = make_int4(m, 0, 0, 0);
+    out[i] = o;
+}
+
+// ---------------------------------------------------------------- single pass
+// Agglomerative build (Apetrei 2014; the bottom-up construction of Sec. 4.2):
+// one thread per leaf climbs the tree.  A node covering leaves [lo, hi] is
+// the left child of the node split between hi and hi + 1 if the keys there
+// share a longer prefix than the keys at lo - 1, lo (delta() with the index
+// appended, -1 past either end); otherwise it is the right child of the node
+// split between lo - 1 and lo.  Both children post their outer range end to
+// the parent's split slot with one atomic exchange; the second to arrive
+// learns the parent's full range, unions the boxes and climbs on.
+//
+// The radix tree over distinct (key, index) pairs is unique, so this is the
+// tree k_karras builds; it is written in the same Karras numbering (the root
+// is 0, a left child is numbered by its last leaf, a right child by its
+// first), which a node learns only when it knows which side of its parent it
+// is on -- so a node's arrays are written one step up the climb.
+template <typename K>
+__global__ void k_apetrei(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T,
+                          const int32_t* __restrict__ perm, const K* __restrict__ keys, int64_t n,
+                          int32_t* __restrict__ left, int32_t* __restrict__ right, int32_t* __restrict__ parent,
+                          float* __restrict__ box, int32_t* __restrict__ hgt, int32_t* __restrict__ ends,
+                          Node* __restrict__ nodes, Tri* __restrict__ tris, DevCounters* c) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int32_t t = perm[j];
+    int32_t i0 = T[3 * (int64_t)t], i1 = T[3 * (int64_t)t + 1], i2 = T[3 * (int64_t)t + 2];
+    float v[3][3];
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
+        raise_error(c, RSI_ERR_INDEX);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[0][a] = v[1][a] = v[2][a] = 0.0f;
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            v[0][a] = V[3 * (int64_t)i0 + a];
+            v[1][a] = V[3 * (int64_t)i1 + a];
+            v[2][a] = V[3 * (int64_t)i2 + a];
+        }
+    }
+    Tri tr;
+    tr.v0 = make_float4(v[0][0], v[0][1], v[0][2], __int_as_float(t));
+    tr.v1 = make_float4(v[1][0], v[1][1], v[1][2], 0.0f);
+    tr.v2 = make_float4(v[2][0], v[2][1], v[2][2], 0.0f);
+    tris[j] = tr;
+    float b[6];   // box of the current node: min xyz, max xyz
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        b[a] = fminf(fminf(v[0][a], v[1][a]), v[2][a]);
+        b[3 + a] = fmaxf(fmaxf(v[0][a], v[1][a]), v[2][a]);
+        box[6 * (n - 1 + j) + a] = b[a];
+        box[6 * (n - 1 + j) + 3 + a] = b[3 + a];
+        atomicMax(&c->dmax_bits[a], __float_as_uint(b[3 + a] - b[a]));
+    }
+    hgt[n - 1 + j] = 0;
+    if (n == 1) {
+        parent[0] = -1;
+        return;
+    }
+    int64_t lo = j, hi = j;
+    int h = 0;
+    int64_t split = -1;   // split of the current node (-1: it is the leaf j)
+    float bl[6], br[6];   // its children's boxes (internal nodes only)
+    for (;;) {
+        const bool root = lo == 0 && hi == n - 1;
+        const bool is_left = !root && delta(keys, n, hi, hi + 1) > delta(keys, n, lo, lo - 1);
+        if (split >= 0) {
+            // the current internal node learns its number and writes itself
+            const int64_t k = root ? 0 : (is_left ? hi : lo);
+            const int32_t lc = lo == split ? (int32_t)(kLeafTag | (uint32_t)split) : (int32_t)split;
+            const int32_t rc = hi == split + 1 ? (int32_t)(kLeafTag | (uint32_t)(split + 1)) : (int32_t)(split + 1);
+            left[k] = lc;
+            right[k] = rc;
+            parent[box_slot(lc, n)] = (int32_t)k;
+            parent[box_slot(rc, n)] = (int32_t)k;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) box[6 * k + a] = b[a];
+            hgt[k] = h;
+            Node nd;
+            nd.lmin = make_float4(bl[0], bl[1], bl[2], __int_as_float(packed_ref(lc)));
+            nd.lmax = make_float4(bl[3], bl[4], bl[5], __int_as_float(packed_ref(rc)));
+            nd.rmin = make_float4(br[0], br[1], br[2], 0.0f);
+            nd.rmax = make_float4(br[3], br[4], br[5], 0.0f);
+            nodes[k] = nd;
+            if (root) {
+                parent[0] = -1;
+                c->height = h;
+            }
+        }
+        if (root) return;
+        const int64_t g = is_left ? hi : lo - 1;   // the parent's split
+        __threadfence();
+        const int32_t other = atomicExch(&ends[g], (int32_t)(is_left ? lo : hi));
+        if (other < 0) return;   // first to arrive: the sibling carries on
+        __threadfence();
+        const int64_t plo = is_left ? lo : (int64_t)other, phi = is_left ? (int64_t)other : hi;
+        // the sibling's number (as in the Karras numbering) and its box
+        const int64_t sib = is_left ? (phi == g + 1 ? n - 1 + g + 1 : g + 1) : (plo == g ? n - 1 + g : g);
+        float s[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) s[a] = __ldcg(box + 6 * sib + a);
+        h = 1 + max(h, __ldcg(hgt + sib));
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            bl[a] = is_left ? b[a] : s[a];
+            br[a] = is_left ? s[a] : b[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            b[a] = fminf(bl[a], br[a]);
+            b[3 + a] = fmaxf(bl[3 + a], br[3 + a]);
+        }
+        lo = plo;
+        hi = phi;
+        split = g;
+    }
+}
+
 template <typename K>
 int sort_pairs(K* ka, int32_t* va, K* kb, int32_t* vb, int64_t n, int passes, uint32_t* hist, cudaStream_t s,
                K** out_k, int32_t** out_v) {
@@ -400,7 +572,8 @@ int sort_pairs(K* ka, int32_t* va, K* kb, int32_t* vb, int64_t n, int passes, ui
 }
 
 template <typename K>
-int build_impl(rsi_bvh_s* h, const float* V, const int32_t* T, cudaStream_t s, char* scratch) {
+int build_impl(rsi_bvh_s* h, const float* V, const int32_t* T, int builder, cudaStream_t s, char* scratch,
+               float* box, int32_t* hgt, int32_t* flag) {
     const int64_t n = h->n_tri;
     K* ka = (K*)scratch;
     K* kb = ka + n;
@@ -416,12 +589,22 @@ int build_impl(rsi_bvh_s* h, const float* V, const int32_t* T, cudaStream_t s, c
     if (rc) return rc;
     RSI_CUDA_TRY(cudaMemcpyAsync(h->sorted_keys, sk, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
     RSI_CUDA_TRY(cudaMemcpyAsync(h->perm, sv, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (builder == RSI_TREE_APETREI) {
+        k_apetrei<K><<<grid_for(n, kBlock), kBlock, 0, s>>>(V, h->n_vert, T, h->perm, (const K*)h->sorted_keys, n,
+                                                             h->left, h->right, h->parent, box, hgt, flag, h->nodes,
+                                                             h->tris, h->ctr);
+        note_launches(1);
+        return RSI_OK;
+    }
     if (n > 1) {
         k_karras<K><<<grid_for(n - 1, kBlock), kBlock, 0, s>>>((const K*)h->sorted_keys, n, h->left, h->right,
                                                                 h->parent);
         note_launches(1);
     } else
         RSI_CUDA_TRY(cudaMemsetAsync(h->parent, 0xFF, sizeof(int32_t), s));
+    k_refit<<<grid_for(n, kBlock), kBlock, 0, s>>>(V, h->n_vert, T, h->perm, n, h->left, h->right, h->parent, box,
+                                                   hgt, flag, h->nodes, h->tris, h->ctr);
+    note_launches(1);
     return RSI_OK;
 }
 
@@ -429,8 +612,8 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, int morton_bits, cudaStream_t s,
-                      rsi_bvh_t* out) {
+int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, int morton_bits, int builder,
+                      cudaStream_t s, rsi_bvh_t* out) {
     rsi_bvh_s* h = new rsi_bvh_s();
     h->n_tri = nt;
     h->n_vert = nv;
@@ -439,8 +622,8 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     const size_t ksz = morton_bits == 30 ? 4 : 8;
     const int ntiles = grid_for(n, 4096);
     // one allocation, carved into the handle's arrays (256-byte aligned)
-    size_t off[12], total = 0;
-    size_t sizes[12] = {
+    size_t off[13], total = 0;
+    size_t sizes[13] = {
         sizeof(Node) * (size_t)ni,                 // 0 nodes
         sizeof(Tri) * (size_t)n,                   // 1 tris
         ksz * (size_t)n,                           // 2 sorted keys
@@ -452,9 +635,10 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
         4 * (size_t)(2 * n - 1),                   // 8 heights
         4 * (size_t)ni,                            // 9 flags
         sizeof(DevCounters),                       // 10 counters
-        2 * ksz * (size_t)n + 8 * (size_t)n + 4 * 256 * (size_t)ntiles   // 11 sort scratch
+        2 * ksz * (size_t)n + 8 * (size_t)n + 4 * 256 * (size_t)ntiles,  // 11 sort scratch
+        sizeof(Node4) * (size_t)ni                 // 12 four-wide nodes
     };
-    for (int i = 0; i < 12; ++i) {
+    for (int i = 0; i < 13; ++i) {
         off[i] = total;
         total += align_up(sizes[i]);
     }
@@ -477,6 +661,7 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     int32_t* flag = (int32_t*)(base + off[9]);
     h->ctr = (DevCounters*)(base + off[10]);
     char* scratch = base + off[11];
+    h->nodes4 = (Node4*)(base + off[12]);
     auto cleanup = [&](int code) {
         cudaStreamSynchronize(s);
         pool_free(base, s);
@@ -484,13 +669,18 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
         return code;
     };
     k_init<<<1, 32, 0, s>>>(h->ctr);
-    note_launches(3);   // k_init, k_extent, k_refit
+    note_launches(2);   // k_init, k_extent
     k_extent<<<grid_for(nv, kBlock) < 4 * 152 ? grid_for(nv, kBlock) : 4 * 152, kBlock, 0, s>>>(V, nv, h->ctr);
-    if (cudaMemsetAsync(flag, 0, 4 * (size_t)ni, s) != cudaSuccess) return cleanup(cuda_fail(cudaGetLastError(), "memset"));
-    int rc = morton_bits == 30 ? build_impl<uint32_t>(h, V, T, s, scratch) : build_impl<uint64_t>(h, V, T, s, scratch);
+    // arrival counters of k_refit start at 0; range-end slots of k_apetrei at -1
+    if (cudaMemsetAsync(flag, builder == RSI_TREE_APETREI ? 0xFF : 0, 4 * (size_t)ni, s) != cudaSuccess)
+        return cleanup(cuda_fail(cudaGetLastError(), "memset"));
+    int rc = morton_bits == 30 ? build_impl<uint32_t>(h, V, T, builder, s, scratch, h->box, hgt, flag)
+                               : build_impl<uint64_t>(h, V, T, builder, s, scratch, h->box, hgt, flag);
     if (rc) return cleanup(rc);
-    k_refit<<<grid_for(n, kBlock), kBlock, 0, s>>>(V, nv, T, h->perm, n, h->left, h->right, h->parent, h->box, hgt,
-                                                   flag, h->nodes, h->tris, h->ctr);
+    if (n > 1) {
+        k_collapse4<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(h->nodes, h->parent, n, h->nodes4);
+        note_launches(1);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "lbvh_build kernels"));
     e = cudaMemcpyAsync(h->h_ctr, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
@@ -515,20 +705,40 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
 
 }  // namespace rsi
 
-extern "C" int lbvh_build(const float* d_vertices, int64_t n_vertices, const int32_t* d_triangles,
-                          int64_t n_triangles, int index_bytes, int morton_bits, void* stream, rsi_bvh_t* out) {
-    if (!out) return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build: out is NULL");
+namespace rsi {
+namespace {
+int build_checked(const char* fn, const float* d_vertices, int64_t n_vertices, const int32_t* d_triangles,
+                  int64_t n_triangles, int index_bytes, int morton_bits, int tree_builder, void* stream,
+                  rsi_bvh_t* out) {
+    const std::string f(fn);
+    if (!out) return fail(RSI_ERR_INVALID_ARG, f + ": out is NULL");
     *out = nullptr;
     if (index_bytes != 4)
-        return rsi::fail(RSI_ERR_DTYPE, "lbvh_build: triangle indices must be int32 (index_bytes = 4), got " +
-                                            std::to_string(index_bytes) + " bytes");
-    if (!d_vertices || !d_triangles) return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build: NULL input pointer");
+        return fail(RSI_ERR_DTYPE, f + ": triangle indices must be int32 (index_bytes = 4), got " +
+                                       std::to_string(index_bytes) + " bytes");
+    if (!d_vertices || !d_triangles) return fail(RSI_ERR_INVALID_ARG, f + ": NULL input pointer");
     if (n_triangles < 1 || n_vertices < 1 || n_triangles > (int64_t)0x3FFFFFFF || n_vertices > ((int64_t)1 << 31))
-        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build: need 1 <= n_triangles < 2^30 and 1 <= n_vertices <= 2^31");
-    if (morton_bits != 30 && morton_bits != 63)
-        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build: morton_bits must be 30 or 63");
-    return rsi::build_from_device(d_vertices, n_vertices, d_triangles, n_triangles, morton_bits,
-                                  (cudaStream_t)stream, out);
+        return fail(RSI_ERR_INVALID_ARG, f + ": need 1 <= n_triangles < 2^30 and 1 <= n_vertices <= 2^31");
+    if (morton_bits != 30 && morton_bits != 63) return fail(RSI_ERR_INVALID_ARG, f + ": morton_bits must be 30 or 63");
+    if (tree_builder != RSI_TREE_KARRAS && tree_builder != RSI_TREE_APETREI)
+        return fail(RSI_ERR_INVALID_ARG, f + ": tree_builder must be RSI_TREE_KARRAS or RSI_TREE_APETREI");
+    return build_from_device(d_vertices, n_vertices, d_triangles, n_triangles, morton_bits, tree_builder,
+                             (cudaStream_t)stream, out);
+}
+}  // namespace
+}  // namespace rsi
+
+extern "C" int lbvh_build(const float* d_vertices, int64_t n_vertices, const int32_t* d_triangles,
+                          int64_t n_triangles, int index_bytes, int morton_bits, void* stream, rsi_bvh_t* out) {
+    return rsi::build_checked("lbvh_build", d_vertices, n_vertices, d_triangles, n_triangles, index_bytes,
+                              morton_bits, RSI_TREE_KARRAS, stream, out);
+}
+
+extern "C" int lbvh_build_ex(const float* d_vertices, int64_t n_vertices, const int32_t* d_triangles,
+                             int64_t n_triangles, int index_bytes, int morton_bits, int tree_builder, void* stream,
+                             rsi_bvh_t* out) {
+    return rsi::build_checked("lbvh_build_ex", d_vertices, n_vertices, d_triangles, n_triangles, index_bytes,
+                              morton_bits, tree_builder, stream, out);
 }
 
 extern "C" int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,

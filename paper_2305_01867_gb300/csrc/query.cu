@@ -34,6 +34,7 @@ namespace rsi {
 // [traversal kernel: begin] (device code of the traversal passes)
 struct QueryArgs {
     const Node* nodes;
+    const Node4* nodes4;   // four-wide nodes of the same hierarchy
     const Tri* tris;
     int64_t n_tri;
     const float* from;
@@ -54,6 +55,7 @@ struct QueryArgs {
 // One (hierarchy, segment batch, outputs) triple of a batched query.
 struct BatchDesc {
     const Node* nodes;
+    const Node4* nodes4;
     const Tri* tris;
     const float* from;
     const float* to;
@@ -111,15 +113,19 @@ __device__ __forceinline__ SegF make_seg(float3 s, float3 e, float dmx, float dm
 // Does the segment pass through the padded box?  The padded slab [lo - pad,
 // hi + pad] becomes parameters (lo - (s + pad)) / d and (hi - (s - pad)) / d
 // with the shifted origins rounded outward; the interval is then widened.
-__device__ __forceinline__ bool slab(const float4& bmin, const float4& bmax, const SegF& g) {
-    float t0x = (bmin.x - g.slo.x) * g.inv.x, t1x = (bmax.x - g.shi.x) * g.inv.x;
-    float t0y = (bmin.y - g.slo.y) * g.inv.y, t1y = (bmax.y - g.shi.y) * g.inv.y;
-    float t0z = (bmin.z - g.slo.z) * g.inv.z, t1z = (bmax.z - g.shi.z) * g.inv.z;
+__device__ __forceinline__ bool slab6(float xlo, float ylo, float zlo, float xhi, float yhi, float zhi,
+                                      const SegF& g) {
+    float t0x = (xlo - g.slo.x) * g.inv.x, t1x = (xhi - g.shi.x) * g.inv.x;
+    float t0y = (ylo - g.slo.y) * g.inv.y, t1y = (yhi - g.shi.y) * g.inv.y;
+    float t0z = (zlo - g.slo.z) * g.inv.z, t1z = (zhi - g.shi.z) * g.inv.z;
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
     float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
     tn = tn - fabsf(tn) * kWiden;
     tf = tf + fabsf(tf) * kWiden;
     return tn <= tf && tn <= 1.0f && tf >= 0.0f;
+}
+__device__ __forceinline__ bool slab(const float4& bmin, const float4& bmax, const SegF& g) {
+    return slab6(bmin.x, bmin.y, bmin.z, bmax.x, bmax.y, bmax.z, g);
 }
 
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -390,7 +396,11 @@ constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^
 // nearest mode visits every pair like the count mode and keeps the certain
 // hit with the smallest upper bound on t; the answer is certain when every
 // other certain hit's lower bound lies above it, else the segment is queued.
-template <int MODE, bool STATS, int STACK, bool BATCHED>
+//
+// WIDE: the node step fetches four-wide nodes (Node4): up to four child boxes
+// per fetch; the first child that passes becomes next and the others are
+// pushed, so children are still visited in leaf order.
+template <int MODE, bool STATS, int STACK, bool BATCHED, bool WIDE>
 __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A, BatchArgs B) {
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -399,6 +409,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
     // BATCHED: the lane's batch and its hierarchy (uniform kernel arguments otherwise)
     int l_batch = 0, l_ntri = 0;
     const Node* l_nodes = nullptr;
+    const Node4* l_nodes4 = nullptr;
     const Tri* l_tris = nullptr;
     unsigned long long visits = 0, tests = 0;
     int wbase = 0, wend = 0;     // warp-uniform chunk [wbase, wend)
@@ -465,6 +476,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
                         dm1 = bd.dmax1;
                         dm2 = bd.dmax2;
                         l_nodes = bd.nodes;
+                        l_nodes4 = bd.nodes4;
                         l_tris = bd.tris;
                         l_ntri = bd.n_tri;
                     }
@@ -502,7 +514,38 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
             continue;
         }
         // node step
-        if (active && next != kDone && next >= 0) {
+        if (WIDE && active && next != kDone && next >= 0) {
+            const float4* p = reinterpret_cast<const float4*>((BATCHED ? l_nodes4 : A.nodes4) + next);
+            const float4 xl = __ldg(p), xh = __ldg(p + 1), yl = __ldg(p + 2), yh = __ldg(p + 3);
+            const float4 zl = __ldg(p + 4), zh = __ldg(p + 5);
+            const int4 rf = __ldg(reinterpret_cast<const int4*>(p + 6));
+            if (STATS) ++visits;
+            const bool h0 = slab6(xl.x, yl.x, zl.x, xh.x, yh.x, zh.x, g);
+            const bool h1 = slab6(xl.y, yl.y, zl.y, xh.y, yh.y, zh.y, g) && rf.y != kEmpty4;
+            const bool h2 = slab6(xl.z, yl.z, zl.z, xh.z, yh.z, zh.z, g) && rf.z != kEmpty4;
+            const bool h3 = slab6(xl.w, yl.w, zl.w, xh.w, yh.w, zh.w, g) && rf.w != kEmpty4;
+            int nx = h3 ? rf.w : kDone;
+            bool over = false;
+#define RSI_PUSH_HIT(HC, RC)                  \
+    if (HC) {                                 \
+        if (nx != kDone) {                    \
+            if (sp < STACK) stack[sp++] = nx; \
+            else over = true;                 \
+        }                                     \
+        nx = (RC);                            \
+    }
+            RSI_PUSH_HIT(h2, rf.z)
+            RSI_PUSH_HIT(h1, rf.y)
+            RSI_PUSH_HIT(h0, rf.x)
+#undef RSI_PUSH_HIT
+            if (over) {   // cannot happen with STACK >= 3 x the four-wide levels; queued
+                raise_error(A.ctr, RSI_ERR_STACK);
+                band = true;
+                stop = true;
+            }
+            next = nx != kDone ? nx : (sp > 0 ? stack[--sp] : kDone);
+        }
+        if (!WIDE && active && next != kDone && next >= 0) {
             float4 lmin, lmax, rmin, rmax;
             load_node(BATCHED ? l_nodes : A.nodes, next, lmin, lmax, rmin, rmax);
             if (STATS) ++visits;
@@ -1152,17 +1195,28 @@ __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->node_visits = c->tri_tests = c->ambiguous = 0;
 }
 
-template <int MODE, bool STATS, int STACK, bool BATCHED>
+template <int MODE, bool STATS, int STACK, bool BATCHED, bool WIDE>
 void launch_fp32(const QueryArgs& A, const BatchArgs& B, int grid, int block, cudaStream_t s) {
-    k_query_fp32<MODE, STATS, STACK, BATCHED><<<grid, block, 0, s>>>(A, B);
+    k_query_fp32<MODE, STATS, STACK, BATCHED, WIDE><<<grid, block, 0, s>>>(A, B);
 }
 
+// Stack entries a traversal needs: the binary walk pushes at most one entry
+// per level (height < STACK); the four-wide walk at most three per four-wide
+// level, and a binary tree of height h has ceil((h + 1) / 2) such levels.
+inline int wide_stack_need(int height) { return 3 * ((height + 2) / 2); }
+inline bool wide_ok(int height) { return wide_stack_need(height) <= 128; }
+
 template <int MODE, bool STATS, bool BATCHED = false>
-void launch_fp32_stack(const QueryArgs& A, int height, int grid, int block, cudaStream_t s,
+void launch_fp32_stack(const QueryArgs& A, int height, bool wide, int grid, int block, cudaStream_t s,
                        const BatchArgs& B = BatchArgs{}) {
-    if (height < 32) launch_fp32<MODE, STATS, 32, BATCHED>(A, B, grid, block, s);
-    else if (height < 64) launch_fp32<MODE, STATS, 64, BATCHED>(A, B, grid, block, s);
-    else launch_fp32<MODE, STATS, 128, BATCHED>(A, B, grid, block, s);
+    if (wide && wide_ok(height)) {
+        const int need = wide_stack_need(height);
+        if (need <= 32) launch_fp32<MODE, STATS, 32, BATCHED, true>(A, B, grid, block, s);
+        else if (need <= 64) launch_fp32<MODE, STATS, 64, BATCHED, true>(A, B, grid, block, s);
+        else launch_fp32<MODE, STATS, 128, BATCHED, true>(A, B, grid, block, s);
+    } else if (height < 32) launch_fp32<MODE, STATS, 32, BATCHED, false>(A, B, grid, block, s);
+    else if (height < 64) launch_fp32<MODE, STATS, 64, BATCHED, false>(A, B, grid, block, s);
+    else launch_fp32<MODE, STATS, 128, BATCHED, false>(A, B, grid, block, s);
 }
 
 template <int MODE, bool BATCHED = false>
@@ -1191,6 +1245,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (h->height >= 127) return fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
     QueryArgs A;
     A.nodes = h->nodes;
+    A.nodes4 = h->nodes4;
     A.tris = h->tris;
     A.n_tri = h->n_tri;
     A.from = d_from;
@@ -1211,6 +1266,9 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
         return fail(RSI_ERR_INVALID_ARG, "rsi_query: block must be a multiple of 32 in [32, 256]");
     if (o.blocks_per_sm < 0) return fail(RSI_ERR_INVALID_ARG, "rsi_query: blocks_per_sm < 0");
+    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 4)
+        return fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2 or 4");
+    const bool wide = o.node_width == 4;
     const int block = o.block > 0 ? o.block : 256;
     const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
     int64_t want = (n + block - 1) / block;
@@ -1240,14 +1298,14 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[0], s));
     if (mode == RSI_ANY_HIT) {
-        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, grid, block, s);
-        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, wide, grid, block, s);
+        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, wide, grid, block, s);
     } else if (mode == RSI_COUNT) {
-        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, grid, block, s);
-        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, wide, grid, block, s);
+        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, wide, grid, block, s);
     } else {
-        if (o.collect_stats) launch_fp32_stack<RSI_NEAREST, true>(A, h->height, grid, block, s);
-        else launch_fp32_stack<RSI_NEAREST, false>(A, h->height, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_NEAREST, true>(A, h->height, wide, grid, block, s);
+        else launch_fp32_stack<RSI_NEAREST, false>(A, h->height, wide, grid, block, s);
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[1], s));
     if (!o.fp32_only) {
@@ -1641,8 +1699,9 @@ void launch_batched(rsi_batch_s* b, const QueryArgs& A, const BatchArgs& B, cuda
     const int bps = b->opt.blocks_per_sm > 0 ? b->opt.blocks_per_sm : 3;
     int64_t want = ((int64_t)b->total + block - 1) / block;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)rsi::device_sm_count() * bps));
-    if (b->opt.collect_stats) launch_fp32_stack<MODE, true, true>(A, b->height, grid, block, s, B);
-    else launch_fp32_stack<MODE, false, true>(A, b->height, grid, block, s, B);
+    const bool wide = b->opt.node_width == 4;
+    if (b->opt.collect_stats) launch_fp32_stack<MODE, true, true>(A, b->height, wide, grid, block, s, B);
+    else launch_fp32_stack<MODE, false, true>(A, b->height, wide, grid, block, s, B);
     if (!b->opt.fp32_only) launch_fp64<MODE, true>(A, b->height, rsi::device_sm_count() * 4, s, B);
 }
 
@@ -1659,6 +1718,8 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
         return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: block must be a multiple of 32 in [32, 256]");
     if (o.blocks_per_sm < 0) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: blocks_per_sm < 0");
+    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 4)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: node_width must be 0, 2 or 4");
     std::vector<int> begins(n_batches + 1, 0);
     std::vector<rsi::BatchDesc> desc(n_batches);
     int height = 0;
@@ -1677,6 +1738,7 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
         height = std::max(height, rb.bvh->height);
         rsi::BatchDesc& d = desc[i];
         d.nodes = rb.bvh->nodes;
+        d.nodes4 = rb.bvh->nodes4;
         d.tris = rb.bvh->tris;
         d.from = rb.d_from;
         d.to = rb.d_to;

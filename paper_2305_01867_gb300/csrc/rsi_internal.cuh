@@ -21,6 +21,21 @@ struct __align__(64) Node {
 };
 static_assert(sizeof(Node) == 64, "node layout");
 
+// Four-wide node of the FP32 traversal: the binary node i at even depth
+// together with its children, so that one fetch of 128 bytes (one L1 line)
+// tests up to four boxes and the segment's chain of dependent fetches is
+// half as long.  Child c's box sits in lane c of the six float4 (structure of
+// arrays), ref[c] is its reference (a four-wide node = the binary index of an
+// even-depth node, ~leaf for a leaf, kEmpty4 for no child).  Stored at the
+// binary index, so slots of odd-depth nodes stay unused.
+struct __align__(128) Node4 {
+    float4 xlo, xhi, ylo, yhi, zlo, zhi;
+    int4 ref;
+    int4 pad;
+};
+static_assert(sizeof(Node4) == 128, "node4 layout");
+constexpr int kEmpty4 = 0x7FFFFFFE;   // no child in this lane of a Node4
+
 // Triangle in leaf (Morton) order: three float4 vertices; v0.w carries the
 // caller's triangle id (int bits).
 struct __align__(16) Tri {
@@ -59,6 +74,7 @@ struct rsi_bvh_s {
     float lo[3], hi[3], dmax[3];
     // packed traversal data
     rsi::Node* nodes = nullptr;   // [max(n_tri - 1, 1)]
+    rsi::Node4* nodes4 = nullptr; // [max(n_tri - 1, 1)], even-depth slots used
     rsi::Tri* tris = nullptr;     // [n_tri]
     // exported build arrays
     void* sorted_keys = nullptr;  // uint32 or uint64 [n_tri]

@@ -54,6 +54,10 @@ def test_host_side_rejections(lib):
     assert rc == -1
     rc = L.lbvh_build(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 4, 31, None, ctypes.byref(h))
     assert rc == -1 and "30 or 63" in lib.last_error()
+    rc = L.lbvh_build_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 4, 30, 2, None, ctypes.byref(h))
+    assert rc == -1 and "tree_builder" in lib.last_error()
+    rc = L.lbvh_build_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 8, 30, 1, None, ctypes.byref(h))
+    assert rc == -2
     rc = L.rsi_query(None, None, None, 0, 0, None, None, None, None, None, None)
     assert rc == -1
     assert L.lbvh_free(None) == 0

@@ -37,10 +37,13 @@ def scene(rsi):
     return items, host
 
 
+@pytest.mark.parametrize("node_width", [2, 4])
 @pytest.mark.parametrize("mode", ["any_hit", "count"])
-def test_batched_equals_single_queries(rsi, scene, mode):
+def test_batched_equals_single_queries(rsi, scene, mode, node_width):
+    """The batched plan (child-pair or four-wide nodes) answers as the
+    single queries (child-pair by default) do."""
     items, host = scene
-    plan = rsi.BatchPlan(items, mode)
+    plan = rsi.BatchPlan(items, mode, node_width=node_width)
     for rep in range(2):   # the graph replays
         plan.run()
         torch.cuda.synchronize()

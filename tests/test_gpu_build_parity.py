@@ -1,6 +1,8 @@
 """GPU build (extent, Morton, sort, radix tree, refit) against the oracle,
 bit for bit, through the C ABI.  Sizes span several sort tiles (4096 keys),
-ragged tails, a single triangle and forced duplicate Morton codes."""
+ragged tails, a single triangle and forced duplicate Morton codes.  Both tree
+constructions are checked: Karras + refit, and the single bottom-up pass
+(Apetrei; Sec. 4.2), which must give the same hierarchy."""
 import numpy as np
 import pytest
 
@@ -50,11 +52,12 @@ def _meshes():
     yield "c2", m.vertices, m.triangles
 
 
+@pytest.mark.parametrize("builder", ["karras", "apetrei"])
 @pytest.mark.parametrize("bits", [30, 63])
-def test_build_bit_exact(rsi, bits):
+def test_build_bit_exact(rsi, bits, builder):
     for name, V, T in _meshes():
         ref = oracle.build_all(V, T, bits=bits)
-        bvh = rsi.LBVH(torch.from_numpy(V).cuda(), torch.from_numpy(T).cuda(), morton_bits=bits)
+        bvh = rsi.LBVH(torch.from_numpy(V).cuda(), torch.from_numpy(T).cuda(), morton_bits=bits, builder=builder)
         got = bvh.export()
         n = len(T)
         assert np.array_equal(got["sorted_keys"], ref["sorted_keys"]), name
@@ -111,3 +114,60 @@ def test_build_from_host_equals_device(rsi):
     b = rsi.LBVH(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda()).export()
     for k in a:
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("bits", [30, 63])
+def test_apetrei_queries_equal_karras(rsi, bits):
+    """The packed traversal nodes and leaf triangles (not exported) are the
+    same too: every answer of both modes agrees on the c1 workload, and the
+    hierarchy stays identical over repeated builds (the range-end slots are
+    reset each time)."""
+    m = W.config_mesh("c1")
+    F, E = W.rays(W.config_rays("c1"), m)
+    dV, dT = torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda()
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    a = rsi.LBVH(dV, dT, morton_bits=bits)
+    ea = a.export()
+    qa = [a.query(dF, dE, mode) for mode in ("any_hit", "count")]
+    for _ in range(3):
+        b = rsi.LBVH(dV, dT, morton_bits=bits, builder="apetrei")
+        eb = b.export()
+        for k in ea:
+            assert np.array_equal(ea[k], eb[k]), k
+        assert a.info()["height"] == b.info()["height"]
+        for mode, ra in zip(("any_hit", "count"), qa):
+            rb = b.query(dF, dE, mode)
+            for k in ra:
+                if isinstance(ra[k], torch.Tensor):
+                    assert torch.equal(ra[k], rb[k]), (mode, k)
+        nb = b.nearest(dF, dE)
+        na = a.nearest(dF, dE)
+        assert torch.equal(na["tri"], nb["tri"]) and torch.equal(na["t"], nb["t"])
+        b.close()
+    a.close()
+
+
+def test_apetrei_rejects_host_inputs(rsi):
+    m = W.config_mesh("c1")
+    with pytest.raises(TypeError):
+        rsi.LBVH(torch.from_numpy(m.vertices), torch.from_numpy(m.triangles), builder="apetrei")
+    with pytest.raises(ValueError):
+        rsi.LBVH(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda(), builder="x")
+
+
+def test_dumps_of_gpu_hierarchy_equal_oracle(rsi):
+    """The text and DOT dumps (Sec. 4.1.1, 4.1.5) of the exported GPU
+    hierarchy are those of the oracle's tree, for both builders."""
+    from paper_2305_01867_gb300 import bvh_dump
+    for name in ("case_study1", "c1"):
+        if name == "c1":
+            m = W.config_mesh("c1")
+            V, T = m.vertices, m.triangles
+        else:
+            g = load("case_study1_sec4_1.txt")
+            V, T = g["vertices"], g["triangles"]
+        ref = oracle.build_all(V, T)
+        for builder in ("karras", "apetrei"):
+            got = rsi.LBVH(torch.from_numpy(V).cuda(), torch.from_numpy(T).cuda(), builder=builder).export()
+            assert bvh_dump.to_text(got, digits=6) == bvh_dump.to_text(ref, digits=6), (name, builder)
+            assert bvh_dump.to_dot(got) == bvh_dump.to_dot(ref), (name, builder)

@@ -66,14 +66,16 @@ def test_case_study1_and_canopy(rsi):
         assert got["amb_hit"].sum() == 0 and got["amb_count"].sum() == 0
 
 
+@pytest.mark.parametrize("node_width", [2, 4])
 @pytest.mark.parametrize("bits", [30, 63])
-def test_c1_full_parity(rsi, bits):
-    """32x32 heightfield, 1e5 segments: every segment checked."""
+def test_c1_full_parity(rsi, bits, node_width):
+    """32x32 heightfield, 1e5 segments: every segment checked, with the
+    child-pair and the four-wide traversal."""
     mesh = W.config_mesh("c1")
     F, E = W.rays(W.config_rays("c1"), mesh)
     ref = oracle.query(mesh.vertices, mesh.triangles, F, E)
     bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles), morton_bits=bits)
-    got = _gpu_both(rsi, bvh, F, E)
+    got = _gpu_both(rsi, bvh, F, E, node_width=node_width)
     nh, nc = _compare(got, ref)
     assert nh > 0.99 * len(F)
     assert np.array_equal(got["hit_from_count"], (got["count"] > 0).astype(np.uint8))
@@ -99,7 +101,8 @@ def test_small_meshes_and_ragged_sizes(rsi):
             E[:, 2] += 0.6
             ref = oracle.query(V, T, F, E)
             bvh = rsi.LBVH(_dev(V), _dev(T))
-            _compare(_gpu_both(rsi, bvh, F, E), ref)
+            for w in (2, 4):
+                _compare(_gpu_both(rsi, bvh, F, E, node_width=w), ref)
 
 
 def test_edge_vertex_and_degenerate_segments(rsi):
@@ -247,3 +250,27 @@ def test_host_path_streams_chunks(rsi):
     # pageable (not page-locked) host memory works too, only slower
     h = bvh.query_host(torch.from_numpy(F), torch.from_numpy(E), "any_hit")
     assert np.array_equal(h["hit"].numpy(), bvh.query(_dev(F), _dev(E), "any_hit")["hit"].cpu().numpy())
+
+
+def test_node_widths_agree_on_c2(rsi):
+    """Child-pair and four-wide traversal give identical outputs, all modes,
+    on 2^21 segments of the c2 workload; a bad width is rejected."""
+    mesh = W.config_mesh("c2")
+    F, E = W.rays(W.config_rays("c2"), mesh, count=1 << 21)
+    bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles))
+    dF, dE = _dev(F), _dev(E)
+    for mode in ("any_hit", "count"):
+        a = bvh.query(dF, dE, mode, node_width=2, stats=True)
+        b = bvh.query(dF, dE, mode, node_width=4, stats=True)
+        for k in ("hit", "count", "ambiguous"):
+            if a[k] is not None:
+                assert torch.equal(a[k], b[k]), (mode, k)
+        # the four-wide walk fetches fewer nodes for the same answers
+        assert b["stats"]["node_visits"] < a["stats"]["node_visits"]
+        assert b["stats"]["band_rays"] == a["stats"]["band_rays"]
+    na, nb = bvh.nearest(dF, dE, node_width=2), bvh.nearest(dF, dE, node_width=4)
+    for k in ("tri", "t", "dist", "ambiguous"):
+        assert torch.equal(na[k], nb[k]), k
+    assert torch.equal(torch.nan_to_num(na["point"], nan=-7.0), torch.nan_to_num(nb["point"], nan=-7.0))
+    with pytest.raises(rsi.RSIError):
+        bvh.query(dF, dE, "any_hit", node_width=3)

@@ -42,35 +42,37 @@ class Mesh:
         return float(self.vertices[:, 2].min())
 
 
-def grid_triangles(n: int) -> np.ndarray:
-    i, j = np.meshgrid(np.arange(n - 1), np.arange(n - 1), indexing="xy")
+def grid_triangles(n: int, ny: int | None = None) -> np.ndarray:
+    ny = n if ny is None else ny
+    i, j = np.meshgrid(np.arange(n - 1), np.arange(ny - 1), indexing="xy")
     i, j = i.ravel(), j.ravel()
     v00 = j * n + i
     v10 = j * n + i + 1
     v11 = (j + 1) * n + i + 1
     v01 = (j + 1) * n + i
-    t = np.empty((2 * (n - 1) ** 2, 3), np.int32)
+    t = np.empty((2 * (n - 1) * (ny - 1), 3), np.int32)
     t[0::2] = np.stack([v00, v10, v11], 1)
     t[1::2] = np.stack([v00, v11, v01], 1)
     return t
 
 
-def heightfield(n: int, seed: int, n_bumps: int = 0, jitter: float = 0.0) -> Mesh:
-    """n x n heightfield: 4 sinusoids 0.1 sin(2 pi (fx x + fy y) + phi) with
-    fx, fy ~ U(-3, 3), phi ~ U(0, 2 pi); n_bumps Gaussian bumps of height
-    U(0.05, 0.2) and width U(0.03, 0.1); xy jitter ~ U(+-jitter cell)."""
+def heightfield(n: int, seed: int, n_bumps: int = 0, jitter: float = 0.0, ny: int | None = None) -> Mesh:
+    """n x n (or n x ny) heightfield over [0, 1]^2: 4 sinusoids
+    0.1 sin(2 pi (fx x + fy y) + phi) with fx, fy ~ U(-3, 3),
+    phi ~ U(0, 2 pi); n_bumps Gaussian bumps of height U(0.05, 0.2) and width
+    U(0.03, 0.1); xy jitter ~ U(+-jitter cell)."""
+    ny = n if ny is None else ny
     rng = np.random.default_rng([seed, 0x4D455348])
     fx, fy = rng.uniform(-3, 3, 4), rng.uniform(-3, 3, 4)
     phi = rng.uniform(0, 2 * math.pi, 4)
     bumps = [(rng.uniform(0, 1), rng.uniform(0, 1), rng.uniform(0.05, 0.2), rng.uniform(0.03, 0.1))
              for _ in range(n_bumps)]
-    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    i, j = np.meshgrid(np.arange(n), np.arange(ny), indexing="xy")
     x = (i.ravel() / (n - 1)).astype(np.float64)
-    y = (j.ravel() / (n - 1)).astype(np.float64)
+    y = (j.ravel() / (ny - 1)).astype(np.float64)
     if jitter > 0:
-        cell = 1.0 / (n - 1)
-        x = x + rng.uniform(-jitter, jitter, x.shape) * cell
-        y = y + rng.uniform(-jitter, jitter, y.shape) * cell
+        x = x + rng.uniform(-jitter, jitter, x.shape) / (n - 1)
+        y = y + rng.uniform(-jitter, jitter, y.shape) / (ny - 1)
     z = np.zeros_like(x)
     for k in range(4):
         z += 0.1 * np.sin(2 * math.pi * (fx[k] * x + fy[k] * y) + phi[k])
@@ -78,7 +80,7 @@ def heightfield(n: int, seed: int, n_bumps: int = 0, jitter: float = 0.0) -> Mes
         z += h * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * s * s))
     V = np.stack([x, y, z], 1).astype(np.float32)
     params = dict(fx=fx.tolist(), fy=fy.tolist(), phi=phi.tolist(), bumps=bumps, jitter=jitter)
-    return Mesh(V, grid_triangles(n), n, seed, params)
+    return Mesh(V, grid_triangles(n, ny), n, seed, params)
 
 
 def _unit_vectors(rng, m):
@@ -278,6 +280,10 @@ def config_mesh(name: str) -> Mesh:
         return heightfield(100, seed=2, n_bumps=8)
     if name == "c3":
         return heightfield(300, seed=3, n_bumps=8, jitter=0.3)
+    if name == "paper":
+        # the paper's test surface has 14,874 vertices and 29,260 triangles
+        # (Sec. 3.3); a 111 x 134 vertex grid has exactly those counts
+        return heightfield(111, seed=6, n_bumps=8, ny=134)
     raise ValueError(name)
 
 
@@ -288,6 +294,8 @@ def config_rays(name: str, n: int | None = None) -> RaySpec:
         return RaySpec("cross_above", n or 10_000_000, seed=2)
     if name == "c3":
         return RaySpec("grazing_mix", n or 100_000_000, seed=3, grazing_frac=0.01)
+    if name == "paper":
+        return RaySpec("cross_above", n or 10_000_000, seed=6)
     raise ValueError(name)
 
 
@@ -295,6 +303,8 @@ CONFIG_DOC = {
     "c1": "32x32-vertex heightfield (1,922 triangles), 1e5 segments z from U(-0.5,0) to U(0.2,0.7)",
     "c2": "100x100-vertex heightfield with 8 bumps (19,602 triangles), 1e7 segments: 50% crossing, 50% above",
     "c3": "300x300-vertex jittered heightfield (178,802 triangles), 1e8 segments, 1% grazing",
+    "paper": "111x134-vertex heightfield with 8 bumps (14,874 vertices, 29,260 triangles, the counts of the "
+             "paper's surface), 1e7 segments: 50% crossing, 50% above",
 }
 
 
