@@ -339,6 +339,7 @@ __global__ void k_refit(const float* __restrict__ V, int64_t nv, const int32_t* 
     tr.v0 = make_float4(v[0][0], v[0][1], v[0][2], __int_as_float(t));
     tr.v1 = make_float4(v[1][0], v[1][1], v[1][2], 0.0f);
     tr.v2 = make_float4(v[2][0], v[2][1], v[2][2], 0.0f);
+    tr.pad = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     tris[j] = tr;
     float* bx = box + 6 * (n - 1 + j);
 #pragma unroll
@@ -478,6 +479,7 @@ __global__ void k_apetrei(const float* __restrict__ V, int64_t nv, const int32_t
     tr.v0 = make_float4(v[0][0], v[0][1], v[0][2], __int_as_float(t));
     tr.v1 = make_float4(v[1][0], v[1][1], v[1][2], 0.0f);
     tr.v2 = make_float4(v[2][0], v[2][1], v[2][2], 0.0f);
+    tr.pad = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     tris[j] = tr;
     float b[6];   // box of the current node: min xyz, max xyz
 #pragma unroll

@@ -199,21 +199,27 @@ __device__ __forceinline__ int tri_fp32(const SegF& g, const Tri& tr, bool want_
     return kBand;
 }
 
+// 32-byte read-only load (sm_100 and later): one lane reads one whole L1
+// sector in a single request instead of two 16-byte halves.  p must be
+// 32-byte aligned (nodes and triangles are 64-byte aligned).
+__device__ __forceinline__ void ld32B(const void* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 __device__ __forceinline__ void load_node(const Node* __restrict__ nodes, int i, float4& a, float4& b, float4& c,
                                           float4& d) {
     const float4* p = reinterpret_cast<const float4*>(nodes + i);
-    a = __ldg(p);
-    b = __ldg(p + 1);
-    c = __ldg(p + 2);
-    d = __ldg(p + 3);
+    ld32B(p, a, b);
+    ld32B(p + 2, c, d);
 }
 
 __device__ __forceinline__ Tri load_tri(const Tri* __restrict__ tris, int j) {
     const float4* p = reinterpret_cast<const float4*>(tris + j);
     Tri t;
-    t.v0 = __ldg(p);
-    t.v1 = __ldg(p + 1);
-    t.v2 = __ldg(p + 2);
+    ld32B(p, t.v0, t.v1);
+    ld32B(p + 2, t.v2, t.pad);
     return t;
 }
 
@@ -400,8 +406,11 @@ constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^
 // WIDE: the node step fetches four-wide nodes (Node4): up to four child boxes
 // per fetch; the first child that passes becomes next and the others are
 // pushed, so children are still visited in leaf order.
+#ifndef RSI_TRAV_MIN_BLOCKS
+#define RSI_TRAV_MIN_BLOCKS 4   // resident 256-thread blocks per SM the register budget is sized for
+#endif
 template <int MODE, bool STATS, int STACK, bool BATCHED, bool WIDE>
-__global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A, BatchArgs B) {
+__global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_query_fp32(QueryArgs A, BatchArgs B) {
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -416,7 +425,11 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
     bool exhausted = false;      // warp-uniform
     int ray = -1;
     SegF g;
-    int next = kDone, slot = -1, sp = 0;
+    // traversal stack: the top entry is cached in a register (`top`, kDone =
+    // empty) so that a pop hands over the next node at once; the entries
+    // below it live in local memory and the load that refills `top` is only
+    // waited for at the following pop
+    int next = kDone, slot = -1, sp = 0, top = kDone;
     int stack[STACK];
     int cnt = 0, plain_cnt = 0;
     bool found = false, band = false, stop = false;
@@ -496,6 +509,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
                         next = (BATCHED ? l_ntri : A.n_tri) == 1 ? ~0 : 0;
                         slot = -1;
                         sp = 0;
+                        top = kDone;
                         cnt = plain_cnt = 0;
                         found = band = stop = false;
                         if (MODE == RSI_NEAREST) {
@@ -516,9 +530,13 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
         // node step
         if (WIDE && active && next != kDone && next >= 0) {
             const float4* p = reinterpret_cast<const float4*>((BATCHED ? l_nodes4 : A.nodes4) + next);
-            const float4 xl = __ldg(p), xh = __ldg(p + 1), yl = __ldg(p + 2), yh = __ldg(p + 3);
-            const float4 zl = __ldg(p + 4), zh = __ldg(p + 5);
-            const int4 rf = __ldg(reinterpret_cast<const int4*>(p + 6));
+            float4 xl, xh, yl, yh, zl, zh, rff, pad;
+            ld32B(p, xl, xh);
+            ld32B(p + 2, yl, yh);
+            ld32B(p + 4, zl, zh);
+            ld32B(p + 6, rff, pad);
+            const int4 rf = make_int4(__float_as_int(rff.x), __float_as_int(rff.y), __float_as_int(rff.z),
+                                      __float_as_int(rff.w));
             if (STATS) ++visits;
             const bool h0 = slab6(xl.x, yl.x, zl.x, xh.x, yh.x, zh.x, g);
             const bool h1 = slab6(xl.y, yl.y, zl.y, xh.y, yh.y, zh.y, g) && rf.y != kEmpty4;
@@ -526,13 +544,16 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
             const bool h3 = slab6(xl.w, yl.w, zl.w, xh.w, yh.w, zh.w, g) && rf.w != kEmpty4;
             int nx = h3 ? rf.w : kDone;
             bool over = false;
-#define RSI_PUSH_HIT(HC, RC)                  \
-    if (HC) {                                 \
-        if (nx != kDone) {                    \
-            if (sp < STACK) stack[sp++] = nx; \
-            else over = true;                 \
-        }                                     \
-        nx = (RC);                            \
+#define RSI_PUSH_HIT(HC, RC)                       \
+    if (HC) {                                      \
+        if (nx != kDone) {                         \
+            if (top != kDone) {                    \
+                if (sp < STACK) stack[sp++] = top; \
+                else over = true;                  \
+            }                                      \
+            top = nx;                              \
+        }                                          \
+        nx = (RC);                                 \
     }
             RSI_PUSH_HIT(h2, rf.z)
             RSI_PUSH_HIT(h1, rf.y)
@@ -543,7 +564,12 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
                 band = true;
                 stop = true;
             }
-            next = nx != kDone ? nx : (sp > 0 ? stack[--sp] : kDone);
+            if (nx != kDone) {
+                next = nx;
+            } else {
+                next = top;
+                top = sp > 0 ? stack[--sp] : kDone;
+            }
         }
         if (!WIDE && active && next != kDone && next >= 0) {
             float4 lmin, lmax, rmin, rmax;
@@ -552,8 +578,9 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
             const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
             const bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
             if (hl && hr) {
-                if (sp < STACK) {
-                    stack[sp++] = rref;
+                if (top == kDone || sp < STACK) {
+                    if (top != kDone) stack[sp++] = top;
+                    top = rref;
                     next = lref;
                 } else {   // cannot happen with STACK > tree height; queued
                     raise_error(A.ctr, RSI_ERR_STACK);
@@ -565,13 +592,15 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : 4) k_query_fp32(QueryArgs A
             } else if (hr) {
                 next = rref;
             } else {
-                next = sp > 0 ? stack[--sp] : kDone;
+                next = top;
+                top = sp > 0 ? stack[--sp] : kDone;
             }
         }
         // park a leaf reference
         if (active && !stop && next < 0 && slot < 0) {
             slot = ~next;
-            next = sp > 0 ? stack[--sp] : kDone;
+            next = top;
+            top = sp > 0 ? stack[--sp] : kDone;
         }
         // leaf phase: all parked leaves of the warp at once
         const unsigned pend = __ballot_sync(kFull, active && slot >= 0);

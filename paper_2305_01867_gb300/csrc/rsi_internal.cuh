@@ -13,8 +13,8 @@
 namespace rsi {
 
 // Packed child-pair node: the boxes of both children next to the two child
-// references, so one 64-byte fetch (two L2 sectors, one L1 line half) lets
-// a segment test both children.  lmin.w holds the left reference, lmax.w the
+// references, so one 64-byte fetch (two 32-byte loads, one L1 sector each)
+// lets a segment test both children.  lmin.w holds the left reference, lmax.w the
 // right one (as int bits): an internal node index >= 0 or ~leaf for a leaf.
 struct __align__(64) Node {
     float4 lmin, lmax, rmin, rmax;
@@ -37,11 +37,12 @@ static_assert(sizeof(Node4) == 128, "node4 layout");
 constexpr int kEmpty4 = 0x7FFFFFFE;   // no child in this lane of a Node4
 
 // Triangle in leaf (Morton) order: three float4 vertices; v0.w carries the
-// caller's triangle id (int bits).
-struct __align__(16) Tri {
-    float4 v0, v1, v2;
+// caller's triangle id (int bits).  Padded to 64 bytes so that a lane fetches
+// it with two 32-byte loads, each reading one whole L1 sector.
+struct __align__(64) Tri {
+    float4 v0, v1, v2, pad;
 };
-static_assert(sizeof(Tri) == 48, "triangle layout");
+static_assert(sizeof(Tri) == 64, "triangle layout");
 
 constexpr uint32_t kLeafTag = 0x80000000u;   // leaf tag of the exported tree
 constexpr float kTau = 1e-6f;                // relative margin of the band
