@@ -60,24 +60,44 @@ def source_hash():
     return hashlib.sha256(q[b:e].encode()).hexdigest()[:16]
 
 
-def traffic_per_launch():
-    """DRAM bytes per launch of the count traversal from the committed ncu
-    summary, if it was taken on the current source (else None)."""
+def profile_values():
+    """Figures of the committed ncu summary of the count traversal, if it was
+    taken on the current source (else {})."""
     try:
         txt = open(TRAFFIC_SUMMARY).read()
     except OSError:
-        return None
+        return {}
     vals = {}
     for line in txt.splitlines():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("source_hash") != source_hash():
+        return {}
+    out = {}
+    for k, v in vals.items():
+        try:
+            out[k] = float(v)
+        except ValueError:
+            pass
+    return out
+
+
+def traffic_per_launch():
+    """DRAM bytes per launch of the count traversal (ncu), or None."""
+    return profile_values().get("dram_bytes_per_launch_full_size")
+
+
+def issue_bound():
+    """The measured L2 / issue bound of the count traversal (ncu, same
+    source): fractions of peak issue slots, L1TEX and L2 throughput."""
+    v = profile_values()
+    if "issue_active_pct" not in v:
         return None
-    try:
-        return float(vals["dram_bytes_per_launch_full_size"])
-    except (KeyError, ValueError):
-        return None
+    return {"kernel": "k_query_fp32<count>", "issue_active_frac": v["issue_active_pct"] / 100,
+            "l1tex_throughput_frac": v.get("l1tex_throughput_pct", float("nan")) / 100,
+            "lts_throughput_frac": v.get("lts_throughput_pct", float("nan")) / 100,
+            "source": "ncu --set full capture of the same kernel source (profiles/k_query_fp32_count_c2.md)"}
 
 
 class ClockSampler:
@@ -629,6 +649,7 @@ def main():
                      else "fallback 6.8 TB/s",
                      "traffic": traffic_per_launch(), "algorithmic_bytes_per_ray": BYTES_PER_RAY_COUNT,
                      "kernel_ms": trav_ms},
+        "l2_issue_bound": issue_bound(),
         "e2e": {"value": ws * n / (e2e_ms / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "matches_device_results": same},
         "gpu_launches": launches,
