@@ -774,6 +774,7 @@ extern "C" int lbvh_free(rsi_bvh_t h) {
     cudaDeviceSynchronize();
     rsi::pool_free(h->nodes, 0);   // base of the single allocation
     rsi::pool_free(h->band_ids, 0);
+    rsi::pool_free(h->pair_mem, 0);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     delete h;
@@ -786,7 +787,7 @@ extern "C" int lbvh_info(rsi_bvh_t h, rsi_bvh_info* out) {
     out->n_vertices = h->n_vert;
     out->morton_bits = h->morton_bits;
     out->height = h->height;
-    out->device_bytes = h->device_bytes + 12 * h->band_cap;
+    out->device_bytes = h->device_bytes + 16 * h->band_cap + h->pair_bytes;
     for (int a = 0; a < 3; ++a) {
         out->extent_lo[a] = h->lo[a];
         out->extent_hi[a] = h->hi[a];

@@ -64,6 +64,8 @@ struct DevCounters {
     unsigned int ext_bits[6];   // extent as order-preserving uint (min xyz, max xyz)
     unsigned int dmax_bits[3];  // largest triangle box side per axis (float bits)
     unsigned int pad1;
+    int pair_count;             // FP64 pass: (segment, triangle) pairs listed
+    int fb_count;               // FP64 pass: segments left to the warp-per-segment kernel
 };
 
 }  // namespace rsi
@@ -88,8 +90,11 @@ struct rsi_bvh_s {
     rsi::DevCounters* ctr = nullptr;
     rsi::DevCounters h_ctr_store{};                // host copy for read-back
     rsi::DevCounters* h_ctr = &h_ctr_store;
-    int32_t* band_ids = nullptr;         // [band_cap] rays queued for FP64
+    int32_t* band_ids = nullptr;         // [band_cap] rays queued for FP64 (then order,
+                                         // proposals and the FP64 fallback list, band_cap each)
     int64_t band_cap = 0;
+    char* pair_mem = nullptr;            // pair lists of the FP64 pass (see PairScratch)
+    int64_t pair_seg_cap = 0, pair_cap = 0, pair_bytes = 0;
     int64_t device_bytes = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // traversal / re-test timing
     bool timed = false;

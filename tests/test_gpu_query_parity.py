@@ -274,3 +274,48 @@ def test_node_widths_agree_on_c2(rsi):
     assert torch.equal(torch.nan_to_num(na["point"], nan=-7.0), torch.nan_to_num(nb["point"], nan=-7.0))
     with pytest.raises(rsi.RSIError):
         bvh.query(dF, dE, "any_hit", node_width=3)
+
+
+def test_fp64_pass_overflow_paths_match_oracle(rsi):
+    """Segments lying in an exactly flat surface: every triangle they cross
+    is an ambiguous pair, so every segment goes to the FP64 pass. 6,000 of
+    them exceed the pass's per-segment list (4,096 entries at this size) and
+    its pair list, and the long ones cross more than 32 triangles: those
+    segments are settled by the warp-per-segment kernel instead. All modes
+    must still equal the oracle, ambiguous marks included."""
+    n = 21
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    V = np.stack([i.ravel() / (n - 1), j.ravel() / (n - 1), np.zeros(n * n)], 1).astype(np.float32)
+    T = W.grid_triangles(n)
+    rng = np.random.default_rng(11)
+    m = 6_000
+    F = np.zeros((m, 3), np.float32)
+    E = np.zeros((m, 3), np.float32)
+    F[:, :2] = rng.uniform(0.02, 0.98, (m, 2))
+    L = np.where(rng.uniform(size=m) < 0.1, 0.9, rng.uniform(0.05, 0.3, m))
+    ang = rng.uniform(0, 2 * np.pi, m)
+    E[:, 0] = F[:, 0] + L * np.cos(ang)
+    E[:, 1] = F[:, 1] + L * np.sin(ang)
+    # and 2,000 steep segments through grid vertices and edge midpoints:
+    # several inclusive crossings at one t (merged to one; the nearest is
+    # the lowest triangle id)
+    k = 2000
+    g = rng.integers(1, 2 * (n - 1), (k, 2)) / (2.0 * (n - 1))
+    tilt = rng.uniform(-0.2, 0.2, (k, 2))
+    F2 = np.concatenate([g - 0.3 * tilt, -0.3 * np.ones((k, 1))], 1).astype(np.float32)
+    E2 = np.concatenate([g + 0.2 * tilt, 0.2 * np.ones((k, 1))], 1).astype(np.float32)
+    F, E = np.concatenate([F, F2]), np.concatenate([E, E2])
+    ref = oracle.query(V, T, F, E)
+    assert ref["count"][m:].sum() > 500 and (ref["near_tri"][m:] >= 0).sum() > 500
+    assert ref["amb_count"].sum() > 4096
+    bvh = rsi.LBVH(_dev(V), _dev(T))
+    got = _gpu_both(rsi, bvh, F, E)
+    _compare(got, ref)
+    st = bvh.query(_dev(F), _dev(E), "count", stats=True)["stats"]
+    assert st["band_rays"] > 4096 and st["device_error"] == 0
+    # ambiguous segments: both sides give the closed-interval reading
+    amb = ref["amb_count"] == 1
+    assert np.array_equal(got["count"][amb], ref["count"][amb])
+    nr = bvh.nearest(_dev(F), _dev(E))
+    assert np.array_equal(nr["tri"].cpu().numpy(), ref["near_tri"])
+    assert np.array_equal(nr["t"].cpu().numpy(), ref["near_t"])
