@@ -405,6 +405,83 @@ def measure_paper_scale(rsi, torch, dev, paper, args):
     return out
 
 
+def measure_precision_c3(rsi, torch, dev, c3, args):
+    """The precision path on c3 (300 x 300 jittered heightfield, 178,802
+    triangles; 1e8 segments, 1 % grazing): both modes with the FP64 re-test
+    of band segments and without it (FP32 only), timed; then the FP64 oracle
+    settles every segment where the two disagree (capped), every segment the
+    GPU marked ambiguous (capped) and a random sample.  Flips are counted on
+    segments the oracle does not mark ambiguous: with the re-test they must
+    be 0, and since the re-tested answer equals the oracle on every checked
+    segment, the FP32-only flips over the whole batch are the disagreements
+    outside the ambiguous set."""
+    import numpy as np
+    import oracle
+    mesh, (F, E) = c3
+    n = F.shape[0]
+    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).to(dev), torch.from_numpy(mesh.triangles).to(dev), morton_bits=63)
+    dF, dE = torch.from_numpy(F).to(dev), torch.from_numpy(E).to(dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "c3: 300x300-vertex jittered heightfield, 8 bumps (178,802 triangles); 1e8 segments, "
+                       "50% crossing / 50% above, 1% grazing (end point within 1e-6 of an edge or vertex, or "
+                       "nearly parallel to a face)", "rays": n, "triangles": int(len(mesh.triangles)), "morton_bits": 63}
+    res = {}
+    for mode in ("any_hit", "count"):
+        for fp32_only in (False, True):
+            key = f"{mode}_{'fp32_only' if fp32_only else 'fp64_retest'}"
+            r = bvh.query(dF, dE, mode, fp32_only=fp32_only)   # warm-up and the result
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                bvh.query(dF, dE, mode, fp32_only=fp32_only, hit=r["hit"], count=r["count"], ambiguous=r["ambiguous"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            st = bvh.query(dF, dE, mode, fp32_only=fp32_only, stats=True)["stats"]
+            val = r["hit"] if mode == "any_hit" else r["count"]
+            res[key] = (val.cpu().numpy(), r["ambiguous"].cpu().numpy())
+            out[key] = {"ms": ms, "rays_per_s": n / (ms / 1e3), "band_rays": st["band_rays"],
+                        "ambiguous": st["ambiguous"]}
+    bvh.close()
+    del dF, dE
+    rng = np.random.default_rng(31)
+    checked = {}
+    for mode in ("any_hit", "count"):
+        a, amb = res[f"{mode}_fp64_retest"]
+        b, _ = res[f"{mode}_fp32_only"]
+        diff = np.flatnonzero(a != b)
+        ambi = np.flatnonzero(amb)
+        cap = args.c3_check
+        pick = [diff if len(diff) <= cap else rng.choice(diff, cap, replace=False),
+                ambi if len(ambi) <= cap // 4 else rng.choice(ambi, cap // 4, replace=False),
+                rng.choice(n, cap // 2, replace=False)]
+        checked[mode] = (diff, ambi, np.unique(np.concatenate(pick)))
+    idx = np.unique(np.concatenate([c[2] for c in checked.values()]))
+    t0 = time.perf_counter()
+    ref = oracle.query(mesh.vertices, mesh.triangles, F[idx], E[idx])
+    oracle_s = time.perf_counter() - t0
+    pos = {int(i): k for k, i in enumerate(idx)}
+    for mode in ("any_hit", "count"):
+        diff, ambi, sel = checked[mode]
+        k = np.array([pos[int(i)] for i in sel])
+        rv, ra = (ref["hit"], ref["amb_hit"]) if mode == "any_hit" else (ref["count"], ref["amb_count"])
+        a, amb = res[f"{mode}_fp64_retest"]
+        b, _ = res[f"{mode}_fp32_only"]
+        ok = ra[k] == 0
+        kd = np.array([pos[int(i)] for i in diff if int(i) in pos], dtype=np.int64)
+        out[mode] = {"checked_by_oracle": int(len(sel)), "disagreements_fp32_only_vs_retest": int(len(diff)),
+                     "disagreements_checked": int(len(kd)),
+                     "flips_with_fp64_retest": int(np.sum(a[sel][ok] != rv[k][ok])),
+                     "ambiguous_marks_differ": int(np.sum(amb[sel] != ra[k])),
+                     "flips_fp32_only_checked": int(np.sum(b[sel][ok] != rv[k][ok])),
+                     "flips_fp32_only_whole_batch": int(np.sum(ref["amb_hit" if mode == "any_hit" else "amb_count"][kd] == 0))
+                     if len(kd) == len(diff) else None,
+                     "gpu_ambiguous": int(len(ambi))}
+    out["oracle"] = {"segments": int(len(idx)), "seconds": oracle_s, "cores": oracle.num_threads()}
+    return out
+
+
 MLP_FLOP_PER_SEGMENT = 2 * (6 * 128 + 128 * 128 + 128 * 256)   # algorithmic (unpadded) multiply-adds x 2
 
 
@@ -488,6 +565,9 @@ def main():
     ap.add_argument("--no-nearest", action="store_true")
     ap.add_argument("--no-builders", action="store_true")
     ap.add_argument("--no-paper-scale", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--c3-rays", type=int, default=100_000_000)
+    ap.add_argument("--c3-check", type=int, default=20_000)
     ap.add_argument("--learned-rays", type=int, default=100_000_000)
     ap.add_argument("--train-rays", type=int, default=10_000_000)
     args = ap.parse_args()
@@ -514,6 +594,10 @@ def main():
     if not args.no_batched and rank == 0:
         jobs = W.batched_meshes(n_meshes=64, seed=4)
         c4 = (jobs, W.rays_many(jobs))           # process pool before any GPU call
+    c3 = None
+    if not args.no_precision and rank == 0:
+        m3 = W.config_mesh("c3")
+        c3 = (m3, W.rays_many([(m3, W.config_rays("c3", args.c3_rays))])[0])
     paper = None
     if not args.no_paper_scale and rank == 0:
         pm = W.config_mesh("paper")
@@ -667,6 +751,9 @@ def main():
                                             c4, reps=max(5, min(args.steps, 20)))
     if paper is not None:
         line["paper_scale_e2e"] = measure_paper_scale(rsi, torch, dev, paper, args)
+    if c3 is not None:
+        line["precision_c3"] = measure_precision_c3(rsi, torch, dev, c3, args)
+        c3 = None
     if not args.no_nearest:
         line["barycentric_c2"] = measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args)
     if c4 is not None:

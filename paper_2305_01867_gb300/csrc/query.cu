@@ -87,8 +87,10 @@ struct PairScratch {
     int32_t* pair_leaf;   // [pair_cap] leaf (triangle in leaf order) of pair i
     double* pair_t;       // [pair_cap] t of pair i when it is an inclusive crossing
     uint8_t* pair_cls;    // [pair_cap] class of pair i, | 4 when inclusive
+    int32_t* hard;        // [pair_cap] pairs the certain FP64 test left undecided
     int32_t* fb_ids;      // [queue capacity] segments left to k_query_fp64
     int seg_cap, pair_cap;
+    int min_queue;        // queues shorter than this go to k_query_fp64 whole
 };
 
 namespace {
@@ -944,7 +946,9 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B, co
 // that keep every lane busy: (1) one warp per queued segment: lane 0 walks
 // the boxes (a light kernel, so many walks run at once) in rounds of up to
 // 32 leaves, the lanes run the FP32 test on each round's leaves side by side
-// and list those that are not a certain miss; (2) one
+// and list those that are not a certain miss -- or, for queues of 32,768
+// segments or more, one thread per segment (divergent, but 32 walks per
+// warp); (2) one
 // thread per listed (segment, triangle) pair classifies it in FP64 -- the
 // certain numerator test, else the definition -- so FP64 instructions run
 // with full warps (a warp's FP64 instruction costs the same however many
@@ -952,6 +956,7 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B, co
 // k_query_fp64 does.  Segments with more than kCandMax candidates, or that
 // do not fit the scratch, go to k_query_fp64 through the fallback list.
 constexpr int kCandMax = 32;
+constexpr int kThreadQueue = 32768;   // from this queue length on, one thread per segment collects
 
 // Band entry gidx (a segment index, global over the batches when batched):
 // its index r within its batch and that batch's hierarchy and outputs.
@@ -988,13 +993,14 @@ __global__ void __launch_bounds__(128) k_band_collect(QueryArgs A, BatchArgs B, 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int nb = *(volatile int*)&A.ctr->band_count;
+    if (nb >= kThreadQueue) return;   // k_band_collect_threads takes long queues
     for (int k = blockIdx.x * kWarps + w; k < nb; k += gridDim.x * kWarps) {
         int64_t r;
         const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
         const float3 s = make_float3(Q.from[3 * r], Q.from[3 * r + 1], Q.from[3 * r + 2]);
         const float3 e = make_float3(Q.to[3 * r], Q.to[3 * r + 1], Q.to[3 * r + 2]);
         const SegF g = make_seg(s, e, Q.dmax0, Q.dmax1, Q.dmax2);
-        bool over = k >= P.seg_cap;
+        bool over = k >= P.seg_cap || nb < P.min_queue;
         bool done = over;
         int nc = 0;
         int node = 0, sp = 0;   // lane 0's walk, resumed every round
@@ -1086,27 +1092,152 @@ __global__ void __launch_bounds__(128) k_band_collect(QueryArgs A, BatchArgs B, 
     }
 }
 
-template <int MODE, bool BATCHED>
-__global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B, PairScratch P) {
-    const int np = min(*(volatile int*)&A.ctr->pair_count, P.pair_cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-        const int k = P.pair_seg[i];
-        if (k < 0) continue;
+// Step 1 for long queues: one thread per queued segment walks the tree and
+// tests the reached leaves itself.
+template <int STACK, bool BATCHED>
+__global__ void __launch_bounds__(128) k_band_collect_threads(QueryArgs A, BatchArgs B, PairScratch P) {
+    const int nb = *(volatile int*)&A.ctr->band_count;
+    if (nb < kThreadQueue) return;   // k_band_collect takes short queues
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
         int64_t r;
         const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
+        int cand[kCandMax];
+        int nc = 0;
+        bool over = k >= P.seg_cap;
+        if (!over) {
+            const float3 s = make_float3(Q.from[3 * r], Q.from[3 * r + 1], Q.from[3 * r + 2]);
+            const float3 e = make_float3(Q.to[3 * r], Q.to[3 * r + 1], Q.to[3 * r + 2]);
+            const SegF g = make_seg(s, e, Q.dmax0, Q.dmax1, Q.dmax2);
+            bool plain;
+            if (Q.n_tri == 1) {
+                if (tri_fp32(g, load_tri(Q.tris, 0), false, plain) != kMiss) cand[nc++] = 0;
+            } else {
+                int node = 0, sp = 0;
+                int stack[STACK];
+                while (true) {
+                    float4 lmin, lmax, rmin, rmax;
+                    load_node(Q.nodes, node, lmin, lmax, rmin, rmax);
+                    const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
+                    bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
+                    if (hl && lref < 0) {
+                        hl = false;
+                        if (tri_fp32(g, load_tri(Q.tris, ~lref), false, plain) != kMiss) {
+                            if (nc == kCandMax) {
+                                over = true;
+                                break;
+                            }
+                            cand[nc++] = ~lref;
+                        }
+                    }
+                    if (hr && rref < 0) {
+                        hr = false;
+                        if (tri_fp32(g, load_tri(Q.tris, ~rref), false, plain) != kMiss) {
+                            if (nc == kCandMax) {
+                                over = true;
+                                break;
+                            }
+                            cand[nc++] = ~rref;
+                        }
+                    }
+                    if (hl && hr) {
+                        if (sp == STACK) {   // k_query_fp64 raises RSI_ERR_STACK for it
+                            over = true;
+                            break;
+                        }
+                        stack[sp++] = rref;
+                        node = lref;
+                    } else if (hl) {
+                        node = lref;
+                    } else if (hr) {
+                        node = rref;
+                    } else if (sp > 0) {
+                        node = stack[--sp];
+                    } else {
+                        break;
+                    }
+                }
+            }
+        }
+        // reserve nc pairs; the counter is read first so that it cannot run far past the capacity
+        if (!over && *(volatile int*)&A.ctr->pair_count <= P.pair_cap - nc) {
+            const int base = atomicAdd(&A.ctr->pair_count, nc);
+            if (base <= P.pair_cap - nc) {
+                for (int i = 0; i < nc; ++i) {
+                    P.pair_seg[base + i] = k;
+                    P.pair_leaf[base + i] = cand[i];
+                }
+                P.seg_off[k] = base;
+                P.seg_cnt[k] = nc;
+                continue;
+            }
+            for (int i = base; i < P.pair_cap && i < base + nc; ++i) P.pair_seg[i] = -1;
+        }
+        if (k < P.seg_cap) P.seg_cnt[k] = -1;
+        P.fb_ids[atomicAdd(&A.ctr->fb_count, 1)] = A.band_ids[k];
+    }
+}
+
+// Step 2a: the certain FP64 test of every pair (no division or square root
+// unless the pair is a certain hit whose t is needed).  In a long pair list
+// the undecided pairs are listed for step 2b, so that the long evaluation of
+// the definition runs in warps made of undecided pairs only; in a short one
+// (fewer than kHardSplit pairs, where the pass is latency-bound) they are
+// settled here.
+constexpr int kHardSplit = 1 << 17;
+template <int MODE, bool BATCHED>
+__global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B, PairScratch P) {
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int np = min(*(volatile int*)&A.ctr->pair_count, P.pair_cap);
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < np; i0 += stride) {
+        const int i = i0 + lane;
+        bool hard = false;
+        if (i < np) {
+            const int k = P.pair_seg[i];
+            if (k >= 0) {
+                int64_t r;
+                const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
+                const D3 sd = {(double)Q.from[3 * r], (double)Q.from[3 * r + 1], (double)Q.from[3 * r + 2]};
+                const D3 ed = {(double)Q.to[3 * r], (double)Q.to[3 * r + 1], (double)Q.to[3 * r + 2]};
+                const Tri tr = load_tri(Q.tris, P.pair_leaf[i]);
+                const D3 a = d3of(tr.v0), b = d3of(tr.v1), c = d3of(tr.v2);
+                int cls = tri_certain64(sd, ed, a, b, c);
+                double t = 0.0;
+                bool incl = cls == kHit;
+                if (cls == kHit && MODE != RSI_ANY_HIT) t = t_of_definition(sd, ed, a, b, c);
+                if (cls == kBand) {
+                    if (np >= kHardSplit) hard = true;
+                    else cls = classify_fp64(sd, ed, a, b, c, t, incl);
+                }
+                P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0));
+                P.pair_t[i] = t;
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, hard);
+        if (m) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&A.ctr->hard_count, __popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (hard) P.hard[base + __popc(m & ((1u << lane) - 1u))] = i;
+        }
+    }
+}
+
+// Step 2b: the definition itself (classify_fp64) for the undecided pairs.
+template <bool BATCHED>
+__global__ void __launch_bounds__(256) k_band_classify_hard(QueryArgs A, BatchArgs B, PairScratch P) {
+    const int nh = *(volatile int*)&A.ctr->hard_count;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += gridDim.x * blockDim.x) {
+        const int i = P.hard[h];
+        int64_t r;
+        const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[P.pair_seg[i]], r);
         const D3 sd = {(double)Q.from[3 * r], (double)Q.from[3 * r + 1], (double)Q.from[3 * r + 2]};
         const D3 ed = {(double)Q.to[3 * r], (double)Q.to[3 * r + 1], (double)Q.to[3 * r + 2]};
         const Tri tr = load_tri(Q.tris, P.pair_leaf[i]);
-        const D3 a = d3of(tr.v0), b = d3of(tr.v1), c = d3of(tr.v2);
-        int cls = tri_certain64(sd, ed, a, b, c);
-        bool incl = false;
         double t = 0.0;
-        if (cls == kHit) {
-            incl = true;
-            if (MODE != RSI_ANY_HIT) t = t_of_definition(sd, ed, a, b, c);
-        } else if (cls == kBand) {
-            cls = classify_fp64(sd, ed, a, b, c, t, incl);
-        }
+        bool incl = false;
+        const int cls = classify_fp64(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2), t, incl);
         P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0));
         P.pair_t[i] = t;
     }
@@ -1475,6 +1606,7 @@ __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->n_confirmed = 0;
     c->pair_count = 0;
     c->fb_count = 0;
+    c->hard_count = 0;
     if (ready != ~0ull) c->ready = ready;   // ~0: a streaming plan, fed by posts
     c->error = 0;
     c->node_visits = c->tri_tests = c->ambiguous = 0;
@@ -1516,26 +1648,39 @@ void launch_fp64(const QueryArgs& A, int height, int grid, cudaStream_t s, const
 
 // The FP64 pass over the queued segments: pair-parallel when scratch P is
 // given (collect, classify, combine, then k_query_fp64 for the fallback
-// list), else k_query_fp64 for every queued segment.  The boolean mode keeps
-// k_query_fp64: it queues ~10x fewer segments (c2: 1,330 of 1e7 against
-// 11,824 in count mode), where the overlapped, early-exiting warps of
-// k_query_fp64 finish first (c2: 0.115 against 0.151 ms; count mode 0.651
-// against 0.283 ms).
+// list), else k_query_fp64 for every queued segment.  In the boolean mode
+// a queue shorter than 2,048 segments goes to k_query_fp64 whole (the
+// collect kernel decides on the device): there its overlapped,
+// early-exiting warps finish first (c2: 1,330 queued, 0.115 against
+// 0.151 ms), while long queues favour the pairs (c3: 4e5 queued).
 template <int MODE, bool BATCHED = false>
-void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P, cudaStream_t s,
+void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P0, cudaStream_t s,
                       const BatchArgs& B = BatchArgs{}) {
     const int grid = device_sm_count() * 4;
-    if (!P || MODE == RSI_ANY_HIT) {
+    if (!P0) {
         launch_fp64<MODE, BATCHED>(A, height, grid, s, &A.ctr->band_count, B);
         return;
     }
+    PairScratch Pm = *P0;
+    Pm.min_queue = MODE == RSI_ANY_HIT ? 2048 : 0;
+    const PairScratch* P = &Pm;
+    // step 1: both collect kernels are launched; the queue length (on the
+    // device) lets exactly one of them work
     const int cgrid = device_sm_count() * 16;   // one warp per queued segment, 4 per block
-    if (height < 32) k_band_collect<32, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
-    else if (height < 64) k_band_collect<64, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
-    else k_band_collect<128, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+    if (height < 32) {
+        k_band_collect<32, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+        k_band_collect_threads<32, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+    } else if (height < 64) {
+        k_band_collect<64, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+        k_band_collect_threads<64, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+    } else {
+        k_band_collect<128, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+        k_band_collect_threads<128, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+    }
     k_band_classify<MODE, BATCHED><<<device_sm_count() * 8, 256, 0, s>>>(A, B, *P);
+    k_band_classify_hard<BATCHED><<<device_sm_count() * 4, 256, 0, s>>>(A, B, *P);
     k_band_reduce<MODE, BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
-    note_launches(3);
+    note_launches(5);
     QueryArgs F = A;
     F.band_ids = P->fb_ids;
     launch_fp64<MODE, BATCHED>(F, height, grid, s, &A.ctr->fb_count, B);
@@ -1646,7 +1791,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
 void pair_sizes(int64_t q, int64_t& seg_cap, int64_t& pair_cap, size_t& bytes) {
     seg_cap = std::min<int64_t>(std::max<int64_t>(q / 16, 4096), 1 << 24);
     pair_cap = 4 * seg_cap;
-    bytes = 8 * (size_t)seg_cap + 17 * (size_t)pair_cap + 6 * 256;   // + alignment of the pieces
+    bytes = 8 * (size_t)seg_cap + 21 * (size_t)pair_cap + 7 * 256;   // + alignment of the pieces
 }
 
 PairScratch carve_pairs(char* mem, int64_t seg_cap, int64_t pair_cap, int32_t* fb_ids) {
@@ -1663,10 +1808,13 @@ PairScratch carve_pairs(char* mem, int64_t seg_cap, int64_t pair_cap, int32_t* f
     o += al(4 * (size_t)pair_cap);
     P.pair_leaf = reinterpret_cast<int32_t*>(mem + o);
     o += al(4 * (size_t)pair_cap);
+    P.hard = reinterpret_cast<int32_t*>(mem + o);
+    o += al(4 * (size_t)pair_cap);
     P.pair_cls = reinterpret_cast<uint8_t*>(mem + o);
     P.fb_ids = fb_ids;
     P.seg_cap = (int)seg_cap;
     P.pair_cap = (int)pair_cap;
+    P.min_queue = 0;
     return P;
 }
 
@@ -2206,8 +2354,7 @@ extern "C" int rsi_query_batched(rsi_batch_t b, void* stream) {
         RSI_CUDA_TRY(cudaEventRecord(b->reset_ev, (cudaStream_t)stream));
     }
     RSI_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
-    // reset, traversal, then the FP64 pass: 1 kernel (boolean) or 4 (count)
-    rsi::note_launches(b->opt.fp32_only ? 2 : (b->mode == RSI_ANY_HIT ? 3 : 6));
+    rsi::note_launches(b->opt.fp32_only ? 2 : 8);   // reset, traversal, the 6 kernels of the FP64 pass
     return RSI_OK;
 }
 

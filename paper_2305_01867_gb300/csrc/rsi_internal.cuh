@@ -66,6 +66,8 @@ struct DevCounters {
     unsigned int pad1;
     int pair_count;             // FP64 pass: (segment, triangle) pairs listed
     int fb_count;               // FP64 pass: segments left to the warp-per-segment kernel
+    int hard_count;             // FP64 pass: pairs the certain FP64 test left undecided
+    int pad2;
 };
 
 }  // namespace rsi

@@ -276,19 +276,21 @@ def test_node_widths_agree_on_c2(rsi):
         bvh.query(dF, dE, "any_hit", node_width=3)
 
 
-def test_fp64_pass_overflow_paths_match_oracle(rsi):
+@pytest.mark.parametrize("m", [6_000, 40_000])
+def test_fp64_pass_overflow_paths_match_oracle(rsi, m):
     """Segments lying in an exactly flat surface: every triangle they cross
-    is an ambiguous pair, so every segment goes to the FP64 pass. 6,000 of
-    them exceed the pass's per-segment list (4,096 entries at this size) and
-    its pair list, and the long ones cross more than 32 triangles: those
-    segments are settled by the warp-per-segment kernel instead. All modes
-    must still equal the oracle, ambiguous marks included."""
+    is an ambiguous pair, so every segment goes to the FP64 pass. 6,000 (a
+    queue the warp-per-segment collect takes) or 40,000 (the thread-per-
+    segment collect) of them exceed the pass's per-segment list (4,096
+    entries at these sizes) and its pair list, and the long ones cross more
+    than 32 triangles: those segments are settled by the warp-per-segment
+    kernel instead. All modes must still equal the oracle, ambiguous marks
+    included."""
     n = 21
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
     V = np.stack([i.ravel() / (n - 1), j.ravel() / (n - 1), np.zeros(n * n)], 1).astype(np.float32)
     T = W.grid_triangles(n)
     rng = np.random.default_rng(11)
-    m = 6_000
     F = np.zeros((m, 3), np.float32)
     E = np.zeros((m, 3), np.float32)
     F[:, :2] = rng.uniform(0.02, 0.98, (m, 2))
@@ -319,3 +321,33 @@ def test_fp64_pass_overflow_paths_match_oracle(rsi):
     nr = bvh.nearest(_dev(F), _dev(E))
     assert np.array_equal(nr["tri"].cpu().numpy(), ref["near_tri"])
     assert np.array_equal(nr["t"].cpu().numpy(), ref["near_t"])
+
+
+def test_fp64_pass_long_pair_list_matches_oracle(rsi):
+    """6e5 segments over an exactly flat surface, 1e5 of them lying in it:
+    the FP64 pass lists more than 2^17 (segment, triangle) pairs, so the
+    undecided ones are settled in a separate pass of their own; the rest
+    lie above the surface. Every mode equals the oracle on every segment."""
+    n = 21
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    V = np.stack([i.ravel() / (n - 1), j.ravel() / (n - 1), np.zeros(n * n)], 1).astype(np.float32)
+    T = W.grid_triangles(n)
+    rng = np.random.default_rng(12)
+    m, k = 600_000, 100_000
+    F = rng.uniform(0.0, 1.0, (m, 3)).astype(np.float32)
+    E = (F + rng.uniform(-0.05, 0.05, (m, 3))).astype(np.float32)
+    F[:, 2] += 0.5
+    E[:, 2] = F[:, 2] + 0.1
+    L = rng.uniform(0.05, 0.3, k)
+    ang = rng.uniform(0, 2 * np.pi, k)
+    F[:k, 2] = 0.0
+    E[:k, 0] = F[:k, 0] + L * np.cos(ang)
+    E[:k, 1] = F[:k, 1] + L * np.sin(ang)
+    E[:k, 2] = 0.0
+    ref = oracle.query(V, T, F, E)
+    bvh = rsi.LBVH(_dev(V), _dev(T))
+    _compare(_gpu_both(rsi, bvh, F, E), ref)
+    st = bvh.query(_dev(F), _dev(E), "count", stats=True)["stats"]
+    assert st["band_rays"] >= 0.9 * k and st["device_error"] == 0
+    nr = bvh.nearest(_dev(F), _dev(E))
+    assert np.array_equal(nr["tri"].cpu().numpy(), ref["near_tri"])
