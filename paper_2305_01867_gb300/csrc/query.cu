@@ -1315,39 +1315,79 @@ __global__ void __launch_bounds__(128) k_band_reduce(QueryArgs A, BatchArgs B, P
 // passes chose: t by the definition's own FP64 operations, the point
 // s + t (e - s) and the distance t |e - s| from the start point, each rounded
 // once to FP32; the leaf is replaced by the caller's triangle index.  No hit:
-// triangle -1, t -1, distance -1, point NaN.
+// triangle -1, t -1, distance -1, point NaN.  Two kernels: the first writes
+// the segments without a hit and lists the hitting ones (in A.band_ids, free
+// once the FP64 pass is over); the second evaluates the listed segments in
+// full warps -- GB300 charges a warp's FP64 instruction the same for 1 or 32
+// active lanes, and the hits are spread over the batch.
+__global__ void __launch_bounds__(256) k_nearest_list(QueryArgs A, float* __restrict__ t_out,
+                                                      float* __restrict__ point, float* __restrict__ dist) {
+    __shared__ int s_warp[8];   // hits per warp, then the warp's first list slot
+    __shared__ int s_base;
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // the block's 256 segments per round (block-uniform loop: one list
+    // reservation per block and round, so the counter is not a hot spot)
+    for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x; b0 < A.n_rays; b0 += stride) {
+        const int64_t r = b0 + threadIdx.x;
+        bool hit = false;
+        if (r < A.n_rays) {
+            int j = A.near[r];
+            if (j >= A.n_tri) {   // no pass wrote this segment: reported, never dereferenced
+                raise_error(A.ctr, RSI_ERR_INDEX);
+                A.near[r] = j = -1;
+            }
+            hit = j >= 0;
+            if (!hit) {
+                const float qnan = __int_as_float(0x7fc00000);
+                if (t_out) t_out[r] = -1.0f;
+                if (dist) dist[r] = -1.0f;
+                if (point) {
+                    point[3 * r] = qnan;
+                    point[3 * r + 1] = qnan;
+                    point[3 * r + 2] = qnan;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, hit);
+        if (lane == 0) s_warp[w] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                const int c = s_warp[k];
+                s_warp[k] = tot;
+                tot += c;
+            }
+            s_base = tot ? atomicAdd(&A.ctr->n_finish, tot) : 0;
+        }
+        __syncthreads();
+        if (hit) A.band_ids[s_base + s_warp[w] + __popc(m & ((1u << lane) - 1u))] = (int32_t)r;
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256) k_nearest_finish(QueryArgs A, float* __restrict__ t_out,
                                                         float* __restrict__ point, float* __restrict__ dist) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n_rays;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        int j = A.near[r];
-        const float qnan = __int_as_float(0x7fc00000);
-        float tf = -1.0f, df = -1.0f, px = qnan, py = qnan, pz = qnan;
-        if (j >= A.n_tri) {   // no pass wrote this segment: reported, never dereferenced
-            raise_error(A.ctr, RSI_ERR_INDEX);
-            A.near[r] = j = -1;
-        }
-        if (j >= 0) {
-            const Tri tr = load_tri(A.tris, j);
-            const D3 sd = {(double)A.from[3 * r], (double)A.from[3 * r + 1], (double)A.from[3 * r + 2]};
-            const D3 ed = {(double)A.to[3 * r], (double)A.to[3 * r + 1], (double)A.to[3 * r + 2]};
-            const double t = t_of_definition(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2));
-            const D3 d = dsub(ed, sd);
-            const D3 p = dadd(sd, dscale(d, t));
-            tf = __double2float_rn(t);
-            px = __double2float_rn(p.x);
-            py = __double2float_rn(p.y);
-            pz = __double2float_rn(p.z);
-            df = __double2float_rn(__dmul_rn(t, dnorm(d)));
-            A.near[r] = __float_as_int(tr.v0.w);
-        }
-        if (t_out) t_out[r] = tf;
-        if (dist) dist[r] = df;
+    const int nf = *(volatile int*)&A.ctr->n_finish;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        const int64_t r = A.band_ids[i];
+        const int j = A.near[r];
+        const Tri tr = load_tri(A.tris, j);
+        const D3 sd = {(double)A.from[3 * r], (double)A.from[3 * r + 1], (double)A.from[3 * r + 2]};
+        const D3 ed = {(double)A.to[3 * r], (double)A.to[3 * r + 1], (double)A.to[3 * r + 2]};
+        const double t = t_of_definition(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2));
+        const D3 d = dsub(ed, sd);
+        const D3 p = dadd(sd, dscale(d, t));
+        if (t_out) t_out[r] = __double2float_rn(t);
+        if (dist) dist[r] = __double2float_rn(__dmul_rn(t, dnorm(d)));
         if (point) {
-            point[3 * r] = px;
-            point[3 * r + 1] = py;
-            point[3 * r + 2] = pz;
+            point[3 * r] = __double2float_rn(p.x);
+            point[3 * r + 1] = __double2float_rn(p.y);
+            point[3 * r + 2] = __double2float_rn(p.z);
         }
+        A.near[r] = __float_as_int(tr.v0.w);
     }
 }
 
@@ -1607,6 +1647,7 @@ __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->pair_count = 0;
     c->fb_count = 0;
     c->hard_count = 0;
+    c->n_finish = 0;
     if (ready != ~0ull) c->ready = ready;   // ~0: a streaming plan, fed by posts
     c->error = 0;
     c->node_visits = c->tri_tests = c->ambiguous = 0;
@@ -1774,9 +1815,10 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
         else launch_fp64_pass<RSI_NEAREST>(A, h->height, pairs, s);
     }
     if (mode == RSI_NEAREST) {
-        k_nearest_finish<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count() * 8)),
-                           256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist);
-        note_launches(1);
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count() * 8));
+        k_nearest_list<<<g, 256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist);
+        k_nearest_finish<<<g, 256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist);
+        note_launches(2);
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[2], s));
     note_launches(2);   // k_reset_query, k_query_fp32 (the FP64 pass counts its own)

@@ -67,7 +67,7 @@ struct DevCounters {
     int pair_count;             // FP64 pass: (segment, triangle) pairs listed
     int fb_count;               // FP64 pass: segments left to the warp-per-segment kernel
     int hard_count;             // FP64 pass: pairs the certain FP64 test left undecided
-    int pad2;
+    int n_finish;               // nearest mode: hitting segments listed for the FP64 finish
 };
 
 }  // namespace rsi
