@@ -143,6 +143,18 @@ __device__ __forceinline__ bool slab6(float xlo, float ylo, float zlo, float xhi
 __device__ __forceinline__ bool slab(const float4& bmin, const float4& bmax, const SegF& g) {
     return slab6(bmin.x, bmin.y, bmin.z, bmax.x, bmax.y, bmax.z, g);
 }
+// The same test, also giving the length of the parameter interval inside the box.
+__device__ __forceinline__ bool slab_len(const float4& bmin, const float4& bmax, const SegF& g, float& len) {
+    float t0x = (bmin.x - g.slo.x) * g.inv.x, t1x = (bmax.x - g.shi.x) * g.inv.x;
+    float t0y = (bmin.y - g.slo.y) * g.inv.y, t1y = (bmax.y - g.shi.y) * g.inv.y;
+    float t0z = (bmin.z - g.slo.z) * g.inv.z, t1z = (bmax.z - g.shi.z) * g.inv.z;
+    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
+    tn = tn - fabsf(tn) * kWiden;
+    tf = tf + fabsf(tf) * kWiden;
+    len = fminf(tf, 1.0f) - fmaxf(tn, 0.0f);
+    return tn <= tf && tn <= 1.0f && tf >= 0.0f;
+}
 
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float3 f3(const float4& v) { return make_float3(v.x, v.y, v.z); }
@@ -403,7 +415,10 @@ __device__ __noinline__ bool wait_ready(DevCounters* c, unsigned long long need,
 constexpr int kLeafMin = 12;     // run the triangle tests once this many lanes hold one
 constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^30)
 
-// Warp-coherent persistent traversal with deferred leaf tests.  Each lane
+// Warp-coherent persistent traversal with deferred leaf tests.  In the
+// boolean mode, when both children pass, the walk goes first into the one
+// whose box holds the longer stretch of the segment (a hit there is more
+// likely, and the first certain hit ends the segment).  Each lane
 // holds its next reference (internal node >= 0, leaf ~j < 0, or kDone) and a
 // one-entry leaf slot.  Every iteration a lane whose next reference is an
 // internal node fetches it and tests both child boxes (the nearer-listed hit
@@ -591,8 +606,21 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
             float4 lmin, lmax, rmin, rmax;
             load_node(BATCHED ? l_nodes : A.nodes, next, lmin, lmax, rmin, rmax);
             if (STATS) ++visits;
-            const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
-            const bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
+            int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
+            bool hl, hr;
+            if (MODE == RSI_ANY_HIT) {   // boolean: the child the segment spends longer in first
+                float ll, lr;
+                hl = slab_len(lmin, lmax, g, ll);
+                hr = slab_len(rmin, rmax, g, lr);
+                if (hl && hr && lr > ll) {
+                    const int tmp = lref;
+                    lref = rref;
+                    rref = tmp;
+                }
+            } else {
+                hl = slab(lmin, lmax, g);
+                hr = slab(rmin, rmax, g);
+            }
             if (hl && hr) {
                 if (top == kDone || sp < STACK) {
                     if (top != kDone) stack[sp++] = top;
