@@ -295,10 +295,16 @@ def measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args):
     hits = int((r["tri"] >= 0).sum())
     bvh.close()
 
+    # page-locked host arrays for the compacted result (sized for every segment)
+    h_out = (torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory(),
+             torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, 3, dtype=torch.float32).pin_memory())
+
     def paper_style():
         b = rsi.LBVH(pV.to(dev, non_blocking=True), pT.to(dev, non_blocking=True))
-        rays, dist, tri, point = b.barycentric(pF.to(dev, non_blocking=True), pE.to(dev, non_blocking=True))
-        out = (rays.cpu(), dist.cpu(), tri.cpu(), point.cpu())
+        res = b.barycentric(pF.to(dev, non_blocking=True), pE.to(dev, non_blocking=True))
+        k = res[0].shape[0]
+        out = tuple(h[:k].copy_(r, non_blocking=True) for h, r in zip(h_out, res))
+        torch.cuda.synchronize()
         b.close()
         return out
 
@@ -314,7 +320,7 @@ def measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args):
             "traverse_ms": statistics.median(trav), "fp64_and_finish_ms": statistics.median(fin),
             "hitting_rays": hits, "band_rays": st["band_rays"], "ambiguous": st["ambiguous"],
             "paper_style_e2e_ms": e2e,
-            "paper_style_e2e": "pinned host segments and mesh -> build -> nearest -> compaction -> host "
+            "paper_style_e2e": "pinned host segments and mesh -> build -> nearest -> compaction -> pinned host "
                                "(rays, distances, triangles, points)"}
 
 
@@ -381,9 +387,15 @@ def measure_paper_scale(rsi, torch, dev, paper, args):
         b.query_host(pF, pE, "count", count=hc, ambiguous=ha)
         b.close()
 
+    h_out = (torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.float32).pin_memory(),
+             torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, 3, dtype=torch.float32).pin_memory())
+
     def barycentric():
         b = rsi.LBVH(pV.to(dev, non_blocking=True), pT.to(dev, non_blocking=True))
-        out = [x.cpu() for x in b.barycentric(pF.to(dev, non_blocking=True), pE.to(dev, non_blocking=True))]
+        res = b.barycentric(pF.to(dev, non_blocking=True), pE.to(dev, non_blocking=True))
+        k = res[0].shape[0]
+        out = [h[:k].copy_(r, non_blocking=True) for h, r in zip(h_out, res)]
+        torch.cuda.synchronize()
         b.close()
         return out
 

@@ -241,10 +241,15 @@ int rsi_nearest_compact(const int32_t* d_tri, const float* d_dist, const float* 
                         int64_t* n_hits, void* stream);
 
 /*
- * As rsi_query with segments and results in HOST memory.  The segments are
- * streamed to the device in chunks of 2^21 and the results back, with copies
- * and traversal overlapped on internal streams; returns after the results are
- * in host memory.  Page-locked host buffers give asynchronous copies.  The
+ * As rsi_query with segments and results in HOST memory; returns after the
+ * results are in host memory.  Batches of up to 2^26 segments are staged
+ * whole on the device (30 B per segment, kept for later calls): the segments
+ * are copied in chunks of 2^21 on an internal stream while the FP32
+ * traversal of each copied chunk runs on `stream`, then one FP64 re-test
+ * settles the whole batch and the results are copied back.  Larger batches,
+ * and queries with opt->ray_sort_tile, stream chunks of 2^21 through two
+ * recycled staging slots (copies and traversal overlapped; the re-test runs
+ * per chunk).  Page-locked host buffers give asynchronous copies.  The
  * staging is shared by all handles of a device: concurrent host-buffer
  * queries on one device run one after the other.
  */

@@ -312,7 +312,7 @@ class LBVH:
         return out
 
     def query_host(self, ray_from, ray_to, mode="any_hit", *, fp32_only=False, stats=False, hit=None, count=None,
-                   ambiguous=None, want_ambiguous=True, stream=None):
+                   ambiguous=None, want_ambiguous=True, ray_sort_tile=0, stream=None):
         """As query() with host (preferably pinned) tensors; blocks until the
         results are in host memory."""
         import torch
@@ -326,7 +326,7 @@ class LBVH:
             count = torch.empty(n, dtype=torch.int32)
         if ambiguous is None and want_ambiguous:
             ambiguous = torch.empty(n, dtype=torch.uint8)
-        opt = Options(int(fp32_only), 0, 0, int(stats), 0, 0, 0)
+        opt = Options(int(fp32_only), 0, 0, int(stats), 0, 0, int(ray_sort_tile))
         st = Stats()
         check(lib.rsi_query_host(self._h, _ptr(ray_from), _ptr(ray_to), n, m, ctypes.byref(opt), _ptr(hit),
                                  _ptr(count), _ptr(ambiguous), ctypes.byref(st), _stream(stream)))

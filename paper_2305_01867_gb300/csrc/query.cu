@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
                     }
                     wbase = (int)b;
                     wend = min(wbase + kWarpChunk, n_rays);
-                    if (BATCHED && B.streamed) {   // device work queue fed by the host
+                    if (B.streamed) {   // device work queue fed by the host (batched plans, host-buffer queries)
                         bool ok = true;
                         if (lane == 0) ok = wait_ready(A.ctr, (unsigned long long)wend, B.timeout_ns);
                         if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) {
@@ -2046,16 +2046,23 @@ extern "C" int rsi_nearest_compact(const int32_t* d_tri, const float* d_dist, co
 namespace {
 constexpr int64_t kHostChunk = 1 << 21;
 
-int host_setup(rsi::DeviceCtx* c, int64_t chunk, int64_t n_chunks) {
-    if (!c->st_in) {
-        RSI_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_in, cudaStreamNonBlocking));
-        RSI_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_out, cudaStreamNonBlocking));
-        for (int i = 0; i < 2; ++i) {
-            RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming));
-            RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_q[i], cudaEventDisableTiming));
-            RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming));
-        }
+// The copy streams and events of host-buffer queries (each made once).
+int host_streams(rsi::DeviceCtx* c) {
+    if (!c->st_in) RSI_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_in, cudaStreamNonBlocking));
+    if (!c->st_out) RSI_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_out, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+        if (!c->ev_in[i]) RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming));
+        if (!c->ev_q[i]) RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_q[i], cudaEventDisableTiming));
+        if (!c->ev_out[i]) RSI_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming));
     }
+    for (cudaEvent_t& e : c->ev_chunk)
+        if (!e) RSI_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return RSI_OK;
+}
+
+int host_setup(rsi::DeviceCtx* c, int64_t chunk, int64_t n_chunks) {
+    int rc = host_streams(c);
+    if (rc) return rc;
     if (c->stage_chunk < chunk) {
         if (c->stage) {
             RSI_CUDA_TRY(cudaDeviceSynchronize());
@@ -2087,6 +2094,141 @@ int host_setup(rsi::DeviceCtx* c, int64_t chunk, int64_t n_chunks) {
 }
 }  // namespace
 
+namespace {
+using namespace rsi;   // the kernels and launchers above
+// Whole-batch host-buffer query (batches of up to kHostWhole segments): the
+// segments are copied in chunks on st_in, each chunk followed by a post of
+// the number of segments now on the device; one persistent FP32 traversal
+// on the caller's stream takes segments as they are posted (a device work
+// queue with bounded waits, as in streaming batched plans), so copies and
+// traversal overlap without a kernel tail per chunk; one FP64 pass then
+// settles the whole queue and the results are copied out.
+constexpr int64_t kHostWhole = (int64_t)1 << 26;
+
+int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, int mode, const rsi_options& o,
+               uint8_t* h_hit, int32_t* h_count, uint8_t* h_amb, rsi_stats* stats, cudaStream_t s,
+               rsi::DeviceCtx* c) {
+    if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: block must be a multiple of 32 in [32, 256]");
+    if (o.blocks_per_sm < 0) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: blocks_per_sm < 0");
+    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 4)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2 or 4");
+    if (h->height >= 127) return rsi::fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
+    int rc = rsi::ensure_band_capacity(h, n, s);
+    if (rc) return rc;
+    if (c->whole_cap < n) {
+        if (c->whole) {
+            RSI_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(c->whole);
+            c->whole = nullptr;
+            c->whole_cap = 0;
+        }
+        if (cudaMalloc(&c->whole, 30 * (size_t)n + 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return rsi::fail(RSI_ERR_OOM, "rsi_query_host: staging allocation failed");
+        }
+        c->whole_cap = n;
+    }
+    rc = host_streams(c);
+    if (rc) return rc;
+    if (!c->h_chunk_ctr) {
+        if (cudaMallocHost(&c->h_chunk_ctr, sizeof(rsi::DevCounters) * 64) != cudaSuccess) {
+            cudaGetLastError();
+            return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
+        }
+        c->h_chunk_cap = 64;
+    }
+    if (!c->h_ready && cudaMallocHost(&c->h_ready, 64 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_ready = nullptr;
+        return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    float* df = reinterpret_cast<float*>(c->whole);
+    float* dt = reinterpret_cast<float*>(c->whole + al(12 * (size_t)n));
+    int32_t* dc = reinterpret_cast<int32_t*>(c->whole + 2 * al(12 * (size_t)n));
+    uint8_t* dh = reinterpret_cast<uint8_t*>(c->whole + 2 * al(12 * (size_t)n) + al(4 * (size_t)n));
+    uint8_t* da = dh + al((size_t)n);
+    const int64_t chunk = std::max<int64_t>(kHostChunk, (n + 63) / 64);
+    const int n_chunks = (int)((n + chunk - 1) / chunk);
+    // empty the work queue, then start the copies once the caller's stream
+    // is done with the previous call's staging
+    RSI_CUDA_TRY(cudaMemsetAsync(&h->ctr->ready, 0, sizeof(unsigned long long), s));
+    RSI_CUDA_TRY(cudaEventRecord(c->ev_chunk[0], s));
+    RSI_CUDA_TRY(cudaStreamWaitEvent(c->st_in, c->ev_chunk[0], 0));
+    for (int k = 0; k < n_chunks; ++k) {
+        const int64_t r0 = k * chunk, m = std::min(chunk, n - r0);
+        RSI_CUDA_TRY(cudaMemcpyAsync(df + 3 * r0, h_from + 3 * r0, 12 * (size_t)m, cudaMemcpyHostToDevice, c->st_in));
+        RSI_CUDA_TRY(cudaMemcpyAsync(dt + 3 * r0, h_to + 3 * r0, 12 * (size_t)m, cudaMemcpyHostToDevice, c->st_in));
+        c->h_ready[k] = (unsigned long long)(r0 + m);   // read by the copy below when it runs
+        RSI_CUDA_TRY(cudaMemcpyAsync(&h->ctr->ready, &c->h_ready[k], sizeof(unsigned long long),
+                                     cudaMemcpyHostToDevice, c->st_in));
+        RSI_CUDA_TRY(cudaEventRecord(c->ev_chunk[k], c->st_in));
+    }
+    QueryArgs A{};
+    A.nodes = h->nodes;
+    A.nodes4 = h->nodes4;
+    A.tris = h->tris;
+    A.n_tri = h->n_tri;
+    A.from = df;
+    A.to = dt;
+    A.hit = h_hit ? dh : nullptr;
+    A.count = mode == RSI_COUNT ? dc : nullptr;
+    A.amb = h_amb ? da : nullptr;
+    A.band_ids = h->band_ids;
+    A.ctr = h->ctr;
+    A.dmax0 = h->dmax[0];
+    A.dmax1 = h->dmax[1];
+    A.dmax2 = h->dmax[2];
+    A.fp32_only = o.fp32_only;
+    const int block = o.block > 0 ? o.block : 256;
+    const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
+    const bool wide = o.node_width == 4;
+    k_reset_query<<<1, 1, 0, s>>>(h->ctr, ~0ull);   // ~0: the queue is fed by the posts above
+    A.n_rays = n;
+    BatchArgs Bs{};
+    Bs.streamed = 1;
+    Bs.timeout_ns = 10000000000ll;   // a post may wait behind pageable-memory copies
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + block - 1) / block,
+                                                                   (int64_t)rsi::device_sm_count() * bps));
+    if (mode == RSI_ANY_HIT) {
+        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, wide, grid, block, s, Bs);
+        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, wide, grid, block, s, Bs);
+    } else {
+        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, wide, grid, block, s, Bs);
+        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, wide, grid, block, s, Bs);
+    }
+    rsi::note_launches(2);
+    // every copy has landed once the traversal ends; the wait orders the FP64 pass after them
+    RSI_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_chunk[n_chunks - 1], 0));
+    if (!o.fp32_only) {
+        const rsi::PairScratch P = rsi::handle_pairs(h);
+        if (mode == RSI_ANY_HIT) launch_fp64_pass<RSI_ANY_HIT>(A, h->height, &P, s);
+        else launch_fp64_pass<RSI_COUNT>(A, h->height, &P, s);
+    }
+    RSI_CUDA_TRY(cudaGetLastError());
+    if (h_hit) RSI_CUDA_TRY(cudaMemcpyAsync(h_hit, dh, (size_t)n, cudaMemcpyDeviceToHost, s));
+    if (h_amb) RSI_CUDA_TRY(cudaMemcpyAsync(h_amb, da, (size_t)n, cudaMemcpyDeviceToHost, s));
+    if (mode == RSI_COUNT) RSI_CUDA_TRY(cudaMemcpyAsync(h_count, dc, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    RSI_CUDA_TRY(cudaMemcpyAsync(c->h_chunk_ctr, h->ctr, sizeof(rsi::DevCounters), cudaMemcpyDeviceToHost, s));
+    RSI_CUDA_TRY(cudaStreamSynchronize(s));
+    const rsi::DevCounters& kc = c->h_chunk_ctr[0];
+    if (stats) {
+        rsi_stats acc{};
+        acc.n_rays = n;
+        acc.tree_height = h->height;
+        acc.node_visits = (int64_t)kc.node_visits;
+        acc.tri_tests = (int64_t)kc.tri_tests;
+        acc.band_rays = kc.band_count;
+        acc.ambiguous = (int64_t)kc.ambiguous;
+        acc.device_error = kc.error;
+        *stats = acc;
+    }
+    if (kc.error) return rsi::fail(kc.error, "rsi_query_host: device error " + std::to_string(kc.error));
+    return RSI_OK;
+}
+}  // namespace
+
 extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n_rays, int mode,
                               const rsi_options* opt, uint8_t* h_hit, int32_t* h_count, uint8_t* h_ambiguous,
                               rsi_stats* stats, void* stream) {
@@ -2096,6 +2238,14 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
     if (n_rays == 0) {
         if (stats) *stats = rsi_stats{};
         return RSI_OK;
+    }
+    rsi_options o = {};
+    if (opt) o = *opt;
+    if (n_rays <= kHostWhole && o.ray_sort_tile == 0) {
+        rsi::DeviceCtx* c = rsi::device_ctx();
+        if (!c) return rsi::fail(RSI_ERR_CUDA, "rsi_query_host: no device context");
+        std::lock_guard<std::mutex> lock(c->host_mu);   // one host-buffer query per device at a time
+        return host_whole(h, h_from, h_to, n_rays, mode, o, h_hit, h_count, h_ambiguous, stats, s, c);
     }
     const int64_t chunk = std::min<int64_t>(n_rays, kHostChunk);
     const int64_t n_chunks = (n_rays + chunk - 1) / chunk;

@@ -137,6 +137,10 @@ struct DeviceCtx {
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_q[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
     DevCounters* h_chunk_ctr = nullptr;    // pinned counters of every chunk of a call
     int64_t h_chunk_cap = 0;
+    char* whole = nullptr;                 // whole-batch staging of host-buffer queries
+    int64_t whole_cap = 0;                 // segments it holds (30 B each)
+    cudaEvent_t ev_chunk[64] = {};         // copy-in events of the whole-batch chunks
+    unsigned long long* h_ready = nullptr; // pinned: segments copied in so far, per chunk
 };
 DeviceCtx* device_ctx();   // the current device's context (NULL without a device)
 int pool_alloc(void** p, size_t bytes, cudaStream_t s);

@@ -235,18 +235,23 @@ def test_ray_sort_tile_changes_nothing(rsi, tile):
 
 
 def test_host_path_streams_chunks(rsi):
-    """Host buffers, several 2M-segment chunks and a ragged tail: the same
-    answers and counters as the device-buffer query."""
+    """Host buffers, several 2M-segment chunks and a ragged tail, staged
+    whole or through recycled slots: the same answers and counters as the
+    device-buffer query."""
     mesh = W.config_mesh("c2")
     F, E = W.rays(W.config_rays("c2", 5_000_007), mesh)
     bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles))
     pF, pE = torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory()
     for mode, key in (("any_hit", "hit"), ("count", "count")):
         d = bvh.query(_dev(F), _dev(E), mode, stats=True)
-        h = bvh.query_host(pF, pE, mode, stats=True)
-        assert np.array_equal(h[key].numpy(), d[key].cpu().numpy()), mode
-        assert np.array_equal(h["ambiguous"].numpy(), d["ambiguous"].cpu().numpy()), mode
-        assert h["stats"]["band_rays"] == d["stats"]["band_rays"] and h["stats"]["ambiguous"] == d["stats"]["ambiguous"]
+        # the whole batch staged on the device, then (with in-tile reordering)
+        # 2M-segment chunks recycled through two staging slots
+        for tile in (0, 2048):
+            h = bvh.query_host(pF, pE, mode, stats=True, ray_sort_tile=tile)
+            assert np.array_equal(h[key].numpy(), d[key].cpu().numpy()), (mode, tile)
+            assert np.array_equal(h["ambiguous"].numpy(), d["ambiguous"].cpu().numpy()), (mode, tile)
+            assert h["stats"]["band_rays"] == d["stats"]["band_rays"], (mode, tile)
+            assert h["stats"]["ambiguous"] == d["stats"]["ambiguous"], (mode, tile)
     # pageable (not page-locked) host memory works too, only slower
     h = bvh.query_host(torch.from_numpy(F), torch.from_numpy(E), "any_hit")
     assert np.array_equal(h["hit"].numpy(), bvh.query(_dev(F), _dev(E), "any_hit")["hit"].cpu().numpy())
