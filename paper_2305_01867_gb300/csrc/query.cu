@@ -1396,11 +1396,147 @@ __global__ void __launch_bounds__(256) k_nearest_list(QueryArgs A, float* __rest
     }
 }
 
-__global__ void __launch_bounds__(256) k_nearest_finish(QueryArgs A, float* __restrict__ t_out,
-                                                        float* __restrict__ point, float* __restrict__ dist) {
+// ---- double-float arithmetic (a value is hi + lo, two FP32 numbers) with
+// the error-free transformations of Knuth (two-sum), Dekker (fast two-sum)
+// and the FMA product; explicit round-to-nearest operations keep the
+// compiler from contracting or reassociating them.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_fast(float a, float b) {   // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const FF s = ff_two_sum(x.hi, y.hi);
+    return ff_fast(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return ff_fast(p, e);
+}
+__device__ __forceinline__ FF ff_div(FF x, FF y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const FF r = ff_add(x, ff_neg(ff_mul({q1, 0.0f}, y)));
+    return ff_fast(q1, __fdiv_rn(r.hi, y.hi));
+}
+__device__ __forceinline__ FF ff_sqrt(FF x) {
+    const float s = __fsqrt_rn(x.hi);
+    const FF r = ff_add(x, ff_neg(ff_mul({s, 0.0f}, {s, 0.0f})));
+    return ff_fast(s, __fdiv_rn(r.hi, __fmul_rn(2.0f, s)));
+}
+__device__ __forceinline__ FF ff_diff(float a, float b) { return ff_two_sum(a, -b); }   // exact a - b
+
+// Round-to-nearest FP32 of every real within r of v, when they all agree:
+// v.hi (the FP32 nearest to v) provided |v.lo| + r stays below half the gap
+// to v.hi's neighbours.
+__device__ __forceinline__ bool ff_round_certain(FF v, float r, float& out) {
+    const float h = v.hi;
+    if (!(fabsf(h) >= 1.17549435e-38f) || !(fabsf(h) < 1e30f)) return false;   // zero, subnormal, huge
+    const float up = fabsf(__int_as_float(__float_as_int(fabsf(h)) + 1) - fabsf(h));
+    const float dn = fabsf(fabsf(h) - __int_as_float(__float_as_int(fabsf(h)) - 1));
+    const float gap = fminf(up, dn);   // the smaller neighbour spacing
+    if (!(__fadd_ru(fabsf(v.lo), r) < 0.5f * gap)) return false;
+    out = h;
+    return true;
+}
+
+// t, point and distance of a hitting segment in double-float, with a bound
+// on their distance from the FP64 evaluation of the definition (t by the
+// definition's operations, s + t d, t |d|): each of the FP64 and the
+// double-float evaluations of T = e2.(sv x e1) and det = e1.(d x e2) is
+// within c u M of the exact value, M the same expression in magnitudes and
+// c u = 8 x 2^-53 (FP64: at most six roundings deep) or 2^-40 (double-float:
+// each operation within 2^-44 of its operands' magnitudes); the quotient
+// and the point and distance formulas add their own rounding terms.  When
+// every rounding is certain the FP32 results are written; false otherwise.
+__device__ __forceinline__ bool nearest_ff(float3 s, float3 e, float3 a, float3 b, float3 c, float& t32, float& px,
+                                           float& py, float& pz, float& d32) {
+    const FF dx = ff_diff(e.x, s.x), dy = ff_diff(e.y, s.y), dz = ff_diff(e.z, s.z);
+    const FF e1x = ff_diff(b.x, a.x), e1y = ff_diff(b.y, a.y), e1z = ff_diff(b.z, a.z);
+    const FF e2x = ff_diff(c.x, a.x), e2y = ff_diff(c.y, a.y), e2z = ff_diff(c.z, a.z);
+    const FF svx = ff_diff(s.x, a.x), svy = ff_diff(s.y, a.y), svz = ff_diff(s.z, a.z);
+    // p = d x e2, det = e1 . p, q = sv x e1, T = e2 . q
+    const FF p0 = ff_add(ff_mul(dy, e2z), ff_neg(ff_mul(dz, e2y)));
+    const FF p1 = ff_add(ff_mul(dz, e2x), ff_neg(ff_mul(dx, e2z)));
+    const FF p2 = ff_add(ff_mul(dx, e2y), ff_neg(ff_mul(dy, e2x)));
+    const FF det = ff_add(ff_add(ff_mul(e1x, p0), ff_mul(e1y, p1)), ff_mul(e1z, p2));
+    const FF q0 = ff_add(ff_mul(svy, e1z), ff_neg(ff_mul(svz, e1y)));
+    const FF q1 = ff_add(ff_mul(svz, e1x), ff_neg(ff_mul(svx, e1z)));
+    const FF q2 = ff_add(ff_mul(svx, e1y), ff_neg(ff_mul(svy, e1x)));
+    const FF T = ff_add(ff_add(ff_mul(e2x, q0), ff_mul(e2y, q1)), ff_mul(e2z, q2));
+    // magnitudes (FP32 from the leading parts, with slack for their own rounding)
+    const float adx = fabsf(dx.hi), ady = fabsf(dy.hi), adz = fabsf(dz.hi);
+    const float a1x = fabsf(e1x.hi), a1y = fabsf(e1y.hi), a1z = fabsf(e1z.hi);
+    const float a2x = fabsf(e2x.hi), a2y = fabsf(e2y.hi), a2z = fabsf(e2z.hi);
+    const float asx = fabsf(svx.hi), asy = fabsf(svy.hi), asz = fabsf(svz.hi);
+    const float Md = 1.001f * (a1x * (ady * a2z + adz * a2y) + a1y * (adz * a2x + adx * a2z) + a1z * (adx * a2y + ady * a2x));
+    const float MT = 1.001f * (a2x * (asy * a1z + asz * a1y) + a2y * (asz * a1x + asx * a1z) + a2z * (asx * a1y + asy * a1x));
+    const float cu = 8.0f * 1.1102230e-16f + 9.0949470e-13f;   // 8 x 2^-53 + 2^-40
+    const float D = fabsf(det.hi);
+    if (!(cu * Md < 0.01f * D)) return false;
+    const FF t = ff_div(T, det);
+    const float at = fabsf(t.hi);
+    const float rt = 1.02f * (cu * (MT + at * Md) / D + (1.1102230e-16f + 9.0949470e-13f) * at);
+    const FF px_ = ff_add({s.x, 0.0f}, ff_mul(dx, t));
+    const FF py_ = ff_add({s.y, 0.0f}, ff_mul(dy, t));
+    const FF pz_ = ff_add({s.z, 0.0f}, ff_mul(dz, t));
+    const FF nrm = ff_sqrt(ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz)));
+    const FF dist = ff_mul(t, nrm);
+    const float cp = 1.8189894e-12f;   // 2^-39: the FP64 and double-float rounding of s + t d and of t |d|
+    const float rpx = 1.02f * (adx * rt + cp * (fabsf(s.x) + adx * at));
+    const float rpy = 1.02f * (ady * rt + cp * (fabsf(s.y) + ady * at));
+    const float rpz = 1.02f * (adz * rt + cp * (fabsf(s.z) + adz * at));
+    const float rd = 1.02f * (fabsf(nrm.hi) * rt + cp * fabsf(dist.hi));
+    return ff_round_certain(t, rt, t32) && ff_round_certain(px_, rpx, px) && ff_round_certain(py_, rpy, py) &&
+           ff_round_certain(pz_, rpz, pz) && ff_round_certain(dist, rd, d32);
+}
+
+// The listed hitting segments: double-float with certified rounding, the
+// rest (rare) listed for the FP64 evaluation.
+__global__ void __launch_bounds__(256) k_nearest_finish_ff(QueryArgs A, float* __restrict__ t_out,
+                                                           float* __restrict__ point, float* __restrict__ dist,
+                                                           int32_t* __restrict__ list64) {
     const int nf = *(volatile int*)&A.ctr->n_finish;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
         const int64_t r = A.band_ids[i];
+        const int j = A.near[r];
+        const Tri tr = load_tri(A.tris, j);
+        const float3 s = make_float3(A.from[3 * r], A.from[3 * r + 1], A.from[3 * r + 2]);
+        const float3 e = make_float3(A.to[3 * r], A.to[3 * r + 1], A.to[3 * r + 2]);
+        float t32, px, py, pz, d32;
+        if (nearest_ff(s, e, f3(tr.v0), f3(tr.v1), f3(tr.v2), t32, px, py, pz, d32)) {
+            if (t_out) t_out[r] = t32;
+            if (dist) dist[r] = d32;
+            if (point) {
+                point[3 * r] = px;
+                point[3 * r + 1] = py;
+                point[3 * r + 2] = pz;
+            }
+            A.near[r] = __float_as_int(tr.v0.w);
+        } else {
+            list64[atomicAdd(&A.ctr->n_finish64, 1)] = (int32_t)r;
+        }
+    }
+}
+
+// FP64 evaluation of the definition for the listed segments (list, *n_list).
+__global__ void __launch_bounds__(256) k_nearest_finish(QueryArgs A, float* __restrict__ t_out,
+                                                        float* __restrict__ point, float* __restrict__ dist,
+                                                        const int32_t* __restrict__ list,
+                                                        const int* __restrict__ n_list) {
+    const int nf = *(volatile const int*)n_list;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        const int64_t r = list[i];
         const int j = A.near[r];
         const Tri tr = load_tri(A.tris, j);
         const D3 sd = {(double)A.from[3 * r], (double)A.from[3 * r + 1], (double)A.from[3 * r + 2]};
@@ -1676,6 +1812,7 @@ __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->fb_count = 0;
     c->hard_count = 0;
     c->n_finish = 0;
+    c->n_finish64 = 0;
     if (ready != ~0ull) c->ready = ready;   // ~0: a streaming plan, fed by posts
     c->error = 0;
     c->node_visits = c->tri_tests = c->ambiguous = 0;
@@ -1845,8 +1982,16 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (mode == RSI_NEAREST) {
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count() * 8));
         k_nearest_list<<<g, 256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist);
-        k_nearest_finish<<<g, 256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist);
-        note_launches(2);
+        if (perm_scratch) {   // double-float first, FP64 for the segments it leaves
+            k_nearest_finish_ff<<<g, 256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist, perm_scratch);
+            k_nearest_finish<<<g, 256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist, perm_scratch,
+                                               &ctr->n_finish64);
+            note_launches(3);
+        } else {
+            k_nearest_finish<<<g, 256, 0, s>>>(A, nearest->t, nearest->point, nearest->dist, A.band_ids,
+                                               &ctr->n_finish);
+            note_launches(2);
+        }
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[2], s));
     note_launches(2);   // k_reset_query, k_query_fp32 (the FP64 pass counts its own)

@@ -67,7 +67,9 @@ struct DevCounters {
     int pair_count;             // FP64 pass: (segment, triangle) pairs listed
     int fb_count;               // FP64 pass: segments left to the warp-per-segment kernel
     int hard_count;             // FP64 pass: pairs the certain FP64 test left undecided
-    int n_finish;               // nearest mode: hitting segments listed for the FP64 finish
+    int n_finish;               // nearest mode: hitting segments listed for the finish
+    int n_finish64;             // nearest mode: of those, left to the FP64 evaluation
+    int pad3;
 };
 
 }  // namespace rsi
