@@ -1455,7 +1455,8 @@ __device__ __forceinline__ bool ff_round_certain(FF v, float r, float& out) {
 // definition's operations, s + t d, t |d|): each of the FP64 and the
 // double-float evaluations of T = e2.(sv x e1) and det = e1.(d x e2) is
 // within c u M of the exact value, M the same expression in magnitudes and
-// c u = 8 x 2^-53 (FP64: at most six roundings deep) or 2^-40 (double-float:
+// c u = 8 x 2^-53 (FP64: each elementary term at most eight roundings deep, the
+// 2 % slack covering gamma_8) or 2^-40 (double-float:
 // each operation within 2^-44 of its operands' magnitudes); the quotient
 // and the point and distance formulas add their own rounding terms.  When
 // every rounding is certain the FP32 results are written; false otherwise.
