@@ -2247,8 +2247,9 @@ using namespace rsi;   // the kernels and launchers above
 // the number of segments now on the device; one persistent FP32 traversal
 // on the caller's stream takes segments as they are posted (a device work
 // queue with bounded waits, as in streaming batched plans), so copies and
-// traversal overlap without a kernel tail per chunk; one FP64 pass then
-// settles the whole queue and the results are copied out.
+// traversal overlap without a kernel tail per chunk (the first chunk is
+// small so that the traversal starts early); one FP64 pass then settles the
+// whole queue and the results are copied out.
 constexpr int64_t kHostWhole = (int64_t)1 << 26;
 
 int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, int mode, const rsi_options& o,
@@ -2295,15 +2296,18 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     int32_t* dc = reinterpret_cast<int32_t*>(c->whole + 2 * al(12 * (size_t)n));
     uint8_t* dh = reinterpret_cast<uint8_t*>(c->whole + 2 * al(12 * (size_t)n) + al(4 * (size_t)n));
     uint8_t* da = dh + al((size_t)n);
-    const int64_t chunk = std::max<int64_t>(kHostChunk, (n + 63) / 64);
-    const int n_chunks = (int)((n + chunk - 1) / chunk);
+    // chunk k covers [first(k), first(k + 1)): a first chunk of 2^18 segments, then 2^21 (at most 64 chunks)
+    const int64_t c0 = std::min<int64_t>(n, (int64_t)1 << 18);
+    const int64_t chunk = std::max<int64_t>(kHostChunk, (n - c0 + 62) / 63);
+    const int n_chunks = 1 + (int)((n - c0 + chunk - 1) / chunk);
+    auto first = [&](int k) { return k == 0 ? (int64_t)0 : std::min<int64_t>(n, c0 + (k - 1) * chunk); };
     // empty the work queue, then start the copies once the caller's stream
     // is done with the previous call's staging
     RSI_CUDA_TRY(cudaMemsetAsync(&h->ctr->ready, 0, sizeof(unsigned long long), s));
     RSI_CUDA_TRY(cudaEventRecord(c->ev_chunk[0], s));
     RSI_CUDA_TRY(cudaStreamWaitEvent(c->st_in, c->ev_chunk[0], 0));
     for (int k = 0; k < n_chunks; ++k) {
-        const int64_t r0 = k * chunk, m = std::min(chunk, n - r0);
+        const int64_t r0 = first(k), m = first(k + 1) - r0;
         RSI_CUDA_TRY(cudaMemcpyAsync(df + 3 * r0, h_from + 3 * r0, 12 * (size_t)m, cudaMemcpyHostToDevice, c->st_in));
         RSI_CUDA_TRY(cudaMemcpyAsync(dt + 3 * r0, h_to + 3 * r0, 12 * (size_t)m, cudaMemcpyHostToDevice, c->st_in));
         c->h_ready[k] = (unsigned long long)(r0 + m);   // read by the copy below when it runs
