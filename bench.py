@@ -226,8 +226,10 @@ def measure_batched(rsi, torch, dev, c4, args):
     same work issued as 64 separate rsi_query calls."""
     jobs, rays = c4
     stream = torch.cuda.current_stream()
+    meshes = [(torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.triangles).to(dev)) for m, _ in jobs]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    bvhs = [rsi.LBVH(torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.triangles).to(dev)) for m, _ in jobs]
+    bvhs = rsi.build_many(meshes)   # all 64 hierarchies in one build
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
     items = [(b, torch.from_numpy(F).to(dev), torch.from_numpy(E).to(dev)) for b, (F, E) in zip(bvhs, rays)]
@@ -328,7 +330,8 @@ def measure_builders(rsi, torch, dev, meshes, c4, reps=20):
     """Build time of the two tree constructions (Karras radix tree + refit,
     and the single bottom-up pass of Sec. 4.2 after Apetrei) on the c2 and
     c3 meshes and on all 64 c4 meshes: wall-clock per lbvh_build call
-    (each call synchronizes its stream once), median over reps."""
+    (each call synchronizes its stream once), median over reps; and the 64
+    c4 meshes in one lbvh_build_batched call."""
     def per_build(V, T, builder):
         for _ in range(3):
             rsi.LBVH(V, T, builder=builder).close()
@@ -351,6 +354,19 @@ def measure_builders(rsi, torch, dev, meshes, c4, reps=20):
         tot = {}
         for b in ("karras", "apetrei"):
             tot[f"{b}_ms"] = sum(per_build(V, T, b) for V, T in jobs)
+        # all 64 in one build (lbvh_build_batched)
+        for _ in range(3):
+            for b in rsi.build_many(jobs):
+                b.close()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hs = rsi.build_many(jobs)
+            ts.append(1e3 * (time.perf_counter() - t0))
+            for b in hs:
+                b.close()
+        tot["one_batched_build_ms"] = statistics.median(ts)
         out["c4_all_64"] = {"triangles": int(sum(len(m.triangles) for m, _ in c4[0])), **tot}
     return out
 

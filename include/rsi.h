@@ -165,6 +165,23 @@ int lbvh_build_ex(const float* d_vertices, int64_t n_vertices, const int32_t* d_
                   int64_t n_triangles, int index_bytes, int morton_bits, int tree_builder, void* stream,
                   rsi_bvh_t* out);
 
+/*
+ * Build the hierarchies of n_meshes independent meshes at once (the many
+ * meshes of a batched query; building many at once has no counterpart in the
+ * paper).  Mesh m: d_vertices[m] [n_vertices[m]][3] float32 and
+ * d_triangles[m] [n_triangles[m]][3] int32, device (host arrays of device
+ * pointers and counts).  Each stage of the build runs as one launch over all
+ * meshes -- extent, Morton codes, a stable sort by code and then by mesh,
+ * the single bottom-up pass of lbvh_build_ex(RSI_TREE_APETREI) and the
+ * four-wide collapse -- and the call synchronizes `stream` once.  out[m]
+ * receives mesh m's handle, identical to what lbvh_build would give it
+ * (release each with lbvh_free).  Errors: as lbvh_build, naming the mesh;
+ * on any error no handle is returned.  At most 2^30 triangles in all.
+ */
+int lbvh_build_batched(int n_meshes, const float* const* d_vertices, const int64_t* n_vertices,
+                       const int32_t* const* d_triangles, const int64_t* n_triangles, int index_bytes,
+                       int morton_bits, void* stream, rsi_bvh_t* out);
+
 /* As lbvh_build, with the mesh in host memory (copied in on `stream`). */
 int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
                     int64_t n_triangles, int index_bytes, int morton_bits, void* stream,

@@ -84,6 +84,9 @@ def _load():
     lib.lbvh_build_host.argtypes = [P, i64, P, i64, i32, i32, P, ctypes.POINTER(P)]
     lib.lbvh_build_ex.argtypes = [P, i64, P, i64, i32, i32, i32, P, ctypes.POINTER(P)]
     lib.lbvh_build_ex.restype = ctypes.c_int
+    lib.lbvh_build_batched.argtypes = [i32, ctypes.POINTER(P), ctypes.POINTER(i64), ctypes.POINTER(P),
+                                       ctypes.POINTER(i64), i32, i32, P, ctypes.POINTER(P)]
+    lib.lbvh_build_batched.restype = ctypes.c_int
     lib.lbvh_free.argtypes = [P]
     lib.lbvh_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.lbvh_export.argtypes = [P, P, ctypes.POINTER(HostView)]
@@ -219,6 +222,14 @@ class LBVH:
                                     triangles.shape[0], index_bytes, morton_bits, _TREE_BUILDERS[builder],
                                     _stream(stream), ctypes.byref(self._h)))
         self.n_triangles = triangles.shape[0]
+
+    @classmethod
+    def _adopt(cls, handle, n_triangles):
+        """Wrap a handle built elsewhere (build_many)."""
+        obj = cls.__new__(cls)
+        obj._h = handle
+        obj.n_triangles = n_triangles
+        return obj
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -372,6 +383,34 @@ class LBVH:
         surface, in increasing segment order."""
         r = self.nearest(ray_from, ray_to, want_t=False, want_ambiguous=False, stream=stream)
         return compact_hits(r["tri"], r["dist"], r["point"], stream=stream)
+
+
+def build_many(meshes, morton_bits: int = 30, stream=None):
+    """Hierarchies of many meshes in one build (lbvh_build_batched): meshes is
+    a list of (vertices, triangles) device tensors ([n, 3] float32, [m, 3]
+    int32); returns one LBVH per mesh, each identical to LBVH(vertices,
+    triangles)."""
+    import torch
+    M = len(meshes)
+    if M < 1:
+        raise ValueError("build_many needs at least one mesh")
+    P = ctypes.c_void_p
+    vp, tp = (P * M)(), (P * M)()
+    nv, nt = (ctypes.c_int64 * M)(), (ctypes.c_int64 * M)()
+    keep = []
+    for m, (V, T) in enumerate(meshes):
+        _check_f32x3(V, "vertices")
+        if not isinstance(T, torch.Tensor) or T.dim() != 2 or T.shape[1] != 3 or T.dtype != torch.int32:
+            raise TypeError("triangles must be int32 tensors of shape [n, 3]")
+        if not (V.is_cuda and T.is_cuda):
+            raise TypeError("build_many takes device tensors")
+        T = T.contiguous()
+        keep.append(T)
+        vp[m], tp[m] = V.data_ptr(), T.data_ptr()
+        nv[m], nt[m] = V.shape[0], T.shape[0]
+    out = (P * M)()
+    check(lib.lbvh_build_batched(M, vp, nv, tp, nt, 4, morton_bits, _stream(stream), out))
+    return [LBVH._adopt(P(out[m]), int(nt[m])) for m in range(M)]
 
 
 def compact_hits(tri, dist, point, stream=None):

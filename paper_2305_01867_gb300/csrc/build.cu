@@ -18,6 +18,8 @@
 #include <stdint.h>
 
 #include <cstring>
+#include <string>
+#include <vector>
 
 #include "rsi_internal.cuh"
 
@@ -43,25 +45,30 @@ __device__ __host__ __forceinline__ float ord2f(unsigned int o) {
 
 __device__ __forceinline__ void raise_error(DevCounters* c, int code) { atomicCAS(&c->error, 0, code); }
 
-__global__ void k_init(DevCounters* c) {
-    if (threadIdx.x == 0) {
-        c->error = 0;
-        c->band_count = 0;
-        c->height = 0;
-        c->node_visits = c->tri_tests = c->ambiguous = 0;
-        for (int a = 0; a < 3; ++a) {
-            c->ext_bits[a] = 0xFFFFFFFFu;   // running min
-            c->ext_bits[3 + a] = 0u;        // running max
-            c->dmax_bits[a] = 0u;
-        }
+__device__ __forceinline__ void init_counters(DevCounters* c) {
+    c->error = 0;
+    c->band_count = 0;
+    c->height = 0;
+    c->node_visits = c->tri_tests = c->ambiguous = 0;
+    for (int a = 0; a < 3; ++a) {
+        c->ext_bits[a] = 0xFFFFFFFFu;   // running min
+        c->ext_bits[3 + a] = 0u;        // running max
+        c->dmax_bits[a] = 0u;
     }
 }
 
-// Per-axis min / max over all vertices; NaN raises RSI_ERR_NAN.
-__global__ void k_extent(const float* __restrict__ V, int64_t nv, DevCounters* c) {
+__global__ void k_init(DevCounters* c) {
+    if (threadIdx.x == 0) init_counters(c);
+}
+
+// Per-axis min / max over all vertices; NaN raises RSI_ERR_NAN.  The
+// calling threads take vertices i0, i0 + stride, ...; every lane of each
+// warp must call it (warp reduction).
+__device__ __forceinline__ void extent_body(const float* __restrict__ V, int64_t nv, DevCounters* c, int64_t i0,
+                                            int64_t stride) {
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool nan = false;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = i0; i < nv; i += stride) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float x = __ldg(V + 3 * i + a);
@@ -87,6 +94,10 @@ __global__ void k_extent(const float* __restrict__ V, int64_t nv, DevCounters* c
             }
         }
     }
+}
+
+__global__ void k_extent(const float* __restrict__ V, int64_t nv, DevCounters* c) {
+    extent_body(V, nv, c, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // Spread the low bits of q so that bit i lands on bit 3i.
@@ -131,19 +142,15 @@ struct MortonTraits<uint64_t> {
 // compiler from fusing any multiply-add, so the code is the same on any host
 // that evaluates the same IEEE operations.
 template <typename K>
-__global__ void k_morton(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T, int64_t nt,
-                         DevCounters* c, K* __restrict__ keys, int32_t* __restrict__ ids) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= nt) return;
+__device__ __forceinline__ K morton_key(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T,
+                                        int64_t j, DevCounters* c) {
     const int b = MortonTraits<K>::kBitsPerAxis;
     const float scale = (float)(1u << b);
     const uint32_t qmax = (1u << b) - 1u;
     int32_t i0 = __ldg(T + 3 * j), i1 = __ldg(T + 3 * j + 1), i2 = __ldg(T + 3 * j + 2);
-    ids[j] = (int32_t)j;
     if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nv || i1 >= nv || i2 >= nv) {
         raise_error(c, RSI_ERR_INDEX);
-        keys[j] = 0;
-        return;
+        return K(0);
     }
     uint32_t q[3];
 #pragma unroll
@@ -156,7 +163,16 @@ __global__ void k_morton(const float* __restrict__ V, int64_t nv, const int32_t*
         uint32_t qq = __float2uint_rz(__fmul_rn(u, scale));
         q[a] = qq > qmax ? qmax : qq;
     }
-    keys[j] = MortonTraits<K>::encode(q[0], q[1], q[2]);
+    return MortonTraits<K>::encode(q[0], q[1], q[2]);
+}
+
+template <typename K>
+__global__ void k_morton(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T, int64_t nt,
+                         DevCounters* c, K* __restrict__ keys, int32_t* __restrict__ ids) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nt) return;
+    ids[j] = (int32_t)j;
+    keys[j] = morton_key<K>(V, nv, T, j, c);
 }
 
 // ---------------------------------------------------------------- radix sort
@@ -273,10 +289,8 @@ __device__ __forceinline__ int delta(const K* __restrict__ k, int64_t n, int64_t
 // and the split gamma by a binary search; children are gamma and gamma + 1,
 // leaves when they coincide with an end of the range.
 template <typename K>
-__global__ void k_karras(const K* __restrict__ k, int64_t n, int32_t* __restrict__ left, int32_t* __restrict__ right,
-                         int32_t* __restrict__ parent) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
+__device__ __forceinline__ void karras_node(const K* __restrict__ k, int64_t n, int64_t i, int32_t* __restrict__ left,
+                                            int32_t* __restrict__ right, int32_t* __restrict__ parent) {
     int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) > 0 ? 1 : -1;
     int dmin = delta(k, n, i, i - d);
     int64_t lmax = 2;
@@ -301,6 +315,13 @@ __global__ void k_karras(const K* __restrict__ k, int64_t n, int32_t* __restrict
     left[i] = lc;
     right[i] = rc;
     if (i == 0) parent[0] = -1;
+}
+
+template <typename K>
+__global__ void k_karras(const K* __restrict__ k, int64_t n, int32_t* __restrict__ left, int32_t* __restrict__ right,
+                         int32_t* __restrict__ parent) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n - 1) karras_node<K>(k, n, i, left, right, parent);
 }
 
 // ---------------------------------------------------------------- refit
@@ -388,10 +409,8 @@ __global__ void k_refit(const float* __restrict__ V, int64_t nv, const int32_t* 
 // Binary node i at even depth becomes a four-wide node holding its children,
 // an internal child being replaced by that child's two children.  Child order
 // is leaf order (Morton order).  Odd-depth nodes get no four-wide node.
-__global__ void k_collapse4(const Node* __restrict__ nodes, const int32_t* __restrict__ parent, int64_t n,
-                            Node4* __restrict__ out) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
+__device__ __forceinline__ void collapse_node(const Node* __restrict__ nodes, const int32_t* __restrict__ parent,
+                                              int64_t i, Node4* __restrict__ out) {
     int depth = 0;
     for (int32_t p = (int32_t)i; p != 0; p = parent[p]) ++depth;
     if (depth & 1) return;
@@ -437,6 +456,12 @@ __global__ void k_collapse4(const Node* __restrict__ nodes, const int32_t* __res
     out[i] = o;
 }
 
+__global__ void k_collapse4(const Node* __restrict__ nodes, const int32_t* __restrict__ parent, int64_t n,
+                            Node4* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n - 1) collapse_node(nodes, parent, i, out);
+}
+
 // ---------------------------------------------------------------- single pass
 // Agglomerative build (Apetrei 2014; the bottom-up construction of Sec. 4.2):
 // one thread per leaf climbs the tree.  A node covering leaves [lo, hi] is
@@ -453,13 +478,12 @@ __global__ void k_collapse4(const Node* __restrict__ nodes, const int32_t* __res
 // first), which a node learns only when it knows which side of its parent it
 // is on -- so a node's arrays are written one step up the climb.
 template <typename K>
-__global__ void k_apetrei(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T,
-                          const int32_t* __restrict__ perm, const K* __restrict__ keys, int64_t n,
-                          int32_t* __restrict__ left, int32_t* __restrict__ right, int32_t* __restrict__ parent,
-                          float* __restrict__ box, int32_t* __restrict__ hgt, int32_t* __restrict__ ends,
-                          Node* __restrict__ nodes, Tri* __restrict__ tris, DevCounters* c) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n) return;
+__device__ __forceinline__ void apetrei_leaf(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T,
+                                             const int32_t* __restrict__ perm, const K* __restrict__ keys, int64_t n,
+                                             int64_t j, int32_t* __restrict__ left, int32_t* __restrict__ right,
+                                             int32_t* __restrict__ parent, float* __restrict__ box,
+                                             int32_t* __restrict__ hgt, int32_t* __restrict__ ends,
+                                             Node* __restrict__ nodes, Tri* __restrict__ tris, DevCounters* c) {
     int32_t t = perm[j];
     int32_t i0 = T[3 * (int64_t)t], i1 = T[3 * (int64_t)t + 1], i2 = T[3 * (int64_t)t + 2];
     float v[3][3];
@@ -555,6 +579,16 @@ __global__ void k_apetrei(const float* __restrict__ V, int64_t nv, const int32_t
 }
 
 template <typename K>
+__global__ void k_apetrei(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T,
+                          const int32_t* __restrict__ perm, const K* __restrict__ keys, int64_t n,
+                          int32_t* __restrict__ left, int32_t* __restrict__ right, int32_t* __restrict__ parent,
+                          float* __restrict__ box, int32_t* __restrict__ hgt, int32_t* __restrict__ ends,
+                          Node* __restrict__ nodes, Tri* __restrict__ tris, DevCounters* c) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < n) apetrei_leaf<K>(V, nv, T, perm, keys, n, j, left, right, parent, box, hgt, ends, nodes, tris, c);
+}
+
+template <typename K>
 int sort_pairs(K* ka, int32_t* va, K* kb, int32_t* vb, int64_t n, int passes, uint32_t* hist, cudaStream_t s,
                K** out_k, int32_t** out_v) {
     int ntiles = grid_for(n, kSortTile);
@@ -610,12 +644,118 @@ int build_impl(rsi_bvh_s* h, const float* V, const int32_t* T, int builder, cuda
     return RSI_OK;
 }
 
+// ---------------------------------------------------------------- many meshes
+// One build of many meshes (lbvh_build_batched): every stage is one launch
+// over all meshes' vertices, triangles or nodes; a thread finds its mesh by
+// a binary search over the prefix of the per-mesh counts and then runs the
+// single-mesh code on that mesh's arrays.
+struct MeshBuild {
+    const float* V;
+    const int32_t* T;
+    int64_t nv, nt;
+    Node* nodes;
+    Node4* nodes4;
+    Tri* tris;
+    void* keys;   // the handle's sorted keys (uint32 or uint64)
+    int32_t *perm, *left, *right, *parent, *hgt, *ends;
+    float* box;
+    DevCounters* ctr;
+};
+
+// The mesh m with pre[m] <= g < pre[m + 1] (pre: M + 1 prefix entries).
+__device__ __forceinline__ int mesh_of(const int64_t* __restrict__ pre, int M, int64_t g) {
+    int lo = 0, hi = M - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(pre + mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_init_seg(const MeshBuild* __restrict__ d, int M) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) init_counters(d[m].ctr);
+}
+
+__global__ void k_extent_seg(const MeshBuild* __restrict__ d) {   // one block per mesh
+    const MeshBuild& mb = d[blockIdx.x];
+    extent_body(mb.V, mb.nv, mb.ctr, threadIdx.x, blockDim.x);
+}
+
+// Morton code of every triangle (global index g, tri_pre = triangle prefix),
+// a copy of it by triangle, the identity as values, and the range-end slots
+// of the bottom-up pass set to -1.
+template <typename K>
+__global__ void k_morton_seg(const MeshBuild* __restrict__ d, const int64_t* __restrict__ tri_pre, int M, int64_t total,
+                             K* __restrict__ keys, K* __restrict__ codes, int32_t* __restrict__ vals) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int m = mesh_of(tri_pre, M, g);
+    const MeshBuild& mb = d[m];
+    const int64_t j = g - tri_pre[m];
+    const K key = morton_key<K>(mb.V, mb.nv, mb.T, j, mb.ctr);
+    keys[g] = key;
+    codes[g] = key;
+    vals[g] = (int32_t)g;
+    if (j < mb.nt - 1) mb.ends[j] = -1;
+}
+
+// The mesh of each entry (values are global triangle indices), as a sort key.
+__global__ void k_mesh_keys(const int32_t* __restrict__ vals, const int64_t* __restrict__ tri_pre, int M, int64_t total,
+                            uint32_t* __restrict__ mk) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < total) mk[g] = (uint32_t)mesh_of(tri_pre, M, vals[g]);
+}
+
+// After the sorts entries are grouped by mesh, in (code, triangle) order
+// within each: give every mesh its sorted keys and leaf order.
+template <typename K>
+__global__ void k_scatter_seg(const MeshBuild* __restrict__ d, const int64_t* __restrict__ tri_pre, int M,
+                              int64_t total, const int32_t* __restrict__ vals, const K* __restrict__ codes) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int m = mesh_of(tri_pre, M, g);
+    const int64_t i = g - tri_pre[m];
+    const int32_t gid = vals[g];
+    d[m].perm[i] = (int32_t)(gid - tri_pre[m]);
+    reinterpret_cast<K*>(d[m].keys)[i] = codes[gid];
+}
+
+template <typename K>
+__global__ void k_apetrei_seg(const MeshBuild* __restrict__ d, const int64_t* __restrict__ tri_pre, int M,
+                              int64_t total) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int m = mesh_of(tri_pre, M, g);
+    const MeshBuild& mb = d[m];
+    apetrei_leaf<K>(mb.V, mb.nv, mb.T, mb.perm, reinterpret_cast<const K*>(mb.keys), mb.nt, g - tri_pre[m], mb.left,
+                    mb.right, mb.parent, mb.box, mb.hgt, mb.ends, mb.nodes, mb.tris, mb.ctr);
+}
+
+// int_pre: prefix of the internal node counts max(nt - 1, 0).
+__global__ void k_collapse4_seg(const MeshBuild* __restrict__ d, const int64_t* __restrict__ int_pre, int M,
+                                int64_t total) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int m = mesh_of(int_pre, M, g);
+    collapse_node(d[m].nodes, d[m].parent, g - int_pre[m], d[m].nodes4);
+}
+
+__global__ void k_gather_ctr(const MeshBuild* __restrict__ d, int M, DevCounters* __restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) out[m] = *d[m].ctr;
+}
+
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, int morton_bits, int builder,
-                      cudaStream_t s, rsi_bvh_t* out) {
+// A handle with its device arrays in one pool allocation (256-byte aligned
+// pieces); sort scratch for a single-mesh build when `sort_scratch`.
+// Returns nullptr (error set) when the allocation fails.
+rsi_bvh_s* alloc_handle(int64_t nv, int64_t nt, int morton_bits, bool sort_scratch, cudaStream_t s, char** base_out,
+                        int32_t** hgt, int32_t** flag, char** scratch) {
     rsi_bvh_s* h = new rsi_bvh_s();
     h->n_tri = nt;
     h->n_vert = nv;
@@ -637,7 +777,7 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
         4 * (size_t)(2 * n - 1),                   // 8 heights
         4 * (size_t)ni,                            // 9 flags
         sizeof(DevCounters),                       // 10 counters
-        2 * ksz * (size_t)n + 8 * (size_t)n + 4 * 256 * (size_t)ntiles,  // 11 sort scratch
+        sort_scratch ? 2 * ksz * (size_t)n + 8 * (size_t)n + 4 * 256 * (size_t)ntiles : 0,  // 11 sort scratch
         sizeof(Node4) * (size_t)ni                 // 12 four-wide nodes
     };
     for (int i = 0; i < 13; ++i) {
@@ -647,9 +787,8 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     char* base = nullptr;
     if (pool_alloc(reinterpret_cast<void**>(&base), total, s) != RSI_OK) {
         delete h;
-        return RSI_ERR_OOM;
+        return nullptr;
     }
-    cudaError_t e = cudaSuccess;
     h->device_bytes = (int64_t)total;
     h->nodes = (Node*)(base + off[0]);
     h->tris = (Tri*)(base + off[1]);
@@ -659,11 +798,36 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     h->right = (int32_t*)(base + off[5]);
     h->parent = (int32_t*)(base + off[6]);
     h->box = (float*)(base + off[7]);
-    int32_t* hgt = (int32_t*)(base + off[8]);
-    int32_t* flag = (int32_t*)(base + off[9]);
+    *hgt = (int32_t*)(base + off[8]);
+    *flag = (int32_t*)(base + off[9]);
     h->ctr = (DevCounters*)(base + off[10]);
-    char* scratch = base + off[11];
+    *scratch = base + off[11];
     h->nodes4 = (Node4*)(base + off[12]);
+    *base_out = base;
+    return h;
+}
+
+// Extent, padding and height of a finished build from its counters.
+void finish_handle(rsi_bvh_s* h, const DevCounters& hc) {
+    h->height = hc.height;
+    for (int a = 0; a < 3; ++a) {
+        h->lo[a] = ord2f(hc.ext_bits[a]);
+        h->hi[a] = ord2f(hc.ext_bits[3 + a]);
+        float f;
+        std::memcpy(&f, &hc.dmax_bits[a], 4);
+        h->dmax[a] = f;
+    }
+}
+
+int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, int morton_bits, int builder,
+                      cudaStream_t s, rsi_bvh_t* out) {
+    const int64_t n = nt, ni = n > 1 ? n - 1 : 1;
+    char* base = nullptr;
+    int32_t *hgt = nullptr, *flag = nullptr;
+    char* scratch = nullptr;
+    rsi_bvh_s* h = alloc_handle(nv, nt, morton_bits, true, s, &base, &hgt, &flag, &scratch);
+    if (!h) return RSI_ERR_OOM;
+    cudaError_t e = cudaSuccess;
     auto cleanup = [&](int code) {
         cudaStreamSynchronize(s);
         pool_free(base, s);
@@ -693,15 +857,119 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
         return cleanup(fail(hc.error, hc.error == RSI_ERR_NAN ? "lbvh_build: NaN vertex coordinate"
                                                              : "lbvh_build: triangle vertex index out of range"));
     }
-    h->height = hc.height;
-    for (int a = 0; a < 3; ++a) {
-        h->lo[a] = ord2f(hc.ext_bits[a]);
-        h->hi[a] = ord2f(hc.ext_bits[3 + a]);
-        float f;
-        std::memcpy(&f, &hc.dmax_bits[a], 4);
-        h->dmax[a] = f;
-    }
+    finish_handle(h, hc);
     *out = h;
+    return RSI_OK;
+}
+
+// Many meshes in one build: ~20 launches in all, one synchronization.
+template <typename K>
+int build_batched_impl(int M, const float* const* V, const int64_t* nv, const int32_t* const* T, const int64_t* nt,
+                       int morton_bits, cudaStream_t s, rsi_bvh_t* out) {
+    std::vector<MeshBuild> mb(M);
+    std::vector<int64_t> tri_pre(M + 1, 0), int_pre(M + 1, 0);
+    std::vector<rsi_bvh_s*> hs(M, nullptr);
+    std::vector<char*> bases(M, nullptr);
+    auto free_all = [&]() {
+        for (int m = 0; m < M; ++m) {
+            if (bases[m]) pool_free(bases[m], s);
+            delete hs[m];
+        }
+    };
+    for (int m = 0; m < M; ++m) {
+        char* scratch = nullptr;
+        int32_t *hgt = nullptr, *ends = nullptr;
+        hs[m] = alloc_handle(nv[m], nt[m], morton_bits, false, s, &bases[m], &hgt, &ends, &scratch);
+        if (!hs[m]) {
+            free_all();
+            return RSI_ERR_OOM;
+        }
+        rsi_bvh_s* h = hs[m];
+        mb[m] = MeshBuild{V[m], T[m], nv[m], nt[m], h->nodes, h->nodes4, h->tris, h->sorted_keys, h->perm,
+                          h->left, h->right, h->parent, hgt, ends, h->box, h->ctr};
+        tri_pre[m + 1] = tri_pre[m] + nt[m];
+        int_pre[m + 1] = int_pre[m] + (nt[m] > 1 ? nt[m] - 1 : 0);
+    }
+    const int64_t total = tri_pre[M], total_int = int_pre[M];
+    const int ntiles = grid_for(total, 4096);
+    // global scratch: table, prefixes, keys x2, codes, values x2, mesh keys x2, histograms, counters
+    size_t off[10], bytes = 0;
+    const size_t sizes[10] = {sizeof(MeshBuild) * (size_t)M, 8 * (size_t)(M + 1), 8 * (size_t)(M + 1),
+                              sizeof(K) * (size_t)total, sizeof(K) * (size_t)total, sizeof(K) * (size_t)total,
+                              8 * (size_t)total, 8 * (size_t)total, 4 * 256 * (size_t)ntiles,
+                              sizeof(DevCounters) * (size_t)M};
+    for (int i = 0; i < 10; ++i) {
+        off[i] = bytes;
+        bytes += align_up(sizes[i]);
+    }
+    char* g = nullptr;
+    if (pool_alloc(reinterpret_cast<void**>(&g), bytes, s) != RSI_OK) {
+        free_all();
+        return RSI_ERR_OOM;
+    }
+    MeshBuild* d_mb = (MeshBuild*)(g + off[0]);
+    int64_t* d_tri_pre = (int64_t*)(g + off[1]);
+    int64_t* d_int_pre = (int64_t*)(g + off[2]);
+    K* ka = (K*)(g + off[3]);
+    K* kb = (K*)(g + off[4]);
+    K* codes = (K*)(g + off[5]);
+    int32_t* va = (int32_t*)(g + off[6]);
+    int32_t* vb = va + total;
+    uint32_t* mka = (uint32_t*)(g + off[7]);
+    uint32_t* mkb = mka + total;
+    uint32_t* hist = (uint32_t*)(g + off[8]);
+    DevCounters* d_ctr = (DevCounters*)(g + off[9]);
+    std::vector<DevCounters> hc(M);
+    auto fail_all = [&](int code) {
+        cudaStreamSynchronize(s);
+        pool_free(g, s);
+        free_all();
+        return code;
+    };
+    cudaError_t e = cudaMemcpyAsync(d_mb, mb.data(), sizeof(MeshBuild) * M, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tri_pre, tri_pre.data(), 8 * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_int_pre, int_pre.data(), 8 * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_all(cuda_fail(e, "lbvh_build_batched: upload"));
+    k_init_seg<<<grid_for(M, 128), 128, 0, s>>>(d_mb, M);
+    k_extent_seg<<<M, kBlock, 0, s>>>(d_mb);
+    k_morton_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total, ka, codes, va);
+    note_launches(3);
+    // stable sort by code, then stably by mesh: (mesh, code, triangle) order
+    K* sk;
+    int32_t* sv;
+    int rc = sort_pairs<K>(ka, va, kb, vb, total, sizeof(K) == 4 ? 4 : 8, hist, s, &sk, &sv);
+    if (rc) return fail_all(rc);
+    int32_t* sv2 = sv == va ? vb : va;   // the other value buffer
+    k_mesh_keys<<<grid_for(total, kBlock), kBlock, 0, s>>>(sv, d_tri_pre, M, total, mka);
+    note_launches(1);
+    uint32_t* smk;
+    int32_t* fv;
+    rc = sort_pairs<uint32_t>(mka, sv, mkb, sv2, total, M <= 256 ? 1 : (M <= 65536 ? 2 : 4), hist, s, &smk, &fv);
+    if (rc) return fail_all(rc);
+    k_scatter_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total, fv, codes);
+    k_apetrei_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total);
+    note_launches(2);
+    if (total_int > 0) {
+        k_collapse4_seg<<<grid_for(total_int, kBlock), kBlock, 0, s>>>(d_mb, d_int_pre, M, total_int);
+        note_launches(1);
+    }
+    k_gather_ctr<<<grid_for(M, 128), 128, 0, s>>>(d_mb, M, d_ctr);
+    note_launches(1);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), d_ctr, sizeof(DevCounters) * M, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_all(cuda_fail(e, "lbvh_build_batched"));
+    for (int m = 0; m < M; ++m) {
+        if (hc[m].error) {
+            const std::string why = hc[m].error == RSI_ERR_NAN ? "NaN vertex coordinate" : "triangle vertex index out of range";
+            return fail_all(fail(hc[m].error, "lbvh_build_batched: mesh " + std::to_string(m) + ": " + why));
+        }
+    }
+    pool_free(g, s);
+    for (int m = 0; m < M; ++m) {
+        finish_handle(hs[m], hc[m]);
+        out[m] = hs[m];
+    }
     return RSI_OK;
 }
 
@@ -741,6 +1009,31 @@ extern "C" int lbvh_build_ex(const float* d_vertices, int64_t n_vertices, const 
                              rsi_bvh_t* out) {
     return rsi::build_checked("lbvh_build_ex", d_vertices, n_vertices, d_triangles, n_triangles, index_bytes,
                               morton_bits, tree_builder, stream, out);
+}
+
+extern "C" int lbvh_build_batched(int n_meshes, const float* const* d_vertices, const int64_t* n_vertices,
+                                  const int32_t* const* d_triangles, const int64_t* n_triangles, int index_bytes,
+                                  int morton_bits, void* stream, rsi_bvh_t* out) {
+    if (!out || n_meshes < 1 || !d_vertices || !n_vertices || !d_triangles || !n_triangles)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_batched: need n_meshes >= 1 and non-NULL arrays");
+    for (int m = 0; m < n_meshes; ++m) out[m] = nullptr;
+    if (index_bytes != 4) return rsi::fail(RSI_ERR_DTYPE, "lbvh_build_batched: triangle indices must be int32");
+    if (morton_bits != 30 && morton_bits != 63)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_batched: morton_bits must be 30 or 63");
+    int64_t total = 0;
+    for (int m = 0; m < n_meshes; ++m) {
+        if (!d_vertices[m] || !d_triangles[m] || n_vertices[m] < 1 || n_triangles[m] < 1 ||
+            n_vertices[m] > ((int64_t)1 << 31))
+            return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_batched: mesh " + std::to_string(m) +
+                                                      " has a NULL pointer or a count out of range");
+        total += n_triangles[m];
+    }
+    if (total > 0x3FFFFFFF)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_batched: more than 2^30 triangles in all");
+    cudaStream_t s = (cudaStream_t)stream;
+    return morton_bits == 30
+               ? rsi::build_batched_impl<uint32_t>(n_meshes, d_vertices, n_vertices, d_triangles, n_triangles, 30, s, out)
+               : rsi::build_batched_impl<uint64_t>(n_meshes, d_vertices, n_vertices, d_triangles, n_triangles, 63, s, out);
 }
 
 extern "C" int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,

@@ -58,6 +58,16 @@ def test_host_side_rejections(lib):
     assert rc == -1 and "tree_builder" in lib.last_error()
     rc = L.lbvh_build_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 8, 30, 1, None, ctypes.byref(h))
     assert rc == -2
+    P, I64 = ctypes.c_void_p, ctypes.c_int64
+    outs = (P * 2)()
+    rc = L.lbvh_build_batched(0, None, None, None, None, 4, 30, None, outs)
+    assert rc == -1
+    vp, tp = (P * 2)(16, 16), (P * 2)(16, None)
+    nv, nt = (I64 * 2)(3, 3), (I64 * 2)(1, 1)
+    rc = L.lbvh_build_batched(2, vp, nv, tp, nt, 4, 30, None, outs)
+    assert rc == -1 and "mesh 1" in lib.last_error() and not outs[0] and not outs[1]
+    rc = L.lbvh_build_batched(2, vp, nv, (P * 2)(16, 16), nt, 4, 31, None, outs)
+    assert rc == -1
     rc = L.rsi_query(None, None, None, 0, 0, None, None, None, None, None, None)
     assert rc == -1
     assert L.lbvh_free(None) == 0

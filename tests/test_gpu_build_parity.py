@@ -171,3 +171,50 @@ def test_dumps_of_gpu_hierarchy_equal_oracle(rsi):
             got = rsi.LBVH(torch.from_numpy(V).cuda(), torch.from_numpy(T).cuda(), builder=builder).export()
             assert bvh_dump.to_text(got, digits=6) == bvh_dump.to_text(ref, digits=6), (name, builder)
             assert bvh_dump.to_dot(got) == bvh_dump.to_dot(ref), (name, builder)
+
+
+@pytest.mark.parametrize("bits", [30, 63])
+def test_build_many_equals_single_builds(rsi, bits):
+    """One batched build of meshes of very different sizes (1, 2 and 3
+    triangles, duplicate codes, heightfields) gives every mesh the hierarchy
+    a build of its own gives it, bit for bit, and the same answers."""
+    meshes = [(V, T) for name, V, T in _meshes()]
+    m2 = W.heightfield(7, seed=9, n_bumps=1)
+    meshes.append((m2.vertices, m2.triangles))
+    dev = [(torch.from_numpy(V).cuda(), torch.from_numpy(np.ascontiguousarray(T)).cuda()) for V, T in meshes]
+    many = rsi.build_many(dev, morton_bits=bits)
+    assert len(many) == len(dev)
+    for k, ((V, T), b) in enumerate(zip(dev, many)):
+        one = rsi.LBVH(V, T, morton_bits=bits)
+        e1, e2 = one.export(), b.export()
+        for key in e1:
+            assert np.array_equal(e1[key], e2[key]), (k, key)
+        i1, i2 = one.info(), b.info()
+        for key in ("height", "extent_lo", "extent_hi", "max_tri_extent", "n_triangles"):
+            assert i1[key] == i2[key], (k, key)
+        one.close()
+    # the packed nodes and triangles answer the same (c1 and c2 meshes)
+    m = W.config_mesh("c1")
+    F, E = W.rays(W.config_rays("c1"), m)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    k1 = [i for i, (V, T) in enumerate(meshes) if len(T) == len(m.triangles)][0]
+    ref = rsi.LBVH(dev[k1][0], dev[k1][1], morton_bits=bits)
+    for mode in ("any_hit", "count"):
+        a, b = ref.query(dF, dE, mode), many[k1].query(dF, dE, mode)
+        key = "hit" if mode == "any_hit" else "count"
+        assert torch.equal(a[key], b[key]) and torch.equal(a["ambiguous"], b["ambiguous"])
+    for b in many:
+        b.close()
+
+
+def test_build_many_reports_the_bad_mesh(rsi):
+    good = W.heightfield(5, seed=1)
+    V = torch.from_numpy(good.vertices).cuda()
+    T = torch.from_numpy(good.triangles).cuda()
+    bad_T = T.clone()
+    bad_T[3, 1] = 10_000
+    with pytest.raises(rsi.RSIError) as e:
+        rsi.build_many([(V, T), (V, bad_T), (V, T)])
+    assert e.value.code == -8 and "mesh 1" in str(e.value)
+    # the library keeps working
+    assert len(rsi.build_many([(V, T)])) == 1
