@@ -210,7 +210,9 @@ size_t lbvh_node_bytes(void);
  *   surface, or nearly parallel and touching); those results are the
  *   closed-interval reading with crossings closer than 1e-9 in t merged.
  * Segments: d_from, d_to [n_rays][3] float32, device.  n_rays == 0 is a
- * no-op.  Asynchronous unless `stats` is given.
+ * no-op.  Asynchronous unless `stats` is given.  The handle grows its
+ * scratch (the FP64 re-test's queue and pair lists, about 22 B per segment
+ * of the largest batch queried so far) on demand; lbvh_free releases it.
  */
 int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
               const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
