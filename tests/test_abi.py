@@ -81,3 +81,20 @@ def test_host_side_rejections(lib):
     rc = L.rsi_nearest_compact(ctypes.c_void_p(16), None, None, 5, None, None, ctypes.c_void_p(16), None,
                                ctypes.byref(k), None)
     assert rc == -1                            # distances asked for without their input
+
+
+def test_binding_rejects_before_the_library(lib):
+    """Argument checks of the binding that need no GPU."""
+    import torch
+    V = torch.zeros(4, 3, dtype=torch.float32)
+    T = torch.zeros(2, 3, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        lib.LBVH(V, T, builder="octree")
+    with pytest.raises(ValueError):
+        lib.build_many([])
+    with pytest.raises(TypeError):
+        lib.build_many([(V, T)])                      # host tensors
+    with pytest.raises(TypeError):
+        lib.build_many([(V, T.to(torch.int64))])      # int64 indices (Sec. 4.1.2)
+    with pytest.raises(TypeError):
+        lib.build_many([(V.to(torch.float64), T)])
