@@ -356,3 +356,21 @@ def test_fp64_pass_long_pair_list_matches_oracle(rsi):
     assert st["band_rays"] >= 0.9 * k and st["device_error"] == 0
     nr = bvh.nearest(_dev(F), _dev(E))
     assert np.array_equal(nr["tri"].cpu().numpy(), ref["near_tri"])
+
+
+@pytest.mark.parametrize("n", [1, 31, 1 << 18, (1 << 18) + 1, (1 << 18) + (1 << 21) + 7])
+def test_host_path_chunk_boundaries(rsi, n):
+    """The whole-batch host path at its chunk boundaries (a first chunk of
+    2^18 segments, then 2^21): the same results as the device path, with and
+    without the FP64 re-test."""
+    mesh = W.config_mesh("c2")
+    F, E = W.rays(W.config_rays("c2", n), mesh)
+    bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles))
+    pF, pE = torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory()
+    for fp32_only in (False, True):
+        for mode, key in (("any_hit", "hit"), ("count", "count")):
+            d = bvh.query(_dev(F), _dev(E), mode, fp32_only=fp32_only)
+            h = bvh.query_host(pF, pE, mode, fp32_only=fp32_only, stats=True)
+            assert np.array_equal(h[key].numpy(), d[key].cpu().numpy()), (n, mode, fp32_only)
+            assert np.array_equal(h["ambiguous"].numpy(), d["ambiguous"].cpu().numpy()), (n, mode, fp32_only)
+            assert h["stats"]["n_rays"] == n and h["stats"]["device_error"] == 0
