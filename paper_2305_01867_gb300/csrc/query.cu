@@ -1558,8 +1558,8 @@ __global__ void __launch_bounds__(256) k_nearest_finish(QueryArgs A, float* __re
 
 // Stream compaction of the hitting segments in index order (the paper's
 // barycentric result lists only the intersecting rays): per-tile counts, one
-// exclusive scan, and an ordered scatter.  Each thread owns 16 consecutive
-// segments of a 4096-segment tile.
+// exclusive scan, and an ordered scatter.  A block takes a 4096-segment tile
+// in 16 rounds of 256 consecutive segments.
 constexpr int kCompactPer = 16;
 constexpr int kCompactTile = 256 * kCompactPer;
 
@@ -1582,13 +1582,17 @@ __device__ __forceinline__ int block_exclusive_scan256(int v, int* wsum, int& to
     return pre + inc - v;
 }
 
+// Segment r of a tile is t0 + k * 256 + thread (k < kCompactPer): each
+// round of the block reads 256 consecutive entries (coalesced).
 __global__ void __launch_bounds__(256) k_compact_count(const int32_t* __restrict__ tri, int64_t n,
                                                        int* __restrict__ tile_count) {
     __shared__ int wsum[8];
-    const int64_t b0 = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPer;
+    const int64_t t0 = (int64_t)blockIdx.x * kCompactTile;
     int c = 0;
-    for (int k = 0; k < kCompactPer; ++k)
-        if (b0 + k < n && tri[b0 + k] >= 0) ++c;
+    for (int k = 0; k < kCompactPer; ++k) {
+        const int64_t r = t0 + k * 256 + threadIdx.x;
+        if (r < n && tri[r] >= 0) ++c;
+    }
     int total;
     block_exclusive_scan256(c, wsum, total);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = total;
@@ -1615,26 +1619,37 @@ __global__ void __launch_bounds__(256) k_compact_scatter(const int32_t* __restri
                                                          const int* __restrict__ tile_off, int32_t* __restrict__ rays,
                                                          int32_t* __restrict__ tri_out, float* __restrict__ dist_out,
                                                          float* __restrict__ point_out) {
-    __shared__ int wsum[8];
-    const int64_t b0 = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPer;
-    int c = 0;
-    for (int k = 0; k < kCompactPer; ++k)
-        if (b0 + k < n && tri[b0 + k] >= 0) ++c;
-    int total;
-    int pos = tile_off[blockIdx.x] + block_exclusive_scan256(c, wsum, total);
-    for (int k = 0; k < kCompactPer; ++k) {
-        const int64_t r = b0 + k;
-        if (r < n && tri[r] >= 0) {
+    __shared__ int wcnt[8];
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t t0 = (int64_t)blockIdx.x * kCompactTile;
+    int base = tile_off[blockIdx.x];
+    for (int k = 0; k < kCompactPer; ++k) {   // rounds of 256 consecutive segments, in index order
+        const int64_t r = t0 + k * 256 + threadIdx.x;
+        const bool hit = r < n && tri[r] >= 0;
+        const unsigned m = __ballot_sync(kFull, hit);
+        if (lane == 0) wcnt[w] = __popc(m);
+        __syncthreads();
+        int pre = 0, tot = 0;
+        for (int q = 0; q < 8; ++q) {
+            const int c = wcnt[q];
+            if (q < w) pre += c;
+            tot += c;
+        }
+        if (hit) {
+            const int64_t pos = base + pre + __popc(m & lt);
             if (rays) rays[pos] = (int32_t)r;
             if (tri_out) tri_out[pos] = tri[r];
             if (dist_out) dist_out[pos] = dist[r];
             if (point_out) {
-                point_out[3 * (int64_t)pos] = point[3 * r];
-                point_out[3 * (int64_t)pos + 1] = point[3 * r + 1];
-                point_out[3 * (int64_t)pos + 2] = point[3 * r + 2];
+                point_out[3 * pos] = point[3 * r];
+                point_out[3 * pos + 1] = point[3 * r + 1];
+                point_out[3 * pos + 2] = point[3 * r + 2];
             }
-            ++pos;
         }
+        base += tot;
+        __syncthreads();
     }
 }
 
