@@ -84,6 +84,10 @@ typedef struct rsi_options {
                            (up to four child boxes per 128-byte fetch; trees
                            of height > 82 fall back to 2).  Results are the
                            same either way.                                 */
+    int fp64_all;       /* 1: skip the FP32 traversal and settle every
+                           segment with the FP64 re-test (a validation mode:
+                           its answers must equal the default path's; slow).
+                           Device-buffer queries only; not with fp32_only. */
 } rsi_options;
 
 /* Per-query counters, filled on the host when a non-NULL pointer is given

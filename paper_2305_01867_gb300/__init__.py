@@ -36,7 +36,7 @@ class RSIError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("fp32_only", ctypes.c_int), ("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("collect_stats", ctypes.c_int), ("timeout_ns", ctypes.c_int64), ("time_kernels", ctypes.c_int),
-                ("ray_sort_tile", ctypes.c_int), ("node_width", ctypes.c_int)]
+                ("ray_sort_tile", ctypes.c_int), ("node_width", ctypes.c_int), ("fp64_all", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -292,7 +292,7 @@ class LBVH:
 
     def query(self, ray_from, ray_to, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0,
               stats=False, hit=None, count=None, ambiguous=None, want_ambiguous=True, time_kernels=False,
-              ray_sort_tile=0, node_width=0, stream=None):
+              ray_sort_tile=0, node_width=0, fp64_all=False, stream=None):
         """Query segments (device tensors [n, 3] float32).  Returns a dict with
         'hit' (uint8, any-hit mode or count > 0), 'count' (int32, count mode),
         'ambiguous' (uint8) and, with stats=True, 'stats'."""
@@ -313,7 +313,7 @@ class LBVH:
         if ambiguous is None and want_ambiguous:
             ambiguous = torch.empty(n, dtype=torch.uint8, device=dev)
         opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels),
-                      int(ray_sort_tile), int(node_width))
+                      int(ray_sort_tile), int(node_width), int(fp64_all))
         st = Stats()
         check(lib.rsi_query(self._h, _ptr(ray_from), _ptr(ray_to), n, m, ctypes.byref(opt), _ptr(hit), _ptr(count),
                             _ptr(ambiguous), ctypes.byref(st) if stats else None, _stream(stream)))
@@ -349,7 +349,7 @@ class LBVH:
 
     def nearest(self, ray_from, ray_to, *, fp32_only=False, block=0, blocks_per_sm=0, stats=False,
                 want_t=True, want_point=True, want_dist=True, want_ambiguous=True, time_kernels=False,
-                ray_sort_tile=0, node_width=0, stream=None):
+                ray_sort_tile=0, node_width=0, fp64_all=False, stream=None):
         """Barycentric mode per segment (rsi_query_nearest): 'tri' (int32, -1
         when no hit), 't', 'point' [n, 3], 'dist' (float32), 'ambiguous'."""
         import torch
@@ -367,7 +367,7 @@ class LBVH:
         dist = torch.empty(n, dtype=torch.float32, device=dev) if want_dist else None
         amb = torch.empty(n, dtype=torch.uint8, device=dev) if want_ambiguous else None
         opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels),
-                      int(ray_sort_tile), int(node_width))
+                      int(ray_sort_tile), int(node_width), int(fp64_all))
         st = Stats()
         check(lib.rsi_query_nearest(self._h, _ptr(ray_from), _ptr(ray_to), n, ctypes.byref(opt), _ptr(tri), _ptr(t),
                                     _ptr(point), _ptr(dist), _ptr(amb), ctypes.byref(st) if stats else None,

@@ -1819,6 +1819,14 @@ __global__ void __launch_bounds__(256) k_verify_proposals(QueryArgs A, const uin
     if (left) order[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)r;
 }
 
+// Validation mode (rsi_options.fp64_all): every segment is queued for the
+// FP64 re-test, none is settled by the FP32 traversal.
+__global__ void k_queue_all(int32_t* __restrict__ band_ids, int64_t n, DevCounters* c) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) band_ids[i] = (int32_t)i;
+    if (i == 0) c->band_count = (int)n;
+}
+
 __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->band_count = 0;
     c->next_ray = 0;
@@ -1950,6 +1958,8 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (o.blocks_per_sm < 0) return fail(RSI_ERR_INVALID_ARG, "rsi_query: blocks_per_sm < 0");
     if (o.node_width != 0 && o.node_width != 2 && o.node_width != 4)
         return fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2 or 4");
+    if (o.fp64_all && (o.fp32_only || order))
+        return fail(RSI_ERR_INVALID_ARG, "rsi_query: fp64_all excludes fp32_only and the learned query");
     const bool wide = o.node_width == 4;
     const int block = o.block > 0 ? o.block : 256;
     const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
@@ -1979,7 +1989,9 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
         k_reset_query<<<1, 1, 0, s>>>(ctr, (unsigned long long)n);
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[0], s));
-    if (mode == RSI_ANY_HIT) {
+    if (o.fp64_all) {
+        k_queue_all<<<grid_for(n, 256), 256, 0, s>>>(band_ids, n, ctr);
+    } else if (mode == RSI_ANY_HIT) {
         if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, wide, grid, block, s);
         else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, wide, grid, block, s);
     } else if (mode == RSI_COUNT) {
@@ -2406,6 +2418,7 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
     }
     rsi_options o = {};
     if (opt) o = *opt;
+    if (o.fp64_all) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_host: fp64_all is for device-buffer queries");
     if (n_rays <= kHostWhole && o.ray_sort_tile == 0) {
         rsi::DeviceCtx* c = rsi::device_ctx();
         if (!c) return rsi::fail(RSI_ERR_CUDA, "rsi_query_host: no device context");

@@ -374,3 +374,29 @@ def test_host_path_chunk_boundaries(rsi, n):
             assert np.array_equal(h[key].numpy(), d[key].cpu().numpy()), (n, mode, fp32_only)
             assert np.array_equal(h["ambiguous"].numpy(), d["ambiguous"].cpu().numpy()), (n, mode, fp32_only)
             assert h["stats"]["n_rays"] == n and h["stats"]["device_error"] == 0
+
+
+@pytest.mark.parametrize("cfg,n", [("c2", 10_000_000), ("c3", 2_000_000)])
+def test_fp32_decisions_equal_fp64_everywhere(rsi, cfg, n):
+    """Every segment of a full-size batch (c2: all 1e7; c3: a 2e6 slice with
+    1 % grazing segments) answered twice: by the default path (FP32 with
+    certified decisions, FP64 for the band) and with every segment settled by
+    the FP64 re-test. All outputs of all three modes must be identical -- the
+    claim that a certain FP32 decision is the FP64 decision, checked on every
+    segment rather than on an oracle sample."""
+    mesh = W.config_mesh(cfg)
+    F, E = W.rays(W.config_rays(cfg), mesh, count=n)
+    bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles), morton_bits=63 if cfg == "c3" else 30)
+    dF, dE = _dev(F), _dev(E)
+    for mode, key in (("any_hit", "hit"), ("count", "count")):
+        a = bvh.query(dF, dE, mode)
+        b = bvh.query(dF, dE, mode, fp64_all=True, stats=True)
+        assert b["stats"]["band_rays"] == n
+        assert torch.equal(a[key], b[key]), mode
+        assert torch.equal(a["ambiguous"], b["ambiguous"]), mode
+    a, b = bvh.nearest(dF, dE), bvh.nearest(dF, dE, fp64_all=True)
+    for k in ("tri", "t", "dist", "ambiguous"):
+        assert torch.equal(a[k], b[k]), k
+    assert torch.equal(torch.nan_to_num(a["point"], nan=-7.0), torch.nan_to_num(b["point"], nan=-7.0))
+    with pytest.raises(rsi.RSIError):
+        bvh.query(dF[:10], dE[:10], "any_hit", fp64_all=True, fp32_only=True)
