@@ -93,6 +93,39 @@ def test_first_adam_step_closed_form():
     assert np.allclose(out["w"], expect, rtol=1e-12, atol=0)
 
 
+def test_later_adam_steps_closed_form():
+    """With a constant gradient the bias-corrected moments stay g and g^2,
+    so every step is -lr g / (|g| + eps); with the gradient g then -g, the
+    second step's first moment is -(1 - b1)^2 g / (1 - b1^2) = -g (1 - b1) /
+    (1 + b1) and its second moment still g^2."""
+    g = np.array([0.3, -2.0, 1e-3])
+    p, state = {"w": np.zeros(3)}, {}
+    for t in range(1, 4):
+        p = mlp.adam_step(p, {"w": g}, state, lr=0.01, b1=0.9, b2=0.999, eps=1e-8)
+        assert np.allclose(p["w"], -0.01 * t * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    p, state = {"w": np.zeros(3)}, {}
+    p1 = mlp.adam_step(p, {"w": g}, state, lr=0.01, b1=0.9, b2=0.999, eps=1e-8)
+    p2 = mlp.adam_step(p1, {"w": -g}, state, lr=0.01, b1=0.9, b2=0.999, eps=1e-8)
+    step2 = -0.01 * (-g * (1 - 0.9) / (1 + 0.9)) / (np.abs(g) + 1e-8)
+    assert np.allclose(p2["w"] - p1["w"], step2, rtol=1e-10, atol=0)
+    assert state["t"] == 2
+
+
 def test_top4_order():
     z = np.array([[0.1, 5.0, 3.0, 5.0, -1.0, 4.0] + [0.0] * 250])
     assert mlp.top4(z).tolist() == [[1, 3, 5, 2]]
+
+
+def test_features_map_the_extent_to_the_unit_cube():
+    """End points at the low / high corner of the extent map to -1 / +1,
+    the centre to 0, points far outside clamp to -4 / +4, a flat axis maps
+    through a unit span, and the ten padding inputs are zero."""
+    lo, hi = np.array([1.0, -2.0, 3.0]), np.array([3.0, 2.0, 3.0])
+    F = np.array([lo, (lo + hi) / 2, [100.0, -100.0, 3.0]])
+    E = np.array([hi, lo, [1.0, 2.0, 3.5]])
+    x = mlp.features(F, E, lo, hi)
+    assert x.shape == (3, mlp.D_PAD)
+    np.testing.assert_array_equal(x[0, :6], [-1, -1, -1, 1, 1, -1])
+    np.testing.assert_array_equal(x[1, :6], [0, 0, -1, -1, -1, -1])
+    np.testing.assert_array_equal(x[2, :6], [4, -4, -1, -1, 1, 0])
+    assert not x[:, 6:].any()

@@ -355,3 +355,193 @@ def test_nearest_on_heightfield_closed_form():
         assert abs(r["near_t"][k] - (z + 1.0) / 2.0) < 1e-6
         np.testing.assert_allclose(r["near_point"][k], [x, y, z], atol=1e-6)
         assert abs(r["near_dist"][k] - (z + 1.0)) < 1e-6
+
+
+# ------------------------------------------------------------ the nearly-parallel branch
+def test_nearest_none_when_every_crossing_lies_past_the_end():
+    """A segment that stops before the plates it points at meets none of
+    them: the inclusive test needs t <= 1 as well as t >= 0 (Sec. 1: a ray is
+    the segment between its two end points)."""
+    V, T = _plates([0.5, 0.0, 0.25])
+    r = oracle.query(V, T, [[0.25, 0.25, -1.0]], [[0.25, 0.25, -0.5]])
+    assert r["near_tri"][0] == -1 and r["count"][0] == 0 and r["hit"][0] == 0
+    cls, q = oracle.classify_pair([0.25, 0.25, -1.0], [0.25, 0.25, -0.5], *TRI)
+    assert cls == MISS and q["incl"] == 0 and q["t"] == 2.0
+
+
+def test_det_rel_is_scale_free_closed_form():
+    """det_rel = det / (|d||e1||e2|) is the sine of the segment's elevation
+    over the plane times sin(e1, e2): for the unit right triangle and a
+    segment rising 2h over a run of L it is -2h / |d|.  A 1000-long segment
+    tilted by 1e-7 through the middle of the face is in the parallel branch
+    (|det_rel| <= tau) and, as it meets the face, ambiguous; the same tilt
+    over a unit run gives the same class."""
+    for half, h in [(500.0, 5e-5), (0.5, 5e-8)]:
+        s = np.array([0.25 - half, 0.25, -h], np.float32)
+        e = np.array([0.25 + half, 0.25, h], np.float32)
+        cls, q = oracle.classify_pair(s, e, *TRI)
+        d = e.astype(np.float64) - s.astype(np.float64)
+        assert q["det_rel"] == pytest.approx(-d[2] / np.linalg.norm(d), rel=1e-12)
+        assert abs(q["det_rel"]) < oracle.TAU and cls == AMB and q["dist"] == 0.0
+
+
+@pytest.mark.parametrize("z,expect", [(1e-4, AMB), (9e-4, AMB), (1.1e-3, MISS), (2e-3, MISS)])
+def test_parallel_band_is_relative_to_segment_length(z, expect):
+    """An exactly parallel segment of length 1000 passing over the face at
+    height z is z away from it; the band is tau |d| = 1e-3 wide."""
+    s, e = [-500.0, 0.25, z], [500.0, 0.25, z]
+    cls, q = oracle.classify_pair(s, e, *TRI)
+    assert q["dist"] == pytest.approx(float(np.float32(z)), rel=1e-12)
+    assert cls == expect
+
+
+def test_skew_pass_beside_an_edge_closed_form():
+    """A segment rising with slope 0.9e-6 along y = 0.5, from x = -0.1 to
+    x = 0.45, passes over the edge x = 0 of the unit right triangle at height
+    3e-7 and ends over the face at 7.05e-7.  Its nearest approach is to the
+    inside of that edge: the distance between the two lines, z(0) /
+    sqrt(1 + slope^2).  That is within tau |d| = 5.5e-7 (ambiguous), while
+    the end point alone (7.05e-7) is not."""
+    s = np.array([-0.1, 0.5, 3e-7 - 0.1 * 0.9e-6], np.float32)
+    e = np.array([0.45, 0.5, 3e-7 + 0.45 * 0.9e-6], np.float32)
+    cls, q = oracle.classify_pair(s, e, *TRI)
+    s64, e64 = s.astype(np.float64), e.astype(np.float64)
+    slope = (e64[2] - s64[2]) / (e64[0] - s64[0])
+    z0 = s64[2] + (0.0 - s64[0]) * slope
+    assert abs(q["det_rel"]) < oracle.TAU and q["incl"] == 0
+    assert q["dist"] == pytest.approx(z0 / np.sqrt(1 + slope * slope), rel=1e-9)
+    assert cls == AMB
+
+
+def _nearly_parallel_pairs(rng, n):
+    """Random triangles and segments tilted by up to 2e-6 rad out of the
+    triangle's plane, offset from it by up to 3e-6 |d|, passing over, beside
+    or across the face: both sides of the det_rel and distance bands."""
+    out = []
+    while len(out) < n:
+        a, b, c = rng.uniform(-1, 1, (3, 3))
+        nrm = np.cross(b - a, c - a)
+        if np.linalg.norm(nrm) < 0.2:
+            continue
+        nrm /= np.linalg.norm(nrm)
+        u = (b - a) / np.linalg.norm(b - a)
+        w = np.cross(nrm, u)
+        phi = rng.uniform(0, 2 * np.pi)
+        d = np.cos(phi) * u + np.sin(phi) * w
+        d = d + rng.uniform(-2e-6, 2e-6) * nrm
+        d /= np.linalg.norm(d)
+        L = rng.uniform(0.05, 3.0)
+        cen = (a + b + c) / 3
+        p = cen + rng.uniform(-1, 1) * u + rng.uniform(-1, 1) * w + rng.uniform(-3e-6, 3e-6) * L * nrm
+        f = rng.uniform(0, 1)
+        out.append([x.astype(np.float32) for x in (p - f * L * d, p + (1 - f) * L * d, a, b, c)])
+    return out
+
+
+def test_classification_is_scale_free():
+    """The margins are relative (det_rel, tau |d|), so scaling the whole
+    configuration by a power of two -- exact in FP32 and FP64 -- changes no
+    class, leaves u, v, t, det_rel unchanged bit for bit and scales the
+    distance exactly."""
+    rng = np.random.default_rng(21)
+    n_par = 0
+    for s, e, a, b, c in _nearly_parallel_pairs(rng, 1500) + _near_boundary_pairs(rng, 500):
+        cls, q = oracle.classify_pair(s, e, a, b, c)
+        n_par += q["dist"] >= 0
+        for k in (-5, 7):
+            f = np.float32(2.0 ** k)
+            cls_k, q_k = oracle.classify_pair(s * f, e * f, a * f, b * f, c * f)
+            assert cls_k == cls
+            assert (q_k["u"], q_k["v"], q_k["t"], q_k["det_rel"]) == (q["u"], q["v"], q["t"], q["det_rel"])
+            assert q_k["dist"] == (q["dist"] * 2.0 ** k if q["dist"] >= 0 else q["dist"])
+    assert n_par > 500
+
+
+def _point_triangle_distance_qp(p, a, b, c):
+    """|p - closest point of the triangle|, by minimising |a + u e1 + v e2 - p|
+    over u, v >= 0, u + v <= 1: the unconstrained minimiser (2x2 normal
+    equations) if feasible, else the best of the three clamped edges."""
+    e1, e2, r = b - a, c - a, p - a
+    G = np.array([[e1 @ e1, e1 @ e2], [e1 @ e2, e2 @ e2]])
+    u, v = np.linalg.solve(G, [e1 @ r, e2 @ r])
+    if u >= 0 and v >= 0 and u + v <= 1:
+        return np.linalg.norm(a + u * e1 + v * e2 - p)
+    best = np.inf
+    for x, y in ((a, b), (b, c), (c, a)):
+        g = y - x
+        tt = min(max((p - x) @ g / (g @ g), 0.0), 1.0)
+        best = min(best, np.linalg.norm(x + tt * g - p))
+    return best
+
+
+def _segment_triangle_distance_search(s, e, a, b, c):
+    """Minimum over the segment of the point-triangle distance, a convex
+    function of the segment parameter: golden-section search."""
+    f = lambda x: _point_triangle_distance_qp(s + x * (e - s), a, b, c)
+    lo, hi = 0.0, 1.0
+    g = (np.sqrt(5) - 1) / 2
+    x1, x2 = hi - g * (hi - lo), lo + g * (hi - lo)
+    f1, f2 = f(x1), f(x2)
+    for _ in range(90):
+        if f1 < f2:
+            hi, x2, f2 = x2, x1, f1
+            x1 = hi - g * (hi - lo)
+            f1 = f(x1)
+        else:
+            lo, x1, f1 = x1, x2, f2
+            x2 = lo + g * (hi - lo)
+            f2 = f(x2)
+    return min(f1, f2, f(0.0), f(1.0))
+
+
+def test_parallel_branch_distance_brute_force():
+    """On the nearly-parallel branch the oracle's distance (end points
+    against the face, the segment against the three edges) equals a direct
+    minimisation of the point-triangle distance along the segment."""
+    rng = np.random.default_rng(23)
+    checked = 0
+    for s, e, a, b, c in _nearly_parallel_pairs(rng, 600):
+        cls, q = oracle.classify_pair(s, e, a, b, c)
+        if q["dist"] < 0 or q["incl"]:
+            continue
+        P = [x.astype(np.float64) for x in (s, e, a, b, c)]
+        ref = _segment_triangle_distance_search(*P)
+        L = np.linalg.norm(P[1] - P[0])
+        assert abs(q["dist"] - ref) <= 1e-10 * L + 1e-9 * ref
+        checked += 1
+    assert checked > 200
+
+
+def test_decisive_hit_settles_boolean_mode():
+    """Boolean mode needs one hit: a decisive crossing of one plate settles
+    the answer although the segment also runs through an edge of another
+    (not ambiguous), while intercept_count is ambiguous on that ray and
+    counts both crossing points.  Without the decisive plate the boolean
+    answer rests on the edge alone and is ambiguous."""
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0],
+                  [0.25, 0, 0.5], [1, 0, 0.5], [0.25, 1, 0.5]], np.float32)
+    T = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    F, E = [[0.25, 0.25, -1.0]], [[0.25, 0.25, 1.0]]
+    r = oracle.query(V, T, F, E)
+    assert (r["hit"][0], r["amb_hit"][0], r["amb_count"][0], r["count"][0]) == (1, 0, 1, 2)
+    assert r["near_tri"][0] == 0 and r["near_t"][0] == 0.5
+    r = oracle.query(V, T[1:], F, E)
+    assert (r["hit"][0], r["amb_hit"][0], r["amb_count"][0], r["count"][0]) == (1, 1, 1, 1)
+
+
+# ------------------------------------------------------------ surface extent
+def test_extent_equals_library_minmax():
+    """Per-axis minimum and maximum over all vertices (Sec. 3.3), against
+    numpy's reductions, including one vertex, all-negative coordinates and
+    the extreme vertex first or last."""
+    rng = np.random.default_rng(9)
+    cases = [rng.uniform(-5, 5, (100, 3)), rng.uniform(-9, -1, (50, 3)), rng.uniform(1, 9, (50, 3)),
+             np.array([[3.0, -2.0, 7.0]])]
+    sorted_desc = np.sort(rng.uniform(-1, 1, (20, 3)), axis=0)[::-1]
+    cases += [sorted_desc, sorted_desc[::-1].copy()]
+    for V in cases:
+        V = V.astype(np.float32)
+        lo, hi = oracle.extent(V)
+        assert lo.tolist() == V.min(0).tolist() and hi.tolist() == V.max(0).tolist()
+    with pytest.raises(ValueError):
+        oracle.extent(np.array([[0, 0, 0], [np.nan, 1, 1]], np.float32))
