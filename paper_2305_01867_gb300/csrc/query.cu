@@ -2127,21 +2127,24 @@ extern "C" int rsi_last_query_ms(rsi_bvh_t h, float* traverse_ms, float* retest_
     return RSI_OK;
 }
 
-static int check_query_args(rsi_bvh_t h, const void* from, const void* to, int64_t n, int mode, const void* hit,
-                            const void* count) {
-    if (!h) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: NULL handle");
-    if (n < 0 || n > 0x7FFFFFFFll) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: need 0 <= n_rays < 2^31");
-    if (mode != RSI_ANY_HIT && mode != RSI_COUNT) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: bad mode");
-    if (n > 0 && (!from || !to)) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: NULL segment pointer");
-    if (n > 0 && mode == RSI_ANY_HIT && !hit) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: any-hit needs hit");
-    if (n > 0 && mode == RSI_COUNT && !count) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: count needs count");
+// Argument checks shared by the boolean / intercept_count entry points; `fn`
+// names the caller in the error message.
+static int check_query_args(const char* fn, rsi_bvh_t h, const void* from, const void* to, int64_t n, int mode,
+                            const void* hit, const void* count) {
+    const std::string f(fn);
+    if (!h) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": NULL handle");
+    if (n < 0 || n > 0x7FFFFFFFll) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": need 0 <= n_rays < 2^31");
+    if (mode != RSI_ANY_HIT && mode != RSI_COUNT) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": bad mode");
+    if (n > 0 && (!from || !to)) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": NULL segment pointer");
+    if (n > 0 && mode == RSI_ANY_HIT && !hit) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": any-hit needs hit");
+    if (n > 0 && mode == RSI_COUNT && !count) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": count needs count");
     return RSI_OK;
 }
 
 extern "C" int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
                          const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
                          rsi_stats* stats, void* stream) {
-    int rc = check_query_args(h, d_from, d_to, n_rays, mode, d_hit, d_count);
+    int rc = check_query_args("rsi_query", h, d_from, d_to, n_rays, mode, d_hit, d_count);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (n_rays == 0) {
@@ -2409,7 +2412,7 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
 extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n_rays, int mode,
                               const rsi_options* opt, uint8_t* h_hit, int32_t* h_count, uint8_t* h_ambiguous,
                               rsi_stats* stats, void* stream) {
-    int rc = check_query_args(h, h_from, h_to, n_rays, mode, h_hit, h_count);
+    int rc = check_query_args("rsi_query_host", h, h_from, h_to, n_rays, mode, h_hit, h_count);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (n_rays == 0) {
@@ -2521,7 +2524,7 @@ extern "C" int rsi_cluster_labels(rsi_bvh_t h, const float* d_from, const float*
 extern "C" int rsi_query_learned(rsi_bvh_t h, rsi_mlp_t m, const float* d_from, const float* d_to, int64_t n_rays,
                                  const rsi_options* opt, uint8_t* d_hit, uint8_t* d_ambiguous, rsi_stats* stats,
                                  void* stream) {
-    int rc = check_query_args(h, d_from, d_to, n_rays, RSI_ANY_HIT, d_hit, nullptr);
+    int rc = check_query_args("rsi_query_learned", h, d_from, d_to, n_rays, RSI_ANY_HIT, d_hit, nullptr);
     if (rc) return rc;
     if (!m) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_learned: NULL network");
     if (n_rays > 0x7FFFFF00ll) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_learned: too many segments");
@@ -2830,7 +2833,7 @@ int noalloc_scratch(void** out) {
 extern "C" int rsi_query_noalloc(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
                                  const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
                                  void* stream) {
-    int rc = check_query_args(h, d_from, d_to, n_rays, mode, d_hit, d_count);
+    int rc = check_query_args("rsi_query_noalloc", h, d_from, d_to, n_rays, mode, d_hit, d_count);
     if (rc) return rc;
     if (n_rays > (int64_t)RSI_NOALLOC_MAX_RAYS)
         return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_noalloc: n_rays " + std::to_string(n_rays) +

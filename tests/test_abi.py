@@ -98,3 +98,47 @@ def test_binding_rejects_before_the_library(lib):
         lib.build_many([(V, T.to(torch.int64))])      # int64 indices (Sec. 4.1.2)
     with pytest.raises(TypeError):
         lib.build_many([(V.to(torch.float64), T)])
+
+
+def test_every_entry_point_rejects_missing_arguments(lib):
+    """Each call that takes a handle or buffers answers RSI_ERR_INVALID_ARG
+    (-1), with a message naming the call, when one is missing or a size is
+    out of range -- before any device work, so no GPU is needed here."""
+    L, P = lib.lib, ctypes.c_void_p
+    f = ctypes.c_float()
+    k = ctypes.c_int64()
+    cases = {
+        "lbvh_info": lambda: L.lbvh_info(None, None),
+        "lbvh_export": lambda: L.lbvh_export(None, None, None),
+        "lbvh_build_host": lambda: L.lbvh_build_host(None, 3, None, 1, 4, 30, None, None),
+        "rsi_query_host": lambda: L.rsi_query_host(None, None, None, 5, 0, None, None, None, None, None, None),
+        "rsi_query_noalloc": lambda: L.rsi_query_noalloc(None, None, None, 5, 0, None, None, None, None, None),
+        "rsi_query_nearest": lambda: L.rsi_query_nearest(None, None, None, 5, None, None, None, None, None, None,
+                                                         None, None),
+        "rsi_nearest_compact": lambda: L.rsi_nearest_compact(None, None, None, -1, None, None, None, None,
+                                                             ctypes.byref(k), None),
+        "rsi_batch_create": lambda: L.rsi_batch_create(None, 0, 0, None, None, None),
+        "rsi_query_batched": lambda: L.rsi_query_batched(None, None),
+        "rsi_batch_post": lambda: L.rsi_batch_post(None, 0, None),
+        "rsi_batch_stats": lambda: L.rsi_batch_stats(None, None, None),
+        "rsi_autotune": lambda: L.rsi_autotune(None, None, None, 5, 0, None, None, None, None),
+        "rsi_mlp_create": lambda: L.rsi_mlp_create(1, None),
+        "rsi_mlp_set_params": lambda: L.rsi_mlp_set_params(None, None, None),
+        "rsi_mlp_get_params": lambda: L.rsi_mlp_get_params(None, None, None, None),
+        "rsi_mlp_forward": lambda: L.rsi_mlp_forward(None, None, None, None, 5, None, None, None),
+        "rsi_mlp_status": lambda: L.rsi_mlp_status(None, None),
+        "rsi_mlp_activation": lambda: L.rsi_mlp_activation(None, -1, None, None, None, None),
+        "rsi_mlp_train_step": lambda: L.rsi_mlp_train_step(None, None, None, None, None, 5, 1e-3, 1, None, None),
+        "rsi_mlp_reset_optimizer": lambda: L.rsi_mlp_reset_optimizer(None, None),
+        "rsi_cluster_labels": lambda: L.rsi_cluster_labels(None, None, None, 5, None, None),
+        "rsi_query_learned": lambda: L.rsi_query_learned(None, None, None, None, 5, None, None, None, None, None),
+        "rsi_last_query_ms": lambda: L.rsi_last_query_ms(None, ctypes.byref(f), ctypes.byref(f)),
+    }
+    for name, call in cases.items():
+        assert call() == -1, name
+        assert name in lib.last_error(), (name, lib.last_error())
+    # releasing nothing is not an error
+    assert L.rsi_batch_free(None) == 0 and L.rsi_mlp_free(None) == 0
+    # the network's parameter count follows from its shape: 16x128 + 128x128 +
+    # 128x256 weights and 128 + 128 + 256 biases
+    assert L.rsi_mlp_num_params() == 16 * 128 + 128 * 128 + 128 * 256 + 128 + 128 + 256
