@@ -173,6 +173,18 @@ def max_over_ranks(pg, value: float, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(pg, values, device):
+    """Element-wise sum of a few integer counters over all ranks: the one
+    exchange of the sharded path (segments sent to the FP64 re-test and left
+    ambiguous), taken after the timed region."""
+    if pg is None:
+        return [int(v) for v in values]
+    import torch
+    t = torch.tensor([int(v) for v in values], dtype=torch.int64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return [int(x) for x in t.tolist()]
+
+
 def run_reference(args, ws, rank):
     """The FP64 oracle as it stands, on this machine's host cores."""
     if rank != 0:
@@ -726,6 +738,8 @@ def main():
     bvh = rsi.LBVH(dV, dT)
     st_c = bvh.query(dF, dE, "count", stats=True)["stats"]
     st_a = bvh.query(dF, dE, "any_hit", stats=True)["stats"]
+    job_counts = sum_over_ranks(pg, [st_c["band_rays"], st_c["ambiguous"], st_a["band_rays"], st_a["ambiguous"]],
+                                dev)
     height = bvh.info()["height"]
     # traversal kernel time by node width (child-pair vs four-wide), same answers
     widths = {}
@@ -772,6 +786,8 @@ def main():
                      "tri_tests_per_ray_count": st_c["tri_tests"] / n, "band_rays_count": st_c["band_rays"],
                      "ambiguous_count": st_c["ambiguous"], "node_visits_per_ray_any": st_a["node_visits"] / n,
                      "band_rays_any": st_a["band_rays"], "ambiguous_any": st_a["ambiguous"]},
+        "counters_all_ranks": dict(zip(("band_rays_count", "ambiguous_count", "band_rays_any", "ambiguous_any"),
+                                       job_counts)),
         "node_width": widths,
     }
     if not args.no_builders:
