@@ -1,0 +1,205 @@
+"""The two arguments that make the FP32 traversal exact, checked on the CPU
+against the oracle (no GPU).
+
+1. Culling: a (segment, triangle) pair that is a hit or ambiguous in the FP64
+   definition is never pruned.  Its segment, extended to t in [-tau, 1 + tau],
+   meets the triangle's box widened per axis by tau |d|_1 + 2 tau D_axis
+   (D_axis the box side): at a non-parallel pair the plane point has
+   barycentric weights >= -tau; at a parallel one some point of the segment
+   lies within tau |d| of the triangle.  The traversal pads node boxes by
+   4 tau (|d|_1 + D_max,axis) and rounds outward, so it keeps every such box.
+2. Certainty: the FP32 Moller-Trumbore test (Sec. 1) decides on numerators
+   with forward error bounds (16 u times the same expression in magnitudes);
+   a pair it calls a certain hit or a certain miss has that class in FP64.
+
+The traversal's FP32 formulas are restated here in numpy float32 -- each dot
+and cross product in two evaluation orders, plain and with fused
+multiply-adds, since the compiler may contract either way -- and run over
+near-boundary, nearly-parallel and near-threshold pairs whose class the
+oracle gives.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from test_oracle_pins import _near_boundary_pairs, _nearly_parallel_pairs
+
+MISS, HIT, AMB = oracle.PAIR_MISS, oracle.PAIR_HIT, oracle.PAIR_AMBIGUOUS
+BAND = 2
+TAU = 1e-6
+
+F32, F64 = np.float32, np.float64
+kU = F32(2.0 ** -24)
+kErrK = F32(16.0) * kU
+kTauHi = F32(1.000001e-6)
+kWiden = F32(1e-6)
+
+
+# ------------------------------------------------------------ float32 restatement
+def _fma(a, b, c):
+    """Single-rounded a * b + c (the product is exact in float64)."""
+    return (a.astype(F64) * b.astype(F64) + c.astype(F64)).astype(F32)
+
+
+def _dot(a, b, fused):
+    if fused:
+        return _fma(a[:, 2], b[:, 2], _fma(a[:, 1], b[:, 1], a[:, 0] * b[:, 0]))
+    return (a[:, 0] * b[:, 0] + a[:, 1] * b[:, 1]) + a[:, 2] * b[:, 2]
+
+
+def _cross(a, b, fused, sign=-1):
+    """a x b (sign -1), or the same products added (sign +1: the magnitude bound)."""
+    out = np.empty_like(a)
+    for k, (i, j) in enumerate(((1, 2), (2, 0), (0, 1))):
+        if fused:
+            out[:, k] = _fma(a[:, i], b[:, j], F32(sign) * (a[:, j] * b[:, i]))
+        else:
+            out[:, k] = a[:, i] * b[:, j] + F32(sign) * (a[:, j] * b[:, i])
+    return out
+
+
+def tri_fp32(s, e, a, b, c, fused):
+    """Certain hit / certain miss / band of each pair, as the traversal decides."""
+    d, e1, e2, sv = e - s, b - a, c - a, s - a
+    p = _cross(d, e2, fused)
+    det = _dot(e1, p, fused)
+    q = _cross(sv, e1, fused)
+    T = _dot(e2, q, fused)
+    ad, ae1, ae2, asv = np.abs(d), np.abs(e1), np.abs(e2), np.abs(sv)
+    pa, qa = _cross(ad, ae2, fused, +1), _cross(asv, ae1, fused, +1)
+    errdet = kErrK * _dot(ae1, pa, fused) + F32(1e-35)
+    errT = kErrK * _dot(ae2, qa, fused) + F32(1e-35)
+    dl1 = (ad[:, 0] + ad[:, 1]) + ad[:, 2]
+    n1 = lambda x: (x[:, 0] + x[:, 1]) + x[:, 2]
+    thr = ((kTauHi * (dl1 * n1(ae1))) * n1(ae2)) * F32(1.000001)
+    Tm = T - det
+    errTm = (errT + errdet) + F32(2.0) * kU * (np.abs(T) + np.abs(det))
+    U, V = _dot(sv, p, fused), _dot(d, q, fused)
+    miss0 = ((T > 0) == (Tm > 0)) & (np.minimum(np.abs(T) - errT, np.abs(Tm) - errTm) > thr)
+    D = np.abs(det)
+    sure = D - errdet > thr
+    sg = np.where(det > 0, F32(1), F32(-1))
+    errU = kErrK * _dot(asv, pa, fused) + F32(1e-35)
+    errV = kErrK * _dot(ad, qa, fused) + F32(1e-35)
+    Us, Vs, Ts = sg * U, sg * V, sg * T
+    Ws = (D - Us) - Vs
+    errW = ((errdet + errU) + errV) + F32(2.0) * kU * ((D + np.abs(U)) + np.abs(V))
+    Tms = D - Ts
+    lim = kTauHi * (D + errdet) * F32(1.000001)
+    hit = sure & (Us - errU > lim) & (Vs - errV > lim) & (Ws - errW > lim) & (Ts - errT > lim) & (Tms - errTm > lim)
+    miss1 = sure & ((Us + errU < -lim) | (Vs + errV < -lim) | (Ws + errW < -lim) | (Ts + errT < -lim)
+                    | (Tms + errTm < -lim))
+    return np.where(miss0, MISS, np.where(hit, HIT, np.where(miss1, MISS, BAND)))
+
+
+def _round_dir(exact, up):
+    """float32 rounding of a float64 value toward +inf (up) or -inf."""
+    r = exact.astype(F32)
+    if up:
+        return np.where(r.astype(F64) < exact, np.nextafter(r, F32(np.inf)), r)
+    return np.where(r.astype(F64) > exact, np.nextafter(r, F32(-np.inf)), r)
+
+
+def slab_pass(s, e, lo, hi, dmax, fused):
+    """The traversal's padded slab test of one box per segment."""
+    d = e - s
+    inv = np.where(np.abs(d) < F32(1e-20), np.copysign(F32(1e20), d), F32(1) / np.where(d == 0, F32(1), d))
+    dl1 = (np.abs(d[:, 0]) + np.abs(d[:, 1])) + np.abs(d[:, 2])
+    k = F32(4.0) * kTauHi
+    pad = _round_dir(k.astype(F64) * _round_dir(dl1[:, None].astype(F64) + dmax.astype(F64), True).astype(F64), True)
+    slo = _round_dir(s.astype(F64) + pad.astype(F64), True)
+    shi = _round_dir(s.astype(F64) - pad.astype(F64), False)
+    t0, t1 = (lo - slo) * inv, (hi - shi) * inv
+    tn = np.minimum(t0, t1).max(axis=1)
+    tf = np.maximum(t0, t1).min(axis=1)
+    if fused:
+        tn, tf = _fma(-np.abs(tn), kWiden, tn), _fma(np.abs(tf), kWiden, tf)
+    else:
+        tn, tf = tn - np.abs(tn) * kWiden, tf + np.abs(tf) * kWiden
+    return (tn <= tf) & (tn <= F32(1)) & (tf >= F32(0))
+
+
+# ------------------------------------------------------------ pairs
+def _margin_pairs(rng, n):
+    """Segments through a plane point with one barycentric weight, or t, within
+    a few tau of a decision threshold (-tau, tau, 1 - tau, 1 + tau)."""
+    out = []
+    while len(out) < n:
+        a = rng.uniform(-1, 1, 3)
+        b, c = a + rng.uniform(-0.5, 0.5, 3), a + rng.uniform(-0.5, 0.5, 3)
+        nrm = np.cross(b - a, c - a)
+        if np.linalg.norm(nrm) < 1e-3:
+            continue
+        w3 = rng.dirichlet([1, 1, 1])
+        k = rng.integers(0, 3)
+        w3[k] = rng.choice([-1, 1]) * TAU * rng.uniform(0.25, 3.0)
+        w3[(k + 1) % 3] = 1 - w3[k] - w3[(k + 2) % 3]
+        p = w3[0] * a + w3[1] * b + w3[2] * c
+        dvec = rng.normal(size=3)
+        dvec /= np.linalg.norm(dvec)
+        L = 10.0 ** rng.uniform(-2, 0.5)
+        t = rng.choice([rng.uniform(0.1, 0.9), TAU * rng.uniform(-3, 3), 1 + TAU * rng.uniform(-3, 3)])
+        out.append([x.astype(F32) for x in (p - t * L * dvec, p + (1 - t) * L * dvec, a, b, c)])
+    return out
+
+
+@pytest.fixture(scope="module")
+def pairs():
+    rng = np.random.default_rng(31)
+    P = _near_boundary_pairs(rng, 8000) + _nearly_parallel_pairs(rng, 6000) + _margin_pairs(rng, 12000)
+    cls = np.array([oracle.classify_pair(*x)[0] for x in P])
+    S, E, A, B, C = (np.stack([x[i] for x in P]) for i in range(5))
+    return S, E, A, B, C, cls
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_certain_fp32_decisions_are_fp64_decisions(pairs, fused):
+    S, E, A, B, C, cls = pairs
+    with np.errstate(all="ignore"):
+        got = tri_fp32(S, E, A, B, C, fused)
+    assert np.all(cls[got == HIT] == HIT)
+    assert np.all(cls[got == MISS] == MISS)
+    # every ambiguous pair lands in the band; the pairs are built to sit near
+    # the thresholds, yet thousands are still decided in FP32
+    assert np.all(got[cls == AMB] == BAND)
+    assert (got == HIT).sum() > 1000 and (got == MISS).sum() > 1000
+
+
+def test_hit_or_ambiguous_pairs_meet_the_widened_box(pairs):
+    """Argument 1 in FP64: the extended segment meets the triangle's box
+    widened by tau |d|_1 + 2 tau D per axis."""
+    S, E, A, B, C, cls = pairs
+    keep = cls != MISS
+    s, e = S[keep].astype(F64), E[keep].astype(F64)
+    V = np.stack([A[keep], B[keep], C[keep]], 1).astype(F64)
+    lo, hi = V.min(1), V.max(1)
+    d = e - s
+    pad = TAU * np.abs(d).sum(1, keepdims=True) + 2 * TAU * (hi - lo)
+    lo, hi = lo - pad, hi + pad
+    with np.errstate(all="ignore"):
+        t0 = np.where(d != 0, (lo - s) / d, np.where((s >= lo) & (s <= hi), -np.inf, np.inf))
+        t1 = np.where(d != 0, (hi - s) / d, np.where((s >= lo) & (s <= hi), np.inf, -np.inf))
+    tn = np.maximum(np.minimum(t0, t1).max(1), -TAU)
+    tf = np.minimum(np.maximum(t0, t1).min(1), 1 + TAU)
+    assert np.all(tn <= tf + 1e-12 * (1 + np.abs(tf)))
+    assert keep.sum() > 2000
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_traversal_slab_keeps_every_hit_or_ambiguous_pair(pairs, fused):
+    """Argument 1 as the traversal computes it in FP32, with the box of the
+    triangle alone and its own box sides as D_max (the tightest padding any
+    node of a hierarchy can get)."""
+    S, E, A, B, C, cls = pairs
+    keep = cls != MISS
+    V = np.stack([A[keep], B[keep], C[keep]], 1)
+    lo, hi = V.min(1), V.max(1)
+    with np.errstate(all="ignore"):
+        ok = slab_pass(S[keep], E[keep], lo, hi, hi - lo, fused)
+    assert ok.all(), np.flatnonzero(~ok)[:10]
+    # and the test does prune: most decisive misses' boxes are rejected
+    miss = cls == MISS
+    Vm = np.stack([A[miss], B[miss], C[miss]], 1)
+    with np.errstate(all="ignore"):
+        pruned = ~slab_pass(S[miss], E[miss], Vm.min(1), Vm.max(1), Vm.max(1) - Vm.min(1), fused)
+    assert pruned.sum() > 0
