@@ -12,11 +12,14 @@ against the oracle (no GPU).
    with forward error bounds (16 u times the same expression in magnitudes);
    a pair it calls a certain hit or a certain miss has that class in FP64.
 
-The traversal's FP32 formulas are restated here in numpy float32 -- each dot
-and cross product in two evaluation orders, plain and with fused
-multiply-adds, since the compiler may contract either way -- and run over
-near-boundary, nearly-parallel and near-threshold pairs whose class the
-oracle gives.
+3. The FP64 re-test first tries the same numerator test in double precision
+   (bound 32 u, tau widened by 1e-9 relative); its certain answers must be
+   the class the definition's own FP64 evaluation gives.
+
+The formulas are restated here in numpy float32 / float64 -- each dot and
+cross product in two evaluation orders, plain and with fused multiply-adds,
+since the compiler may contract either way -- and run over near-boundary,
+nearly-parallel and near-threshold pairs whose class the oracle gives.
 """
 import numpy as np
 import pytest
@@ -119,6 +122,72 @@ def slab_pass(s, e, lo, hi, dmax, fused):
     return (tn <= tf) & (tn <= F32(1)) & (tf >= F32(0))
 
 
+# ------------------------------------------------------------ float64 restatement
+def _two_prod(a, b):
+    """a * b = p + e exactly (Dekker's splitting)."""
+    p = a * b
+    sp = 134217729.0                          # 2^27 + 1
+    ah = a * sp - (a * sp - a)
+    al = a - ah
+    bh = b * sp - (b * sp - b)
+    bl = b - bh
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def _fma64(a, b, c):
+    """a * b + c with one final rounding (up to rare double roundings)."""
+    p, pe = _two_prod(a, b)
+    s = p + c
+    bb = s - p
+    se = (p - (s - bb)) + (c - bb)
+    return s + (se + pe)
+
+
+def tri_certain64(s, e, a, b, c, fused):
+    """The FP64 pass's certain test: the FP32 one in double precision with
+    the bound 32 u (u = 2^-53) and tau widened by 1e-9 relative."""
+    u, tau = 2.0 ** -53, TAU * (1 + 1e-9)
+    K = 32 * u
+    s, e, a, b, c = (x.astype(F64) for x in (s, e, a, b, c))
+    d, e1, e2, sv = e - s, b - a, c - a, s - a
+
+    def dot(x, y):
+        if fused:
+            return _fma64(x[:, 2], y[:, 2], _fma64(x[:, 1], y[:, 1], x[:, 0] * y[:, 0]))
+        return x[:, 0] * y[:, 0] + x[:, 1] * y[:, 1] + x[:, 2] * y[:, 2]
+
+    def cross(x, y, sign=-1.0):
+        out = np.empty_like(x)
+        for k, (i, j) in enumerate(((1, 2), (2, 0), (0, 1))):
+            out[:, k] = _fma64(x[:, i], y[:, j], sign * (x[:, j] * y[:, i])) if fused else \
+                x[:, i] * y[:, j] + sign * (x[:, j] * y[:, i])
+        return out
+
+    p, q = cross(d, e2), cross(sv, e1)
+    det, T, U, V = dot(e1, p), dot(e2, q), dot(sv, p), dot(d, q)
+    ad, a1, a2, asv = np.abs(d), np.abs(e1), np.abs(e2), np.abs(sv)
+    pa, qa = cross(ad, a2, 1.0), cross(asv, a1, 1.0)
+    errdet = K * dot(a1, pa) + 1e-300
+    errT = K * dot(a2, qa) + 1e-300
+    thr = tau * (ad.sum(1) * a1.sum(1)) * a2.sum(1)
+    Tm = T - det
+    errTm = errT + errdet + 4 * u * (np.abs(T) + np.abs(det))
+    miss0 = ((T > 0) == (Tm > 0)) & (np.minimum(np.abs(T) - errT, np.abs(Tm) - errTm) > thr)
+    D = np.abs(det)
+    sure = D - errdet > thr
+    sg = np.where(det > 0, 1.0, -1.0)
+    errU, errV = K * dot(asv, pa) + 1e-300, K * dot(ad, qa) + 1e-300
+    Us, Vs, Ts = sg * U, sg * V, sg * T
+    Ws = D - Us - Vs
+    errW = errdet + errU + errV + 4 * u * (D + np.abs(U) + np.abs(V))
+    Tms = D - Ts
+    lim = tau * (D + errdet)
+    hit = sure & (Us - errU > lim) & (Vs - errV > lim) & (Ws - errW > lim) & (Ts - errT > lim) & (Tms - errTm > lim)
+    miss1 = sure & ((Us + errU < -lim) | (Vs + errV < -lim) | (Ws + errW < -lim) | (Ts + errT < -lim)
+                    | (Tms + errTm < -lim))
+    return np.where(miss0, MISS, np.where(hit, HIT, np.where(miss1, MISS, BAND)))
+
+
 # ------------------------------------------------------------ pairs
 def _margin_pairs(rng, n):
     """Segments through a plane point with one barycentric weight, or t, within
@@ -147,14 +216,16 @@ def _margin_pairs(rng, n):
 def pairs():
     rng = np.random.default_rng(31)
     P = _near_boundary_pairs(rng, 8000) + _nearly_parallel_pairs(rng, 6000) + _margin_pairs(rng, 12000)
-    cls = np.array([oracle.classify_pair(*x)[0] for x in P])
+    res = [oracle.classify_pair(*x) for x in P]
+    cls = np.array([r[0] for r in res])
     S, E, A, B, C = (np.stack([x[i] for x in P]) for i in range(5))
-    return S, E, A, B, C, cls
+    det_rel = np.array([abs(r[1]["det_rel"]) for r in res])
+    return S, E, A, B, C, cls, det_rel
 
 
 @pytest.mark.parametrize("fused", [False, True])
 def test_certain_fp32_decisions_are_fp64_decisions(pairs, fused):
-    S, E, A, B, C, cls = pairs
+    S, E, A, B, C, cls, det_rel = pairs
     with np.errstate(all="ignore"):
         got = tri_fp32(S, E, A, B, C, fused)
     assert np.all(cls[got == HIT] == HIT)
@@ -168,7 +239,7 @@ def test_certain_fp32_decisions_are_fp64_decisions(pairs, fused):
 def test_hit_or_ambiguous_pairs_meet_the_widened_box(pairs):
     """Argument 1 in FP64: the extended segment meets the triangle's box
     widened by tau |d|_1 + 2 tau D per axis."""
-    S, E, A, B, C, cls = pairs
+    S, E, A, B, C, cls, det_rel = pairs
     keep = cls != MISS
     s, e = S[keep].astype(F64), E[keep].astype(F64)
     V = np.stack([A[keep], B[keep], C[keep]], 1).astype(F64)
@@ -190,7 +261,7 @@ def test_traversal_slab_keeps_every_hit_or_ambiguous_pair(pairs, fused):
     """Argument 1 as the traversal computes it in FP32, with the box of the
     triangle alone and its own box sides as D_max (the tightest padding any
     node of a hierarchy can get)."""
-    S, E, A, B, C, cls = pairs
+    S, E, A, B, C, cls, det_rel = pairs
     keep = cls != MISS
     V = np.stack([A[keep], B[keep], C[keep]], 1)
     lo, hi = V.min(1), V.max(1)
@@ -203,3 +274,20 @@ def test_traversal_slab_keeps_every_hit_or_ambiguous_pair(pairs, fused):
     with np.errstate(all="ignore"):
         pruned = ~slab_pass(S[miss], E[miss], Vm.min(1), Vm.max(1), Vm.max(1) - Vm.min(1), fused)
     assert pruned.sum() > 0
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_certain_fp64_decisions_are_the_definitions(pairs, fused):
+    """The FP64 pass decides most queued pairs without square roots or
+    divisions; each certain decision must be the class the definition's own
+    FP64 evaluation gives (the oracle's).  Of the decisive pairs clear of
+    the parallel branch (|det_rel| > 2 tau), it leaves almost none to the
+    definition, where the FP32 test leaves half of these adversarial pairs."""
+    S, E, A, B, C, cls, det_rel = pairs
+    with np.errstate(all="ignore"):
+        got = tri_certain64(S, E, A, B, C, fused)
+    assert np.all(cls[got == HIT] == HIT)
+    assert np.all(cls[got == MISS] == MISS)
+    assert np.all(got[cls == AMB] == BAND)
+    clear = (cls != AMB) & (det_rel > 2 * TAU)
+    assert clear.sum() > 10000 and (got[clear] == BAND).sum() < 0.001 * clear.sum()
