@@ -142,3 +142,35 @@ def test_every_entry_point_rejects_missing_arguments(lib):
     # the network's parameter count follows from its shape: 16x128 + 128x128 +
     # 128x256 weights and 128 + 128 + 256 biases
     assert L.rsi_mlp_num_params() == 16 * 128 + 128 * 128 + 128 * 256 + 128 + 128 + 256
+
+
+def test_struct_layouts_match_the_header(lib):
+    """Every structure the binding passes through the ABI has the header's
+    layout: the offset of each field and the size of the whole, as a C
+    compiler lays out include/rsi.h on this host."""
+    import json
+    import subprocess
+    pairs = {"rsi_options": lib.Options, "rsi_stats": lib.Stats, "rsi_bvh_info": lib.Info,
+             "rsi_bvh_host_view": lib.HostView, "rsi_tuning": lib.Tuning, "rsi_ray_batch": lib.RayBatch}
+    lines = ['#include <stdio.h>', '#include "rsi.h"', "int main(void) {", 'printf("{");']
+    for k, (cname, py) in enumerate(pairs.items()):
+        sep = "," if k else ""
+        lines.append(f'printf("{sep}\\"{cname}\\": {{\\"size\\": %zu", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf(", \\"{f}\\": %zu", offsetof({cname}, {f}));')
+        lines.append('printf("}");')
+    lines += ['printf("}\\n");', "return 0; }"]
+    scratch = os.path.join(ROOT, "tests", ".abi_layout")
+    os.makedirs(scratch, exist_ok=True)
+    exe = os.path.join(scratch, f"layout_{os.getpid()}")
+    try:
+        cc = subprocess.run(["gcc", "-std=c11", "-x", "c", "-", "-I", os.path.join(ROOT, "include"), "-o", exe],
+                            input="\n".join(lines), capture_output=True, text=True)
+        assert cc.returncode == 0, cc.stderr
+        got = json.loads(subprocess.run([exe], capture_output=True, text=True, check=True).stdout)
+    finally:
+        shutil.rmtree(scratch, ignore_errors=True)
+    for cname, py in pairs.items():
+        assert got[cname]["size"] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[cname][f] == getattr(py, f).offset, (cname, f)
