@@ -35,7 +35,10 @@
  * example of Sec. 4.1, closed-box parity, exact rational predicates, a
  * second independent tree construction, library sorts).  The de-duplication
  * of crossing points on ambiguous rays (intercept_count, Sec. 1 "unique
- * intersections") has no rule in the paper: parity unpinned.
+ * intersections") is pinned by convexity where several triangles report one
+ * point (a shared vertex or edge of a closed box: one crossing); the merge
+ * distance for distinct but close points (1e-9 in t) has no rule in the
+ * paper: parity unpinned for that distance.
  */
 #include <math.h>
 #include <pthread.h>

@@ -156,6 +156,36 @@ def test_closed_box_crossing_parity():
     assert both_out.sum() > 500 and one_in.sum() > 500
 
 
+def test_crossings_through_shared_edges_and_vertices_count_once():
+    """The reading of "unique intersections" (Sec. 1) pinned by convexity: a
+    segment from inside the closed box to outside crosses its surface at
+    exactly one point, also where that point is a vertex (3 to 6 triangles
+    meet there), an edge, or the diagonal splitting a face, so the distinct
+    crossing points number 1 although several triangles report a hit; a
+    segment along the main diagonal, both ends outside, crosses at 2
+    vertices.  The rays are ambiguous (they meet edges), and the count is the
+    closed-interval one."""
+    V, T = _cube()
+    c = np.full(3, 0.5)
+    corners = [np.array(v, float) for v in V]
+    edges = [(corners[i] + corners[j]) / 2 for i in range(8) for j in range(i + 1, 8)
+             if np.sum(corners[i] != corners[j]) == 1]
+    diag = []
+    for a, b, cc in T.reshape(-1, 2, 3)[:, 0]:      # first triangle of each face: (a, b, c), diagonal a-c
+        diag += [(corners[a] + corners[cc]) / 2, 0.75 * corners[a] + 0.25 * corners[cc]]
+    targets = corners + edges + diag
+    assert len(edges) == 12 and len(diag) == 12
+    F = np.array([c] * len(targets), np.float32)
+    E = np.array([c + 2 * (p - c) for p in targets], np.float32)
+    r = oracle.query(V, T, F, E)
+    assert r["count"].tolist() == [1] * len(targets)
+    assert r["amb_count"].all() and r["hit"].all()
+    incl = [sum(oracle.classify_pair(F[i], E[i], *V[t])[1]["incl"] for t in T) for i in range(len(targets))]
+    assert min(incl) >= 2 and max(incl) >= 3           # several triangles report each point
+    r = oracle.query(V, T, [[-0.5, -0.5, -0.5]], [[1.5, 1.5, 1.5]])
+    assert r["count"][0] == 2 and r["amb_count"][0] == 1
+
+
 # ------------------------------------------------------------ exact predicates
 def _F(x):
     return [Fraction(float(v)) for v in x]
