@@ -468,6 +468,16 @@ uint64_t rsi_kernel_launches(void);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* rsi_last_error(void);
 
+/*
+ * Failure injection for tests of the callers' error paths (no counterpart in
+ * the paper).  With after >= 0, the next `after` device or pinned allocations
+ * the library makes (all threads, all devices) succeed and every later one
+ * fails as if the memory were exhausted: the call that needed it returns
+ * RSI_ERR_OOM, releases what it had taken and leaves its handle usable.
+ * after < 0 switches injection off (the default).  Always returns RSI_OK.
+ */
+int rsi_debug_fail_allocations(int64_t after);
+
 #ifdef __cplusplus
 }
 #endif

@@ -133,6 +133,8 @@ def _load():
                  "rsi_mlp_forward", "rsi_mlp_status"):
         getattr(lib, name).restype = ctypes.c_int
     lib.rsi_last_error.restype = ctypes.c_char_p
+    lib.rsi_debug_fail_allocations.argtypes = [i64]
+    lib.rsi_debug_fail_allocations.restype = i32
     lib.rsi_last_error.argtypes = []
     for name in ("lbvh_build", "lbvh_build_host", "lbvh_free", "lbvh_info", "lbvh_export", "rsi_query",
                  "rsi_query_host"):
@@ -155,6 +157,12 @@ def check(rc: int):
 def kernel_launches() -> int:
     """Kernels the library has launched since it was loaded."""
     return int(lib.rsi_kernel_launches())
+
+
+def fail_allocations(after: int | None):
+    """Test hook: the next `after` allocations of the library succeed, the
+    later ones fail with RSI_ERR_OOM; None switches injection off."""
+    lib.rsi_debug_fail_allocations(-1 if after is None else int(after))
 
 
 def node_bytes() -> int:

@@ -53,8 +53,20 @@ DeviceCtx* device_ctx() {
     return g_ctx[dev];
 }
 
+// Allocations left before injected failures start; -1 = no injection.
+static std::atomic<long long> g_alloc_left{-1};
+
+bool alloc_injected() {
+    long long v = g_alloc_left.load(std::memory_order_relaxed);
+    while (v > 0 && !g_alloc_left.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) {
+    }
+    return v == 0;
+}
+
 int pool_alloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
+    if (alloc_injected())
+        return fail(RSI_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
     DeviceCtx* c = device_ctx();
     if (!c) return fail(RSI_ERR_CUDA, "no CUDA device context");
     if (cudaMallocFromPoolAsync(p, bytes, c->pool, s) != cudaSuccess) {
@@ -81,3 +93,8 @@ int device_sm_count() {
 extern "C" const char* rsi_last_error(void) { return rsi::g_last_error.c_str(); }
 
 extern "C" uint64_t rsi_kernel_launches(void) { return rsi::g_launches.load(); }
+
+extern "C" int rsi_debug_fail_allocations(int64_t after) {
+    rsi::g_alloc_left.store(after < 0 ? -1 : (long long)after);
+    return RSI_OK;
+}

@@ -642,7 +642,7 @@ int train_step(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, co
             m->act = nullptr;
             m->act_cap = 0;
         }
-        if (cudaMalloc(&m->act, sizeof(float) * need) != cudaSuccess) {
+        if (rsi::dev_malloc(&m->act, sizeof(float) * need) != cudaSuccess) {
             cudaGetLastError();
             return fail(RSI_ERR_OOM, "rsi_mlp_train_step: activation buffers");
         }
@@ -728,7 +728,7 @@ extern "C" int rsi_mlp_create(uint64_t seed, rsi_mlp_t* out) {
     auto* m = new rsi_mlp_s();
     const size_t pb = sizeof(float) * kParams;
     char* base = nullptr;
-    if (cudaMalloc(&base, 4 * pb + kImgBytes + 512 * 4 + 256) != cudaSuccess) {
+    if (rsi::dev_malloc(&base, 4 * pb + kImgBytes + 512 * 4 + 256) != cudaSuccess) {
         cudaGetLastError();
         delete m;
         return rsi::fail(RSI_ERR_OOM, "rsi_mlp_create: allocation failed");

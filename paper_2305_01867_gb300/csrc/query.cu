@@ -2246,7 +2246,7 @@ int host_setup(rsi::DeviceCtx* c, int64_t chunk, int64_t n_chunks) {
             c->stage = nullptr;
             c->stage_chunk = 0;
         }
-        if (cudaMalloc(&c->stage, 2 * 32 * (size_t)chunk) != cudaSuccess) {   // 2 slots x (24 + 1 + 4 + 1) B
+        if (rsi::dev_malloc(&c->stage, 2 * 32 * (size_t)chunk) != cudaSuccess) {   // 2 slots x (24 + 1 + 4 + 1) B
             cudaGetLastError();
             return rsi::fail(RSI_ERR_OOM, "rsi_query_host: staging allocation failed");
         }
@@ -2259,7 +2259,7 @@ int host_setup(rsi::DeviceCtx* c, int64_t chunk, int64_t n_chunks) {
             c->h_chunk_ctr = nullptr;
         }
         const int64_t cap = std::max<int64_t>(n_chunks, 64);
-        if (cudaMallocHost(&c->h_chunk_ctr, sizeof(rsi::DevCounters) * (size_t)cap) != cudaSuccess) {
+        if (rsi::host_malloc_pinned(&c->h_chunk_ctr, sizeof(rsi::DevCounters) * (size_t)cap) != cudaSuccess) {
             cudaGetLastError();
             c->h_chunk_cap = 0;
             return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
@@ -2300,7 +2300,7 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
             c->whole = nullptr;
             c->whole_cap = 0;
         }
-        if (cudaMalloc(&c->whole, 30 * (size_t)n + 1024) != cudaSuccess) {
+        if (rsi::dev_malloc(&c->whole, 30 * (size_t)n + 1024) != cudaSuccess) {
             cudaGetLastError();
             return rsi::fail(RSI_ERR_OOM, "rsi_query_host: staging allocation failed");
         }
@@ -2309,13 +2309,13 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     rc = host_streams(c);
     if (rc) return rc;
     if (!c->h_chunk_ctr) {
-        if (cudaMallocHost(&c->h_chunk_ctr, sizeof(rsi::DevCounters) * 64) != cudaSuccess) {
+        if (rsi::host_malloc_pinned(&c->h_chunk_ctr, sizeof(rsi::DevCounters) * 64) != cudaSuccess) {
             cudaGetLastError();
             return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
         }
         c->h_chunk_cap = 64;
     }
-    if (!c->h_ready && cudaMallocHost(&c->h_ready, 64 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (!c->h_ready && rsi::host_malloc_pinned(&c->h_ready, 64 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         c->h_ready = nullptr;
         return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
@@ -2690,8 +2690,8 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     size_t pair_bytes;
     rsi::pair_sizes(std::max<int64_t>(total, 1), b_seg_cap, b_pair_cap, pair_bytes);
     const size_t bytes = off_pairs + pair_bytes;
-    if (cudaMalloc(&b->dev, bytes) != cudaSuccess || cudaMallocHost(&b->h_ctr, sizeof(rsi::DevCounters)) != cudaSuccess ||
-        cudaMallocHost(&b->h_post, 256 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (rsi::dev_malloc(&b->dev, bytes) != cudaSuccess || rsi::host_malloc_pinned(&b->h_ctr, sizeof(rsi::DevCounters)) != cudaSuccess ||
+        rsi::host_malloc_pinned(&b->h_post, 256 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         batch_destroy(b);
         return rsi::fail(RSI_ERR_OOM, "rsi_batch_create: allocation failed");

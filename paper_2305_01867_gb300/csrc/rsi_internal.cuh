@@ -148,6 +148,26 @@ DeviceCtx* device_ctx();   // the current device's context (NULL without a devic
 int pool_alloc(void** p, size_t bytes, cudaStream_t s);
 void pool_free(void* p, cudaStream_t s);
 
+// Allocation-failure injection (rsi_debug_fail_allocations): true when the
+// current allocation is to fail.  Every device and pinned allocation of the
+// library asks it first.
+bool alloc_injected();
+// cudaMalloc / cudaMallocHost that honour the injection and leave *p NULL
+// after any failure, so a later release never sees a stale pointer.
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+    cudaError_t e = alloc_injected() ? cudaErrorMemoryAllocation : cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) *p = nullptr;
+    return e;
+}
+template <class T>
+cudaError_t host_malloc_pinned(T** p, size_t bytes) {
+    cudaError_t e =
+        alloc_injected() ? cudaErrorMemoryAllocation : cudaMallocHost(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) *p = nullptr;
+    return e;
+}
+
 // Count of kernel launches made by the library (rsi_kernel_launches).
 void note_launches(int n);
 

@@ -174,3 +174,24 @@ def test_struct_layouts_match_the_header(lib):
         assert got[cname]["size"] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[cname][f] == getattr(py, f).offset, (cname, f)
+
+
+def test_allocation_failure_injection_on_the_host(lib):
+    """With injection at 0, the first allocation of a build from host memory
+    fails with RSI_ERR_OOM (-3) before any device work and no handle is
+    returned; switched off, the same call goes on to the device."""
+    import numpy as np
+    L = lib.lib
+    V = np.zeros((3, 3), np.float32)
+    T = np.array([[0, 1, 2]], np.int32)
+    h = ctypes.c_void_p()
+    lib.fail_allocations(0)
+    try:
+        rc = L.lbvh_build_host(V.ctypes.data, 3, T.ctypes.data, 1, 4, 30, None, ctypes.byref(h))
+        assert rc == -3 and "injected" in lib.last_error() and not h.value
+    finally:
+        lib.fail_allocations(None)
+    rc = L.lbvh_build_host(V.ctypes.data, 3, T.ctypes.data, 1, 4, 30, None, ctypes.byref(h))
+    assert rc == 0 or "injected" not in lib.last_error()
+    if rc == 0:
+        L.lbvh_free(h)
