@@ -9,7 +9,8 @@ pass.  The oracle in the repository is never modified.
 
 Left out on purpose: the merge distance of crossing points on ambiguous
 rays (no rule in the paper; parity unpinned) and rewrites that cannot change
-a result (e.g. a loop bound the loop never reaches).
+a result (a loop bound the loop never reaches; the network's padding rows,
+which only ever multiply zero inputs).
 """
 import os
 import shutil
@@ -95,6 +96,32 @@ MUTANTS = [
     ("Adam bias correction frozen", M, "mh = m / (1 - b1 ** t)", "mh = m / (1 - b1)"),
     ("top-4 ties to the higher index", M, 'np.argsort(-logits, axis=1, kind="stable")',
      'np.argsort(logits, axis=1, kind="stable")[:, ::-1]'),
+    # more bounds, distance helpers, tree indices, network backward and optimiser
+    ("inclusive drops w", C, "incl = (u >= 0.0 && v >= 0.0 && w >= 0.0 &&", "incl = (u >= 0.0 && v >= 0.0 &&"),
+    ("inclusive drops t >= 0", C, "&& t >= 0.0 && t <= 1.0);", "&& t <= 1.0);"),
+    ("decisive miss ignores t < -tau", C, "w < -tau || t < -tau ||", "w < -tau ||"),
+    ("decisive hit ignores t > tau", C, "w > tau && t > tau && t < 1.0 - tau)", "w > tau && t < 1.0 - tau)"),
+    ("parallel skips edge a-b", C, "dd = segment_segment_distance(s, e, a, b); if (dd < dist) dist = dd;", ""),
+    ("point-triangle inside test drops a side", C, "if (s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0) return",
+     "if (s0 >= 0.0 && s1 >= 0.0) return"),
+    ("point-segment unclamped", C, "clamp01(v_dot(v_sub(p, a), ab) / len2)", "(v_dot(v_sub(p, a), ab) / len2)"),
+    ("segment-segment interior ignores s", C, "if (s >= 0.0 && s <= 1.0 && t >= 0.0 && t <= 1.0) {",
+     "if (t >= 0.0 && t <= 1.0) {"),
+    ("Morton drops the top bit", C, "for (int i = 0; i < b; ++i)", "for (int i = 0; i < b - 1; ++i)"),
+    ("left child's parent slot", C, "left[node] = (int32_t)g;\n        parent[g] = (int32_t)node;",
+     "left[node] = (int32_t)g;\n        parent[g + 1] = (int32_t)node;"),
+    ("node range one short", C, "range_hi[node] = (int32_t)b;", "range_hi[node] = (int32_t)(b - 1);"),
+    ("W1 gradient scaled", M, 'g["W1"] = cache["a0"].T @ dz1', 'g["W1"] = cache["a0"].T @ dz1 * 0.5'),
+    ("backward GELU slope of the wrong layer", M, 'dz2 = da2 * gelu_grad(cache["z2"])',
+     'dz2 = da2 * gelu_grad(cache["z1"])'),
+    ("loss sign", M, "np.maximum(z, 0) - z * y", "np.maximum(z, 0) + z * y"),
+    ("loss mean over the batch only", M, "/ (n * D_OUT)", "/ n"),
+    ("Adam second moment of |g|", M, "v[...] = b2 * v + (1 - b2) * g[k] ** 2",
+     "v[...] = b2 * v + (1 - b2) * np.abs(g[k])"),
+    ("Adam eps inside the root", M, "np.sqrt(vh) + eps", "np.sqrt(vh + eps)"),
+    ("features clamped at 3", M, "np.clip(2.0 * f - 1.0, -4.0, 4.0)", "np.clip(2.0 * f - 1.0, -3.0, 3.0)"),
+    ("feature padding not zero", M, "x = np.zeros((len(f), D_PAD))", "x = np.ones((len(f), D_PAD))"),
+    ("forward drops the output bias", M, 'z3 = a2 @ W3 + p["b3"]', "z3 = a2 @ W3"),
 ]
 
 
