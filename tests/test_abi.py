@@ -195,3 +195,31 @@ def test_allocation_failure_injection_on_the_host(lib):
     assert rc == 0 or "injected" not in lib.last_error()
     if rc == 0:
         L.lbvh_free(h)
+
+
+def test_size_limits_at_the_boundary(lib):
+    """The largest sizes the header allows pass the argument checks and the
+    next ones are refused, before any device work: n_triangles < 2^30,
+    n_vertices <= 2^31, n_rays < 2^31, and RSI_NOALLOC_MAX_RAYS for the
+    no-allocation query.  (The accepted build stops at its first allocation,
+    refused by the failure-injection hook.)"""
+    L, P = lib.lib, ctypes.c_void_p
+    h = ctypes.c_void_p()
+    fake = P(256)                       # never dereferenced on these paths
+    assert L.lbvh_build(fake, 3, fake, 1 << 30, 4, 30, None, ctypes.byref(h)) == -1
+    assert "n_triangles" in lib.last_error()
+    assert L.lbvh_build(fake, (1 << 31) + 1, fake, 1, 4, 30, None, ctypes.byref(h)) == -1
+    lib.fail_allocations(0)
+    try:
+        assert L.lbvh_build(fake, 1 << 31, fake, (1 << 30) - 1, 4, 30, None, ctypes.byref(h)) == -3
+        assert "injected" in lib.last_error() and not h.value
+    finally:
+        lib.fail_allocations(None)
+    big = 1 << 31
+    assert L.rsi_query(fake, fake, fake, big, 0, None, fake, None, None, None, None) == -1
+    assert "2^31" in lib.last_error()
+    assert L.rsi_query_host(fake, fake, fake, big, 1, None, None, fake, None, None, None) == -1
+    assert L.rsi_query_nearest(fake, fake, fake, big, None, fake, None, None, None, None, None, None) == -1
+    assert L.rsi_query_noalloc(fake, fake, fake, big, 0, None, fake, None, None, None) == -1
+    assert L.rsi_query_noalloc(fake, fake, fake, 2_097_152 + 1, 0, None, fake, None, None, None) == -1
+    assert "RSI_NOALLOC_MAX_RAYS" in lib.last_error()
