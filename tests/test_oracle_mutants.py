@@ -122,6 +122,8 @@ MUTANTS = [
     ("features clamped at 3", M, "np.clip(2.0 * f - 1.0, -4.0, 4.0)", "np.clip(2.0 * f - 1.0, -3.0, 3.0)"),
     ("feature padding not zero", M, "x = np.zeros((len(f), D_PAD))", "x = np.ones((len(f), D_PAD))"),
     ("forward drops the output bias", M, 'z3 = a2 @ W3 + p["b3"]', "z3 = a2 @ W3"),
+    ("thread ranges skip a row", C, "nR * k / nthreads, nR * (k + 1) / nthreads,",
+     "nR * k / nthreads + (k > 0), nR * (k + 1) / nthreads,"),
 ]
 
 

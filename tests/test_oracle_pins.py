@@ -308,6 +308,20 @@ def test_shared_edge_counted_once_on_ambiguous_ray():
     assert r["amb_count"][0] == 1 and r["count"][0] == 1 and r["hit"][0] == 1
 
 
+def test_answers_do_not_depend_on_the_thread_count():
+    """The brute force splits the segments into contiguous ranges, one per
+    thread: every split gives the same arrays as one thread."""
+    g = load("canopy_sec4_1_5.txt")
+    rng = np.random.default_rng(4)
+    F = rng.uniform([11.8, 1.8, 0.5], [13.2, 3.2, 2.0], (257, 3)).astype(np.float32)
+    E = rng.uniform([11.8, 1.8, 0.5], [13.2, 3.2, 2.0], (257, 3)).astype(np.float32)
+    one = oracle.query(g["vertices"], g["triangles"], F, E, nthreads=1)
+    for k in (2, 3, 7, 300):
+        many = oracle.query(g["vertices"], g["triangles"], F, E, nthreads=k)
+        for key in one:
+            assert np.array_equal(one[key], many[key], equal_nan=True), (k, key)
+
+
 def test_bad_index_rejected():
     V = np.zeros((3, 3), np.float32)
     with pytest.raises(ValueError):
