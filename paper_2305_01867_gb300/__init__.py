@@ -179,6 +179,26 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _check_out(t, name, dtype, n, device):
+    """A caller-supplied output buffer: `dtype`, contiguous, at least n
+    elements, on `device` (a torch.device, or "host" for host memory).  The
+    kernels write through its pointer, so a wrong buffer is refused here."""
+    import torch
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype:
+        raise TypeError(f"{name} must be a {dtype} tensor")
+    if not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous")
+    if device == "host":
+        if t.is_cuda:
+            raise TypeError(f"{name} must be in host memory")
+    elif t.device != device:
+        raise TypeError(f"{name} must be on {device}")
+    if t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, {n} are written")
+
+
 def _check_f32x3(t, name):
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 3:
@@ -320,6 +340,11 @@ class LBVH:
             count = torch.empty(n, dtype=torch.int32, device=dev)
         if ambiguous is None and want_ambiguous:
             ambiguous = torch.empty(n, dtype=torch.uint8, device=dev)
+        if ray_to.device != dev:
+            raise TypeError("ray_from and ray_to must be on the same device")
+        _check_out(hit, "hit", torch.uint8, n, dev)
+        _check_out(count, "count", torch.int32, n, dev)
+        _check_out(ambiguous, "ambiguous", torch.uint8, n, dev)
         opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels),
                       int(ray_sort_tile), int(node_width), int(fp64_all))
         st = Stats()
@@ -337,6 +362,10 @@ class LBVH:
         import torch
         _check_f32x3(ray_from, "ray_from")
         _check_f32x3(ray_to, "ray_to")
+        if ray_from.shape != ray_to.shape:
+            raise ValueError("ray_from and ray_to differ in shape")
+        if ray_from.is_cuda or ray_to.is_cuda:
+            raise TypeError("query_host() takes host tensors; use query() for device tensors")
         m = _mode(mode)
         n = ray_from.shape[0]
         if hit is None and m == RSI_ANY_HIT:
@@ -345,6 +374,9 @@ class LBVH:
             count = torch.empty(n, dtype=torch.int32)
         if ambiguous is None and want_ambiguous:
             ambiguous = torch.empty(n, dtype=torch.uint8)
+        _check_out(hit, "hit", torch.uint8, n, "host")
+        _check_out(count, "count", torch.int32, n, "host")
+        _check_out(ambiguous, "ambiguous", torch.uint8, n, "host")
         opt = Options(int(fp32_only), 0, 0, int(stats), 0, 0, int(ray_sort_tile))
         st = Stats()
         check(lib.rsi_query_host(self._h, _ptr(ray_from), _ptr(ray_to), n, m, ctypes.byref(opt), _ptr(hit),
@@ -367,6 +399,8 @@ class LBVH:
             raise ValueError("ray_from and ray_to differ in shape")
         if not (ray_from.is_cuda and ray_to.is_cuda):
             raise TypeError("nearest() takes device tensors")
+        if ray_to.device != ray_from.device:
+            raise TypeError("ray_from and ray_to must be on the same device")
         n = ray_from.shape[0]
         dev = ray_from.device
         tri = torch.empty(n, dtype=torch.int32, device=dev)
@@ -615,11 +649,17 @@ def query_learned(bvh, net, ray_from, ray_to, stats=False, hit=None, ambiguous=N
     import torch
     _check_f32x3(ray_from, "ray_from")
     _check_f32x3(ray_to, "ray_to")
+    if ray_from.shape != ray_to.shape:
+        raise ValueError("ray_from and ray_to differ in shape")
+    if not (ray_from.is_cuda and ray_to.is_cuda) or ray_to.device != ray_from.device:
+        raise TypeError("query_learned() takes device tensors on one device")
     n = ray_from.shape[0]
     if hit is None:
         hit = torch.empty(n, dtype=torch.uint8, device=ray_from.device)
     if ambiguous is None:
         ambiguous = torch.empty(n, dtype=torch.uint8, device=ray_from.device)
+    _check_out(hit, "hit", torch.uint8, n, ray_from.device)
+    _check_out(ambiguous, "ambiguous", torch.uint8, n, ray_from.device)
     opt = Options(int(opts.get("fp32_only", 0)), int(opts.get("block", 0)), int(opts.get("blocks_per_sm", 0)),
                   int(stats), 0, 0, 0, int(opts.get("node_width", 0)))
     st = Stats()
@@ -635,6 +675,8 @@ def activation(z, stream=None):
     """(erf by the network's approximation, CUDA erff, GELU) of a device
     float32 vector (rsi_mlp_activation)."""
     import torch
+    if not isinstance(z, torch.Tensor) or not z.is_cuda or z.dtype != torch.float32 or not z.is_contiguous():
+        raise TypeError("z must be a contiguous float32 device tensor")
     a, b, g = torch.empty_like(z), torch.empty_like(z), torch.empty_like(z)
     check(lib.rsi_mlp_activation(_ptr(z), z.numel(), _ptr(a), _ptr(b), _ptr(g), _stream(stream)))
     return a, b, g

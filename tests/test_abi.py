@@ -223,3 +223,32 @@ def test_size_limits_at_the_boundary(lib):
     assert L.rsi_query_noalloc(fake, fake, fake, big, 0, None, fake, None, None, None) == -1
     assert L.rsi_query_noalloc(fake, fake, fake, 2_097_152 + 1, 0, None, fake, None, None, None) == -1
     assert "RSI_NOALLOC_MAX_RAYS" in lib.last_error()
+
+
+def test_binding_refuses_bad_buffers_before_any_call(lib):
+    """Buffers the library would read or write through are checked first:
+    segments of different shapes or in the wrong memory, outputs of the wrong
+    type, too small or not contiguous.  (A handle is never reached: the
+    object below has none.)"""
+    import torch
+    b = lib.LBVH.__new__(lib.LBVH)
+    b._h = None
+    F = torch.zeros(10, 3, dtype=torch.float32)
+    with pytest.raises(TypeError):
+        b.query(F, F, "any_hit")                                   # host segments to the device query
+    with pytest.raises(TypeError):
+        b.nearest(F, F)
+    with pytest.raises(ValueError):
+        b.query_host(F, F[:5], "any_hit")                           # lengths differ
+    with pytest.raises(TypeError):
+        b.query_host(F, F, "any_hit", hit=torch.zeros(10, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        b.query_host(F, F, "count", count=torch.zeros(9, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        b.query_host(F, F, "any_hit", ambiguous=torch.zeros(20, dtype=torch.uint8)[::2])
+    with pytest.raises(TypeError):
+        b.query_host(F[:, [0, 2, 1]].t().contiguous().t(), F, "any_hit")   # not contiguous
+    with pytest.raises(TypeError):
+        lib.query_learned(None, None, F, F)
+    with pytest.raises(TypeError):
+        lib.activation(torch.zeros(4))
