@@ -180,9 +180,10 @@ def _stream(stream):
 
 
 def _check_out(t, name, dtype, n, device):
-    """A caller-supplied output buffer: `dtype`, contiguous, at least n
-    elements, on `device` (a torch.device, or "host" for host memory).  The
-    kernels write through its pointer, so a wrong buffer is refused here."""
+    """A caller-supplied buffer the library reads or writes: `dtype`,
+    contiguous, at least n elements, on `device` (a torch.device, or "host"
+    for host memory).  Only its pointer crosses the ABI, so a wrong buffer is
+    refused here.  None passes (an optional buffer left out)."""
     import torch
     if t is None:
         return
@@ -197,6 +198,17 @@ def _check_out(t, name, dtype, n, device):
         raise TypeError(f"{name} must be on {device}")
     if t.numel() < n:
         raise ValueError(f"{name} holds {t.numel()} elements, {n} are written")
+
+
+def _check_segments(ray_from, ray_to):
+    """Segment end points for a device call: [n, 3] float32, contiguous,
+    equal shapes, both on one GPU."""
+    _check_f32x3(ray_from, "ray_from")
+    _check_f32x3(ray_to, "ray_to")
+    if ray_from.shape != ray_to.shape:
+        raise ValueError("ray_from and ray_to differ in shape")
+    if not (ray_from.is_cuda and ray_to.is_cuda) or ray_to.device != ray_from.device:
+        raise TypeError("segments must be device tensors on one GPU")
 
 
 def _check_f32x3(t, name):
@@ -459,8 +471,13 @@ def compact_hits(tri, dist, point, stream=None):
     """rsi_nearest_compact: (segment indices, distances, triangles, points)
     of the entries with tri >= 0, in index order."""
     import torch
+    if not isinstance(tri, torch.Tensor) or tri.dim() != 1 or not tri.is_cuda:
+        raise TypeError("tri must be a 1-D device tensor")
     n = tri.shape[0]
     dev = tri.device
+    _check_out(tri, "tri", torch.int32, n, dev)
+    _check_out(dist, "dist", torch.float32, n, dev)
+    _check_out(point, "point", torch.float32, 3 * n, dev)
     rays = torch.empty(n, dtype=torch.int32, device=dev)
     tri_o = torch.empty(n, dtype=torch.int32, device=dev)
     dist_o = torch.empty(n, dtype=torch.float32, device=dev) if dist is not None else None
@@ -490,8 +507,7 @@ class BatchPlan:
         self.hit, self.count, self.ambiguous = [], [], []
         arr = (RayBatch * len(items))()
         for i, (bvh, f, t) in enumerate(items):
-            _check_f32x3(f, "ray_from")
-            _check_f32x3(t, "ray_to")
+            _check_segments(f, t)
             n = f.shape[0]
             h = torch.empty(n, dtype=torch.uint8, device=f.device) if m == RSI_ANY_HIT else None
             c = torch.empty(n, dtype=torch.int32, device=f.device) if m == RSI_COUNT else None
@@ -578,7 +594,8 @@ class MLP:
     def set_params(self, params, stream=None):
         import numpy as np
         flat = self.flatten(params) if isinstance(params, dict) else np.ascontiguousarray(params, np.float32)
-        assert flat.size == self.n_params
+        if flat.size != self.n_params:
+            raise ValueError(f"{flat.size} parameters given, the network has {self.n_params}")
         check(lib.rsi_mlp_set_params(self._m, flat.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
 
     def get_params(self, grads=False, stream=None):
@@ -592,8 +609,7 @@ class MLP:
     def forward(self, bvh, ray_from, ray_to, logits=True, top4=True, stream=None):
         """Tensor-core inference: dict(logits=[n,256] float32, top4=[n,4] uint8)."""
         import torch
-        _check_f32x3(ray_from, "ray_from")
-        _check_f32x3(ray_to, "ray_to")
+        _check_segments(ray_from, ray_to)
         n = ray_from.shape[0]
         lg = torch.empty(n, 256, dtype=torch.float32, device=ray_from.device) if logits else None
         t4 = torch.empty(n, 4, dtype=torch.uint8, device=ray_from.device) if top4 else None
@@ -607,6 +623,12 @@ class MLP:
     def train_step(self, bvh, ray_from, ray_to, labels, lr=1e-3, apply=True, want_loss=False, stream=None):
         """One GPU training step on a batch (labels: [n, 8] int32 bit masks).
         Returns the batch loss when want_loss (synchronizes)."""
+        import torch
+        _check_segments(ray_from, ray_to)
+        n = ray_from.shape[0]
+        if not isinstance(labels, torch.Tensor) or labels.dim() != 2 or labels.shape != (n, 8):
+            raise TypeError("labels must be an [n, 8] tensor")
+        _check_out(labels, "labels", torch.int32, 8 * n, ray_from.device)
         loss = ctypes.c_float()
         check(lib.rsi_mlp_train_step(self._m, bvh.handle, _ptr(ray_from), _ptr(ray_to), _ptr(labels),
                                      ray_from.shape[0], float(lr), int(apply),
@@ -637,6 +659,7 @@ class MLP:
 def cluster_labels(bvh, ray_from, ray_to, stream=None):
     """[n, 8] int32 bit masks of the clusters each segment meets (rsi_cluster_labels)."""
     import torch
+    _check_segments(ray_from, ray_to)
     n = ray_from.shape[0]
     out = torch.empty(n, 8, dtype=torch.int32, device=ray_from.device)
     check(lib.rsi_cluster_labels(bvh.handle, _ptr(ray_from), _ptr(ray_to), n, _ptr(out), _stream(stream)))

@@ -252,3 +252,26 @@ def test_binding_refuses_bad_buffers_before_any_call(lib):
         lib.query_learned(None, None, F, F)
     with pytest.raises(TypeError):
         lib.activation(torch.zeros(4))
+
+
+def test_binding_refuses_bad_buffers_of_the_other_calls(lib):
+    """As above for the compaction, the batched plans, the network and the
+    labels: host tensors, mismatched shapes, wrong element types and sizes are
+    refused before the library is called."""
+    import numpy as np
+    import torch
+    F = torch.zeros(6, 3, dtype=torch.float32)
+    with pytest.raises(TypeError):
+        lib.compact_hits(torch.zeros(6, dtype=torch.int32), None, None)        # host memory
+    with pytest.raises(TypeError):
+        lib.BatchPlan([(None, F, F)], "any_hit")
+    with pytest.raises(TypeError):
+        lib.cluster_labels(None, F, F)
+    net = lib.MLP.__new__(lib.MLP)
+    net._m, net.n_params = None, 16 * 128 + 128 * 128 + 128 * 256 + 128 + 128 + 256
+    with pytest.raises(TypeError):
+        net.forward(None, F, F)
+    with pytest.raises(TypeError):
+        net.train_step(None, F, F, torch.zeros(6, 8, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        net.set_params(np.zeros(10, np.float32))
