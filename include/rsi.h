@@ -186,7 +186,10 @@ int lbvh_build_batched(int n_meshes, const float* const* d_vertices, const int64
                        const int32_t* const* d_triangles, const int64_t* n_triangles, int index_bytes,
                        int morton_bits, void* stream, rsi_bvh_t* out);
 
-/* As lbvh_build, with the mesh in host memory (copied in on `stream`). */
+/* As lbvh_build, with the mesh in host memory: h_vertices and h_triangles
+ * are copied in on `stream` (page-locked arrays copy asynchronously) and may
+ * be freed when the call returns; the call synchronizes `stream` as
+ * lbvh_build does.  Errors as lbvh_build, plus RSI_ERR_OOM for the copies. */
 int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
                     int64_t n_triangles, int index_bytes, int morton_bits, void* stream,
                     rsi_bvh_t* out);
@@ -194,9 +197,16 @@ int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* 
 /* Release a handle (synchronizes the device first).  NULL is a no-op. */
 int lbvh_free(rsi_bvh_t h);
 
+/* Describe a built hierarchy (host read of values kept in the handle; no
+ * device work).  device_bytes counts the hierarchy plus the query scratch
+ * the handle holds now.  RSI_ERR_INVALID_ARG for a NULL argument. */
 int lbvh_info(rsi_bvh_t h, rsi_bvh_info* out);
 
-/* Copy the hierarchy to host arrays (synchronizes `stream`). */
+/* Copy the hierarchy to the caller's host arrays (layout and sizes in
+ * rsi_bvh_host_view; 30-bit codes are widened to uint64).  Synchronizes
+ * `stream` first, so every build and query enqueued there is complete, and
+ * returns after the copies.  RSI_ERR_INVALID_ARG for a NULL argument,
+ * RSI_ERR_CUDA if a copy fails. */
 int lbvh_export(rsi_bvh_t h, void* stream, rsi_bvh_host_view* out);
 
 /* sizeof of one packed hierarchy node on the device (the paper's
@@ -218,6 +228,14 @@ size_t lbvh_node_bytes(void);
  * scratch (the FP64 re-test's queue and pair lists, about 22 B per segment
  * of the largest batch queried so far) on demand; lbvh_free releases it.
  */
+/* Errors: RSI_ERR_INVALID_ARG for a NULL handle or segment pointer, n_rays
+ * outside [0, 2^31), a mode other than the two above, the output the mode
+ * writes missing, or option values out of range; RSI_ERR_OOM when the
+ * scratch cannot grow; RSI_ERR_STACK for a tree of height 127 or more
+ * (a Karras tree over n < 2^30 leaves is at most 63 + 30 high); RSI_ERR_CUDA
+ * for a failed launch.  A kernel's own error (RSI_ERR_OVERFLOW: a segment
+ * with more than 64 inclusive crossings to de-duplicate in the FP64 pass) is
+ * returned in stats->device_error. */
 int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
               const rsi_options* opt, uint8_t* d_hit, int32_t* d_count, uint8_t* d_ambiguous,
               rsi_stats* stats, void* stream);
@@ -396,7 +414,10 @@ int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_
  *   W1 [16][128] (rows 6..15 unused), b1 [128], W2 [128][128], b2 [128],
  *   W3 [128][256], b3 [256]   (row-major, y = x W + b).
  */
-/* New network with seeded He-normal weights and zero biases. */
+/* New network with seeded He-normal weights and zero biases (one device
+ * allocation: weights, gradients, Adam moments, BF16 images).  RSI_ERR_OOM
+ * if it fails.  rsi_mlp_free releases it (NULL is a no-op);
+ * rsi_mlp_num_params is the parameter count (51,712). */
 int rsi_mlp_create(uint64_t seed, rsi_mlp_t* out);
 int rsi_mlp_free(rsi_mlp_t m);
 int rsi_mlp_num_params(void);
@@ -412,6 +433,9 @@ int rsi_mlp_get_params(rsi_mlp_t m, float* h_params, float* h_grads, void* strea
  * that ran out (RSI_ERR_TIMEOUT). */
 int rsi_mlp_forward(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
                     float* d_logits, uint8_t* d_top4, void* stream);
+/* Synchronizes `stream` and returns RSI_ERR_TIMEOUT if a tensor-core wait of
+ * an earlier forward on the network ran out (its outputs are then not
+ * valid), else RSI_OK. */
 int rsi_mlp_status(rsi_mlp_t m, void* stream);
 
 /* The network's activation on n device floats z (for tests): d_erf gets the
@@ -430,6 +454,7 @@ int rsi_mlp_activation(const float* d_z, int64_t n, float* d_erf, float* d_erf_c
  * batch loss before the step (the call then synchronizes `stream`). */
 int rsi_mlp_train_step(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* d_to,
                        const uint32_t* d_labels, int64_t n, float lr, int apply, float* h_loss, void* stream);
+/* Zero the Adam moments and step count (the weights are kept). */
 int rsi_mlp_reset_optimizer(rsi_mlp_t m, void* stream);
 
 /*
