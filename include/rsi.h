@@ -29,6 +29,10 @@
  *   - Device memory of handles and their scratch comes from a private
  *     stream-ordered pool per device: up to 4 GiB of freed blocks stay cached
  *     for later handles, and frees do not synchronize the device.
+ *   - A handle, plan or network belongs to the device that was current when
+ *     it was created; the library never switches devices, so that device
+ *     must be current (and the buffers and stream must be on it) for every
+ *     later call on it.
  *   - Every function returns RSI_OK (0) or a negative RSI_ERR_* code and
  *     never throws; rsi_last_error() then describes the failure.
  */
