@@ -741,9 +741,10 @@ def main():
     job_counts = sum_over_ranks(pg, [st_c["band_rays"], st_c["ambiguous"], st_a["band_rays"], st_a["ambiguous"]],
                                 dev)
     height = bvh.info()["height"]
-    # traversal kernel time by node width (child-pair vs four-wide), same answers
+    # traversal kernel time by node width (child-pair, compressed child-pair,
+    # four-wide), same answers
     widths = {}
-    for w in (2, 4):
+    for w in (2, 3, 4):
         st_w = bvh.query(dF, dE, "count", stats=True, node_width=w)["stats"]
         per = {}
         for mode in ("any_hit", "count"):

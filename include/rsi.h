@@ -86,8 +86,11 @@ typedef struct rsi_options {
     int node_width;     /* nodes the FP32 traversal fetches: 2 (or 0, the
                            default) = child-pair nodes; 4 = four-wide nodes
                            (up to four child boxes per 128-byte fetch; trees
-                           of height > 82 fall back to 2).  Results are the
-                           same either way.                                 */
+                           of height > 82 fall back to 2); 3 = compressed
+                           child-pair nodes (32 bytes: child boxes on an
+                           8-bit grid, rebuilt rounded outward; single
+                           queries of single builds, else 2).  Results are
+                           the same in every case.                          */
     int fp64_all;       /* 1: skip the FP32 traversal and settle every
                            segment with the FP64 re-test (a validation mode:
                            its answers must equal the default path's; slow).

@@ -1,6 +1,6 @@
 // autotune.cu -- picks the launch shape of the traversal (threads per block,
-// resident blocks per SM), the node width it fetches (child-pair or
-// four-wide) and the in-tile segment reordering of a query by
+// resident blocks per SM), the node width it fetches (child-pair,
+// compressed child-pair or four-wide) and the in-tile segment reordering of a query by
 // timing candidates on a sample of its own segments with CUDA events, and
 // reports the traversal stack the tree needs (the smallest of 32 / 64 / 128
 // entries that holds the chosen walk's worst case).  Choices are cached in a JSON file keyed
@@ -146,11 +146,11 @@ extern "C" int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to,
         cudaEventCreate(&e1);
         const int shapes[][2] = {{256, 4}, {256, 3}, {256, 2}, {128, 8}, {128, 6}, {64, 16}};
         const int tiles[] = {0, 2048, 8192};
-        const int widths[] = {2, 4};
+        const int widths[] = {2, 3, 4};
         float best_ms = INFINITY;
         int rc = RSI_OK;
         for (const auto& sh : shapes) {
-            for (int c = 0; c < 6; ++c) {
+            for (int c = 0; c < 9; ++c) {
                 const int tile = tiles[c % 3], width = widths[c / 3];
                 if (width == 4 && !wide_ok) continue;
                 rsi_options o = *inout;

@@ -462,6 +462,86 @@ __global__ void k_collapse4(const Node* __restrict__ nodes, const int32_t* __res
     if (i < n - 1) collapse_node(nodes, parent, i, out);
 }
 
+// ---------------------------------------------------------------- compressed nodes
+// Smallest power of two 2^k (k >= -126, a normal float) whose 255 multiples
+// reach `ext` with a little to spare.
+__device__ __forceinline__ int grid_exponent(double ext) {
+    int k = -126;
+    if (ext > 0.0) {
+        const double need = ext * (1.0 + 0x1p-40);
+        k = ilogb(need / 255.0);
+        while (ldexp(255.0, k) < need) ++k;
+        while (k > -126 && ldexp(255.0, k - 1) >= need) --k;
+        if (k < -126) k = -126;
+    }
+    return k;
+}
+
+// Grid coordinate of a lower plane: the largest q whose rebuilt value
+// fma_rd(q, step, o) does not exceed x (q = 0 gives o <= x).
+__device__ __forceinline__ unsigned quant_lo(float x, float o, float step) {
+    double q = floor(((double)x - (double)o) / (double)step);
+    unsigned u = q < 0.0 ? 0u : (q > 255.0 ? 255u : (unsigned)q);
+    while (u > 0 && __fmaf_rd((float)u, step, o) > x) --u;
+    while (u < 255 && __fmaf_rd((float)(u + 1), step, o) <= x) ++u;
+    return u;
+}
+
+// Grid coordinate of an upper plane: the smallest q whose rebuilt value
+// fma_ru(q, step, o) is at least x (255 always is, by the choice of step).
+__device__ __forceinline__ unsigned quant_hi(float x, float o, float step) {
+    double q = ceil(((double)x - (double)o) / (double)step);
+    unsigned u = q < 0.0 ? 0u : (q > 255.0 ? 255u : (unsigned)q);
+    while (u < 255 && __fmaf_ru((float)u, step, o) < x) ++u;
+    while (u > 0 && __fmaf_ru((float)(u - 1), step, o) >= x) --u;
+    return u;
+}
+
+// One compressed node per internal node.  The right child must be the left
+// one + 1 (Karras numbering); anything else raises RSI_ERR_INDEX.
+__global__ void k_quantize(const Node* __restrict__ nodes, int64_t n, NodeQ* __restrict__ out,
+                           DevCounters* __restrict__ ctr) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const Node nd = nodes[i];
+    const float lo[3] = {fminf(nd.lmin.x, nd.rmin.x), fminf(nd.lmin.y, nd.rmin.y), fminf(nd.lmin.z, nd.rmin.z)};
+    const float hi[3] = {fmaxf(nd.lmax.x, nd.rmax.x), fmaxf(nd.lmax.y, nd.rmax.y), fmaxf(nd.lmax.z, nd.rmax.z)};
+    float step[3];
+    unsigned meta = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int k = grid_exponent((double)hi[a] - (double)lo[a]);
+        step[a] = __int_as_float((k + 127) << 23);
+        meta |= (unsigned)(k + 127) << (8 * a);
+    }
+    const float clo[2][3] = {{nd.lmin.x, nd.lmin.y, nd.lmin.z}, {nd.rmin.x, nd.rmin.y, nd.rmin.z}};
+    const float chi[2][3] = {{nd.lmax.x, nd.lmax.y, nd.lmax.z}, {nd.rmax.x, nd.rmax.y, nd.rmax.z}};
+    unsigned b[12];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            b[6 * c + a] = quant_lo(clo[c][a], lo[a], step[a]);
+            b[6 * c + 3 + a] = quant_hi(chi[c][a], lo[a], step[a]);
+        }
+    }
+    const int lref = __float_as_int(nd.lmin.w), rref = __float_as_int(nd.lmax.w);
+    const int split = lref >= 0 ? lref : ~lref;
+    const int right = rref >= 0 ? rref : ~rref;
+    if (right != split + 1) atomicCAS(&ctr->error, 0, RSI_ERR_INDEX);
+    meta |= (lref < 0 ? 1u : 0u) << 24 | (rref < 0 ? 1u : 0u) << 25;
+    NodeQ q;
+    q.ox = lo[0];
+    q.oy = lo[1];
+    q.oz = lo[2];
+    q.meta = meta;
+    q.w0 = b[0] | b[1] << 8 | b[2] << 16 | b[3] << 24;
+    q.w1 = b[4] | b[5] << 8 | b[6] << 16 | b[7] << 24;
+    q.w2 = b[8] | b[9] << 8 | b[10] << 16 | b[11] << 24;
+    q.split = split;
+    out[i] = q;
+}
+
 // ---------------------------------------------------------------- single pass
 // Agglomerative build (Apetrei 2014; the bottom-up construction of Sec. 4.2):
 // one thread per leaf climbs the tree.  A node covering leaves [lo, hi] is
@@ -764,8 +844,8 @@ rsi_bvh_s* alloc_handle(int64_t nv, int64_t nt, int morton_bits, bool sort_scrat
     const size_t ksz = morton_bits == 30 ? 4 : 8;
     const int ntiles = grid_for(n, 4096);
     // one allocation, carved into the handle's arrays (256-byte aligned)
-    size_t off[13], total = 0;
-    size_t sizes[13] = {
+    size_t off[14], total = 0;
+    size_t sizes[14] = {
         sizeof(Node) * (size_t)ni,                 // 0 nodes
         sizeof(Tri) * (size_t)n,                   // 1 tris
         ksz * (size_t)n,                           // 2 sorted keys
@@ -778,9 +858,10 @@ rsi_bvh_s* alloc_handle(int64_t nv, int64_t nt, int morton_bits, bool sort_scrat
         4 * (size_t)ni,                            // 9 flags
         sizeof(DevCounters),                       // 10 counters
         sort_scratch ? 2 * ksz * (size_t)n + 8 * (size_t)n + 4 * 256 * (size_t)ntiles : 0,  // 11 sort scratch
-        sizeof(Node4) * (size_t)ni                 // 12 four-wide nodes
+        sizeof(Node4) * (size_t)ni,                // 12 four-wide nodes
+        sizeof(NodeQ) * (size_t)ni                 // 13 compressed nodes
     };
-    for (int i = 0; i < 13; ++i) {
+    for (int i = 0; i < 14; ++i) {
         off[i] = total;
         total += align_up(sizes[i]);
     }
@@ -803,6 +884,7 @@ rsi_bvh_s* alloc_handle(int64_t nv, int64_t nt, int morton_bits, bool sort_scrat
     h->ctr = (DevCounters*)(base + off[10]);
     *scratch = base + off[11];
     h->nodes4 = (Node4*)(base + off[12]);
+    h->nodesq = (NodeQ*)(base + off[13]);
     *base_out = base;
     return h;
 }
@@ -845,7 +927,8 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     if (rc) return cleanup(rc);
     if (n > 1) {
         k_collapse4<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(h->nodes, h->parent, n, h->nodes4);
-        note_launches(1);
+        k_quantize<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(h->nodes, n, h->nodesq, h->ctr);
+        note_launches(2);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "lbvh_build kernels"));
@@ -858,6 +941,7 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
                                                              : "lbvh_build: triangle vertex index out of range"));
     }
     finish_handle(h, hc);
+    h->has_q = n > 1;
     *out = h;
     return RSI_OK;
 }

@@ -35,6 +35,7 @@ namespace rsi {
 struct QueryArgs {
     const Node* nodes;
     const Node4* nodes4;   // four-wide nodes of the same hierarchy
+    const NodeQ* nodesq;   // compressed child-pair nodes (single queries)
     const Tri* tris;
     int64_t n_tri;
     const float* from;
@@ -434,13 +435,16 @@ constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^
 // hit with the smallest upper bound on t; the answer is certain when every
 // other certain hit's lower bound lies above it, else the segment is queued.
 //
-// WIDE: the node step fetches four-wide nodes (Node4): up to four child boxes
+// NW 1: the node step fetches four-wide nodes (Node4): up to four child boxes
 // per fetch; the first child that passes becomes next and the others are
-// pushed, so children are still visited in leaf order.
+// pushed, so children are still visited in leaf order.  NW 2: compressed
+// child-pair nodes (NodeQ, one 32-byte load); the child boxes are rebuilt
+// with outward rounding, so they contain the exact ones, and the walk is the
+// child-pair walk.  NW 0: child-pair nodes (Node).
 #ifndef RSI_TRAV_MIN_BLOCKS
 #define RSI_TRAV_MIN_BLOCKS 4   // resident 256-thread blocks per SM the register budget is sized for
 #endif
-template <int MODE, bool STATS, int STACK, bool BATCHED, bool WIDE>
+template <int MODE, bool STATS, int STACK, bool BATCHED, int NW>
 __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_query_fp32(QueryArgs A, BatchArgs B) {
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
             continue;
         }
         // node step
-        if (WIDE && active && next != kDone && next >= 0) {
+        if (NW == 1 && active && next != kDone && next >= 0) {
             const float4* p = reinterpret_cast<const float4*>((BATCHED ? l_nodes4 : A.nodes4) + next);
             float4 xl, xh, yl, yh, zl, zh, rff, pad;
             ld32B(p, xl, xh);
@@ -602,11 +606,36 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
                 top = sp > 0 ? stack[--sp] : kDone;
             }
         }
-        if (!WIDE && active && next != kDone && next >= 0) {
+        if (NW != 1 && active && next != kDone && next >= 0) {
             float4 lmin, lmax, rmin, rmax;
-            load_node(BATCHED ? l_nodes : A.nodes, next, lmin, lmax, rmin, rmax);
+            int lref, rref;
+            if (NW == 2) {
+                float4 fa, fb;
+                ld32B(reinterpret_cast<const float4*>(A.nodesq + next), fa, fb);
+                const unsigned meta = __float_as_uint(fa.w);
+                const float sx = __uint_as_float((meta & 0xFFu) << 23);
+                const float sy = __uint_as_float(((meta >> 8) & 0xFFu) << 23);
+                const float sz = __uint_as_float(((meta >> 16) & 0xFFu) << 23);
+                const unsigned w0 = __float_as_uint(fb.x), w1 = __float_as_uint(fb.y), w2 = __float_as_uint(fb.z);
+                const int split = __float_as_int(fb.w);
+#define RSI_QB(W, K) __uint2float_rn(((W) >> (8 * (K))) & 0xFFu)
+                lmin = make_float4(__fmaf_rd(RSI_QB(w0, 0), sx, fa.x), __fmaf_rd(RSI_QB(w0, 1), sy, fa.y),
+                                   __fmaf_rd(RSI_QB(w0, 2), sz, fa.z), 0.0f);
+                lmax = make_float4(__fmaf_ru(RSI_QB(w0, 3), sx, fa.x), __fmaf_ru(RSI_QB(w1, 0), sy, fa.y),
+                                   __fmaf_ru(RSI_QB(w1, 1), sz, fa.z), 0.0f);
+                rmin = make_float4(__fmaf_rd(RSI_QB(w1, 2), sx, fa.x), __fmaf_rd(RSI_QB(w1, 3), sy, fa.y),
+                                   __fmaf_rd(RSI_QB(w2, 0), sz, fa.z), 0.0f);
+                rmax = make_float4(__fmaf_ru(RSI_QB(w2, 1), sx, fa.x), __fmaf_ru(RSI_QB(w2, 2), sy, fa.y),
+                                   __fmaf_ru(RSI_QB(w2, 3), sz, fa.z), 0.0f);
+#undef RSI_QB
+                lref = (meta >> 24) & 1u ? ~split : split;
+                rref = (meta >> 25) & 1u ? ~(split + 1) : split + 1;
+            } else {
+                load_node(BATCHED ? l_nodes : A.nodes, next, lmin, lmax, rmin, rmax);
+                lref = __float_as_int(lmin.w);
+                rref = __float_as_int(lmax.w);
+            }
             if (STATS) ++visits;
-            int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
             bool hl, hr;
             if (MODE == RSI_ANY_HIT) {   // boolean: the child the segment spends longer in first
                 float ll, lr;
@@ -1842,9 +1871,9 @@ __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->node_visits = c->tri_tests = c->ambiguous = 0;
 }
 
-template <int MODE, bool STATS, int STACK, bool BATCHED, bool WIDE>
+template <int MODE, bool STATS, int STACK, bool BATCHED, int NW>
 void launch_fp32(const QueryArgs& A, const BatchArgs& B, int grid, int block, cudaStream_t s) {
-    k_query_fp32<MODE, STATS, STACK, BATCHED, WIDE><<<grid, block, 0, s>>>(A, B);
+    k_query_fp32<MODE, STATS, STACK, BATCHED, NW><<<grid, block, 0, s>>>(A, B);
 }
 
 // Stack entries a traversal needs: the binary walk pushes at most one entry
@@ -1853,17 +1882,23 @@ void launch_fp32(const QueryArgs& A, const BatchArgs& B, int grid, int block, cu
 inline int wide_stack_need(int height) { return 3 * ((height + 2) / 2); }
 inline bool wide_ok(int height) { return wide_stack_need(height) <= 128; }
 
+// nw: 0 child-pair nodes, 1 four-wide nodes, 2 compressed child-pair nodes
+// (single queries only; batched plans pass 0 or 1).
 template <int MODE, bool STATS, bool BATCHED = false>
-void launch_fp32_stack(const QueryArgs& A, int height, bool wide, int grid, int block, cudaStream_t s,
+void launch_fp32_stack(const QueryArgs& A, int height, int nw, int grid, int block, cudaStream_t s,
                        const BatchArgs& B = BatchArgs{}) {
-    if (wide && wide_ok(height)) {
+    if (nw == 1 && wide_ok(height)) {
         const int need = wide_stack_need(height);
-        if (need <= 32) launch_fp32<MODE, STATS, 32, BATCHED, true>(A, B, grid, block, s);
-        else if (need <= 64) launch_fp32<MODE, STATS, 64, BATCHED, true>(A, B, grid, block, s);
-        else launch_fp32<MODE, STATS, 128, BATCHED, true>(A, B, grid, block, s);
-    } else if (height < 32) launch_fp32<MODE, STATS, 32, BATCHED, false>(A, B, grid, block, s);
-    else if (height < 64) launch_fp32<MODE, STATS, 64, BATCHED, false>(A, B, grid, block, s);
-    else launch_fp32<MODE, STATS, 128, BATCHED, false>(A, B, grid, block, s);
+        if (need <= 32) launch_fp32<MODE, STATS, 32, BATCHED, 1>(A, B, grid, block, s);
+        else if (need <= 64) launch_fp32<MODE, STATS, 64, BATCHED, 1>(A, B, grid, block, s);
+        else launch_fp32<MODE, STATS, 128, BATCHED, 1>(A, B, grid, block, s);
+    } else if (!BATCHED && nw == 2) {
+        if (height < 32) launch_fp32<MODE, STATS, 32, false, 2>(A, B, grid, block, s);
+        else if (height < 64) launch_fp32<MODE, STATS, 64, false, 2>(A, B, grid, block, s);
+        else launch_fp32<MODE, STATS, 128, false, 2>(A, B, grid, block, s);
+    } else if (height < 32) launch_fp32<MODE, STATS, 32, BATCHED, 0>(A, B, grid, block, s);
+    else if (height < 64) launch_fp32<MODE, STATS, 64, BATCHED, 0>(A, B, grid, block, s);
+    else launch_fp32<MODE, STATS, 128, BATCHED, 0>(A, B, grid, block, s);
 }
 
 // k_query_fp64 over the first *n_list entries of A.band_ids.
@@ -1936,6 +1971,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     QueryArgs A;
     A.nodes = h->nodes;
     A.nodes4 = h->nodes4;
+    A.nodesq = h->nodesq;
     A.tris = h->tris;
     A.n_tri = h->n_tri;
     A.from = d_from;
@@ -1956,11 +1992,11 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
         return fail(RSI_ERR_INVALID_ARG, "rsi_query: block must be a multiple of 32 in [32, 256]");
     if (o.blocks_per_sm < 0) return fail(RSI_ERR_INVALID_ARG, "rsi_query: blocks_per_sm < 0");
-    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 4)
-        return fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2 or 4");
+    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 3 && o.node_width != 4)
+        return fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2, 3 or 4");
     if (o.fp64_all && (o.fp32_only || order))
         return fail(RSI_ERR_INVALID_ARG, "rsi_query: fp64_all excludes fp32_only and the learned query");
-    const bool wide = o.node_width == 4;
+    const int nw = o.node_width == 4 ? 1 : (o.node_width == 3 && h->has_q ? 2 : 0);
     const int block = o.block > 0 ? o.block : 256;
     const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
     int64_t want = (n + block - 1) / block;
@@ -1992,14 +2028,14 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (o.fp64_all) {
         k_queue_all<<<grid_for(n, 256), 256, 0, s>>>(band_ids, n, ctr);
     } else if (mode == RSI_ANY_HIT) {
-        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, wide, grid, block, s);
-        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, wide, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, nw, grid, block, s);
+        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, nw, grid, block, s);
     } else if (mode == RSI_COUNT) {
-        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, wide, grid, block, s);
-        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, wide, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, nw, grid, block, s);
+        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, nw, grid, block, s);
     } else {
-        if (o.collect_stats) launch_fp32_stack<RSI_NEAREST, true>(A, h->height, wide, grid, block, s);
-        else launch_fp32_stack<RSI_NEAREST, false>(A, h->height, wide, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_NEAREST, true>(A, h->height, nw, grid, block, s);
+        else launch_fp32_stack<RSI_NEAREST, false>(A, h->height, nw, grid, block, s);
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[1], s));
     if (!o.fp32_only) {
@@ -2288,8 +2324,8 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
         return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: block must be a multiple of 32 in [32, 256]");
     if (o.blocks_per_sm < 0) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: blocks_per_sm < 0");
-    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 4)
-        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2 or 4");
+    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 3 && o.node_width != 4)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2, 3 or 4");
     if (h->height >= 127) return rsi::fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
     int rc = rsi::ensure_band_capacity(h, n, s);
     if (rc) return rc;
@@ -2348,6 +2384,7 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     QueryArgs A{};
     A.nodes = h->nodes;
     A.nodes4 = h->nodes4;
+    A.nodesq = h->nodesq;
     A.tris = h->tris;
     A.n_tri = h->n_tri;
     A.from = df;
@@ -2363,7 +2400,7 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     A.fp32_only = o.fp32_only;
     const int block = o.block > 0 ? o.block : 256;
     const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
-    const bool wide = o.node_width == 4;
+    const int nw = o.node_width == 4 ? 1 : (o.node_width == 3 && h->has_q ? 2 : 0);
     k_reset_query<<<1, 1, 0, s>>>(h->ctr, ~0ull);   // ~0: the queue is fed by the posts above
     A.n_rays = n;
     BatchArgs Bs{};
@@ -2372,11 +2409,11 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + block - 1) / block,
                                                                    (int64_t)rsi::device_sm_count() * bps));
     if (mode == RSI_ANY_HIT) {
-        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, wide, grid, block, s, Bs);
-        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, wide, grid, block, s, Bs);
+        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, nw, grid, block, s, Bs);
+        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, nw, grid, block, s, Bs);
     } else {
-        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, wide, grid, block, s, Bs);
-        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, wide, grid, block, s, Bs);
+        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, nw, grid, block, s, Bs);
+        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, nw, grid, block, s, Bs);
     }
     rsi::note_launches(2);
     // every copy has landed once the traversal ends; the wait orders the FP64 pass after them
@@ -2619,9 +2656,9 @@ void launch_batched(rsi_batch_s* b, const QueryArgs& A, const BatchArgs& B, cuda
     const int bps = b->opt.blocks_per_sm > 0 ? b->opt.blocks_per_sm : 3;
     int64_t want = ((int64_t)b->total + block - 1) / block;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)rsi::device_sm_count() * bps));
-    const bool wide = b->opt.node_width == 4;
-    if (b->opt.collect_stats) launch_fp32_stack<MODE, true, true>(A, b->height, wide, grid, block, s, B);
-    else launch_fp32_stack<MODE, false, true>(A, b->height, wide, grid, block, s, B);
+    const int nw = b->opt.node_width == 4 ? 1 : 0;
+    if (b->opt.collect_stats) launch_fp32_stack<MODE, true, true>(A, b->height, nw, grid, block, s, B);
+    else launch_fp32_stack<MODE, false, true>(A, b->height, nw, grid, block, s, B);
     if (!b->opt.fp32_only) {
         const rsi::PairScratch P = rsi::carve_pairs(b->pairs, b->seg_cap, b->pair_cap, b->fb);
         launch_fp64_pass<MODE, true>(A, b->height, &P, s, B);

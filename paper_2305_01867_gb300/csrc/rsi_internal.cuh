@@ -36,6 +36,24 @@ struct __align__(128) Node4 {
 static_assert(sizeof(Node4) == 128, "node4 layout");
 constexpr int kEmpty4 = 0x7FFFFFFE;   // no child in this lane of a Node4
 
+// Compressed child-pair node (32 bytes, one 32-byte load): the node's own
+// box minimum as the frame origin, a power-of-two grid step per axis and the
+// children's boxes as 8-bit grid coordinates, rounded outward when built and
+// rebuilt with directed-rounding FMAs when read, so a rebuilt box always
+// contains the exact one (culling stays conservative).  In Karras numbering
+// the right child is the left one + 1, so one index names both children.
+//   meta bits 0-7 / 8-15 / 16-23: biased exponents of the x / y / z steps
+//   (step = 2^(e - 127)); bit 24: the left child is a leaf; bit 25: the right.
+//   q bytes, low byte first: w0 = l.xlo l.ylo l.zlo l.xhi,
+//   w1 = l.yhi l.zhi r.xlo r.ylo, w2 = r.zlo r.xhi r.yhi r.zhi.
+struct __align__(32) NodeQ {
+    float ox, oy, oz;
+    uint32_t meta;
+    uint32_t w0, w1, w2;
+    int32_t split;   // left child index (leaf or internal); right child = split + 1
+};
+static_assert(sizeof(NodeQ) == 32, "compressed node layout");
+
 // Triangle in leaf (Morton) order: three float4 vertices; v0.w carries the
 // caller's triangle id (int bits).  Padded to 64 bytes so that a lane fetches
 // it with two 32-byte loads, each reading one whole L1 sector.
@@ -82,6 +100,8 @@ struct rsi_bvh_s {
     // packed traversal data
     rsi::Node* nodes = nullptr;   // [max(n_tri - 1, 1)]
     rsi::Node4* nodes4 = nullptr; // [max(n_tri - 1, 1)], even-depth slots used
+    rsi::NodeQ* nodesq = nullptr; // [max(n_tri - 1, 1)] compressed child-pair nodes
+    bool has_q = false;           // nodesq written (single builds)
     rsi::Tri* tris = nullptr;     // [n_tri]
     // exported build arrays
     void* sorted_keys = nullptr;  // uint32 or uint64 [n_tri]

@@ -29,7 +29,7 @@ def test_autotune_caches_and_keeps_results(rsi, tmp_path):
     t1 = bvh.autotune(dF, dE, "count", cache_path=cache)
     assert t1["from_cache"] == 0 and t1["candidates"] >= 6 and t1["ms"] > 0
     h = bvh.info()["height"]
-    assert t1["node_width"] in (2, 4)
+    assert t1["node_width"] in (2, 3, 4)
     assert t1["stack"] >= (3 * ((h + 2) // 2) if t1["node_width"] == 4 else h + 1)
     t2 = bvh.autotune(dF, dE, "count", cache_path=cache)
     assert t2["from_cache"] == 1 and t2["candidates"] == 0

@@ -50,6 +50,8 @@ def _meshes():
     yield "c1", m.vertices, m.triangles
     m = W.config_mesh("c2")
     yield "c2", m.vertices, m.triangles
+    m = W.config_mesh("c3")                 # 178,802 triangles, jittered grid
+    yield "c3", m.vertices, m.triangles
 
 
 @pytest.mark.parametrize("builder", ["karras", "apetrei"])

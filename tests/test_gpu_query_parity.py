@@ -66,7 +66,7 @@ def test_case_study1_and_canopy(rsi):
         assert got["amb_hit"].sum() == 0 and got["amb_count"].sum() == 0
 
 
-@pytest.mark.parametrize("node_width", [2, 4])
+@pytest.mark.parametrize("node_width", [2, 3, 4])
 @pytest.mark.parametrize("bits", [30, 63])
 def test_c1_full_parity(rsi, bits, node_width):
     """32x32 heightfield, 1e5 segments: every segment checked, with the
@@ -273,12 +273,22 @@ def test_node_widths_agree_on_c2(rsi):
         # the four-wide walk fetches fewer nodes for the same answers
         assert b["stats"]["node_visits"] < a["stats"]["node_visits"]
         assert b["stats"]["band_rays"] == a["stats"]["band_rays"]
+        # compressed nodes: the same answers from boxes that are only ever larger
+        q = bvh.query(dF, dE, mode, node_width=3, stats=True)
+        for k in ("hit", "count", "ambiguous"):
+            if a[k] is not None:
+                assert torch.equal(a[k], q[k]), (mode, k)
+        if mode == "count":   # every overlap is visited: larger boxes, at least the same visits
+            assert a["stats"]["node_visits"] <= q["stats"]["node_visits"]
+        assert q["stats"]["node_visits"] <= 1.05 * a["stats"]["node_visits"]
     na, nb = bvh.nearest(dF, dE, node_width=2), bvh.nearest(dF, dE, node_width=4)
+    nq = bvh.nearest(dF, dE, node_width=3)
     for k in ("tri", "t", "dist", "ambiguous"):
         assert torch.equal(na[k], nb[k]), k
+        assert torch.equal(na[k], nq[k]), k
     assert torch.equal(torch.nan_to_num(na["point"], nan=-7.0), torch.nan_to_num(nb["point"], nan=-7.0))
     with pytest.raises(rsi.RSIError):
-        bvh.query(dF, dE, "any_hit", node_width=3)
+        bvh.query(dF, dE, "any_hit", node_width=5)
 
 
 @pytest.mark.parametrize("m", [6_000, 40_000])
