@@ -485,7 +485,8 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
                         break;
                     }
                     wbase = (int)b;
-                    wend = min(wbase + kWarpChunk, n_rays);
+                    // in 64 bits: the last chunk of a batch near 2^31 segments must not wrap
+                    wend = (int)min((long long)wbase + kWarpChunk, (long long)n_rays);
                     if (B.streamed) {   // device work queue fed by the host (batched plans, host-buffer queries)
                         bool ok = true;
                         if (lane == 0) ok = wait_ready(A.ctr, (unsigned long long)wend, B.timeout_ns);

@@ -220,3 +220,27 @@ def test_build_many_reports_the_bad_mesh(rsi):
     assert e.value.code == -8 and "mesh 1" in str(e.value)
     # the library keeps working
     assert len(rsi.build_many([(V, T)])) == 1
+
+
+@pytest.mark.parametrize("bits", [30, 63])
+def test_build_many_c4_meshes_equal_oracle(rsi, bits):
+    """The 64 heightfields of the batching workload (1e3 to 1e5 triangles
+    each, 1.16e6 in all), built by one batched build: every mesh's keys,
+    order, children, parents, boxes, height and extent equal the oracle's
+    plain-definition build bit for bit (Sec. 3.2 codes and sort, Sec. 4.2
+    tree and boxes)."""
+    jobs = W.batched_meshes(64, seed=4, max_rays=1)
+    dev = [(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda()) for m, _ in jobs]
+    many = rsi.build_many(dev, morton_bits=bits)
+    for k, ((m, _), b) in enumerate(zip(jobs, many)):
+        ref = oracle.build_all(m.vertices, m.triangles, bits=bits)
+        got = b.export()
+        for key in ("sorted_keys", "perm", "left", "right", "parent"):
+            assert np.array_equal(got[key], ref[key]), (k, key)
+        assert np.array_equal(got["box"].view(np.uint32), ref["box"].view(np.uint32)), k
+        info = b.info()
+        assert info["height"] == ref["height"], k
+        lo, hi = oracle.extent(m.vertices)
+        assert np.array_equal(np.array(info["extent_lo"], np.float32), lo), k
+        assert np.array_equal(np.array(info["extent_hi"], np.float32), hi), k
+        b.close()

@@ -1,11 +1,11 @@
 """Every segment of the 1e7-segment c2 batch against the oracle, in all three
-modes (opt-in: about three minutes of brute force on 16 host cores).
+modes: the exhaustive search of Sec. 1 on 2e11 segment/triangle pairs, about
+three minutes of FP64 brute force on 16 host cores.
 
-Run with RSI_FULL_ORACLE=1; otherwise skipped.  The default GPU tests check
-a seeded sample plus every segment the GPU marks, and every segment against
-the FP64-everywhere mode.  The bar is the sampled tests': ambiguity marks
-identical; hit flags and counts identical on every unmarked segment; the
-nearest crossing (triangle, t, point, distance) identical on every segment."""
+Part of the default GPU run; RSI_SKIP_FULL_ORACLE=1 skips it for quick local
+iterations.  The bar: ambiguity marks identical; hit flags and counts
+identical on every unmarked segment; the nearest crossing (triangle, t,
+point, distance) identical on every segment."""
 import os
 
 import numpy as np
@@ -21,8 +21,8 @@ torch = pytest.importorskip("torch")
 
 @pytest.fixture(scope="module")
 def rsi():
-    if os.environ.get("RSI_FULL_ORACLE") != "1":
-        pytest.skip("opt-in: set RSI_FULL_ORACLE=1 (about 3 min of CPU brute force)")
+    if os.environ.get("RSI_SKIP_FULL_ORACLE") == "1":
+        pytest.skip("RSI_SKIP_FULL_ORACLE=1")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     import paper_2305_01867_gb300 as m

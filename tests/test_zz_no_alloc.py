@@ -46,10 +46,18 @@ def test_noalloc_matches_rsi_query_twice(rsi):
         cnt = torch.full((n,), -7, dtype=torch.int32, device="cuda")
         amb_c = torch.full((n,), 7, dtype=torch.uint8, device="cuda")
         free0 = torch.cuda.mem_get_info()[0]
-        assert _noalloc(rsi, bvh, dF, dE, rsi.RSI_ANY_HIT, hit=hit, amb=amb) == 0, rsi.last_error()
-        assert _noalloc(rsi, bvh, dF, dE, rsi.RSI_COUNT, count=cnt, amb=amb_c) == 0, rsi.last_error()
-        torch.cuda.synchronize()
-        if call == 1:   # set-up done on the first call: nothing allocated now
+        if call == 1:
+            # set-up done on the first call: from now on any allocation the
+            # library attempts fails (RSI_ERR_OOM), even one its memory pool
+            # could serve from cached blocks without touching free memory
+            rsi.fail_allocations(0)
+        try:
+            assert _noalloc(rsi, bvh, dF, dE, rsi.RSI_ANY_HIT, hit=hit, amb=amb) == 0, rsi.last_error()
+            assert _noalloc(rsi, bvh, dF, dE, rsi.RSI_COUNT, count=cnt, amb=amb_c) == 0, rsi.last_error()
+            torch.cuda.synchronize()
+        finally:
+            rsi.fail_allocations(None)
+        if call == 1:   # and nothing outside the library's pool was taken either
             assert torch.cuda.mem_get_info()[0] == free0
         # flags and counts are integers: the bar is exact equality
         assert torch.equal(hit, ref_a["hit"]) and torch.equal(amb, ref_a["ambiguous"])
@@ -65,3 +73,47 @@ def test_noalloc_rejects_oversize_batches(rsi):
     hit = torch.zeros(n, dtype=torch.uint8, device="cuda")
     rc = _noalloc(rsi, bvh, dF, dF, rsi.RSI_ANY_HIT, hit=hit)
     assert rc == -1 and "RSI_NOALLOC_MAX_RAYS" in rsi.last_error()
+
+
+def test_noalloc_grazing_batch_at_the_cap(rsi):
+    """A full-size call (RSI_NOALLOC_MAX_RAYS segments) from the jittered
+    300 x 300 mesh with 1 % grazing segments: many segments go to the FP64
+    re-test, which here runs from the fixed array.  Both modes equal
+    rsi_query on every segment, with every library allocation failing, and
+    a sample (all marked ambiguous segments up to 400, plus 600 others)
+    equals the oracle."""
+    import oracle
+    mesh = W.config_mesh("c3")
+    n = rsi.NOALLOC_MAX_RAYS
+    F, E = W.rays(W.config_rays("c3"), mesh, 0, n)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).cuda(), torch.from_numpy(mesh.triangles).cuda(), morton_bits=63)
+    ref_a = bvh.query(dF, dE, "any_hit", stats=True)
+    ref_c = bvh.query(dF, dE, "count", stats=True)
+    assert ref_c["stats"]["band_rays"] > 10_000   # the FP64 pass has real work
+    hit = torch.full((n,), 7, dtype=torch.uint8, device="cuda")
+    amb = torch.full((n,), 7, dtype=torch.uint8, device="cuda")
+    cnt = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    amb_c = torch.full((n,), 7, dtype=torch.uint8, device="cuda")
+    assert _noalloc(rsi, bvh, dF, dE, rsi.RSI_COUNT, count=cnt, amb=amb_c) == 0, rsi.last_error()   # set-up
+    rsi.fail_allocations(0)
+    try:
+        for _ in range(2):
+            assert _noalloc(rsi, bvh, dF, dE, rsi.RSI_ANY_HIT, hit=hit, amb=amb) == 0, rsi.last_error()
+            assert _noalloc(rsi, bvh, dF, dE, rsi.RSI_COUNT, count=cnt, amb=amb_c) == 0, rsi.last_error()
+            torch.cuda.synchronize()
+            assert torch.equal(hit, ref_a["hit"]) and torch.equal(amb, ref_a["ambiguous"])
+            assert torch.equal(cnt, ref_c["count"]) and torch.equal(amb_c, ref_c["ambiguous"])
+    finally:
+        rsi.fail_allocations(None)
+    got_amb = amb_c.cpu().numpy()
+    rng = np.random.default_rng(5)
+    marked = np.flatnonzero(got_amb)[:400]
+    idx = np.unique(np.concatenate([marked, rng.choice(n, 600, replace=False)]))
+    ref = oracle.query(mesh.vertices, mesh.triangles, F[idx], E[idx])
+    h, a = hit.cpu().numpy()[idx], amb.cpu().numpy()[idx]
+    c, ac = cnt.cpu().numpy()[idx], got_amb[idx]
+    assert np.array_equal(a, ref["amb_hit"]) and np.array_equal(ac, ref["amb_count"])
+    assert np.array_equal(h[a == 0], ref["hit"][a == 0])
+    assert np.array_equal(c[ac == 0], ref["count"][ac == 0])
+    bvh.close()
