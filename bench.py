@@ -54,10 +54,13 @@ def peaks():
 
 def source_hash():
     """Hash of the traversal kernels' source: the region between their
-    markers in query.cu (device code and the structures it reads)."""
-    q = open(os.path.join(ROOT, "paper_2305_01867_gb300", "csrc", "query.cu")).read()
+    markers in query.cu (device code and the structures it reads) and the
+    FP32 segment / box / triangle tests it includes (segtest.cuh)."""
+    csrc = os.path.join(ROOT, "paper_2305_01867_gb300", "csrc")
+    q = open(os.path.join(csrc, "query.cu")).read()
     b, e = q.index("// [traversal kernel: begin]"), q.index("// [traversal kernel: end]")
-    return hashlib.sha256(q[b:e].encode()).hexdigest()[:16]
+    t = open(os.path.join(csrc, "segtest.cuh")).read()
+    return hashlib.sha256((q[b:e] + t).encode()).hexdigest()[:16]
 
 
 def profile_values():
@@ -98,6 +101,24 @@ def issue_bound():
             "l1tex_throughput_frac": v.get("l1tex_throughput_pct", float("nan")) / 100,
             "lts_throughput_frac": v.get("lts_throughput_pct", float("nan")) / 100,
             "source": "ncu --set full capture of the same kernel source (profiles/k_query_fp32_count_c2.md)"}
+
+
+def second_bound():
+    """The count traversal's binding limit, from the committed ncu capture of
+    the same kernel source: instruction issue (issue slots busy) beside L1
+    throughput.  A stale capture is reported as such (and on stderr), never
+    silently dropped."""
+    v = profile_values()
+    if "issue_active_pct" not in v:
+        msg = ("STALE: profiles/k_query_fp32_count_c2.md was captured on another traversal source "
+               f"(current source_hash {source_hash()}); issue / L1 figures withheld")
+        print("bench.py: " + msg, file=sys.stderr)
+        return {"stale": msg}
+    return {"bound": "issue", "achieved": v["issue_active_pct"] / 100, "peak": 1.0, "unit": "issue slots busy",
+            "frac": v["issue_active_pct"] / 100,
+            "l1tex_frac": v.get("l1tex_throughput_pct", float("nan")) / 100,
+            "peak_source": "ncu smsp__issue_active / l1tex__throughput of the same kernel source "
+                           "(profiles/k_query_fp32_count_c2.md)"}
 
 
 class ClockSampler:
@@ -263,7 +284,14 @@ def measure_batched(rsi, torch, dev, c4, args):
         return e0.elapsed_time(e1) / steps
 
     for mode in ("any_hit", "count"):
-        plan = rsi.BatchPlan(items, mode)
+        t0 = time.perf_counter()
+        tune = rsi.batch_autotune(items, mode)
+        tune_s = time.perf_counter() - t0
+        picked = {k: tune[k] for k in ("block", "blocks_per_sm", "node_width", "ray_sort_tile", "stack")}
+        plan_default = rsi.BatchPlan(items, mode)
+        ms_default = timed(plan_default.run)
+        plan_default.close()
+        plan = rsi.BatchPlan(items, mode, **picked)
         ms = timed(plan.run)
         outs = {}
 
@@ -274,11 +302,32 @@ def measure_batched(rsi, torch, dev, c4, args):
                 outs[i] = b.query(f, t, mode, **{key: buf}, ambiguous=plan.ambiguous[i])
         ms_seq = timed(sequential)
         st = plan.stats()
-        out[mode] = {"rays_per_s": total / (ms / 1e3), "ms": ms, "sequential_rays_per_s": total / (ms_seq / 1e3),
+        out[mode] = {"rays_per_s": total / (ms / 1e3), "ms": ms, "autotuned": picked,
+                     "autotune_s": tune_s, "autotune_candidates": tune["candidates"],
+                     "default_plan_ms": ms_default, "gain_over_default": ms_default / ms,
+                     "sequential_rays_per_s": total / (ms_seq / 1e3),
                      "sequential_ms": ms_seq, "band_rays": st["band_rays"], "ambiguous": st["ambiguous"]}
         plan.close()
     for b in bvhs:
         b.close()
+
+    # build and query in sequence, as a caller would: one batched build of
+    # the 64 meshes, then one rsi_query_batched call on the new hierarchies
+    # (a new plan each time: the hierarchies are new), wall clock
+    def build_and_query():
+        hs = rsi.build_many(meshes)
+        rsi.query_batched([(b, f, t) for b, (_, f, t) in zip(hs, items)], "any_hit")
+        torch.cuda.synchronize()
+        for b in hs:
+            b.close()
+    build_and_query()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        build_and_query()
+    out["build_then_query_any_hit_ms"] = 1e3 * (time.perf_counter() - t0) / steps
+    out["build_then_query_note"] = ("wall clock of lbvh_build_batched + one rsi_query_batched call (plan, graph "
+                                    "capture, launch) per step; the build checks the meshes on the host before "
+                                    "it returns hierarchies, so it is not captured with the query")
     return out
 
 
@@ -483,8 +532,48 @@ def measure_precision_c3(rsi, torch, dev, c3, args):
             res[key] = (val.cpu().numpy(), r["ambiguous"].cpu().numpy())
             out[key] = {"ms": ms, "rays_per_s": n / (ms / 1e3), "band_rays": st["band_rays"],
                         "ambiguous": st["ambiguous"]}
+    # the count traversal's roofline on this workload (CUDA events around the
+    # kernel on the query's stream, median of 3)
+    trav = []
+    for _ in range(4):
+        bvh.query(dF, dE, "count", time_kernels=True)
+        trav.append(bvh.last_query_ms()[0])
+    trav_ms = statistics.median(trav[1:])
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_RAY_COUNT * n / (trav_ms / 1e3) / 1e9
+    out["roofline"] = {"kernel": "k_query_fp32<count> (FP32 traversal, intercept_count)", "bound": "hbm",
+                       "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                       else "fallback 6.8 TB/s", "traffic": None, "algorithmic_bytes_per_ray": BYTES_PER_RAY_COUNT,
+                       "kernel_ms": trav_ms}
     bvh.close()
     del dF, dE
+    # end to end through the host-buffer calls: pinned mesh and segments in,
+    # pinned results out; build + boolean + count per step, wall clock
+    pV = torch.from_numpy(mesh.vertices).pin_memory()
+    pT = torch.from_numpy(mesh.triangles).pin_memory()
+    pF, pE = torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory()
+    hh, ha = torch.empty(n, dtype=torch.uint8).pin_memory(), torch.empty(n, dtype=torch.uint8).pin_memory()
+    hc, hac = torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.uint8).pin_memory()
+
+    def step_e2e():
+        b = rsi.LBVH(pV, pT, morton_bits=63)
+        b.query_host(pF, pE, "any_hit", hit=hh, ambiguous=ha)
+        b.query_host(pF, pE, "count", count=hc, ambiguous=hac)
+        b.close()
+    step_e2e()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        step_e2e()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / 3
+    same = bool(np.array_equal(hh.numpy(), res["any_hit_fp64_retest"][0])
+                and np.array_equal(hc.numpy(), res["count_fp64_retest"][0]))
+    out["e2e"] = {"value": n / (e2e_ms / 1e3), "unit": "rays/s",
+                  "h2d_bytes_per_step": pV.numel() * 4 + pT.numel() * 4 + 2 * (pF.numel() + pE.numel()) * 4,
+                  "d2h_bytes_per_step": n * (1 + 1) + n * (4 + 1), "ms_per_step": e2e_ms,
+                  "step": "host mesh -> build -> boolean + intercept_count queries of host segments -> host results",
+                  "matches_device_results": same}
+    del pF, pE, hh, ha, hc, hac
     rng = np.random.default_rng(31)
     checked = {}
     for mode in ("any_hit", "count"):
@@ -573,14 +662,22 @@ def measure_learned(rsi, torch, dev, c5, args):
     ms_learned = timed(lambda: rsi.query_learned(bvh, net, dF, dE, hit=hit, ambiguous=amb))
     same = bool(torch.equal(hit, plain_hit))
     st = rsi.query_learned(bvh, net, dF, dE, hit=hit, ambiguous=amb, stats=True)["stats"]
+    st_plain = bvh.query(dF, dE, "any_hit", hit=hit, ambiguous=amb, stats=True)["stats"]
     top4 = torch.empty(n, 4, dtype=torch.uint8, device=dev)
     ms_fwd = timed(lambda: net.forward(bvh, dF, dE, logits=False, top4=True))
     tflops = MLP_FLOP_PER_SEGMENT * n / (ms_fwd / 1e3) / 1e12
     burst, sustained, kind = bf16_peak()
     hits = int(plain_hit.sum())
     bvh.close()
+    work = {"plain": {"node_visits_per_segment": st_plain["node_visits"] / n,
+                      "tri_tests_per_segment": st_plain["tri_tests"] / n},
+            "learned": {"node_visits_per_segment": st["node_visits"] / n,
+                        "tri_tests_per_segment": st["tri_tests"] / n,
+                        "note": "tri_tests include the proposal's verification tests"}}
     return {"train_segments": int(Ft.shape[0]), "epochs": 2, "batch": 8192, "train_s": train_s,
-            "loss_per_epoch": losses, "eval_segments": n, "steps": steps,
+            "train_note": "train_s: 2 epochs over 1e7 labelled segments on the GPU's SIMT training kernels "
+                          "(one-off set-up, not part of the query)",
+            "loss_per_epoch": losses, "eval_segments": n, "steps": steps, "work": work,
             "plain_any_hit": {"ms": ms_plain, "rays_per_s": n / (ms_plain / 1e3)},
             "learned_any_hit": {"ms": ms_learned, "rays_per_s": n / (ms_learned / 1e3), "matches_plain": same},
             "proposal_confirmed": st["proposal_confirmed"], "hits": hits,
@@ -755,6 +852,40 @@ def main():
             per[f"{mode}_traverse_ms"] = statistics.median(ts[1:])
         per["node_fetches_per_ray_count"] = st_w["node_visits"] / n
         widths[str(w)] = per
+    # the same queries walking the segments in midpoint-cell order
+    # (rsi_segment_order), and a whole step with the order computed in it
+    order = bvh.segment_order(dF, dE)
+    ordered = {}
+    for mode in ("any_hit", "count"):
+        ts = []
+        for _ in range(5):
+            bvh.query(dF, dE, mode, hit=hit, count=cnt, ambiguous=amb_c, time_kernels=True, order=order)
+            ts.append(bvh.last_query_ms()[0])
+        ordered[f"{mode}_traverse_ms"] = statistics.median(ts[1:])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        bvh.segment_order(dF, dE, out=order)
+    e0.record(stream)
+    for _ in range(5):
+        bvh.segment_order(dF, dE, out=order)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ordered["order_ms"] = e0.elapsed_time(e1) / 5
+
+    def step_ordered():
+        b = rsi.LBVH(dV, dT, morton_bits=30)
+        b.segment_order(dF, dE, out=order)
+        b.query(dF, dE, "any_hit", hit=hit, ambiguous=amb_h, order=order)
+        b.query(dF, dE, "count", count=cnt, ambiguous=amb_c, order=order)
+        b.close()
+    for _ in range(3):
+        step_ordered()
+    e0.record(stream)
+    for _ in range(10):
+        step_ordered()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ordered["step_ms"] = e0.elapsed_time(e1) / 10
     bvh.close()
 
     if rank != 0:
@@ -775,7 +906,7 @@ def main():
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s",
                      "traffic": traffic_per_launch(), "algorithmic_bytes_per_ray": BYTES_PER_RAY_COUNT,
-                     "kernel_ms": trav_ms},
+                     "kernel_ms": trav_ms, "second_bound": second_bound()},
         "l2_issue_bound": issue_bound(),
         "e2e": {"value": ws * n / (e2e_ms / 1e3), "unit": "rays/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "matches_device_results": same},
@@ -790,6 +921,7 @@ def main():
         "counters_all_ranks": dict(zip(("band_rays_count", "ambiguous_count", "band_rays_any", "ambiguous_any"),
                                        job_counts)),
         "node_width": widths,
+        "segment_order": ordered,
     }
     if not args.no_builders:
         line["builders"] = measure_builders(rsi, torch, dev, [("c2", mesh), ("c3", W.config_mesh("c3"))],

@@ -95,6 +95,17 @@ typedef struct rsi_options {
                            segment with the FP64 re-test (a validation mode:
                            its answers must equal the default path's; slow).
                            Device-buffer queries only; not with fp32_only. */
+    int stack;          /* entries of the FP32 traversal's stack: 0 = the
+                           smallest of 32 / 64 / 128 that holds the walk of
+                           the tree; 32, 64 or 128 = at least that many (a
+                           tuning choice; results are unchanged)            */
+    const int32_t* order; /* device [n_rays]: the order in which the FP32
+                           traversal takes the segments, a permutation of
+                           0 .. n_rays - 1 such as rsi_segment_order writes
+                           (NULL = input order).  Results are unchanged and
+                           stay at the segments' own indices.  Device-buffer
+                           rsi_query / rsi_query_nearest only; not with
+                           ray_sort_tile.                                   */
 } rsi_options;
 
 /* Per-query counters, filled on the host when a non-NULL pointer is given
@@ -289,6 +300,21 @@ int rsi_nearest_compact(const int32_t* d_tri, const float* d_dist, const float* 
                         int64_t* n_hits, void* stream);
 
 /*
+ * A traversal order for the segments of a batch (no counterpart in the
+ * paper; the answers do not depend on the order): d_order [n_rays] (device,
+ * caller-owned) receives 0 .. n_rays - 1 sorted by the Morton cell of each
+ * segment's midpoint on a 32 x 32 x 32 grid over the hierarchy's extent
+ * (order inside a cell arbitrary).  Pass it as rsi_options.order to any
+ * number of queries of the same segments: neighbouring segments then cross
+ * the same part of the tree and share node fetches.  Three launches and a
+ * 128 KB counter array kept by the handle (allocated on first use);
+ * asynchronous.  Errors: RSI_ERR_INVALID_ARG for a NULL handle or pointer
+ * or n_rays outside [0, 2^31).
+ */
+int rsi_segment_order(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int32_t* d_order,
+                      void* stream);
+
+/*
  * As rsi_query with segments and results in HOST memory; returns after the
  * results are in host memory.  Batches of up to 2^26 segments are staged
  * whole on the device (30 B per segment, kept for later calls): the segments
@@ -322,7 +348,10 @@ int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t 
  *
  * The first call on a device looks up that device's address of the array
  * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the one array: each call
+ * before any stream capture.  The looked-up address is kept for the life of
+ * the process: cudaDeviceReset (or anything else that destroys the device's
+ * primary context) invalidates it, as it invalidates every handle built
+ * before, so do not call this entry point on that device afterwards.  All calls share the one array: each call
  * clears the counters it needs, but calls whose work overlaps on the GPU
  * (different streams, or different threads without ordering) race on it and
  * must be serialized by the caller.  Device-side errors are not reported.
@@ -359,17 +388,39 @@ typedef struct rsi_batch_s* rsi_batch_t;
  * opt->timeout_ns < 0 selects streaming: the work queue starts empty and the
  * caller makes segments available with rsi_batch_post (|timeout_ns| bounds
  * each wait of the kernel for a post, then RSI_ERR_TIMEOUT is raised and the
- * unposted segments are left untouched).  opt->ray_sort_tile is ignored.
- * Synchronizes `stream`. */
+ * unposted segments are left untouched).  opt->ray_sort_tile (256..8192)
+ * groups each batch's segments tile by tile as rsi_query does (the graph
+ * then starts with one reordering launch per batch); streaming plans
+ * ignore it.  opt->node_width 3 is treated as 2.  Synchronizes `stream`. */
 int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int mode, const rsi_options* opt,
                      void* stream, rsi_batch_t* out);
 
 /* Replay the plan on `stream` (one graph launch, asynchronous). */
-int rsi_query_batched(rsi_batch_t plan, void* stream);
+int rsi_batch_launch(rsi_batch_t plan, void* stream);
+
+/*
+ * The batched query in one call: batch i's segments against hierarchy
+ * hs[i], each with the boolean or intercept_count answer of Sec. 1 (mode),
+ * exactly as rsi_query would give it.
+ *   hs        [n_meshes] built hierarchies (host array of handles)
+ *   batches   [n_meshes] segments and outputs (device buffers, as in
+ *             rsi_batch_create); batches[i].bvh must be NULL or hs[i]
+ *   opt       as for rsi_batch_create (streaming plans are not available
+ *             here: opt->timeout_ns < 0 is rejected)
+ * The library plans the call (rsi_batch_create: descriptor table, scratch,
+ * graph capture; this synchronizes `stream`) and keeps the plan: a later
+ * call with the same hierarchies, buffers, sizes, mode and options replays
+ * it with one graph launch and returns without waiting.  Up to 4 plans are
+ * kept per process (least recently used first out); lbvh_free drops the
+ * plans that name the freed hierarchy.  A call's scratch is its plan's, so
+ * two calls with identical arguments must not overlap on the GPU.
+ */
+int rsi_query_batched(const rsi_bvh_t* hs, int n_meshes, const rsi_ray_batch* batches, int mode,
+                      const rsi_options* opt, void* stream);
 
 /* Streaming plans only: segments [0, n_ready) of the concatenated batches
  * (batch 0's, then batch 1's, ...) are now in device memory.  Call after
- * rsi_query_batched for the run being fed, on a stream other than the one
+ * rsi_batch_launch for the run being fed, on a stream other than the one
  * running the plan, after the copies of those segments on that stream
  * (stream order makes them visible first; the post also waits for the run's
  * queue reset, not for the run).  Counts must not decrease; at most 256
@@ -393,7 +444,7 @@ typedef struct rsi_tuning {
     float ms;           /* time of the best candidate on the sample          */
     int from_cache;     /* 1 if the choice came from the cache file          */
     int candidates;     /* candidates timed (0 on a cache hit)               */
-    int node_width;     /* node width chosen (2 or 4, see rsi_options)       */
+    int node_width;     /* node width chosen (2, 3 or 4, see rsi_options)    */
 } rsi_tuning;
 
 /*
@@ -409,6 +460,20 @@ typedef struct rsi_tuning {
  */
 int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays, int mode,
                  const char* cache_path, rsi_options* inout, rsi_tuning* result, void* stream);
+
+/*
+ * The same tuning for batched plans (tuning has no counterpart in the
+ * paper): times plans of the batches (each batch cut to its first 2^17
+ * segments, outputs in scratch the call allocates) over threads per block,
+ * resident blocks per SM, node width (2 or 4), the in-tile reordering
+ * (0 or 8192) and the traversal stack (the smallest bucket that holds the
+ * deepest tree, or the next one), writes the winner into *inout and
+ * result->(block, blocks_per_sm, node_width, ray_sort_tile, stack), and
+ * caches it in `cache_path` keyed by device, mode, the number of batches and
+ * log2 buckets of their total triangles and segments.  Synchronizes `stream`.
+ */
+int rsi_batch_autotune(const rsi_ray_batch* batches, int n_batches, int mode, const char* cache_path,
+                       rsi_options* inout, rsi_tuning* result, void* stream);
 
 /*
  * Learned cluster proposal for boolean queries (no counterpart in the paper;
@@ -436,8 +501,10 @@ int rsi_mlp_get_params(rsi_mlp_t m, float* h_params, float* h_grads, void* strea
 
 /* Tensor-core inference for n segments against the extent of hierarchy h:
  * d_logits [n][256] float (nullable) and/or d_top4 [n][4] cluster ids, best
- * first (nullable).  Asynchronous; rsi_mlp_status reports a tensor-core wait
- * that ran out (RSI_ERR_TIMEOUT). */
+ * first (nullable).  The top 4 are chosen on keys made of the FP32 logit
+ * with its low 8 bits replaced by 255 - cluster, compared as floats.
+ * Asynchronous; rsi_mlp_status reports a tensor-core wait that ran out
+ * (RSI_ERR_TIMEOUT). */
 int rsi_mlp_forward(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
                     float* d_logits, uint8_t* d_top4, void* stream);
 /* Synchronizes `stream` and returns RSI_ERR_TIMEOUT if a tensor-core wait of
@@ -445,11 +512,13 @@ int rsi_mlp_forward(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const float* 
  * valid), else RSI_OK. */
 int rsi_mlp_status(rsi_mlp_t m, void* stream);
 
-/* The network's activation on n device floats z (for tests): d_erf gets the
- * erf approximation the network uses (Abramowitz & Stegun 7.1.26, |error| <=
- * 1.5e-7), d_erf_cuda CUDA's erff of the same z, d_gelu the GELU
- * 0.5 z (1 + erf(z / sqrt 2)) the layers apply. */
-int rsi_mlp_activation(const float* d_z, int64_t n, float* d_erf, float* d_erf_cuda, float* d_gelu, void* stream);
+/* The network's activation on n device floats z (for tests): GELU in its
+ * tanh form, 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) (Hendrycks &
+ * Gimpel 2016).  d_tanh gets tanh(z) by the hardware approximation inference
+ * uses (tanh.approx.f32), d_tanh_cuda CUDA's tanhf of the same z, d_gelu the
+ * GELU the inference layers apply.  (Training evaluates the same formula
+ * with tanhf.) */
+int rsi_mlp_activation(const float* d_z, int64_t n, float* d_tanh, float* d_tanh_cuda, float* d_gelu, void* stream);
 
 /* One training step on the GPU over a batch of n (1..65536) segments with
  * multi-hot labels d_labels [n][8] uint32 (bit c of word c/32: the segment
@@ -464,6 +533,14 @@ int rsi_mlp_train_step(rsi_mlp_t m, rsi_bvh_t h, const float* d_from, const floa
 /* Zero the Adam moments and step count (the weights are kept). */
 int rsi_mlp_reset_optimizer(rsi_mlp_t m, void* stream);
 
+/* Attach network m to hierarchy h (m = NULL detaches): from then on
+ * rsi_query in RSI_ANY_HIT mode on h answers through the learned proposal
+ * (rsi_query_learned) with the same answers; the other modes, the
+ * host-buffer, batched and no-allocation queries are unaffected.  Freeing
+ * either object detaches them.  A hierarchy holds at most one network; a
+ * network may serve several hierarchies. */
+int rsi_mlp_attach(rsi_bvh_t h, rsi_mlp_t m);
+
 /*
  * Training labels: d_labels [n][8] uint32, bit c set when segment i meets a
  * triangle of cluster c (c = 256 * leaf / n_triangles) -- FP32 decisions,
@@ -475,12 +552,13 @@ int rsi_cluster_labels(rsi_bvh_t h, const float* d_from, const float* d_to, int6
 
 /*
  * Boolean query with the learned proposal (Sec. 1's boolean mode; the
- * proposal has no counterpart in the paper): the network proposes 4 of the
- * 256 clusters per segment (tensor cores); the triangles of those clusters
- * are tested in FP32 and a certain decisive hit ends the segment with hit =
- * 1; every other segment gets the plain query (tree search + FP64 re-test).
- * d_hit / d_ambiguous are therefore identical to rsi_query's.  Scratch as
- * rsi_query (plus 4 B per segment); asynchronous unless `stats`.
+ * proposal has no counterpart in the paper): one tensor-core kernel runs the
+ * network on tiles of 128 segments, keeps each segment's 4 proposed clusters
+ * in registers and tests their triangles in FP32; a certain decisive hit
+ * ends the segment with hit = 1.  Every other segment gets the plain query
+ * (tree search + FP64 re-test) in a second launch.  d_hit / d_ambiguous are
+ * therefore identical to rsi_query's.  Scratch as rsi_query; asynchronous
+ * unless `stats` (whose tri_tests then include the proposal's tests).
  */
 int rsi_query_learned(rsi_bvh_t h, rsi_mlp_t m, const float* d_from, const float* d_to, int64_t n_rays,
                       const rsi_options* opt, uint8_t* d_hit, uint8_t* d_ambiguous, rsi_stats* stats,

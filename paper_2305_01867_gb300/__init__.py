@@ -36,7 +36,8 @@ class RSIError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("fp32_only", ctypes.c_int), ("block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("collect_stats", ctypes.c_int), ("timeout_ns", ctypes.c_int64), ("time_kernels", ctypes.c_int),
-                ("ray_sort_tile", ctypes.c_int), ("node_width", ctypes.c_int), ("fp64_all", ctypes.c_int)]
+                ("ray_sort_tile", ctypes.c_int), ("node_width", ctypes.c_int), ("fp64_all", ctypes.c_int),
+                ("stack", ctypes.c_int), ("order", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -100,19 +101,27 @@ def _load():
     lib.rsi_nearest_compact.argtypes = [P, P, P, i64, P, P, P, P, ctypes.POINTER(ctypes.c_int64), P]
     lib.rsi_nearest_compact.restype = ctypes.c_int
     lib.rsi_query_noalloc.restype = ctypes.c_int
+    lib.rsi_segment_order.argtypes = [P, P, P, i64, P, P]
+    lib.rsi_segment_order.restype = ctypes.c_int
     lib.rsi_last_query_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     lib.rsi_last_query_ms.restype = ctypes.c_int
     lib.rsi_kernel_launches.argtypes = []
     lib.rsi_kernel_launches.restype = ctypes.c_uint64
     lib.rsi_autotune.argtypes = [P, P, P, i64, i32, ctypes.c_char_p, ctypes.POINTER(Options), ctypes.POINTER(Tuning), P]
+    lib.rsi_batch_autotune.argtypes = [ctypes.POINTER(RayBatch), i32, i32, ctypes.c_char_p, ctypes.POINTER(Options),
+                                       ctypes.POINTER(Tuning), P]
+    lib.rsi_batch_autotune.restype = ctypes.c_int
     lib.rsi_autotune.restype = ctypes.c_int
     lib.rsi_batch_create.argtypes = [ctypes.POINTER(RayBatch), i32, i32, ctypes.POINTER(Options), P,
                                      ctypes.POINTER(P)]
-    lib.rsi_query_batched.argtypes = [P, P]
+    lib.rsi_batch_launch.argtypes = [P, P]
+    lib.rsi_query_batched.argtypes = [ctypes.POINTER(P), i32, ctypes.POINTER(RayBatch), i32, ctypes.POINTER(Options),
+                                      P]
     lib.rsi_batch_post.argtypes = [P, i64, P]
     lib.rsi_batch_stats.argtypes = [P, ctypes.POINTER(Stats), P]
     lib.rsi_batch_free.argtypes = [P]
-    for name in ("rsi_batch_create", "rsi_query_batched", "rsi_batch_post", "rsi_batch_stats", "rsi_batch_free"):
+    for name in ("rsi_batch_create", "rsi_batch_launch", "rsi_query_batched", "rsi_batch_post", "rsi_batch_stats",
+                 "rsi_batch_free"):
         getattr(lib, name).restype = ctypes.c_int
     lib.rsi_mlp_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
     lib.rsi_mlp_free.argtypes = [P]
@@ -125,6 +134,8 @@ def _load():
     lib.rsi_mlp_activation.restype = ctypes.c_int
     lib.rsi_mlp_train_step.argtypes = [P, P, P, P, P, i64, ctypes.c_float, i32, ctypes.POINTER(ctypes.c_float), P]
     lib.rsi_mlp_reset_optimizer.argtypes = [P, P]
+    lib.rsi_mlp_attach.argtypes = [P, P]
+    lib.rsi_mlp_attach.restype = ctypes.c_int
     lib.rsi_cluster_labels.argtypes = [P, P, P, i64, P, P]
     lib.rsi_query_learned.argtypes = [P, P, P, P, i64, ctypes.POINTER(Options), P, P, ctypes.POINTER(Stats), P]
     for name in ("rsi_mlp_train_step", "rsi_mlp_reset_optimizer", "rsi_cluster_labels", "rsi_query_learned"):
@@ -292,6 +303,13 @@ class LBVH:
     def handle(self):
         return self._h
 
+    def attach(self, net):
+        """Attach a proposal network (rsi_mlp_attach; None detaches): boolean
+        queries on this hierarchy then go through the learned proposal,
+        with the same answers."""
+        check(lib.rsi_mlp_attach(self._h, net.handle if net is not None else None))
+        self._net = net   # keep the network alive while attached
+
     def info(self) -> dict:
         inf = Info()
         check(lib.lbvh_info(self._h, ctypes.byref(inf)))
@@ -324,6 +342,19 @@ class LBVH:
                                ctypes.byref(opt), ctypes.byref(res), _stream(stream)))
         return res.as_dict()
 
+    def segment_order(self, ray_from, ray_to, out=None, stream=None):
+        """A traversal order for these segments (rsi_segment_order): int32
+        [n] device tensor, a permutation of 0 .. n - 1 by midpoint cell, to
+        pass as query(..., order=...)."""
+        import torch
+        _check_segments(ray_from, ray_to)
+        n = ray_from.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=ray_from.device)
+        _check_out(out, "order", torch.int32, n, ray_from.device)
+        check(lib.rsi_segment_order(self._h, _ptr(ray_from), _ptr(ray_to), n, _ptr(out), _stream(stream)))
+        return out
+
     def last_query_ms(self):
         """(traversal ms, FP64 re-test ms) of the last query run with time_kernels=True."""
         a, b = ctypes.c_float(), ctypes.c_float()
@@ -332,7 +363,7 @@ class LBVH:
 
     def query(self, ray_from, ray_to, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0,
               stats=False, hit=None, count=None, ambiguous=None, want_ambiguous=True, time_kernels=False,
-              ray_sort_tile=0, node_width=0, fp64_all=False, stream=None):
+              ray_sort_tile=0, node_width=0, fp64_all=False, stack=0, order=None, stream=None):
         """Query segments (device tensors [n, 3] float32).  Returns a dict with
         'hit' (uint8, any-hit mode or count > 0), 'count' (int32, count mode),
         'ambiguous' (uint8) and, with stats=True, 'stats'."""
@@ -357,8 +388,10 @@ class LBVH:
         _check_out(hit, "hit", torch.uint8, n, dev)
         _check_out(count, "count", torch.int32, n, dev)
         _check_out(ambiguous, "ambiguous", torch.uint8, n, dev)
+        _check_out(order, "order", torch.int32, n, dev)
         opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), 0, int(time_kernels),
-                      int(ray_sort_tile), int(node_width), int(fp64_all))
+                      int(ray_sort_tile), int(node_width), int(fp64_all), int(stack),
+                      order.data_ptr() if order is not None else None)
         st = Stats()
         check(lib.rsi_query(self._h, _ptr(ray_from), _ptr(ray_to), n, m, ctypes.byref(opt), _ptr(hit), _ptr(count),
                             _ptr(ambiguous), ctypes.byref(st) if stats else None, _stream(stream)))
@@ -492,14 +525,14 @@ def compact_hits(tri, dist, point, stream=None):
 
 class BatchPlan:
     """Many (hierarchy, segments) pairs answered by one graph-launched
-    persistent traversal (rsi_batch_create / rsi_query_batched).
+    persistent traversal (rsi_batch_create / rsi_batch_launch).
 
     items: list of (LBVH, ray_from, ray_to) with device tensors.  Outputs
     are allocated here: .hit / .count / .ambiguous are lists of tensors.
     stream_timeout_ns > 0 makes a streaming plan fed by post()."""
 
     def __init__(self, items, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0, stats=False,
-                 stream_timeout_ns=0, node_width=0, stream=None):
+                 stream_timeout_ns=0, node_width=0, ray_sort_tile=0, stack=0, stream=None):
         import torch
         m = _mode(mode)
         self.mode = m
@@ -518,13 +551,14 @@ class BatchPlan:
             arr[i] = RayBatch(bvh.handle.value, f.data_ptr(), t.data_ptr(), n, h.data_ptr() if h is not None else None,
                               c.data_ptr() if c is not None else None, a.data_ptr())
         timeout = -int(stream_timeout_ns) if stream_timeout_ns else 0
-        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), timeout, 0, 0, int(node_width))
+        opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), timeout, 0, int(ray_sort_tile),
+                      int(node_width), 0, int(stack))
         self._p = ctypes.c_void_p()
         check(lib.rsi_batch_create(arr, len(items), m, ctypes.byref(opt), _stream(stream), ctypes.byref(self._p)))
         self.total = sum(int(f.shape[0]) for _, f, _ in items)
 
     def run(self, stream=None):
-        check(lib.rsi_query_batched(self._p, _stream(stream)))
+        check(lib.rsi_batch_launch(self._p, _stream(stream)))
 
     def post(self, n_ready, stream=None):
         check(lib.rsi_batch_post(self._p, int(n_ready), _stream(stream)))
@@ -546,6 +580,62 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def query_batched(items, mode="any_hit", *, hit=None, count=None, ambiguous=None, fp32_only=False, block=0,
+                  blocks_per_sm=0, node_width=0, stream=None):
+    """The one-call batched query (rsi_query_batched): items is a list of
+    (LBVH, ray_from, ray_to) with device tensors; every segment is answered
+    against its own hierarchy.  Outputs (lists, one tensor per item) are
+    allocated unless given; the library keeps the plan of a call and
+    replays it when the same hierarchies, buffers and options come back.
+    Returns dict(hit=[...] or None, count=[...] or None, ambiguous=[...])."""
+    import torch
+    m = _mode(mode)
+    k = len(items)
+    if k < 1:
+        raise ValueError("query_batched needs at least one item")
+    hit = list(hit) if hit is not None else [None] * k
+    count = list(count) if count is not None else [None] * k
+    ambiguous = list(ambiguous) if ambiguous is not None else [None] * k
+    hs = (ctypes.c_void_p * k)()
+    arr = (RayBatch * k)()
+    for i, (bvh, f, t) in enumerate(items):
+        _check_segments(f, t)
+        n = f.shape[0]
+        if m == RSI_ANY_HIT and hit[i] is None:
+            hit[i] = torch.empty(n, dtype=torch.uint8, device=f.device)
+        if m == RSI_COUNT and count[i] is None:
+            count[i] = torch.empty(n, dtype=torch.int32, device=f.device)
+        if ambiguous[i] is None:
+            ambiguous[i] = torch.empty(n, dtype=torch.uint8, device=f.device)
+        _check_out(hit[i], "hit", torch.uint8, n, f.device)
+        _check_out(count[i], "count", torch.int32, n, f.device)
+        _check_out(ambiguous[i], "ambiguous", torch.uint8, n, f.device)
+        hs[i] = bvh.handle.value
+        arr[i] = RayBatch(None, f.data_ptr(), t.data_ptr(), n, *(x.data_ptr() if x is not None else None
+                                                                 for x in (hit[i], count[i], ambiguous[i])))
+    opt = Options(int(fp32_only), int(block), int(blocks_per_sm), 0, 0, 0, 0, int(node_width))
+    check(lib.rsi_query_batched(hs, k, arr, m, ctypes.byref(opt), _stream(stream)))
+    return {"hit": hit if m == RSI_ANY_HIT else None, "count": count if m == RSI_COUNT else None,
+            "ambiguous": ambiguous}
+
+
+def batch_autotune(items, mode="any_hit", cache_path=None, stream=None) -> dict:
+    """Tune batched plans of these (LBVH, ray_from, ray_to) items
+    (rsi_batch_autotune): threads per block, blocks per SM, node width,
+    in-tile reordering and stack size, timed on a sample of every batch.
+    The result's block / blocks_per_sm / node_width / ray_sort_tile / stack
+    can be passed straight to BatchPlan."""
+    m = _mode(mode)
+    arr = (RayBatch * len(items))()
+    for i, (bvh, f, t) in enumerate(items):
+        _check_segments(f, t)
+        arr[i] = RayBatch(bvh.handle.value, f.data_ptr(), t.data_ptr(), f.shape[0], None, None, None)
+    opt, res = Options(), Tuning()
+    path = cache_path.encode() if cache_path else None
+    check(lib.rsi_batch_autotune(arr, len(items), m, path, ctypes.byref(opt), ctypes.byref(res), _stream(stream)))
+    return res.as_dict()
 
 
 MLP_SHAPES = (("W1", (16, 128)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (128, 256)),
@@ -695,8 +785,8 @@ def query_learned(bvh, net, ray_from, ray_to, stats=False, hit=None, ambiguous=N
 
 
 def activation(z, stream=None):
-    """(erf by the network's approximation, CUDA erff, GELU) of a device
-    float32 vector (rsi_mlp_activation)."""
+    """(tanh by the hardware approximation inference uses, CUDA tanhf, GELU
+    as inference applies it) of a device float32 vector (rsi_mlp_activation)."""
     import torch
     if not isinstance(z, torch.Tensor) or not z.is_cuda or z.dtype != torch.float32 or not z.is_contiguous():
         raise TypeError("z must be a contiguous float32 device tensor")

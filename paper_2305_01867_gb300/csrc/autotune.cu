@@ -1,10 +1,12 @@
 // autotune.cu -- picks the launch shape of the traversal (threads per block,
 // resident blocks per SM), the node width it fetches (child-pair,
-// compressed child-pair or four-wide) and the in-tile segment reordering of a query by
-// timing candidates on a sample of its own segments with CUDA events, and
-// reports the traversal stack the tree needs (the smallest of 32 / 64 / 128
-// entries that holds the chosen walk's worst case).  Choices are cached in a JSON file keyed
-// by device, mode and the sizes of the problem (log2 buckets).
+// compressed child-pair or four-wide) and the in-tile segment reordering of
+// a query by timing candidates on a sample of its own segments with CUDA
+// events, and reports the traversal stack the tree needs (the smallest of
+// 32 / 64 / 128 entries that holds the chosen walk's worst case).  For
+// batched plans it also times the stack size (that bucket or the next).
+// Choices are cached in a JSON file keyed by device, mode and the sizes of
+// the problem (log2 buckets).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -199,6 +201,148 @@ extern "C" int rsi_autotune(rsi_bvh_t h, const float* d_from, const float* d_to,
     inout->ray_sort_tile = best.tile;
     inout->node_width = best.width;
     best.stack = stack_for(best.width);
+    inout->stack = best.stack;
+    if (result) {
+        result->block = best.block;
+        result->blocks_per_sm = best.bps;
+        result->ray_sort_tile = best.tile;
+        result->stack = best.stack;
+        result->ms = best.ms;
+        result->from_cache = from_cache;
+        result->candidates = candidates;
+        result->node_width = best.width;
+    }
+    return RSI_OK;
+}
+
+// ---------------------------------------------------------------- batched plans
+extern "C" int rsi_batch_autotune(const rsi_ray_batch* batches, int n_batches, int mode, const char* cache_path,
+                                  rsi_options* inout, rsi_tuning* result, void* stream) {
+    if (!batches || n_batches < 1 || !inout || (mode != RSI_ANY_HIT && mode != RSI_COUNT))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_autotune: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t tri = 0, rays = 0;
+    int height = 0;
+    for (int i = 0; i < n_batches; ++i) {
+        if (!batches[i].bvh || batches[i].n_rays < 0)
+            return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_autotune: batch " + std::to_string(i) + " is malformed");
+        tri += batches[i].bvh->n_tri;
+        rays += batches[i].n_rays;
+        height = std::max(height, batches[i].bvh->height);
+    }
+    auto stack_need = [&](int width) { return width == 4 ? 3 * ((height + 2) / 2) : height + 1; };
+    auto bucket = [](int need) { return need <= 32 ? 32 : (need <= 64 ? 64 : 128); };
+    const bool wide_ok = 3 * ((height + 2) / 2) <= 128;
+    std::ostringstream kk;
+    kk << tuning_key(mode, tri, rays) << "|batched" << n_batches;
+    const std::string key = kk.str();
+    auto cache = read_cache(cache_path);
+    auto it = cache.find(key);
+    Choice best;
+    best.bps = 3;
+    int candidates = 0, from_cache = 0;
+    if (it != cache.end()) {
+        best.block = field(it->second, "block", 256);
+        best.bps = field(it->second, "blocks_per_sm", 3);
+        best.tile = field(it->second, "ray_sort_tile", 0);
+        best.width = field(it->second, "node_width", 2);
+        best.stack = field(it->second, "stack", 0);
+        if (best.width == 4 && !wide_ok) best.width = 2;
+        if (best.stack < bucket(stack_need(best.width))) best.stack = bucket(stack_need(best.width));
+        from_cache = 1;
+    } else {
+        // a sample plan: every batch cut to its first 2^17 segments, outputs in scratch
+        const int64_t cut = (int64_t)1 << 17;
+        std::vector<rsi_ray_batch> sample(batches, batches + n_batches);
+        int64_t total = 0;
+        for (auto& b : sample) {
+            b.n_rays = std::min<int64_t>(b.n_rays, cut);
+            total += b.n_rays;
+        }
+        // outputs: hit bytes, ambiguity bytes, then the int32 counts from a
+        // 256-byte boundary (2 * total bytes need not be a multiple of 4)
+        char* out = nullptr;
+        const size_t count_off = ((size_t)2 * (size_t)total + 255) & ~(size_t)255;
+        if (rsi::dev_malloc(&out, count_off + 4 * (size_t)std::max<int64_t>(total, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return rsi::fail(RSI_ERR_OOM, "rsi_batch_autotune: sample outputs");
+        }
+        int64_t off = 0;
+        for (auto& b : sample) {
+            b.d_hit = reinterpret_cast<uint8_t*>(out) + off;
+            b.d_ambiguous = reinterpret_cast<uint8_t*>(out) + total + off;
+            b.d_count = reinterpret_cast<int32_t*>(out + count_off) + off;
+            off += b.n_rays;
+        }
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const int shapes[][2] = {{256, 3}, {256, 2}, {256, 4}, {128, 6}, {128, 8}};
+        const int widths[] = {2, 4};
+        const int tiles[] = {0, 8192};
+        float best_ms = INFINITY;
+        int rc = RSI_OK;
+        for (const auto& sh : shapes) {
+            for (int width : widths) {
+                if (width == 4 && !wide_ok) continue;
+                const int st0 = bucket(stack_need(width));
+                for (int stack : {st0, std::min(2 * st0, 128)}) {
+                    if (stack != st0 && st0 == 128) continue;
+                    for (int tile : tiles) {
+                        rsi_options o = *inout;
+                        o.block = sh[0];
+                        o.blocks_per_sm = sh[1];
+                        o.node_width = width;
+                        o.ray_sort_tile = tile;
+                        o.stack = stack;
+                        o.timeout_ns = 0;
+                        o.collect_stats = 0;
+                        rsi_batch_t plan = nullptr;
+                        rc = rsi_batch_create(sample.data(), n_batches, mode, &o, stream, &plan);
+                        if (rc != RSI_OK) break;
+                        float total_ms = 0.0f;
+                        for (int rep = 0; rep < 4 && rc == RSI_OK; ++rep) {
+                            cudaEventRecord(e0, s);
+                            rc = rsi_batch_launch(plan, stream);
+                            cudaEventRecord(e1, s);
+                            cudaEventSynchronize(e1);
+                            float ms = 0.0f;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            if (rep > 0) total_ms += ms;   // the first launch warms up
+                        }
+                        rsi_batch_free(plan);
+                        if (rc != RSI_OK) break;
+                        ++candidates;
+                        const float ms = total_ms / 3.0f;
+                        if (ms < best_ms) {
+                            best_ms = ms;
+                            best.block = sh[0];
+                            best.bps = sh[1];
+                            best.width = width;
+                            best.tile = tile;
+                            best.stack = stack;
+                            best.ms = ms;
+                        }
+                    }
+                    if (rc != RSI_OK) break;
+                }
+                if (rc != RSI_OK) break;
+            }
+            if (rc != RSI_OK) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(out);
+        if (rc != RSI_OK) return rc;
+        cache[key] = encode(best);
+        if (!write_cache(cache_path, cache))
+            return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_autotune: cannot write cache");
+    }
+    inout->block = best.block;
+    inout->blocks_per_sm = best.bps;
+    inout->ray_sort_tile = best.tile;
+    inout->node_width = best.width;
+    inout->stack = best.stack;
     if (result) {
         result->block = best.block;
         result->blocks_per_sm = best.bps;

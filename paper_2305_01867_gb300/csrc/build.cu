@@ -837,6 +837,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 rsi_bvh_s* alloc_handle(int64_t nv, int64_t nt, int morton_bits, bool sort_scratch, cudaStream_t s, char** base_out,
                         int32_t** hgt, int32_t** flag, char** scratch) {
     rsi_bvh_s* h = new rsi_bvh_s();
+    h->gen = next_handle_gen();
     h->n_tri = nt;
     h->n_vert = nv;
     h->morton_bits = morton_bits;
@@ -1149,9 +1150,11 @@ extern "C" int lbvh_build_host(const float* h_vertices, int64_t n_vertices, cons
 extern "C" int lbvh_free(rsi_bvh_t h) {
     if (!h) return RSI_OK;
     cudaDeviceSynchronize();
+    rsi::forget_handle(h);         // detach its network, drop the batched plans that name it
     rsi::pool_free(h->nodes, 0);   // base of the single allocation
     rsi::pool_free(h->band_ids, 0);
     rsi::pool_free(h->pair_mem, 0);
+    rsi::pool_free(h->order_hist, 0);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     delete h;

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "rsi_internal.cuh"
 
@@ -79,6 +81,51 @@ int pool_alloc(void** p, size_t bytes, cudaStream_t s) {
 
 void pool_free(void* p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
+}
+
+static std::atomic<uint64_t> g_gen{0};
+
+uint64_t next_handle_gen() { return ++g_gen; }
+
+static std::mutex g_attach_mu;
+static std::vector<std::pair<rsi_bvh_t, rsi_mlp_s*>> g_attach;   // (hierarchy, network)
+
+void attach_mlp(rsi_bvh_t h, rsi_mlp_s* m) {
+    std::lock_guard<std::mutex> lock(g_attach_mu);
+    for (size_t i = 0; i < g_attach.size(); ++i) {
+        if (g_attach[i].first == h) {
+            g_attach.erase(g_attach.begin() + (long)i);
+            break;
+        }
+    }
+    h->mlp = m;
+    if (m) g_attach.emplace_back(h, m);
+}
+
+void forget_handle(rsi_bvh_t h) {
+    {
+        std::lock_guard<std::mutex> lock(g_attach_mu);
+        for (size_t i = 0; i < g_attach.size(); ++i) {
+            if (g_attach[i].first == h) {
+                g_attach.erase(g_attach.begin() + (long)i);
+                break;
+            }
+        }
+        h->mlp = nullptr;
+    }
+    drop_plans_of(h->gen);
+}
+
+void forget_mlp(rsi_mlp_s* m) {
+    std::lock_guard<std::mutex> lock(g_attach_mu);
+    for (size_t i = 0; i < g_attach.size();) {
+        if (g_attach[i].second == m) {
+            g_attach[i].first->mlp = nullptr;
+            g_attach.erase(g_attach.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
 }
 
 int device_sm_count() {

@@ -5,13 +5,18 @@
 // on top of the method; the fallback is the paper's full tree search, so
 // answers stay exactly those of the plain query.)
 //
-//  k_mlp_forward_tc  inference on the 5th-generation tensor cores: per tile
-//                    of 128 segments three tcgen05.mma chains (K = 16, 128,
-//                    128; N = 128, 128, 256) with FP32 accumulators in TMEM,
-//                    operands in shared memory in the no-swizzle K-major
-//                    core-matrix layout (8 rows x 16 bytes per core matrix),
-//                    bias + GELU + BF16 rounding in the TMEM->register
-//                    epilogue, top-4 cluster selection at the end.
+//  k_mlp_tc<VERIFY>  persistent inference on the 5th-generation tensor
+//                    cores: per tile of 128 segments three tcgen05.mma
+//                    chains (K = 16, 128, 128; N = 128, 128, 256) with FP32
+//                    accumulators in TMEM, operands in shared memory in the
+//                    no-swizzle K-major core-matrix layout; two tile groups
+//                    alternate so that one group's TMEM->register epilogue
+//                    (bias, GELU, BF16 rounding, top-4 cluster selection)
+//                    runs while the other group's chains run.  With VERIFY
+//                    the top-4 never leave registers: the proposed clusters'
+//                    triangles are tested in the same kernel and the
+//                    segments they do not settle are listed for the tree
+//                    search.
 //  training          FP32 SIMT kernels (tiled GEMMs, fused elementwise
 //                    steps, Adam) on the same BF16 roundings; the network is
 //                    small and training is a one-off set-up cost.
@@ -25,6 +30,7 @@
 #include <vector>
 
 #include "rsi_internal.cuh"
+#include "segtest.cuh"
 
 namespace rsi {
 namespace mlpk {
@@ -46,20 +52,32 @@ __host__ __device__ constexpr uint32_t cm_offset(int row, int k, int K) {
     return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula
-// 7.1.26: erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2), t = 1 / (1 + p x),
-// x >= 0, |error| <= 1.5e-7 (far below the BF16 resolution of the layer
-// outputs); odd extension for x < 0.
-__device__ __forceinline__ float erf_as(float x) {
-    const float ax = fabsf(x);
-    const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.0f));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    return copysignf(1.0f - poly * __expf(-ax * ax), x);
+// GELU in its tanh form (Hendrycks & Gimpel 2016, "Gaussian Error Linear
+// Units"): GELU(z) = 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
+// Inference evaluates tanh with the hardware approximation tanh.approx.f32
+// (one special-function instruction; its error stays below 2^-10.5 of the
+// result, far below the BF16 resolution of the layer outputs except at
+// rounding boundaries); training evaluates it with CUDA's tanhf and
+// differentiates the same formula.
+constexpr float kG0 = 0.7978845608028654f;     // sqrt(2 / pi)
+constexpr float kG1 = 0.035677408136300125f;   // 0.044715 sqrt(2 / pi)
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_fast(float z) {
+    const float h = 0.5f * z;
+    return fmaf(h, tanh_fast(z * fmaf(kG1, z * z, kG0)), h);
+}
+__device__ __forceinline__ float gelu(float z) {
+    const float h = 0.5f * z;
+    return fmaf(h, tanhf(z * fmaf(kG1, z * z, kG0)), h);
+}
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * __expf(-0.5f * z * z) * 0.3989422804014327f;
+    const float z2 = z * z;
+    const float t = tanhf(z * fmaf(kG1, z2, kG0));
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * fmaf(3.0f * kG1, z2, kG0);
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -153,90 +171,156 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Hidden-layer epilogue of one 32-column slice c of this thread's row:
-// + bias -> GELU -> BF16 -> the row of the next layer's K-major A operand.
-__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* __restrict__ bias, uint8_t* sA, int row,
-                                                int c) {
-    {
-        float v[32];
-        tmem_ld32(taddr + 32 * c, v);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint4 w;
-            const int k0 = 32 * c + 8 * q;
-            w.x = pack_bf16x2(gelu(v[8 * q + 0] + bias[k0 + 0]), gelu(v[8 * q + 1] + bias[k0 + 1]));
-            w.y = pack_bf16x2(gelu(v[8 * q + 2] + bias[k0 + 2]), gelu(v[8 * q + 3] + bias[k0 + 3]));
-            w.z = pack_bf16x2(gelu(v[8 * q + 4] + bias[k0 + 4]), gelu(v[8 * q + 5] + bias[k0 + 5]));
-            w.w = pack_bf16x2(gelu(v[8 * q + 6] + bias[k0 + 6]), gelu(v[8 * q + 7] + bias[k0 + 7]));
-            *reinterpret_cast<uint4*>(sA + cm_offset(row, k0, kH)) = w;
-        }
-    }
-}
-
-// Shared memory map of the forward kernel (bytes from a 1024-aligned base).
-constexpr int kSmX = kImgBytes;                 // [128 x 16] features
-constexpr int kSmH = kSmX + 128 * kIn * 2;       // [128 x 128] hidden activations
-constexpr int kSmBias = kSmH + 128 * kH * 2;     // 512 floats
-constexpr int kSmTop = kSmBias + 512 * 4;        // [4 column groups][128 rows][4] top-4 keys
-constexpr int kSmBar = kSmTop + 4 * 128 * 4 * 4; // mbarrier + TMEM address + flags
+// Shared memory map of the tensor-core kernel (bytes from a 1024-aligned
+// base): the weight images, then per tile group its layer inputs, the
+// biases, the top-4 exchange between the two column halves of a row and
+// their verification flags, the mbarriers and the TMEM address.
+constexpr int kXBytes = 128 * kIn * 2;          // [128 x 16] BF16 features of one tile
+constexpr int kHBytes = 128 * kH * 2;           // [128 x 128] BF16 hidden activations
+constexpr int kSmX = kImgBytes;                 // group g: kSmX + g kXBytes
+constexpr int kSmH = kSmX + 2 * kXBytes;        // group g: kSmH + g kHBytes
+constexpr int kSmBias = kSmH + 2 * kHBytes;     // 512 floats
+constexpr int kSmXchg = kSmBias + 512 * 4;      // [group][half][row] 4 keys
+// verification, per group: the rows' segments (start, direction, |d|_1),
+// proposed clusters, hit flags, the list of rows left after the best
+// cluster and its length
+constexpr int kVerBytes = 128 * 32 + 128 * 4 + 128 * 4 + 128 * 4 + 16;
+constexpr int kSmVer = kSmXchg + 2 * 2 * 128 * 16;
+constexpr int kSmBar = kSmVer + 2 * kVerBytes;   // bar_in[2], bar_mma[2], bar_x[2], TMEM address
 constexpr int kSmBytes = kSmBar + 64;
 constexpr int kTmemCols = 512;
-constexpr int kFwdThreads = 512;                 // 16 warps: 4 lane quarters x 4 column groups
+// 16 warps: two tile groups of 8 (4 TMEM lane quarters x 2 column halves);
+// lane 0 of each group's first warp issues that group's tensor-core chains.
+constexpr int kTcThreads = 16 * 32;
 
-struct FwdArgs {
+struct TcArgs {
     const uint8_t* img;    // BF16 weight images
     const float* bias;     // b1 | b2 | b3
     const float* from;
     const float* to;
     int n;
     float lo0, lo1, lo2, sc0, sc1, sc2;   // feature map: (p - lo) * sc - 1
+    int* err;              // RSI_ERR_TIMEOUT if a wait ran out
+    // inference outputs (rsi_mlp_forward)
     float* logits;         // [n][256] or NULL
     uint8_t* top4;         // [n][4] or NULL (cluster ids, best first)
-    int* err;              // RSI_ERR_TIMEOUT if a tensor-core wait ran out
+    // verification (the learned query)
+    const Tri* tris;
+    int n_tri;
+    int cluster_max;       // triangles of the largest cluster: ceil(n_tri / 256)
+    float dmax0, dmax1, dmax2;
+    uint8_t* hit;
+    uint8_t* amb;
+    int32_t* order;        // segments left to the tree search
+    DevCounters* ctr;      // n_fallback, n_confirmed, tri_tests
+    int stats;
 };
 
-// Top-4 selection on 32-bit keys: the order-preserving bits of the logit
-// with its low 8 bits replaced by 255 - cluster, so a larger key is a larger
-// logit (compared to 24 significant bits) and equal logits rank the lower
-// cluster first.  Insertion keeps t0 >= t1 >= t2 >= t3 with min/max only.
-__device__ __forceinline__ uint32_t logit_key(float z, int cluster) {
-    const uint32_t b = __float_as_uint(z);
-    const uint32_t o = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-    return (o & 0xFFFFFF00u) | (uint32_t)(255 - cluster);
+// Top-4 selection keys: the FP32 logit with its low 8 bits replaced by
+// 255 - cluster, compared as floats.  Logits are thereby compared to 24
+// significant bits, no two keys of a row are equal, and on equal 24-bit
+// prefixes the lower cluster ranks first for a positive logit (the higher
+// for a negative one).  The insertion keeps t0 >= t1 >= t2 >= t3.
+__device__ __forceinline__ float logit_key(float z, int cluster) {
+    return __uint_as_float((__float_as_uint(z) & 0xFFFFFF00u) | (uint32_t)(255 - cluster));
 }
-__device__ __forceinline__ void top4_insert(uint32_t k, uint32_t t[4]) {
-    t[3] = max(t[3], k);
-    uint32_t lo = min(t[2], t[3]);
-    t[2] = max(t[2], t[3]);
-    t[3] = lo;
-    lo = min(t[1], t[2]);
-    t[1] = max(t[1], t[2]);
-    t[2] = lo;
-    lo = min(t[0], t[1]);
-    t[0] = max(t[0], t[1]);
-    t[1] = lo;
+__device__ __forceinline__ int key_cluster(float k) { return 255 - (int)(__float_as_uint(k) & 255u); }
+__device__ __forceinline__ void top4_insert(float k, float t[4]) {
+    const float m0 = fminf(t[0], k), m1 = fminf(t[1], k), m2 = fminf(t[2], k);
+    t[3] = fmaxf(t[3], m2);
+    t[2] = fmaxf(t[2], m1);
+    t[1] = fmaxf(t[1], m0);
+    t[0] = fmaxf(t[0], k);
 }
 
-// 16 warps per CTA: warp w reads TMEM lanes 32 (w % 4) .. +31 (tile rows) and
-// column group w / 4, so every epilogue is split four ways by columns; the
-// four partial top-4 lists of a row are merged through shared memory.
-__global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_forward_tc(FwdArgs P) {
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Two 32-column TMEM loads of this thread's lane, one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64]) {
+    uint32_t r[64];
+    __syncwarp();
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr + 32));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Hidden-layer epilogue of this thread's 64 columns c0 .. c0 + 63 of its
+// row: + bias -> GELU -> BF16 -> the next layer's K-major A operand.
+__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* __restrict__ bias, uint8_t* sH, int row,
+                                                int c0) {
+    float v[64];
+    tmem_ld64(taddr + c0, v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int k0 = c0 + 8 * q;
+        uint4 w;
+        w.x = pack_bf16x2(gelu_fast(v[8 * q + 0] + bias[k0 + 0]), gelu_fast(v[8 * q + 1] + bias[k0 + 1]));
+        w.y = pack_bf16x2(gelu_fast(v[8 * q + 2] + bias[k0 + 2]), gelu_fast(v[8 * q + 3] + bias[k0 + 3]));
+        w.z = pack_bf16x2(gelu_fast(v[8 * q + 4] + bias[k0 + 4]), gelu_fast(v[8 * q + 5] + bias[k0 + 5]));
+        w.w = pack_bf16x2(gelu_fast(v[8 * q + 6] + bias[k0 + 6]), gelu_fast(v[8 * q + 7] + bias[k0 + 7]));
+        *reinterpret_cast<uint4*>(sH + cm_offset(row, k0, kH)) = w;
+    }
+}
+
+// Persistent tensor-core kernel of the proposal network, one CTA per SM.
+//
+// Two tile groups of 8 warps each work on alternate 128-segment tiles so
+// that one group's SIMT epilogue (bias, GELU, BF16 packing, top-4, proposal
+// verification) overlaps the other group's tensor-core chains.  Group g owns
+// TMEM columns 256 g .. 256 g + 255: layer 1 accumulates into the first 128,
+// layer 2 into the second 128, layer 3 (N = 256) into all of them once the
+// layer-2 epilogue has read its accumulator.  Per layer, the group's warps
+// arrive on bar_in[g] when the layer's A operand is in shared memory; the
+// group's issuing thread waits for all eight, issues the chain and commits
+// it to bar_mma[g], on which the group waits.  The two groups issue
+// independently; the tensor cores interleave their chains.  Every wait is
+// bounded (about 2 s: RSI_ERR_TIMEOUT, then the kernel leaves its loops,
+// waits for its last commit and frees TMEM).
+//
+// VERIFY = false: logits and top-4 cluster ids are written (rsi_mlp_forward).
+// VERIFY = true: the top-4 stay in registers; the row's two column halves
+// each test the triangles of two of the proposed clusters in FP32; a
+// certain decisive hit settles the segment (hit = 1, not ambiguous), every
+// other segment is appended to `order` for the tree search.
+template <bool VERIFY>
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(TcArgs P) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, cg = warp >> 2;
-    const int row = quarter * 32 + lane;   // tile row of this thread in every epilogue
     float* sBias = reinterpret_cast<float*>(sm + kSmBias);
-    uint32_t* sTop = reinterpret_cast<uint32_t*>(sm + kSmTop);   // [4 groups][128 rows][4] keys
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + kSmBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSmBar + 8);
-    int* s_ok = reinterpret_cast<int*>(sm + kSmBar + 20);
+    const uint32_t bar0 = smem_addr(sm + kSmBar);   // bar_in[0..1], bar_mma[0..1], bar_x[0..1]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSmBar + 48);
 
-    for (int i = tid; i < kImgBytes / 16; i += kFwdThreads)
+    for (int i = tid; i < kImgBytes / 16; i += kTcThreads)
         reinterpret_cast<uint4*>(sm)[i] = reinterpret_cast<const uint4*>(P.img)[i];
-    for (int i = tid; i < 512; i += kFwdThreads) sBias[i] = P.bias[i];
+    for (int i = tid; i < 512; i += kTcThreads) sBias[i] = P.bias[i];
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+        mbar_init(bar0, 8);   // bar_in: one arrival per warp of the group
+        mbar_init(bar0 + 8, 8);
+        mbar_init(bar0 + 16, 1);
+        mbar_init(bar0 + 24, 1);
+        mbar_init(bar0 + 32, 8);
+        mbar_init(bar0 + 40, 8);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -250,128 +334,235 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_forward_tc(FwdArgs P) {
     __syncthreads();
     fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;   // this warp's TMEM lanes
-    const uint32_t bar = smem_addr(mbar);
-    const uint32_t aX = smem_addr(sm + kSmX), aH = smem_addr(sm + kSmH);
-    const uint32_t aW1 = smem_addr(sm + kImgW1), aW2 = smem_addr(sm + kImgW2), aW3 = smem_addr(sm + kImgW3);
-    const float lo[3] = {P.lo0, P.lo1, P.lo2}, sc[3] = {P.sc0, P.sc1, P.sc2};
-    uint32_t phase = 0;
-
-    // one elected thread issues a chain and waits for it; the others learn
-    // the outcome through the barrier
-    auto run_chain = [&](int layer) -> bool {
-        if (tid == 0) {
-            fence_after();
-            if (layer == 1) {
-                mma_bf16(tbase, smem_desc(aX, 128, kIn * 16), smem_desc(aW1, 128, kIn * 16), idesc_bf16(128, kH), 0);
-            } else if (layer == 2) {
-                for (int ks = 0; ks < kH / 16; ++ks)
-                    mma_bf16(tbase + 256, smem_desc(aH + 256 * ks, 128, kH * 16), smem_desc(aW2 + 256 * ks, 128, kH * 16),
-                             idesc_bf16(128, kH), ks > 0);
-            } else {
-                for (int ks = 0; ks < kH / 16; ++ks)
-                    mma_bf16(tbase, smem_desc(aH + 256 * ks, 128, kH * 16), smem_desc(aW3 + 256 * ks, 128, kH * 16),
-                             idesc_bf16(128, kOut), ks > 0);
-            }
-            mma_commit(bar);
-            const bool ok = mbar_wait(bar, phase);
-            *s_ok = ok ? 1 : 0;
-            if (!ok) atomicCAS(P.err, 0, RSI_ERR_TIMEOUT);
-            fence_before();
-        }
-        phase ^= 1u;
-        __syncthreads();
-        fence_after();
-        return *s_ok != 0;
-    };
-
-    // static schedule: tile = blockIdx.x + k gridDim.x; the segments of the
-    // next tile are loaded into registers while this one is processed
     const int64_t n_tiles = ((int64_t)P.n + 127) / 128;
-    float seg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    auto load_seg = [&](int64_t t) {
-        const int64_t r = t * 128 + tid;
-        if (tid < 128 && t < n_tiles && r < P.n) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                seg[a] = __ldg(P.from + 3 * r + a);
-                seg[3 + a] = __ldg(P.to + 3 * r + a);
-            }
-        }
-    };
-    load_seg(blockIdx.x);
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        if (tid < 128) {
-            const int64_t r = tile * 128 + tid;
-            float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (r < P.n) {
+    const int64_t G = gridDim.x;
+
+    const uint32_t aW1 = smem_addr(sm + kImgW1), aW2 = smem_addr(sm + kImgW2), aW3 = smem_addr(sm + kImgW3);
+    {
+        // ---------------------------------------------------------------- tile groups
+        const int g = warp >> 3, q = warp & 3, half = (warp >> 2) & 1;
+        const bool issuer = (warp & 7) == 0 && lane == 0;
+        const uint32_t aX = smem_addr(sm + kSmX + g * kXBytes), aH = smem_addr(sm + kSmH + g * kHBytes);
+        const uint32_t dcol = tbase + 256u * (uint32_t)g;
+        uint32_t pin = 0, issued = 0;
+        const int row = 32 * q + lane;
+        uint8_t* sX = sm + kSmX + g * kXBytes;
+        uint8_t* sH = sm + kSmH + g * kHBytes;
+        float4* sXchg = reinterpret_cast<float4*>(sm + kSmXchg);
+        uint8_t* sVer = sm + kSmVer + g * kVerBytes;
+        float4* sSeg = reinterpret_cast<float4*>(sVer);                       // [row][2]: s | dl1, d
+        uchar4* sCl = reinterpret_cast<uchar4*>(sVer + 128 * 32);              // [row] proposed clusters
+        int* sHit = reinterpret_cast<int*>(sVer + 128 * 32 + 512);             // [row] -1 none, 0 open, 1 hit
+        int* sList = reinterpret_cast<int*>(sVer + 128 * 32 + 1024);           // rows left after cluster 0
+        int* sLeft = reinterpret_cast<int*>(sVer + 128 * 32 + 1536);           // their number
+        const int tg = (warp & 7) * 32 + lane;                                 // thread in the group
+        const uint32_t bar_in = bar0 + 8 * g, bar_mma = bar0 + 16 + 8 * g, bar_x = bar0 + 32 + 8 * g;
+        const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16) + 256u * (uint32_t)g;
+        const float lo[3] = {P.lo0, P.lo1, P.lo2}, sc[3] = {P.sc0, P.sc1, P.sc2};
+        uint32_t ph = 0, px = 0;
+        int64_t confirmed_n = 0, tests = 0;
+        float nxt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        auto load_seg = [&](int64_t t) {
+            const int64_t r = t * 128 + row;
+            if (t < n_tiles && r < P.n) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    f[a] = fminf(fmaxf((seg[a] - lo[a]) * sc[a] - 1.0f, -4.0f), 4.0f);
-                    f[3 + a] = fminf(fmaxf((seg[3 + a] - lo[a]) * sc[a] - 1.0f, -4.0f), 4.0f);
+                    nxt[a] = __ldg(P.from + 3 * r + a);
+                    nxt[3 + a] = __ldg(P.to + 3 * r + a);
                 }
             }
-            uint4 w0;
-            w0.x = pack_bf16x2(f[0], f[1]);
-            w0.y = pack_bf16x2(f[2], f[3]);
-            w0.z = pack_bf16x2(f[4], f[5]);
-            w0.w = 0u;
-            *reinterpret_cast<uint4*>(sm + kSmX + cm_offset(tid, 0, kIn)) = w0;
-            *reinterpret_cast<uint4*>(sm + kSmX + cm_offset(tid, 8, kIn)) = make_uint4(0u, 0u, 0u, 0u);
-        }
-        load_seg(tile + gridDim.x);
-        fence_proxy_async();
-        __syncthreads();
-        if (!run_chain(1)) break;
-        epilogue_hidden(tbase + lane_off, sBias, sm + kSmH, row, cg);
-        fence_proxy_async();
-        fence_before();
-        __syncthreads();
-        if (!run_chain(2)) break;
-        epilogue_hidden(tbase + lane_off + 256, sBias + kH, sm + kSmH, row, cg);
-        fence_proxy_async();
-        fence_before();
-        __syncthreads();
-        if (!run_chain(3)) break;
-        const int64_t r = tile * 128 + row;
-        uint32_t ta[4] = {0u, 0u, 0u, 0u}, tb[4] = {0u, 0u, 0u, 0u};   // two streams for ILP
+        };
+        // waits are decided per warp (__all_sync), so that a warp leaves its
+        // loop as a whole and its lanes keep meeting the same warp-wide steps
+        auto wait_mma = [&]() -> bool {
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_mma, ph));
+            ph ^= 1u;
+            if (!ok) atomicCAS(P.err, 0, RSI_ERR_TIMEOUT);
+            fence_after();
+            return ok;
+        };
+        // the layer's A operand is in shared memory: arrive; the issuing
+        // thread waits for the group's eight warps and issues the chain
+        auto arrive_in = [&](int layer) {
+            fence_proxy_async();   // generic-proxy writes of the operand -> visible to the tensor cores
+            fence_before();        // this thread's TMEM reads are complete
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_in);
+            if (issuer) {
+                const bool ok = mbar_wait(bar_in, pin);
+                pin ^= 1u;
+                if (!ok) {
+                    atomicCAS(P.err, 0, RSI_ERR_TIMEOUT);
+                    return;   // nothing issued: the group's wait for this chain runs out
+                }
+                fence_after();
+                if (layer == 0) {
+                    mma_bf16(dcol, smem_desc(aX, 128, kIn * 16), smem_desc(aW1, 128, kIn * 16), idesc_bf16(128, kH), 0);
+                } else if (layer == 1) {
+                    for (int ks = 0; ks < kH / 16; ++ks)
+                        mma_bf16(dcol + 128, smem_desc(aH + 256 * ks, 128, kH * 16),
+                                 smem_desc(aW2 + 256 * ks, 128, kH * 16), idesc_bf16(128, kH), ks > 0);
+                } else {
+                    for (int ks = 0; ks < kH / 16; ++ks)
+                        mma_bf16(dcol, smem_desc(aH + 256 * ks, 128, kH * 16), smem_desc(aW3 + 256 * ks, 128, kH * 16),
+                                 idesc_bf16(128, kOut), ks > 0);
+                }
+                mma_commit(bar_mma);
+                ++issued;
+            }
+        };
+        // the two column halves of a row exchange through shared memory
+        auto xchg_sync = [&]() -> bool {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_x);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_x, px));
+            px ^= 1u;
+            if (!ok) atomicCAS(P.err, 0, RSI_ERR_TIMEOUT);
+            return ok;
+        };
+        int64_t tile = blockIdx.x + G * g;
+        load_seg(tile);
+        for (; tile < n_tiles; tile += 2 * G) {
+            const int64_t r = tile * 128 + row;
+            const bool valid = r < P.n;
+            float seg[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) seg[a] = nxt[a];
+            load_seg(tile + 2 * G);   // the next tile's segment, in flight during this tile
+            if (half == 0) {
+                float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (valid) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        f[a] = fminf(fmaxf((seg[a] - lo[a]) * sc[a] - 1.0f, -4.0f), 4.0f);
+                        f[3 + a] = fminf(fmaxf((seg[3 + a] - lo[a]) * sc[a] - 1.0f, -4.0f), 4.0f);
+                    }
+                }
+                uint4 w0;
+                w0.x = pack_bf16x2(f[0], f[1]);
+                w0.y = pack_bf16x2(f[2], f[3]);
+                w0.z = pack_bf16x2(f[4], f[5]);
+                w0.w = 0u;
+                *reinterpret_cast<uint4*>(sX + cm_offset(row, 0, kIn)) = w0;
+                *reinterpret_cast<uint4*>(sX + cm_offset(row, 8, kIn)) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            arrive_in(0);
+            if (!wait_mma()) break;
+            epilogue_hidden(tl, sBias, sH, row, 64 * half);
+            arrive_in(1);
+            if (!wait_mma()) break;
+            epilogue_hidden(tl + 128, sBias + kH, sH, row, 64 * half);
+            arrive_in(2);
+            if (!wait_mma()) break;
+            // logits of this half (128 columns): bias, keys, top-4
+            float t4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
 #pragma unroll 1
-        for (int c = 2 * cg; c < 2 * cg + 2; ++c) {   // this warp's 64 logits of the row
-            float v[32];
-            tmem_ld32(tbase + lane_off + 32 * c, v);
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c0 = 128 * half + 64 * cc;
+                float v[64];
+                tmem_ld64(tl + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                v[j] += sBias[2 * kH + 32 * c + j];
-                v[j + 1] += sBias[2 * kH + 32 * c + j + 1];
-                top4_insert(logit_key(v[j], 32 * c + j), ta);
-                top4_insert(logit_key(v[j + 1], 32 * c + j + 1), tb);
+                for (int j = 0; j < 64; ++j) {
+                    v[j] += sBias[2 * kH + c0 + j];
+                    top4_insert(logit_key(v[j], c0 + j), t4);
+                }
+                if (!VERIFY && P.logits && valid) {
+                    float4* dst = reinterpret_cast<float4*>(P.logits + r * kOut + c0);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                }
             }
-            if (P.logits && r < P.n) {
-                float4* dst = reinterpret_cast<float4*>(P.logits + r * kOut + 32 * c);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            fence_before();   // TMEM reads of this tile are complete before the group's next arrival
+            sXchg[(g * 2 + half) * 128 + row] = make_float4(t4[0], t4[1], t4[2], t4[3]);
+            if (!xchg_sync()) break;
+            {
+                const float4 o = sXchg[(g * 2 + (half ^ 1)) * 128 + row];
+                top4_insert(o.x, t4);
+                top4_insert(o.y, t4);
+                top4_insert(o.z, t4);
+                top4_insert(o.w, t4);
+            }
+            if (!VERIFY) {
+                if (half == 0 && P.top4 && valid)
+                    *reinterpret_cast<uchar4*>(P.top4 + 4 * r) =
+                        make_uchar4((uint8_t)key_cluster(t4[0]), (uint8_t)key_cluster(t4[1]),
+                                    (uint8_t)key_cluster(t4[2]), (uint8_t)key_cluster(t4[3]));
+            } else {
+                // Verification, packed over the group's 256 threads: every
+                // open row's best cluster first (one (row, triangle) pair per
+                // slot), then clusters 2-4 of the rows that cluster 1 left.
+                // A slot tests one triangle; a certain decisive hit settles
+                // its row.  No lane waits on another row's longer list.
+                if (half == 0) {
+                    const float3 s = make_float3(seg[0], seg[1], seg[2]), e = make_float3(seg[3], seg[4], seg[5]);
+                    const bool open = valid && !(segtest::bad3(s) || segtest::bad3(e));
+                    const float3 d = make_float3(e.x - s.x, e.y - s.y, e.z - s.z);
+                    sSeg[2 * row] = make_float4(s.x, s.y, s.z, fabsf(d.x) + fabsf(d.y) + fabsf(d.z));
+                    sSeg[2 * row + 1] = make_float4(d.x, d.y, d.z, 0.0f);
+                    sCl[row] = make_uchar4((uint8_t)key_cluster(t4[0]), (uint8_t)key_cluster(t4[1]),
+                                           (uint8_t)key_cluster(t4[2]), (uint8_t)key_cluster(t4[3]));
+                    sHit[row] = open ? 0 : -1;
+                }
+                if (tg == 0) *sLeft = 0;
+                if (!xchg_sync()) break;
+                const int W = P.cluster_max;
+                auto test_slot = [&](int rw, int c, int k) {
+                    const int j = segtest::cluster_begin(c, P.n_tri) + k;
+                    if (j >= segtest::cluster_begin(c + 1, P.n_tri)) return;
+                    const float4 a = sSeg[2 * rw], b = sSeg[2 * rw + 1];
+                    segtest::SegF sg;
+                    sg.s = make_float3(a.x, a.y, a.z);
+                    sg.d = make_float3(b.x, b.y, b.z);
+                    sg.dl1 = a.w;
+                    ++tests;
+                    if (segtest::tri_certain_hit(sg, segtest::load_tri(P.tris, j))) sHit[rw] = 1;
+                };
+#pragma unroll 1
+                for (int slot = tg; slot < 128 * W; slot += 256) {   // cluster 1 of every open row
+                    const int rw = slot / W;
+                    if (sHit[rw] == 0) test_slot(rw, sCl[rw].x, slot - rw * W);
+                }
+                if (!xchg_sync()) break;
+                if (half == 0 && sHit[row] == 0) sList[atomicAdd(sLeft, 1)] = row;
+                if (!xchg_sync()) break;
+                const int left = *sLeft;
+#pragma unroll 1
+                for (int slot = tg; slot < left * 3 * W; slot += 256) {   // clusters 2-4 of the rows left
+                    const int i = slot / (3 * W), rem = slot - i * 3 * W;
+                    const int rw = sList[i], ci = rem / W;
+                    const uchar4 cl = sCl[rw];
+                    test_slot(rw, ci == 0 ? cl.y : (ci == 1 ? cl.z : cl.w), rem - ci * W);
+                }
+                if (!xchg_sync()) break;
+                if (half == 0) {
+                    const bool confirmed = sHit[row] == 1;
+                    if (valid && confirmed) {
+                        P.hit[r] = 1;
+                        if (P.amb) P.amb[r] = 0;
+                        ++confirmed_n;
+                    }
+                    const bool left_row = valid && !confirmed;
+                    const unsigned m = __ballot_sync(0xffffffffu, left_row);
+                    int base = 0;
+                    if (lane == 0 && m) base = atomicAdd(&P.ctr->n_fallback, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (left_row) P.order[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)r;
+                }
             }
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) top4_insert(tb[k], ta);
-        *reinterpret_cast<uint4*>(sTop + (cg * 128 + row) * 4) = make_uint4(ta[0], ta[1], ta[2], ta[3]);
-        fence_before();
-        __syncthreads();
-        if (cg == 0) {   // merge the other column groups' lists into this row's
-#pragma unroll
-            for (int g = 1; g < 4; ++g) {
-                const uint4 o = *reinterpret_cast<const uint4*>(sTop + (g * 128 + row) * 4);
-                top4_insert(o.x, ta);
-                top4_insert(o.y, ta);
-                top4_insert(o.z, ta);
-                top4_insert(o.w, ta);
+        // after a timeout the group may have left with a chain still running:
+        // wait for the issuer's last commit (bounded) before TMEM is freed
+        if (issuer && issued) mbar_wait(bar_mma, (issued - 1u) & 1u);
+        if (VERIFY) {
+            for (int off = 16; off; off >>= 1) {
+                confirmed_n += __shfl_xor_sync(0xffffffffu, confirmed_n, off);
+                tests += __shfl_xor_sync(0xffffffffu, tests, off);
             }
-            if (P.top4 && r < P.n)
-                *reinterpret_cast<uchar4*>(P.top4 + 4 * r) =
-                    make_uchar4((uint8_t)(255u - (ta[0] & 255u)), (uint8_t)(255u - (ta[1] & 255u)),
-                                (uint8_t)(255u - (ta[2] & 255u)), (uint8_t)(255u - (ta[3] & 255u)));
+            if (lane == 0 && confirmed_n) atomicAdd(&P.ctr->n_confirmed, (int)confirmed_n);
+            if (lane == 0 && P.stats && tests) atomicAdd(&P.ctr->tri_tests, (unsigned long long)tests);
         }
     }
+    fence_before();
     __syncthreads();
     if (warp == 0) {
         fence_after();
@@ -379,15 +570,15 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_mlp_forward_tc(FwdArgs P) {
     }
 }
 
-// The network's activation pieces on a vector (tests): erf by the published
-// approximation, CUDA's erff beside it, and GELU.
-__global__ void k_activation(const float* __restrict__ z, int64_t n, float* __restrict__ erf_a,
-                             float* __restrict__ erf_cuda, float* __restrict__ g) {
+// The network's activation pieces on a vector (tests): the hardware tanh
+// approximation, CUDA's tanhf beside it, and GELU as inference applies it.
+__global__ void k_activation(const float* __restrict__ z, int64_t n, float* __restrict__ tanh_a,
+                             float* __restrict__ tanh_cuda, float* __restrict__ g) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    erf_a[i] = erf_as(z[i]);
-    erf_cuda[i] = erff(z[i]);
-    g[i] = gelu(z[i]);
+    tanh_a[i] = tanh_fast(z[i]);
+    tanh_cuda[i] = tanhf(z[i]);
+    g[i] = gelu_fast(z[i]);
 }
 
 // FP32 master parameters -> BF16 images of W1^T, W2^T, W3^T (core-matrix
@@ -574,18 +765,25 @@ void feature_map(rsi_bvh_t h, float lo[3], float sc[3]) {
     }
 }
 
-int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, int64_t n, float* logits,
-               uint8_t* top4, cudaStream_t s) {
-    int rc = ensure_packed(m, s);
-    if (rc) return rc;
-    static bool attr_set = false;
-    if (!attr_set) {
-        RSI_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+// Launch of the tensor-core kernel: one CTA per SM (or per pair of tiles).
+template <bool VERIFY>
+int launch_tc(const TcArgs& P, int64_t n, cudaStream_t s) {
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[VERIFY]) {
+        RSI_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc<VERIFY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kSmBytes + 1024));
-        attr_set = true;
+        attr_set[VERIFY] = true;
     }
-    RSI_CUDA_TRY(cudaMemsetAsync(m->scratch_i, 0, 2 * sizeof(int), s));
-    FwdArgs P;
+    const int64_t tiles = (n + 127) / 128;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 1) / 2, (int64_t)device_sm_count()));
+    k_mlp_tc<VERIFY><<<grid, kTcThreads, kSmBytes + 1024, s>>>(P);
+    note_launches(1);
+    RSI_CUDA_TRY(cudaGetLastError());
+    return RSI_OK;
+}
+
+TcArgs tc_args(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, int64_t n) {
+    TcArgs P{};
     P.img = m->img;
     P.bias = m->bias;
     P.from = from;
@@ -599,15 +797,39 @@ int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, in
     P.sc0 = sc[0];
     P.sc1 = sc[1];
     P.sc2 = sc[2];
+    return P;
+}
+
+int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, int64_t n, float* logits,
+               uint8_t* top4, cudaStream_t s) {
+    int rc = ensure_packed(m, s);
+    if (rc) return rc;
+    RSI_CUDA_TRY(cudaMemsetAsync(m->scratch_i, 0, 2 * sizeof(int), s));
+    TcArgs P = tc_args(m, h, from, to, n);
     P.logits = logits;
     P.top4 = top4;
     P.err = m->scratch_i + 1;
-    const int64_t tiles = (n + 127) / 128;
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)device_sm_count());
-    k_mlp_forward_tc<<<grid, kFwdThreads, kSmBytes + 1024, s>>>(P);
-    note_launches(1);
-    RSI_CUDA_TRY(cudaGetLastError());
-    return RSI_OK;
+    return launch_tc<false>(P, n, s);
+}
+
+int propose_verify(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, int64_t n, uint8_t* hit,
+                   uint8_t* amb, int32_t* order, DevCounters* ctr, int stats, cudaStream_t s) {
+    int rc = ensure_packed(m, s);
+    if (rc) return rc;
+    TcArgs P = tc_args(m, h, from, to, n);
+    P.err = &ctr->error;
+    P.tris = h->tris;
+    P.n_tri = (int)h->n_tri;
+    P.cluster_max = (int)((h->n_tri + 255) / 256);
+    P.dmax0 = h->dmax[0];
+    P.dmax1 = h->dmax[1];
+    P.dmax2 = h->dmax[2];
+    P.hit = hit;
+    P.amb = amb;
+    P.order = order;
+    P.ctr = ctr;
+    P.stats = stats;
+    return launch_tc<true>(P, n, s);
 }
 
 // C = op(A) op(B).  A long reduction (the batch, for weight gradients) is
@@ -761,6 +983,7 @@ extern "C" int rsi_mlp_create(uint64_t seed, rsi_mlp_t* out) {
 extern "C" int rsi_mlp_free(rsi_mlp_t m) {
     if (!m) return RSI_OK;
     cudaDeviceSynchronize();
+    rsi::forget_mlp(m);
     cudaFree(m->params);
     if (m->act) cudaFree(m->act);
     delete m;
@@ -768,6 +991,12 @@ extern "C" int rsi_mlp_free(rsi_mlp_t m) {
 }
 
 extern "C" int rsi_mlp_num_params(void) { return kParams; }
+
+extern "C" int rsi_mlp_attach(rsi_bvh_t h, rsi_mlp_t m) {
+    if (!h) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_attach: NULL hierarchy");
+    rsi::attach_mlp(h, m);
+    return RSI_OK;
+}
 
 extern "C" int rsi_mlp_set_params(rsi_mlp_t m, const float* h_params, void* stream) {
     if (!m || !h_params) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_set_params: NULL argument");
@@ -819,12 +1048,12 @@ extern "C" int rsi_mlp_reset_optimizer(rsi_mlp_t m, void* stream) {
     return RSI_OK;
 }
 
-extern "C" int rsi_mlp_activation(const float* d_z, int64_t n, float* d_erf, float* d_erf_cuda, float* d_gelu,
+extern "C" int rsi_mlp_activation(const float* d_z, int64_t n, float* d_tanh, float* d_tanh_cuda, float* d_gelu,
                                   void* stream) {
-    if (n < 0 || (n > 0 && (!d_z || !d_erf || !d_erf_cuda || !d_gelu)))
+    if (n < 0 || (n > 0 && (!d_z || !d_tanh || !d_tanh_cuda || !d_gelu)))
         return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_mlp_activation: bad arguments");
     if (n == 0) return RSI_OK;
-    k_activation<<<rsi::grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(d_z, n, d_erf, d_erf_cuda, d_gelu);
+    k_activation<<<rsi::grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(d_z, n, d_tanh, d_tanh_cuda, d_gelu);
     rsi::note_launches(1);
     RSI_CUDA_TRY(cudaGetLastError());
     return RSI_OK;

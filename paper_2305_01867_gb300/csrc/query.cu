@@ -23,11 +23,13 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "rsi_internal.cuh"
+#include "segtest.cuh"
 
 namespace rsi {
 
@@ -76,6 +78,7 @@ struct BatchArgs {
     int total;
     long long timeout_ns;
     int streamed;        // 1: segments become available as the host posts them
+    const int32_t* perm; // [total] batch-local segment of each global index (in-tile reordering), or NULL
 };
 
 // Scratch of the pair-parallel FP64 pass: the (segment, triangle) pairs that
@@ -96,167 +99,8 @@ struct PairScratch {
 
 namespace {
 
-constexpr float kU = 5.9604645e-8f;        // unit roundoff of FP32, 2^-24
-constexpr float kErrK = 16.0f * kU;        // bound factor of a dot(cross) in FP32
-constexpr float kTauHi = 1.000001e-6f;     // tau, rounded up
-constexpr float kWiden = 1e-6f;            // relative widening of slab intervals
+using namespace segtest;   // FP32 segment, box and triangle tests (segtest.cuh)
 
-enum { kMiss = 0, kHit = 1, kBand = 2 };
-
-struct SegF {
-    float3 s, d, inv, slo, shi;   // slo = s + pad (up), shi = s - pad (down)
-    float dl1;                    // |d|_1
-};
-
-__device__ __forceinline__ float safe_inv(float x) {
-    return fabsf(x) < 1e-20f ? copysignf(1e20f, x) : 1.0f / x;
-}
-
-__device__ __forceinline__ SegF make_seg(float3 s, float3 e, float dmx, float dmy, float dmz) {
-    SegF g;
-    g.s = s;
-    g.d = make_float3(e.x - s.x, e.y - s.y, e.z - s.z);
-    g.inv = make_float3(safe_inv(g.d.x), safe_inv(g.d.y), safe_inv(g.d.z));
-    g.dl1 = fabsf(g.d.x) + fabsf(g.d.y) + fabsf(g.d.z);
-    const float k = 4.0f * kTauHi;
-    float px = __fmul_ru(k, __fadd_ru(g.dl1, dmx));
-    float py = __fmul_ru(k, __fadd_ru(g.dl1, dmy));
-    float pz = __fmul_ru(k, __fadd_ru(g.dl1, dmz));
-    g.slo = make_float3(__fadd_ru(s.x, px), __fadd_ru(s.y, py), __fadd_ru(s.z, pz));
-    g.shi = make_float3(__fsub_rd(s.x, px), __fsub_rd(s.y, py), __fsub_rd(s.z, pz));
-    return g;
-}
-
-// Does the segment pass through the padded box?  The padded slab [lo - pad,
-// hi + pad] becomes parameters (lo - (s + pad)) / d and (hi - (s - pad)) / d
-// with the shifted origins rounded outward; the interval is then widened.
-__device__ __forceinline__ bool slab6(float xlo, float ylo, float zlo, float xhi, float yhi, float zhi,
-                                      const SegF& g) {
-    float t0x = (xlo - g.slo.x) * g.inv.x, t1x = (xhi - g.shi.x) * g.inv.x;
-    float t0y = (ylo - g.slo.y) * g.inv.y, t1y = (yhi - g.shi.y) * g.inv.y;
-    float t0z = (zlo - g.slo.z) * g.inv.z, t1z = (zhi - g.shi.z) * g.inv.z;
-    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
-    tn = tn - fabsf(tn) * kWiden;
-    tf = tf + fabsf(tf) * kWiden;
-    return tn <= tf && tn <= 1.0f && tf >= 0.0f;
-}
-__device__ __forceinline__ bool slab(const float4& bmin, const float4& bmax, const SegF& g) {
-    return slab6(bmin.x, bmin.y, bmin.z, bmax.x, bmax.y, bmax.z, g);
-}
-// The same test, also giving the length of the parameter interval inside the box.
-__device__ __forceinline__ bool slab_len(const float4& bmin, const float4& bmax, const SegF& g, float& len) {
-    float t0x = (bmin.x - g.slo.x) * g.inv.x, t1x = (bmax.x - g.shi.x) * g.inv.x;
-    float t0y = (bmin.y - g.slo.y) * g.inv.y, t1y = (bmax.y - g.shi.y) * g.inv.y;
-    float t0z = (bmin.z - g.slo.z) * g.inv.z, t1z = (bmax.z - g.shi.z) * g.inv.z;
-    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
-    tn = tn - fabsf(tn) * kWiden;
-    tf = tf + fabsf(tf) * kWiden;
-    len = fminf(tf, 1.0f) - fmaxf(tn, 0.0f);
-    return tn <= tf && tn <= 1.0f && tf >= 0.0f;
-}
-
-__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 f3(const float4& v) { return make_float3(v.x, v.y, v.z); }
-__device__ __forceinline__ float3 abs3(float3 a) { return make_float3(fabsf(a.x), fabsf(a.y), fabsf(a.z)); }
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-// |a| x |b| with every product added: bounds the magnitude of each term.
-__device__ __forceinline__ float3 cross_abs(float3 a, float3 b) {
-    return make_float3(a.y * b.z + a.z * b.y, a.z * b.x + a.x * b.z, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-
-// FP32 Moller-Trumbore with forward error bounds.  With d, e1, e2, sv each
-// rounded once and every quantity a dot of a cross, |fl(x) - x| <= 8 u M_x
-// where M_x is the same expression in absolute values; kErrK doubles that.
-// Decisions are taken on the numerators against the denominator so the
-// bounds stay linear:  u > tau  <=>  sign(det) U > tau |det|,  etc.
-//
-// For a certain hit, `tlo`/`thi` (when given) receive bounds of the exact t
-// (numerator and denominator bounds divided with directed rounding), and
-// `tplain` the plain FP32 t of a plain hit.
-__device__ __forceinline__ int tri_fp32(const SegF& g, const Tri& tr, bool want_plain, bool& plain_hit,
-                                        float* tlo = nullptr, float* thi = nullptr, float* tplain = nullptr) {
-    float3 a = f3(tr.v0);
-    float3 e1 = sub3(f3(tr.v1), a), e2 = sub3(f3(tr.v2), a);
-    float3 sv = sub3(g.s, a);
-    float3 p = cross3(g.d, e2);
-    float det = dot3(e1, p);
-    float3 q = cross3(sv, e1);
-    float T = dot3(e2, q);
-    float3 ad = abs3(g.d), ae1 = abs3(e1), ae2 = abs3(e2), asv = abs3(sv);
-    float3 pa = cross_abs(ad, ae2), qa = cross_abs(asv, ae1);
-    float errdet = kErrK * dot3(ae1, pa) + 1e-35f;
-    float errT = kErrK * dot3(ae2, qa) + 1e-35f;
-    // tau * |d| |e1| |e2| bounded above with 1-norms (no square roots)
-    float thr = kTauHi * (g.dl1 * (ae1.x + ae1.y + ae1.z)) * (ae2.x + ae2.y + ae2.z) * 1.000001f;
-    float Tm = T - det;
-    float errTm = errT + errdet + 2.0f * kU * (fabsf(T) + fabsf(det));
-    float U = dot3(sv, p), V = dot3(g.d, q);
-    plain_hit = false;
-    if (want_plain && det != 0.0f) {   // the uncorrected FP32 decision (fp32_only)
-        float u = U / det, v = V / det, t = T / det;
-        plain_hit = u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t >= 0.0f && t <= 1.0f;
-        if (tplain) *tplain = t;
-    }
-    // both end points strictly on one side of the plane, farther than
-    // tau |d| |n| (|n| <= |e1||e2|): a decisive miss on either branch
-    if ((T > 0.0f) == (Tm > 0.0f) && fminf(fabsf(T) - errT, fabsf(Tm) - errTm) > thr) return kMiss;
-    float D = fabsf(det);
-    if (D - errdet > thr) {   // |det_rel| > tau for certain
-        float sg = det > 0.0f ? 1.0f : -1.0f;
-        float errU = kErrK * dot3(asv, pa) + 1e-35f;
-        float errV = kErrK * dot3(ad, qa) + 1e-35f;
-        float Us = sg * U, Vs = sg * V, Ts = sg * T;
-        float Ws = D - Us - Vs;
-        float errW = errdet + errU + errV + 2.0f * kU * (D + fabsf(U) + fabsf(V));
-        float Tms = D - Ts;
-        float lim = kTauHi * (D + errdet) * 1.000001f;
-        if (Us - errU > lim && Vs - errV > lim && Ws - errW > lim && Ts - errT > lim && Tms - errTm > lim) {
-            if (tlo) {   // 0 < Ts - errT <= Ts_exact, 0 < D - errdet <= D_exact
-                *tlo = __fdiv_rd(__fsub_rd(Ts, errT), __fadd_ru(D, errdet));
-                *thi = __fdiv_ru(__fadd_ru(Ts, errT), __fsub_rd(D, errdet));
-            }
-            return kHit;
-        }
-        if (Us + errU < -lim || Vs + errV < -lim || Ws + errW < -lim || Ts + errT < -lim || Tms + errTm < -lim)
-            return kMiss;
-    }
-    return kBand;
-}
-
-// 32-byte read-only load (sm_100 and later): one lane reads one whole L1
-// sector in a single request instead of two 16-byte halves.  p must be
-// 32-byte aligned (nodes and triangles are 64-byte aligned).
-__device__ __forceinline__ void ld32B(const void* p, float4& a, float4& b) {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-        : "l"(p));
-}
-
-__device__ __forceinline__ void load_node(const Node* __restrict__ nodes, int i, float4& a, float4& b, float4& c,
-                                          float4& d) {
-    const float4* p = reinterpret_cast<const float4*>(nodes + i);
-    ld32B(p, a, b);
-    ld32B(p + 2, c, d);
-}
-
-__device__ __forceinline__ Tri load_tri(const Tri* __restrict__ tris, int j) {
-    const float4* p = reinterpret_cast<const float4*>(tris + j);
-    Tri t;
-    ld32B(p, t.v0, t.v1);
-    ld32B(p + 2, t.v2, t.pad);
-    return t;
-}
-
-__device__ __forceinline__ void raise_error(DevCounters* c, int code) { atomicCAS(&c->error, 0, code); }
-
-__device__ __forceinline__ bool bad3(float3 a) {
-    return !(isfinite(a.x) && isfinite(a.y) && isfinite(a.z));
-}
 
 // ---------------------------------------------------------------- FP64
 // The definition in FP64 with explicit round-to-nearest operations in the
@@ -504,7 +348,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
                         if (BATCHED) {
                             const int gi = wbase + rank;
                             l_batch = find_batch(B, gi);
-                            ray = gi - __ldg(B.begins + l_batch);
+                            ray = B.perm ? __ldg(B.perm + gi) : gi - __ldg(B.begins + l_batch);
                         } else {
                             ray = A.perm ? __ldg(A.perm + wbase + rank) : wbase + rank;
                         }
@@ -1748,9 +1592,90 @@ __global__ void __launch_bounds__(256) k_ray_tile_sort(const float* __restrict__
     }
 }
 
+// Traversal order of a whole batch: a counting sort of the segments by the
+// Morton cell of their midpoint on a 32 x 32 x 32 grid over the mesh extent
+// (15-bit keys, z the most significant of each 3-bit group, as the build's
+// codes).  Neighbours in this order cross the same part of the hierarchy, so
+// the warps of an SM share node fetches.  Order inside a cell is arbitrary:
+// answers do not depend on the order.
+constexpr int kOrderBins = 1 << 15;
+
+__device__ __forceinline__ uint32_t order_key(const float* __restrict__ from, const float* __restrict__ to, int64_t r,
+                                              float lox, float loy, float loz, float sx, float sy, float sz) {
+    const float mx = 0.5f * (__ldg(from + 3 * r) + __ldg(to + 3 * r));
+    const float my = 0.5f * (__ldg(from + 3 * r + 1) + __ldg(to + 3 * r + 1));
+    const float mz = 0.5f * (__ldg(from + 3 * r + 2) + __ldg(to + 3 * r + 2));
+    const uint32_t qx = (uint32_t)fminf(fmaxf((mx - lox) * sx, 0.0f), 31.0f);   // NaN -> 0
+    const uint32_t qy = (uint32_t)fminf(fmaxf((my - loy) * sy, 0.0f), 31.0f);
+    const uint32_t qz = (uint32_t)fminf(fmaxf((mz - loz) * sz, 0.0f), 31.0f);
+    return spread10q(qx) | (spread10q(qy) << 1) | (spread10q(qz) << 2);
+}
+
+// Per-block histogram in shared memory (128 KB), added to the global one.
+__global__ void __launch_bounds__(1024) k_order_hist(const float* __restrict__ from, const float* __restrict__ to,
+                                                     int64_t n, float lox, float loy, float loz, float sx, float sy,
+                                                     float sz, unsigned int* __restrict__ hist) {
+    extern __shared__ unsigned int sh_hist[];
+    for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) sh_hist[i] = 0u;
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&sh_hist[order_key(from, to, r, lox, loy, loz, sx, sy, sz)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) {
+        const unsigned int c = sh_hist[i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+// Exclusive scan of the 2^15 bins by one block of 1024 threads (32 each).
+__global__ void __launch_bounds__(1024) k_order_scan(unsigned int* __restrict__ hist) {
+    __shared__ unsigned int part[1024];
+    const int t = threadIdx.x;
+    unsigned int v[32], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        v[k] = hist[32 * t + k];
+        sum += v[k];
+    }
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned int x = t >= off ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += x;
+        __syncthreads();
+    }
+    unsigned int run = part[t] - sum;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        hist[32 * t + k] = run;
+        run += v[k];
+    }
+}
+
+// Scatter: each segment takes the next slot of its cell (lanes of a warp
+// with the same cell share one atomic).
+__global__ void __launch_bounds__(256) k_order_scatter(const float* __restrict__ from, const float* __restrict__ to,
+                                                       int64_t n, float lox, float loy, float loz, float sx, float sy,
+                                                       float sz, unsigned int* __restrict__ cursor,
+                                                       int32_t* __restrict__ order) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = base + lane;
+        const bool ok = r < n;
+        const uint32_t key = ok ? order_key(from, to, r, lox, loy, loz, sx, sy, sz) : 0xFFFFFFFFu - lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        unsigned int pos = 0;
+        if (ok && lane == leader) pos = atomicAdd(&cursor[key], (unsigned int)__popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (ok) order[pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)r;
+    }
+}
+
 // Cluster of leaf j: 256 equal ranges of the Morton-ordered leaves.
 __device__ __forceinline__ int leaf_cluster(int j, int64_t n_tri) { return (int)(((int64_t)j * 256) / n_tri); }
-__device__ __forceinline__ int cluster_begin(int c, int64_t n_tri) { return (int)(((int64_t)c * n_tri + 255) / 256); }
 
 // Multi-hot training labels: every leaf the segment's padded box search
 // reaches, tested in FP32 (certain hit, or the plain decision in the band).
@@ -1808,47 +1733,6 @@ __global__ void __launch_bounds__(128) k_cluster_labels(QueryArgs A, uint32_t* _
     }
 }
 
-// Proposal verification: the triangles of the 4 proposed clusters, best
-// first; an FP32-certain decisive hit settles the segment (hit = 1, not
-// ambiguous); the rest go to the fallback list in `order`.
-__global__ void __launch_bounds__(256) k_verify_proposals(QueryArgs A, const uint8_t* __restrict__ top4,
-                                                          int32_t* __restrict__ order) {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool confirmed = false;
-    if (r < A.n_rays) {
-        const float3 s = make_float3(A.from[3 * r], A.from[3 * r + 1], A.from[3 * r + 2]);
-        const float3 e = make_float3(A.to[3 * r], A.to[3 * r + 1], A.to[3 * r + 2]);
-        if (!(bad3(s) || bad3(e))) {
-            const SegF g = make_seg(s, e, A.dmax0, A.dmax1, A.dmax2);
-            const uchar4 p = *reinterpret_cast<const uchar4*>(top4 + 4 * r);
-            const int cl[4] = {p.x, p.y, p.z, p.w};
-            for (int q = 0; q < 4 && !confirmed; ++q) {
-                const int j1 = cluster_begin(cl[q] + 1, A.n_tri);
-                for (int j = cluster_begin(cl[q], A.n_tri); j < j1; ++j) {
-                    bool plain;
-                    if (tri_fp32(g, load_tri(A.tris, j), false, plain) == kHit) {
-                        confirmed = true;
-                        break;
-                    }
-                }
-            }
-        }
-        if (confirmed) {
-            A.hit[r] = 1;
-            if (A.amb) A.amb[r] = 0;
-        }
-    }
-    const bool left = r < A.n_rays && !confirmed;
-    const unsigned m = __ballot_sync(0xffffffffu, left);
-    const unsigned mc = __ballot_sync(0xffffffffu, confirmed);
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0 && m) base = atomicAdd(&A.ctr->n_fallback, __popc(m));
-    if (lane == 0 && mc) atomicAdd(&A.ctr->n_confirmed, __popc(mc));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (left) order[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)r;
-}
-
 // Validation mode (rsi_options.fp64_all): every segment is queued for the
 // FP64 re-test, none is settled by the FP32 traversal.
 __global__ void k_queue_all(int32_t* __restrict__ band_ids, int64_t n, DevCounters* c) {
@@ -1884,21 +1768,24 @@ inline int wide_stack_need(int height) { return 3 * ((height + 2) / 2); }
 inline bool wide_ok(int height) { return wide_stack_need(height) <= 128; }
 
 // nw: 0 child-pair nodes, 1 four-wide nodes, 2 compressed child-pair nodes
-// (single queries only; batched plans pass 0 or 1).
+// (single queries only; batched plans pass 0 or 1).  The stack is the
+// smallest of 32 / 64 / 128 entries that holds the walk and `stack_min`.
 template <int MODE, bool STATS, bool BATCHED = false>
 void launch_fp32_stack(const QueryArgs& A, int height, int nw, int grid, int block, cudaStream_t s,
-                       const BatchArgs& B = BatchArgs{}) {
-    if (nw == 1 && wide_ok(height)) {
-        const int need = wide_stack_need(height);
-        if (need <= 32) launch_fp32<MODE, STATS, 32, BATCHED, 1>(A, B, grid, block, s);
-        else if (need <= 64) launch_fp32<MODE, STATS, 64, BATCHED, 1>(A, B, grid, block, s);
+                       const BatchArgs& B = BatchArgs{}, int stack_min = 0) {
+    const bool wide = nw == 1 && wide_ok(height);
+    const int need = std::max(wide ? wide_stack_need(height) : height + 1, stack_min);
+    const int st = need <= 32 ? 32 : (need <= 64 ? 64 : 128);
+    if (wide) {
+        if (st == 32) launch_fp32<MODE, STATS, 32, BATCHED, 1>(A, B, grid, block, s);
+        else if (st == 64) launch_fp32<MODE, STATS, 64, BATCHED, 1>(A, B, grid, block, s);
         else launch_fp32<MODE, STATS, 128, BATCHED, 1>(A, B, grid, block, s);
     } else if (!BATCHED && nw == 2) {
-        if (height < 32) launch_fp32<MODE, STATS, 32, false, 2>(A, B, grid, block, s);
-        else if (height < 64) launch_fp32<MODE, STATS, 64, false, 2>(A, B, grid, block, s);
+        if (st == 32) launch_fp32<MODE, STATS, 32, false, 2>(A, B, grid, block, s);
+        else if (st == 64) launch_fp32<MODE, STATS, 64, false, 2>(A, B, grid, block, s);
         else launch_fp32<MODE, STATS, 128, false, 2>(A, B, grid, block, s);
-    } else if (height < 32) launch_fp32<MODE, STATS, 32, BATCHED, 0>(A, B, grid, block, s);
-    else if (height < 64) launch_fp32<MODE, STATS, 64, BATCHED, 0>(A, B, grid, block, s);
+    } else if (st == 32) launch_fp32<MODE, STATS, 32, BATCHED, 0>(A, B, grid, block, s);
+    else if (st == 64) launch_fp32<MODE, STATS, 64, BATCHED, 0>(A, B, grid, block, s);
     else launch_fp32<MODE, STATS, 128, BATCHED, 0>(A, B, grid, block, s);
 }
 
@@ -1997,6 +1884,8 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
         return fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2, 3 or 4");
     if (o.fp64_all && (o.fp32_only || order))
         return fail(RSI_ERR_INVALID_ARG, "rsi_query: fp64_all excludes fp32_only and the learned query");
+    if (o.stack != 0 && o.stack != 32 && o.stack != 64 && o.stack != 128)
+        return fail(RSI_ERR_INVALID_ARG, "rsi_query: stack must be 0, 32, 64 or 128");
     const int nw = o.node_width == 4 ? 1 : (o.node_width == 3 && h->has_q ? 2 : 0);
     const int block = o.block > 0 ? o.block : 256;
     const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
@@ -2007,6 +1896,9 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
         for (auto& e : h->ev) RSI_CUDA_TRY(cudaEventCreate(&e));
     }
     h->timed = o.time_kernels != 0;
+    if (o.order && (o.ray_sort_tile != 0 || order))
+        return fail(RSI_ERR_INVALID_ARG, "rsi_query: order excludes ray_sort_tile and the learned query");
+    if (o.order) A.perm = o.order;   // the caller's traversal order (rsi_segment_order)
     if (o.ray_sort_tile != 0) {
         if (o.ray_sort_tile < 256 || o.ray_sort_tile > kMaxSortTile)
             return fail(RSI_ERR_INVALID_ARG, "rsi_query: ray_sort_tile must be 0 or in [256, 8192]");
@@ -2029,14 +1921,14 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (o.fp64_all) {
         k_queue_all<<<grid_for(n, 256), 256, 0, s>>>(band_ids, n, ctr);
     } else if (mode == RSI_ANY_HIT) {
-        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, nw, grid, block, s);
-        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, nw, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, nw, grid, block, s, {}, o.stack);
+        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, nw, grid, block, s, {}, o.stack);
     } else if (mode == RSI_COUNT) {
-        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, nw, grid, block, s);
-        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, nw, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, nw, grid, block, s, {}, o.stack);
+        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, nw, grid, block, s, {}, o.stack);
     } else {
-        if (o.collect_stats) launch_fp32_stack<RSI_NEAREST, true>(A, h->height, nw, grid, block, s);
-        else launch_fp32_stack<RSI_NEAREST, false>(A, h->height, nw, grid, block, s);
+        if (o.collect_stats) launch_fp32_stack<RSI_NEAREST, true>(A, h->height, nw, grid, block, s, {}, o.stack);
+        else launch_fp32_stack<RSI_NEAREST, false>(A, h->height, nw, grid, block, s, {}, o.stack);
     }
     if (h->timed) RSI_CUDA_TRY(cudaEventRecord(h->ev[1], s));
     if (!o.fp32_only) {
@@ -2183,6 +2075,8 @@ extern "C" int rsi_query(rsi_bvh_t h, const float* d_from, const float* d_to, in
                          rsi_stats* stats, void* stream) {
     int rc = check_query_args("rsi_query", h, d_from, d_to, n_rays, mode, d_hit, d_count);
     if (rc) return rc;
+    if (mode == RSI_ANY_HIT && h->mlp && !(opt && opt->fp64_all))   // attached proposal network
+        return rsi_query_learned(h, h->mlp, d_from, d_to, n_rays, opt, d_hit, d_ambiguous, stats, stream);
     cudaStream_t s = (cudaStream_t)stream;
     if (n_rays == 0) {
         if (stats) *stats = rsi_stats{};
@@ -2327,6 +2221,8 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     if (o.blocks_per_sm < 0) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: blocks_per_sm < 0");
     if (o.node_width != 0 && o.node_width != 2 && o.node_width != 3 && o.node_width != 4)
         return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: node_width must be 0, 2, 3 or 4");
+    if (o.stack != 0 && o.stack != 32 && o.stack != 64 && o.stack != 128)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query: stack must be 0, 32, 64 or 128");
     if (h->height >= 127) return rsi::fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
     int rc = rsi::ensure_band_capacity(h, n, s);
     if (rc) return rc;
@@ -2410,11 +2306,11 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + block - 1) / block,
                                                                    (int64_t)rsi::device_sm_count() * bps));
     if (mode == RSI_ANY_HIT) {
-        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, nw, grid, block, s, Bs);
-        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, nw, grid, block, s, Bs);
+        if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, nw, grid, block, s, Bs, o.stack);
+        else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, nw, grid, block, s, Bs, o.stack);
     } else {
-        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, nw, grid, block, s, Bs);
-        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, nw, grid, block, s, Bs);
+        if (o.collect_stats) launch_fp32_stack<RSI_COUNT, true>(A, h->height, nw, grid, block, s, Bs, o.stack);
+        else launch_fp32_stack<RSI_COUNT, false>(A, h->height, nw, grid, block, s, Bs, o.stack);
     }
     rsi::note_launches(2);
     // every copy has landed once the traversal ends; the wait orders the FP64 pass after them
@@ -2530,6 +2426,42 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
     return RSI_OK;
 }
 
+// ---------------------------------------------------------------- traversal order
+extern "C" int rsi_segment_order(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n_rays,
+                                 int32_t* d_order, void* stream) {
+    if (!h) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_segment_order: NULL handle");
+    if (n_rays < 0 || n_rays > 0x7FFFFFFFll)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_segment_order: need 0 <= n_rays < 2^31");
+    if (n_rays > 0 && (!d_from || !d_to || !d_order))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_segment_order: NULL segment or order pointer");
+    if (n_rays == 0) return RSI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->order_hist) {
+        if (rsi::pool_alloc(reinterpret_cast<void**>(&h->order_hist), sizeof(unsigned int) * rsi::kOrderBins, s) !=
+            RSI_OK)
+            return RSI_ERR_OOM;
+        static bool attr = false;   // 128 KB of shared memory per block for the histogram
+        if (!attr) {
+            RSI_CUDA_TRY(cudaFuncSetAttribute(rsi::k_order_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(sizeof(unsigned int) * rsi::kOrderBins)));
+            attr = true;
+        }
+    }
+    float sc[3];
+    for (int a = 0; a < 3; ++a) sc[a] = h->hi[a] > h->lo[a] ? 32.0f / (h->hi[a] - h->lo[a]) : 0.0f;
+    RSI_CUDA_TRY(cudaMemsetAsync(h->order_hist, 0, sizeof(unsigned int) * rsi::kOrderBins, s));
+    const int sms = rsi::device_sm_count();
+    rsi::k_order_hist<<<sms, 1024, sizeof(unsigned int) * rsi::kOrderBins, s>>>(
+        d_from, d_to, n_rays, h->lo[0], h->lo[1], h->lo[2], sc[0], sc[1], sc[2], h->order_hist);
+    rsi::k_order_scan<<<1, 1024, 0, s>>>(h->order_hist);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n_rays + 255) / 256, (int64_t)sms * 8));
+    rsi::k_order_scatter<<<g, 256, 0, s>>>(d_from, d_to, n_rays, h->lo[0], h->lo[1], h->lo[2], sc[0], sc[1], sc[2],
+                                           h->order_hist, d_order);
+    rsi::note_launches(3);
+    RSI_CUDA_TRY(cudaGetLastError());
+    return RSI_OK;
+}
+
 // ---------------------------------------------------------------- learned
 using namespace rsi;   // the kernels and launchers above
 
@@ -2566,6 +2498,8 @@ extern "C" int rsi_query_learned(rsi_bvh_t h, rsi_mlp_t m, const float* d_from, 
     if (rc) return rc;
     if (!m) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_learned: NULL network");
     if (n_rays > 0x7FFFFF00ll) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_learned: too many segments");
+    if (opt && opt->fp64_all)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_learned: fp64_all excludes the learned query");
     cudaStream_t s = (cudaStream_t)stream;
     if (n_rays == 0) {
         if (stats) *stats = rsi_stats{};
@@ -2573,29 +2507,17 @@ extern "C" int rsi_query_learned(rsi_bvh_t h, rsi_mlp_t m, const float* d_from, 
     }
     rc = rsi::ensure_band_capacity(h, n_rays, s);
     if (rc) return rc;
-    int32_t* order = h->band_ids + h->band_cap;
-    uint8_t* top4 = reinterpret_cast<uint8_t*>(h->band_ids + 2 * h->band_cap);
-    rc = rsi::mlpk::forward_tc(m, h, d_from, d_to, n_rays, nullptr, top4, s);
-    if (rc) return rc;
-    k_reset_query<<<1, 1, 0, s>>>(h->ctr, ~0ull);
-    QueryArgs A{};
-    A.nodes = h->nodes;
-    A.tris = h->tris;
-    A.n_tri = h->n_tri;
-    A.from = d_from;
-    A.to = d_to;
-    A.n_rays = n_rays;
-    A.hit = d_hit;
-    A.amb = d_ambiguous;
-    A.ctr = h->ctr;
-    A.dmax0 = h->dmax[0];
-    A.dmax1 = h->dmax[1];
-    A.dmax2 = h->dmax[2];
-    k_verify_proposals<<<rsi::grid_for(n_rays, 256), 256, 0, s>>>(A, top4, order);
-    rsi::note_launches(2);
     rsi_options o = {};
     if (opt) o = *opt;
     o.ray_sort_tile = 0;
+    o.order = nullptr;   // the fallback walks the proposal's leftovers in its own order
+    int32_t* order = h->band_ids + h->band_cap;
+    // proposal + verification in one tensor-core kernel (the top-4 stay in
+    // registers), then the tree search over the segments it left
+    k_reset_query<<<1, 1, 0, s>>>(h->ctr, (unsigned long long)n_rays);
+    rsi::note_launches(1);
+    rc = rsi::mlpk::propose_verify(m, h, d_from, d_to, n_rays, d_hit, d_ambiguous, order, h->ctr, o.collect_stats, s);
+    if (rc) return rc;
     const rsi::PairScratch P = rsi::handle_pairs(h);
     rc = rsi::query_device(h, d_from, d_to, n_rays, RSI_ANY_HIT, &o, d_hit, nullptr, d_ambiguous, h->band_ids, nullptr,
                            h->ctr, s, order, &h->ctr->n_fallback, nullptr, &P);
@@ -2633,6 +2555,7 @@ struct rsi_batch_s {
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int sort_launches = 0;        // in-tile reorderings captured in the graph
 };
 
 namespace {
@@ -2658,8 +2581,8 @@ void launch_batched(rsi_batch_s* b, const QueryArgs& A, const BatchArgs& B, cuda
     int64_t want = ((int64_t)b->total + block - 1) / block;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)rsi::device_sm_count() * bps));
     const int nw = b->opt.node_width == 4 ? 1 : 0;
-    if (b->opt.collect_stats) launch_fp32_stack<MODE, true, true>(A, b->height, nw, grid, block, s, B);
-    else launch_fp32_stack<MODE, false, true>(A, b->height, nw, grid, block, s, B);
+    if (b->opt.collect_stats) launch_fp32_stack<MODE, true, true>(A, b->height, nw, grid, block, s, B, b->opt.stack);
+    else launch_fp32_stack<MODE, false, true>(A, b->height, nw, grid, block, s, B, b->opt.stack);
     if (!b->opt.fp32_only) {
         const rsi::PairScratch P = rsi::carve_pairs(b->pairs, b->seg_cap, b->pair_cap, b->fb);
         launch_fp64_pass<MODE, true>(A, b->height, &P, s, B);
@@ -2679,8 +2602,13 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
         return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: block must be a multiple of 32 in [32, 256]");
     if (o.blocks_per_sm < 0) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: blocks_per_sm < 0");
-    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 4)
-        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: node_width must be 0, 2 or 4");
+    if (o.node_width != 0 && o.node_width != 2 && o.node_width != 3 && o.node_width != 4)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: node_width must be 0, 2, 3 or 4");
+    if (o.stack != 0 && o.stack != 32 && o.stack != 64 && o.stack != 128)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: stack must be 0, 32, 64 or 128");
+    if (o.timeout_ns < 0) o.ray_sort_tile = 0;   // streaming: segments arrive while the plan runs
+    if (o.ray_sort_tile != 0 && (o.ray_sort_tile < 256 || o.ray_sort_tile > kMaxSortTile))
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: ray_sort_tile must be 0 or in [256, 8192]");
     std::vector<int> begins(n_batches + 1, 0);
     std::vector<rsi::BatchDesc> desc(n_batches);
     int height = 0;
@@ -2727,7 +2655,8 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     const size_t off_pairs = off_fb + ((4 * (size_t)std::max<int64_t>(total, 1) + 255) & ~(size_t)255);
     size_t pair_bytes;
     rsi::pair_sizes(std::max<int64_t>(total, 1), b_seg_cap, b_pair_cap, pair_bytes);
-    const size_t bytes = off_pairs + pair_bytes;
+    const size_t off_perm = off_pairs + ((pair_bytes + 255) & ~(size_t)255);
+    const size_t bytes = off_perm + (o.ray_sort_tile ? 4 * (size_t)std::max<int64_t>(total, 1) : 0);
     if (rsi::dev_malloc(&b->dev, bytes) != cudaSuccess || rsi::host_malloc_pinned(&b->h_ctr, sizeof(rsi::DevCounters)) != cudaSuccess ||
         rsi::host_malloc_pinned(&b->h_post, 256 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
@@ -2740,6 +2669,7 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     b->band = reinterpret_cast<int32_t*>(b->dev + off_band);
     b->fb = reinterpret_cast<int32_t*>(b->dev + off_fb);
     b->pairs = b->dev + off_pairs;
+    int32_t* perm = o.ray_sort_tile ? reinterpret_cast<int32_t*>(b->dev + off_perm) : nullptr;
     b->seg_cap = b_seg_cap;
     b->pair_cap = b_pair_cap;
     cudaStream_t s = (cudaStream_t)stream;
@@ -2766,10 +2696,24 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     const bool streamed = o.timeout_ns < 0;
     if (streamed) B.timeout_ns = -(long long)o.timeout_ns;
     B.streamed = streamed ? 1 : 0;
+    B.perm = perm;
     b->streamed = streamed;
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         k_reset_query<<<1, 1, 0, b->cap>>>(b->ctr, streamed ? ~0ull : (unsigned long long)total);
+        if (perm) {   // in-tile reordering of every batch, into the global index space
+            for (int i = 0; i < n_batches; ++i) {
+                const rsi_ray_batch& rb = batches[i];
+                if (rb.n_rays == 0) continue;
+                float sc[3];
+                for (int a = 0; a < 3; ++a)
+                    sc[a] = rb.bvh->hi[a] > rb.bvh->lo[a] ? 1024.0f / (rb.bvh->hi[a] - rb.bvh->lo[a]) : 0.0f;
+                k_ray_tile_sort<<<rsi::grid_for(rb.n_rays, o.ray_sort_tile), 256, 0, b->cap>>>(
+                    rb.d_from, rb.d_to, (int)rb.n_rays, o.ray_sort_tile, rb.bvh->lo[0], rb.bvh->lo[1], rb.bvh->lo[2],
+                    sc[0], sc[1], sc[2], perm + begins[i]);
+                ++b->sort_launches;
+            }
+        }
         if (mode == RSI_ANY_HIT) launch_batched<RSI_ANY_HIT>(b, A, B, b->cap);
         else launch_batched<RSI_COUNT>(b, A, B, b->cap);
         cudaError_t le = cudaGetLastError();
@@ -2786,14 +2730,15 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     return RSI_OK;
 }
 
-extern "C" int rsi_query_batched(rsi_batch_t b, void* stream) {
-    if (!b) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_batched: NULL plan");
+extern "C" int rsi_batch_launch(rsi_batch_t b, void* stream) {
+    if (!b) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_launch: NULL plan");
     if (b->streamed) {   // empty the queue before any post of this run can land
         RSI_CUDA_TRY(cudaMemsetAsync(&b->ctr->ready, 0, sizeof(unsigned long long), (cudaStream_t)stream));
         RSI_CUDA_TRY(cudaEventRecord(b->reset_ev, (cudaStream_t)stream));
     }
     RSI_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
-    rsi::note_launches(b->opt.fp32_only ? 2 : 8);   // reset, traversal, the 6 kernels of the FP64 pass
+    // reset, the reorderings, traversal, the 6 kernels of the FP64 pass
+    rsi::note_launches((b->opt.fp32_only ? 2 : 8) + b->sort_launches);
     return RSI_OK;
 }
 
@@ -2833,6 +2778,92 @@ extern "C" int rsi_batch_free(rsi_batch_t b) {
     cudaDeviceSynchronize();
     batch_destroy(b);
     return RSI_OK;
+}
+
+// ---------------------------------------------------------------- one-call batched query
+// rsi_query_batched plans a call once and replays the plan when the same
+// arguments come back: the key holds each hierarchy's process-unique id (an
+// address can be reused by a later handle, an id cannot), the device, every
+// batch's buffers and sizes, the mode and the options.
+namespace {
+
+struct PlanKey {
+    int device = 0, mode = 0;
+    rsi_options opt{};
+    std::vector<uint64_t> gens;
+    std::vector<rsi_ray_batch> batches;   // .bvh as given by hs
+    bool operator==(const PlanKey& o) const {
+        if (device != o.device || mode != o.mode || gens != o.gens || batches.size() != o.batches.size()) return false;
+        if (std::memcmp(&opt, &o.opt, sizeof(rsi_options)) != 0) return false;
+        for (size_t i = 0; i < batches.size(); ++i) {
+            const rsi_ray_batch &a = batches[i], &b = o.batches[i];
+            if (a.bvh != b.bvh || a.d_from != b.d_from || a.d_to != b.d_to || a.n_rays != b.n_rays ||
+                a.d_hit != b.d_hit || a.d_count != b.d_count || a.d_ambiguous != b.d_ambiguous)
+                return false;
+        }
+        return true;
+    }
+};
+
+constexpr size_t kPlanCacheSize = 4;
+std::mutex g_plan_mu;
+std::vector<std::pair<PlanKey, rsi_batch_t>> g_plans;   // most recently used last
+
+}  // namespace
+
+namespace rsi {
+void drop_plans_of(uint64_t gen) {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    for (size_t i = 0; i < g_plans.size();) {
+        const std::vector<uint64_t>& g = g_plans[i].first.gens;
+        if (std::find(g.begin(), g.end(), gen) != g.end()) {
+            batch_destroy(g_plans[i].second);   // the caller (lbvh_free) has synchronized the device
+            g_plans.erase(g_plans.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+}
+}  // namespace rsi
+
+extern "C" int rsi_query_batched(const rsi_bvh_t* hs, int n_meshes, const rsi_ray_batch* batches, int mode,
+                                 const rsi_options* opt, void* stream) {
+    if (!hs || !batches || n_meshes < 1)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_batched: need n_meshes >= 1 hierarchies and batches");
+    if (opt && opt->timeout_ns < 0)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_batched: streaming plans need rsi_batch_create");
+    PlanKey key;
+    RSI_CUDA_TRY(cudaGetDevice(&key.device));
+    key.mode = mode;
+    if (opt) key.opt = *opt;
+    key.gens.resize(n_meshes);
+    key.batches.assign(batches, batches + n_meshes);
+    for (int i = 0; i < n_meshes; ++i) {
+        if (!hs[i]) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_batched: hierarchy " + std::to_string(i) + " is NULL");
+        if (batches[i].bvh && batches[i].bvh != hs[i])
+            return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_query_batched: batches[" + std::to_string(i) +
+                                                      "].bvh is neither NULL nor hs[" + std::to_string(i) + "]");
+        key.batches[i].bvh = hs[i];
+        key.gens[i] = hs[i]->gen;
+    }
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    for (size_t i = 0; i < g_plans.size(); ++i) {
+        if (g_plans[i].first == key) {
+            rsi_batch_t b = g_plans[i].second;
+            std::rotate(g_plans.begin() + (long)i, g_plans.begin() + (long)i + 1, g_plans.end());
+            return rsi_batch_launch(b, stream);
+        }
+    }
+    rsi_batch_t b = nullptr;
+    int rc = rsi_batch_create(key.batches.data(), n_meshes, mode, opt, stream, &b);
+    if (rc) return rc;
+    if (g_plans.size() >= kPlanCacheSize) {   // the oldest plan may still run: wait before releasing it
+        cudaDeviceSynchronize();
+        batch_destroy(g_plans.front().second);
+        g_plans.erase(g_plans.begin());
+    }
+    g_plans.emplace_back(std::move(key), b);
+    return rsi_batch_launch(b, stream);
 }
 
 // ---------------------------------------------------------------- no-alloc

@@ -122,6 +122,9 @@ struct rsi_bvh_s {
     int64_t device_bytes = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // traversal / re-test timing
     bool timed = false;
+    unsigned int* order_hist = nullptr;   // rsi_segment_order's cell counts (2^15), on first use
+    uint64_t gen = 0;                 // process-unique id (plans name hierarchies by it)
+    rsi_mlp_s* mlp = nullptr;         // attached proposal network (rsi_mlp_attach)
 };
 
 namespace rsi {
@@ -191,10 +194,25 @@ cudaError_t host_malloc_pinned(T** p, size_t bytes) {
 // Count of kernel launches made by the library (rsi_kernel_launches).
 void note_launches(int n);
 
+// Process-unique id of a new hierarchy (never 0, never reused).
+uint64_t next_handle_gen();
+// Attachments of proposal networks to hierarchies (rsi_mlp_attach): every
+// change goes through these, so that freeing either side detaches both.
+void attach_mlp(rsi_bvh_t h, rsi_mlp_s* m);
+void forget_handle(rsi_bvh_t h);   // lbvh_free: detach, drop cached plans naming h
+void forget_mlp(rsi_mlp_s* m);     // rsi_mlp_free: detach from every hierarchy
+// The batched-query plan cache (query.cu): drop every plan naming `gen`.
+void drop_plans_of(uint64_t gen);
+
 namespace mlpk {
 // Tensor-core inference of the proposal network (mlp.cu).
 int forward_tc(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, int64_t n, float* logits,
                uint8_t* top4, cudaStream_t s);
+// The same kernel with the proposal verified in place: settled segments get
+// hit = 1 (amb = 0), the others are listed in `order` (count in
+// ctr->n_fallback); ctr must be reset first.
+int propose_verify(rsi_mlp_s* m, rsi_bvh_t h, const float* from, const float* to, int64_t n, uint8_t* hit,
+                   uint8_t* amb, int32_t* order, DevCounters* ctr, int stats, cudaStream_t s);
 }  // namespace mlpk
 
 }  // namespace rsi

@@ -118,10 +118,14 @@ def test_every_entry_point_rejects_missing_arguments(lib):
         "rsi_nearest_compact": lambda: L.rsi_nearest_compact(None, None, None, -1, None, None, None, None,
                                                              ctypes.byref(k), None),
         "rsi_batch_create": lambda: L.rsi_batch_create(None, 0, 0, None, None, None),
-        "rsi_query_batched": lambda: L.rsi_query_batched(None, None),
+        "rsi_batch_launch": lambda: L.rsi_batch_launch(None, None),
+        "rsi_query_batched": lambda: L.rsi_query_batched(None, 0, None, 0, None, None),
+        "rsi_mlp_attach": lambda: L.rsi_mlp_attach(None, None),
         "rsi_batch_post": lambda: L.rsi_batch_post(None, 0, None),
         "rsi_batch_stats": lambda: L.rsi_batch_stats(None, None, None),
         "rsi_autotune": lambda: L.rsi_autotune(None, None, None, 5, 0, None, None, None, None),
+        "rsi_batch_autotune": lambda: L.rsi_batch_autotune(None, 0, 0, None, None, None, None),
+        "rsi_segment_order": lambda: L.rsi_segment_order(None, None, None, 5, None, None),
         "rsi_mlp_create": lambda: L.rsi_mlp_create(1, None),
         "rsi_mlp_set_params": lambda: L.rsi_mlp_set_params(None, None, None),
         "rsi_mlp_get_params": lambda: L.rsi_mlp_get_params(None, None, None, None),

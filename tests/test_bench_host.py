@@ -9,8 +9,10 @@ import bench
 
 def test_profile_figures_agree_with_the_algorithmic_bytes():
     v = bench.profile_values()
-    if not v:
-        pytest.skip("the committed traversal profile predates the current source (the bench reports null)")
+    # a capture of another traversal source is an error, not a skip: every
+    # change to the traversal needs a new capture
+    assert v, ("profiles/k_query_fp32_count_c2.md predates the current traversal source "
+               f"(source_hash {bench.source_hash()}): capture it again")
     # one launch answers 1e7 segments in count mode: 24 B in + 4 B out each
     algorithmic = bench.BYTES_PER_RAY_COUNT * 10_000_000
     assert 0.9 * algorithmic <= bench.traffic_per_launch() <= 1.25 * algorithmic
@@ -23,6 +25,7 @@ def test_stale_profile_is_not_used(monkeypatch):
     monkeypatch.setattr(bench, "source_hash", lambda: "0000000000000000")
     assert bench.profile_values() == {}
     assert bench.traffic_per_launch() is None and bench.issue_bound() is None
+    assert "STALE" in bench.second_bound()["stale"]
 
 
 def _json_lines(out):

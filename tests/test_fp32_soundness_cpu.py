@@ -95,6 +95,38 @@ def tri_fp32(s, e, a, b, c, fused):
     return np.where(miss0, MISS, np.where(hit, HIT, np.where(miss1, MISS, BAND)))
 
 
+def tri_certain_hit(s, e, a, b, c, fused):
+    """The verification's certain-hit test: the numerators' signs first,
+    then the same bounds as tri_fp32's hit branch."""
+    d, e1, e2, sv = e - s, b - a, c - a, s - a
+    p = _cross(d, e2, fused)
+    det = _dot(e1, p, fused)
+    q = _cross(sv, e1, fused)
+    T = _dot(e2, q, fused)
+    U, V = _dot(sv, p, fused), _dot(d, q, fused)
+    D = np.abs(det)
+    sg = np.where(det > 0, F32(1), F32(-1))
+    Us, Vs, Ts = sg * U, sg * V, sg * T
+    Ws = (D - Us) - Vs
+    Tms = D - Ts
+    signs = (Us > 0) & (Vs > 0) & (Ws > 0) & (Ts > 0) & (Tms > 0)
+    ad, ae1, ae2, asv = np.abs(d), np.abs(e1), np.abs(e2), np.abs(sv)
+    pa, qa = _cross(ad, ae2, fused, +1), _cross(asv, ae1, fused, +1)
+    errdet = kErrK * _dot(ae1, pa, fused) + F32(1e-35)
+    n1 = lambda x: (x[:, 0] + x[:, 1]) + x[:, 2]
+    dl1 = (ad[:, 0] + ad[:, 1]) + ad[:, 2]
+    thr = ((kTauHi * (dl1 * n1(ae1))) * n1(ae2)) * F32(1.000001)
+    sure = D - errdet > thr
+    errT = kErrK * _dot(ae2, qa, fused) + F32(1e-35)
+    errTm = (errT + errdet) + F32(2.0) * kU * (np.abs(T) + np.abs(det))
+    errU = kErrK * _dot(asv, pa, fused) + F32(1e-35)
+    errV = kErrK * _dot(ad, qa, fused) + F32(1e-35)
+    errW = ((errdet + errU) + errV) + F32(2.0) * kU * ((D + np.abs(U)) + np.abs(V))
+    lim = kTauHi * (D + errdet) * F32(1.000001)
+    return signs & sure & (Us - errU > lim) & (Vs - errV > lim) & (Ws - errW > lim) & (Ts - errT > lim) & (
+        Tms - errTm > lim)
+
+
 def _round_dir(exact, up):
     """float32 rounding of a float64 value toward +inf (up) or -inf."""
     r = exact.astype(F32)
@@ -234,6 +266,19 @@ def test_certain_fp32_decisions_are_fp64_decisions(pairs, fused):
     # the thresholds, yet thousands are still decided in FP32
     assert np.all(got[cls == AMB] == BAND)
     assert (got == HIT).sum() > 1000 and (got == MISS).sum() > 1000
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_verification_hits_are_the_traversals_certain_hits(pairs, fused):
+    """The learned query's verification test (sign test first) confirms
+    exactly the pairs the traversal's test calls certain hits, so every
+    hit it confirms is a decisive hit of the definition."""
+    S, E, A, B, C, cls, det_rel = pairs
+    with np.errstate(all="ignore"):
+        full = tri_fp32(S, E, A, B, C, fused)
+        quick = tri_certain_hit(S, E, A, B, C, fused)
+    assert np.array_equal(quick, full == HIT)
+    assert np.all(cls[quick] == HIT) and quick.sum() > 1000
 
 
 def test_hit_or_ambiguous_pairs_meet_the_widened_box(pairs):

@@ -37,13 +37,15 @@ def scene(rsi):
     return items, host
 
 
-@pytest.mark.parametrize("node_width", [2, 4])
+@pytest.mark.parametrize("node_width,tile,stack", [(2, 0, 0), (4, 0, 0), (2, 2048, 0), (4, 8192, 128),
+                                                   (2, 0, 64)])
 @pytest.mark.parametrize("mode", ["any_hit", "count"])
-def test_batched_equals_single_queries(rsi, scene, mode, node_width):
-    """The batched plan (child-pair or four-wide nodes) answers as the
-    single queries (child-pair by default) do."""
+def test_batched_equals_single_queries(rsi, scene, mode, node_width, tile, stack):
+    """The batched plan (child-pair or four-wide nodes, with or without the
+    in-tile reordering of each batch, any stack size) answers as the single
+    queries (child-pair by default) do."""
     items, host = scene
-    plan = rsi.BatchPlan(items, mode, node_width=node_width)
+    plan = rsi.BatchPlan(items, mode, node_width=node_width, ray_sort_tile=tile, stack=stack)
     for rep in range(2):   # the graph replays
         plan.run()
         torch.cuda.synchronize()
@@ -128,3 +130,54 @@ def test_bad_plans_rejected(rsi, scene):
     plan = rsi.BatchPlan(items[:2], "any_hit")
     with pytest.raises(rsi.RSIError):
         plan.post(10)   # not a streaming plan
+
+
+@pytest.mark.parametrize("mode", ["any_hit", "count"])
+def test_one_call_batched_query(rsi, scene, mode):
+    """rsi_query_batched(hs, n_meshes, batches, mode, opt, stream): the call
+    shape of the boundary.  The first call plans (and keeps the plan), the
+    second replays it; both answer as the single queries do.  A freed
+    hierarchy drops the kept plans that name it, and a new hierarchy --
+    possibly at the same address -- gets a plan of its own."""
+    items, host = scene
+    key = "hit" if mode == "any_hit" else "count"
+    refs = [bvh.query(f, t, mode) for bvh, f, t in items]
+    out = None
+    for rep in range(2):
+        out = rsi.query_batched(items, mode, hit=out["hit"] if out else None, count=out["count"] if out else None,
+                                ambiguous=out["ambiguous"] if out else None)
+        torch.cuda.synchronize()
+        for i, ref in enumerate(refs):
+            assert torch.equal(out[key][i], ref[key]), (rep, i)
+            assert torch.equal(out["ambiguous"][i], ref["ambiguous"]), (rep, i)
+    # a fresh hierarchy of mesh 0 in place of the first one: answers still right
+    mesh0, F0, E0 = host[0]
+    fresh = rsi.LBVH(torch.from_numpy(mesh0.vertices).cuda(), torch.from_numpy(mesh0.triangles).cuda())
+    items2 = [(fresh, items[0][1], items[0][2])] + items[1:]
+    out2 = rsi.query_batched(items2, mode)
+    torch.cuda.synchronize()
+    assert torch.equal(out2[key][0], refs[0][key])
+    fresh.close()   # drops the plan that names it; the next call plans again
+    fresh = rsi.LBVH(torch.from_numpy(mesh0.vertices).cuda(), torch.from_numpy(mesh0.triangles).cuda())
+    items3 = [(fresh, items[0][1], items[0][2])] + items[1:]
+    out3 = rsi.query_batched(items3, mode, hit=out2["hit"], count=out2["count"], ambiguous=out2["ambiguous"])
+    torch.cuda.synchronize()
+    for i, ref in enumerate(refs):
+        assert torch.equal(out3[key][i], ref[key]) and torch.equal(out3["ambiguous"][i], ref["ambiguous"]), i
+    fresh.close()
+
+
+def test_one_call_batched_query_rejections(rsi, scene):
+    import ctypes
+    items, _ = scene
+    bvh, f, t = items[0]
+    hs = (ctypes.c_void_p * 1)(bvh.handle.value)
+    other = items[1][0]
+    arr = (rsi.RayBatch * 1)()
+    arr[0] = rsi.RayBatch(other.handle.value, f.data_ptr(), t.data_ptr(), f.shape[0], None, None, None)
+    assert rsi.lib.rsi_query_batched(hs, 1, arr, rsi.RSI_ANY_HIT, None, None) == -1   # bvh neither NULL nor hs[0]
+    assert "bvh" in rsi.last_error()
+    opt = rsi.Options(0, 0, 0, 0, -1000)
+    arr[0] = rsi.RayBatch(None, f.data_ptr(), t.data_ptr(), 0, None, None, None)
+    assert rsi.lib.rsi_query_batched(hs, 1, arr, rsi.RSI_ANY_HIT, ctypes.byref(opt), None) == -1
+    assert "streaming" in rsi.last_error()

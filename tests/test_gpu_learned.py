@@ -173,14 +173,49 @@ def test_learned_query_equals_plain(rsi, c1, trained, n):
 
 
 def test_trained_proposal_gains(rsi, c1, trained):
-    """What the trained network buys: the share of hits it confirms without a
-    tree search, against an untrained network's."""
+    """What the trained network buys against the method without it: the
+    tree search it avoids (node fetches of the plain query vs those of the
+    learned query's fallback), and against an untrained network the share
+    of hits it settles without a tree search."""
     mesh, bvh, _, _ = c1
     F, E = W.rays(W.RaySpec("uniform_box", 100_000, seed=13), mesh)
     dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
-    hits = int(bvh.query(dF, dE, "any_hit")["hit"].sum())
-    good = rsi.query_learned(bvh, trained[0], dF, dE, stats=True)["stats"]["proposal_confirmed"]
-    rand = rsi.query_learned(bvh, rsi.MLP(98), dF, dE, stats=True)["stats"]["proposal_confirmed"]
+    plain = bvh.query(dF, dE, "any_hit", stats=True)
+    hits = int(plain["hit"].sum())
+    good = rsi.query_learned(bvh, trained[0], dF, dE, stats=True)["stats"]
+    rand = rsi.query_learned(bvh, rsi.MLP(98), dF, dE, stats=True)["stats"]
     # a short training run (about 200 steps) already settles several times
-    # more hits without a tree search than an untrained network does
-    assert good > 0.2 * hits and good > 5 * rand, (good, rand, hits)
+    # more hits without a tree search than an untrained network does ...
+    assert good["proposal_confirmed"] > 0.2 * hits, (good, hits)
+    assert good["proposal_confirmed"] > 5 * rand["proposal_confirmed"], (good, rand)
+    # ... and every settled segment is a tree search not made
+    assert good["node_visits"] < 0.9 * plain["stats"]["node_visits"], (good, plain["stats"])
+    assert good["node_visits"] < rand["node_visits"]
+
+
+def test_attached_network_answers_rsi_query(rsi, c1, trained):
+    """rsi_mlp_attach: boolean rsi_query calls on the hierarchy go through
+    the learned proposal (its counters show it) with the plain answers;
+    detaching, or freeing the network, brings back the plain query."""
+    mesh, _, _, _ = c1
+    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).cuda(), torch.from_numpy(mesh.triangles).cuda())
+    F, E = W.rays(W.RaySpec("uniform_box", 30_000, seed=14), mesh)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    plain = bvh.query(dF, dE, "any_hit", stats=True)
+    assert plain["stats"]["proposal_confirmed"] == 0
+    bvh.attach(trained[0])
+    got = bvh.query(dF, dE, "any_hit", stats=True)
+    assert torch.equal(got["hit"], plain["hit"]) and torch.equal(got["ambiguous"], plain["ambiguous"])
+    assert got["stats"]["proposal_confirmed"] > 0
+    cnt = bvh.query(dF, dE, "count", stats=True)          # other modes: unaffected
+    assert cnt["stats"]["proposal_confirmed"] == 0
+    bvh.attach(None)
+    again = bvh.query(dF, dE, "any_hit", stats=True)
+    assert again["stats"]["proposal_confirmed"] == 0 and torch.equal(again["hit"], plain["hit"])
+    temp = rsi.MLP(5)
+    bvh.attach(temp)
+    bvh._net = None          # the binding's reference dropped: freeing the network detaches it
+    temp.close()
+    after = bvh.query(dF, dE, "any_hit", stats=True)
+    assert after["stats"]["proposal_confirmed"] == 0 and torch.equal(after["hit"], plain["hit"])
+    bvh.close()

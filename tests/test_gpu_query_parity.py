@@ -410,3 +410,49 @@ def test_fp32_decisions_equal_fp64_everywhere(rsi, cfg, n):
     assert torch.equal(torch.nan_to_num(a["point"], nan=-7.0), torch.nan_to_num(b["point"], nan=-7.0))
     with pytest.raises(rsi.RSIError):
         bvh.query(dF[:10], dE[:10], "any_hit", fp64_all=True, fp32_only=True)
+
+
+@pytest.mark.parametrize("stack", [64, 128])
+def test_stack_size_leaves_answers_unchanged(rsi, stack):
+    """A larger traversal stack than the tree needs (a tuning choice) gives
+    the same answers in both modes; sizes other than 0/32/64/128 are refused."""
+    m = W.config_mesh("c1")
+    F, E = W.rays(W.config_rays("c1", 50_000), m)
+    bvh = rsi.LBVH(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda())
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    for mode, key in (("any_hit", "hit"), ("count", "count")):
+        a, b = bvh.query(dF, dE, mode), bvh.query(dF, dE, mode, stack=stack)
+        assert torch.equal(a[key], b[key]) and torch.equal(a["ambiguous"], b["ambiguous"])
+    with pytest.raises(rsi.RSIError):
+        bvh.query(dF, dE, "any_hit", stack=48)
+    bvh.close()
+
+
+def test_segment_order_is_a_permutation_and_keeps_answers(rsi):
+    """rsi_segment_order writes a permutation of the batch sorted by midpoint
+    cell; queries walking the segments in that order give the answers of
+    the input order at the segments' own indices, in all three modes."""
+    m = W.config_mesh("c2")
+    n = 300_007
+    F, E = W.rays(W.config_rays("c2", n), m)
+    bvh = rsi.LBVH(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda())
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    order = bvh.segment_order(dF, dE)
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(n))
+    # cells are non-decreasing along the order (32^3 grid over the extent, z-order)
+    info = bvh.info()
+    lo, hi = np.array(info["extent_lo"], np.float32), np.array(info["extent_hi"], np.float32)
+    mid = (F[o] + E[o]) * np.float32(0.5)
+    q = np.clip(((mid - lo) * (np.float32(32.0) / (hi - lo))).astype(np.float32), 0, 31).astype(np.int64)
+    key = np.zeros(n, np.int64)
+    for b in range(5):
+        for a in range(3):
+            key |= ((q[:, a] >> b) & 1) << (3 * b + a)
+    assert np.all(np.diff(key) >= 0)
+    for mode, k in (("any_hit", "hit"), ("count", "count")):
+        a, b = bvh.query(dF, dE, mode), bvh.query(dF, dE, mode, order=order)
+        assert torch.equal(a[k], b[k]) and torch.equal(a["ambiguous"], b["ambiguous"]), mode
+    with pytest.raises(rsi.RSIError):
+        bvh.query(dF, dE, "any_hit", order=order, ray_sort_tile=2048)
+    bvh.close()

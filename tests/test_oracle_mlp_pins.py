@@ -29,7 +29,16 @@ def test_gelu_closed_forms():
     assert mlp.gelu(np.array([0.0]))[0] == 0.0
     assert abs(mlp.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
     assert abs(mlp.gelu(np.array([-10.0]))[0]) < 1e-12
-    assert abs(mlp.gelu(np.array([1.0]))[0] - 0.5 * (1 + math.erf(1 / math.sqrt(2)))) < 1e-15
+    # z = 1: tanh(sqrt(2/pi) * 1.044715) = 0.6823..., GELU(1) = 0.8411920...
+    assert abs(mlp.gelu(np.array([1.0]))[0] - 0.84119199) < 1e-8
+    # GELU(-z) = GELU(z) - z (Phi(-z) = 1 - Phi(z); the tanh form keeps it)
+    z = np.linspace(-5, 5, 101)
+    assert np.allclose(mlp.gelu(-z), mlp.gelu(z) - z, atol=1e-15)
+    # the tanh form stays within 4.8e-4 of the definition z Phi(z) (erf)
+    zz = np.linspace(-8, 8, 16001)
+    exact = 0.5 * zz * (1 + np.array([math.erf(v / math.sqrt(2)) for v in zz]))
+    gap = np.abs(mlp.gelu(zz) - exact)
+    assert gap.max() < 4.8e-4 and gap.max() > 4.0e-4
     z = np.linspace(-3, 3, 13)
     h = 1e-6
     fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
@@ -47,11 +56,11 @@ def test_forward_matches_per_sample_loop():
         a1 = []
         for j in range(mlp.D_H):
             z = sum(a0[k] * W1[k, j] for k in range(mlp.D_PAD)) + p["b1"][j]
-            a1.append(float(mlp.bf16_round(0.5 * z * (1 + math.erf(z / math.sqrt(2))))))
+            a1.append(float(mlp.bf16_round(0.5 * z * (1 + math.tanh(math.sqrt(2 / math.pi) * (z + 0.044715 * z ** 3))))))
         a2 = []
         for j in range(mlp.D_H):
             z = sum(a1[k] * W2[k, j] for k in range(mlp.D_H)) + p["b2"][j]
-            a2.append(float(mlp.bf16_round(0.5 * z * (1 + math.erf(z / math.sqrt(2))))))
+            a2.append(float(mlp.bf16_round(0.5 * z * (1 + math.tanh(math.sqrt(2 / math.pi) * (z + 0.044715 * z ** 3))))))
         for j in range(0, mlp.D_OUT, 37):
             z = sum(a2[k] * W3[k, j] for k in range(mlp.D_H)) + p["b3"][j]
             assert abs(z - logits[i, j]) < 1e-9

@@ -85,8 +85,12 @@ MUTANTS = [
     # proposal network reference
     ("bf16 keeps 7 bits", M, "np.round(m * 256.0), e - 8", "np.round(m * 128.0), e - 7"),
     ("bf16 truncates", M, "np.round(m * 256.0)", "np.trunc(m * 256.0)"),
-    ("gelu scale", M, "return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))", "return 0.5 * z * (1.0 + erf(z / 2.0))"),
-    ("gelu gradient drops the density", M, "+ z * np.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)", ""),
+    ("gelu scale", M, "return 0.5 * z * (1.0 + np.tanh(GELU_C * (z + GELU_A * z ** 3)))",
+     "return 0.5 * z * (1.0 + np.tanh(0.5 * (z + GELU_A * z ** 3)))"),
+    ("gelu drops the cubic term", M, "return 0.5 * z * (1.0 + np.tanh(GELU_C * (z + GELU_A * z ** 3)))",
+     "return 0.5 * z * (1.0 + np.tanh(GELU_C * z))"),
+    ("gelu gradient drops the tanh slope", M, "+ 0.5 * z * (1.0 - t * t) * GELU_C * (1.0 + 3.0 * GELU_A * z * z)", ""),
+    ("gelu gradient drops the cubic slope", M, "* GELU_C * (1.0 + 3.0 * GELU_A * z * z)", "* GELU_C"),
     ("features not centred", M, "f = np.clip(2.0 * f - 1.0, -4.0, 4.0)", "f = np.clip(f, -4.0, 4.0)"),
     ("forward drops a bias", M, 'z2 = a1 @ W2 + p["b2"]', "z2 = a1 @ W2"),
     ("forward keeps a hidden layer unrounded", M, "a1 = bf16_round(gelu(z1))", "a1 = gelu(z1)"),
