@@ -8,10 +8,13 @@ it, length U(0.05, 1), random directions -- seeded synthetic data standing in
 for the paper's unavailable generator.
 
 One step = the whole hot path on one batch: GPU build of the hierarchy
-(extent, Morton codes, radix sort, radix tree, refit) + the boolean query +
-the intercept_count query of every segment (FP32 traversal with the FP64
-re-test of band segments).  value = segments fully answered (both modes) per
-second, summed over ranks.  The segments (240 MB) exceed the 129 MB L2, so no
+(extent, Morton codes, radix sort, radix tree, refit) + the boolean and the
+intercept_count answer of every segment (FP32 traversal with the FP64
+re-test of band segments).  The count pass yields the boolean answer too
+(hit = count > 0; the boolean-mode ambiguity flag from the same pass), so
+one traversal answers both modes (RSI_BOTH); the line also reports the step
+with the two modes queried separately.  value = segments fully answered
+(both modes) per second, summed over ranks.  The segments (240 MB) exceed the 129 MB L2, so no
 flush is needed between steps.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (a
@@ -35,7 +38,8 @@ sys.path.insert(0, ROOT)
 METRIC = "rays/s (exact vs FP64 oracle) plain vs batched+learned on 1 GB300; % roofline"
 WORKLOAD = ("c2: 100x100-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (19,602 FP32 triangles); "
             "1e7 FP32 segments, 50% crossing / 50% above, length U(0.05,1), random directions; "
-            "step = lbvh_build + boolean query + intercept_count query")
+            "step = lbvh_build + the boolean and intercept_count answers of every segment "
+            "(one traversal answers both: rsi_query mode RSI_BOTH)")
 W_DOC_PAPER = ("paper scale: 111x134-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (14,874 vertices, "
                "29,260 triangles, the paper's counts); 1e7 segments, 50% crossing / 50% above")
 BYTES_PER_RAY_COUNT = 28   # 24 B of segment in + 4 B of count out (algorithmic)
@@ -554,12 +558,11 @@ def measure_precision_c3(rsi, torch, dev, c3, args):
     pT = torch.from_numpy(mesh.triangles).pin_memory()
     pF, pE = torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory()
     hh, ha = torch.empty(n, dtype=torch.uint8).pin_memory(), torch.empty(n, dtype=torch.uint8).pin_memory()
-    hc, hac = torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.uint8).pin_memory()
+    hc = torch.empty(n, dtype=torch.int32).pin_memory()
 
     def step_e2e():
         b = rsi.LBVH(pV, pT, morton_bits=63)
-        b.query_host(pF, pE, "any_hit", hit=hh, ambiguous=ha)
-        b.query_host(pF, pE, "count", count=hc, ambiguous=hac)
+        b.query_host(pF, pE, "both", hit=hh, count=hc, ambiguous=ha)
         b.close()
     step_e2e()
     t0 = time.perf_counter()
@@ -567,13 +570,16 @@ def measure_precision_c3(rsi, torch, dev, c3, args):
         step_e2e()
     e2e_ms = 1e3 * (time.perf_counter() - t0) / 3
     same = bool(np.array_equal(hh.numpy(), res["any_hit_fp64_retest"][0])
-                and np.array_equal(hc.numpy(), res["count_fp64_retest"][0]))
+                and np.array_equal(hc.numpy(), res["count_fp64_retest"][0])
+                and np.array_equal(ha.numpy() & 1, res["any_hit_fp64_retest"][1])
+                and np.array_equal(ha.numpy() >> 1, res["count_fp64_retest"][1]))
     out["e2e"] = {"value": n / (e2e_ms / 1e3), "unit": "rays/s",
-                  "h2d_bytes_per_step": pV.numel() * 4 + pT.numel() * 4 + 2 * (pF.numel() + pE.numel()) * 4,
-                  "d2h_bytes_per_step": n * (1 + 1) + n * (4 + 1), "ms_per_step": e2e_ms,
-                  "step": "host mesh -> build -> boolean + intercept_count queries of host segments -> host results",
+                  "h2d_bytes_per_step": pV.numel() * 4 + pT.numel() * 4 + (pF.numel() + pE.numel()) * 4,
+                  "d2h_bytes_per_step": n * (1 + 4 + 1), "ms_per_step": e2e_ms,
+                  "step": "host mesh -> build -> boolean and intercept_count answers of the host segments in one "
+                          "pass (RSI_BOTH) -> host results",
                   "matches_device_results": same}
-    del pF, pE, hh, ha, hc, hac
+    del pF, pE, hh, ha, hc
     rng = np.random.default_rng(31)
     checked = {}
     for mode in ("any_hit", "count"):
@@ -707,6 +713,8 @@ def main():
     ap.add_argument("--c3-check", type=int, default=20_000)
     ap.add_argument("--learned-rays", type=int, default=100_000_000)
     ap.add_argument("--train-rays", type=int, default=10_000_000)
+    ap.add_argument("--order", action="store_true",
+                    help="walk the segments in midpoint-cell order in the timed step (rsi_segment_order inside it)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local, pg = dist_setup(args)
@@ -758,7 +766,26 @@ def main():
     amb_c = torch.empty(n, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    amb2 = torch.empty(n, dtype=torch.uint8, device=dev)
+    step_order = torch.empty(n, dtype=torch.int32, device=dev) if args.order else None
+
     def step(evs=None, trav=None):
+        if evs:
+            evs[0].record(stream)
+        bvh = rsi.LBVH(dV, dT, morton_bits=30)
+        if evs:
+            evs[1].record(stream)
+        if step_order is not None:
+            bvh.segment_order(dF, dE, out=step_order)
+        bvh.query(dF, dE, "both", hit=hit, count=cnt, ambiguous=amb2, time_kernels=trav is not None,
+                  order=step_order)
+        if evs:
+            evs[2].record(stream)
+        if trav is not None:
+            trav.append(bvh.last_query_ms()[0])
+        bvh.close()
+
+    def step_separate(evs=None):
         if evs:
             evs[0].record(stream)
         bvh = rsi.LBVH(dV, dT, morton_bits=30)
@@ -767,11 +794,9 @@ def main():
         bvh.query(dF, dE, "any_hit", hit=hit, ambiguous=amb_h)
         if evs:
             evs[2].record(stream)
-        bvh.query(dF, dE, "count", count=cnt, ambiguous=amb_c, time_kernels=trav is not None)
+        bvh.query(dF, dE, "count", count=cnt, ambiguous=amb_c)
         if evs:
             evs[3].record(stream)
-        if trav is not None:
-            trav.append(bvh.last_query_ms()[0])
         bvh.close()
 
     def barrier():
@@ -787,7 +812,7 @@ def main():
         step()
     barrier()
     n_ev = args.steps
-    phase = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_ev)]
+    phase = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_ev)]
     trav = []
     l0 = rsi.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -802,21 +827,38 @@ def main():
     ms = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps, dev)
     value = ws * n / (ms / 1e3)
     build_ms = statistics.median(p[0].elapsed_time(p[1]) for p in phase)
-    any_ms = statistics.median(p[1].elapsed_time(p[2]) for p in phase)
-    count_ms = statistics.median(p[2].elapsed_time(p[3]) for p in phase)
+    both_ms = statistics.median(p[1].elapsed_time(p[2]) for p in phase)
     trav_ms = statistics.mean(trav)
+    # the same step with the two modes queried separately (context): the
+    # answers must be those of the combined pass
+    for _ in range(3):
+        step_separate()
+    sep = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        step_separate(sep[k])
+    torch.cuda.synchronize()
+    separate = {"step_ms": statistics.median(p[0].elapsed_time(p[3]) for p in sep),
+                "any_hit_query_ms": statistics.median(p[1].elapsed_time(p[2]) for p in sep),
+                "count_query_ms": statistics.median(p[2].elapsed_time(p[3]) for p in sep)}
+    bvh = rsi.LBVH(dV, dT, morton_bits=30)
+    bvh.query(dF, dE, "both", hit=hit, count=cnt, ambiguous=amb2)
+    both_hit, both_cnt, both_amb = hit.clone(), cnt.clone(), amb2.clone()
+    bvh.query(dF, dE, "any_hit", hit=hit, ambiguous=amb_h)
+    bvh.query(dF, dE, "count", count=cnt, ambiguous=amb_c)
+    separate["answers_equal_combined_pass"] = bool(
+        torch.equal(both_hit, hit) and torch.equal(both_cnt, cnt) and torch.equal(both_amb & 1, amb_h)
+        and torch.equal(both_amb >> 1, amb_c))
+    bvh.close()
 
     # end to end through the host-buffer C-ABI calls: mesh and segments in
     # pinned host memory, results back in pinned host memory, every step
     hh = torch.empty(n, dtype=torch.uint8).pin_memory()
     ha = torch.empty(n, dtype=torch.uint8).pin_memory()
     hc = torch.empty(n, dtype=torch.int32).pin_memory()
-    hac = torch.empty(n, dtype=torch.uint8).pin_memory()
 
     def step_e2e():
         bvh = rsi.LBVH(pV, pT, morton_bits=30)
-        bvh.query_host(pF, pE, "any_hit", hit=hh, ambiguous=ha)
-        bvh.query_host(pF, pE, "count", count=hc, ambiguous=hac)
+        bvh.query_host(pF, pE, "both", hit=hh, count=hc, ambiguous=ha)
         bvh.close()
 
     for _ in range(args.warmup):
@@ -827,9 +869,10 @@ def main():
         step_e2e()
     barrier()
     e2e_ms = max_over_ranks(pg, 1e3 * (time.perf_counter() - t0) / args.steps, dev)
-    same = bool(torch.equal(hh, hit.cpu()) and torch.equal(hc, cnt.cpu()))
-    h2d = (pV.numel() * 4 + pT.numel() * 4) + 2 * (pF.numel() + pE.numel()) * 4
-    d2h = n * (1 + 1) + n * (4 + 1)
+    same = bool(torch.equal(hh, both_hit.cpu()) and torch.equal(hc, both_cnt.cpu())
+                and torch.equal(ha, both_amb.cpu()))
+    h2d = (pV.numel() * 4 + pT.numel() * 4) + (pF.numel() + pE.numel()) * 4
+    d2h = n * (1 + 4 + 1)
 
     # counters of one extra (untimed) pass
     bvh = rsi.LBVH(dV, dT)
@@ -875,8 +918,7 @@ def main():
     def step_ordered():
         b = rsi.LBVH(dV, dT, morton_bits=30)
         b.segment_order(dF, dE, out=order)
-        b.query(dF, dE, "any_hit", hit=hit, ambiguous=amb_h, order=order)
-        b.query(dF, dE, "count", count=cnt, ambiguous=amb_c, order=order)
+        b.query(dF, dE, "both", hit=hit, count=cnt, ambiguous=amb2, order=order)
         b.close()
     for _ in range(3):
         step_ordered()
@@ -900,6 +942,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_triangles": int(len(mesh.triangles)), "rays_per_gpu": n,
                    "morton_bits": 30, "l2": "inputs larger than L2 (240 MB of segments per batch), no flush",
+                   "segment_order": bool(args.order),
                    "fp64_retest": "on (band segments re-tested in FP64)"},
         "roofline": {"kernel": "k_query_fp32<count> (FP32 traversal, intercept_count)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -912,8 +955,11 @@ def main():
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "matches_device_results": same},
         "gpu_launches": launches,
         "clocks": clocks,
-        "phases_ms": {"build": build_ms, "any_hit_query": any_ms, "count_query": count_ms},
-        "query_rays_per_s": {"any_hit": n / (any_ms / 1e3), "count": n / (count_ms / 1e3)},
+        "phases_ms": {"build": build_ms, "both_modes_query": both_ms},
+        "query_rays_per_s": {"both_modes": n / (both_ms / 1e3),
+                             "any_hit_alone": n / (separate["any_hit_query_ms"] / 1e3),
+                             "count_alone": n / (separate["count_query_ms"] / 1e3)},
+        "separate_queries": separate,
         "counters": {"tree_height": height, "node_visits_per_ray_count": st_c["node_visits"] / n,
                      "tri_tests_per_ray_count": st_c["tri_tests"] / n, "band_rays_count": st_c["band_rays"],
                      "ambiguous_count": st_c["ambiguous"], "node_visits_per_ray_any": st_a["node_visits"] / n,

@@ -61,6 +61,7 @@ extern "C" {
 #define RSI_ANY_HIT 0 /* "boolean": does the segment meet the surface       */
 #define RSI_COUNT 1   /* "intercept_count": number of distinct crossings    */
 #define RSI_NEAREST 2 /* "barycentric": nearest crossing (rsi_query_nearest) */
+#define RSI_BOTH 3    /* boolean and intercept_count answers from one pass    */
 
 typedef struct rsi_bvh_s* rsi_bvh_t;
 typedef struct rsi_mlp_s* rsi_mlp_t;
@@ -237,17 +238,25 @@ size_t lbvh_node_bytes(void);
  *   mode RSI_ANY_HIT: d_hit[i] = 1 if segment i meets the surface, else 0.
  *   mode RSI_COUNT  : d_count[i] = number of distinct crossings; d_hit, if
  *                     not NULL, gets count > 0.
+ *   mode RSI_BOTH   : both answers from one traversal (the count pass):
+ *                     d_count as RSI_COUNT and d_hit (required) the boolean
+ *                     answer, which is count > 0; d_ambiguous gets bit 0 =
+ *                     the boolean mode's flag, bit 1 = the count mode's.
+ *                     Every value equals what the two separate queries
+ *                     write.
  *   d_ambiguous (optional): 1 where the segment lies within the 1e-6
  *   relative margin band even in FP64 (an end point, edge or vertex on the
  *   surface, or nearly parallel and touching); those results are the
  *   closed-interval reading with crossings closer than 1e-9 in t merged.
+ *   In the boolean mode a decisive hit settles a segment whatever its other
+ *   pairs are, so fewer segments are flagged than in the count mode.
  * Segments: d_from, d_to [n_rays][3] float32, device.  n_rays == 0 is a
  * no-op.  Asynchronous unless `stats` is given.  The handle grows its
  * scratch (the FP64 re-test's queue and pair lists, about 22 B per segment
  * of the largest batch queried so far) on demand; lbvh_free releases it.
  */
 /* Errors: RSI_ERR_INVALID_ARG for a NULL handle or segment pointer, n_rays
- * outside [0, 2^31), a mode other than the two above, the output the mode
+ * outside [0, 2^31), a mode other than the three above, the output the mode
  * writes missing, or option values out of range; RSI_ERR_OOM when the
  * scratch cannot grow; RSI_ERR_STACK for a tree of height 127 or more
  * (a Karras tree over n < 2^30 leaves is at most 63 + 30 high); RSI_ERR_CUDA

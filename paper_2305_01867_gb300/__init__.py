@@ -20,7 +20,7 @@ from .build import LIB as _LIB_PATH
 from .build import build as build_library
 
 RSI_OK = 0
-RSI_ANY_HIT, RSI_COUNT, RSI_NEAREST = 0, 1, 2
+RSI_ANY_HIT, RSI_COUNT, RSI_NEAREST, RSI_BOTH = 0, 1, 2, 3
 NOALLOC_MAX_RAYS = 1 << 21   # RSI_NOALLOC_MAX_RAYS of include/rsi.h
 LEAF_TAG = 0x80000000
 ERRORS = {-1: "INVALID_ARG", -2: "DTYPE", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "STACK", -7: "NAN",
@@ -235,6 +235,8 @@ def _mode(mode):
         return RSI_ANY_HIT
     if mode in ("count", "intercept_count", RSI_COUNT):
         return RSI_COUNT
+    if mode in ("both", RSI_BOTH):
+        return RSI_BOTH
     raise ValueError(f"unknown mode {mode!r}")
 
 
@@ -364,9 +366,11 @@ class LBVH:
     def query(self, ray_from, ray_to, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0,
               stats=False, hit=None, count=None, ambiguous=None, want_ambiguous=True, time_kernels=False,
               ray_sort_tile=0, node_width=0, fp64_all=False, stack=0, order=None, stream=None):
-        """Query segments (device tensors [n, 3] float32).  Returns a dict with
-        'hit' (uint8, any-hit mode or count > 0), 'count' (int32, count mode),
-        'ambiguous' (uint8) and, with stats=True, 'stats'."""
+        """Query segments (device tensors [n, 3] float32).  mode: "any_hit",
+        "count" or "both" (one pass answering both; 'ambiguous' then holds
+        bit 0 = the boolean mode's flag, bit 1 = the count mode's).  Returns
+        a dict with 'hit' (uint8, any-hit answer or count > 0), 'count'
+        (int32), 'ambiguous' (uint8) and, with stats=True, 'stats'."""
         import torch
         _check_f32x3(ray_from, "ray_from")
         _check_f32x3(ray_to, "ray_to")
@@ -377,9 +381,9 @@ class LBVH:
         m = _mode(mode)
         n = ray_from.shape[0]
         dev = ray_from.device
-        if hit is None and m == RSI_ANY_HIT:
+        if hit is None and m in (RSI_ANY_HIT, RSI_BOTH):
             hit = torch.empty(n, dtype=torch.uint8, device=dev)
-        if count is None and m == RSI_COUNT:
+        if count is None and m in (RSI_COUNT, RSI_BOTH):
             count = torch.empty(n, dtype=torch.int32, device=dev)
         if ambiguous is None and want_ambiguous:
             ambiguous = torch.empty(n, dtype=torch.uint8, device=dev)
@@ -413,9 +417,9 @@ class LBVH:
             raise TypeError("query_host() takes host tensors; use query() for device tensors")
         m = _mode(mode)
         n = ray_from.shape[0]
-        if hit is None and m == RSI_ANY_HIT:
+        if hit is None and m in (RSI_ANY_HIT, RSI_BOTH):
             hit = torch.empty(n, dtype=torch.uint8)
-        if count is None and m == RSI_COUNT:
+        if count is None and m in (RSI_COUNT, RSI_BOTH):
             count = torch.empty(n, dtype=torch.int32)
         if ambiguous is None and want_ambiguous:
             ambiguous = torch.empty(n, dtype=torch.uint8)

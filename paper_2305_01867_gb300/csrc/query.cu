@@ -53,6 +53,7 @@ struct QueryArgs {
     DevCounters* ctr;
     float dmax0, dmax1, dmax2;
     int fp32_only;
+    int amb_bits;          // RSI_BOTH (count pass): amb = boolean-mode flag | count-mode flag << 1
 };
 
 // One (hierarchy, segment batch, outputs) triple of a batched query.
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
                         if (hit) hit[r] = 0;
                         if (MODE == RSI_COUNT) count[r] = 0;
                         if (MODE == RSI_NEAREST) A.near[r] = -1;
-                        if (amb) amb[r] = 1;
+                        if (amb) amb[r] = A.amb_bits ? 3 : 1;
                         ray = -1;
                     } else {
                         g = make_seg(s, e, dm0, dm1, dm2);
@@ -606,6 +607,16 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
 }
 
 // [traversal kernel: end]
+
+// Ambiguity byte of a count-mode result.  In RSI_BOTH the count pass also
+// answers the boolean mode: its hit flag (count > 0) is the boolean answer,
+// and a segment is ambiguous for the boolean mode when it is for the count
+// mode and no pair is a decisive hit (a decisive hit settles the boolean
+// answer alone); bit 0 carries that flag, bit 1 the count mode's.
+__device__ __forceinline__ uint8_t both_modes_amb(int amb_bits, bool amb, int n_decisive_hits) {
+    if (!amb_bits) return (uint8_t)amb;
+    return (uint8_t)((amb ? 2 : 0) | (amb && n_decisive_hits == 0 ? 1 : 0));
+}
 
 // Certain decisions in FP64 without square roots or divisions: the FP32 test
 // above in double precision, with the bound factor 32 u (u = 2^-53) and a
@@ -836,7 +847,7 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B, co
                 }
                 Q.count[r] = count;
                 if (Q.hit) Q.hit[r] = (uint8_t)(count > 0);
-                if (Q.amb) Q.amb[r] = (uint8_t)amb;
+                if (Q.amb) Q.amb[r] = both_modes_amb(A.amb_bits, amb, n_hit);
             }
         }
         __syncwarp();
@@ -1206,7 +1217,7 @@ __global__ void __launch_bounds__(128) k_band_reduce(QueryArgs A, BatchArgs B, P
             }
             Q.count[r] = count;
             if (Q.hit) Q.hit[r] = (uint8_t)(count > 0);
-            if (Q.amb) Q.amb[r] = (uint8_t)amb;
+            if (Q.amb) Q.amb[r] = both_modes_amb(A.amb_bits, amb, n_hit);
         }
     }
 }
@@ -1856,6 +1867,8 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     rsi_options o = {};
     if (opt) o = *opt;
     if (h->height >= 127) return fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
+    const bool both = mode == RSI_BOTH;   // the count pass, which also answers the boolean mode
+    if (both) mode = RSI_COUNT;
     QueryArgs A;
     A.nodes = h->nodes;
     A.nodes4 = h->nodes4;
@@ -1877,6 +1890,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     A.dmax1 = h->dmax[1];
     A.dmax2 = h->dmax[2];
     A.fp32_only = o.fp32_only;
+    A.amb_bits = both ? 1 : 0;
     if (o.block != 0 && (o.block < 32 || o.block > 256 || o.block % 32 != 0))
         return fail(RSI_ERR_INVALID_ARG, "rsi_query: block must be a multiple of 32 in [32, 256]");
     if (o.blocks_per_sm < 0) return fail(RSI_ERR_INVALID_ARG, "rsi_query: blocks_per_sm < 0");
@@ -2063,10 +2077,11 @@ static int check_query_args(const char* fn, rsi_bvh_t h, const void* from, const
     const std::string f(fn);
     if (!h) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": NULL handle");
     if (n < 0 || n > 0x7FFFFFFFll) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": need 0 <= n_rays < 2^31");
-    if (mode != RSI_ANY_HIT && mode != RSI_COUNT) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": bad mode");
+    if (mode != RSI_ANY_HIT && mode != RSI_COUNT && mode != RSI_BOTH)
+        return rsi::fail(RSI_ERR_INVALID_ARG, f + ": bad mode");
     if (n > 0 && (!from || !to)) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": NULL segment pointer");
-    if (n > 0 && mode == RSI_ANY_HIT && !hit) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": any-hit needs hit");
-    if (n > 0 && mode == RSI_COUNT && !count) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": count needs count");
+    if (n > 0 && mode != RSI_COUNT && !hit) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": any-hit needs hit");
+    if (n > 0 && mode != RSI_ANY_HIT && !count) return rsi::fail(RSI_ERR_INVALID_ARG, f + ": count needs count");
     return RSI_OK;
 }
 
@@ -2286,6 +2301,9 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     A.n_tri = h->n_tri;
     A.from = df;
     A.to = dt;
+    const bool both = mode == RSI_BOTH;   // the count pass, which also answers the boolean mode
+    if (both) mode = RSI_COUNT;
+    A.amb_bits = both ? 1 : 0;
     A.hit = h_hit ? dh : nullptr;
     A.count = mode == RSI_COUNT ? dc : nullptr;
     A.amb = h_amb ? da : nullptr;
@@ -2391,7 +2409,7 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
             break;
         }
         const rsi::PairScratch P = rsi::handle_pairs(h);
-        rc = rsi::query_device(h, df, dt, m, mode, opt, h_hit ? dh : nullptr, mode == RSI_COUNT ? dc : nullptr,
+        rc = rsi::query_device(h, df, dt, m, mode, opt, h_hit ? dh : nullptr, mode != RSI_ANY_HIT ? dc : nullptr,
                                h_ambiguous ? da : nullptr, h->band_ids, h->band_ids + h->band_cap, h->ctr, s, nullptr,
                                nullptr, nullptr, &P);
         if (rc) break;
@@ -2401,7 +2419,7 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
         if (e == cudaSuccess && h_hit) e = cudaMemcpyAsync(h_hit + r0, dh, (size_t)m, cudaMemcpyDeviceToHost, c->st_out);
         if (e == cudaSuccess && h_ambiguous)
             e = cudaMemcpyAsync(h_ambiguous + r0, da, (size_t)m, cudaMemcpyDeviceToHost, c->st_out);
-        if (e == cudaSuccess && mode == RSI_COUNT)
+        if (e == cudaSuccess && mode != RSI_ANY_HIT)
             e = cudaMemcpyAsync(h_count + r0, dc, 4 * (size_t)m, cudaMemcpyDeviceToHost, c->st_out);
         if (e == cudaSuccess) e = cudaEventRecord(c->ev_out[b], c->st_out);
         if (e != cudaSuccess) rc = rsi::cuda_fail(e, "rsi_query_host copy out");

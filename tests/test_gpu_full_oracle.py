@@ -37,10 +37,13 @@ def test_c2_every_segment(rsi):
     dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
     a = bvh.query(dF, dE, "any_hit")
     c = bvh.query(dF, dE, "count")
+    b = bvh.query(dF, dE, "both")
     nr = bvh.nearest(dF, dE)
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in (("hit", a["hit"]), ("amb_hit", a["ambiguous"]),
                                             ("count", c["count"]), ("amb_count", c["ambiguous"]),
+                                            ("both_hit", b["hit"]), ("both_count", b["count"]),
+                                            ("both_amb", b["ambiguous"]),
                                             ("near_tri", nr["tri"]), ("near_t", nr["t"]),
                                             ("near_point", nr["point"]), ("near_dist", nr["dist"]))}
     bvh.close()
@@ -50,6 +53,10 @@ def test_c2_every_segment(rsi):
     ok_h, ok_c = ref["amb_hit"] == 0, ref["amb_count"] == 0
     assert np.array_equal(got["hit"][ok_h], ref["hit"][ok_h])
     assert np.array_equal(got["count"][ok_c], ref["count"][ok_c])
+    # the combined pass (RSI_BOTH): both answers and both flags from one traversal
+    assert np.array_equal(got["both_amb"] & 1, ref["amb_hit"]) and np.array_equal(got["both_amb"] >> 1, ref["amb_count"])
+    assert np.array_equal(got["both_hit"][ok_h], ref["hit"][ok_h])
+    assert np.array_equal(got["both_count"][ok_c], ref["count"][ok_c])
     assert np.array_equal(got["near_tri"], ref["near_tri"])
     hit = ref["near_tri"] >= 0
     for k in ("near_t", "near_dist"):

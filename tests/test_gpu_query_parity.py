@@ -456,3 +456,54 @@ def test_segment_order_is_a_permutation_and_keeps_answers(rsi):
     with pytest.raises(rsi.RSIError):
         bvh.query(dF, dE, "any_hit", order=order, ray_sort_tile=2048)
     bvh.close()
+
+
+def _both_matches(rsi, bvh, dF, dE):
+    """RSI_BOTH against the two separate queries on every segment: the hit
+    flag is the boolean answer, the count the count answer, and the
+    ambiguity byte carries both modes' flags (bit 0 boolean, bit 1 count)."""
+    a = bvh.query(dF, dE, "any_hit")
+    c = bvh.query(dF, dE, "count")
+    b = bvh.query(dF, dE, "both")
+    assert torch.equal(b["hit"], a["hit"])
+    assert torch.equal(b["count"], c["count"])
+    assert torch.equal(b["ambiguous"] & 1, a["ambiguous"])
+    assert torch.equal(b["ambiguous"] >> 1, c["ambiguous"])
+    return b
+
+
+def test_both_modes_in_one_pass_c1_against_oracle(rsi):
+    """The combined pass on the c1 workload, every segment against the
+    oracle's boolean and intercept_count answers (Sec. 1)."""
+    m = W.config_mesh("c1")
+    F, E = W.rays(W.config_rays("c1"), m)
+    F[11] = np.nan    # undefined segment: ambiguous in both modes, hit 0, count 0
+    bvh = rsi.LBVH(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda())
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    b = _both_matches(rsi, bvh, dF, dE)
+    ref = oracle.query(m.vertices, m.triangles, F, E)
+    amb = b["ambiguous"].cpu().numpy()
+    hit, cnt = b["hit"].cpu().numpy(), b["count"].cpu().numpy()
+    assert np.array_equal(amb & 1, ref["amb_hit"]) and np.array_equal(amb >> 1, ref["amb_count"])
+    ok_h, ok_c = ref["amb_hit"] == 0, ref["amb_count"] == 0
+    assert np.array_equal(hit[ok_h], ref["hit"][ok_h]) and np.array_equal(cnt[ok_c], ref["count"][ok_c])
+    assert amb[11] == 3 and hit[11] == 0 and cnt[11] == 0
+    bvh.close()
+
+
+def test_both_modes_in_one_pass_grazing_and_host(rsi):
+    """On a grazing-heavy slice of the c3 recipe (1 % of the segments end
+    within 1e-6 of an edge or vertex or run nearly parallel to a face) the
+    two modes' ambiguity flags differ on many segments; the combined pass
+    still equals both separate queries, on device and host buffers."""
+    m = W.config_mesh("c3")
+    F, E = W.rays(W.config_rays("c3"), m, 0, 1 << 20)
+    bvh = rsi.LBVH(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda(), morton_bits=63)
+    dF, dE = torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()
+    b = _both_matches(rsi, bvh, dF, dE)
+    amb = b["ambiguous"].cpu().numpy()
+    assert ((amb >> 1) != (amb & 1)).sum() > 100   # count-ambiguous segments settled by a decisive hit
+    h = bvh.query_host(torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory(), "both")
+    for k in ("hit", "count", "ambiguous"):
+        assert torch.equal(h[k], b[k].cpu()), k
+    bvh.close()
