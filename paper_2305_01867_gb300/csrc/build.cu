@@ -1167,7 +1167,7 @@ extern "C" int lbvh_info(rsi_bvh_t h, rsi_bvh_info* out) {
     out->n_vertices = h->n_vert;
     out->morton_bits = h->morton_bits;
     out->height = h->height;
-    out->device_bytes = h->device_bytes + 16 * h->band_cap + h->pair_bytes;
+    out->device_bytes = h->device_bytes + 12 * h->band_cap + h->pair_bytes;
     for (int a = 0; a < 3; ++a) {
         out->extent_lo[a] = h->lo[a];
         out->extent_hi[a] = h->hi[a];

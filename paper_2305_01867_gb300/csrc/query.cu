@@ -2015,8 +2015,8 @@ int ensure_band_capacity(rsi_bvh_t h, int64_t n, cudaStream_t s) {
         h->band_cap = 0;
         h->pair_bytes = 0;
     }
-    // band | order | proposals | FP64 fallback list
-    if (pool_alloc(reinterpret_cast<void**>(&h->band_ids), 16 * (size_t)cap, s) != RSI_OK) return RSI_ERR_OOM;
+    // band | order (in-tile reordering, the learned query's leftovers, the nearest mode's list) | FP64 fallback list
+    if (pool_alloc(reinterpret_cast<void**>(&h->band_ids), 12 * (size_t)cap, s) != RSI_OK) return RSI_ERR_OOM;
     int64_t seg_cap, pair_cap;
     size_t bytes;
     pair_sizes(cap, seg_cap, pair_cap, bytes);
@@ -2033,7 +2033,7 @@ int ensure_band_capacity(rsi_bvh_t h, int64_t n, cudaStream_t s) {
 }
 
 PairScratch handle_pairs(rsi_bvh_t h) {
-    return carve_pairs(h->pair_mem, h->pair_seg_cap, h->pair_cap, h->band_ids + 3 * h->band_cap);
+    return carve_pairs(h->pair_mem, h->pair_seg_cap, h->pair_cap, h->band_ids + 2 * h->band_cap);
 }
 
 int read_stats(rsi_bvh_t h, DevCounters* ctr, int64_t n, rsi_stats* st, cudaStream_t s) {

@@ -20,8 +20,9 @@ constexpr float kWiden = 1e-6f;            // relative widening of slab interval
 enum { kMiss = 0, kHit = 1, kBand = 2 };
 
 struct SegF {
-    float3 s, d, inv, slo, shi;   // slo = s + pad (up), shi = s - pad (down)
-    float dl1;                    // |d|_1
+    float3 s, d, inv;
+    float3 olo, ohi;   // slab offsets of the lower / upper planes (see make_seg)
+    float dl1;         // |d|_1
 };
 
 __device__ __forceinline__ float safe_inv(float x) {
@@ -38,19 +39,33 @@ __device__ __forceinline__ SegF make_seg(float3 s, float3 e, float dmx, float dm
     float px = __fmul_ru(k, __fadd_ru(g.dl1, dmx));
     float py = __fmul_ru(k, __fadd_ru(g.dl1, dmy));
     float pz = __fmul_ru(k, __fadd_ru(g.dl1, dmz));
-    g.slo = make_float3(__fadd_ru(s.x, px), __fadd_ru(s.y, py), __fadd_ru(s.z, pz));
-    g.shi = make_float3(__fsub_rd(s.x, px), __fsub_rd(s.y, py), __fsub_rd(s.z, pz));
+    // the padded slab [lo - pad, hi + pad] gives the parameters (lo - slo) inv
+    // and (hi - shi) inv, slo = s + pad and shi = s - pad rounded outward.  Each
+    // is evaluated as one FMA, b inv + o, with the offset o = -slo inv (or
+    // -shi inv) rounded toward the conservative side: down for the plane the
+    // segment enters through (the lower plane when inv >= 0, the upper one
+    // otherwise), up for the plane it leaves through.  The FMA's exact sum is
+    // then never inside (lo - slo) inv, so only its single rounding remains,
+    // which the relative widening of the interval covers.
+    const float3 slo = make_float3(__fadd_ru(s.x, px), __fadd_ru(s.y, py), __fadd_ru(s.z, pz));
+    const float3 shi = make_float3(__fsub_rd(s.x, px), __fsub_rd(s.y, py), __fsub_rd(s.z, pz));
+    g.olo = make_float3(g.inv.x >= 0.0f ? __fmul_rd(-slo.x, g.inv.x) : __fmul_ru(-slo.x, g.inv.x),
+                        g.inv.y >= 0.0f ? __fmul_rd(-slo.y, g.inv.y) : __fmul_ru(-slo.y, g.inv.y),
+                        g.inv.z >= 0.0f ? __fmul_rd(-slo.z, g.inv.z) : __fmul_ru(-slo.z, g.inv.z));
+    g.ohi = make_float3(g.inv.x >= 0.0f ? __fmul_ru(-shi.x, g.inv.x) : __fmul_rd(-shi.x, g.inv.x),
+                        g.inv.y >= 0.0f ? __fmul_ru(-shi.y, g.inv.y) : __fmul_rd(-shi.y, g.inv.y),
+                        g.inv.z >= 0.0f ? __fmul_ru(-shi.z, g.inv.z) : __fmul_rd(-shi.z, g.inv.z));
     return g;
 }
 
-// Does the segment pass through the padded box?  The padded slab [lo - pad,
-// hi + pad] becomes parameters (lo - (s + pad)) / d and (hi - (s - pad)) / d
-// with the shifted origins rounded outward; the interval is then widened.
+// Does the segment pass through the padded box?  One FMA per plane (the
+// offsets of make_seg), the entry and exit parameters per axis, their
+// intersection widened by 1e-6 relative.
 __device__ __forceinline__ bool slab6(float xlo, float ylo, float zlo, float xhi, float yhi, float zhi,
                                       const SegF& g) {
-    float t0x = (xlo - g.slo.x) * g.inv.x, t1x = (xhi - g.shi.x) * g.inv.x;
-    float t0y = (ylo - g.slo.y) * g.inv.y, t1y = (yhi - g.shi.y) * g.inv.y;
-    float t0z = (zlo - g.slo.z) * g.inv.z, t1z = (zhi - g.shi.z) * g.inv.z;
+    float t0x = fmaf(xlo, g.inv.x, g.olo.x), t1x = fmaf(xhi, g.inv.x, g.ohi.x);
+    float t0y = fmaf(ylo, g.inv.y, g.olo.y), t1y = fmaf(yhi, g.inv.y, g.ohi.y);
+    float t0z = fmaf(zlo, g.inv.z, g.olo.z), t1z = fmaf(zhi, g.inv.z, g.ohi.z);
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
     float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
     tn = tn - fabsf(tn) * kWiden;
@@ -62,9 +77,9 @@ __device__ __forceinline__ bool slab(const float4& bmin, const float4& bmax, con
 }
 // The same test, also giving the length of the parameter interval inside the box.
 __device__ __forceinline__ bool slab_len(const float4& bmin, const float4& bmax, const SegF& g, float& len) {
-    float t0x = (bmin.x - g.slo.x) * g.inv.x, t1x = (bmax.x - g.shi.x) * g.inv.x;
-    float t0y = (bmin.y - g.slo.y) * g.inv.y, t1y = (bmax.y - g.shi.y) * g.inv.y;
-    float t0z = (bmin.z - g.slo.z) * g.inv.z, t1z = (bmax.z - g.shi.z) * g.inv.z;
+    float t0x = fmaf(bmin.x, g.inv.x, g.olo.x), t1x = fmaf(bmax.x, g.inv.x, g.ohi.x);
+    float t0y = fmaf(bmin.y, g.inv.y, g.olo.y), t1y = fmaf(bmax.y, g.inv.y, g.ohi.y);
+    float t0z = fmaf(bmin.z, g.inv.z, g.olo.z), t1z = fmaf(bmax.z, g.inv.z, g.ohi.z);
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
     float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
     tn = tn - fabsf(tn) * kWiden;

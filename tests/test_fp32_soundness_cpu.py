@@ -144,7 +144,14 @@ def slab_pass(s, e, lo, hi, dmax, fused):
     pad = _round_dir(k.astype(F64) * _round_dir(dl1[:, None].astype(F64) + dmax.astype(F64), True).astype(F64), True)
     slo = _round_dir(s.astype(F64) + pad.astype(F64), True)
     shi = _round_dir(s.astype(F64) - pad.astype(F64), False)
-    t0, t1 = (lo - slo) * inv, (hi - shi) * inv
+    # one FMA per plane with offsets rounded toward the conservative side:
+    # down for the entry plane (lower plane when inv >= 0), up for the exit one
+    pos = inv >= 0
+    plo = -slo.astype(F64) * inv.astype(F64)          # exact products in float64
+    phi = -shi.astype(F64) * inv.astype(F64)
+    olo = np.where(pos, _round_dir(plo, False), _round_dir(plo, True))
+    ohi = np.where(pos, _round_dir(phi, True), _round_dir(phi, False))
+    t0, t1 = _fma(lo, inv, olo), _fma(hi, inv, ohi)
     tn = np.minimum(t0, t1).max(axis=1)
     tf = np.maximum(t0, t1).min(axis=1)
     if fused:
@@ -336,3 +343,53 @@ def test_certain_fp64_decisions_are_the_definitions(pairs, fused):
     assert np.all(got[cls == AMB] == BAND)
     clear = (cls != AMB) & (det_rel > 2 * TAU)
     assert clear.sum() > 10000 and (got[clear] == BAND).sum() < 0.001 * clear.sum()
+
+
+def _padded_slab_exact(s, e, lo, hi, pad):
+    """Does the segment meet the padded box [lo - pad, hi + pad]?  Float64
+    slab arithmetic on the float32 inputs (a reference far finer than the
+    float32 test's own rounding)."""
+    s, e = s.astype(F64), e.astype(F64)
+    d = e - s
+    blo, bhi = lo.astype(F64) - pad.astype(F64), hi.astype(F64) + pad.astype(F64)
+    with np.errstate(all="ignore"):
+        inside = (s >= blo) & (s <= bhi)
+        t0 = np.where(d != 0, (blo - s) / d, np.where(inside, -np.inf, np.inf))
+        t1 = np.where(d != 0, (bhi - s) / d, np.where(inside, np.inf, -np.inf))
+    tn = np.minimum(t0, t1).max(1)
+    tf = np.maximum(t0, t1).min(1)
+    return (tn <= tf) & (tn <= 1.0) & (tf >= 0.0)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_slab_accepts_every_box_the_segment_touches(fused):
+    """The traversal's FP32 slab test (one FMA per plane, offsets rounded
+    toward the conservative side, interval widened) never rejects a padded
+    box the segment meets: boxes shrunk to a point on the segment and then
+    pushed out by exactly the padding, so the segment grazes the padded box's
+    faces, edges or corners; segments near and far from the origin, some
+    nearly parallel to an axis."""
+    rng = np.random.default_rng(17)
+    n = 300_000
+    scale = np.where(rng.uniform(size=(n, 1)) < 0.5, 1.0, 1e3)
+    shift = np.where(rng.uniform(size=(n, 1)) < 0.3, rng.uniform(-5e3, 5e3, (n, 3)), 0.0)
+    s = (rng.uniform(-1, 1, (n, 3)) * scale + shift).astype(F32)
+    d = rng.normal(size=(n, 3)) * rng.uniform(0.05, 1.0, (n, 1)) * scale
+    flat = rng.uniform(size=(n, 3)) < 0.1
+    d = np.where(flat, d * rng.choice([0.0, 1e-9, 1e-5], size=(n, 3)), d)
+    e = (s.astype(F64) + d).astype(F32)
+    dmax = (rng.uniform(0, 0.05, (n, 3)) * scale).astype(F32)
+    # the kernel's padding, rounded as it rounds it
+    dd = e - s
+    dl1 = (np.abs(dd[:, 0]) + np.abs(dd[:, 1])) + np.abs(dd[:, 2])
+    k = F32(4.0) * kTauHi
+    pad = _round_dir(k.astype(F64) * _round_dir(dl1[:, None].astype(F64) + dmax.astype(F64), True).astype(F64), True)
+    t = rng.uniform(-2e-6, 1 + 2e-6, (n, 1))
+    c = s.astype(F64) + t * (e.astype(F64) - s.astype(F64))
+    sign = rng.choice([-1.0, 1.0], size=(n, 3))
+    q = (c + sign * pad.astype(F64)).astype(F32)           # a point box whose padded cube touches c
+    exact = _padded_slab_exact(s, e, q, q, pad)
+    with np.errstate(all="ignore"):
+        got = slab_pass(s, e, q, q, dmax, fused)
+    assert exact.sum() > n // 4
+    assert np.all(got[exact]), int((exact & ~got).sum())
