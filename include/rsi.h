@@ -404,6 +404,24 @@ typedef struct rsi_batch_s* rsi_batch_t;
 int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int mode, const rsi_options* opt,
                      void* stream, rsi_batch_t* out);
 
+/* A plan whose graph first rebuilds every batch's hierarchy in place from
+ * its mesh and then answers the query: build and query in one graph launch,
+ * with the batched build's kernels and no host synchronization between them.
+ *   d_vertices[i], d_triangles[i]  device float32 [n][3] / int32 [m][3] with
+ *       the vertex and triangle counts of batches[i].bvh's own build; read at
+ *       every launch, so the caller may change them between launches.
+ * Otherwise as rsi_batch_create (no streaming; each hierarchy at most once;
+ * all hierarchies of one Morton width).  The heights of the rebuilt trees
+ * are not known when the graph is captured, so every walk uses a 128-entry
+ * stack and child-pair nodes.  Mesh errors (a NaN vertex, an index out of
+ * range) are reported by rsi_batch_stats, which also brings the
+ * hierarchies' host-side summaries (extent, padding, height, which lbvh_info
+ * and single queries read) up to date: call it before using a rebuilt
+ * hierarchy outside the plan.  Rebuilding has no counterpart in the paper. */
+int rsi_batch_create_rebuild(const rsi_ray_batch* batches, int n_batches, const float* const* d_vertices,
+                             const int32_t* const* d_triangles, int mode, const rsi_options* opt, void* stream,
+                             rsi_batch_t* out);
+
 /* Replay the plan on `stream` (one graph launch, asynchronous). */
 int rsi_batch_launch(rsi_batch_t plan, void* stream);
 

@@ -115,6 +115,9 @@ def _load():
     lib.rsi_batch_create.argtypes = [ctypes.POINTER(RayBatch), i32, i32, ctypes.POINTER(Options), P,
                                      ctypes.POINTER(P)]
     lib.rsi_batch_launch.argtypes = [P, P]
+    lib.rsi_batch_create_rebuild.argtypes = [ctypes.POINTER(RayBatch), i32, ctypes.POINTER(P), ctypes.POINTER(P), i32,
+                                             ctypes.POINTER(Options), P, ctypes.POINTER(P)]
+    lib.rsi_batch_create_rebuild.restype = ctypes.c_int
     lib.rsi_query_batched.argtypes = [ctypes.POINTER(P), i32, ctypes.POINTER(RayBatch), i32, ctypes.POINTER(Options),
                                       P]
     lib.rsi_batch_post.argtypes = [P, i64, P]
@@ -536,7 +539,7 @@ class BatchPlan:
     stream_timeout_ns > 0 makes a streaming plan fed by post()."""
 
     def __init__(self, items, mode="any_hit", *, fp32_only=False, block=0, blocks_per_sm=0, stats=False,
-                 stream_timeout_ns=0, node_width=0, ray_sort_tile=0, stack=0, stream=None):
+                 stream_timeout_ns=0, node_width=0, ray_sort_tile=0, stack=0, rebuild=None, stream=None):
         import torch
         m = _mode(mode)
         self.mode = m
@@ -558,7 +561,21 @@ class BatchPlan:
         opt = Options(int(fp32_only), int(block), int(blocks_per_sm), int(stats), timeout, 0, int(ray_sort_tile),
                       int(node_width), 0, int(stack))
         self._p = ctypes.c_void_p()
-        check(lib.rsi_batch_create(arr, len(items), m, ctypes.byref(opt), _stream(stream), ctypes.byref(self._p)))
+        if rebuild is None:
+            check(lib.rsi_batch_create(arr, len(items), m, ctypes.byref(opt), _stream(stream), ctypes.byref(self._p)))
+        else:   # (vertices, triangles) device tensors per item: rebuilt in the graph before the query
+            if len(rebuild) != len(items):
+                raise ValueError("rebuild needs one (vertices, triangles) pair per item")
+            vp, tp = (ctypes.c_void_p * len(items))(), (ctypes.c_void_p * len(items))()
+            for i, ((bvh, _, _), (V, T)) in enumerate(zip(items, rebuild)):
+                _check_f32x3(V, "vertices")
+                _check_out(T, "triangles", __import__("torch").int32, 3 * bvh.n_triangles, V.device)
+                if V.shape[0] != bvh.info()["n_vertices"] or T.shape != (bvh.n_triangles, 3):
+                    raise ValueError(f"rebuild mesh {i} differs in size from its hierarchy")
+                vp[i], tp[i] = V.data_ptr(), T.data_ptr()
+            self._rebuild = rebuild   # keep the buffers alive
+            check(lib.rsi_batch_create_rebuild(arr, len(items), vp, tp, m, ctypes.byref(opt), _stream(stream),
+                                               ctypes.byref(self._p)))
         self.total = sum(int(f.shape[0]) for _, f, _ in items)
 
     def run(self, stream=None):

@@ -882,6 +882,8 @@ rsi_bvh_s* alloc_handle(int64_t nv, int64_t nt, int morton_bits, bool sort_scrat
     h->box = (float*)(base + off[7]);
     *hgt = (int32_t*)(base + off[8]);
     *flag = (int32_t*)(base + off[9]);
+    h->hgt = *hgt;
+    h->flags = *flag;
     h->ctr = (DevCounters*)(base + off[10]);
     *scratch = base + off[11];
     h->nodes4 = (Node4*)(base + off[12]);
@@ -945,6 +947,44 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     h->has_q = n > 1;
     *out = h;
     return RSI_OK;
+}
+
+// The kernels of a batched build, in stream order and without any host
+// synchronization (so that a CUDA graph can capture them): counters reset,
+// extents, Morton codes, the stable sort by code and then by mesh, leaf
+// scatter, the bottom-up tree and boxes, four-wide nodes, and a copy of
+// every mesh's counters into d_ctr.
+template <typename K>
+int enqueue_batched_build(const MeshBuild* d_mb, const int64_t* d_tri_pre, const int64_t* d_int_pre, int M,
+                          int64_t total, int64_t total_int, K* ka, K* kb, K* codes, int32_t* va, int32_t* vb,
+                          uint32_t* mka, uint32_t* mkb, uint32_t* hist, DevCounters* d_ctr, cudaStream_t s) {
+    k_init_seg<<<grid_for(M, 128), 128, 0, s>>>(d_mb, M);
+    k_extent_seg<<<M, kBlock, 0, s>>>(d_mb);
+    k_morton_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total, ka, codes, va);
+    note_launches(3);
+    // stable sort by code, then stably by mesh: (mesh, code, triangle) order
+    K* sk;
+    int32_t* sv;
+    int rc = sort_pairs<K>(ka, va, kb, vb, total, sizeof(K) == 4 ? 4 : 8, hist, s, &sk, &sv);
+    if (rc) return rc;
+    int32_t* sv2 = sv == va ? vb : va;   // the other value buffer
+    k_mesh_keys<<<grid_for(total, kBlock), kBlock, 0, s>>>(sv, d_tri_pre, M, total, mka);
+    note_launches(1);
+    uint32_t* smk;
+    int32_t* fv;
+    rc = sort_pairs<uint32_t>(mka, sv, mkb, sv2, total, M <= 256 ? 1 : (M <= 65536 ? 2 : 4), hist, s, &smk, &fv);
+    if (rc) return rc;
+    k_scatter_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total, fv, codes);
+    k_apetrei_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total);
+    note_launches(2);
+    if (total_int > 0) {
+        k_collapse4_seg<<<grid_for(total_int, kBlock), kBlock, 0, s>>>(d_mb, d_int_pre, M, total_int);
+        note_launches(1);
+    }
+    k_gather_ctr<<<grid_for(M, 128), 128, 0, s>>>(d_mb, M, d_ctr);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RSI_OK : cuda_fail(e, "batched build launch");
 }
 
 // Many meshes in one build: ~20 launches in all, one synchronization.
@@ -1015,31 +1055,9 @@ int build_batched_impl(int M, const float* const* V, const int64_t* nv, const in
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_tri_pre, tri_pre.data(), 8 * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_int_pre, int_pre.data(), 8 * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_all(cuda_fail(e, "lbvh_build_batched: upload"));
-    k_init_seg<<<grid_for(M, 128), 128, 0, s>>>(d_mb, M);
-    k_extent_seg<<<M, kBlock, 0, s>>>(d_mb);
-    k_morton_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total, ka, codes, va);
-    note_launches(3);
-    // stable sort by code, then stably by mesh: (mesh, code, triangle) order
-    K* sk;
-    int32_t* sv;
-    int rc = sort_pairs<K>(ka, va, kb, vb, total, sizeof(K) == 4 ? 4 : 8, hist, s, &sk, &sv);
+    int rc = enqueue_batched_build<K>(d_mb, d_tri_pre, d_int_pre, M, total, total_int, ka, kb, codes, va, vb, mka,
+                                      mkb, hist, d_ctr, s);
     if (rc) return fail_all(rc);
-    int32_t* sv2 = sv == va ? vb : va;   // the other value buffer
-    k_mesh_keys<<<grid_for(total, kBlock), kBlock, 0, s>>>(sv, d_tri_pre, M, total, mka);
-    note_launches(1);
-    uint32_t* smk;
-    int32_t* fv;
-    rc = sort_pairs<uint32_t>(mka, sv, mkb, sv2, total, M <= 256 ? 1 : (M <= 65536 ? 2 : 4), hist, s, &smk, &fv);
-    if (rc) return fail_all(rc);
-    k_scatter_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total, fv, codes);
-    k_apetrei_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total);
-    note_launches(2);
-    if (total_int > 0) {
-        k_collapse4_seg<<<grid_for(total_int, kBlock), kBlock, 0, s>>>(d_mb, d_int_pre, M, total_int);
-        note_launches(1);
-    }
-    k_gather_ctr<<<grid_for(M, 128), 128, 0, s>>>(d_mb, M, d_ctr);
-    note_launches(1);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), d_ctr, sizeof(DevCounters) * M, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1056,6 +1074,99 @@ int build_batched_impl(int M, const float* const* V, const int64_t* nv, const in
         out[m] = hs[m];
     }
     return RSI_OK;
+}
+
+// ---------------------------------------------------------------- rebuild in place
+int rebuild_prepare(const rsi_bvh_t* hs, int M, const float* const* V, const int32_t* const* T, cudaStream_t s,
+                    RebuildSpec* out) {
+    if (!out || !hs || !V || !T || M < 1) return fail(RSI_ERR_INVALID_ARG, "rebuild: bad arguments");
+    RebuildSpec& r = *out;
+    r = RebuildSpec{};
+    r.M = M;
+    r.morton_bits = hs[0] ? hs[0]->morton_bits : 30;
+    std::vector<MeshBuild> mb(M);
+    std::vector<int64_t> tri_pre(M + 1, 0), int_pre(M + 1, 0);
+    for (int m = 0; m < M; ++m) {
+        const rsi_bvh_s* h = hs[m];
+        if (!h || !V[m] || !T[m])
+            return fail(RSI_ERR_INVALID_ARG, "rebuild: mesh " + std::to_string(m) + " lacks a hierarchy or buffer");
+        if (h->morton_bits != r.morton_bits)
+            return fail(RSI_ERR_INVALID_ARG, "rebuild: the hierarchies differ in morton_bits");
+        if (!h->hgt || !h->flags) return fail(RSI_ERR_INVALID_ARG, "rebuild: hierarchy without build scratch");
+        mb[m] = MeshBuild{V[m], T[m], h->n_vert, h->n_tri, h->nodes, h->nodes4, h->tris, h->sorted_keys, h->perm,
+                          h->left, h->right, h->parent, h->hgt, h->flags, h->box, h->ctr};
+        tri_pre[m + 1] = tri_pre[m] + h->n_tri;
+        int_pre[m + 1] = int_pre[m] + (h->n_tri > 1 ? h->n_tri - 1 : 0);
+    }
+    r.total = tri_pre[M];
+    r.total_int = int_pre[M];
+    r.hs.assign(hs, hs + M);
+    for (int m = 0; m < M; ++m) hs[m]->has_q = false;   // the batched build writes no compressed nodes
+    const size_t ksz = r.morton_bits == 30 ? 4 : 8;
+    const int ntiles = grid_for(r.total, 4096);
+    size_t off[10], bytes = 0;
+    const size_t sizes[10] = {sizeof(MeshBuild) * (size_t)M, 8 * (size_t)(M + 1), 8 * (size_t)(M + 1),
+                              ksz * (size_t)r.total, ksz * (size_t)r.total, ksz * (size_t)r.total,
+                              8 * (size_t)r.total, 8 * (size_t)r.total, 4 * 256 * (size_t)ntiles,
+                              sizeof(DevCounters) * (size_t)M};
+    for (int i = 0; i < 10; ++i) {
+        off[i] = bytes;
+        bytes += align_up(sizes[i]);
+    }
+    if (pool_alloc(reinterpret_cast<void**>(&r.mem), bytes, s) != RSI_OK) return RSI_ERR_OOM;
+    char* g = r.mem;
+    r.d_mb = g + off[0];
+    r.d_tri_pre = (int64_t*)(g + off[1]);
+    r.d_int_pre = (int64_t*)(g + off[2]);
+    r.ka = g + off[3];
+    r.kb = g + off[4];
+    r.codes = g + off[5];
+    r.va = (int32_t*)(g + off[6]);
+    r.vb = r.va + r.total;
+    r.mka = (uint32_t*)(g + off[7]);
+    r.mkb = r.mka + r.total;
+    r.hist = (uint32_t*)(g + off[8]);
+    r.d_ctr = (DevCounters*)(g + off[9]);
+    cudaError_t e = cudaMemcpyAsync(r.d_mb, mb.data(), sizeof(MeshBuild) * M, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r.d_tri_pre, tri_pre.data(), 8 * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r.d_int_pre, int_pre.data(), 8 * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host tables above go out of scope
+    if (e != cudaSuccess) {
+        rebuild_release(r);
+        return cuda_fail(e, "rebuild: upload");
+    }
+    return RSI_OK;
+}
+
+int rebuild_enqueue(const RebuildSpec& r, cudaStream_t s) {
+    const MeshBuild* d_mb = static_cast<const MeshBuild*>(r.d_mb);
+    if (r.morton_bits == 30)
+        return enqueue_batched_build<uint32_t>(d_mb, r.d_tri_pre, r.d_int_pre, r.M, r.total, r.total_int,
+                                               (uint32_t*)r.ka, (uint32_t*)r.kb, (uint32_t*)r.codes, r.va, r.vb, r.mka,
+                                               r.mkb, r.hist, r.d_ctr, s);
+    return enqueue_batched_build<uint64_t>(d_mb, r.d_tri_pre, r.d_int_pre, r.M, r.total, r.total_int,
+                                           (uint64_t*)r.ka, (uint64_t*)r.kb, (uint64_t*)r.codes, r.va, r.vb, r.mka,
+                                           r.mkb, r.hist, r.d_ctr, s);
+}
+
+void rebuild_release(RebuildSpec& r) {
+    if (r.mem) pool_free(r.mem, 0);
+    r.mem = nullptr;
+}
+
+int refresh_handles(const RebuildSpec& r, cudaStream_t s) {
+    std::vector<DevCounters> hc(r.M);
+    RSI_CUDA_TRY(cudaMemcpyAsync(hc.data(), r.d_ctr, sizeof(DevCounters) * r.M, cudaMemcpyDeviceToHost, s));
+    RSI_CUDA_TRY(cudaStreamSynchronize(s));
+    int rc = RSI_OK;
+    for (int m = 0; m < r.M; ++m) {
+        if (hc[m].error && rc == RSI_OK) {
+            const std::string why = hc[m].error == RSI_ERR_NAN ? "NaN vertex coordinate" : "triangle vertex index out of range";
+            rc = fail(hc[m].error, "rebuild: mesh " + std::to_string(m) + ": " + why);
+        }
+        finish_handle(r.hs[m], hc[m]);
+    }
+    return rc;
 }
 
 }  // namespace rsi

@@ -768,12 +768,9 @@ void feature_map(rsi_bvh_t h, float lo[3], float sc[3]) {
 // Launch of the tensor-core kernel: one CTA per SM (or per pair of tiles).
 template <bool VERIFY>
 int launch_tc(const TcArgs& P, int64_t n, cudaStream_t s) {
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[VERIFY]) {
-        RSI_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc<VERIFY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kSmBytes + 1024));
-        attr_set[VERIFY] = true;
-    }
+    // set on every launch: the attribute belongs to the current device's context
+    RSI_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc<VERIFY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kSmBytes + 1024));
     const int64_t tiles = (n + 127) / 128;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 1) / 2, (int64_t)device_sm_count()));
     k_mlp_tc<VERIFY><<<grid, kTcThreads, kSmBytes + 1024, s>>>(P);

@@ -1744,6 +1744,17 @@ __global__ void __launch_bounds__(128) k_cluster_labels(QueryArgs A, uint32_t* _
     }
 }
 
+// After a rebuild in the graph: each descriptor's padding extent (the largest
+// triangle box side per axis) from its mesh's new build counters.
+__global__ void k_desc_dmax(BatchDesc* __restrict__ desc, const DevCounters* __restrict__ ctr, int M) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) {
+        desc[m].dmax0 = __uint_as_float(ctr[m].dmax_bits[0]);
+        desc[m].dmax1 = __uint_as_float(ctr[m].dmax_bits[1]);
+        desc[m].dmax2 = __uint_as_float(ctr[m].dmax_bits[2]);
+    }
+}
+
 // Validation mode (rsi_options.fp64_all): every segment is queued for the
 // FP64 re-test, none is settled by the FP32 traversal.
 __global__ void k_queue_all(int32_t* __restrict__ band_ids, int64_t n, DevCounters* c) {
@@ -2458,13 +2469,11 @@ extern "C" int rsi_segment_order(rsi_bvh_t h, const float* d_from, const float* 
         if (rsi::pool_alloc(reinterpret_cast<void**>(&h->order_hist), sizeof(unsigned int) * rsi::kOrderBins, s) !=
             RSI_OK)
             return RSI_ERR_OOM;
-        static bool attr = false;   // 128 KB of shared memory per block for the histogram
-        if (!attr) {
-            RSI_CUDA_TRY(cudaFuncSetAttribute(rsi::k_order_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(sizeof(unsigned int) * rsi::kOrderBins)));
-            attr = true;
-        }
     }
+    // 128 KB of shared memory per block for the histogram (set on every call:
+    // the attribute belongs to the current device's context)
+    RSI_CUDA_TRY(cudaFuncSetAttribute(rsi::k_order_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(unsigned int) * rsi::kOrderBins)));
     float sc[3];
     for (int a = 0; a < 3; ++a) sc[a] = h->hi[a] > h->lo[a] ? 32.0f / (h->hi[a] - h->lo[a]) : 0.0f;
     RSI_CUDA_TRY(cudaMemsetAsync(h->order_hist, 0, sizeof(unsigned int) * rsi::kOrderBins, s));
@@ -2574,6 +2583,9 @@ struct rsi_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int sort_launches = 0;        // in-tile reorderings captured in the graph
+    int64_t graph_kernels = 0;    // kernel nodes of the graph (launches per replay)
+    rsi::RebuildSpec rebuild;     // rebuilding plans: the in-place rebuild that precedes the query
+    bool rebuilds = false;
 };
 
 namespace {
@@ -2589,8 +2601,10 @@ void batch_destroy(rsi_batch_s* b) {
     if (b->dev) cudaFree(b->dev);
     if (b->h_ctr) cudaFreeHost(b->h_ctr);
     if (b->h_post) cudaFreeHost(b->h_post);
+    if (b->rebuilds) rsi::rebuild_release(b->rebuild);
     delete b;
 }
+
 
 template <int MODE>
 void launch_batched(rsi_batch_s* b, const QueryArgs& A, const BatchArgs& B, cudaStream_t s) {
@@ -2609,8 +2623,9 @@ void launch_batched(rsi_batch_s* b, const QueryArgs& A, const BatchArgs& B, cuda
 
 }  // namespace
 
-extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int mode, const rsi_options* opt,
-                                void* stream, rsi_batch_t* out) {
+namespace {
+int batch_create_impl(const rsi_ray_batch* batches, int n_batches, int mode, const rsi_options* opt, void* stream,
+                      rsi_batch_t* out, const float* const* rebuild_V, const int32_t* const* rebuild_T) {
     if (!out) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: out is NULL");
     *out = nullptr;
     if (!batches || n_batches < 1) return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create: need >= 1 batch");
@@ -2660,6 +2675,18 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
         d.dmax2 = rb.bvh->dmax[2];
     }
     begins[n_batches] = (int)total;
+    if (rebuild_V) {
+        // the trees are rebuilt inside the graph: their heights are not known
+        // when it is captured, so every walk gets the deepest stack
+        for (int i = 0; i < n_batches; ++i)
+            for (int j = 0; j < i; ++j)
+                if (batches[i].bvh == batches[j].bvh)
+                    return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create_rebuild: hierarchy of batch " +
+                                                              std::to_string(i) + " appears twice");
+        height = 126;
+        o.stack = 128;
+        if (o.node_width == 4) o.node_width = 0;
+    }
     int64_t b_seg_cap = 0, b_pair_cap = 0;
     auto* b = new rsi_batch_s();
     b->mode = mode;
@@ -2704,7 +2731,17 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
         batch_destroy(b);
         return rc;
     }
-    // capture reset -> traversal -> FP64 pass into a graph
+    if (rebuild_V) {
+        std::vector<rsi_bvh_t> hs(n_batches);
+        for (int i = 0; i < n_batches; ++i) hs[i] = batches[i].bvh;
+        int rc = rsi::rebuild_prepare(hs.data(), n_batches, rebuild_V, rebuild_T, s, &b->rebuild);
+        if (rc) {
+            batch_destroy(b);
+            return rc;
+        }
+        b->rebuilds = true;
+    }
+    // capture [rebuild ->] reset -> traversal -> FP64 pass into a graph
     QueryArgs A{};
     A.band_ids = b->band;
     A.ctr = b->ctr;
@@ -2716,8 +2753,13 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     B.streamed = streamed ? 1 : 0;
     B.perm = perm;
     b->streamed = streamed;
+    const uint64_t noted0 = rsi_kernel_launches();
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+        if (b->rebuilds) {
+            rsi::rebuild_enqueue(b->rebuild, b->cap);
+            rsi::k_desc_dmax<<<rsi::grid_for(n_batches, 128), 128, 0, b->cap>>>(b->desc, b->rebuild.d_ctr, n_batches);
+        }
         k_reset_query<<<1, 1, 0, b->cap>>>(b->ctr, streamed ? ~0ull : (unsigned long long)total);
         if (perm) {   // in-tile reordering of every batch, into the global index space
             for (int i = 0; i < n_batches; ++i) {
@@ -2738,7 +2780,21 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
         e = cudaStreamEndCapture(b->cap, &b->graph);
         if (e == cudaSuccess) e = le;
     }
+    // launches noted while capturing run on every replay instead: count the
+    // graph's kernel nodes once and note that many per launch
+    rsi::note_launches(-(int)(rsi_kernel_launches() - noted0));
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) {
+        size_t n_nodes = 0;
+        e = cudaGraphGetNodes(b->graph, nullptr, &n_nodes);
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        if (e == cudaSuccess && n_nodes) e = cudaGraphGetNodes(b->graph, nodes.data(), &n_nodes);
+        for (size_t i = 0; e == cudaSuccess && i < n_nodes; ++i) {
+            cudaGraphNodeType t;
+            e = cudaGraphNodeGetType(nodes[i], &t);
+            if (t == cudaGraphNodeTypeKernel) ++b->graph_kernels;
+        }
+    }
     if (e != cudaSuccess) {
         int rc = rsi::cuda_fail(e, "rsi_batch_create: graph capture");
         batch_destroy(b);
@@ -2746,6 +2802,22 @@ extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int
     }
     *out = b;
     return RSI_OK;
+}
+}  // namespace
+
+extern "C" int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int mode, const rsi_options* opt,
+                                void* stream, rsi_batch_t* out) {
+    return batch_create_impl(batches, n_batches, mode, opt, stream, out, nullptr, nullptr);
+}
+
+extern "C" int rsi_batch_create_rebuild(const rsi_ray_batch* batches, int n_batches, const float* const* d_vertices,
+                                        const int32_t* const* d_triangles, int mode, const rsi_options* opt,
+                                        void* stream, rsi_batch_t* out) {
+    if (!d_vertices || !d_triangles)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create_rebuild: NULL mesh arrays");
+    if (opt && opt->timeout_ns < 0)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "rsi_batch_create_rebuild: streaming plans cannot rebuild");
+    return batch_create_impl(batches, n_batches, mode, opt, stream, out, d_vertices, d_triangles);
 }
 
 extern "C" int rsi_batch_launch(rsi_batch_t b, void* stream) {
@@ -2755,8 +2827,7 @@ extern "C" int rsi_batch_launch(rsi_batch_t b, void* stream) {
         RSI_CUDA_TRY(cudaEventRecord(b->reset_ev, (cudaStream_t)stream));
     }
     RSI_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
-    // reset, the reorderings, traversal, the 6 kernels of the FP64 pass
-    rsi::note_launches((b->opt.fp32_only ? 2 : 8) + b->sort_launches);
+    rsi::note_launches((int)b->graph_kernels);
     return RSI_OK;
 }
 
@@ -2779,6 +2850,10 @@ extern "C" int rsi_batch_stats(rsi_batch_t b, rsi_stats* st, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     RSI_CUDA_TRY(cudaMemcpyAsync(b->h_ctr, b->ctr, sizeof(rsi::DevCounters), cudaMemcpyDeviceToHost, s));
     RSI_CUDA_TRY(cudaStreamSynchronize(s));
+    if (b->rebuilds) {   // the rebuilt hierarchies' host-side extent, padding and height
+        const int rc = rsi::refresh_handles(b->rebuild, s);
+        if (rc) return rc;
+    }
     const rsi::DevCounters& c = *b->h_ctr;
     st->n_rays = b->total;
     st->node_visits = (int64_t)c.node_visits;

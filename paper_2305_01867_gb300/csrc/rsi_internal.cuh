@@ -7,6 +7,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "rsi.h"
 
@@ -123,6 +124,8 @@ struct rsi_bvh_s {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // traversal / re-test timing
     bool timed = false;
     unsigned int* order_hist = nullptr;   // rsi_segment_order's cell counts (2^15), on first use
+    int32_t* hgt = nullptr;               // build scratch in the handle's allocation: node heights,
+    int32_t* flags = nullptr;             // arrival flags / range ends (rebuilds reuse them)
     uint64_t gen = 0;                 // process-unique id (plans name hierarchies by it)
     rsi_mlp_s* mlp = nullptr;         // attached proposal network (rsi_mlp_attach)
 };
@@ -193,6 +196,32 @@ cudaError_t host_malloc_pinned(T** p, size_t bytes) {
 
 // Count of kernel launches made by the library (rsi_kernel_launches).
 void note_launches(int n);
+
+// A batched rebuild prepared for capture: the hierarchies' own arrays are
+// rebuilt in place from the meshes' current buffers (the sizes fixed at
+// preparation), by kernels that rebuild_enqueue issues without any host
+// synchronization.  d_ctr receives every mesh's build counters (errors,
+// height, extent, padding); refresh_handles copies them to the handles.
+struct RebuildSpec {
+    char* mem = nullptr;        // one allocation: table, prefixes, sort buffers, counters
+    int M = 0, morton_bits = 30;
+    int64_t total = 0, total_int = 0;
+    void* d_mb = nullptr;       // [M] per-mesh build descriptors
+    int64_t* d_tri_pre = nullptr;
+    int64_t* d_int_pre = nullptr;
+    void *ka = nullptr, *kb = nullptr, *codes = nullptr;
+    int32_t *va = nullptr, *vb = nullptr;
+    uint32_t *mka = nullptr, *mkb = nullptr, *hist = nullptr;
+    DevCounters* d_ctr = nullptr;
+    std::vector<rsi_bvh_t> hs;
+};
+int rebuild_prepare(const rsi_bvh_t* hs, int M, const float* const* V, const int32_t* const* T, cudaStream_t s,
+                    RebuildSpec* out);
+int rebuild_enqueue(const RebuildSpec& r, cudaStream_t s);
+void rebuild_release(RebuildSpec& r);
+// Host copies of the hierarchies' extent, padding and height after a rebuild
+// has run (synchronizes s); the first mesh error found, else RSI_OK.
+int refresh_handles(const RebuildSpec& r, cudaStream_t s);
 
 // Process-unique id of a new hierarchy (never 0, never reused).
 uint64_t next_handle_gen();

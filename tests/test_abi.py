@@ -119,6 +119,7 @@ def test_every_entry_point_rejects_missing_arguments(lib):
                                                              ctypes.byref(k), None),
         "rsi_batch_create": lambda: L.rsi_batch_create(None, 0, 0, None, None, None),
         "rsi_batch_launch": lambda: L.rsi_batch_launch(None, None),
+        "rsi_batch_create_rebuild": lambda: L.rsi_batch_create_rebuild(None, 0, None, None, 0, None, None, None),
         "rsi_query_batched": lambda: L.rsi_query_batched(None, 0, None, 0, None, None),
         "rsi_mlp_attach": lambda: L.rsi_mlp_attach(None, None),
         "rsi_batch_post": lambda: L.rsi_batch_post(None, 0, None),

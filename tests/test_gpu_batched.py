@@ -181,3 +181,53 @@ def test_one_call_batched_query_rejections(rsi, scene):
     arr[0] = rsi.RayBatch(None, f.data_ptr(), t.data_ptr(), 0, None, None, None)
     assert rsi.lib.rsi_query_batched(hs, 1, arr, rsi.RSI_ANY_HIT, ctypes.byref(opt), None) == -1
     assert "streaming" in rsi.last_error()
+
+
+@pytest.mark.parametrize("mode", ["any_hit", "count"])
+def test_rebuild_and_query_in_one_graph(rsi, mode):
+    """rsi_batch_create_rebuild: each launch rebuilds every hierarchy in place
+    from its mesh buffers, then queries, in one graph.  After the vertices
+    move, a launch gives what a fresh build and query of the moved meshes
+    give, and the rebuilt hierarchies equal fresh builds bit for bit; a NaN
+    vertex is reported by the plan's stats with its mesh."""
+    jobs = W.batched_meshes(n_meshes=5, seed=5, max_rays=30_000)
+    meshes = [(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda()) for m, _ in jobs]
+    rays = [W.rays(spec, m) for m, spec in jobs]
+    bvhs = rsi.build_many(meshes)
+    items = [(b, torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()) for b, (F, E) in zip(bvhs, rays)]
+    key = "hit" if mode == "any_hit" else "count"
+    plan = rsi.BatchPlan(items, mode, rebuild=meshes)
+
+    def check_against_fresh():
+        plan.run()
+        st = plan.stats()                 # synchronizes, refreshes the hierarchies' summaries
+        assert st["device_error"] == 0
+        for i, ((b, f, t), (V, T)) in enumerate(zip(items, meshes)):
+            fresh = rsi.LBVH(V, T)
+            ref = fresh.query(f, t, mode)
+            got = plan.hit[i] if mode == "any_hit" else plan.count[i]
+            assert torch.equal(got, ref[key]) and torch.equal(plan.ambiguous[i], ref["ambiguous"]), i
+            e1, e2 = fresh.export(), b.export()
+            for k in e1:
+                assert np.array_equal(e1[k], e2[k]), (i, k)
+            i1, i2 = fresh.info(), b.info()
+            for k in ("height", "extent_lo", "extent_hi", "max_tri_extent"):
+                assert i1[k] == i2[k], (i, k)
+            fresh.close()
+
+    check_against_fresh()
+    for V, _ in meshes:                   # move the meshes: stretch the relief, shift the grid
+        V[:, 2] *= 1.7
+        V[:, :2] += 0.013
+    check_against_fresh()
+    keep = meshes[2][0][4, 1].item()
+    meshes[2][0][4, 1] = float("nan")
+    plan.run()
+    with pytest.raises(rsi.RSIError) as e:
+        plan.stats()
+    assert e.value.code == -7 and "mesh 2" in str(e.value)
+    meshes[2][0][4, 1] = keep
+    check_against_fresh()
+    plan.close()
+    for b in bvhs:
+        b.close()
