@@ -44,6 +44,7 @@ W_DOC_PAPER = ("paper scale: 111x134-vertex heightfield, 4 sinusoids + 8 Gaussia
                "29,260 triangles, the paper's counts); 1e7 segments, 50% crossing / 50% above")
 BYTES_PER_RAY_COUNT = 28   # 24 B of segment in + 4 B of count out (algorithmic)
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_query_fp32_count_c2.md")
+TRAFFIC_SUMMARY_C3 = os.path.join(ROOT, "profiles", "k_query_fp32_count_c3.md")
 
 
 def peaks():
@@ -67,11 +68,11 @@ def source_hash():
     return hashlib.sha256((q[b:e] + t).encode()).hexdigest()[:16]
 
 
-def profile_values():
-    """Figures of the committed ncu summary of the count traversal, if it was
-    taken on the current source (else {})."""
+def profile_values(path=None):
+    """Figures of a committed ncu summary of the count traversal (the c2
+    capture by default), if it was taken on the current source (else {})."""
     try:
-        txt = open(TRAFFIC_SUMMARY).read()
+        txt = open(path or TRAFFIC_SUMMARY).read()
     except OSError:
         return {}
     vals = {}
@@ -561,7 +562,8 @@ def measure_precision_c3(rsi, torch, dev, c3, args):
     out["roofline"] = {"kernel": "k_query_fp32<count> (FP32 traversal, intercept_count)", "bound": "hbm",
                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                       else "fallback 6.8 TB/s", "traffic": None, "algorithmic_bytes_per_ray": BYTES_PER_RAY_COUNT,
+                       else "fallback 6.8 TB/s", "traffic": profile_values(TRAFFIC_SUMMARY_C3).get(
+                           "dram_bytes_per_launch_full_size"), "algorithmic_bytes_per_ray": BYTES_PER_RAY_COUNT,
                        "kernel_ms": trav_ms}
     bvh.close()
     del dF, dE
@@ -726,6 +728,8 @@ def main():
     ap.add_argument("--c3-check", type=int, default=20_000)
     ap.add_argument("--learned-rays", type=int, default=100_000_000)
     ap.add_argument("--train-rays", type=int, default=10_000_000)
+    ap.add_argument("--c3-only", action="store_true",
+                    help="run the c3 precision leg alone and print its object (for profiler captures)")
     ap.add_argument("--order", action="store_true",
                     help="walk the segments in midpoint-cell order in the timed step (rsi_segment_order inside it)")
     args = ap.parse_args()
@@ -743,6 +747,13 @@ def main():
 
     import paper_2305_01867_gb300 as rsi
     import workloads as W
+
+    if args.c3_only:   # the c3 leg by itself: its own JSON object, no contract line
+        m3 = W.config_mesh("c3")
+        c3 = (m3, W.rays_many([(m3, W.config_rays("c3", args.c3_rays))])[0])
+        torch.cuda.set_device(local)
+        print(json.dumps({"precision_c3": measure_precision_c3(rsi, torch, torch.device("cuda", local), c3, args)}))
+        return
 
     mesh = W.config_mesh("c2")
     spec = W.config_rays("c2", args.rays)

@@ -2887,7 +2887,11 @@ struct PlanKey {
     std::vector<rsi_ray_batch> batches;   // .bvh as given by hs
     bool operator==(const PlanKey& o) const {
         if (device != o.device || mode != o.mode || gens != o.gens || batches.size() != o.batches.size()) return false;
-        if (std::memcmp(&opt, &o.opt, sizeof(rsi_options)) != 0) return false;
+        // the fields a plan depends on (compared one by one: the struct has padding)
+        if (opt.fp32_only != o.opt.fp32_only || opt.block != o.opt.block || opt.blocks_per_sm != o.opt.blocks_per_sm ||
+            opt.collect_stats != o.opt.collect_stats || opt.timeout_ns != o.opt.timeout_ns ||
+            opt.ray_sort_tile != o.opt.ray_sort_tile || opt.node_width != o.opt.node_width || opt.stack != o.opt.stack)
+            return false;
         for (size_t i = 0; i < batches.size(); ++i) {
             const rsi_ray_batch &a = batches[i], &b = o.batches[i];
             if (a.bvh != b.bvh || a.d_from != b.d_from || a.d_to != b.d_to || a.n_rays != b.n_rays ||

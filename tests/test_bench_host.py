@@ -21,6 +21,16 @@ def test_profile_figures_agree_with_the_algorithmic_bytes():
         assert 0.0 < b[k] < 1.0, k
 
 
+def test_c3_profile_figures_agree_with_the_algorithmic_bytes():
+    """The c3 leg's traffic comes from its own capture (6e6 of the leg's 1e8
+    segments, scaled); it too must match the current traversal source."""
+    v = bench.profile_values(bench.TRAFFIC_SUMMARY_C3)
+    assert v, ("profiles/k_query_fp32_count_c3.md predates the current traversal source "
+               f"(source_hash {bench.source_hash()}): capture it again")
+    algorithmic = bench.BYTES_PER_RAY_COUNT * 100_000_000
+    assert 0.9 * algorithmic <= v["dram_bytes_per_launch_full_size"] <= 1.25 * algorithmic
+
+
 def test_stale_profile_is_not_used(monkeypatch):
     monkeypatch.setattr(bench, "source_hash", lambda: "0000000000000000")
     assert bench.profile_values() == {}
