@@ -258,8 +258,16 @@ __device__ __noinline__ bool wait_ready(DevCounters* c, unsigned long long need,
     return true;
 }
 
-constexpr int kLeafMin = 12;     // run the triangle tests once this many lanes hold one
+constexpr int kLeafMin = 10;     // run the triangle tests once this many lanes hold one
+constexpr int kNodeSteps = 4;    // node steps per round of the traversal loop
+constexpr int kSharedStack = 32; // a stack of this depth lives in shared memory
 constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^30)
+
+// Dynamic shared memory of a traversal launch: the 32-entry stacks of the
+// block's threads, else none.
+inline size_t trav_smem_bytes(int stack, int block) {
+    return stack == kSharedStack ? sizeof(int) * (size_t)kSharedStack * (size_t)block : 0;
+}
 
 // Warp-coherent persistent traversal with deferred leaf tests.  In the
 // boolean mode, when both children pass, the walk goes first into the one
@@ -274,7 +282,13 @@ constexpr int kDone = 0x7FFFFFFF;  // "no next node" (node indices stay below 2^
 // kLeafMin lanes hold one or no lane can move on without it, so node work and
 // triangle work both run with most lanes active.  Lanes whose segment is done
 // are refilled together from a per-warp chunk of segment indices (one atomic
-// per chunk).  A segment with a band pair and no certain answer is queued for
+// per chunk).  Each round of the loop runs kNodeSteps node steps (a lane
+// parks the leaf it reaches between them), so the refill and leaf-phase
+// ballots are paid once per round; the child-pair step updates the walk
+// with selects rather than branches.  A 32-entry stack lives in shared
+// memory, one column per thread ([entry][thread]: a warp's accesses are
+// free of bank conflicts whatever the lanes' depths), deeper ones in local
+// memory.  A segment with a band pair and no certain answer is queued for
 // k_query_fp64 (count and nearest modes stop at the first band pair).  The
 // nearest mode visits every pair like the count mode and keeps the certain
 // hit with the smallest upper bound on t; the answer is certain when every
@@ -307,10 +321,15 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
     SegF g;
     // traversal stack: the top entry is cached in a register (`top`, kDone =
     // empty) so that a pop hands over the next node at once; the entries
-    // below it live in local memory and the load that refills `top` is only
-    // waited for at the following pop
+    // below it live in shared memory (STACK == kSharedStack: entry i of this
+    // thread at s_stack[i * blockDim.x + threadIdx.x]) or local memory
     int next = kDone, slot = -1, sp = 0, top = kDone;
-    int stack[STACK];
+    extern __shared__ int s_stack[];
+    constexpr bool kShared = STACK == kSharedStack;
+    int l_stack[kShared ? 1 : STACK];
+    int* const s_col = s_stack + threadIdx.x;
+    const int s_stride = blockDim.x;
+#define RSI_STK(i) (*(kShared ? s_col + (i) * s_stride : &l_stack[(i)]))
     int cnt = 0, plain_cnt = 0;
     bool found = false, band = false, stop = false;
     // nearest mode: best certain hit (leaf n1, t in [lo1, hi1]), smallest lower
@@ -319,7 +338,9 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
     float lo1 = 0.0f, hi1 = 0.0f, m2 = 0.0f, pbt = 0.0f;
     while (true) {
         unsigned idle = __ballot_sync(kFull, ray < 0);
+        bool refilled = false;
         if (!exhausted && (__popc(idle) >= kRefillMin || idle == kFull)) {
+            refilled = true;
             while (idle) {
                 if (wbase >= wend) {
                     unsigned long long b = 0;
@@ -403,128 +424,141 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
             }
         }
         const bool active = ray >= 0;
-        const unsigned act = __ballot_sync(kFull, active);
+        const unsigned act = refilled ? __ballot_sync(kFull, active) : ~idle;
         if (act == 0) {
             if (exhausted) break;
             continue;
         }
-        // node step
-        if (NW == 1 && active && next != kDone && next >= 0) {
-            const float4* p = reinterpret_cast<const float4*>((BATCHED ? l_nodes4 : A.nodes4) + next);
-            float4 xl, xh, yl, yh, zl, zh, rff, pad;
-            ld32B(p, xl, xh);
-            ld32B(p + 2, yl, yh);
-            ld32B(p + 4, zl, zh);
-            ld32B(p + 6, rff, pad);
-            const int4 rf = make_int4(__float_as_int(rff.x), __float_as_int(rff.y), __float_as_int(rff.z),
-                                      __float_as_int(rff.w));
-            if (STATS) ++visits;
-            const bool h0 = slab6(xl.x, yl.x, zl.x, xh.x, yh.x, zh.x, g);
-            const bool h1 = slab6(xl.y, yl.y, zl.y, xh.y, yh.y, zh.y, g) && rf.y != kEmpty4;
-            const bool h2 = slab6(xl.z, yl.z, zl.z, xh.z, yh.z, zh.z, g) && rf.z != kEmpty4;
-            const bool h3 = slab6(xl.w, yl.w, zl.w, xh.w, yh.w, zh.w, g) && rf.w != kEmpty4;
-            int nx = h3 ? rf.w : kDone;
-            bool over = false;
-#define RSI_PUSH_HIT(HC, RC)                       \
-    if (HC) {                                      \
-        if (nx != kDone) {                         \
-            if (top != kDone) {                    \
-                if (sp < STACK) stack[sp++] = top; \
-                else over = true;                  \
-            }                                      \
-            top = nx;                              \
-        }                                          \
-        nx = (RC);                                 \
+#pragma unroll
+        for (int step = 0; step < kNodeSteps; ++step) {
+            // node step
+            if (NW == 1 && active && next != kDone && next >= 0) {
+                const float4* p = reinterpret_cast<const float4*>((BATCHED ? l_nodes4 : A.nodes4) + next);
+                float4 xl, xh, yl, yh, zl, zh, rff, pad;
+                ld32B(p, xl, xh);
+                ld32B(p + 2, yl, yh);
+                ld32B(p + 4, zl, zh);
+                ld32B(p + 6, rff, pad);
+                const int4 rf = make_int4(__float_as_int(rff.x), __float_as_int(rff.y), __float_as_int(rff.z),
+                                          __float_as_int(rff.w));
+                if (STATS) ++visits;
+                const bool h0 = slab6(xl.x, yl.x, zl.x, xh.x, yh.x, zh.x, g);
+                const bool h1 = slab6(xl.y, yl.y, zl.y, xh.y, yh.y, zh.y, g) && rf.y != kEmpty4;
+                const bool h2 = slab6(xl.z, yl.z, zl.z, xh.z, yh.z, zh.z, g) && rf.z != kEmpty4;
+                const bool h3 = slab6(xl.w, yl.w, zl.w, xh.w, yh.w, zh.w, g) && rf.w != kEmpty4;
+                int nx = h3 ? rf.w : kDone;
+                bool over = false;
+#define RSI_PUSH_HIT(HC, RC)           \
+    if (HC) {                          \
+        if (nx != kDone) {             \
+            if (top != kDone) {        \
+                if (sp < STACK) {      \
+                    RSI_STK(sp) = top; \
+                    ++sp;              \
+                } else {               \
+                    over = true;       \
+                }                      \
+            }                          \
+            top = nx;                  \
+        }                              \
+        nx = (RC);                     \
     }
-            RSI_PUSH_HIT(h2, rf.z)
-            RSI_PUSH_HIT(h1, rf.y)
-            RSI_PUSH_HIT(h0, rf.x)
+                RSI_PUSH_HIT(h2, rf.z)
+                RSI_PUSH_HIT(h1, rf.y)
+                RSI_PUSH_HIT(h0, rf.x)
 #undef RSI_PUSH_HIT
-            if (over) {   // cannot happen with STACK >= 3 x the four-wide levels; queued
-                raise_error(A.ctr, RSI_ERR_STACK);
-                band = true;
-                stop = true;
-            }
-            if (nx != kDone) {
-                next = nx;
-            } else {
-                next = top;
-                top = sp > 0 ? stack[--sp] : kDone;
-            }
-        }
-        if (NW != 1 && active && next != kDone && next >= 0) {
-            float4 lmin, lmax, rmin, rmax;
-            int lref, rref;
-            if (NW == 2) {
-                float4 fa, fb;
-                ld32B(reinterpret_cast<const float4*>(A.nodesq + next), fa, fb);
-                const unsigned meta = __float_as_uint(fa.w);
-                const float sx = __uint_as_float((meta & 0xFFu) << 23);
-                const float sy = __uint_as_float(((meta >> 8) & 0xFFu) << 23);
-                const float sz = __uint_as_float(((meta >> 16) & 0xFFu) << 23);
-                const unsigned w0 = __float_as_uint(fb.x), w1 = __float_as_uint(fb.y), w2 = __float_as_uint(fb.z);
-                const int split = __float_as_int(fb.w);
-#define RSI_QB(W, K) __uint2float_rn(((W) >> (8 * (K))) & 0xFFu)
-                lmin = make_float4(__fmaf_rd(RSI_QB(w0, 0), sx, fa.x), __fmaf_rd(RSI_QB(w0, 1), sy, fa.y),
-                                   __fmaf_rd(RSI_QB(w0, 2), sz, fa.z), 0.0f);
-                lmax = make_float4(__fmaf_ru(RSI_QB(w0, 3), sx, fa.x), __fmaf_ru(RSI_QB(w1, 0), sy, fa.y),
-                                   __fmaf_ru(RSI_QB(w1, 1), sz, fa.z), 0.0f);
-                rmin = make_float4(__fmaf_rd(RSI_QB(w1, 2), sx, fa.x), __fmaf_rd(RSI_QB(w1, 3), sy, fa.y),
-                                   __fmaf_rd(RSI_QB(w2, 0), sz, fa.z), 0.0f);
-                rmax = make_float4(__fmaf_ru(RSI_QB(w2, 1), sx, fa.x), __fmaf_ru(RSI_QB(w2, 2), sy, fa.y),
-                                   __fmaf_ru(RSI_QB(w2, 3), sz, fa.z), 0.0f);
-#undef RSI_QB
-                lref = (meta >> 24) & 1u ? ~split : split;
-                rref = (meta >> 25) & 1u ? ~(split + 1) : split + 1;
-            } else {
-                load_node(BATCHED ? l_nodes : A.nodes, next, lmin, lmax, rmin, rmax);
-                lref = __float_as_int(lmin.w);
-                rref = __float_as_int(lmax.w);
-            }
-            if (STATS) ++visits;
-            bool hl, hr;
-            if (MODE == RSI_ANY_HIT) {   // boolean: the child the segment spends longer in first
-                float ll, lr;
-                hl = slab_len(lmin, lmax, g, ll);
-                hr = slab_len(rmin, rmax, g, lr);
-                if (hl && hr && lr > ll) {
-                    const int tmp = lref;
-                    lref = rref;
-                    rref = tmp;
-                }
-            } else {
-                hl = slab(lmin, lmax, g);
-                hr = slab(rmin, rmax, g);
-            }
-            if (hl && hr) {
-                if (top == kDone || sp < STACK) {
-                    if (top != kDone) stack[sp++] = top;
-                    top = rref;
-                    next = lref;
-                } else {   // cannot happen with STACK > tree height; queued
+                if (over) {   // cannot happen with STACK >= 3 x the four-wide levels; queued
                     raise_error(A.ctr, RSI_ERR_STACK);
                     band = true;
                     stop = true;
                 }
-            } else if (hl) {
-                next = lref;
-            } else if (hr) {
-                next = rref;
-            } else {
-                next = top;
-                top = sp > 0 ? stack[--sp] : kDone;
+                if (nx != kDone) {
+                    next = nx;
+                } else {
+                    next = top;
+                    top = sp > 0 ? RSI_STK(sp - 1) : kDone;
+                    sp = sp > 0 ? sp - 1 : 0;
+                }
             }
-        }
-        // park a leaf reference
-        if (active && !stop && next < 0 && slot < 0) {
-            slot = ~next;
-            next = top;
-            top = sp > 0 ? stack[--sp] : kDone;
-        }
-        // leaf phase: all parked leaves of the warp at once
+            if (NW != 1 && active && next != kDone && next >= 0) {
+                float4 lmin, lmax, rmin, rmax;
+                int lref, rref;
+                if (NW == 2) {
+                    float4 fa, fb;
+                    ld32B(reinterpret_cast<const float4*>(A.nodesq + next), fa, fb);
+                    const unsigned meta = __float_as_uint(fa.w);
+                    const float sx = __uint_as_float((meta & 0xFFu) << 23);
+                    const float sy = __uint_as_float(((meta >> 8) & 0xFFu) << 23);
+                    const float sz = __uint_as_float(((meta >> 16) & 0xFFu) << 23);
+                    const unsigned w0 = __float_as_uint(fb.x), w1 = __float_as_uint(fb.y), w2 = __float_as_uint(fb.z);
+                    const int split = __float_as_int(fb.w);
+#define RSI_QB(W, K) __uint2float_rn(((W) >> (8 * (K))) & 0xFFu)
+                    lmin = make_float4(__fmaf_rd(RSI_QB(w0, 0), sx, fa.x), __fmaf_rd(RSI_QB(w0, 1), sy, fa.y),
+                                       __fmaf_rd(RSI_QB(w0, 2), sz, fa.z), 0.0f);
+                    lmax = make_float4(__fmaf_ru(RSI_QB(w0, 3), sx, fa.x), __fmaf_ru(RSI_QB(w1, 0), sy, fa.y),
+                                       __fmaf_ru(RSI_QB(w1, 1), sz, fa.z), 0.0f);
+                    rmin = make_float4(__fmaf_rd(RSI_QB(w1, 2), sx, fa.x), __fmaf_rd(RSI_QB(w1, 3), sy, fa.y),
+                                       __fmaf_rd(RSI_QB(w2, 0), sz, fa.z), 0.0f);
+                    rmax = make_float4(__fmaf_ru(RSI_QB(w2, 1), sx, fa.x), __fmaf_ru(RSI_QB(w2, 2), sy, fa.y),
+                                       __fmaf_ru(RSI_QB(w2, 3), sz, fa.z), 0.0f);
+#undef RSI_QB
+                    lref = (meta >> 24) & 1u ? ~split : split;
+                    rref = (meta >> 25) & 1u ? ~(split + 1) : split + 1;
+                } else {
+                    load_node(BATCHED ? l_nodes : A.nodes, next, lmin, lmax, rmin, rmax);
+                    lref = __float_as_int(lmin.w);
+                    rref = __float_as_int(lmax.w);
+                }
+                if (STATS) ++visits;
+                bool hl, hr;
+                if (MODE == RSI_ANY_HIT) {   // boolean: the child the segment spends longer in first
+                    float ll, lr;
+                    hl = slab_len(lmin, lmax, g, ll);
+                    hr = slab_len(rmin, rmax, g, lr);
+                    if (hl && hr && lr > ll) {
+                        const int tmp = lref;
+                        lref = rref;
+                        rref = tmp;
+                    }
+                } else {
+                    hl = slab(lmin, lmax, g);
+                    hr = slab(rmin, rmax, g);
+                }
+                // both children: go left, the right one becomes the cached top
+                // and the old top is pushed; one child: go there; none: pop
+                const bool both = hl && hr, any = hl || hr;
+                const int t0 = top;
+                if (both && t0 != kDone) {
+                    if (sp < STACK) {
+                        RSI_STK(sp) = t0;
+                        ++sp;
+                    } else {   // cannot happen with STACK > tree height; queued
+                        raise_error(A.ctr, RSI_ERR_STACK);
+                        band = true;
+                        stop = true;
+                    }
+                }
+                int popped = kDone;
+                if (!any && sp > 0) {
+                    --sp;
+                    popped = RSI_STK(sp);
+                }
+                next = any ? (hl ? lref : rref) : t0;
+                top = both ? rref : (any ? t0 : popped);
+            }
+            // park a leaf reference
+            if (active && !stop && next < 0 && slot < 0) {
+                slot = ~next;
+                next = top;
+                top = sp > 0 ? RSI_STK(sp - 1) : kDone;
+                sp = sp > 0 ? sp - 1 : 0;
+            }
+        }   // node steps
+        // leaf phase: all parked leaves of the warp at once, once kLeafMin
+        // lanes hold one or no lane can move on without it
         const unsigned pend = __ballot_sync(kFull, active && slot >= 0);
-        const unsigned moving = __ballot_sync(kFull, active && !stop && next != kDone && (next >= 0 || slot < 0));
-        if (pend && (__popc(pend) >= kLeafMin || moving == 0)) {
+        if (pend && (__popc(pend) >= kLeafMin ||
+                     __ballot_sync(kFull, active && !stop && next != kDone && (next >= 0 || slot < 0)) == 0)) {
             if (slot >= 0) {
                 if (STATS) ++tests;
                 const Tri tr = load_tri(BATCHED ? l_tris : A.tris, slot);
@@ -594,6 +628,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
             ray = -1;
         }
     }
+#undef RSI_STK
     if (STATS) {
         for (int off = 16; off; off >>= 1) {
             visits += __shfl_xor_sync(kFull, visits, off);
@@ -1780,7 +1815,7 @@ __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
 
 template <int MODE, bool STATS, int STACK, bool BATCHED, int NW>
 void launch_fp32(const QueryArgs& A, const BatchArgs& B, int grid, int block, cudaStream_t s) {
-    k_query_fp32<MODE, STATS, STACK, BATCHED, NW><<<grid, block, 0, s>>>(A, B);
+    k_query_fp32<MODE, STATS, STACK, BATCHED, NW><<<grid, block, trav_smem_bytes(STACK, block), s>>>(A, B);
 }
 
 // Stack entries a traversal needs: the binary walk pushes at most one entry

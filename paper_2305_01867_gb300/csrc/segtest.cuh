@@ -15,7 +15,7 @@ namespace segtest {
 constexpr float kU = 5.9604645e-8f;        // unit roundoff of FP32, 2^-24
 constexpr float kErrK = 16.0f * kU;        // bound factor of a dot(cross) in FP32
 constexpr float kTauHi = 1.000001e-6f;     // tau, rounded up
-constexpr float kWiden = 1e-6f;            // relative widening of slab intervals
+constexpr float kSlabGrow = 1.000002f;     // growth of the slab interval's upper end
 
 enum { kMiss = 0, kHit = 1, kBand = 2 };
 
@@ -46,7 +46,7 @@ __device__ __forceinline__ SegF make_seg(float3 s, float3 e, float dmx, float dm
     // segment enters through (the lower plane when inv >= 0, the upper one
     // otherwise), up for the plane it leaves through.  The FMA's exact sum is
     // then never inside (lo - slo) inv, so only its single rounding remains,
-    // which the relative widening of the interval covers.
+    // which the growth of the interval covers (see slab6).
     const float3 slo = make_float3(__fadd_ru(s.x, px), __fadd_ru(s.y, py), __fadd_ru(s.z, pz));
     const float3 shi = make_float3(__fsub_rd(s.x, px), __fsub_rd(s.y, py), __fsub_rd(s.z, pz));
     g.olo = make_float3(g.inv.x >= 0.0f ? __fmul_rd(-slo.x, g.inv.x) : __fmul_ru(-slo.x, g.inv.x),
@@ -58,34 +58,48 @@ __device__ __forceinline__ SegF make_seg(float3 s, float3 e, float dmx, float dm
     return g;
 }
 
+// Three-input minimum / maximum (one instruction on sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Does the segment pass through the padded box?  One FMA per plane (the
-// offsets of make_seg), the entry and exit parameters per axis, their
-// intersection widened by 1e-6 relative.
+// offsets of make_seg) gives the entry and exit parameters per axis; the
+// segment's part [0, 1] of the line meets the box when
+//     max(tn, 0) <= min(tf, 1) x kSlabGrow.
+// Each computed parameter is within one rounding (relative 2^-24) of the
+// exact one, on the conservative side of the padded plane, so whenever the
+// exact interval [max(tn, 0), min(tf, 1)] is non-empty the computed left
+// side is at most (1 + 2^-24) / (1 - 2^-24) times the right one before the
+// growth, well inside kSlabGrow (2e-6): no box the segment meets is culled.
 __device__ __forceinline__ bool slab6(float xlo, float ylo, float zlo, float xhi, float yhi, float zhi,
                                       const SegF& g) {
-    float t0x = fmaf(xlo, g.inv.x, g.olo.x), t1x = fmaf(xhi, g.inv.x, g.ohi.x);
-    float t0y = fmaf(ylo, g.inv.y, g.olo.y), t1y = fmaf(yhi, g.inv.y, g.ohi.y);
-    float t0z = fmaf(zlo, g.inv.z, g.olo.z), t1z = fmaf(zhi, g.inv.z, g.ohi.z);
-    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
-    tn = tn - fabsf(tn) * kWiden;
-    tf = tf + fabsf(tf) * kWiden;
-    return tn <= tf && tn <= 1.0f && tf >= 0.0f;
+    const float t0x = fmaf(xlo, g.inv.x, g.olo.x), t1x = fmaf(xhi, g.inv.x, g.ohi.x);
+    const float t0y = fmaf(ylo, g.inv.y, g.olo.y), t1y = fmaf(yhi, g.inv.y, g.ohi.y);
+    const float t0z = fmaf(zlo, g.inv.z, g.olo.z), t1z = fmaf(zhi, g.inv.z, g.ohi.z);
+    const float tn = fmaxf(max3f(fminf(t0x, t1x), fminf(t0y, t1y), fminf(t0z, t1z)), 0.0f);
+    const float tf = fminf(min3f(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fmaxf(t0z, t1z)), 1.0f);
+    return tn <= tf * kSlabGrow;
 }
 __device__ __forceinline__ bool slab(const float4& bmin, const float4& bmax, const SegF& g) {
     return slab6(bmin.x, bmin.y, bmin.z, bmax.x, bmax.y, bmax.z, g);
 }
 // The same test, also giving the length of the parameter interval inside the box.
 __device__ __forceinline__ bool slab_len(const float4& bmin, const float4& bmax, const SegF& g, float& len) {
-    float t0x = fmaf(bmin.x, g.inv.x, g.olo.x), t1x = fmaf(bmax.x, g.inv.x, g.ohi.x);
-    float t0y = fmaf(bmin.y, g.inv.y, g.olo.y), t1y = fmaf(bmax.y, g.inv.y, g.ohi.y);
-    float t0z = fmaf(bmin.z, g.inv.z, g.olo.z), t1z = fmaf(bmax.z, g.inv.z, g.ohi.z);
-    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
-    tn = tn - fabsf(tn) * kWiden;
-    tf = tf + fabsf(tf) * kWiden;
-    len = fminf(tf, 1.0f) - fmaxf(tn, 0.0f);
-    return tn <= tf && tn <= 1.0f && tf >= 0.0f;
+    const float t0x = fmaf(bmin.x, g.inv.x, g.olo.x), t1x = fmaf(bmax.x, g.inv.x, g.ohi.x);
+    const float t0y = fmaf(bmin.y, g.inv.y, g.olo.y), t1y = fmaf(bmax.y, g.inv.y, g.ohi.y);
+    const float t0z = fmaf(bmin.z, g.inv.z, g.olo.z), t1z = fmaf(bmax.z, g.inv.z, g.ohi.z);
+    const float tn = fmaxf(max3f(fminf(t0x, t1x), fminf(t0y, t1y), fminf(t0z, t1z)), 0.0f);
+    const float tf = fminf(min3f(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fmaxf(t0z, t1z)), 1.0f);
+    len = tf - tn;
+    return tn <= tf * kSlabGrow;
 }
 
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
