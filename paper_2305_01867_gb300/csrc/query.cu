@@ -2271,8 +2271,9 @@ using namespace rsi;   // the kernels and launchers above
 // queue with bounded waits, as in streaming batched plans), so copies and
 // traversal overlap without a kernel tail per chunk (the first chunk is
 // small so that the traversal starts early); one FP64 pass then settles the
-// whole queue and the results are copied out.
-constexpr int64_t kHostWhole = (int64_t)1 << 26;
+// whole queue and the results are copied out.  Up to 2^28 segments (8 GB of
+// staging); a batch whose staging does not fit goes through the two slots.
+constexpr int64_t kHostWhole = (int64_t)1 << 28;
 
 int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, int mode, const rsi_options& o,
                uint8_t* h_hit, int32_t* h_count, uint8_t* h_amb, rsi_stats* stats, cudaStream_t s,
@@ -2424,7 +2425,9 @@ extern "C" int rsi_query_host(rsi_bvh_t h, const float* h_from, const float* h_t
         rsi::DeviceCtx* c = rsi::device_ctx();
         if (!c) return rsi::fail(RSI_ERR_CUDA, "rsi_query_host: no device context");
         std::lock_guard<std::mutex> lock(c->host_mu);   // one host-buffer query per device at a time
-        return host_whole(h, h_from, h_to, n_rays, mode, o, h_hit, h_count, h_ambiguous, stats, s, c);
+        rc = host_whole(h, h_from, h_to, n_rays, mode, o, h_hit, h_count, h_ambiguous, stats, s, c);
+        // no room to stage the whole batch (nothing was enqueued): stream it through the slots
+        if (rc != RSI_ERR_OOM) return rc;
     }
     const int64_t chunk = std::min<int64_t>(n_rays, kHostChunk);
     const int64_t n_chunks = (n_rays + chunk - 1) / chunk;

@@ -386,6 +386,30 @@ def test_host_path_chunk_boundaries(rsi, n):
             assert h["stats"]["n_rays"] == n and h["stats"]["device_error"] == 0
 
 
+def test_host_path_whole_batch_above_2_26(rsi):
+    """A host batch of 2^26 + 12,345 segments (1.6 GB of segments in, 64
+    chunks): staged whole, its answers in both modes at once equal the
+    device path's on every segment.  Segments drawn on the device from a
+    seeded generator over the c1 mesh's box (the bulk is what is tested)."""
+    n = (1 << 26) + 12_345
+    mesh = W.config_mesh("c1")
+    bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles))
+    lo = torch.tensor(mesh.vertices.min(0), device="cuda")
+    hi = torch.tensor(mesh.vertices.max(0), device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(2626)
+    span = (hi - lo) * 1.2
+    dF = (lo - 0.1 * (hi - lo) + torch.rand(n, 3, device="cuda", generator=g) * span).contiguous()
+    dE = (lo - 0.1 * (hi - lo) + torch.rand(n, 3, device="cuda", generator=g) * span).contiguous()
+    d = bvh.query(dF, dE, "both")
+    pF, pE = dF.cpu().pin_memory(), dE.cpu().pin_memory()
+    del dF, dE
+    h = bvh.query_host(pF, pE, "both", stats=True)
+    assert h["stats"]["n_rays"] == n and h["stats"]["device_error"] == 0
+    for k in ("hit", "count", "ambiguous"):
+        assert torch.equal(h[k], d[k].cpu()), k
+    assert int(d["hit"].sum()) > n // 10
+
+
 @pytest.mark.parametrize("cfg,n", [("c2", 10_000_000), ("c3", 2_000_000)])
 def test_fp32_decisions_equal_fp64_everywhere(rsi, cfg, n):
     """Every segment of a full-size batch (c2: all 1e7; c3: a 2e6 slice with
