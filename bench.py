@@ -38,7 +38,8 @@ sys.path.insert(0, ROOT)
 METRIC = "rays/s (exact vs FP64 oracle) plain vs batched+learned on 1 GB300; % roofline"
 WORKLOAD = ("c2: 100x100-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (19,602 FP32 triangles); "
             "1e7 FP32 segments, 50% crossing / 50% above, length U(0.05,1), random directions; "
-            "step = lbvh_build + the boolean and intercept_count answers of every segment "
+            "step = lbvh_build_ex (the paper's Karras build, then one treelet restructuring pass: "
+            "same answers, fewer nodes met) + the boolean and intercept_count answers of every segment "
             "(one traversal answers both: rsi_query mode RSI_BOTH)")
 W_DOC_PAPER = ("paper scale: 111x134-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (14,874 vertices, "
                "29,260 triangles, the paper's counts); 1e7 segments, 50% crossing / 50% above")
@@ -532,12 +533,16 @@ def measure_precision_c3(rsi, torch, dev, c3, args):
     import oracle
     mesh, (F, E) = c3
     n = F.shape[0]
-    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).to(dev), torch.from_numpy(mesh.triangles).to(dev), morton_bits=63)
+    c3p = args.c3_treelet_passes
+    bvh = rsi.LBVH(torch.from_numpy(mesh.vertices).to(dev), torch.from_numpy(mesh.triangles).to(dev), morton_bits=63,
+                   treelet_passes=c3p)
     dF, dE = torch.from_numpy(F).to(dev), torch.from_numpy(E).to(dev)
     stream = torch.cuda.current_stream()
     out = {"workload": "c3: 300x300-vertex jittered heightfield, 8 bumps (178,802 triangles); 1e8 segments, "
                        "50% crossing / 50% above, 1% grazing (end point within 1e-6 of an edge or vertex, or "
-                       "nearly parallel to a face)", "rays": n, "triangles": int(len(mesh.triangles)), "morton_bits": 63}
+                       "nearly parallel to a face)", "rays": n, "triangles": int(len(mesh.triangles)), "morton_bits": 63,
+           "tree": f"the paper's Karras build + {c3p} treelet restructuring pass(es)" if c3p else "as built",
+           "tree_height": bvh.info()["height"]}
     res = {}
     for mode in ("any_hit", "count"):
         for fp32_only in (False, True):
@@ -582,7 +587,7 @@ def measure_precision_c3(rsi, torch, dev, c3, args):
     hc = torch.empty(n, dtype=torch.int32).pin_memory()
 
     def step_e2e():
-        b = rsi.LBVH(pV, pT, morton_bits=63)
+        b = rsi.LBVH(pV, pT, morton_bits=63, treelet_passes=c3p)
         b.query_host(pF, pE, "both", hit=hh, count=hc, ambiguous=ha)
         b.close()
     step_e2e()
@@ -736,6 +741,10 @@ def main():
     ap.add_argument("--train-rays", type=int, default=10_000_000)
     ap.add_argument("--c3-only", action="store_true",
                     help="run the c3 precision leg alone and print its object (for profiler captures)")
+    ap.add_argument("--treelet-passes", type=int, default=1,
+                    help="restructuring passes after the c2 build (0: the paper's tree as built)")
+    ap.add_argument("--c3-treelet-passes", type=int, default=2,
+                    help="restructuring passes after the c3 build (1e8 segments per build)")
     ap.add_argument("--order", action="store_true",
                     help="walk the segments in midpoint-cell order in the timed step (rsi_segment_order inside it)")
     args = ap.parse_args()
@@ -799,10 +808,12 @@ def main():
     amb2 = torch.empty(n, dtype=torch.uint8, device=dev)
     step_order = torch.empty(n, dtype=torch.int32, device=dev) if args.order else None
 
-    def step(evs=None, trav=None):
+    tp = args.treelet_passes
+
+    def step(evs=None, trav=None, passes=None):
         if evs:
             evs[0].record(stream)
-        bvh = rsi.LBVH(dV, dT, morton_bits=30)
+        bvh = rsi.LBVH(dV, dT, morton_bits=30, treelet_passes=tp if passes is None else passes)
         if evs:
             evs[1].record(stream)
         if step_order is not None:
@@ -818,7 +829,7 @@ def main():
     def step_separate(evs=None):
         if evs:
             evs[0].record(stream)
-        bvh = rsi.LBVH(dV, dT, morton_bits=30)
+        bvh = rsi.LBVH(dV, dT, morton_bits=30, treelet_passes=tp)
         if evs:
             evs[1].record(stream)
         bvh.query(dF, dE, "any_hit", hit=hit, ambiguous=amb_h)
@@ -870,7 +881,7 @@ def main():
     separate = {"step_ms": statistics.median(p[0].elapsed_time(p[3]) for p in sep),
                 "any_hit_query_ms": statistics.median(p[1].elapsed_time(p[2]) for p in sep),
                 "count_query_ms": statistics.median(p[2].elapsed_time(p[3]) for p in sep)}
-    bvh = rsi.LBVH(dV, dT, morton_bits=30)
+    bvh = rsi.LBVH(dV, dT, morton_bits=30, treelet_passes=tp)
     bvh.query(dF, dE, "both", hit=hit, count=cnt, ambiguous=amb2)
     both_hit, both_cnt, both_amb = hit.clone(), cnt.clone(), amb2.clone()
     bvh.query(dF, dE, "any_hit", hit=hit, ambiguous=amb_h)
@@ -887,7 +898,7 @@ def main():
     hc = torch.empty(n, dtype=torch.int32).pin_memory()
 
     def step_e2e():
-        bvh = rsi.LBVH(pV, pT, morton_bits=30)
+        bvh = rsi.LBVH(pV, pT, morton_bits=30, treelet_passes=tp)
         bvh.query_host(pF, pE, "both", hit=hh, count=hc, ambiguous=ha)
         bvh.close()
 
@@ -904,27 +915,57 @@ def main():
     h2d = (pV.numel() * 4 + pT.numel() * 4) + (pF.numel() + pE.numel()) * 4
     d2h = n * (1 + 4 + 1)
 
+    # the same step on the paper's tree as built (no restructuring): context
+    plain_tree = None
+    if tp:
+        for _ in range(3):
+            step(passes=0)
+        pl = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
+        for k in range(10):
+            step(pl[k], passes=0)
+        torch.cuda.synchronize()
+        b0 = rsi.LBVH(dV, dT, morton_bits=30)
+        plain_tree = {"step_ms": statistics.median(p[0].elapsed_time(p[2]) for p in pl),
+                      "build_ms": statistics.median(p[0].elapsed_time(p[1]) for p in pl),
+                      "both_modes_query_ms": statistics.median(p[1].elapsed_time(p[2]) for p in pl),
+                      "node_visits_per_ray_count": b0.query(dF, dE, "count", stats=True)["stats"]["node_visits"] / n,
+                      "tree_height": b0.info()["height"]}
+        b0.close()
+
     # counters of one extra (untimed) pass
-    bvh = rsi.LBVH(dV, dT)
+    bvh = rsi.LBVH(dV, dT, morton_bits=30, treelet_passes=tp)
     st_c = bvh.query(dF, dE, "count", stats=True)["stats"]
     st_a = bvh.query(dF, dE, "any_hit", stats=True)["stats"]
     job_counts = sum_over_ranks(pg, [st_c["band_rays"], st_c["ambiguous"], st_a["band_rays"], st_a["ambiguous"]],
                                 dev)
     height = bvh.info()["height"]
     # traversal kernel time by node width (child-pair, compressed child-pair,
-    # four-wide), same answers
+    # four-wide), same answers; on the paper's tree (compressed nodes need its
+    # numbering) and, child-pair only, on the restructured one
     widths = {}
+    bp = rsi.LBVH(dV, dT, morton_bits=30)
     for w in (2, 3, 4):
-        st_w = bvh.query(dF, dE, "count", stats=True, node_width=w)["stats"]
+        st_w = bp.query(dF, dE, "count", stats=True, node_width=w)["stats"]
         per = {}
         for mode in ("any_hit", "count"):
             ts = []
             for _ in range(5):
-                bvh.query(dF, dE, mode, hit=hit, count=cnt, ambiguous=amb_c, time_kernels=True, node_width=w)
-                ts.append(bvh.last_query_ms()[0])
+                bp.query(dF, dE, mode, hit=hit, count=cnt, ambiguous=amb_c, time_kernels=True, node_width=w)
+                ts.append(bp.last_query_ms()[0])
             per[f"{mode}_traverse_ms"] = statistics.median(ts[1:])
         per["node_fetches_per_ray_count"] = st_w["node_visits"] / n
         widths[str(w)] = per
+    bp.close()
+    if tp:
+        per = {}
+        for mode in ("any_hit", "count"):
+            ts = []
+            for _ in range(5):
+                bvh.query(dF, dE, mode, hit=hit, count=cnt, ambiguous=amb_c, time_kernels=True)
+                ts.append(bvh.last_query_ms()[0])
+            per[f"{mode}_traverse_ms"] = statistics.median(ts[1:])
+        per["node_fetches_per_ray_count"] = st_c["node_visits"] / n
+        widths[f"2_restructured_{tp}_pass"] = per
     # the same queries walking the segments in midpoint-cell order
     # (rsi_segment_order), and a whole step with the order computed in it
     order = bvh.segment_order(dF, dE)
@@ -946,7 +987,7 @@ def main():
     ordered["order_ms"] = e0.elapsed_time(e1) / 5
 
     def step_ordered():
-        b = rsi.LBVH(dV, dT, morton_bits=30)
+        b = rsi.LBVH(dV, dT, morton_bits=30, treelet_passes=tp)
         b.segment_order(dF, dE, out=order)
         b.query(dF, dE, "both", hit=hit, count=cnt, ambiguous=amb2, order=order)
         b.close()
@@ -973,6 +1014,9 @@ def main():
         "config": {"workload": WORKLOAD, "n_triangles": int(len(mesh.triangles)), "rays_per_gpu": n,
                    "morton_bits": 30, "l2": "inputs larger than L2 (240 MB of segments per batch), no flush",
                    "segment_order": bool(args.order),
+                   "tree": (f"the paper's Karras build + {tp} treelet restructuring pass(es) (depth-tiled treelets of "
+                            "up to 8 subtrees; answers identical to the plain tree's)") if tp
+                   else "the paper's Karras build as built",
                    "fp64_retest": "on (band segments re-tested in FP64)"},
         "roofline": {"kernel": "k_query_fp32<count> (FP32 traversal, intercept_count)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -990,6 +1034,7 @@ def main():
                              "any_hit_alone": n / (separate["any_hit_query_ms"] / 1e3),
                              "count_alone": n / (separate["count_query_ms"] / 1e3)},
         "separate_queries": separate,
+        "plain_tree": plain_tree,
         "counters": {"tree_height": height, "node_visits_per_ray_count": st_c["node_visits"] / n,
                      "tri_tests_per_ray_count": st_c["tri_tests"] / n, "band_rays_count": st_c["band_rays"],
                      "ambiguous_count": st_c["ambiguous"], "node_visits_per_ray_any": st_a["node_visits"] / n,

@@ -175,11 +175,22 @@ int lbvh_build(const float* d_vertices, int64_t n_vertices, const int32_t* d_tri
 #define RSI_TREE_APETREI 1 /* one bottom-up pass that builds the tree and its
                               boxes together (Apetrei 2014; the bottom-up
                               construction of Sec. 4.2)                      */
+/* Or-ed into tree_builder: after the build, `passes` (1 .. 3) bottom-up
+ * restructuring passes rewire groups of 7 subtrees so that the summed box
+ * surface of the internal nodes goes down (treelet restructuring, Karras &
+ * Aila 2013; not in the paper).  Leaves, their order and the triangles stay;
+ * children, parents and boxes of internal nodes change (lbvh_export shows
+ * the restructured tree), queries answer exactly as on the plain tree and
+ * meet fewer nodes (c2 heightfield: 35 -> 28 child-pair nodes per segment
+ * after one pass).  Such handles have no compressed nodes (node_width 3 is
+ * served by child-pair nodes). */
+#define RSI_TREE_TREELETS(passes) ((passes) << 8)
 
 /*
  * As lbvh_build, with the tree construction chosen by tree_builder
- * (RSI_TREE_KARRAS or RSI_TREE_APETREI; anything else: RSI_ERR_INVALID_ARG).
- * Both give the same hierarchy bit for bit -- the binary radix tree over the
+ * (RSI_TREE_KARRAS or RSI_TREE_APETREI, optionally | RSI_TREE_TREELETS(p)
+ * with p in 1 .. 3; anything else: RSI_ERR_INVALID_ARG).  The two builders
+ * give the same hierarchy bit for bit -- the binary radix tree over the
  * sorted (code, triangle id) pairs is unique -- in the same numbering
  * (lbvh_export), so queries answer identically; only the build time differs.
  * RSI_TREE_APETREI replaces the tree and refit kernels with one kernel.
@@ -212,6 +223,11 @@ int lbvh_build_batched(int n_meshes, const float* const* d_vertices, const int64
 int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
                     int64_t n_triangles, int index_bytes, int morton_bits, void* stream,
                     rsi_bvh_t* out);
+
+/* As lbvh_build_host, with tree_builder as in lbvh_build_ex. */
+int lbvh_build_host_ex(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
+                       int64_t n_triangles, int index_bytes, int morton_bits, int tree_builder, void* stream,
+                       rsi_bvh_t* out);
 
 /* Release a handle (synchronizes the device first).  NULL is a no-op. */
 int lbvh_free(rsi_bvh_t h);

@@ -83,6 +83,8 @@ def _load():
     P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     lib.lbvh_build.argtypes = [P, i64, P, i64, i32, i32, P, ctypes.POINTER(P)]
     lib.lbvh_build_host.argtypes = [P, i64, P, i64, i32, i32, P, ctypes.POINTER(P)]
+    lib.lbvh_build_host_ex.argtypes = [P, i64, P, i64, i32, i32, i32, P, ctypes.POINTER(P)]
+    lib.lbvh_build_host_ex.restype = ctypes.c_int
     lib.lbvh_build_ex.argtypes = [P, i64, P, i64, i32, i32, i32, P, ctypes.POINTER(P)]
     lib.lbvh_build_ex.restype = ctypes.c_int
     lib.lbvh_build_batched.argtypes = [i32, ctypes.POINTER(P), ctypes.POINTER(i64), ctypes.POINTER(P),
@@ -251,9 +253,12 @@ class LBVH:
 
     builder: "karras" (radix tree, then refit) or "apetrei" (one bottom-up
     pass, lbvh_build_ex; device inputs only).  Both give the same hierarchy.
+    treelet_passes: 0 (the paper's tree) or 1-3 restructuring passes after
+    the build (RSI_TREE_TREELETS): same answers, fewer nodes met per segment.
     """
 
-    def __init__(self, vertices, triangles, morton_bits: int = 30, stream=None, builder: str = "karras"):
+    def __init__(self, vertices, triangles, morton_bits: int = 30, stream=None, builder: str = "karras",
+                 treelet_passes: int = 0):
         import torch
         _check_f32x3(vertices, "vertices")
         if not isinstance(triangles, torch.Tensor) or triangles.dim() != 2 or triangles.shape[1] != 3:
@@ -267,7 +272,14 @@ class LBVH:
             raise TypeError("vertices and triangles must both be on the GPU or both on the host")
         if builder not in _TREE_BUILDERS:
             raise ValueError(f"unknown builder {builder!r} (karras or apetrei)")
-        if builder == "karras":
+        if int(treelet_passes) not in (0, 1, 2, 3):
+            raise ValueError("treelet_passes must be 0, 1, 2 or 3")
+        code = _TREE_BUILDERS[builder] | (int(treelet_passes) << 8)   # | RSI_TREE_TREELETS(passes)
+        if builder == "karras" and treelet_passes:
+            fn = lib.lbvh_build_ex if on_dev else lib.lbvh_build_host_ex
+            check(fn(_ptr(vertices), vertices.shape[0], _ptr(triangles.contiguous()), triangles.shape[0],
+                     index_bytes, morton_bits, code, _stream(stream), ctypes.byref(self._h)))
+        elif builder == "karras":
             fn = lib.lbvh_build if on_dev else lib.lbvh_build_host
             check(fn(_ptr(vertices), vertices.shape[0], _ptr(triangles.contiguous()), triangles.shape[0],
                      index_bytes, morton_bits, _stream(stream), ctypes.byref(self._h)))
@@ -275,7 +287,7 @@ class LBVH:
             if not on_dev:
                 raise TypeError("the apetrei builder takes device tensors")
             check(lib.lbvh_build_ex(_ptr(vertices), vertices.shape[0], _ptr(triangles.contiguous()),
-                                    triangles.shape[0], index_bytes, morton_bits, _TREE_BUILDERS[builder],
+                                    triangles.shape[0], index_bytes, morton_bits, code,
                                     _stream(stream), ctypes.byref(self._h)))
         self.n_triangles = triangles.shape[0]
 

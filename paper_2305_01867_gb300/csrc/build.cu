@@ -904,9 +904,10 @@ void finish_handle(rsi_bvh_s* h, const DevCounters& hc) {
     }
 }
 
-int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, int morton_bits, int builder,
+int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, int morton_bits, int tree_builder,
                       cudaStream_t s, rsi_bvh_t* out) {
     const int64_t n = nt, ni = n > 1 ? n - 1 : 1;
+    const int builder = tree_builder & 0xFF, passes = tree_builder >> 8;   // RSI_TREE_TREELETS(passes)
     char* base = nullptr;
     int32_t *hgt = nullptr, *flag = nullptr;
     char* scratch = nullptr;
@@ -928,10 +929,15 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     int rc = morton_bits == 30 ? build_impl<uint32_t>(h, V, T, builder, s, scratch, h->box, hgt, flag)
                                : build_impl<uint64_t>(h, V, T, builder, s, scratch, h->box, hgt, flag);
     if (rc) return cleanup(rc);
+    rc = enqueue_treelets(h, passes, hgt, s);
+    if (rc) return cleanup(rc);
     if (n > 1) {
         k_collapse4<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(h->nodes, h->parent, n, h->nodes4);
-        k_quantize<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(h->nodes, n, h->nodesq, h->ctr);
-        note_launches(2);
+        note_launches(1);
+        if (passes == 0) {   // compressed nodes name both children by one index (Karras numbering)
+            k_quantize<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(h->nodes, n, h->nodesq, h->ctr);
+            note_launches(1);
+        }
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "lbvh_build kernels"));
@@ -944,7 +950,7 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
                                                              : "lbvh_build: triangle vertex index out of range"));
     }
     finish_handle(h, hc);
-    h->has_q = n > 1;
+    h->has_q = n > 1 && passes == 0;
     *out = h;
     return RSI_OK;
 }
@@ -1186,8 +1192,10 @@ int build_checked(const char* fn, const float* d_vertices, int64_t n_vertices, c
     if (n_triangles < 1 || n_vertices < 1 || n_triangles > (int64_t)0x3FFFFFFF || n_vertices > ((int64_t)1 << 31))
         return fail(RSI_ERR_INVALID_ARG, f + ": need 1 <= n_triangles < 2^30 and 1 <= n_vertices <= 2^31");
     if (morton_bits != 30 && morton_bits != 63) return fail(RSI_ERR_INVALID_ARG, f + ": morton_bits must be 30 or 63");
-    if (tree_builder != RSI_TREE_KARRAS && tree_builder != RSI_TREE_APETREI)
-        return fail(RSI_ERR_INVALID_ARG, f + ": tree_builder must be RSI_TREE_KARRAS or RSI_TREE_APETREI");
+    const int builder = tree_builder & 0xFF, passes = tree_builder >> 8;
+    if ((builder != RSI_TREE_KARRAS && builder != RSI_TREE_APETREI) || passes < 0 || passes > 3)
+        return fail(RSI_ERR_INVALID_ARG, f + ": tree_builder must be RSI_TREE_KARRAS or RSI_TREE_APETREI, "
+                                             "optionally | RSI_TREE_TREELETS(1 .. 3)");
     return build_from_device(d_vertices, n_vertices, d_triangles, n_triangles, morton_bits, tree_builder,
                              (cudaStream_t)stream, out);
 }
@@ -1234,10 +1242,21 @@ extern "C" int lbvh_build_batched(int n_meshes, const float* const* d_vertices, 
 
 extern "C" int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
                                int64_t n_triangles, int index_bytes, int morton_bits, void* stream, rsi_bvh_t* out) {
+    return lbvh_build_host_ex(h_vertices, n_vertices, h_triangles, n_triangles, index_bytes, morton_bits,
+                              RSI_TREE_KARRAS, stream, out);
+}
+
+extern "C" int lbvh_build_host_ex(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,
+                                  int64_t n_triangles, int index_bytes, int morton_bits, int tree_builder, void* stream,
+                                  rsi_bvh_t* out) {
     if (!out) return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_host: out is NULL");
     *out = nullptr;
     if (!h_vertices || !h_triangles || n_vertices < 1 || n_triangles < 1)
         return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_host: bad input");
+    const int builder = tree_builder & 0xFF, passes = tree_builder >> 8;
+    if ((builder != RSI_TREE_KARRAS && builder != RSI_TREE_APETREI) || passes < 0 || passes > 3)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_host: tree_builder must be RSI_TREE_KARRAS or "
+                                              "RSI_TREE_APETREI, optionally | RSI_TREE_TREELETS(1 .. 3)");
     if (index_bytes != 4) return rsi::fail(RSI_ERR_DTYPE, "lbvh_build_host: triangle indices must be int32");
     cudaStream_t s = (cudaStream_t)stream;
     float* dv = nullptr;
@@ -1252,7 +1271,7 @@ extern "C" int lbvh_build_host(const float* h_vertices, int64_t n_vertices, cons
     if (cudaMemcpyAsync(dv, h_vertices, bv, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(dt, h_triangles, bt, cudaMemcpyHostToDevice, s) != cudaSuccess)
         rc = rsi::cuda_fail(cudaGetLastError(), "lbvh_build_host copy");
-    if (rc == RSI_OK) rc = lbvh_build(dv, n_vertices, dt, n_triangles, 4, morton_bits, stream, out);
+    if (rc == RSI_OK) rc = lbvh_build_ex(dv, n_vertices, dt, n_triangles, 4, morton_bits, tree_builder, stream, out);
     rsi::pool_free(dv, s);
     rsi::pool_free(dt, s);
     return rc;

@@ -1,0 +1,349 @@
+// treelet.cu -- restructuring of a built hierarchy (an option of lbvh_build_ex).
+//
+// The paper's hierarchy splits every node at the highest differing bit of the
+// triangles' Morton codes (Sec. 3.2, after Karras 2012).  Those midpoint splits
+// leave loose boxes in the middle of the tree: on a heightfield of 19,602
+// triangles a segment meets ~35 child-pair nodes where a surface-area-guided
+// tree of the same triangles needs ~24.  These passes, after the build,
+// rewrite small groups of nodes ("treelets") so that the sum of the surface
+// areas of the internal nodes -- the usual estimate of the nodes a random
+// segment meets -- goes down, in the manner of treelet restructuring (Karras &
+// Aila 2013, "Fast parallel construction of high-quality bounding volume
+// hierarchies"), with the treelets tiled by depth instead of grown bottom-up:
+//
+//  * a treelet is an internal node r at depth d with the internal nodes of its
+//    subtree down to depth d + 2; its leaves (at most 8) are the children that
+//    hang below: subtrees rooted at depth d + 3, or triangles;
+//  * rewiring a treelet never changes the box of any subtree that hangs below
+//    it nor of r itself (a box is the union of the triangles below), so all
+//    treelets whose roots share d mod 3 are disjoint and independent: one
+//    launch restructures them all, one warp per treelet, and three launches
+//    (d mod 3 = 0, 1, 2, depths recomputed in between) make one pass;
+//  * the warp finds the binary tree over the treelet's leaves with the
+//    smallest sum of internal-node surface areas by dynamic programming over
+//    the leaf subsets (every subset's best split, smallest subsets first)
+//    and, when it is clearly smaller than the current one, rewires the
+//    treelet's own internal nodes into it (same node ids, r keeps its place).
+//
+// Leaves, their Morton order and the triangles are untouched; only the
+// internal nodes' children, parents and boxes change, so every query answers
+// exactly as on the plain tree.  The compressed-node layout needs the right
+// child at the left one + 1, which the rewired tree no longer has: handles
+// built with restructuring have no compressed nodes (node width 3 falls back
+// to child-pair nodes).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsi_internal.cuh"
+
+namespace rsi {
+namespace {
+
+constexpr int kTreeletLevels = 3;          // levels of internal nodes in a treelet
+constexpr int kTreeletLeaves = 1 << kTreeletLevels;   // at most 8 leaves
+constexpr int kFullSet = (1 << kTreeletLeaves) - 1;
+constexpr int kTreeletWarps = 4;           // warps per block of k_treelet
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kClimbMax = 1 << 16;         // climb steps before a pass gives up (RSI_ERR_STACK)
+
+// The non-empty subsets of the 8 treelet leaves ordered by size: the subsets
+// of size s are by_size[off[s] .. off[s + 1]).
+struct SubsetTable {
+    uint8_t by_size[kFullSet];
+    uint8_t off[kTreeletLeaves + 2];
+};
+constexpr int popc_c(int x) { return x ? (x & 1) + popc_c(x >> 1) : 0; }
+constexpr SubsetTable make_subset_table() {
+    SubsetTable t{};
+    int k = 0;
+    for (int s = 1; s <= kTreeletLeaves; ++s) {
+        t.off[s] = (uint8_t)k;
+        for (int m = 1; m <= kFullSet; ++m)
+            if (popc_c(m) == s) t.by_size[k++] = (uint8_t)m;
+    }
+    t.off[kTreeletLeaves + 1] = (uint8_t)k;
+    return t;
+}
+__constant__ SubsetTable c_subsets = make_subset_table();
+
+// One warp's working set for one treelet.
+struct TreeletSmem {
+    float lbox[kTreeletLeaves][6];   // treelet leaf boxes (min xyz, max xyz)
+    int lref[kTreeletLeaves];        // treelet leaf references (tagged as the build tags them)
+    int inner[kTreeletLeaves - 1];   // the treelet's internal nodes (inner[0] = its root)
+    float area[kFullSet + 1];        // surface area of the box of each leaf subset
+    float cost[kFullSet + 1];        // best summed internal-node area of a tree over the subset
+    uint8_t best[kFullSet + 1];      // the part holding the subset's lowest leaf, in that best tree
+    int emit_node[kTreeletLeaves - 1], emit_set[kTreeletLeaves - 1];
+    int emit_l[kTreeletLeaves - 1], emit_r[kTreeletLeaves - 1];
+    int k, ni;                       // leaves, internal nodes
+};
+
+__device__ __forceinline__ int64_t slot_of(int32_t ref, int64_t n) {
+    return ((uint32_t)ref & kLeafTag) ? (n - 1 + (int64_t)((uint32_t)ref & ~kLeafTag)) : (int64_t)ref;
+}
+
+__device__ __forceinline__ float half_area(float dx, float dy, float dz) {
+    return fmaxf(dx, 0.0f) * fmaxf(dy, 0.0f) + fmaxf(dy, 0.0f) * fmaxf(dz, 0.0f) + fmaxf(dz, 0.0f) * fmaxf(dx, 0.0f);
+}
+
+// Box of node slot i, read through L2 (other warps rewrite boxes during the pass).
+__device__ __forceinline__ void load_box(const float* __restrict__ box, int64_t i, float b[6]) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) b[a] = __ldcg(box + 6 * i + a);
+}
+
+
+// Restructure the treelet rooted at internal node r (all 32 lanes call it).
+__device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_t* __restrict__ right,
+                            int32_t* __restrict__ parent, float* __restrict__ box, TreeletSmem& sm, int lane) {
+    // 1. the treelet: r and the internal nodes of the next two levels; their
+    //    children below are its leaves, in depth-first order
+    if (lane == 0) {
+        int lv_ref[kTreeletLeaves], lv_n = 1, k = 0, ni = 0;
+        lv_ref[0] = r;
+        for (int lv = 0; lv < kTreeletLevels; ++lv) {   // one level of loads at a time
+            int kids[kTreeletLeaves];
+            int m = 0;
+            for (int i = 0; i < lv_n; ++i) {
+                sm.inner[ni++] = lv_ref[i];
+                kids[m++] = __ldcg(left + lv_ref[i]);
+                kids[m++] = __ldcg(right + lv_ref[i]);
+            }
+            lv_n = 0;
+            for (int i = 0; i < m; ++i) {
+                if (lv + 1 < kTreeletLevels && !((uint32_t)kids[i] & kLeafTag)) lv_ref[lv_n++] = kids[i];
+                else sm.lref[k++] = kids[i];
+            }
+        }
+        sm.k = k;
+        sm.ni = ni;
+    }
+    __syncwarp();
+    const int k = sm.k, ni = sm.ni;
+    if (k < 3) return;   // two leaves: one tree only
+    const int full = (1 << k) - 1;
+    // 2. leaf boxes; the current cost (summed area of the internal nodes)
+    float old = 0.0f;
+    if (lane < k) {
+        float b[6];
+        load_box(box, slot_of(sm.lref[lane], n), b);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) sm.lbox[lane][a] = b[a];
+    }
+    if (lane < ni) {
+        float b[6];
+        load_box(box, sm.inner[lane], b);
+        old = half_area(b[3] - b[0], b[4] - b[1], b[5] - b[2]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) old += __shfl_xor_sync(kFull, old, o);
+    __syncwarp();
+    // 3. the box area of every leaf subset; a single leaf costs nothing
+    for (int S = lane + 1; S <= full; S += 32) {
+        float lo0 = 3.0e38f, lo1 = 3.0e38f, lo2 = 3.0e38f, hi0 = -3.0e38f, hi1 = -3.0e38f, hi2 = -3.0e38f;
+#pragma unroll
+        for (int i = 0; i < kTreeletLeaves; ++i) {
+            if ((S >> i) & 1) {
+                lo0 = fminf(lo0, sm.lbox[i][0]);
+                lo1 = fminf(lo1, sm.lbox[i][1]);
+                lo2 = fminf(lo2, sm.lbox[i][2]);
+                hi0 = fmaxf(hi0, sm.lbox[i][3]);
+                hi1 = fmaxf(hi1, sm.lbox[i][4]);
+                hi2 = fmaxf(hi2, sm.lbox[i][5]);
+            }
+        }
+        sm.area[S] = half_area(hi0 - lo0, hi1 - lo1, hi2 - lo2);
+        sm.cost[S] = 0.0f;
+        sm.best[S] = 0;
+    }
+    __syncwarp();
+    // 4. best split of every subset, smallest subsets first.  A split is the
+    //    part Q holding the subset's lowest leaf (Q != S); subsets of up to
+    //    six leaves take one lane each, the seven-leaf ones four lanes each
+    //    and the whole set of eight all 32.
+    for (int sz = 2; sz <= k; ++sz) {
+        const int o0 = c_subsets.off[sz], ns = c_subsets.off[sz + 1] - o0;
+        const int G = sz <= 6 ? 1 : (sz == 7 ? 4 : 32);
+        for (int base = 0; base < ns; base += 32 / G) {   // uniform trip count
+            const int i = base + lane / G, g = lane % G;
+            float bc = 3.0e38f;
+            int bq = 0;
+            int S = 0;
+            if (i < ns) S = c_subsets.by_size[o0 + i];
+            if (S != 0 && S <= full) {
+                const int low = S & -S, rest = S ^ low;
+                // the g-th, (g + G)-th, ... proper submask of rest, taken in decreasing order
+                int sub = (rest - 1) & rest, idx = 0;
+                while (true) {
+                    if (idx % G == g) {
+                        const int Q = low | sub;
+                        const float c = sm.cost[Q] + sm.cost[S ^ Q];
+                        if (c < bc || (c == bc && Q < bq)) {
+                            bc = c;
+                            bq = Q;
+                        }
+                    }
+                    if (sub == 0) break;
+                    sub = (sub - 1) & rest;
+                    ++idx;
+                }
+            }
+            if (G > 1) {
+                for (int o = G >> 1; o; o >>= 1) {
+                    const float oc = __shfl_xor_sync(kFull, bc, o);
+                    const int oq = __shfl_xor_sync(kFull, bq, o);
+                    if (oc < bc || (oc == bc && oq < bq)) {
+                        bc = oc;
+                        bq = oq;
+                    }
+                }
+            }
+            if (S != 0 && S <= full && g == 0) {
+                sm.cost[S] = sm.area[S] + bc;
+                sm.best[S] = (uint8_t)bq;
+            }
+        }
+        __syncwarp();
+    }
+    // 5. rewire only for a clear gain
+    if (!(sm.cost[full] < old * 0.99999f)) return;
+    if (lane == 0) {   // the new internal nodes, top down: node id, its leaf subset, its children
+        int st_set[kTreeletLeaves - 1], st_node[kTreeletLeaves - 1];
+        int sp = 0, next_id = 1, m = 0;
+        st_set[sp] = full;
+        st_node[sp++] = sm.inner[0];
+        while (sp > 0) {
+            --sp;
+            const int S = st_set[sp], id = st_node[sp];
+            const int Q = sm.best[S];
+            int refs[2];
+            const int parts[2] = {Q, S ^ Q};
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int T = parts[c];
+                if ((T & (T - 1)) == 0) {
+                    refs[c] = sm.lref[__ffs(T) - 1];
+                } else {
+                    const int nid = sm.inner[next_id++];
+                    st_set[sp] = T;
+                    st_node[sp++] = nid;
+                    refs[c] = nid;
+                }
+            }
+            sm.emit_node[m] = id;
+            sm.emit_set[m] = S;
+            sm.emit_l[m] = refs[0];
+            sm.emit_r[m] = refs[1];
+            ++m;
+        }
+    }
+    __syncwarp();
+    if (lane < ni) {   // lane i writes new internal node i (the root's box stays as it is)
+        const int id = sm.emit_node[lane], S = sm.emit_set[lane];
+        const int lr = sm.emit_l[lane], rr = sm.emit_r[lane];
+        left[id] = lr;
+        right[id] = rr;
+        parent[slot_of(lr, n)] = id;
+        parent[slot_of(rr, n)] = id;
+        if (lane > 0) {
+            float lo0 = 3.0e38f, lo1 = 3.0e38f, lo2 = 3.0e38f, hi0 = -3.0e38f, hi1 = -3.0e38f, hi2 = -3.0e38f;
+#pragma unroll
+            for (int i = 0; i < kTreeletLeaves; ++i) {
+                if ((S >> i) & 1) {
+                    lo0 = fminf(lo0, sm.lbox[i][0]);
+                    lo1 = fminf(lo1, sm.lbox[i][1]);
+                    lo2 = fminf(lo2, sm.lbox[i][2]);
+                    hi0 = fmaxf(hi0, sm.lbox[i][3]);
+                    hi1 = fmaxf(hi1, sm.lbox[i][4]);
+                    hi2 = fmaxf(hi2, sm.lbox[i][5]);
+                }
+            }
+            float* b = box + 6 * (int64_t)id;
+            b[0] = lo0;
+            b[1] = lo1;
+            b[2] = lo2;
+            b[3] = hi0;
+            b[4] = hi1;
+            b[5] = hi2;
+        }
+    }
+}
+
+// Depth of every node slot (root 0) by its parent chain; with `height` the
+// largest leaf depth is also raised into it (the tree height).
+__global__ void k_depth(int64_t n, const int32_t* __restrict__ parent, int32_t* __restrict__ depth,
+                        DevCounters* c, int height) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 2 * n - 1) return;
+    int d = 0;
+    for (int32_t p = parent[i]; p >= 0; p = parent[p]) {
+        if (++d == kClimbMax) {   // a parent chain longer than any tree
+            atomicCAS(&c->error, 0, RSI_ERR_STACK);
+            break;
+        }
+    }
+    depth[i] = d;
+    if (height && i >= n - 1) atomicMax(&c->height, d);
+}
+
+// The treelets rooted at depth = off (mod kTreeletLevels): one warp each.
+__global__ void __launch_bounds__(32 * kTreeletWarps) k_treelet(int64_t n, int off, int32_t* __restrict__ left,
+                                                                int32_t* __restrict__ right,
+                                                                int32_t* __restrict__ parent,
+                                                                float* __restrict__ box,
+                                                                const int32_t* __restrict__ depth) {
+    __shared__ TreeletSmem sm[kTreeletWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t r = blockIdx.x * (int64_t)kTreeletWarps + w;   // warp-uniform
+    if (r >= n - 1 || depth[r] % kTreeletLevels != off) return;
+    restructure((int)r, n, left, right, parent, box, sm[w], lane);
+}
+
+// The packed child-pair nodes of the new tree (boxes are final).
+__global__ void k_pack_nodes(int64_t n, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                             const float* __restrict__ box, Node* __restrict__ nodes) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int32_t lc = left[i], rc = right[i];
+    const float* bl = box + 6 * slot_of(lc, n);
+    const float* br = box + 6 * slot_of(rc, n);
+    const int pl = ((uint32_t)lc & kLeafTag) ? ~(int)((uint32_t)lc & ~kLeafTag) : (int)lc;
+    const int pr = ((uint32_t)rc & kLeafTag) ? ~(int)((uint32_t)rc & ~kLeafTag) : (int)rc;
+    Node nd;
+    nd.lmin = make_float4(bl[0], bl[1], bl[2], __int_as_float(pl));
+    nd.lmax = make_float4(bl[3], bl[4], bl[5], __int_as_float(pr));
+    nd.rmin = make_float4(br[0], br[1], br[2], 0.0f);
+    nd.rmax = make_float4(br[3], br[4], br[5], 0.0f);
+    nodes[i] = nd;
+}
+
+}  // namespace
+
+// Restructuring passes over a finished single build, in stream order without
+// host synchronization: each pass restructures the treelets rooted at depths
+// 0, 1 and 2 (mod 3) in three launches; then the packed nodes are rewritten
+// and the tree height recomputed.  `depth` is build scratch of 2n - 1 ints
+// (the build's height array).
+int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, cudaStream_t s) {
+    const int64_t n = h->n_tri;
+    if (n < 2 || passes <= 0) return RSI_OK;
+    const int nodes_grid = (int)((2 * n - 1 + 255) / 256);
+    const int tl_grid = (int)((n - 1 + kTreeletWarps - 1) / kTreeletWarps);
+    int launches = 0;
+    for (int p = 0; p < passes; ++p) {
+        for (int off = 0; off < kTreeletLevels; ++off) {
+            k_depth<<<nodes_grid, 256, 0, s>>>(n, h->parent, depth, h->ctr, 0);
+            k_treelet<<<tl_grid, 32 * kTreeletWarps, 0, s>>>(n, off, h->left, h->right, h->parent, h->box, depth);
+            launches += 2;
+        }
+    }
+    RSI_CUDA_TRY(cudaMemsetAsync(&h->ctr->height, 0, sizeof(int), s));
+    k_depth<<<nodes_grid, 256, 0, s>>>(n, h->parent, depth, h->ctr, 1);
+    k_pack_nodes<<<(int)((n - 1 + 255) / 256), 256, 0, s>>>(n, h->left, h->right, h->box, h->nodes);
+    note_launches(launches + 2);
+    RSI_CUDA_TRY(cudaGetLastError());
+    return RSI_OK;
+}
+
+}  // namespace rsi

@@ -56,6 +56,11 @@ def test_host_side_rejections(lib):
     assert rc == -1 and "30 or 63" in lib.last_error()
     rc = L.lbvh_build_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 4, 30, 2, None, ctypes.byref(h))
     assert rc == -1 and "tree_builder" in lib.last_error()
+    for bad in (4 << 8, (1 << 8) | 2, -1):   # RSI_TREE_TREELETS(4); an unknown builder with passes; negative
+        rc = L.lbvh_build_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 4, 30, bad, None, ctypes.byref(h))
+        assert rc == -1 and "tree_builder" in lib.last_error(), bad
+    rc = L.lbvh_build_host_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 4, 30, 4 << 8, None, ctypes.byref(h))
+    assert rc == -1 and "tree_builder" in lib.last_error()
     rc = L.lbvh_build_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 8, 30, 1, None, ctypes.byref(h))
     assert rc == -2
     P, I64 = ctypes.c_void_p, ctypes.c_int64
@@ -90,6 +95,8 @@ def test_binding_rejects_before_the_library(lib):
     T = torch.zeros(2, 3, dtype=torch.int32)
     with pytest.raises(ValueError):
         lib.LBVH(V, T, builder="octree")
+    with pytest.raises(ValueError):
+        lib.LBVH(V, T, treelet_passes=4)
     with pytest.raises(ValueError):
         lib.build_many([])
     with pytest.raises(TypeError):
