@@ -929,7 +929,7 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     int rc = morton_bits == 30 ? build_impl<uint32_t>(h, V, T, builder, s, scratch, h->box, hgt, flag)
                                : build_impl<uint64_t>(h, V, T, builder, s, scratch, h->box, hgt, flag);
     if (rc) return cleanup(rc);
-    rc = enqueue_treelets(h, passes, hgt, s);
+    rc = enqueue_treelets(h, passes, hgt, reinterpret_cast<int32_t*>(scratch), s);   // the sort scratch is free now
     if (rc) return cleanup(rc);
     if (n > 1) {
         k_collapse4<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(h->nodes, h->parent, n, h->nodes4);

@@ -197,7 +197,7 @@ cudaError_t host_malloc_pinned(T** p, size_t bytes) {
 // Count of kernel launches made by the library (rsi_kernel_launches).
 void note_launches(int n);
 // Restructuring passes after a single build (treelet.cu).
-int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, cudaStream_t s);
+int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, int32_t* list, cudaStream_t s);
 
 // A batched rebuild prepared for capture: the hierarchies' own arrays are
 // rebuilt in place from the meshes' current buffers (the sizes fixed at

@@ -34,6 +34,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "rsi_internal.cuh"
 
 namespace rsi {
@@ -159,25 +161,33 @@ __device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_
     }
     __syncwarp();
     // 4. best split of every subset, smallest subsets first.  A split is the
-    //    part Q holding the subset's lowest leaf (Q != S); subsets of up to
-    //    six leaves take one lane each, the seven-leaf ones four lanes each
-    //    and the whole set of eight all 32.
+    //    part Q holding the subset's lowest leaf (Q != S): Q = lowest | sub,
+    //    sub a proper submask of the rest.  Subsets of up to six leaves take
+    //    one lane each; a seven-leaf subset takes four lanes and the whole set
+    //    of eight all 32: lane g of a group of G = 2^b lanes fixes the top b
+    //    bits of the rest at the pattern g and walks the submasks of the
+    //    remaining low bits.
     for (int sz = 2; sz <= k; ++sz) {
         const int o0 = c_subsets.off[sz], ns = c_subsets.off[sz + 1] - o0;
-        const int G = sz <= 6 ? 1 : (sz == 7 ? 4 : 32);
+        const int lg = sz <= 6 ? 0 : (sz == 7 ? 2 : 5), G = 1 << lg;
         for (int base = 0; base < ns; base += 32 / G) {   // uniform trip count
-            const int i = base + lane / G, g = lane % G;
+            const int i = base + (lane >> lg), g = lane & (G - 1);
             float bc = 3.0e38f;
             int bq = 0;
-            int S = 0;
-            if (i < ns) S = c_subsets.by_size[o0 + i];
+            const int S = i < ns ? (int)c_subsets.by_size[o0 + i] : 0;
             if (S != 0 && S <= full) {
                 const int low = S & -S, rest = S ^ low;
-                // the g-th, (g + G)-th, ... proper submask of rest, taken in decreasing order
-                int sub = (rest - 1) & rest, idx = 0;
-                while (true) {
-                    if (idx % G == g) {
-                        const int Q = low | sub;
+                int lowbits = rest, hi = 0;   // rest without its top lg set bits; g spread over those
+                for (int t = 0; t < lg; ++t) {
+                    const int b = 1 << (31 - __clz(lowbits));
+                    lowbits ^= b;
+                    if ((g >> (lg - 1 - t)) & 1) hi |= b;
+                }
+                int sub = lowbits;
+                while (true) {   // submasks of lowbits, decreasing, with the fixed top pattern
+                    const int m = hi | sub;
+                    if (m != rest) {
+                        const int Q = low | m;
                         const float c = sm.cost[Q] + sm.cost[S ^ Q];
                         if (c < bc || (c == bc && Q < bq)) {
                             bc = c;
@@ -185,8 +195,7 @@ __device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_
                         }
                     }
                     if (sub == 0) break;
-                    sub = (sub - 1) & rest;
-                    ++idx;
+                    sub = (sub - 1) & lowbits;
                 }
             }
             if (G > 1) {
@@ -271,33 +280,46 @@ __device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_
 }
 
 // Depth of every node slot (root 0) by its parent chain; with `height` the
-// largest leaf depth is also raised into it (the tree height).
+// largest leaf depth is also raised into it (the tree height).  With off >= 0
+// the internal nodes at depth = off (mod kTreeletLevels) are appended to
+// roots[] (count in *n_roots).
 __global__ void k_depth(int64_t n, const int32_t* __restrict__ parent, int32_t* __restrict__ depth,
-                        DevCounters* c, int height) {
+                        DevCounters* c, int height, int off, int32_t* __restrict__ roots, int* __restrict__ n_roots) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= 2 * n - 1) return;
     int d = 0;
-    for (int32_t p = parent[i]; p >= 0; p = parent[p]) {
-        if (++d == kClimbMax) {   // a parent chain longer than any tree
-            atomicCAS(&c->error, 0, RSI_ERR_STACK);
-            break;
+    if (i < 2 * n - 1) {
+        for (int32_t p = parent[i]; p >= 0; p = parent[p]) {
+            if (++d == kClimbMax) {   // a parent chain longer than any tree
+                atomicCAS(&c->error, 0, RSI_ERR_STACK);
+                break;
+            }
         }
+        depth[i] = d;
+        if (height && i >= n - 1) atomicMax(&c->height, d);
     }
-    depth[i] = d;
-    if (height && i >= n - 1) atomicMax(&c->height, d);
+    if (off < 0) return;
+    const bool root = i < n - 1 && d % kTreeletLevels == off;
+    const unsigned m = __ballot_sync(kFull, root);   // one atomic per warp
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(n_roots, __popc(m));
+    base = __shfl_sync(kFull, base, __ffs(m) - 1);
+    if (root) roots[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
-// The treelets rooted at depth = off (mod kTreeletLevels): one warp each.
-__global__ void __launch_bounds__(32 * kTreeletWarps) k_treelet(int64_t n, int off, int32_t* __restrict__ left,
+// The treelets whose roots k_depth listed: each warp takes roots in turn.
+__global__ void __launch_bounds__(32 * kTreeletWarps) k_treelet(int64_t n, int32_t* __restrict__ left,
                                                                 int32_t* __restrict__ right,
                                                                 int32_t* __restrict__ parent,
                                                                 float* __restrict__ box,
-                                                                const int32_t* __restrict__ depth) {
+                                                                const int32_t* __restrict__ roots,
+                                                                const int* __restrict__ n_roots) {
     __shared__ TreeletSmem sm[kTreeletWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t r = blockIdx.x * (int64_t)kTreeletWarps + w;   // warp-uniform
-    if (r >= n - 1 || depth[r] % kTreeletLevels != off) return;
-    restructure((int)r, n, left, right, parent, box, sm[w], lane);
+    const int nr = *n_roots;
+    for (int t = blockIdx.x * kTreeletWarps + w; t < nr; t += gridDim.x * kTreeletWarps)
+        restructure(roots[t], n, left, right, parent, box, sm[w], lane);
 }
 
 // The packed child-pair nodes of the new tree (boxes are final).
@@ -322,24 +344,30 @@ __global__ void k_pack_nodes(int64_t n, const int32_t* __restrict__ left, const 
 
 // Restructuring passes over a finished single build, in stream order without
 // host synchronization: each pass restructures the treelets rooted at depths
-// 0, 1 and 2 (mod 3) in three launches; then the packed nodes are rewritten
-// and the tree height recomputed.  `depth` is build scratch of 2n - 1 ints
-// (the build's height array).
-int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, cudaStream_t s) {
+// 0, 1 and 2 (mod 3) in turn (a depth kernel lists the roots, a persistent
+// kernel takes them); then the packed nodes are rewritten and the tree
+// height recomputed.  `depth` is build scratch of 2n - 1 ints (the build's
+// height array), `list` build scratch of at least n + 16 ints (the sort's).
+int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, int32_t* list, cudaStream_t s) {
     const int64_t n = h->n_tri;
     if (n < 2 || passes <= 0) return RSI_OK;
+    passes = passes > 3 ? 3 : passes;
+    int* counts = list + n;   // one root count per (pass, offset)
+    RSI_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * 3 * kTreeletLevels, s));
     const int nodes_grid = (int)((2 * n - 1 + 255) / 256);
-    const int tl_grid = (int)((n - 1 + kTreeletWarps - 1) / kTreeletWarps);
+    const int64_t need = (n + 3 * kTreeletWarps - 1) / (3 * kTreeletWarps);   // about a third of the nodes are roots
+    const int tl_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * 16));
     int launches = 0;
     for (int p = 0; p < passes; ++p) {
         for (int off = 0; off < kTreeletLevels; ++off) {
-            k_depth<<<nodes_grid, 256, 0, s>>>(n, h->parent, depth, h->ctr, 0);
-            k_treelet<<<tl_grid, 32 * kTreeletWarps, 0, s>>>(n, off, h->left, h->right, h->parent, h->box, depth);
+            int* cnt = counts + p * kTreeletLevels + off;
+            k_depth<<<nodes_grid, 256, 0, s>>>(n, h->parent, depth, h->ctr, 0, off, list, cnt);
+            k_treelet<<<tl_grid, 32 * kTreeletWarps, 0, s>>>(n, h->left, h->right, h->parent, h->box, list, cnt);
             launches += 2;
         }
     }
     RSI_CUDA_TRY(cudaMemsetAsync(&h->ctr->height, 0, sizeof(int), s));
-    k_depth<<<nodes_grid, 256, 0, s>>>(n, h->parent, depth, h->ctr, 1);
+    k_depth<<<nodes_grid, 256, 0, s>>>(n, h->parent, depth, h->ctr, 1, -1, nullptr, nullptr);
     k_pack_nodes<<<(int)((n - 1 + 255) / 256), 256, 0, s>>>(n, h->left, h->right, h->box, h->nodes);
     note_launches(launches + 2);
     RSI_CUDA_TRY(cudaGetLastError());
