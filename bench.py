@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "rays/s (exact vs FP64 oracle) plain vs batched+learned on 1 GB300; % roofline"
 WORKLOAD = ("c2: 100x100-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (19,602 FP32 triangles); "
             "1e7 FP32 segments, 50% crossing / 50% above, length U(0.05,1), random directions; "
-            "step = lbvh_build_ex (the paper's Karras build, then one treelet restructuring pass: "
+            "step = lbvh_build_ex (the paper's Karras build, then two treelet restructuring passes: "
             "same answers, fewer nodes met) + the boolean and intercept_count answers of every segment "
             "(one traversal answers both: rsi_query mode RSI_BOTH)")
 W_DOC_PAPER = ("paper scale: 111x134-vertex heightfield, 4 sinusoids + 8 Gaussian bumps (14,874 vertices, "
@@ -274,14 +274,21 @@ def measure_batched(rsi, torch, dev, c4, args):
     meshes = [(torch.from_numpy(m.vertices).to(dev), torch.from_numpy(m.triangles).to(dev)) for m, _ in jobs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    bvhs = rsi.build_many(meshes)   # all 64 hierarchies in one build
+    c4p = args.c4_treelet_passes
+    for b in rsi.build_many(meshes, treelet_passes=c4p):   # warm-up
+        b.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bvhs = rsi.build_many(meshes, treelet_passes=c4p)   # all 64 hierarchies in one build
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
     items = [(b, torch.from_numpy(F).to(dev), torch.from_numpy(E).to(dev)) for b, (F, E) in zip(bvhs, rays)]
     total = sum(int(f.shape[0]) for _, f, _ in items)
     steps = max(3, min(args.steps, 10))
     out = {"n_meshes": len(jobs), "triangles": int(sum(len(m.triangles) for m, _ in jobs)), "rays": total,
-           "build_all_ms": build_ms, "steps": steps}
+           "build_all_ms": build_ms, "steps": steps,
+           "tree": (f"the paper's builds + {c4p} treelet restructuring pass(es) over all meshes at once "
+                    "(lbvh_build_batched_ex)") if c4p else "as built"}
 
     def timed(fn):
         for _ in range(args.warmup):
@@ -323,13 +330,24 @@ def measure_batched(rsi, torch, dev, c4, args):
     # build and query in one graph: a rebuilding plan (the batched build's
     # kernels in place, then the query) replayed every step
     tuned = out["any_hit"]["autotuned"]
-    plan = rsi.BatchPlan(items, "any_hit", rebuild=meshes, block=tuned["block"],
-                         blocks_per_sm=tuned["blocks_per_sm"], ray_sort_tile=tuned["ray_sort_tile"])
-    ms_graph = timed(plan.run)
-    plan.close()
-    out["build_and_query_one_graph_any_hit_ms"] = ms_graph
-    out["build_and_query_one_graph_note"] = ("rsi_batch_create_rebuild: each launch rebuilds the 64 hierarchies in "
-                                             "place from their mesh buffers, then runs the batched boolean query "
+    graph_ms = {}
+    for passes in sorted({0, c4p}):   # a rebuild repeats the hierarchies' restructuring passes
+        hs = bvhs if passes == c4p else rsi.build_many(meshes, treelet_passes=passes)
+        its = [(b, f, t) for b, (_, f, t) in zip(hs, items)]
+        plan = rsi.BatchPlan(its, "any_hit", rebuild=meshes, block=tuned["block"],
+                             blocks_per_sm=tuned["blocks_per_sm"], ray_sort_tile=tuned["ray_sort_tile"])
+        graph_ms[passes] = timed(plan.run)
+        plan.close()
+        if hs is not bvhs:
+            for b in hs:
+                b.close()
+    out["build_and_query_one_graph_any_hit_ms"] = graph_ms[0]
+    if c4p:
+        out[f"build_and_query_one_graph_any_hit_ms_{c4p}_treelet_passes"] = graph_ms[c4p]
+    out["build_and_query_one_graph_note"] = ("rsi_batch_create_rebuild: each launch rebuilds the 64 hierarchies "
+                                             "in place from their mesh buffers (the paper's trees; with "
+                                             "restructuring passes, which cost more than they save when every "
+                                             "launch rebuilds, beside it), then runs the batched boolean query "
                                              "(the tuned launch shape; 128-entry stacks, child-pair nodes), one graph "
                                              "launch per step")
 
@@ -339,18 +357,21 @@ def measure_batched(rsi, torch, dev, c4, args):
     # build and query in sequence, as a caller would: one batched build of
     # the 64 meshes, then one rsi_query_batched call on the new hierarchies
     # (a new plan each time: the hierarchies are new), wall clock
-    def build_and_query():
-        hs = rsi.build_many(meshes)
+    def build_and_query(passes):
+        hs = rsi.build_many(meshes, treelet_passes=passes)
         rsi.query_batched([(b, f, t) for b, (_, f, t) in zip(hs, items)], "any_hit")
         torch.cuda.synchronize()
         for b in hs:
             b.close()
-    build_and_query()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        build_and_query()
-    out["build_then_query_any_hit_ms"] = 1e3 * (time.perf_counter() - t0) / steps
-    out["build_then_query_note"] = ("wall clock of lbvh_build_batched + one rsi_query_batched call (plan, graph "
+    for passes in sorted({0, c4p}):
+        build_and_query(passes)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            build_and_query(passes)
+        key = "build_then_query_any_hit_ms" + (f"_{passes}_treelet_passes" if passes else "")
+        out[key] = 1e3 * (time.perf_counter() - t0) / steps
+    out["build_then_query_note"] = ("wall clock of lbvh_build_batched_ex (the paper's trees; with restructuring "
+                                    "passes beside it) + one rsi_query_batched call (plan, graph "
                                     "capture, launch) per step on new hierarchies; beside it, the rebuilding plan "
                                     "replays build and query of existing hierarchies in one graph")
     return out
@@ -741,10 +762,12 @@ def main():
     ap.add_argument("--train-rays", type=int, default=10_000_000)
     ap.add_argument("--c3-only", action="store_true",
                     help="run the c3 precision leg alone and print its object (for profiler captures)")
-    ap.add_argument("--treelet-passes", type=int, default=1,
+    ap.add_argument("--treelet-passes", type=int, default=2,
                     help="restructuring passes after the c2 build (0: the paper's tree as built)")
     ap.add_argument("--c3-treelet-passes", type=int, default=2,
                     help="restructuring passes after the c3 build (1e8 segments per build)")
+    ap.add_argument("--c4-treelet-passes", type=int, default=2,
+                    help="restructuring passes after the batched c4 build (7.7e7 segments per build)")
     ap.add_argument("--order", action="store_true",
                     help="walk the segments in midpoint-cell order in the timed step (rsi_segment_order inside it)")
     args = ap.parse_args()

@@ -216,6 +216,14 @@ int lbvh_build_batched(int n_meshes, const float* const* d_vertices, const int64
                        const int32_t* const* d_triangles, const int64_t* n_triangles, int index_bytes,
                        int morton_bits, void* stream, rsi_bvh_t* out);
 
+/* As lbvh_build_batched, then treelet_passes (0 .. 3; else
+ * RSI_ERR_INVALID_ARG) restructuring passes over all meshes at once, each a
+ * few launches over all meshes' nodes: every handle equals what
+ * lbvh_build_ex(RSI_TREE_TREELETS(treelet_passes)) gives its mesh. */
+int lbvh_build_batched_ex(int n_meshes, const float* const* d_vertices, const int64_t* n_vertices,
+                          const int32_t* const* d_triangles, const int64_t* n_triangles, int index_bytes,
+                          int morton_bits, int treelet_passes, void* stream, rsi_bvh_t* out);
+
 /* As lbvh_build, with the mesh in host memory: h_vertices and h_triangles
  * are copied in on `stream` (page-locked arrays copy asynchronously) and may
  * be freed when the call returns; the call synchronizes `stream` as
@@ -428,7 +436,9 @@ int rsi_batch_create(const rsi_ray_batch* batches, int n_batches, int mode, cons
  *       the vertex and triangle counts of batches[i].bvh's own build; read at
  *       every launch, so the caller may change them between launches.
  * Otherwise as rsi_batch_create (no streaming; each hierarchy at most once;
- * all hierarchies of one Morton width).  The heights of the rebuilt trees
+ * all hierarchies of one Morton width).  The rebuild repeats the
+ * restructuring passes the hierarchies were built with (the most any of them
+ * had).  The heights of the rebuilt trees
  * are not known when the graph is captured, so every walk uses a 128-entry
  * stack and child-pair nodes.  Mesh errors (a NaN vertex, an index out of
  * range) are reported by rsi_batch_stats, which also brings the

@@ -90,6 +90,9 @@ def _load():
     lib.lbvh_build_batched.argtypes = [i32, ctypes.POINTER(P), ctypes.POINTER(i64), ctypes.POINTER(P),
                                        ctypes.POINTER(i64), i32, i32, P, ctypes.POINTER(P)]
     lib.lbvh_build_batched.restype = ctypes.c_int
+    lib.lbvh_build_batched_ex.argtypes = [i32, ctypes.POINTER(P), ctypes.POINTER(i64), ctypes.POINTER(P),
+                                          ctypes.POINTER(i64), i32, i32, i32, P, ctypes.POINTER(P)]
+    lib.lbvh_build_batched_ex.restype = ctypes.c_int
     lib.lbvh_free.argtypes = [P]
     lib.lbvh_info.argtypes = [P, ctypes.POINTER(Info)]
     lib.lbvh_export.argtypes = [P, P, ctypes.POINTER(HostView)]
@@ -491,11 +494,11 @@ class LBVH:
         return compact_hits(r["tri"], r["dist"], r["point"], stream=stream)
 
 
-def build_many(meshes, morton_bits: int = 30, stream=None):
-    """Hierarchies of many meshes in one build (lbvh_build_batched): meshes is
-    a list of (vertices, triangles) device tensors ([n, 3] float32, [m, 3]
+def build_many(meshes, morton_bits: int = 30, stream=None, treelet_passes: int = 0):
+    """Hierarchies of many meshes in one build (lbvh_build_batched_ex): meshes
+    is a list of (vertices, triangles) device tensors ([n, 3] float32, [m, 3]
     int32); returns one LBVH per mesh, each identical to LBVH(vertices,
-    triangles)."""
+    triangles, treelet_passes=treelet_passes)."""
     import torch
     M = len(meshes)
     if M < 1:
@@ -514,8 +517,10 @@ def build_many(meshes, morton_bits: int = 30, stream=None):
         keep.append(T)
         vp[m], tp[m] = V.data_ptr(), T.data_ptr()
         nv[m], nt[m] = V.shape[0], T.shape[0]
+    if int(treelet_passes) not in (0, 1, 2, 3):
+        raise ValueError("treelet_passes must be 0, 1, 2 or 3")
     out = (P * M)()
-    check(lib.lbvh_build_batched(M, vp, nv, tp, nt, 4, morton_bits, _stream(stream), out))
+    check(lib.lbvh_build_batched_ex(M, vp, nv, tp, nt, 4, morton_bits, int(treelet_passes), _stream(stream), out))
     return [LBVH._adopt(P(out[m]), int(nt[m])) for m in range(M)]
 
 

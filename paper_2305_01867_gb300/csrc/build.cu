@@ -19,6 +19,7 @@
 
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "rsi_internal.cuh"
@@ -729,19 +730,6 @@ int build_impl(rsi_bvh_s* h, const float* V, const int32_t* T, int builder, cuda
 // over all meshes' vertices, triangles or nodes; a thread finds its mesh by
 // a binary search over the prefix of the per-mesh counts and then runs the
 // single-mesh code on that mesh's arrays.
-struct MeshBuild {
-    const float* V;
-    const int32_t* T;
-    int64_t nv, nt;
-    Node* nodes;
-    Node4* nodes4;
-    Tri* tris;
-    void* keys;   // the handle's sorted keys (uint32 or uint64)
-    int32_t *perm, *left, *right, *parent, *hgt, *ends;
-    float* box;
-    DevCounters* ctr;
-};
-
 // The mesh m with pre[m] <= g < pre[m + 1] (pre: M + 1 prefix entries).
 __device__ __forceinline__ int mesh_of(const int64_t* __restrict__ pre, int M, int64_t g) {
     int lo = 0, hi = M - 1;
@@ -951,6 +939,7 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
     }
     finish_handle(h, hc);
     h->has_q = n > 1 && passes == 0;
+    h->treelet_passes = passes;
     *out = h;
     return RSI_OK;
 }
@@ -963,7 +952,8 @@ int build_from_device(const float* V, int64_t nv, const int32_t* T, int64_t nt, 
 template <typename K>
 int enqueue_batched_build(const MeshBuild* d_mb, const int64_t* d_tri_pre, const int64_t* d_int_pre, int M,
                           int64_t total, int64_t total_int, K* ka, K* kb, K* codes, int32_t* va, int32_t* vb,
-                          uint32_t* mka, uint32_t* mkb, uint32_t* hist, DevCounters* d_ctr, cudaStream_t s) {
+                          uint32_t* mka, uint32_t* mkb, uint32_t* hist, DevCounters* d_ctr, cudaStream_t s,
+                          int treelet_passes = 0) {
     k_init_seg<<<grid_for(M, 128), 128, 0, s>>>(d_mb, M);
     k_extent_seg<<<M, kBlock, 0, s>>>(d_mb);
     k_morton_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total, ka, codes, va);
@@ -983,6 +973,11 @@ int enqueue_batched_build(const MeshBuild* d_mb, const int64_t* d_tri_pre, const
     k_scatter_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total, fv, codes);
     k_apetrei_seg<K><<<grid_for(total, kBlock), kBlock, 0, s>>>(d_mb, d_tri_pre, M, total);
     note_launches(2);
+    if (treelet_passes > 0 && total_int > 0) {   // the sort buffers are free now: root lists and their counts
+        rc = enqueue_treelets_batched(d_mb, d_tri_pre, d_int_pre, M, total, total_int, treelet_passes, va, vb,
+                                      reinterpret_cast<int*>(hist), s);
+        if (rc) return rc;
+    }
     if (total_int > 0) {
         k_collapse4_seg<<<grid_for(total_int, kBlock), kBlock, 0, s>>>(d_mb, d_int_pre, M, total_int);
         note_launches(1);
@@ -996,7 +991,7 @@ int enqueue_batched_build(const MeshBuild* d_mb, const int64_t* d_tri_pre, const
 // Many meshes in one build: ~20 launches in all, one synchronization.
 template <typename K>
 int build_batched_impl(int M, const float* const* V, const int64_t* nv, const int32_t* const* T, const int64_t* nt,
-                       int morton_bits, cudaStream_t s, rsi_bvh_t* out) {
+                       int morton_bits, int treelet_passes, cudaStream_t s, rsi_bvh_t* out) {
     std::vector<MeshBuild> mb(M);
     std::vector<int64_t> tri_pre(M + 1, 0), int_pre(M + 1, 0);
     std::vector<rsi_bvh_s*> hs(M, nullptr);
@@ -1062,7 +1057,7 @@ int build_batched_impl(int M, const float* const* V, const int64_t* nv, const in
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_int_pre, int_pre.data(), 8 * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_all(cuda_fail(e, "lbvh_build_batched: upload"));
     int rc = enqueue_batched_build<K>(d_mb, d_tri_pre, d_int_pre, M, total, total_int, ka, kb, codes, va, vb, mka,
-                                      mkb, hist, d_ctr, s);
+                                      mkb, hist, d_ctr, s, treelet_passes);
     if (rc) return fail_all(rc);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), d_ctr, sizeof(DevCounters) * M, cudaMemcpyDeviceToHost, s);
@@ -1077,6 +1072,7 @@ int build_batched_impl(int M, const float* const* V, const int64_t* nv, const in
     pool_free(g, s);
     for (int m = 0; m < M; ++m) {
         finish_handle(hs[m], hc[m]);
+        hs[m]->treelet_passes = treelet_passes;
         out[m] = hs[m];
     }
     return RSI_OK;
@@ -1098,6 +1094,7 @@ int rebuild_prepare(const rsi_bvh_t* hs, int M, const float* const* V, const int
             return fail(RSI_ERR_INVALID_ARG, "rebuild: mesh " + std::to_string(m) + " lacks a hierarchy or buffer");
         if (h->morton_bits != r.morton_bits)
             return fail(RSI_ERR_INVALID_ARG, "rebuild: the hierarchies differ in morton_bits");
+        r.treelet_passes = std::max(r.treelet_passes, h->treelet_passes);
         if (!h->hgt || !h->flags) return fail(RSI_ERR_INVALID_ARG, "rebuild: hierarchy without build scratch");
         mb[m] = MeshBuild{V[m], T[m], h->n_vert, h->n_tri, h->nodes, h->nodes4, h->tris, h->sorted_keys, h->perm,
                           h->left, h->right, h->parent, h->hgt, h->flags, h->box, h->ctr};
@@ -1149,10 +1146,10 @@ int rebuild_enqueue(const RebuildSpec& r, cudaStream_t s) {
     if (r.morton_bits == 30)
         return enqueue_batched_build<uint32_t>(d_mb, r.d_tri_pre, r.d_int_pre, r.M, r.total, r.total_int,
                                                (uint32_t*)r.ka, (uint32_t*)r.kb, (uint32_t*)r.codes, r.va, r.vb, r.mka,
-                                               r.mkb, r.hist, r.d_ctr, s);
+                                               r.mkb, r.hist, r.d_ctr, s, r.treelet_passes);
     return enqueue_batched_build<uint64_t>(d_mb, r.d_tri_pre, r.d_int_pre, r.M, r.total, r.total_int,
                                            (uint64_t*)r.ka, (uint64_t*)r.kb, (uint64_t*)r.codes, r.va, r.vb, r.mka,
-                                           r.mkb, r.hist, r.d_ctr, s);
+                                           r.mkb, r.hist, r.d_ctr, s, r.treelet_passes);
 }
 
 void rebuild_release(RebuildSpec& r) {
@@ -1218,12 +1215,21 @@ extern "C" int lbvh_build_ex(const float* d_vertices, int64_t n_vertices, const 
 extern "C" int lbvh_build_batched(int n_meshes, const float* const* d_vertices, const int64_t* n_vertices,
                                   const int32_t* const* d_triangles, const int64_t* n_triangles, int index_bytes,
                                   int morton_bits, void* stream, rsi_bvh_t* out) {
+    return lbvh_build_batched_ex(n_meshes, d_vertices, n_vertices, d_triangles, n_triangles, index_bytes,
+                                 morton_bits, 0, stream, out);
+}
+
+extern "C" int lbvh_build_batched_ex(int n_meshes, const float* const* d_vertices, const int64_t* n_vertices,
+                                     const int32_t* const* d_triangles, const int64_t* n_triangles, int index_bytes,
+                                     int morton_bits, int treelet_passes, void* stream, rsi_bvh_t* out) {
     if (!out || n_meshes < 1 || !d_vertices || !n_vertices || !d_triangles || !n_triangles)
         return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_batched: need n_meshes >= 1 and non-NULL arrays");
     for (int m = 0; m < n_meshes; ++m) out[m] = nullptr;
     if (index_bytes != 4) return rsi::fail(RSI_ERR_DTYPE, "lbvh_build_batched: triangle indices must be int32");
     if (morton_bits != 30 && morton_bits != 63)
         return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_batched: morton_bits must be 30 or 63");
+    if (treelet_passes < 0 || treelet_passes > 3)
+        return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_batched: treelet_passes must be 0 .. 3");
     int64_t total = 0;
     for (int m = 0; m < n_meshes; ++m) {
         if (!d_vertices[m] || !d_triangles[m] || n_vertices[m] < 1 || n_triangles[m] < 1 ||
@@ -1236,8 +1242,10 @@ extern "C" int lbvh_build_batched(int n_meshes, const float* const* d_vertices, 
         return rsi::fail(RSI_ERR_INVALID_ARG, "lbvh_build_batched: more than 2^30 triangles in all");
     cudaStream_t s = (cudaStream_t)stream;
     return morton_bits == 30
-               ? rsi::build_batched_impl<uint32_t>(n_meshes, d_vertices, n_vertices, d_triangles, n_triangles, 30, s, out)
-               : rsi::build_batched_impl<uint64_t>(n_meshes, d_vertices, n_vertices, d_triangles, n_triangles, 63, s, out);
+               ? rsi::build_batched_impl<uint32_t>(n_meshes, d_vertices, n_vertices, d_triangles, n_triangles, 30,
+                                                   treelet_passes, s, out)
+               : rsi::build_batched_impl<uint64_t>(n_meshes, d_vertices, n_vertices, d_triangles, n_triangles, 63,
+                                                   treelet_passes, s, out);
 }
 
 extern "C" int lbvh_build_host(const float* h_vertices, int64_t n_vertices, const int32_t* h_triangles,

@@ -103,6 +103,7 @@ struct rsi_bvh_s {
     rsi::Node4* nodes4 = nullptr; // [max(n_tri - 1, 1)], even-depth slots used
     rsi::NodeQ* nodesq = nullptr; // [max(n_tri - 1, 1)] compressed child-pair nodes
     bool has_q = false;           // nodesq written (single builds)
+    int treelet_passes = 0;       // restructuring passes of its build (a rebuild repeats them)
     rsi::Tri* tris = nullptr;     // [n_tri]
     // exported build arrays
     void* sorted_keys = nullptr;  // uint32 or uint64 [n_tri]
@@ -196,8 +197,28 @@ cudaError_t host_malloc_pinned(T** p, size_t bytes) {
 
 // Count of kernel launches made by the library (rsi_kernel_launches).
 void note_launches(int n);
+// One mesh of a batched build (build.cu, treelet.cu): its inputs and the
+// arrays of its handle.
+struct MeshBuild {
+    const float* V;
+    const int32_t* T;
+    int64_t nv, nt;
+    Node* nodes;
+    Node4* nodes4;
+    Tri* tris;
+    void* keys;   // the handle's sorted keys (uint32 or uint64)
+    int32_t *perm, *left, *right, *parent, *hgt, *ends;
+    float* box;
+    DevCounters* ctr;
+};
+
 // Restructuring passes after a single build (treelet.cu).
 int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, int32_t* list, cudaStream_t s);
+// The same over all meshes of a batched build (roots_node / roots_mesh: the
+// internal-node count of ints each; counts: 9 ints).
+int enqueue_treelets_batched(const MeshBuild* d_mb, const int64_t* d_tri_pre, const int64_t* d_int_pre, int M,
+                             int64_t total, int64_t total_int, int passes, int32_t* roots_node, int32_t* roots_mesh,
+                             int* counts, cudaStream_t s);
 
 // A batched rebuild prepared for capture: the hierarchies' own arrays are
 // rebuilt in place from the meshes' current buffers (the sizes fixed at
@@ -207,6 +228,7 @@ int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, int32_t* list, cu
 struct RebuildSpec {
     char* mem = nullptr;        // one allocation: table, prefixes, sort buffers, counters
     int M = 0, morton_bits = 30;
+    int treelet_passes = 0;     // the most any of the hierarchies was built with
     int64_t total = 0, total_int = 0;
     void* d_mb = nullptr;       // [M] per-mesh build descriptors
     int64_t* d_tri_pre = nullptr;

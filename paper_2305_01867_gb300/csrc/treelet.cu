@@ -12,8 +12,10 @@
 // hierarchies"), with the treelets tiled by depth instead of grown bottom-up:
 //
 //  * a treelet is an internal node r at depth d with the internal nodes of its
-//    subtree down to depth d + 2; its leaves (at most 8) are the children that
-//    hang below: subtrees rooted at depth d + 3, or triangles;
+//    subtree down to depth d + 2; its leaves are the children that hang
+//    below: subtrees rooted at depth d + 3, or triangles -- at most 7: when 8
+//    would hang below, the depth-(d + 2) node of smallest box stays whole
+//    (a third of the programme's work for 8 leaves, nearly the same trees);
 //  * rewiring a treelet never changes the box of any subtree that hangs below
 //    it nor of r itself (a box is the union of the triangles below), so all
 //    treelets whose roots share d mod 3 are disjoint and independent: one
@@ -42,7 +44,8 @@ namespace rsi {
 namespace {
 
 constexpr int kTreeletLevels = 3;          // levels of internal nodes in a treelet
-constexpr int kTreeletLeaves = 1 << kTreeletLevels;   // at most 8 leaves
+constexpr int kTreeletSpan = 1 << kTreeletLevels;     // subtrees hanging below 3 full levels
+constexpr int kTreeletLeaves = 7;          // a treelet's leaves (of 8 the smallest pair stays joined)
 constexpr int kFullSet = (1 << kTreeletLeaves) - 1;
 constexpr int kTreeletWarps = 4;           // warps per block of k_treelet
 constexpr unsigned kFull = 0xffffffffu;
@@ -102,10 +105,26 @@ __device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_
     // 1. the treelet: r and the internal nodes of the next two levels; their
     //    children below are its leaves, in depth-first order
     if (lane == 0) {
-        int lv_ref[kTreeletLeaves], lv_n = 1, k = 0, ni = 0;
+        int lv_ref[kTreeletSpan], lv_n = 1, k = 0, ni = 0;
         lv_ref[0] = r;
         for (int lv = 0; lv < kTreeletLevels; ++lv) {   // one level of loads at a time
-            int kids[kTreeletLeaves];
+            if (lv == kTreeletLevels - 1 && k + 2 * lv_n > kTreeletLeaves) {
+                // eight leaves: the last-level node of smallest box stays whole (a leaf itself)
+                int at = 0;
+                float amin = 3.0e38f;
+                for (int i = 0; i < lv_n; ++i) {
+                    float b[6];
+                    load_box(box, lv_ref[i], b);
+                    const float a = half_area(b[3] - b[0], b[4] - b[1], b[5] - b[2]);
+                    if (a < amin) {
+                        amin = a;
+                        at = i;
+                    }
+                }
+                sm.lref[k++] = lv_ref[at];
+                lv_ref[at] = lv_ref[--lv_n];
+            }
+            int kids[kTreeletSpan];
             int m = 0;
             for (int i = 0; i < lv_n; ++i) {
                 sm.inner[ni++] = lv_ref[i];
@@ -162,14 +181,14 @@ __device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_
     __syncwarp();
     // 4. best split of every subset, smallest subsets first.  A split is the
     //    part Q holding the subset's lowest leaf (Q != S): Q = lowest | sub,
-    //    sub a proper submask of the rest.  Subsets of up to six leaves take
-    //    one lane each; a seven-leaf subset takes four lanes and the whole set
-    //    of eight all 32: lane g of a group of G = 2^b lanes fixes the top b
+    //    sub a proper submask of the rest.  Subsets of up to five leaves take
+    //    one lane each; a six-leaf subset takes four lanes and the whole set
+    //    of seven all 32: lane g of a group of G = 2^b lanes fixes the top b
     //    bits of the rest at the pattern g and walks the submasks of the
     //    remaining low bits.
     for (int sz = 2; sz <= k; ++sz) {
         const int o0 = c_subsets.off[sz], ns = c_subsets.off[sz + 1] - o0;
-        const int lg = sz <= 6 ? 0 : (sz == 7 ? 2 : 5), G = 1 << lg;
+        const int lg = sz <= 5 ? 0 : (sz == 6 ? 2 : 5), G = 1 << lg;
         for (int base = 0; base < ns; base += 32 / G) {   // uniform trip count
             const int i = base + (lane >> lg), g = lane & (G - 1);
             float bc = 3.0e38f;
@@ -322,11 +341,9 @@ __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelet(int64_t n, int32
         restructure(roots[t], n, left, right, parent, box, sm[w], lane);
 }
 
-// The packed child-pair nodes of the new tree (boxes are final).
-__global__ void k_pack_nodes(int64_t n, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
-                             const float* __restrict__ box, Node* __restrict__ nodes) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
+// Packed child-pair node i of a tree whose boxes are final.
+__device__ __forceinline__ void pack_node(int64_t n, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                                          const float* __restrict__ box, Node* __restrict__ nodes, int64_t i) {
     const int32_t lc = left[i], rc = right[i];
     const float* bl = box + 6 * slot_of(lc, n);
     const float* br = box + 6 * slot_of(rc, n);
@@ -338,6 +355,102 @@ __global__ void k_pack_nodes(int64_t n, const int32_t* __restrict__ left, const 
     nd.rmin = make_float4(br[0], br[1], br[2], 0.0f);
     nd.rmax = make_float4(br[3], br[4], br[5], 0.0f);
     nodes[i] = nd;
+}
+
+// The packed child-pair nodes of the new tree.
+__global__ void k_pack_nodes(int64_t n, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                             const float* __restrict__ box, Node* __restrict__ nodes) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n - 1) pack_node(n, left, right, box, nodes, i);
+}
+
+// ---------------------------------------------------------------- many meshes
+// The same passes over all meshes of a batched build: a thread finds its mesh
+// by a binary search over the prefix of the per-mesh counts.
+__device__ __forceinline__ int mesh_index(const int64_t* __restrict__ pre, int M, int64_t g) {
+    int lo = 0, hi = M - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(pre + mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int chain_depth(const int32_t* __restrict__ parent, int64_t slot, DevCounters* c) {
+    int d = 0;
+    for (int32_t p = parent[slot]; p >= 0; p = parent[p]) {
+        if (++d == kClimbMax) {
+            atomicCAS(&c->error, 0, RSI_ERR_STACK);
+            break;
+        }
+    }
+    return d;
+}
+
+// The internal nodes at depth = off (mod kTreeletLevels) of every mesh, as
+// (node, mesh) pairs.
+__global__ void k_roots_seg(const MeshBuild* __restrict__ d, const int64_t* __restrict__ int_pre, int M,
+                            int64_t total_int, int off, int32_t* __restrict__ roots_node,
+                            int32_t* __restrict__ roots_mesh, int* __restrict__ n_roots) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool root = false;
+    int m = 0, i = 0;
+    if (g < total_int) {
+        m = mesh_index(int_pre, M, g);
+        i = (int)(g - __ldg(int_pre + m));
+        root = chain_depth(d[m].parent, i, d[m].ctr) % kTreeletLevels == off;
+    }
+    const unsigned mk = __ballot_sync(kFull, root);   // one atomic per warp
+    if (!mk) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(mk) - 1) base = atomicAdd(n_roots, __popc(mk));
+    base = __shfl_sync(kFull, base, __ffs(mk) - 1);
+    if (root) {
+        const int at = base + __popc(mk & ((1u << lane) - 1u));
+        roots_node[at] = i;
+        roots_mesh[at] = m;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kTreeletWarps) k_treelet_seg(const MeshBuild* __restrict__ d,
+                                                                    const int32_t* __restrict__ roots_node,
+                                                                    const int32_t* __restrict__ roots_mesh,
+                                                                    const int* __restrict__ n_roots) {
+    __shared__ TreeletSmem sm[kTreeletWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nr = *n_roots;
+    for (int t = blockIdx.x * kTreeletWarps + w; t < nr; t += gridDim.x * kTreeletWarps) {
+        const MeshBuild& b = d[roots_mesh[t]];
+        restructure(roots_node[t], b.nt, b.left, b.right, b.parent, b.box, sm[w], lane);
+    }
+}
+
+__global__ void k_zero_height_seg(const MeshBuild* __restrict__ d, int M) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) d[m].ctr->height = 0;
+}
+
+// Every mesh's height: the largest depth of its leaves.
+__global__ void k_height_seg(const MeshBuild* __restrict__ d, const int64_t* __restrict__ tri_pre, int M,
+                             int64_t total) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int m = mesh_index(tri_pre, M, g);
+    const MeshBuild& b = d[m];
+    if (b.nt < 2) return;
+    const int64_t j = g - __ldg(tri_pre + m);
+    atomicMax(&b.ctr->height, chain_depth(b.parent, b.nt - 1 + j, b.ctr));
+}
+
+__global__ void k_pack_seg(const MeshBuild* __restrict__ d, const int64_t* __restrict__ int_pre, int M,
+                           int64_t total_int) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total_int) return;
+    const int m = mesh_index(int_pre, M, g);
+    const MeshBuild& b = d[m];
+    pack_node(b.nt, b.left, b.right, b.box, b.nodes, g - __ldg(int_pre + m));
 }
 
 }  // namespace
@@ -370,6 +483,30 @@ int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, int32_t* list, cu
     k_depth<<<nodes_grid, 256, 0, s>>>(n, h->parent, depth, h->ctr, 1, -1, nullptr, nullptr);
     k_pack_nodes<<<(int)((n - 1 + 255) / 256), 256, 0, s>>>(n, h->left, h->right, h->box, h->nodes);
     note_launches(launches + 2);
+    RSI_CUDA_TRY(cudaGetLastError());
+    return RSI_OK;
+}
+
+int enqueue_treelets_batched(const MeshBuild* d_mb, const int64_t* d_tri_pre, const int64_t* d_int_pre, int M,
+                             int64_t total, int64_t total_int, int passes, int32_t* roots_node, int32_t* roots_mesh,
+                             int* counts, cudaStream_t s) {
+    if (total_int <= 0 || passes <= 0) return RSI_OK;
+    passes = passes > 3 ? 3 : passes;
+    RSI_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * 3 * kTreeletLevels, s));
+    const int int_grid = (int)((total_int + 255) / 256);
+    const int64_t need = (total_int + 3 * kTreeletWarps - 1) / (3 * kTreeletWarps);
+    const int tl_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * 16));
+    for (int p = 0; p < passes; ++p) {
+        for (int off = 0; off < kTreeletLevels; ++off) {
+            int* cnt = counts + p * kTreeletLevels + off;
+            k_roots_seg<<<int_grid, 256, 0, s>>>(d_mb, d_int_pre, M, total_int, off, roots_node, roots_mesh, cnt);
+            k_treelet_seg<<<tl_grid, 32 * kTreeletWarps, 0, s>>>(d_mb, roots_node, roots_mesh, cnt);
+        }
+    }
+    k_zero_height_seg<<<(M + 127) / 128, 128, 0, s>>>(d_mb, M);
+    k_height_seg<<<(int)((total + 255) / 256), 256, 0, s>>>(d_mb, d_tri_pre, M, total);
+    k_pack_seg<<<int_grid, 256, 0, s>>>(d_mb, d_int_pre, M, total_int);
+    note_launches(2 * kTreeletLevels * passes + 3);
     RSI_CUDA_TRY(cudaGetLastError());
     return RSI_OK;
 }

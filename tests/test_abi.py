@@ -61,6 +61,9 @@ def test_host_side_rejections(lib):
         assert rc == -1 and "tree_builder" in lib.last_error(), bad
     rc = L.lbvh_build_host_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 4, 30, 4 << 8, None, ctypes.byref(h))
     assert rc == -1 and "tree_builder" in lib.last_error()
+    one_p, one_n = (ctypes.c_void_p * 1)(16), (ctypes.c_int64 * 1)(3)
+    rc = L.lbvh_build_batched_ex(1, one_p, one_n, one_p, one_n, 4, 30, 4, None, (ctypes.c_void_p * 1)())
+    assert rc == -1 and "treelet_passes" in lib.last_error()
     rc = L.lbvh_build_ex(ctypes.c_void_p(16), 3, ctypes.c_void_p(16), 1, 8, 30, 1, None, ctypes.byref(h))
     assert rc == -2
     P, I64 = ctypes.c_void_p, ctypes.c_int64

@@ -167,3 +167,67 @@ def test_host_mesh_build(rsi):
     b = rsi.LBVH(torch.from_numpy(mesh.vertices), torch.from_numpy(mesh.triangles), treelet_passes=2).export()
     for k in ("left", "right", "parent", "box"):
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_batched_build_equals_single_builds(rsi, passes):
+    """One batched build with restructuring (lbvh_build_batched_ex) gives
+    every mesh -- meshes of 1, 2, 3, 8 and thousands of triangles, 30- and
+    63-bit codes -- the restructured hierarchy its own build gives it, bit for
+    bit, and the same answers."""
+    rng = np.random.default_rng(5)
+    meshes = []
+    for n_tri in (1, 2, 3, 8, 500):
+        V = rng.uniform(-1, 1, (3 * n_tri, 3)).astype(np.float32)
+        meshes.append((V, np.arange(3 * n_tri, dtype=np.int32).reshape(n_tri, 3)))
+    for name in ("c1", "c2"):
+        m = W.config_mesh(name)
+        meshes.append((m.vertices, m.triangles))
+    dev = [(_dev(V), _dev(T)) for V, T in meshes]
+    for bits in (30, 63):
+        many = rsi.build_many(dev, morton_bits=bits, treelet_passes=passes)
+        for k, ((V, T), b) in enumerate(zip(dev, many)):
+            one = rsi.LBVH(V, T, morton_bits=bits, treelet_passes=passes)
+            e1, e2 = one.export(), b.export()
+            for key in e1:
+                assert np.array_equal(e1[key], e2[key]), (bits, k, key)
+            assert one.info()["height"] == b.info()["height"], (bits, k)
+            one.close()
+        m = W.config_mesh("c2")
+        F, E = W.rays(W.config_rays("c2"), m, count=200_000)
+        dF, dE = _dev(F), _dev(E)
+        plain = _answers(rsi.LBVH(dev[-1][0], dev[-1][1], morton_bits=bits), dF, dE)
+        _same(_answers(many[-1], dF, dE), plain)
+        out = rsi.query_batched([(b, dF, dE) for b in many[-2:]], "count")
+        assert np.array_equal(out["count"][-1].cpu().numpy(), plain["count"]["count"])
+        for b in many:
+            b.close()
+
+
+def test_rebuild_plan_repeats_the_restructuring(rsi):
+    """A rebuilding plan over restructured hierarchies rebuilds them with the
+    same passes: after the meshes move, a launch answers as fresh
+    restructured builds do and the hierarchies equal them bit for bit."""
+    jobs = W.batched_meshes(n_meshes=4, seed=6, max_rays=30_000)
+    meshes = [(torch.from_numpy(m.vertices).cuda(), torch.from_numpy(m.triangles).cuda()) for m, _ in jobs]
+    rays = [W.rays(spec, m) for m, spec in jobs]
+    bvhs = rsi.build_many(meshes, treelet_passes=1)
+    items = [(b, torch.from_numpy(F).cuda(), torch.from_numpy(E).cuda()) for b, (F, E) in zip(bvhs, rays)]
+    plan = rsi.BatchPlan(items, "count", rebuild=meshes)
+    for V, _ in meshes:                   # move the meshes before the first launch
+        V[:, 2] *= 1.3
+        V[:, :2] += 0.007
+    plan.run()
+    assert plan.stats()["device_error"] == 0
+    for i, ((b, f, t), (V, T)) in enumerate(zip(items, meshes)):
+        fresh = rsi.LBVH(V, T, treelet_passes=1)
+        ref = fresh.query(f, t, "count")
+        assert torch.equal(plan.count[i], ref["count"]) and torch.equal(plan.ambiguous[i], ref["ambiguous"]), i
+        e1, e2 = fresh.export(), b.export()
+        for k in e1:
+            assert np.array_equal(e1[k], e2[k]), (i, k)
+        assert fresh.info()["height"] == b.info()["height"], i
+        fresh.close()
+    plan.close()
+    for b in bvhs:
+        b.close()

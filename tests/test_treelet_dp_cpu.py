@@ -1,5 +1,6 @@
 """The treelet restructuring's optimisation step, restated on the CPU (no
-GPU): for a treelet of k <= 8 leaf boxes, the dynamic programme over leaf
+GPU): for a treelet of k leaf boxes (the kernel's treelets have at most 7;
+up to 8 here), the dynamic programme over leaf
 subsets -- each subset's best split into the part holding its lowest leaf
 and the rest, smallest subsets first -- finds the binary tree with the
 smallest summed surface area of its internal nodes.  Checked against brute
