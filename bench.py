@@ -385,7 +385,8 @@ def measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args):
     stream = torch.cuda.current_stream()
     n = dF.shape[0]
     steps = max(3, min(args.steps, 10))
-    bvh = rsi.LBVH(dV, dT)
+    tp = args.treelet_passes
+    bvh = rsi.LBVH(dV, dT, treelet_passes=tp)
     for _ in range(args.warmup):
         bvh.nearest(dF, dE)
     torch.cuda.synchronize()
@@ -409,7 +410,7 @@ def measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args):
              torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, 3, dtype=torch.float32).pin_memory())
 
     def paper_style():
-        b = rsi.LBVH(pV.to(dev, non_blocking=True), pT.to(dev, non_blocking=True))
+        b = rsi.LBVH(pV.to(dev, non_blocking=True), pT.to(dev, non_blocking=True), treelet_passes=tp)
         res = b.barycentric(pF.to(dev, non_blocking=True), pE.to(dev, non_blocking=True))
         k = res[0].shape[0]
         out = tuple(h[:k].copy_(r, non_blocking=True) for h, r in zip(h_out, res))
@@ -425,7 +426,7 @@ def measure_nearest(rsi, torch, dev, pV, pT, pF, pE, dV, dT, dF, dE, args):
         out = paper_style()
     e2e = 1e3 * (time.perf_counter() - t0) / steps
     assert out[0].shape[0] == hits
-    return {"rays": n, "steps": steps, "ms": ms, "rays_per_s": n / (ms / 1e3),
+    return {"rays": n, "steps": steps, "ms": ms, "rays_per_s": n / (ms / 1e3), "treelet_passes": tp,
             "traverse_ms": statistics.median(trav), "fp64_and_finish_ms": statistics.median(fin),
             "hitting_rays": hits, "band_rays": st["band_rays"], "ambiguous": st["ambiguous"],
             "paper_style_e2e_ms": e2e,
@@ -499,14 +500,15 @@ def measure_paper_scale(rsi, torch, dev, paper, args):
     hc = torch.empty(n, dtype=torch.int32).pin_memory()
     ha = torch.empty(n, dtype=torch.uint8).pin_memory()
     steps = max(3, min(args.steps, 10))
+    tp = args.treelet_passes
 
     def boolean():
-        b = rsi.LBVH(pV, pT)
+        b = rsi.LBVH(pV, pT, treelet_passes=tp)
         b.query_host(pF, pE, "any_hit", hit=hh, ambiguous=ha)
         b.close()
 
     def intercept_count():
-        b = rsi.LBVH(pV, pT)
+        b = rsi.LBVH(pV, pT, treelet_passes=tp)
         b.query_host(pF, pE, "count", count=hc, ambiguous=ha)
         b.close()
 
@@ -514,7 +516,7 @@ def measure_paper_scale(rsi, torch, dev, paper, args):
              torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, 3, dtype=torch.float32).pin_memory())
 
     def barycentric():
-        b = rsi.LBVH(pV.to(dev, non_blocking=True), pT.to(dev, non_blocking=True))
+        b = rsi.LBVH(pV.to(dev, non_blocking=True), pT.to(dev, non_blocking=True), treelet_passes=tp)
         res = b.barycentric(pF.to(dev, non_blocking=True), pE.to(dev, non_blocking=True))
         k = res[0].shape[0]
         out = [h[:k].copy_(r, non_blocking=True) for h, r in zip(h_out, res)]
@@ -523,7 +525,8 @@ def measure_paper_scale(rsi, torch, dev, paper, args):
         return out
 
     out = {"workload": W_DOC_PAPER, "rays": n, "triangles": int(len(mesh.triangles)), "steps": steps,
-           "timing": "wall clock, pinned host mesh and segments in, host results out, build included"}
+           "timing": "wall clock, pinned host mesh and segments in, host results out, build included",
+           "tree": f"the paper's Karras build + {tp} treelet restructuring pass(es)" if tp else "as built"}
     for name, fn in (("boolean", boolean), ("intercept_count", intercept_count), ("barycentric", barycentric)):
         for _ in range(args.warmup):
             fn()
