@@ -357,7 +357,10 @@ int rsi_segment_order(rsi_bvh_t h, const float* d_from, const float* d_to, int64
  * Larger batches, batches whose staging does not fit in device memory, and
  * queries with opt->ray_sort_tile stream chunks of 2^21 through two recycled
  * staging slots (copies and traversal overlapped; the re-test runs per
- * chunk).  Page-locked host buffers give asynchronous copies.  The
+ * chunk).  Page-locked host buffers give asynchronous copies; with
+ * page-locked outputs the FP32 answers are copied out while the FP64
+ * re-test runs and the re-tested segments' answers are then written into
+ * the host arrays by the device.  The
  * staging is shared by all handles of a device: concurrent host-buffer
  * queries on one device run one after the other.
  */

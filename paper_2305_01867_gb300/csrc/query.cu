@@ -2274,6 +2274,45 @@ using namespace rsi;   // the kernels and launchers above
 // whole queue and the results are copied out.  Up to 2^28 segments (8 GB of
 // staging); a batch whose staging does not fit goes through the two slots.
 constexpr int64_t kHostWhole = (int64_t)1 << 28;
+}  // namespace
+
+namespace rsi {
+namespace {
+// After the FP64 pass: the queued segments' answers, from the device arrays
+// into the caller's page-locked host arrays through their mapped addresses
+// (launched once the bulk copy of the FP32 answers has landed there).
+__global__ void k_patch_host(const int32_t* __restrict__ band_ids, const int* __restrict__ n_band,
+                             const uint8_t* __restrict__ dh, const int32_t* __restrict__ dc,
+                             const uint8_t* __restrict__ da, uint8_t* hh, int32_t* hc, uint8_t* ha) {
+    const int nb = *n_band;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+        const int i = band_ids[k];
+        if (hh) hh[i] = dh[i];
+        if (hc) hc[i] = dc[i];
+        if (ha) ha[i] = da[i];
+    }
+}
+}  // namespace
+}  // namespace rsi
+
+namespace {
+using namespace rsi;
+
+// The device address of a page-locked host buffer (NULL stays NULL); false
+// for pageable memory.
+template <typename T>
+bool mapped_host(T* p, T** dev) {
+    *dev = nullptr;
+    if (!p) return true;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return false;
+    *dev = static_cast<T*>(at.devicePointer);
+    return true;
+}
 
 int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, int mode, const rsi_options& o,
                uint8_t* h_hit, int32_t* h_count, uint8_t* h_amb, rsi_stats* stats, cudaStream_t s,
@@ -2380,15 +2419,38 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     rsi::note_launches(2);
     // every copy has landed once the traversal ends; the wait orders the FP64 pass after them
     RSI_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_chunk[n_chunks - 1], 0));
+    // page-locked outputs: the FP32 answers are copied out on st_out while the
+    // FP64 pass runs, then the queued segments' answers are written into them
+    uint8_t *mh = nullptr, *ma = nullptr;
+    int32_t* mc = nullptr;
+    const bool overlap = !o.fp32_only && mapped_host(h_hit, &mh) && mapped_host(h_amb, &ma) &&
+                         mapped_host(mode == RSI_COUNT ? h_count : (int32_t*)nullptr, &mc);
+    if (overlap) {
+        RSI_CUDA_TRY(cudaEventRecord(c->ev_q[0], s));
+        RSI_CUDA_TRY(cudaStreamWaitEvent(c->st_out, c->ev_q[0], 0));
+        if (h_hit) RSI_CUDA_TRY(cudaMemcpyAsync(h_hit, dh, (size_t)n, cudaMemcpyDeviceToHost, c->st_out));
+        if (h_amb) RSI_CUDA_TRY(cudaMemcpyAsync(h_amb, da, (size_t)n, cudaMemcpyDeviceToHost, c->st_out));
+        if (mode == RSI_COUNT)
+            RSI_CUDA_TRY(cudaMemcpyAsync(h_count, dc, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->st_out));
+        RSI_CUDA_TRY(cudaEventRecord(c->ev_out[0], c->st_out));
+    }
     if (!o.fp32_only) {
         const rsi::PairScratch P = rsi::handle_pairs(h);
         if (mode == RSI_ANY_HIT) launch_fp64_pass<RSI_ANY_HIT>(A, h->height, &P, s);
         else launch_fp64_pass<RSI_COUNT>(A, h->height, &P, s);
     }
     RSI_CUDA_TRY(cudaGetLastError());
-    if (h_hit) RSI_CUDA_TRY(cudaMemcpyAsync(h_hit, dh, (size_t)n, cudaMemcpyDeviceToHost, s));
-    if (h_amb) RSI_CUDA_TRY(cudaMemcpyAsync(h_amb, da, (size_t)n, cudaMemcpyDeviceToHost, s));
-    if (mode == RSI_COUNT) RSI_CUDA_TRY(cudaMemcpyAsync(h_count, dc, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    if (overlap) {
+        RSI_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_out[0], 0));
+        rsi::k_patch_host<<<rsi::device_sm_count() * 4, 256, 0, s>>>(h->band_ids, &h->ctr->band_count, dh,
+                                                                mode == RSI_COUNT ? dc : nullptr, da, mh, mc, ma);
+        rsi::note_launches(1);
+        RSI_CUDA_TRY(cudaGetLastError());
+    } else {
+        if (h_hit) RSI_CUDA_TRY(cudaMemcpyAsync(h_hit, dh, (size_t)n, cudaMemcpyDeviceToHost, s));
+        if (h_amb) RSI_CUDA_TRY(cudaMemcpyAsync(h_amb, da, (size_t)n, cudaMemcpyDeviceToHost, s));
+        if (mode == RSI_COUNT) RSI_CUDA_TRY(cudaMemcpyAsync(h_count, dc, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    }
     RSI_CUDA_TRY(cudaMemcpyAsync(c->h_chunk_ctr, h->ctr, sizeof(rsi::DevCounters), cudaMemcpyDeviceToHost, s));
     RSI_CUDA_TRY(cudaStreamSynchronize(s));
     const rsi::DevCounters& kc = c->h_chunk_ctr[0];

@@ -386,6 +386,32 @@ def test_host_path_chunk_boundaries(rsi, n):
             assert h["stats"]["n_rays"] == n and h["stats"]["device_error"] == 0
 
 
+@pytest.mark.parametrize("mode", ["any_hit", "count", "both"])
+def test_host_path_pinned_outputs(rsi, mode):
+    """Page-locked host outputs: the FP32 answers are copied out while the
+    FP64 pass runs and the queued segments' answers are written into the host
+    arrays afterwards -- every entry equals the device path's, on the grazing
+    c3 mix (many queued segments) and on a short c2 batch."""
+    for cfg, n, bits in (("c3", 600_000, 63), ("c2", 70_001, 30)):
+        mesh = W.config_mesh(cfg)
+        F, E = W.rays(W.config_rays(cfg), mesh, count=n)
+        bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles), morton_bits=bits)
+        d = bvh.query(_dev(F), _dev(E), mode)
+        outs = {}
+        if mode in ("any_hit", "both"):
+            outs["hit"] = torch.empty(n, dtype=torch.uint8).pin_memory()
+        if mode in ("count", "both"):
+            outs["count"] = torch.empty(n, dtype=torch.int32).pin_memory()
+        outs["ambiguous"] = torch.empty(n, dtype=torch.uint8).pin_memory()
+        for t in outs.values():
+            t.fill_(0xAB if t.dtype == torch.uint8 else -7)   # stale values must not survive
+        h = bvh.query_host(torch.from_numpy(F).pin_memory(), torch.from_numpy(E).pin_memory(), mode,
+                           stats=True, **outs)
+        assert h["stats"]["band_rays"] > 0
+        for k, t in outs.items():
+            assert torch.equal(t, d[k].cpu()), (cfg, mode, k)
+
+
 def test_host_path_whole_batch_above_2_26(rsi):
     """A host batch of 2^26 + 12,345 segments (1.6 GB of segments in, 64
     chunks): staged whole, its answers in both modes at once equal the
