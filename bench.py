@@ -1041,7 +1041,7 @@ def main():
                    "morton_bits": 30, "l2": "inputs larger than L2 (240 MB of segments per batch), no flush",
                    "segment_order": bool(args.order),
                    "tree": (f"the paper's Karras build + {tp} treelet restructuring pass(es) (depth-tiled treelets of "
-                            "up to 8 subtrees; answers identical to the plain tree's)") if tp
+                            "up to 7 subtrees; answers identical to the plain tree's)") if tp
                    else "the paper's Karras build as built",
                    "fp64_retest": "on (band segments re-tested in FP64)"},
         "roofline": {"kernel": "k_query_fp32<count> (FP32 traversal, intercept_count)", "bound": "hbm",
