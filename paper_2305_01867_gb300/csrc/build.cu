@@ -29,6 +29,20 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Atomic add at GPU scope with acquire-release ordering: this thread's earlier
+// writes are visible to a thread that reads the result, and that thread's
+// later loads see the writes released before it.
+__device__ __forceinline__ int atomic_add_acq_rel(int32_t* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int32_t atomic_exch_acq_rel(int32_t* p, int32_t v) {
+    int32_t old;
+    asm volatile("atom.acq_rel.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ unsigned int f2ord(float f) {
     unsigned int b = __float_as_uint(f);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
@@ -167,13 +181,18 @@ __device__ __forceinline__ K morton_key(const float* __restrict__ V, int64_t nv,
     return MortonTraits<K>::encode(q[0], q[1], q[2]);
 }
 
+// With `hist0`, also the count of every lowest 8-bit digit per sort tile of
+// `tile` keys (tile-major, 256 counters per tile): the first pass's histogram.
 template <typename K>
 __global__ void k_morton(const float* __restrict__ V, int64_t nv, const int32_t* __restrict__ T, int64_t nt,
-                         DevCounters* c, K* __restrict__ keys, int32_t* __restrict__ ids) {
+                         DevCounters* c, K* __restrict__ keys, int32_t* __restrict__ ids, uint32_t* __restrict__ hist0,
+                         int tile) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= nt) return;
     ids[j] = (int32_t)j;
-    keys[j] = morton_key<K>(V, nv, T, j, c);
+    const K key = morton_key<K>(V, nv, T, j, c);
+    keys[j] = key;
+    if (hist0) atomicAdd(&hist0[(j / tile) * 256 + (uint32_t)(key & 255u)], 1u);
 }
 
 // ---------------------------------------------------------------- radix sort
@@ -218,16 +237,19 @@ __global__ void k_rs_scan(uint32_t* __restrict__ h, int64_t m) {
     }
 }
 
+// Stable scatter of `rounds` rounds of 256 keys from tile0 on: keys are
+// ranked inside each round in index order (warp match, then the warps in
+// order) and go to base[digit] + rank; base[] advances by each round's
+// counts.  With `hist_next`, every written key is also counted under its next
+// digit in the histogram of the output tile (tsize keys) it lands in.
 template <typename K>
-__global__ void __launch_bounds__(256) k_rs_scatter(const K* __restrict__ kin, const int32_t* __restrict__ vin,
-                                                    K* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
-                                                    int shift, const uint32_t* __restrict__ hist, int ntiles) {
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wcnt[8][256];
+__device__ __forceinline__ void scatter_rounds(const K* __restrict__ kin, const int32_t* __restrict__ vin,
+                                               K* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
+                                               int shift, int64_t tile0, int rounds, uint32_t* base,
+                                               uint32_t (*wcnt)[256], uint32_t* __restrict__ hist_next,
+                                               int64_t tsize) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    base[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-    int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
-    for (int r = 0; r < kSortTile / 256; ++r) {
+    for (int r = 0; r < rounds; ++r) {
         int64_t i = tile0 + r * 256 + threadIdx.x;
         bool valid = i < n;
         K key = valid ? kin[i] : K(0);
@@ -253,12 +275,86 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const K* __restrict__ kin, c
                 uint32_t pos = base[dig] + wcnt[warp][dig] + rank;
                 kout[pos] = key;
                 vout[pos] = vin[i];
+                if (hist_next) atomicAdd(&hist_next[(pos / tsize) * 256 + ((uint32_t)(key >> (shift + 8)) & 255u)], 1u);
             }
             __syncthreads();
             base[threadIdx.x] += run;
         }
         __syncthreads();
     }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_rs_scatter(const K* __restrict__ kin, const int32_t* __restrict__ vin,
+                                                    K* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
+                                                    int shift, const uint32_t* __restrict__ hist, int ntiles) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[8][256];
+    base[threadIdx.x] = hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    scatter_rounds<K>(kin, vin, kout, vout, n, shift, (int64_t)blockIdx.x * kSortTile, kSortTile / 256, base, wcnt,
+                      nullptr, 1);
+}
+
+// One pass of the single-mesh sort (at most kScanTiles tiles of 256 * rounds
+// keys): the block sums the tile histograms itself -- digit d of tile b
+// starts after every key of a smaller digit and the keys of digit d in tiles
+// before b -- then scatters its tile stably and counts the next digit of the
+// written keys per output tile (hist_next, null in the last pass).
+constexpr int kScanTiles = 128;
+template <typename K>
+__global__ void __launch_bounds__(256) k_rs_pass(const K* __restrict__ kin, const int32_t* __restrict__ vin,
+                                                 K* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
+                                                 int shift, int rounds, int ntiles, const uint32_t* __restrict__ hist,
+                                                 uint32_t* __restrict__ hist_next) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[8][256];
+    __shared__ uint32_t wsum[8];
+    const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
+    uint32_t before = 0, total = 0;
+    for (int t0 = 0; t0 < ntiles; t0 += 32) {   // 32 independent loads in flight per thread
+        uint32_t c[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) c[u] = t0 + u < ntiles ? __ldcg(hist + (int64_t)(t0 + u) * 256 + d) : 0u;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+            before += t0 + u < (int)blockIdx.x ? c[u] : 0u;
+            total += c[u];
+        }
+    }
+    uint32_t incl = total;   // inclusive scan of the digit totals: warps, then across warps
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    base[d] = wpre + incl - total + before;
+    const int64_t tsize = (int64_t)rounds * 256;
+    scatter_rounds<K>(kin, vin, kout, vout, n, shift, (int64_t)blockIdx.x * tsize, rounds, base, wcnt, hist_next,
+                      tsize);
+}
+
+// How a single mesh's keys are sorted: up to kScanTiles * kSortTile keys in
+// tiles of 256 * rounds keys (rounds as small as the tile limit allows, so
+// that small meshes get many short blocks), one launch per pass; more keys
+// take the three-launch passes over tiles of kSortTile keys.
+struct SortPlan {
+    int rounds, ntiles;
+    bool fused;
+};
+inline SortPlan sort_plan(int64_t n) {
+    if (n > (int64_t)kScanTiles * kSortTile) return {kSortTile / 256, grid_for(n, kSortTile), false};
+    int64_t rounds = (n + 256LL * kScanTiles - 1) / (256LL * kScanTiles);
+    if (rounds < 1) rounds = 1;
+    return {(int)rounds, grid_for(n, 256 * (int)rounds), true};
+}
+inline size_t sort_hist_bytes(int64_t n, int passes) {
+    const SortPlan sp = sort_plan(n);
+    const size_t three = 4 * 256 * (size_t)grid_for(n, kSortTile);
+    return sp.fused ? std::max(three, 4 * 256 * (size_t)sp.ntiles * passes) : three;
 }
 
 // ---------------------------------------------------------------- radix tree
@@ -364,37 +460,48 @@ __global__ void k_refit(const float* __restrict__ V, int64_t nv, const int32_t* 
     tr.pad = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     tris[j] = tr;
     float* bx = box + 6 * (n - 1 + j);
+    float cb[6];   // the box and height of the subtree this thread climbs from
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float mn = fminf(fminf(v[0][a], v[1][a]), v[2][a]);
         float mx = fmaxf(fmaxf(v[0][a], v[1][a]), v[2][a]);
-        bx[a] = mn;
-        bx[3 + a] = mx;
+        bx[a] = cb[a] = mn;
+        bx[3 + a] = cb[3 + a] = mx;
         atomicMax(&c->dmax_bits[a], __float_as_uint(mx - mn));   // >= 0: uint order = float order
     }
     hgt[n - 1 + j] = 0;
     if (n == 1) return;
+    int ch = 0;
+    int64_t from = n - 1 + j;
     int32_t node = parent[n - 1 + j];
     while (node >= 0) {
-        __threadfence();
-        if (atomicAdd(&flag[node], 1) == 0) return;
-        __threadfence();
-        int32_t lc = left[node], rc = right[node];
-        int64_t sl = box_slot(lc, n), sr = box_slot(rc, n);
+        // the node's links are fixed during the pass: read them before arriving
+        const int32_t lc = left[node], rc = right[node], up = parent[node];
+        // release this thread's box writes and acquire the sibling's: the
+        // first arrival stops, the second unions the two children
+        if (atomic_add_acq_rel(&flag[node], 1) == 0) return;
+        const int64_t sl = box_slot(lc, n), sr = box_slot(rc, n);
+        const bool from_left = sl == from;
+        const int64_t sib = from_left ? sr : sl;
+        float sb[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) sb[a] = __ldcg(box + 6 * sib + a);
+        const int h = 1 + max(ch, __ldcg(hgt + sib));
         float bl[6], br[6];
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
-            bl[a] = __ldcg(box + 6 * sl + a);
-            br[a] = __ldcg(box + 6 * sr + a);
+            bl[a] = from_left ? cb[a] : sb[a];
+            br[a] = from_left ? sb[a] : cb[a];
         }
-        int h = 1 + max(__ldcg(hgt + sl), __ldcg(hgt + sr));
         float* bn = box + 6 * (int64_t)node;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            bn[a] = fminf(bl[a], br[a]);
-            bn[3 + a] = fmaxf(bl[3 + a], br[3 + a]);
+            bn[a] = cb[a] = fminf(bl[a], br[a]);
+            bn[3 + a] = cb[3 + a] = fmaxf(bl[3 + a], br[3 + a]);
         }
         hgt[node] = h;
+        ch = h;
+        from = node;
         Node nd;
         nd.lmin = make_float4(bl[0], bl[1], bl[2], __int_as_float(packed_ref(lc)));
         nd.lmax = make_float4(bl[3], bl[4], bl[5], __int_as_float(packed_ref(rc)));
@@ -402,7 +509,7 @@ __global__ void k_refit(const float* __restrict__ V, int64_t nv, const int32_t* 
         nd.rmax = make_float4(br[3], br[4], br[5], 0.0f);
         nodes[node] = nd;
         if (node == 0) c->height = h;
-        node = parent[node];
+        node = up;
     }
 }
 
@@ -632,10 +739,9 @@ __device__ __forceinline__ void apetrei_leaf(const float* __restrict__ V, int64_
         }
         if (root) return;
         const int64_t g = is_left ? hi : lo - 1;   // the parent's split
-        __threadfence();
-        const int32_t other = atomicExch(&ends[g], (int32_t)(is_left ? lo : hi));
+        // released with this thread's writes; acquires the sibling's
+        const int32_t other = atomic_exch_acq_rel(&ends[g], (int32_t)(is_left ? lo : hi));
         if (other < 0) return;   // first to arrive: the sibling carries on
-        __threadfence();
         const int64_t plo = is_left ? lo : (int64_t)other, phi = is_left ? (int64_t)other : hi;
         // the sibling's number (as in the Karras numbering) and its box
         const int64_t sib = is_left ? (phi == g + 1 ? n - 1 + g + 1 : g + 1) : (plo == g ? n - 1 + g : g);
@@ -688,6 +794,29 @@ int sort_pairs(K* ka, int32_t* va, K* kb, int32_t* vb, int64_t n, int passes, ui
     return e == cudaSuccess ? RSI_OK : rsi::cuda_fail(e, "radix sort launch");
 }
 
+// The fused passes (sort_plan(n).fused): hist holds one tile-major
+// histogram per pass, zeroed, the first filled by k_morton; the last pass
+// writes the sorted keys and values to out_k / out_v.
+template <typename K>
+int sort_pairs_fused(K* ka, int32_t* va, K* kb, int32_t* vb, int64_t n, int passes, const SortPlan& sp,
+                     uint32_t* hist, K* out_k, int32_t* out_v, cudaStream_t s) {
+    const size_t per = (size_t)256 * sp.ntiles;
+    for (int p = 0; p < passes; ++p) {
+        const bool last = p + 1 == passes;
+        k_rs_pass<K><<<sp.ntiles, 256, 0, s>>>(ka, va, last ? out_k : kb, last ? out_v : vb, n, 8 * p, sp.rounds,
+                                                sp.ntiles, hist + per * p, last ? nullptr : hist + per * (p + 1));
+        K* tk = ka;
+        ka = kb;
+        kb = tk;
+        int32_t* tv = va;
+        va = vb;
+        vb = tv;
+    }
+    note_launches(passes);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? RSI_OK : rsi::cuda_fail(e, "radix sort launch");
+}
+
 template <typename K>
 int build_impl(rsi_bvh_s* h, const float* V, const int32_t* T, int builder, cudaStream_t s, char* scratch,
                float* box, int32_t* hgt, int32_t* flag) {
@@ -697,15 +826,23 @@ int build_impl(rsi_bvh_s* h, const float* V, const int32_t* T, int builder, cuda
     int32_t* va = (int32_t*)(kb + n);
     int32_t* vb = va + n;
     uint32_t* hist = (uint32_t*)(vb + n);
-    k_morton<K><<<grid_for(n, kBlock), kBlock, 0, s>>>(V, h->n_vert, T, n, h->ctr, ka, va);
-    note_launches(1);
     const int passes = sizeof(K) == 4 ? 4 : 8;   // 30-bit codes: 4 digits; 63-bit: 8
-    K* sk;
-    int32_t* sv;
-    int rc = sort_pairs<K>(ka, va, kb, vb, n, passes, hist, s, &sk, &sv);
-    if (rc) return rc;
-    RSI_CUDA_TRY(cudaMemcpyAsync(h->sorted_keys, sk, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
-    RSI_CUDA_TRY(cudaMemcpyAsync(h->perm, sv, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    const SortPlan sp = sort_plan(n);
+    if (sp.fused) RSI_CUDA_TRY(cudaMemsetAsync(hist, 0, (size_t)4 * 256 * sp.ntiles * passes, s));
+    k_morton<K><<<grid_for(n, kBlock), kBlock, 0, s>>>(V, h->n_vert, T, n, h->ctr, ka, va, sp.fused ? hist : nullptr,
+                                                       256 * sp.rounds);
+    note_launches(1);
+    if (sp.fused) {
+        const int rc = sort_pairs_fused<K>(ka, va, kb, vb, n, passes, sp, hist, (K*)h->sorted_keys, h->perm, s);
+        if (rc) return rc;
+    } else {
+        K* sk;
+        int32_t* sv;
+        const int rc = sort_pairs<K>(ka, va, kb, vb, n, passes, hist, s, &sk, &sv);
+        if (rc) return rc;
+        RSI_CUDA_TRY(cudaMemcpyAsync(h->sorted_keys, sk, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
+        RSI_CUDA_TRY(cudaMemcpyAsync(h->perm, sv, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
     if (builder == RSI_TREE_APETREI) {
         k_apetrei<K><<<grid_for(n, kBlock), kBlock, 0, s>>>(V, h->n_vert, T, h->perm, (const K*)h->sorted_keys, n,
                                                              h->left, h->right, h->parent, box, hgt, flag, h->nodes,
@@ -831,7 +968,6 @@ rsi_bvh_s* alloc_handle(int64_t nv, int64_t nt, int morton_bits, bool sort_scrat
     h->morton_bits = morton_bits;
     const int64_t n = nt, ni = n > 1 ? n - 1 : 1;
     const size_t ksz = morton_bits == 30 ? 4 : 8;
-    const int ntiles = grid_for(n, 4096);
     // one allocation, carved into the handle's arrays (256-byte aligned)
     size_t off[14], total = 0;
     size_t sizes[14] = {
@@ -846,7 +982,7 @@ rsi_bvh_s* alloc_handle(int64_t nv, int64_t nt, int morton_bits, bool sort_scrat
         4 * (size_t)(2 * n - 1),                   // 8 heights
         4 * (size_t)ni,                            // 9 flags
         sizeof(DevCounters),                       // 10 counters
-        sort_scratch ? 2 * ksz * (size_t)n + 8 * (size_t)n + 4 * 256 * (size_t)ntiles : 0,  // 11 sort scratch
+        sort_scratch ? 2 * ksz * (size_t)n + 8 * (size_t)n + sort_hist_bytes(n, ksz == 4 ? 4 : 8) : 0,  // 11 sort scratch
         sizeof(Node4) * (size_t)ni,                // 12 four-wide nodes
         sizeof(NodeQ) * (size_t)ni                 // 13 compressed nodes
     };

@@ -82,22 +82,6 @@ struct BatchArgs {
     const int32_t* perm; // [total] batch-local segment of each global index (in-tile reordering), or NULL
 };
 
-// Scratch of the pair-parallel FP64 pass: the (segment, triangle) pairs that
-// the FP32 test could not reject for certain, listed per queued segment
-// ("band entry" k = position in the FP64 queue).
-struct PairScratch {
-    int32_t* seg_off;     // [seg_cap] first pair of band entry k
-    int32_t* seg_cnt;     // [seg_cap] its number of pairs; -1: left to k_query_fp64
-    int32_t* pair_seg;    // [pair_cap] band entry of pair i (-1: slot unused)
-    int32_t* pair_leaf;   // [pair_cap] leaf (triangle in leaf order) of pair i
-    double* pair_t;       // [pair_cap] t of pair i when it is an inclusive crossing
-    uint8_t* pair_cls;    // [pair_cap] class of pair i, | 4 when inclusive
-    int32_t* hard;        // [pair_cap] pairs the certain FP64 test left undecided
-    int32_t* fb_ids;      // [queue capacity] segments left to k_query_fp64
-    int seg_cap, pair_cap;
-    int min_queue;        // queues shorter than this go to k_query_fp64 whole
-};
-
 namespace {
 
 using namespace segtest;   // FP32 segment, box and triangle tests (segtest.cuh)
@@ -643,6 +627,28 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
 
 // [traversal kernel: end]
 
+}  // namespace
+
+// Scratch of the pair-parallel FP64 pass: the (segment, triangle) pairs that
+// the FP32 test could not reject for certain, listed per queued segment
+// ("band entry" k = position in the FP64 queue).
+struct PairScratch {
+    int32_t* seg_off;     // [seg_cap] first pair of band entry k
+    int32_t* seg_cnt;     // [seg_cap] its number of pairs; -1: left to k_query_fp64
+    int32_t* pair_seg;    // [pair_cap] band entry of pair i (-1: slot unused)
+    int32_t* pair_leaf;   // [pair_cap] leaf (triangle in leaf order) of pair i
+    double* pair_t;       // [pair_cap] t of pair i when it is an inclusive crossing
+    uint8_t* pair_cls;    // [pair_cap] class of pair i, | 4 when inclusive, | 8 when its t is not computed
+    int32_t* todo;        // [pair_cap] pairs for the FP64 classification
+    int32_t* hard;        // [pair_cap] pairs the certain FP64 test left undecided
+    int32_t* fb_ids;      // [queue capacity] segments left to k_query_fp64
+    int seg_cap, pair_cap;
+    int min_queue;        // queues shorter than this go to k_query_fp64 whole
+    int fp32_hits;        // 1: a certain FP32 hit is entered as a hit without the FP64 step
+};
+
+namespace {
+
 // Ambiguity byte of a count-mode result.  In RSI_BOTH the count pass also
 // answers the boolean mode: its hit flag (count > 0) is the boolean answer,
 // and a segment is ambiguous for the boolean mode when it is for the count
@@ -891,20 +897,24 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B, co
 
 // ---------------------------------------------------------------- pair-parallel FP64 pass
 // The same settlement of the queued segments as k_query_fp64 in three steps
-// that keep every lane busy: (1) one warp per queued segment: lane 0 walks
-// the boxes (a light kernel, so many walks run at once) in rounds of up to
-// 32 leaves, the lanes run the FP32 test on each round's leaves side by side
-// and list those that are not a certain miss -- or, for queues of 32,768
-// segments or more, one thread per segment (divergent, but 32 walks per
-// warp); (2) one
-// thread per listed (segment, triangle) pair classifies it in FP64 -- the
-// certain numerator test, else the definition -- so FP64 instructions run
-// with full warps (a warp's FP64 instruction costs the same however many
+// that keep the lanes busy: (1) the pairs of each queued segment are listed
+// -- for queues of up to 32,767 segments by one warp per segment whose lanes
+// walk the boxes together (every round each lane takes one node of the
+// warp's node list), for longer queues by one thread per segment -- with the
+// FP32 test on each reached leaf: a certain miss is dropped; with
+// P.fp32_hits (boolean and count modes) a certain FP32 hit is entered as a
+// hit at once, the FP32 test being sound, and only the undecided pairs are
+// listed for step 2; (2) one thread per listed pair classifies it in FP64 --
+// the certain numerator test, else the definition -- so FP64 instructions
+// run with full warps (a warp's FP64 instruction costs the same however many
 // lanes take part); (3) one thread per segment combines its pairs exactly as
-// k_query_fp64 does.  Segments with more than kCandMax candidates, or that
-// do not fit the scratch, go to k_query_fp64 through the fallback list.
+// k_query_fp64 does, computing the t of a hit only where the count mode
+// needs it (an ambiguous segment's distinct crossings).  Segments with more
+// than kCandMax candidates, or that do not fit the scratch, go to
+// k_query_fp64 through the fallback list.
 constexpr int kCandMax = 32;
 constexpr int kThreadQueue = 32768;   // from this queue length on, one thread per segment collects
+constexpr uint8_t kTPending = 8;      // pair_cls flag: inclusive hit whose t is not computed yet
 
 // Band entry gidx (a segment index, global over the batches when batched):
 // its index r within its batch and that batch's hierarchy and outputs.
@@ -932,11 +942,33 @@ __device__ __forceinline__ QueryArgs band_segment(const QueryArgs& A, const Batc
     return Q;
 }
 
-template <int STACK, bool BATCHED>
-__global__ void __launch_bounds__(128) k_band_collect(QueryArgs A, BatchArgs B, PairScratch P) {
-    constexpr int kWarps = 4;
-    __shared__ int s_leaf[kWarps][32];          // leaves whose box the segment passes (one round)
-    __shared__ int s_cand[kWarps][kCandMax];    // those the FP32 test does not reject
+// Class byte of a listed candidate and whether it waits for the FP64 step.
+__device__ __forceinline__ bool pair_preset(const PairScratch& P, bool fp32_hit, uint8_t& cls) {
+    const bool pre = P.fp32_hits && fp32_hit;
+    cls = pre ? (uint8_t)(kHit | 4 | kTPending) : (uint8_t)0;
+    return !pre;
+}
+
+// Lanes in `want` append `item` to list[] (count in *counter), one atomic per warp.
+__device__ __forceinline__ void warp_append(bool want, int32_t item, int32_t* list, int* counter) {
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(kFull, want);
+    if (!m) return;
+    int base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(kFull, base, __ffs(m) - 1);
+    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = item;
+}
+
+constexpr int kFront = 256;   // a warp's node list; a walk that needs more goes to k_query_fp64
+template <bool BATCHED>
+__global__ void __launch_bounds__(128, 12) k_band_collect(QueryArgs A, BatchArgs B, PairScratch P) {
+    constexpr int kWarps = 4, kLeafBuf = 96;
+    __shared__ int s_front[kWarps][kFront];     // nodes still to open
+    __shared__ int s_leaf[kWarps][kLeafBuf];    // leaves whose box the segment passes, not yet tested
+    __shared__ int s_cand[kWarps][kCandMax];    // leaves the FP32 test does not reject
+    __shared__ uint8_t s_hit[kWarps][kCandMax]; // ... and whether it is a certain FP32 hit
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -948,70 +980,71 @@ __global__ void __launch_bounds__(128) k_band_collect(QueryArgs A, BatchArgs B, 
         const float3 s = make_float3(Q.from[3 * r], Q.from[3 * r + 1], Q.from[3 * r + 2]);
         const float3 e = make_float3(Q.to[3 * r], Q.to[3 * r + 1], Q.to[3 * r + 2]);
         const SegF g = make_seg(s, e, Q.dmax0, Q.dmax1, Q.dmax2);
-        bool over = k >= P.seg_cap || nb < P.min_queue;
-        bool done = over;
-        int nc = 0;
-        int node = 0, sp = 0;   // lane 0's walk, resumed every round
-        int stack[STACK];
-        while (!done) {
-            int nl = 0;
-            if (lane == 0) {   // walk the boxes until 31 leaves are reached or the walk ends
-                if (Q.n_tri == 1) {
-                    s_leaf[w][nl++] = 0;
-                    done = true;
-                }
-                while (!done && nl <= 30) {
+        bool over = k >= P.seg_cap || nb < P.min_queue;   // warp-uniform
+        int nc = 0, nf = 0, nl = 0;                        // warp-uniform list lengths
+        if (!over) {
+            if (Q.n_tri == 1) {
+                if (lane == 0) s_leaf[w][0] = 0;
+                nl = 1;
+            } else {
+                if (lane == 0) s_front[w][0] = 0;
+                nf = 1;
+            }
+        }
+        __syncwarp();
+        while (!over && (nf > 0 || nl > 0)) {
+            if (nf > 0) {   // open up to 32 nodes, one per lane
+                const int m = min(32, nf);
+                const int node = lane < m ? s_front[w][nf - 1 - lane] : 0;
+                nf -= m;
+                __syncwarp();   // the entries are read before the pushes below overwrite them
+                bool hl = false, hr = false;
+                int lref = 0, rref = 0;
+                if (lane < m) {
                     float4 lmin, lmax, rmin, rmax;
                     load_node(Q.nodes, node, lmin, lmax, rmin, rmax);
-                    const int lref = __float_as_int(lmin.w), rref = __float_as_int(lmax.w);
-                    bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
-                    if (hl && lref < 0) {
-                        hl = false;
-                        s_leaf[w][nl++] = ~lref;
-                    }
-                    if (hr && rref < 0) {
-                        hr = false;
-                        s_leaf[w][nl++] = ~rref;
-                    }
-                    if (hl && hr) {
-                        if (sp == STACK) {   // k_query_fp64 raises RSI_ERR_STACK for it
-                            over = true;
-                            done = true;
-                        } else {
-                            stack[sp++] = rref;
-                            node = lref;
-                        }
-                    } else if (hl) {
-                        node = lref;
-                    } else if (hr) {
-                        node = rref;
-                    } else if (sp > 0) {
-                        node = stack[--sp];
-                    } else {
-                        done = true;
-                    }
+                    lref = __float_as_int(lmin.w);
+                    rref = __float_as_int(lmax.w);
+                    hl = slab(lmin, lmax, g);
+                    hr = slab(rmin, rmax, g);
                 }
+                const unsigned il = __ballot_sync(kFull, hl && lref >= 0), ir = __ballot_sync(kFull, hr && rref >= 0);
+                const unsigned ll = __ballot_sync(kFull, hl && lref < 0), lr = __ballot_sync(kFull, hr && rref < 0);
+                const int npush = __popc(il) + __popc(ir), nleaf = __popc(ll) + __popc(lr);
+                if (nf + npush > kFront) {
+                    over = true;   // k_query_fp64 walks it with its own stack
+                } else {
+                    if ((il >> lane) & 1u) s_front[w][nf + __popc(il & lt)] = lref;
+                    if ((ir >> lane) & 1u) s_front[w][nf + __popc(il) + __popc(ir & lt)] = rref;
+                    if ((ll >> lane) & 1u) s_leaf[w][nl + __popc(ll & lt)] = ~lref;
+                    if ((lr >> lane) & 1u) s_leaf[w][nl + __popc(ll) + __popc(lr & lt)] = ~rref;
+                    nf += npush;
+                    nl += nleaf;   // below 32 + 64 (tested below once 32 wait)
+                }
+                __syncwarp();
             }
-            nl = __shfl_sync(kFull, nl, 0);
-            done = __shfl_sync(kFull, done ? 1 : 0, 0) != 0;
-            over = __shfl_sync(kFull, over ? 1 : 0, 0) != 0;
-            __syncwarp();
-            bool keep = false;   // the FP32 triangle tests, side by side
-            int leaf = 0;
-            if (!over && lane < nl) {
-                bool plain;
-                leaf = s_leaf[w][lane];
-                keep = tri_fp32(g, load_tri(Q.tris, leaf), false, plain) != kMiss;
+            // the FP32 test on the reached leaves, 32 at a time, once 32 wait or the walk is over
+            while (!over && (nl >= 32 || (nf == 0 && nl > 0))) {
+                const int t = min(32, nl);
+                int leaf = 0, cls = kMiss;
+                if (lane < t) {
+                    bool plain;
+                    leaf = s_leaf[w][nl - 1 - lane];
+                    cls = tri_fp32(g, load_tri(Q.tris, leaf), false, plain);
+                }
+                nl -= t;
+                const unsigned mk = __ballot_sync(kFull, cls != kMiss);
+                if (nc + __popc(mk) > kCandMax) {
+                    over = true;
+                } else {
+                    if (cls != kMiss) {
+                        s_cand[w][nc + __popc(mk & lt)] = leaf;
+                        s_hit[w][nc + __popc(mk & lt)] = (uint8_t)(cls == kHit);
+                    }
+                    nc += __popc(mk);
+                }
+                __syncwarp();
             }
-            const unsigned m = __ballot_sync(kFull, keep);
-            if (nc + __popc(m) > kCandMax) {
-                over = true;
-                done = true;
-            } else {
-                if (keep) s_cand[w][nc + __popc(m & lt)] = leaf;
-                nc += __popc(m);
-            }
-            __syncwarp();
         }
         int base = -1;
         // reserve nc pairs; the counter is read first so that it cannot run far past the capacity
@@ -1024,10 +1057,15 @@ __global__ void __launch_bounds__(128) k_band_collect(QueryArgs A, BatchArgs B, 
         }
         base = __shfl_sync(kFull, base, 0);
         if (base >= 0) {
+            bool undecided = false;
             if (lane < nc) {
+                uint8_t cls;
+                undecided = pair_preset(P, s_hit[w][lane] != 0, cls);
                 P.pair_seg[base + lane] = k;
                 P.pair_leaf[base + lane] = s_cand[w][lane];
+                P.pair_cls[base + lane] = cls;
             }
+            warp_append(undecided, base + lane, P.todo, &A.ctr->todo_count);
             if (lane == 0) {
                 P.seg_off[k] = base;
                 P.seg_cnt[k] = nc;
@@ -1041,24 +1079,34 @@ __global__ void __launch_bounds__(128) k_band_collect(QueryArgs A, BatchArgs B, 
 }
 
 // Step 1 for long queues: one thread per queued segment walks the tree and
-// tests the reached leaves itself.
+// tests the reached leaves itself; the warp reserves its pairs and lists its
+// undecided ones with one atomic each.
 template <int STACK, bool BATCHED>
 __global__ void __launch_bounds__(128) k_band_collect_threads(QueryArgs A, BatchArgs B, PairScratch P) {
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int nb = *(volatile int*)&A.ctr->band_count;
     if (nb < kThreadQueue) return;   // k_band_collect takes short queues
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
-        int64_t r;
-        const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
+    const int stride = gridDim.x * blockDim.x;
+    for (int k0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < nb; k0 += stride) {   // warp-uniform
+        const int k = k0 + lane;
         int cand[kCandMax];
+        unsigned hits = 0;   // bit i: cand[i] is a certain FP32 hit
         int nc = 0;
         bool over = k >= P.seg_cap;
-        if (!over) {
+        if (k < nb && !over) {
+            int64_t r;
+            const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
             const float3 s = make_float3(Q.from[3 * r], Q.from[3 * r + 1], Q.from[3 * r + 2]);
             const float3 e = make_float3(Q.to[3 * r], Q.to[3 * r + 1], Q.to[3 * r + 2]);
             const SegF g = make_seg(s, e, Q.dmax0, Q.dmax1, Q.dmax2);
             bool plain;
             if (Q.n_tri == 1) {
-                if (tri_fp32(g, load_tri(Q.tris, 0), false, plain) != kMiss) cand[nc++] = 0;
+                const int c = tri_fp32(g, load_tri(Q.tris, 0), false, plain);
+                if (c != kMiss) {
+                    hits = c == kHit ? 1u : 0u;
+                    cand[nc++] = 0;
+                }
             } else {
                 int node = 0, sp = 0;
                 int stack[STACK];
@@ -1069,21 +1117,25 @@ __global__ void __launch_bounds__(128) k_band_collect_threads(QueryArgs A, Batch
                     bool hl = slab(lmin, lmax, g), hr = slab(rmin, rmax, g);
                     if (hl && lref < 0) {
                         hl = false;
-                        if (tri_fp32(g, load_tri(Q.tris, ~lref), false, plain) != kMiss) {
+                        const int c = tri_fp32(g, load_tri(Q.tris, ~lref), false, plain);
+                        if (c != kMiss) {
                             if (nc == kCandMax) {
                                 over = true;
                                 break;
                             }
+                            hits |= (c == kHit ? 1u : 0u) << nc;
                             cand[nc++] = ~lref;
                         }
                     }
                     if (hr && rref < 0) {
                         hr = false;
-                        if (tri_fp32(g, load_tri(Q.tris, ~rref), false, plain) != kMiss) {
+                        const int c = tri_fp32(g, load_tri(Q.tris, ~rref), false, plain);
+                        if (c != kMiss) {
                             if (nc == kCandMax) {
                                 over = true;
                                 break;
                             }
+                            hits |= (c == kHit ? 1u : 0u) << nc;
                             cand[nc++] = ~rref;
                         }
                     }
@@ -1106,29 +1158,69 @@ __global__ void __launch_bounds__(128) k_band_collect_threads(QueryArgs A, Batch
                 }
             }
         }
-        // reserve nc pairs; the counter is read first so that it cannot run far past the capacity
-        if (!over && *(volatile int*)&A.ctr->pair_count <= P.pair_cap - nc) {
-            const int base = atomicAdd(&A.ctr->pair_count, nc);
-            if (base <= P.pair_cap - nc) {
-                for (int i = 0; i < nc; ++i) {
-                    P.pair_seg[base + i] = k;
-                    P.pair_leaf[base + i] = cand[i];
-                }
-                P.seg_off[k] = base;
-                P.seg_cnt[k] = nc;
-                continue;
-            }
-            for (int i = base; i < P.pair_cap && i < base + nc; ++i) P.pair_seg[i] = -1;
+        // the warp's pairs: one reservation; if the scratch cannot take them all, every segment of
+        // the warp goes to the fallback list (the counter is read first so that it cannot run far
+        // past the capacity)
+        const bool want = k < nb && !over;
+        int incl = want ? nc : 0;   // inclusive scan of the pair counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
         }
-        if (k < P.seg_cap) P.seg_cnt[k] = -1;
-        P.fb_ids[atomicAdd(&A.ctr->fb_count, 1)] = A.band_ids[k];
+        const int total = __shfl_sync(kFull, incl, 31);
+        int base = -1;
+        if (lane == 0 && total > 0 && *(volatile int*)&A.ctr->pair_count <= P.pair_cap - total) {
+            base = atomicAdd(&A.ctr->pair_count, total);
+            if (base > P.pair_cap - total) {
+                for (int i = base; i < P.pair_cap && i < base + total; ++i) P.pair_seg[i] = -1;
+                base = -1;
+            }
+        }
+        base = total > 0 ? __shfl_sync(kFull, base, 0) : 0;
+        const bool placed = want && base >= 0;
+        int n_undec = 0;
+        if (placed) {
+            const int off = base + incl - nc;
+            for (int i = 0; i < nc; ++i) {
+                uint8_t cls;
+                n_undec += pair_preset(P, (hits >> i) & 1u, cls) ? 1 : 0;
+                P.pair_seg[off + i] = k;
+                P.pair_leaf[off + i] = cand[i];
+                P.pair_cls[off + i] = cls;
+            }
+            P.seg_off[k] = off;
+            P.seg_cnt[k] = nc;
+        } else if (k < nb) {
+            if (k < P.seg_cap) P.seg_cnt[k] = -1;
+        }
+        // the undecided pairs, listed for step 2 (one reservation for the warp)
+        int uincl = n_undec;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, uincl, o);
+            if (lane >= o) uincl += v;
+        }
+        const int utotal = __shfl_sync(kFull, uincl, 31);
+        if (utotal > 0) {
+            int ubase = 0;
+            if (lane == 0) ubase = atomicAdd(&A.ctr->todo_count, utotal);
+            ubase = __shfl_sync(kFull, ubase, 0) + uincl - n_undec;
+            if (placed) {
+                const int off = base + incl - nc;
+                for (int i = 0; i < nc; ++i)
+                    if (!(P.fp32_hits && ((hits >> i) & 1u))) P.todo[ubase++] = off + i;
+            }
+        }
+        warp_append(k < nb && !placed, k < nb ? A.band_ids[k] : 0, P.fb_ids, &A.ctr->fb_count);
     }
 }
 
-// Step 2a: the certain FP64 test of every pair (no division or square root
-// unless the pair is a certain hit whose t is needed).  In a long pair list
-// the undecided pairs are listed for step 2b, so that the long evaluation of
-// the definition runs in warps made of undecided pairs only; in a short one
+// Step 2a: the certain FP64 test of every listed pair (no division or square
+// root unless the nearest mode needs the t of a certain hit; the count mode
+// computes it in step 3 where needed).  In a long list the pairs this test
+// leaves undecided are listed for step 2b, so that the long evaluation of the
+// definition runs in warps made of undecided pairs only; in a short one
 // (fewer than kHardSplit pairs, where the pass is latency-bound) they are
 // settled here.
 constexpr int kHardSplit = 1 << 17;
@@ -1136,12 +1228,12 @@ template <int MODE, bool BATCHED>
 __global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B, PairScratch P) {
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int np = min(*(volatile int*)&A.ctr->pair_count, P.pair_cap);
+    const int np = min(*(volatile int*)&A.ctr->todo_count, P.pair_cap);
     const int stride = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < np; i0 += stride) {
-        const int i = i0 + lane;
+    for (int j0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < np; j0 += stride) {
+        const int i = j0 + lane < np ? P.todo[j0 + lane] : -1;
         bool hard = false;
-        if (i < np) {
+        if (i >= 0) {
             const int k = P.pair_seg[i];
             if (k >= 0) {
                 int64_t r;
@@ -1153,12 +1245,13 @@ __global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B,
                 int cls = tri_certain64(sd, ed, a, b, c);
                 double t = 0.0;
                 bool incl = cls == kHit;
-                if (cls == kHit && MODE != RSI_ANY_HIT) t = t_of_definition(sd, ed, a, b, c);
+                if (cls == kHit && MODE == RSI_NEAREST) t = t_of_definition(sd, ed, a, b, c);
                 if (cls == kBand) {
                     if (np >= kHardSplit) hard = true;
                     else cls = classify_fp64(sd, ed, a, b, c, t, incl);
                 }
-                P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0));
+                const bool pending = cls == kHit && MODE == RSI_COUNT;   // t of a certain hit: step 3, if needed
+                P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0) | (pending ? kTPending : 0));
                 P.pair_t[i] = t;
             }
         }
@@ -1209,9 +1302,8 @@ __global__ void __launch_bounds__(128) k_band_reduce(QueryArgs A, BatchArgs B, P
             n_hit += (c & 3) == kHit;
             n_amb += (c & 3) == kBand;
             if (c & 4) {
-                const double t = P.pair_t[off + j];
-                if (MODE == RSI_COUNT) ts[n_incl] = t;
                 if (MODE == RSI_NEAREST) {
+                    const double t = P.pair_t[off + j];
                     const int leaf = P.pair_leaf[off + j];
                     const int id = __float_as_int(Q.tris[leaf].v0.w);
                     if (t < best_t || (t == best_t && id < best_id)) {
@@ -1236,6 +1328,19 @@ __global__ void __launch_bounds__(128) k_band_reduce(QueryArgs A, BatchArgs B, P
             const bool amb = n_amb > 0;
             int count = n_hit;
             if (amb) {   // distinct crossings of the closed-interval reading
+                const D3 sd = {(double)Q.from[3 * r], (double)Q.from[3 * r + 1], (double)Q.from[3 * r + 2]};
+                const D3 ed = {(double)Q.to[3 * r], (double)Q.to[3 * r + 1], (double)Q.to[3 * r + 2]};
+                int m = 0;
+                for (int j = 0; j < cnt; ++j) {   // t of every inclusive crossing (a certain hit's computed here)
+                    const int c = P.pair_cls[off + j];
+                    if (!(c & 4)) continue;
+                    double t = P.pair_t[off + j];
+                    if (c & kTPending) {
+                        const Tri tr = load_tri(Q.tris, P.pair_leaf[off + j]);
+                        t = t_of_definition(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2));
+                    }
+                    ts[m++] = t;
+                }
                 for (int i = 1; i < n_incl; ++i) {
                     const double x = ts[i];
                     int k2 = i - 1;
@@ -1806,6 +1911,7 @@ __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->pair_count = 0;
     c->fb_count = 0;
     c->hard_count = 0;
+    c->todo_count = 0;
     c->n_finish = 0;
     c->n_finish64 = 0;
     if (ready != ~0ull) c->ready = ready;   // ~0: a streaming plan, fed by posts
@@ -1873,20 +1979,15 @@ void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P0, cud
     }
     PairScratch Pm = *P0;
     Pm.min_queue = MODE == RSI_ANY_HIT ? 2048 : 0;
+    Pm.fp32_hits = MODE != RSI_NEAREST;   // the nearest mode needs every hit's t
     const PairScratch* P = &Pm;
     // step 1: both collect kernels are launched; the queue length (on the
     // device) lets exactly one of them work
     const int cgrid = device_sm_count() * 16;   // one warp per queued segment, 4 per block
-    if (height < 32) {
-        k_band_collect<32, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
-        k_band_collect_threads<32, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
-    } else if (height < 64) {
-        k_band_collect<64, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
-        k_band_collect_threads<64, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
-    } else {
-        k_band_collect<128, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
-        k_band_collect_threads<128, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
-    }
+    k_band_collect<BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+    if (height < 32) k_band_collect_threads<32, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+    else if (height < 64) k_band_collect_threads<64, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
+    else k_band_collect_threads<128, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
     k_band_classify<MODE, BATCHED><<<device_sm_count() * 8, 256, 0, s>>>(A, B, *P);
     k_band_classify_hard<BATCHED><<<device_sm_count() * 4, 256, 0, s>>>(A, B, *P);
     k_band_reduce<MODE, BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
@@ -2023,7 +2124,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
 void pair_sizes(int64_t q, int64_t& seg_cap, int64_t& pair_cap, size_t& bytes) {
     seg_cap = std::min<int64_t>(std::max<int64_t>(q / 16, 4096), 1 << 24);
     pair_cap = 4 * seg_cap;
-    bytes = 8 * (size_t)seg_cap + 21 * (size_t)pair_cap + 7 * 256;   // + alignment of the pieces
+    bytes = 8 * (size_t)seg_cap + 25 * (size_t)pair_cap + 8 * 256;   // + alignment of the pieces
 }
 
 PairScratch carve_pairs(char* mem, int64_t seg_cap, int64_t pair_cap, int32_t* fb_ids) {
@@ -2042,11 +2143,14 @@ PairScratch carve_pairs(char* mem, int64_t seg_cap, int64_t pair_cap, int32_t* f
     o += al(4 * (size_t)pair_cap);
     P.hard = reinterpret_cast<int32_t*>(mem + o);
     o += al(4 * (size_t)pair_cap);
+    P.todo = reinterpret_cast<int32_t*>(mem + o);
+    o += al(4 * (size_t)pair_cap);
     P.pair_cls = reinterpret_cast<uint8_t*>(mem + o);
     P.fb_ids = fb_ids;
     P.seg_cap = (int)seg_cap;
     P.pair_cap = (int)pair_cap;
     P.min_queue = 0;
+    P.fp32_hits = 0;
     return P;
 }
 

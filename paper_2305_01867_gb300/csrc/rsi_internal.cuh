@@ -88,7 +88,7 @@ struct DevCounters {
     int hard_count;             // FP64 pass: pairs the certain FP64 test left undecided
     int n_finish;               // nearest mode: hitting segments listed for the finish
     int n_finish64;             // nearest mode: of those, left to the FP64 evaluation
-    int pad3;
+    int todo_count;             // FP64 pass: listed pairs the FP32 test left undecided
 };
 
 }  // namespace rsi

@@ -44,10 +44,10 @@ namespace rsi {
 namespace {
 
 constexpr int kTreeletLevels = 3;          // levels of internal nodes in a treelet
-constexpr int kTreeletSpan = 1 << kTreeletLevels;     // subtrees hanging below 3 full levels
 constexpr int kTreeletLeaves = 7;          // a treelet's leaves (of 8 the smallest pair stays joined)
 constexpr int kFullSet = (1 << kTreeletLeaves) - 1;
 constexpr int kTreeletWarps = 4;           // warps per block of k_treelet
+constexpr int kTreeletBlocksPerSm = 12;    // register budget: 48 warps per SM, a warp per root of a c2-sized launch
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClimbMax = 1 << 16;         // climb steps before a pass gives up (RSI_ERR_STACK)
 
@@ -76,6 +76,11 @@ struct TreeletSmem {
     float lbox[kTreeletLeaves][6];   // treelet leaf boxes (min xyz, max xyz)
     int lref[kTreeletLeaves];        // treelet leaf references (tagged as the build tags them)
     int inner[kTreeletLeaves - 1];   // the treelet's internal nodes (inner[0] = its root)
+    float lowbox[16][6];             // boxes of the subsets of leaves 0-3 (index: the subset)
+    float highbox[8][6];             // boxes of the subsets of leaves 4-6 (index: the subset >> 4)
+    int g[4];                        // the third level: child c of r's child s at g[2 * s + c]
+    int y[8];                        // the fourth level: child c of g[q] at y[2 * q + c]
+    float g_area[4];                 // half areas of the internal g[q]
     float area[kFullSet + 1];        // surface area of the box of each leaf subset
     float cost[kFullSet + 1];        // best summed internal-node area of a tree over the subset
     uint8_t best[kFullSet + 1];      // the part holding the subset's lowest leaf, in that best tree
@@ -99,43 +104,82 @@ __device__ __forceinline__ void load_box(const float* __restrict__ box, int64_t 
 }
 
 
+__device__ __forceinline__ bool is_leaf_ref(int32_t ref) { return ((uint32_t)ref & kLeafTag) != 0; }
+
+__device__ __forceinline__ void box_union(float b[6], const float* o) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        b[c] = fminf(b[c], o[c]);
+        b[3 + c] = fmaxf(b[3 + c], o[3 + c]);
+    }
+}
+
+// Box of the leaf subset S (non-empty) from the boxes of its two halves.
+__device__ __forceinline__ void subset_box(const TreeletSmem& sm, int S, float b[6]) {
+    const int lo = S & 15, hi = S >> 4;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) b[c] = lo ? sm.lowbox[lo][c] : (c < 3 ? 3.0e38f : -3.0e38f);
+    if (hi) box_union(b, sm.highbox[hi]);
+}
+
 // Restructure the treelet rooted at internal node r (all 32 lanes call it).
 __device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_t* __restrict__ right,
                             int32_t* __restrict__ parent, float* __restrict__ box, TreeletSmem& sm, int lane) {
     // 1. the treelet: r and the internal nodes of the next two levels; their
-    //    children below are its leaves, in depth-first order
+    //    children below are its leaves.  Three rounds of loads spread over
+    //    the lanes -- r's children; their children; the children and boxes
+    //    of the level below -- then lane 0 lists leaves and internal nodes
+    //    level by level, in child order.
+    int32_t v = 0;
+    if (lane < 2) v = __ldcg((lane ? right : left) + r);
+    const int32_t a = __shfl_sync(kFull, v, 0), b = __shfl_sync(kFull, v, 1);
+    v = (int32_t)kLeafTag;   // "no internal node here"
+    if (lane < 4) {
+        const int32_t p = (lane >> 1) ? b : a;
+        if (!is_leaf_ref(p)) v = __ldcg((lane & 1 ? right : left) + p);
+        sm.g[lane] = v;
+    }
+    const int32_t gq = __shfl_sync(kFull, v, (lane >> 1) & 3), gb = __shfl_sync(kFull, v, (lane - 8) & 3);
+    if (lane < 8) {
+        sm.y[lane] = is_leaf_ref(gq) ? 0 : __ldcg((lane & 1 ? right : left) + gq);
+    } else if (lane < 12) {
+        float bb[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (!is_leaf_ref(gb)) load_box(box, gb, bb);
+        sm.g_area[lane - 8] = half_area(bb[3] - bb[0], bb[4] - bb[1], bb[5] - bb[2]);
+    }
+    __syncwarp();
     if (lane == 0) {
-        int lv_ref[kTreeletSpan], lv_n = 1, k = 0, ni = 0;
-        lv_ref[0] = r;
-        for (int lv = 0; lv < kTreeletLevels; ++lv) {   // one level of loads at a time
-            if (lv == kTreeletLevels - 1 && k + 2 * lv_n > kTreeletLeaves) {
-                // eight leaves: the last-level node of smallest box stays whole (a leaf itself)
-                int at = 0;
-                float amin = 3.0e38f;
-                for (int i = 0; i < lv_n; ++i) {
-                    float b[6];
-                    load_box(box, lv_ref[i], b);
-                    const float a = half_area(b[3] - b[0], b[4] - b[1], b[5] - b[2]);
-                    if (a < amin) {
-                        amin = a;
-                        at = i;
-                    }
+        int k = 0, ni = 0, n2 = 0;
+        int l2q[4];   // the internal nodes of the third level, as indices into g
+        sm.inner[ni++] = r;
+        if (is_leaf_ref(a)) sm.lref[k++] = a;
+        if (is_leaf_ref(b)) sm.lref[k++] = b;
+        if (!is_leaf_ref(a)) sm.inner[ni++] = a;
+        if (!is_leaf_ref(b)) sm.inner[ni++] = b;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (is_leaf_ref(q < 2 ? a : b)) continue;
+            if (is_leaf_ref(sm.g[q])) sm.lref[k++] = sm.g[q];
+            else l2q[n2++] = q;
+        }
+        if (n2 > 0 && k + 2 * n2 > kTreeletLeaves) {
+            // eight leaves: the third-level node of smallest box stays whole (a leaf itself)
+            int at = 0;
+            float amin = 3.0e38f;
+            for (int i = 0; i < n2; ++i) {
+                const float ai = sm.g_area[l2q[i]];
+                if (ai < amin) {
+                    amin = ai;
+                    at = i;
                 }
-                sm.lref[k++] = lv_ref[at];
-                lv_ref[at] = lv_ref[--lv_n];
             }
-            int kids[kTreeletSpan];
-            int m = 0;
-            for (int i = 0; i < lv_n; ++i) {
-                sm.inner[ni++] = lv_ref[i];
-                kids[m++] = __ldcg(left + lv_ref[i]);
-                kids[m++] = __ldcg(right + lv_ref[i]);
-            }
-            lv_n = 0;
-            for (int i = 0; i < m; ++i) {
-                if (lv + 1 < kTreeletLevels && !((uint32_t)kids[i] & kLeafTag)) lv_ref[lv_n++] = kids[i];
-                else sm.lref[k++] = kids[i];
-            }
+            sm.lref[k++] = sm.g[l2q[at]];
+            l2q[at] = l2q[--n2];
+        }
+        for (int i = 0; i < n2; ++i) {
+            sm.inner[ni++] = sm.g[l2q[i]];
+            sm.lref[k++] = sm.y[2 * l2q[i]];
+            sm.lref[k++] = sm.y[2 * l2q[i] + 1];
         }
         sm.k = k;
         sm.ni = ni;
@@ -160,21 +204,29 @@ __device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_
 #pragma unroll
     for (int o = 16; o; o >>= 1) old += __shfl_xor_sync(kFull, old, o);
     __syncwarp();
-    // 3. the box area of every leaf subset; a single leaf costs nothing
-    for (int S = lane + 1; S <= full; S += 32) {
-        float lo0 = 3.0e38f, lo1 = 3.0e38f, lo2 = 3.0e38f, hi0 = -3.0e38f, hi1 = -3.0e38f, hi2 = -3.0e38f;
+    // 3. the box area of every leaf subset (a single leaf costs nothing):
+    //    the boxes of the subsets of leaves 0-3 (lanes 1-15) and of leaves
+    //    4-6 (lanes 17-23) first; a subset's box is the union of its halves'
+    if (lane >= 1 && lane < 16 && lane <= full) {
+        float bb[6] = {3.0e38f, 3.0e38f, 3.0e38f, -3.0e38f, -3.0e38f, -3.0e38f};
 #pragma unroll
-        for (int i = 0; i < kTreeletLeaves; ++i) {
-            if ((S >> i) & 1) {
-                lo0 = fminf(lo0, sm.lbox[i][0]);
-                lo1 = fminf(lo1, sm.lbox[i][1]);
-                lo2 = fminf(lo2, sm.lbox[i][2]);
-                hi0 = fmaxf(hi0, sm.lbox[i][3]);
-                hi1 = fmaxf(hi1, sm.lbox[i][4]);
-                hi2 = fmaxf(hi2, sm.lbox[i][5]);
-            }
-        }
-        sm.area[S] = half_area(hi0 - lo0, hi1 - lo1, hi2 - lo2);
+        for (int i = 0; i < 4; ++i)
+            if ((lane >> i) & 1) box_union(bb, sm.lbox[i]);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sm.lowbox[lane][c] = bb[c];
+    } else if (lane >= 17 && lane < 24 && ((lane - 16) << 4) <= full) {
+        float bb[6] = {3.0e38f, 3.0e38f, 3.0e38f, -3.0e38f, -3.0e38f, -3.0e38f};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (((lane - 16) >> i) & 1) box_union(bb, sm.lbox[4 + i]);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sm.highbox[lane - 16][c] = bb[c];
+    }
+    __syncwarp();
+    for (int S = lane + 1; S <= full; S += 32) {
+        float bb[6];
+        subset_box(sm, S, bb);
+        sm.area[S] = half_area(bb[3] - bb[0], bb[4] - bb[1], bb[5] - bb[2]);
         sm.cost[S] = 0.0f;
         sm.best[S] = 0;
     }
@@ -275,25 +327,11 @@ __device__ void restructure(int r, int64_t n, int32_t* __restrict__ left, int32_
         parent[slot_of(lr, n)] = id;
         parent[slot_of(rr, n)] = id;
         if (lane > 0) {
-            float lo0 = 3.0e38f, lo1 = 3.0e38f, lo2 = 3.0e38f, hi0 = -3.0e38f, hi1 = -3.0e38f, hi2 = -3.0e38f;
+            float bb[6];
+            subset_box(sm, S, bb);
+            float* bo = box + 6 * (int64_t)id;
 #pragma unroll
-            for (int i = 0; i < kTreeletLeaves; ++i) {
-                if ((S >> i) & 1) {
-                    lo0 = fminf(lo0, sm.lbox[i][0]);
-                    lo1 = fminf(lo1, sm.lbox[i][1]);
-                    lo2 = fminf(lo2, sm.lbox[i][2]);
-                    hi0 = fmaxf(hi0, sm.lbox[i][3]);
-                    hi1 = fmaxf(hi1, sm.lbox[i][4]);
-                    hi2 = fmaxf(hi2, sm.lbox[i][5]);
-                }
-            }
-            float* b = box + 6 * (int64_t)id;
-            b[0] = lo0;
-            b[1] = lo1;
-            b[2] = lo2;
-            b[3] = hi0;
-            b[4] = hi1;
-            b[5] = hi2;
+            for (int c = 0; c < 6; ++c) bo[c] = bb[c];
         }
     }
 }
@@ -328,7 +366,7 @@ __global__ void k_depth(int64_t n, const int32_t* __restrict__ parent, int32_t* 
 }
 
 // The treelets whose roots k_depth listed: each warp takes roots in turn.
-__global__ void __launch_bounds__(32 * kTreeletWarps) k_treelet(int64_t n, int32_t* __restrict__ left,
+__global__ void __launch_bounds__(32 * kTreeletWarps, kTreeletBlocksPerSm) k_treelet(int64_t n, int32_t* __restrict__ left,
                                                                 int32_t* __restrict__ right,
                                                                 int32_t* __restrict__ parent,
                                                                 float* __restrict__ box,
@@ -414,7 +452,7 @@ __global__ void k_roots_seg(const MeshBuild* __restrict__ d, const int64_t* __re
     }
 }
 
-__global__ void __launch_bounds__(32 * kTreeletWarps) k_treelet_seg(const MeshBuild* __restrict__ d,
+__global__ void __launch_bounds__(32 * kTreeletWarps, kTreeletBlocksPerSm) k_treelet_seg(const MeshBuild* __restrict__ d,
                                                                     const int32_t* __restrict__ roots_node,
                                                                     const int32_t* __restrict__ roots_mesh,
                                                                     const int* __restrict__ n_roots) {
@@ -453,6 +491,28 @@ __global__ void k_pack_seg(const MeshBuild* __restrict__ d, const int64_t* __res
     pack_node(b.nt, b.left, b.right, b.box, b.nodes, g - __ldg(int_pre + m));
 }
 
+// Blocks of a treelet launch: one warp per treelet while the resident warps
+// suffice (a third of the internal nodes are roots of one launch, so a launch
+// over fewer warps would run some of them twice in a row), else every
+// resident warp, taking roots in turn.
+int treelet_grid(int64_t n_internal, bool batched) {
+    static int per_sm[2] = {0, 0};
+    int& b = per_sm[batched ? 1 : 0];
+    if (b == 0) {
+        int v = 0;
+        const cudaError_t e =
+            batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_treelet_seg, 32 * kTreeletWarps, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_treelet, 32 * kTreeletWarps, 0);
+        if (e != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 8;
+        }
+        b = v;
+    }
+    const int64_t need = (n_internal + kTreeletWarps - 1) / kTreeletWarps;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * b));
+}
+
 }  // namespace
 
 // Restructuring passes over a finished single build, in stream order without
@@ -468,8 +528,7 @@ int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, int32_t* list, cu
     int* counts = list + n;   // one root count per (pass, offset)
     RSI_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * 3 * kTreeletLevels, s));
     const int nodes_grid = (int)((2 * n - 1 + 255) / 256);
-    const int64_t need = (n + 3 * kTreeletWarps - 1) / (3 * kTreeletWarps);   // about a third of the nodes are roots
-    const int tl_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * 16));
+    const int tl_grid = treelet_grid(n - 1, false);
     int launches = 0;
     for (int p = 0; p < passes; ++p) {
         for (int off = 0; off < kTreeletLevels; ++off) {
@@ -494,8 +553,7 @@ int enqueue_treelets_batched(const MeshBuild* d_mb, const int64_t* d_tri_pre, co
     passes = passes > 3 ? 3 : passes;
     RSI_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * 3 * kTreeletLevels, s));
     const int int_grid = (int)((total_int + 255) / 256);
-    const int64_t need = (total_int + 3 * kTreeletWarps - 1) / (3 * kTreeletWarps);
-    const int tl_grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * 16));
+    const int tl_grid = treelet_grid(total_int, true);
     for (int p = 0; p < passes; ++p) {
         for (int off = 0; off < kTreeletLevels; ++off) {
             int* cnt = counts + p * kTreeletLevels + off;

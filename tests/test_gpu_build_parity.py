@@ -1,6 +1,9 @@
 """GPU build (extent, Morton, sort, radix tree, refit) against the oracle,
-bit for bit, through the C ABI.  Sizes span several sort tiles (4096 keys),
-ragged tails, a single triangle and forced duplicate Morton codes.  Both tree
+bit for bit, through the C ABI.  Sizes span several sort tiles, ragged tails,
+a single triangle and forced duplicate Morton codes, and both sort plans: up
+to 524,288 keys one launch per pass over at most 128 tiles of 256 * R keys
+(sizes on either side of the R steps and of that limit), above it three
+launches per pass over tiles of 4096 keys.  Both tree
 constructions are checked: Karras + refit, and the single bottom-up pass
 (Apetrei; Sec. 4.2), which must give the same hierarchy."""
 import numpy as np
@@ -41,7 +44,7 @@ def _soup(n, seed, dup_frac=0.0):
 def _meshes():
     g = load("case_study1_sec4_1.txt")
     yield "case_study1", g["vertices"], g["triangles"]
-    for n in (1, 2, 3, 1023, 1024, 1025, 4097, 9000):
+    for n in (1, 2, 3, 255, 256, 257, 1023, 1024, 1025, 4097, 9000, 32768, 32769, 65537, 524288, 524289):
         V, T = _soup(n, seed=n)
         yield f"soup{n}", V, T
     V, T = _soup(5000, seed=3, dup_frac=0.3)
