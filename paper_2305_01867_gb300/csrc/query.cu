@@ -649,6 +649,95 @@ struct PairScratch {
 
 namespace {
 
+// classify_fp64 evaluated by a whole warp on one pair (every lane passes the
+// same pair and gets the same answer): the same FP64 operations, spread over
+// the lanes.  On GB300 a warp's FP64 instruction occupies the FP64 pipe the
+// same for 1 or 32 active lanes, so one pair's definition costs the warp
+// about as much as 32 pairs' would; here the three norms, the three
+// quotients and the distance terms run side by side.  The distance from the
+// segment to the triangle is the smallest of: the distance of an end point
+// to the triangle's plane where its projection falls inside the triangle,
+// the nine point-to-segment distances between the end points and the edges
+// and between the vertices and the segment, and the interior closest
+// approaches of the segment and each edge -- the same set of terms whose
+// minimum classify_fp64 takes (its point-to-triangle terms use the same
+// point-to-edge distances), and a minimum does not depend on order.
+__device__ int classify_fp64_warp(D3 s, D3 e, D3 a, D3 b, D3 c, double& t_out, bool& incl) {
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const double tau = kTauD;
+    const D3 d = dsub(e, s);
+    const D3 e1 = dsub(b, a), e2 = dsub(c, a);
+    const D3 n = dcross(e1, e2);
+    incl = false;
+    t_out = 0.0;
+    if ((d.x == 0.0 && d.y == 0.0 && d.z == 0.0) || (n.x == 0.0 && n.y == 0.0 && n.z == 0.0)) return kMiss;
+    const D3 p = dcross(d, e2);
+    const double det = ddot(e1, p);
+    const D3 sv = dsub(s, a);
+    const D3 q = dcross(sv, e1);
+    // lanes 0-2: |d|, |e1|, |e2|; lanes 3-5: u, v, t
+    const D3 nv = lane == 0 ? d : (lane == 1 ? e1 : e2);
+    const double nrm = lane < 3 ? dnorm(nv) : 0.0;
+    const D3 qa = lane == 3 ? sv : (lane == 4 ? d : e2);
+    const D3 qb = lane == 3 ? p : q;
+    const double quo = (lane >= 3 && lane < 6 && det != 0.0) ? __ddiv_rn(ddot(qa, qb), det) : 0.0;
+    const double nd = __shfl_sync(kFull, nrm, 0), n1 = __shfl_sync(kFull, nrm, 1), n2 = __shfl_sync(kFull, nrm, 2);
+    const double det_rel = __ddiv_rn(det, __dmul_rn(__dmul_rn(nd, n1), n2));
+    double u = 0.0, v = 0.0, t = 0.0, w = 0.0;
+    if (det != 0.0) {
+        u = __shfl_sync(kFull, quo, 3);
+        v = __shfl_sync(kFull, quo, 4);
+        t = __shfl_sync(kFull, quo, 5);
+        w = __dsub_rn(__dsub_rn(1.0, u), v);
+        incl = (u >= 0.0 && v >= 0.0 && w >= 0.0 && t >= 0.0 && t <= 1.0);
+    }
+    t_out = t;
+    if (fabs(det_rel) > tau) {
+        if (u > tau && v > tau && w > tau && t > tau && t < 1.0 - tau) return kHit;
+        if (u < -tau || v < -tau || w < -tau || t < -tau || t > 1.0 + tau) return kMiss;
+        return kBand;   // ambiguous
+    }
+    if (incl) return kBand;   // distance 0, never above tau |d|
+    // the distance terms: lanes 0-8 point to segment, 9-11 interior approaches, 12-13 planes
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    double dist = inf;
+    if (lane < 9) {   // lanes 0-5: end point lane / 3 to edge lane % 3; 6-8: vertex lane - 6 to the segment
+        const int ei = lane < 6 ? lane % 3 : lane - 6;
+        const D3 v0 = ei == 0 ? a : (ei == 1 ? b : c), v1 = ei == 0 ? b : (ei == 1 ? c : a);
+        const D3 pt = lane < 6 ? (lane < 3 ? s : e) : v0;
+        dist = pt_seg(pt, lane < 6 ? v0 : s, lane < 6 ? v1 : e);
+    } else if (lane < 12) {
+        const int ei = lane - 9;
+        const D3 q0 = ei == 0 ? a : (ei == 1 ? b : c), q1 = ei == 0 ? b : (ei == 1 ? c : a);
+        const D3 uu = dsub(e, s), vv = dsub(q1, q0), w0 = dsub(s, q0);
+        const double aa = ddot(uu, uu), bb = ddot(uu, vv), cc = ddot(vv, vv);
+        const double dd = ddot(uu, w0), ee = ddot(vv, w0);
+        const double den = __dsub_rn(__dmul_rn(aa, cc), __dmul_rn(bb, bb));
+        if (den > 0.0) {
+            const double ss = __ddiv_rn(__dsub_rn(__dmul_rn(bb, ee), __dmul_rn(cc, dd)), den);
+            const double tt = __ddiv_rn(__dsub_rn(__dmul_rn(aa, ee), __dmul_rn(bb, dd)), den);
+            if (ss >= 0.0 && ss <= 1.0 && tt >= 0.0 && tt <= 1.0) dist = dnorm(dsub(dadd(w0, dscale(uu, ss)), dscale(vv, tt)));
+        }
+    } else if (lane < 14) {
+        const D3 pp = lane == 12 ? s : e;
+        const D3 nn3 = dcross(dsub(b, a), dsub(c, a));
+        const double nn = ddot(nn3, nn3);
+        const double h = __ddiv_rn(ddot(dsub(pp, a), nn3), nn);
+        const D3 proj = dsub(pp, dscale(nn3, h));
+        const double s0 = ddot(dcross(dsub(b, a), dsub(proj, a)), nn3);
+        const double s1 = ddot(dcross(dsub(c, b), dsub(proj, b)), nn3);
+        const double s2 = ddot(dcross(dsub(a, c), dsub(proj, c)), nn3);
+        if (s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0) dist = __dmul_rn(fabs(h), __dsqrt_rn(nn));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const double x = __shfl_xor_sync(kFull, dist, o);
+        dist = x < dist ? x : dist;
+    }
+    return dist > __dmul_rn(tau, nd) ? kMiss : kBand;
+}
+
 // Ambiguity byte of a count-mode result.  In RSI_BOTH the count pass also
 // answers the boolean mode: its hit flag (count > 0) is the boolean answer,
 // and a segment is ambiguous for the boolean mode when it is for the count
@@ -1218,12 +1307,11 @@ __global__ void __launch_bounds__(128) k_band_collect_threads(QueryArgs A, Batch
 
 // Step 2a: the certain FP64 test of every listed pair (no division or square
 // root unless the nearest mode needs the t of a certain hit; the count mode
-// computes it in step 3 where needed).  In a long list the pairs this test
-// leaves undecided are listed for step 2b, so that the long evaluation of the
-// definition runs in warps made of undecided pairs only; in a short one
-// (fewer than kHardSplit pairs, where the pass is latency-bound) they are
-// settled here.
-constexpr int kHardSplit = 1 << 17;
+// computes it in step 3 where needed).  The pairs this test leaves undecided
+// are listed for step 2b, so that the long evaluation of the definition runs
+// apart: a few of them one warp each (k_band_classify_hard_warp, whose lanes
+// share the work of one pair), many of them one thread each.
+constexpr int kHardWarpMax = 2048;   // undecided pairs up to which each gets a warp
 template <int MODE, bool BATCHED>
 __global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B, PairScratch P) {
     const unsigned kFull = 0xffffffffu;
@@ -1246,11 +1334,8 @@ __global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B,
                 double t = 0.0;
                 bool incl = cls == kHit;
                 if (cls == kHit && MODE == RSI_NEAREST) t = t_of_definition(sd, ed, a, b, c);
-                if (cls == kBand) {
-                    if (np >= kHardSplit) hard = true;
-                    else cls = classify_fp64(sd, ed, a, b, c, t, incl);
-                }
-                const bool pending = cls == kHit && MODE == RSI_COUNT;   // t of a certain hit: step 3, if needed
+                hard = cls == kBand;   // settled by the definition in step 2b
+                const bool pending = incl && MODE == RSI_COUNT;   // t of a certain hit: step 3, if needed
                 P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0) | (pending ? kTPending : 0));
                 P.pair_t[i] = t;
             }
@@ -1265,10 +1350,12 @@ __global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B,
     }
 }
 
-// Step 2b: the definition itself (classify_fp64) for the undecided pairs.
+// Step 2b: the definition itself (classify_fp64) for the undecided pairs:
+// one thread per pair for long lists, one warp per pair for short ones.
 template <bool BATCHED>
 __global__ void __launch_bounds__(256) k_band_classify_hard(QueryArgs A, BatchArgs B, PairScratch P) {
     const int nh = *(volatile int*)&A.ctr->hard_count;
+    if (nh < kHardWarpMax) return;   // k_band_classify_hard_warp takes short lists
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += gridDim.x * blockDim.x) {
         const int i = P.hard[h];
         int64_t r;
@@ -1284,63 +1371,116 @@ __global__ void __launch_bounds__(256) k_band_classify_hard(QueryArgs A, BatchAr
     }
 }
 
+template <bool BATCHED>
+__global__ void __launch_bounds__(128) k_band_classify_hard_warp(QueryArgs A, BatchArgs B, PairScratch P) {
+    const int nh = *(volatile int*)&A.ctr->hard_count;
+    if (nh >= kHardWarpMax) return;   // k_band_classify_hard takes long lists
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int h = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < nh; h += warps) {
+        const int i = P.hard[h];
+        int64_t r;
+        const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[P.pair_seg[i]], r);
+        const D3 sd = {(double)Q.from[3 * r], (double)Q.from[3 * r + 1], (double)Q.from[3 * r + 2]};
+        const D3 ed = {(double)Q.to[3 * r], (double)Q.to[3 * r + 1], (double)Q.to[3 * r + 2]};
+        const Tri tr = load_tri(Q.tris, P.pair_leaf[i]);
+        double t = 0.0;
+        bool incl = false;
+        const int cls = classify_fp64_warp(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2), t, incl);
+        if (lane == 0) {
+            P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0));
+            P.pair_t[i] = t;
+        }
+    }
+}
+
+// Step 3, one thread per queued segment; in the count mode an ambiguous
+// segment (its distinct crossings need every crossing's t) is finished by the
+// whole warp, one lane per pair, since a certain hit's t is computed here.
 template <int MODE, bool BATCHED>
 __global__ void __launch_bounds__(128) k_band_reduce(QueryArgs A, BatchArgs B, PairScratch P) {
+    __shared__ double s_ts[4][kCandMax];   // count mode: the t of an ambiguous segment's crossings
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int nb = min(*(volatile int*)&A.ctr->band_count, P.seg_cap);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
-        const int cnt = P.seg_cnt[k];
-        if (cnt < 0) continue;
-        const int off = P.seg_off[k];
-        int64_t r;
-        const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
-        int n_hit = 0, n_amb = 0, n_incl = 0;
-        double ts[kCandMax];
-        double best_t = __longlong_as_double(0x7ff0000000000000ll);
-        int best_id = 0x7FFFFFFF, best_leaf = -1;
-        for (int j = 0; j < cnt; ++j) {
-            const int c = P.pair_cls[off + j];
-            n_hit += (c & 3) == kHit;
-            n_amb += (c & 3) == kBand;
-            if (c & 4) {
-                if (MODE == RSI_NEAREST) {
-                    const double t = P.pair_t[off + j];
-                    const int leaf = P.pair_leaf[off + j];
-                    const int id = __float_as_int(Q.tris[leaf].v0.w);
-                    if (t < best_t || (t == best_t && id < best_id)) {
-                        best_t = t;
-                        best_id = id;
-                        best_leaf = leaf;
+    const int stride = gridDim.x * blockDim.x;
+    for (int k0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < nb; k0 += stride) {   // warp-uniform
+        const int k = k0 + lane;
+        const int cnt = k < nb ? P.seg_cnt[k] : -1;
+        bool amb_count = false;   // an ambiguous count-mode segment, finished below
+        if (cnt >= 0) {
+            const int off = P.seg_off[k];
+            int64_t r;
+            const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
+            int n_hit = 0, n_amb = 0, n_incl = 0;
+            double best_t = __longlong_as_double(0x7ff0000000000000ll);
+            int best_id = 0x7FFFFFFF, best_leaf = -1;
+            for (int j = 0; j < cnt; ++j) {
+                const int c = P.pair_cls[off + j];
+                n_hit += (c & 3) == kHit;
+                n_amb += (c & 3) == kBand;
+                if (c & 4) {
+                    if (MODE == RSI_NEAREST) {
+                        const double t = P.pair_t[off + j];
+                        const int leaf = P.pair_leaf[off + j];
+                        const int id = __float_as_int(Q.tris[leaf].v0.w);
+                        if (t < best_t || (t == best_t && id < best_id)) {
+                            best_t = t;
+                            best_id = id;
+                            best_leaf = leaf;
+                        }
                     }
+                    ++n_incl;
                 }
-                ++n_incl;
+            }
+            if (MODE == RSI_ANY_HIT) {
+                const bool amb = n_hit == 0 && n_amb > 0;
+                Q.hit[r] = (uint8_t)(n_hit > 0 || (amb && n_incl > 0));
+                if (Q.amb) Q.amb[r] = (uint8_t)amb;
+                if (amb) atomicAdd(&A.ctr->ambiguous, 1ull);
+            } else if (MODE == RSI_NEAREST) {
+                Q.near[r] = best_leaf;
+                if (Q.amb) Q.amb[r] = (uint8_t)(n_amb > 0);
+                if (n_amb > 0) atomicAdd(&A.ctr->ambiguous, 1ull);
+            } else if (n_amb > 0) {
+                amb_count = true;
+            } else {
+                Q.count[r] = n_hit;
+                if (Q.hit) Q.hit[r] = (uint8_t)(n_hit > 0);
+                if (Q.amb) Q.amb[r] = both_modes_amb(A.amb_bits, false, n_hit);
             }
         }
-        if (MODE == RSI_ANY_HIT) {
-            const bool amb = n_hit == 0 && n_amb > 0;
-            Q.hit[r] = (uint8_t)(n_hit > 0 || (amb && n_incl > 0));
-            if (Q.amb) Q.amb[r] = (uint8_t)amb;
-            if (amb) atomicAdd(&A.ctr->ambiguous, 1ull);
-        } else if (MODE == RSI_NEAREST) {
-            Q.near[r] = best_leaf;
-            if (Q.amb) Q.amb[r] = (uint8_t)(n_amb > 0);
-            if (n_amb > 0) atomicAdd(&A.ctr->ambiguous, 1ull);
-        } else {
-            const bool amb = n_amb > 0;
-            int count = n_hit;
-            if (amb) {   // distinct crossings of the closed-interval reading
-                const D3 sd = {(double)Q.from[3 * r], (double)Q.from[3 * r + 1], (double)Q.from[3 * r + 2]};
-                const D3 ed = {(double)Q.to[3 * r], (double)Q.to[3 * r + 1], (double)Q.to[3 * r + 2]};
-                int m = 0;
-                for (int j = 0; j < cnt; ++j) {   // t of every inclusive crossing (a certain hit's computed here)
-                    const int c = P.pair_cls[off + j];
-                    if (!(c & 4)) continue;
-                    double t = P.pair_t[off + j];
-                    if (c & kTPending) {
-                        const Tri tr = load_tri(Q.tris, P.pair_leaf[off + j]);
+        if (MODE != RSI_COUNT) continue;
+        // distinct crossings of the closed-interval reading, one ambiguous segment at a time
+        unsigned m = __ballot_sync(kFull, amb_count);
+        while (m) {
+            const int kk = k0 + __ffs(m) - 1;
+            m &= m - 1;
+            const int cc = P.seg_cnt[kk], oo = P.seg_off[kk];
+            int64_t rr;
+            const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[kk], rr);
+            int c = 0;
+            double t = 0.0;
+            if (lane < cc) {
+                c = P.pair_cls[oo + lane];
+                if (c & 4) {
+                    t = P.pair_t[oo + lane];
+                    if (c & kTPending) {   // a certain hit's t, by the definition's operations
+                        const D3 sd = {(double)Q.from[3 * rr], (double)Q.from[3 * rr + 1], (double)Q.from[3 * rr + 2]};
+                        const D3 ed = {(double)Q.to[3 * rr], (double)Q.to[3 * rr + 1], (double)Q.to[3 * rr + 2]};
+                        const Tri tr = load_tri(Q.tris, P.pair_leaf[oo + lane]);
                         t = t_of_definition(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2));
                     }
-                    ts[m++] = t;
                 }
+            }
+            const unsigned im = __ballot_sync(kFull, (c & 4) != 0);
+            const unsigned hm = __ballot_sync(kFull, lane < cc && (c & 3) == kHit);
+            if (c & 4) s_ts[w][__popc(im & lt)] = t;
+            __syncwarp();
+            if (lane == 0) {
+                double* ts = s_ts[w];
+                const int n_incl = __popc(im);
                 for (int i = 1; i < n_incl; ++i) {
                     const double x = ts[i];
                     int k2 = i - 1;
@@ -1350,14 +1490,15 @@ __global__ void __launch_bounds__(128) k_band_reduce(QueryArgs A, BatchArgs B, P
                     }
                     ts[k2 + 1] = x;
                 }
-                count = 0;
+                int count = 0;
                 for (int i = 0; i < n_incl; ++i)
                     if (i == 0 || __dsub_rn(ts[i], ts[i - 1]) > kTMerge) ++count;
                 atomicAdd(&A.ctr->ambiguous, 1ull);
+                Q.count[rr] = count;
+                if (Q.hit) Q.hit[rr] = (uint8_t)(count > 0);
+                if (Q.amb) Q.amb[rr] = both_modes_amb(A.amb_bits, true, __popc(hm));
             }
-            Q.count[r] = count;
-            if (Q.hit) Q.hit[r] = (uint8_t)(count > 0);
-            if (Q.amb) Q.amb[r] = both_modes_amb(A.amb_bits, amb, n_hit);
+            __syncwarp();
         }
     }
 }
@@ -1978,7 +2119,7 @@ void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P0, cud
         return;
     }
     PairScratch Pm = *P0;
-    Pm.min_queue = MODE == RSI_ANY_HIT ? 2048 : 0;
+    Pm.min_queue = 0;
     Pm.fp32_hits = MODE != RSI_NEAREST;   // the nearest mode needs every hit's t
     const PairScratch* P = &Pm;
     // step 1: both collect kernels are launched; the queue length (on the
@@ -1990,8 +2131,9 @@ void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P0, cud
     else k_band_collect_threads<128, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
     k_band_classify<MODE, BATCHED><<<device_sm_count() * 8, 256, 0, s>>>(A, B, *P);
     k_band_classify_hard<BATCHED><<<device_sm_count() * 4, 256, 0, s>>>(A, B, *P);
+    k_band_classify_hard_warp<BATCHED><<<device_sm_count() * 4, 128, 0, s>>>(A, B, *P);
     k_band_reduce<MODE, BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
-    note_launches(5);
+    note_launches(6);
     QueryArgs F = A;
     F.band_ids = P->fb_ids;
     launch_fp64<MODE, BATCHED>(F, height, grid, s, &A.ctr->fb_count, B);
