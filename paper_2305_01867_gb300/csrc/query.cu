@@ -989,7 +989,8 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B, co
 // that keep the lanes busy: (1) the pairs of each queued segment are listed
 // -- for queues of up to 32,767 segments by one warp per segment whose lanes
 // walk the boxes together (every round each lane takes one node of the
-// warp's node list), for longer queues by one thread per segment -- with the
+// warp's node list), for longer queues (whose walks are long and many) by
+// one thread per segment -- with the
 // FP32 test on each reached leaf: a certain miss is dropped; with
 // P.fp32_hits (boolean and count modes) a certain FP32 hit is entered as a
 // hit at once, the FP32 test being sound, and only the undecided pairs are
@@ -997,8 +998,10 @@ __global__ void __launch_bounds__(128) k_query_fp64(QueryArgs A, BatchArgs B, co
 // the certain numerator test, else the definition -- so FP64 instructions
 // run with full warps (a warp's FP64 instruction costs the same however many
 // lanes take part); (3) one thread per segment combines its pairs exactly as
-// k_query_fp64 does, computing the t of a hit only where the count mode
-// needs it (an ambiguous segment's distinct crossings).  Segments with more
+// k_query_fp64 does; the count mode's ambiguous segments (whose distinct
+// crossings need every crossing's t) are listed with the certain hits whose
+// t is still to compute, one thread per such pair computes it, and one
+// thread per listed segment counts the crossings.  Segments with more
 // than kCandMax candidates, or that do not fit the scratch, go to
 // k_query_fp64 through the fallback list.
 constexpr int kCandMax = 32;
@@ -1394,15 +1397,14 @@ __global__ void __launch_bounds__(128) k_band_classify_hard_warp(QueryArgs A, Ba
     }
 }
 
-// Step 3, one thread per queued segment; in the count mode an ambiguous
-// segment (its distinct crossings need every crossing's t) is finished by the
-// whole warp, one lane per pair, since a certain hit's t is computed here.
+// Step 3, one thread per queued segment.  In the count mode an ambiguous
+// segment (its distinct crossings need every crossing's t) is listed, and
+// so are its certain hits whose t is not computed yet; k_band_tfix and
+// k_band_crossings finish it.
 template <int MODE, bool BATCHED>
 __global__ void __launch_bounds__(128) k_band_reduce(QueryArgs A, BatchArgs B, PairScratch P) {
-    __shared__ double s_ts[4][kCandMax];   // count mode: the t of an ambiguous segment's crossings
     const unsigned kFull = 0xffffffffu;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
+    const int lane = threadIdx.x & 31;
     const int nb = min(*(volatile int*)&A.ctr->band_count, P.seg_cap);
     const int stride = gridDim.x * blockDim.x;
     for (int k0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < nb; k0 += stride) {   // warp-uniform
@@ -1452,54 +1454,79 @@ __global__ void __launch_bounds__(128) k_band_reduce(QueryArgs A, BatchArgs B, P
             }
         }
         if (MODE != RSI_COUNT) continue;
-        // distinct crossings of the closed-interval reading, one ambiguous segment at a time
-        unsigned m = __ballot_sync(kFull, amb_count);
-        while (m) {
-            const int kk = k0 + __ffs(m) - 1;
-            m &= m - 1;
-            const int cc = P.seg_cnt[kk], oo = P.seg_off[kk];
-            int64_t rr;
-            const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[kk], rr);
-            int c = 0;
-            double t = 0.0;
-            if (lane < cc) {
-                c = P.pair_cls[oo + lane];
-                if (c & 4) {
-                    t = P.pair_t[oo + lane];
-                    if (c & kTPending) {   // a certain hit's t, by the definition's operations
-                        const D3 sd = {(double)Q.from[3 * rr], (double)Q.from[3 * rr + 1], (double)Q.from[3 * rr + 2]};
-                        const D3 ed = {(double)Q.to[3 * rr], (double)Q.to[3 * rr + 1], (double)Q.to[3 * rr + 2]};
-                        const Tri tr = load_tri(Q.tris, P.pair_leaf[oo + lane]);
-                        t = t_of_definition(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2));
-                    }
-                }
-            }
-            const unsigned im = __ballot_sync(kFull, (c & 4) != 0);
-            const unsigned hm = __ballot_sync(kFull, lane < cc && (c & 3) == kHit);
-            if (c & 4) s_ts[w][__popc(im & lt)] = t;
-            __syncwarp();
-            if (lane == 0) {
-                double* ts = s_ts[w];
-                const int n_incl = __popc(im);
-                for (int i = 1; i < n_incl; ++i) {
-                    const double x = ts[i];
-                    int k2 = i - 1;
-                    while (k2 >= 0 && ts[k2] > x) {
-                        ts[k2 + 1] = ts[k2];
-                        --k2;
-                    }
-                    ts[k2 + 1] = x;
-                }
-                int count = 0;
-                for (int i = 0; i < n_incl; ++i)
-                    if (i == 0 || __dsub_rn(ts[i], ts[i - 1]) > kTMerge) ++count;
-                atomicAdd(&A.ctr->ambiguous, 1ull);
-                Q.count[rr] = count;
-                if (Q.hit) Q.hit[rr] = (uint8_t)(count > 0);
-                if (Q.amb) Q.amb[rr] = both_modes_amb(A.amb_bits, true, __popc(hm));
-            }
-            __syncwarp();
+        // the ambiguous segments and their pending t's, one reservation per warp each
+        int npend = 0;
+        if (amb_count)
+            for (int j = 0; j < cnt; ++j) npend += (P.pair_cls[P.seg_off[k] + j] & kTPending) ? 1 : 0;
+        int incl = npend;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
         }
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (total > 0) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&A.ctr->tpend_count, total);
+            base = __shfl_sync(kFull, base, 0) + incl - npend;
+            if (npend > 0) {
+                const int off = P.seg_off[k];
+                for (int j = 0; j < cnt; ++j)
+                    if (P.pair_cls[off + j] & kTPending) P.hard[base++] = off + j;
+            }
+        }
+        warp_append(amb_count, k, P.todo, &A.ctr->amb_seg_count);
+    }
+}
+
+// The t of the listed certain hits, one thread each, by the definition's operations.
+template <bool BATCHED>
+__global__ void __launch_bounds__(128) k_band_tfix(QueryArgs A, BatchArgs B, PairScratch P) {
+    const int np = *(volatile int*)&A.ctr->tpend_count;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
+        const int i = P.hard[j];
+        int64_t r;
+        const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[P.pair_seg[i]], r);
+        const D3 sd = {(double)Q.from[3 * r], (double)Q.from[3 * r + 1], (double)Q.from[3 * r + 2]};
+        const D3 ed = {(double)Q.to[3 * r], (double)Q.to[3 * r + 1], (double)Q.to[3 * r + 2]};
+        const Tri tr = load_tri(Q.tris, P.pair_leaf[i]);
+        P.pair_t[i] = t_of_definition(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2));
+    }
+}
+
+// The distinct crossings of each listed ambiguous segment (closed-interval
+// reading: inclusive crossings whose t differ by more than 1e-9 count apart).
+template <bool BATCHED>
+__global__ void __launch_bounds__(128) k_band_crossings(QueryArgs A, BatchArgs B, PairScratch P) {
+    const int na = *(volatile int*)&A.ctr->amb_seg_count;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < na; j += gridDim.x * blockDim.x) {
+        const int k = P.todo[j];
+        const int cnt = P.seg_cnt[k], off = P.seg_off[k];
+        int64_t r;
+        const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
+        double ts[kCandMax];
+        int n_incl = 0, n_hit = 0;
+        for (int i = 0; i < cnt; ++i) {
+            const int c = P.pair_cls[off + i];
+            n_hit += (c & 3) == kHit;
+            if (c & 4) ts[n_incl++] = P.pair_t[off + i];
+        }
+        for (int i = 1; i < n_incl; ++i) {
+            const double x = ts[i];
+            int k2 = i - 1;
+            while (k2 >= 0 && ts[k2] > x) {
+                ts[k2 + 1] = ts[k2];
+                --k2;
+            }
+            ts[k2 + 1] = x;
+        }
+        int count = 0;
+        for (int i = 0; i < n_incl; ++i)
+            if (i == 0 || __dsub_rn(ts[i], ts[i - 1]) > kTMerge) ++count;
+        atomicAdd(&A.ctr->ambiguous, 1ull);
+        Q.count[r] = count;
+        if (Q.hit) Q.hit[r] = (uint8_t)(count > 0);
+        if (Q.amb) Q.amb[r] = both_modes_amb(A.amb_bits, true, n_hit);
     }
 }
 
@@ -2053,6 +2080,8 @@ __global__ void k_reset_query(DevCounters* c, unsigned long long ready) {
     c->fb_count = 0;
     c->hard_count = 0;
     c->todo_count = 0;
+    c->amb_seg_count = 0;
+    c->tpend_count = 0;
     c->n_finish = 0;
     c->n_finish64 = 0;
     if (ready != ~0ull) c->ready = ready;   // ~0: a streaming plan, fed by posts
@@ -2134,6 +2163,11 @@ void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P0, cud
     k_band_classify_hard_warp<BATCHED><<<device_sm_count() * 4, 128, 0, s>>>(A, B, *P);
     k_band_reduce<MODE, BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
     note_launches(6);
+    if (MODE == RSI_COUNT) {   // the ambiguous segments' crossings
+        k_band_tfix<BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
+        k_band_crossings<BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
+        note_launches(2);
+    }
     QueryArgs F = A;
     F.band_ids = P->fb_ids;
     launch_fp64<MODE, BATCHED>(F, height, grid, s, &A.ctr->fb_count, B);

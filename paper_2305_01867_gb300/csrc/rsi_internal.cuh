@@ -74,7 +74,7 @@ struct DevCounters {
     int error;          // first RSI_ERR_* raised by a kernel (0 = none)
     int band_count;     // rays queued for the FP64 re-test
     int height;         // tree height (written by the refit)
-    int pad0;
+    int amb_seg_count;  // FP64 pass, count mode: ambiguous segments listed for the crossing count
     unsigned long long node_visits, tri_tests, ambiguous;
     unsigned long long next_ray;   // work counter of the persistent traversal
     unsigned long long ready;      // segments available to the work queue
@@ -82,7 +82,7 @@ struct DevCounters {
     int n_confirmed;               // learned query: hits confirmed by the proposal
     unsigned int ext_bits[6];   // extent as order-preserving uint (min xyz, max xyz)
     unsigned int dmax_bits[3];  // largest triangle box side per axis (float bits)
-    unsigned int pad1;
+    int tpend_count;            // FP64 pass, count mode: certain hits of those whose t is computed
     int pair_count;             // FP64 pass: (segment, triangle) pairs listed
     int fb_count;               // FP64 pass: segments left to the warp-per-segment kernel
     int hard_count;             // FP64 pass: pairs the certain FP64 test left undecided

@@ -47,7 +47,7 @@ constexpr int kTreeletLevels = 3;          // levels of internal nodes in a tree
 constexpr int kTreeletLeaves = 7;          // a treelet's leaves (of 8 the smallest pair stays joined)
 constexpr int kFullSet = (1 << kTreeletLeaves) - 1;
 constexpr int kTreeletWarps = 4;           // warps per block of k_treelet
-constexpr int kTreeletBlocksPerSm = 12;    // register budget: 48 warps per SM, a warp per root of a c2-sized launch
+constexpr int kTreeletBlocksPerSm = 12;    // register budget: 12 resident blocks (48 warps) per SM
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClimbMax = 1 << 16;         // climb steps before a pass gives up (RSI_ERR_STACK)
 
@@ -491,26 +491,11 @@ __global__ void k_pack_seg(const MeshBuild* __restrict__ d, const int64_t* __res
     pack_node(b.nt, b.left, b.right, b.box, b.nodes, g - __ldg(int_pre + m));
 }
 
-// Blocks of a treelet launch: one warp per treelet while the resident warps
-// suffice (a third of the internal nodes are roots of one launch, so a launch
-// over fewer warps would run some of them twice in a row), else every
-// resident warp, taking roots in turn.
-int treelet_grid(int64_t n_internal, bool batched) {
-    static int per_sm[2] = {0, 0};
-    int& b = per_sm[batched ? 1 : 0];
-    if (b == 0) {
-        int v = 0;
-        const cudaError_t e =
-            batched ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_treelet_seg, 32 * kTreeletWarps, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_treelet, 32 * kTreeletWarps, 0);
-        if (e != cudaSuccess || v < 1) {
-            cudaGetLastError();
-            v = 8;
-        }
-        b = v;
-    }
-    const int64_t need = (n_internal + kTreeletWarps - 1) / kTreeletWarps;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * b));
+// Blocks of a treelet launch: a warp for every internal node that could be a
+// root (about a third are), so that no warp takes two treelets in a row;
+// blocks past the root count return at once.
+int treelet_grid(int64_t n_internal) {
+    return (int)std::max<int64_t>(1, (n_internal + kTreeletWarps - 1) / kTreeletWarps);
 }
 
 }  // namespace
@@ -528,7 +513,7 @@ int enqueue_treelets(rsi_bvh_s* h, int passes, int32_t* depth, int32_t* list, cu
     int* counts = list + n;   // one root count per (pass, offset)
     RSI_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * 3 * kTreeletLevels, s));
     const int nodes_grid = (int)((2 * n - 1 + 255) / 256);
-    const int tl_grid = treelet_grid(n - 1, false);
+    const int tl_grid = treelet_grid(n - 1);
     int launches = 0;
     for (int p = 0; p < passes; ++p) {
         for (int off = 0; off < kTreeletLevels; ++off) {
@@ -553,7 +538,7 @@ int enqueue_treelets_batched(const MeshBuild* d_mb, const int64_t* d_tri_pre, co
     passes = passes > 3 ? 3 : passes;
     RSI_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * 3 * kTreeletLevels, s));
     const int int_grid = (int)((total_int + 255) / 256);
-    const int tl_grid = treelet_grid(total_int, true);
+    const int tl_grid = treelet_grid(total_int);
     for (int p = 0; p < passes; ++p) {
         for (int off = 0; off < kTreeletLevels; ++off) {
             int* cnt = counts + p * kTreeletLevels + off;

@@ -436,20 +436,24 @@ def test_host_path_whole_batch_above_2_26(rsi):
     assert int(d["hit"].sum()) > n // 10
 
 
-@pytest.mark.parametrize("cfg,n", [("c2", 10_000_000), ("c3", 2_000_000)])
+@pytest.mark.parametrize("cfg,n", [("c2", 10_000_000), ("c3", 2_000_000), ("c3", 4_000_000)])
 def test_fp32_decisions_equal_fp64_everywhere(rsi, cfg, n):
-    """Every segment of a full-size batch (c2: all 1e7; c3: a 2e6 slice with
-    1 % grazing segments) answered twice: by the default path (FP32 with
-    certified decisions, FP64 for the band) and with every segment settled by
-    the FP64 re-test. All outputs of all three modes must be identical -- the
-    claim that a certain FP32 decision is the FP64 decision, checked on every
+    """Every segment of a full-size batch (c2: all 1e7; c3: 2e6 and 4e6
+    slices with 1 % grazing segments -- the larger one queues over 32,768
+    segments in the count mode, so the default path takes the long-queue
+    collect) answered twice: by the default path (FP32 with certified
+    decisions, FP64 for the band) and with every segment settled by the FP64
+    re-test. All outputs of all three modes must be identical -- the claim
+    that a certain FP32 decision is the FP64 decision, checked on every
     segment rather than on an oracle sample."""
     mesh = W.config_mesh(cfg)
     F, E = W.rays(W.config_rays(cfg), mesh, count=n)
     bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles), morton_bits=63 if cfg == "c3" else 30)
     dF, dE = _dev(F), _dev(E)
     for mode, key in (("any_hit", "hit"), ("count", "count")):
-        a = bvh.query(dF, dE, mode)
+        a = bvh.query(dF, dE, mode, stats=True)
+        if cfg == "c3" and n > 3_000_000 and mode == "count":
+            assert a["stats"]["band_rays"] >= 32768   # the long-queue collect ran
         b = bvh.query(dF, dE, mode, fp64_all=True, stats=True)
         assert b["stats"]["band_rays"] == n
         assert torch.equal(a[key], b[key]), mode
