@@ -54,6 +54,9 @@ struct QueryArgs {
     float dmax0, dmax1, dmax2;
     int fp32_only;
     int amb_bits;          // RSI_BOTH (count pass): amb = boolean-mode flag | count-mode flag << 1
+    unsigned int* done;    // host-buffer queries (the DONE traversal): finished segments per output
+                           // chunk of 2^done_shift, in device memory the host polls with copies
+    int done_shift;
 };
 
 // One (hierarchy, segment batch, outputs) triple of a batched query.
@@ -200,6 +203,49 @@ __device__ int classify_fp64(D3 s, D3 e, D3 a, D3 b, D3 c, double& t_out, bool& 
     return dist > __dmul_rn(tau, dnorm(d)) ? kMiss : kBand;
 }
 
+// Host-buffer queries: finished segments are counted per output chunk into
+// device counters that the host polls (by copying them out) to copy out the
+// chunks already answered.  A lane notes its finished segments in two
+// (chunk, count) slots; the warp adds them up per chunk and posts them
+// together, once a slot of some lane holds 64 or the second slot is in use,
+// and at the end: a warp barrier, then one fence by the posting lane (which
+// makes the warp's result writes visible at GPU scope, where the copy engine
+// reads them, before the count) and one atomic per chunk.
+struct DoneSlots {
+    int c0 = -1, c1 = -1;
+    unsigned n0 = 0, n1 = 0;
+};
+__device__ __forceinline__ void done_note(const QueryArgs& A, int64_t r, DoneSlots& d) {
+    const int k = (int)(r >> A.done_shift);
+    if (d.n0 == 0 || k == d.c0) {
+        d.c0 = k;
+        ++d.n0;
+    } else if (d.n1 == 0 || k == d.c1) {
+        d.c1 = k;
+        ++d.n1;
+    } else {   // a third chunk before the warp's next post (rare): posted alone
+        __threadfence();
+        atomicAdd(A.done + k, 1u);
+    }
+}
+__device__ __forceinline__ void done_post_slot(const QueryArgs& A, int c, unsigned n, int lane) {
+    const unsigned m = __match_any_sync(0xffffffffu, n ? c : -1);
+    const unsigned sum = __reduce_add_sync(m, n);
+    if (n && lane == __ffs(m) - 1) {
+        __threadfence();
+        atomicAdd(A.done + c, sum);
+    }
+}
+// All lanes of the warp call it (converged); `force` posts whatever is held.
+__device__ __forceinline__ void done_post(const QueryArgs& A, DoneSlots& d, int lane, bool force) {
+    const bool want = force ? (d.n0 | d.n1) != 0 : (d.n1 != 0 || d.n0 >= 64);
+    if (!__ballot_sync(0xffffffffu, want)) return;
+    __syncwarp();   // the warp's result writes happen before the posting lanes' fences
+    done_post_slot(A, d.c0, d.n0, lane);
+    done_post_slot(A, d.c1, d.n1, lane);
+    d = DoneSlots();
+}
+
 constexpr int kWarpChunk = 64;   // segments a warp takes per atomic
 constexpr int kRefillMin = 4;    // refill once this many lanes of a warp are idle
 
@@ -287,7 +333,7 @@ inline size_t trav_smem_bytes(int stack, int block) {
 #ifndef RSI_TRAV_MIN_BLOCKS
 #define RSI_TRAV_MIN_BLOCKS 4   // resident 256-thread blocks per SM the register budget is sized for
 #endif
-template <int MODE, bool STATS, int STACK, bool BATCHED, int NW>
+template <int MODE, bool STATS, int STACK, bool BATCHED, int NW, bool DONE = false>
 __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_query_fp32(QueryArgs A, BatchArgs B) {
     const unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -320,7 +366,9 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
     // bound m2 of the other certain hits, and the plain FP32 nearest (fp32_only)
     int n1 = -1, pbest = -1;
     float lo1 = 0.0f, hi1 = 0.0f, m2 = 0.0f, pbt = 0.0f;
+    DoneSlots dn;   // DONE (host-buffer queries): the lane's finished segments not yet posted
     while (true) {
+        if (DONE) done_post(A, dn, lane, false);
         unsigned idle = __ballot_sync(kFull, ray < 0);
         bool refilled = false;
         if (!exhausted && (__popc(idle) >= kRefillMin || idle == kFull)) {
@@ -389,6 +437,7 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
                         if (MODE == RSI_COUNT) count[r] = 0;
                         if (MODE == RSI_NEAREST) A.near[r] = -1;
                         if (amb) amb[r] = A.amb_bits ? 3 : 1;
+                        if (DONE) done_note(A, r, dn);
                         ray = -1;
                     } else {
                         g = make_seg(s, e, dm0, dm1, dm2);
@@ -609,9 +658,11 @@ __global__ void __launch_bounds__(256, BATCHED ? 3 : RSI_TRAV_MIN_BLOCKS) k_quer
                 }
                 if (amb) amb[r] = 0;
             }
+            if (DONE) done_note(A, r, dn);
             ray = -1;
         }
     }
+    if (DONE) done_post(A, dn, lane, true);
 #undef RSI_STK
     if (STATS) {
         for (int off = 16; off; off >>= 1) {
@@ -2094,6 +2145,17 @@ void launch_fp32(const QueryArgs& A, const BatchArgs& B, int grid, int block, cu
     k_query_fp32<MODE, STATS, STACK, BATCHED, NW><<<grid, block, trav_smem_bytes(STACK, block), s>>>(A, B);
 }
 
+// The host-buffer traversal that counts its finished segments per output
+// chunk (child-pair nodes, no statistics).
+template <int MODE>
+void launch_fp32_done(const QueryArgs& A, int height, int grid, int block, cudaStream_t s, const BatchArgs& B,
+                      int stack_min) {
+    const int need = std::max(height + 1, stack_min);
+    if (need <= 32) k_query_fp32<MODE, false, 32, false, 0, true><<<grid, block, trav_smem_bytes(32, block), s>>>(A, B);
+    else if (need <= 64) k_query_fp32<MODE, false, 64, false, 0, true><<<grid, block, trav_smem_bytes(64, block), s>>>(A, B);
+    else k_query_fp32<MODE, false, 128, false, 0, true><<<grid, block, trav_smem_bytes(128, block), s>>>(A, B);
+}
+
 // Stack entries a traversal needs: the binary walk pushes at most one entry
 // per level (height < STACK); the four-wide walk at most three per four-wide
 // level, and a binary tree of height h has ceil((h + 1) / 2) such levels.
@@ -2192,7 +2254,7 @@ int query_device(rsi_bvh_t h, const float* d_from, const float* d_to, int64_t n,
     if (h->height >= 127) return fail(RSI_ERR_STACK, "rsi_query: tree height exceeds the 128-entry traversal stack");
     const bool both = mode == RSI_BOTH;   // the count pass, which also answers the boolean mode
     if (both) mode = RSI_COUNT;
-    QueryArgs A;
+    QueryArgs A{};
     A.nodes = h->nodes;
     A.nodes4 = h->nodes4;
     A.nodesq = h->nodesq;
@@ -2551,9 +2613,16 @@ using namespace rsi;   // the kernels and launchers above
 // queue with bounded waits, as in streaming batched plans), so copies and
 // traversal overlap without a kernel tail per chunk (the first chunk is
 // small so that the traversal starts early); one FP64 pass then settles the
-// whole queue and the results are copied out.  Up to 2^28 segments (8 GB of
-// staging); a batch whose staging does not fit goes through the two slots.
+// whole queue and the results are copied out.  With page-locked outputs the
+// traversal counts its finished segments per output chunk of 2^21 segments
+// into page-locked counters, and the host copies each chunk out as soon as
+// it is answered, while the traversal goes on; the queued segments' answers
+// are written into the host arrays after the FP64 pass.  Up to 2^28 segments
+// (8 GB of staging); a batch whose staging does not fit goes through the two
+// slots.
 constexpr int64_t kHostWhole = (int64_t)1 << 28;
+constexpr int kOutShift = 21;
+constexpr int kOutChunks = (int)(kHostWhole >> kOutShift);
 }  // namespace
 
 namespace rsi {
@@ -2634,6 +2703,17 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
         c->h_ready = nullptr;
         return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
     }
+    if (!c->h_done && rsi::host_malloc_pinned(&c->h_done, kOutChunks * sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_done = nullptr;
+        return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
+    }
+    if (!c->d_done && rsi::dev_malloc(&c->d_done, kOutChunks * sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_done = nullptr;
+        return rsi::fail(RSI_ERR_OOM, "rsi_query_host: counter allocation failed");
+    }
+    if (!c->st_poll) RSI_CUDA_TRY(cudaStreamCreateWithFlags(&c->st_poll, cudaStreamNonBlocking));
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     float* df = reinterpret_cast<float*>(c->whole);
     float* dt = reinterpret_cast<float*>(c->whole + al(12 * (size_t)n));
@@ -2682,6 +2762,24 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     const int block = o.block > 0 ? o.block : 256;
     const int bps = o.blocks_per_sm > 0 ? o.blocks_per_sm : 8;
     const int nw = o.node_width == 4 ? 1 : (o.node_width == 3 && h->has_q ? 2 : 0);
+    // page-locked outputs: the FP32 answers are copied out chunk by chunk as
+    // the traversal finishes them, then the queued segments' answers are
+    // written into them after the FP64 pass
+    uint8_t *mh = nullptr, *ma = nullptr;
+    int32_t* mc = nullptr;
+    const bool overlap = !o.fp32_only && mapped_host(h_hit, &mh) && mapped_host(h_amb, &ma) &&
+                         mapped_host(mode == RSI_COUNT ? h_count : (int32_t*)nullptr, &mc);
+    const int n_out = (int)((n + ((int64_t)1 << kOutShift) - 1) >> kOutShift);
+    // the counting traversal: child-pair nodes without statistics; otherwise
+    // the answers are copied out once the traversal has ended
+    const bool counted = overlap && nw == 0 && !o.collect_stats;
+    if (counted) {
+        RSI_CUDA_TRY(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned int) * (size_t)n_out, s));
+        RSI_CUDA_TRY(cudaEventRecord(c->ev_q[1], s));   // the polls read the counters after this
+        RSI_CUDA_TRY(cudaStreamWaitEvent(c->st_poll, c->ev_q[1], 0));
+        A.done = c->d_done;
+        A.done_shift = kOutShift;
+    }
     k_reset_query<<<1, 1, 0, s>>>(h->ctr, ~0ull);   // ~0: the queue is fed by the posts above
     A.n_rays = n;
     BatchArgs Bs{};
@@ -2689,7 +2787,10 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     Bs.timeout_ns = 10000000000ll;   // a post may wait behind pageable-memory copies
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + block - 1) / block,
                                                                    (int64_t)rsi::device_sm_count() * bps));
-    if (mode == RSI_ANY_HIT) {
+    if (counted) {
+        if (mode == RSI_ANY_HIT) launch_fp32_done<RSI_ANY_HIT>(A, h->height, grid, block, s, Bs, o.stack);
+        else launch_fp32_done<RSI_COUNT>(A, h->height, grid, block, s, Bs, o.stack);
+    } else if (mode == RSI_ANY_HIT) {
         if (o.collect_stats) launch_fp32_stack<RSI_ANY_HIT, true>(A, h->height, nw, grid, block, s, Bs, o.stack);
         else launch_fp32_stack<RSI_ANY_HIT, false>(A, h->height, nw, grid, block, s, Bs, o.stack);
     } else {
@@ -2697,23 +2798,9 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
         else launch_fp32_stack<RSI_COUNT, false>(A, h->height, nw, grid, block, s, Bs, o.stack);
     }
     rsi::note_launches(2);
+    RSI_CUDA_TRY(cudaEventRecord(c->ev_q[0], s));   // the traversal has ended
     // every copy has landed once the traversal ends; the wait orders the FP64 pass after them
     RSI_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_chunk[n_chunks - 1], 0));
-    // page-locked outputs: the FP32 answers are copied out on st_out while the
-    // FP64 pass runs, then the queued segments' answers are written into them
-    uint8_t *mh = nullptr, *ma = nullptr;
-    int32_t* mc = nullptr;
-    const bool overlap = !o.fp32_only && mapped_host(h_hit, &mh) && mapped_host(h_amb, &ma) &&
-                         mapped_host(mode == RSI_COUNT ? h_count : (int32_t*)nullptr, &mc);
-    if (overlap) {
-        RSI_CUDA_TRY(cudaEventRecord(c->ev_q[0], s));
-        RSI_CUDA_TRY(cudaStreamWaitEvent(c->st_out, c->ev_q[0], 0));
-        if (h_hit) RSI_CUDA_TRY(cudaMemcpyAsync(h_hit, dh, (size_t)n, cudaMemcpyDeviceToHost, c->st_out));
-        if (h_amb) RSI_CUDA_TRY(cudaMemcpyAsync(h_amb, da, (size_t)n, cudaMemcpyDeviceToHost, c->st_out));
-        if (mode == RSI_COUNT)
-            RSI_CUDA_TRY(cudaMemcpyAsync(h_count, dc, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->st_out));
-        RSI_CUDA_TRY(cudaEventRecord(c->ev_out[0], c->st_out));
-    }
     if (!o.fp32_only) {
         const rsi::PairScratch P = rsi::handle_pairs(h);
         if (mode == RSI_ANY_HIT) launch_fp64_pass<RSI_ANY_HIT>(A, h->height, &P, s);
@@ -2721,6 +2808,46 @@ int host_whole(rsi_bvh_t h, const float* h_from, const float* h_to, int64_t n, i
     }
     RSI_CUDA_TRY(cudaGetLastError());
     if (overlap) {
+        // copy out each output chunk once the traversal has finished all its
+        // segments (or, for whatever is left, once the traversal has ended)
+        auto copy_out = [&](int k) -> int {
+            const int64_t a = (int64_t)k << kOutShift, m = std::min<int64_t>(n, a + ((int64_t)1 << kOutShift)) - a;
+            if (h_hit) RSI_CUDA_TRY(cudaMemcpyAsync(h_hit + a, dh + a, (size_t)m, cudaMemcpyDeviceToHost, c->st_out));
+            if (h_amb) RSI_CUDA_TRY(cudaMemcpyAsync(h_amb + a, da + a, (size_t)m, cudaMemcpyDeviceToHost, c->st_out));
+            if (mode == RSI_COUNT)
+                RSI_CUDA_TRY(cudaMemcpyAsync(h_count + a, dc + a, 4 * (size_t)m, cudaMemcpyDeviceToHost, c->st_out));
+            return RSI_OK;
+        };
+        std::vector<char> out_done((size_t)n_out, 0);
+        int left = n_out;
+        const unsigned int* hd = c->h_done;
+        while (counted && left > 0) {
+            const bool ended = cudaEventQuery(c->ev_q[0]) == cudaSuccess;
+            if (ended) break;
+            RSI_CUDA_TRY(cudaMemcpyAsync(c->h_done, c->d_done, sizeof(unsigned int) * (size_t)n_out,
+                                         cudaMemcpyDeviceToHost, c->st_poll));
+            RSI_CUDA_TRY(cudaStreamSynchronize(c->st_poll));
+            for (int k = 0; k < n_out; ++k) {
+                const int64_t a = (int64_t)k << kOutShift;
+                const int64_t m = std::min<int64_t>(n, a + ((int64_t)1 << kOutShift)) - a;
+                if (!out_done[k] && (int64_t)hd[k] >= m) {
+                    rc = copy_out(k);
+                    if (rc) return rc;
+                    out_done[k] = 1;
+                    --left;
+                }
+            }
+        }
+        cudaGetLastError();   // cudaErrorNotReady of the event queries
+        if (left > 0) {
+            RSI_CUDA_TRY(cudaStreamWaitEvent(c->st_out, c->ev_q[0], 0));
+            for (int k = 0; k < n_out; ++k)
+                if (!out_done[k]) {
+                    rc = copy_out(k);
+                    if (rc) return rc;
+                }
+        }
+        RSI_CUDA_TRY(cudaEventRecord(c->ev_out[0], c->st_out));
         RSI_CUDA_TRY(cudaStreamWaitEvent(s, c->ev_out[0], 0));
         rsi::k_patch_host<<<rsi::device_sm_count() * 4, 256, 0, s>>>(h->band_ids, &h->ctr->band_count, dh,
                                                                 mode == RSI_COUNT ? dc : nullptr, da, mh, mc, ma);

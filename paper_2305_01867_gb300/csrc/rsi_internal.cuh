@@ -170,6 +170,9 @@ struct DeviceCtx {
     int64_t whole_cap = 0;                 // segments it holds (30 B each)
     cudaEvent_t ev_chunk[64] = {};         // copy-in events of the whole-batch chunks
     unsigned long long* h_ready = nullptr; // pinned: segments copied in so far, per chunk
+    unsigned int* d_done = nullptr;        // device: finished segments per output chunk of a whole-batch query
+    unsigned int* h_done = nullptr;        // pinned: the host's copy of them
+    cudaStream_t st_poll = nullptr;        // copies of those counters
 };
 DeviceCtx* device_ctx();   // the current device's context (NULL without a device)
 int pool_alloc(void** p, size_t bytes, cudaStream_t s);

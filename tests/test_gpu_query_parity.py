@@ -388,11 +388,12 @@ def test_host_path_chunk_boundaries(rsi, n):
 
 @pytest.mark.parametrize("mode", ["any_hit", "count", "both"])
 def test_host_path_pinned_outputs(rsi, mode):
-    """Page-locked host outputs: the FP32 answers are copied out while the
-    FP64 pass runs and the queued segments' answers are written into the host
-    arrays afterwards -- every entry equals the device path's, on the grazing
-    c3 mix (many queued segments) and on a short c2 batch."""
-    for cfg, n, bits in (("c3", 600_000, 63), ("c2", 70_001, 30)):
+    """Page-locked host outputs: the FP32 answers are copied out chunk by
+    chunk (2^21 segments) as the traversal finishes them and the queued
+    segments' answers are written into the host arrays after the FP64 pass --
+    every entry equals the device path's, on the grazing c3 mix (many queued
+    segments), on a short c2 batch and on a c3 batch of three output chunks."""
+    for cfg, n, bits in (("c3", 600_000, 63), ("c2", 70_001, 30), ("c3", 4_500_001, 63)):
         mesh = W.config_mesh(cfg)
         F, E = W.rays(W.config_rays(cfg), mesh, count=n)
         bvh = rsi.LBVH(_dev(mesh.vertices), _dev(mesh.triangles), morton_bits=bits)
