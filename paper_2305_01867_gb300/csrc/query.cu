@@ -694,7 +694,6 @@ struct PairScratch {
     int32_t* hard;        // [pair_cap] pairs the certain FP64 test left undecided
     int32_t* fb_ids;      // [queue capacity] segments left to k_query_fp64
     int seg_cap, pair_cap;
-    int min_queue;        // queues shorter than this go to k_query_fp64 whole
     int fp32_hits;        // 1: a certain FP32 hit is entered as a hit without the FP64 step
 };
 
@@ -1123,7 +1122,7 @@ __global__ void __launch_bounds__(128, 12) k_band_collect(QueryArgs A, BatchArgs
         const float3 s = make_float3(Q.from[3 * r], Q.from[3 * r + 1], Q.from[3 * r + 2]);
         const float3 e = make_float3(Q.to[3 * r], Q.to[3 * r + 1], Q.to[3 * r + 2]);
         const SegF g = make_seg(s, e, Q.dmax0, Q.dmax1, Q.dmax2);
-        bool over = k >= P.seg_cap || nb < P.min_queue;   // warp-uniform
+        bool over = k >= P.seg_cap;   // warp-uniform
         int nc = 0, nf = 0, nl = 0;                        // warp-uniform list lengths
         if (!over) {
             if (Q.n_tri == 1) {
@@ -2196,11 +2195,9 @@ void launch_fp64(const QueryArgs& A, int height, int grid, cudaStream_t s, const
 
 // The FP64 pass over the queued segments: pair-parallel when scratch P is
 // given (collect, classify, combine, then k_query_fp64 for the fallback
-// list), else k_query_fp64 for every queued segment.  In the boolean mode
-// a queue shorter than 2,048 segments goes to k_query_fp64 whole (the
-// collect kernel decides on the device): there its overlapped,
-// early-exiting warps finish first (c2: 1,330 queued, 0.115 against
-// 0.151 ms), while long queues favour the pairs (c3: 4e5 queued).
+// list), else k_query_fp64 for every queued segment.  The pair path serves
+// queues of every length and all three modes (c2 boolean mode, 1,330
+// queued: 0.072 ms against 0.137 ms with k_query_fp64 for the whole queue).
 template <int MODE, bool BATCHED = false>
 void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P0, cudaStream_t s,
                       const BatchArgs& B = BatchArgs{}) {
@@ -2210,7 +2207,6 @@ void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P0, cud
         return;
     }
     PairScratch Pm = *P0;
-    Pm.min_queue = 0;
     Pm.fp32_hits = MODE != RSI_NEAREST;   // the nearest mode needs every hit's t
     const PairScratch* P = &Pm;
     // step 1: both collect kernels are launched; the queue length (on the
@@ -2387,7 +2383,6 @@ PairScratch carve_pairs(char* mem, int64_t seg_cap, int64_t pair_cap, int32_t* f
     P.fb_ids = fb_ids;
     P.seg_cap = (int)seg_cap;
     P.pair_cap = (int)pair_cap;
-    P.min_queue = 0;
     P.fp32_hits = 0;
     return P;
 }
