@@ -351,16 +351,19 @@ int rsi_segment_order(rsi_bvh_t h, const float* d_from, const float* d_to, int64
  * As rsi_query with segments and results in HOST memory; returns after the
  * results are in host memory.  Batches of up to 2^28 segments are staged
  * whole on the device (30 B per segment, kept for later calls): the segments
- * are copied in at most 64 chunks on an internal stream while one
- * persistent FP32 traversal on `stream` takes each chunk as it lands, then
- * one FP64 re-test settles the whole batch and the results are copied back.
+ * are copied in at most 64 chunks on an internal stream (2^16 segments,
+ * then doubling up to 2^21) while one persistent FP32 traversal on `stream`
+ * takes each chunk as it lands, then one FP64 re-test settles the whole
+ * batch and the results are copied back.
  * Larger batches, batches whose staging does not fit in device memory, and
  * queries with opt->ray_sort_tile stream chunks of 2^21 through two recycled
  * staging slots (copies and traversal overlapped; the re-test runs per
  * chunk).  Page-locked host buffers give asynchronous copies; with
- * page-locked outputs the FP32 answers are copied out while the FP64
- * re-test runs and the re-tested segments' answers are then written into
- * the host arrays by the device.  The
+ * page-locked outputs (and child-pair nodes, no statistics) the traversal
+ * counts its finished segments per chunk of 2^21 and the calling thread,
+ * polling those counts, copies each chunk's FP32 answers out while the
+ * traversal and the FP64 re-test go on; the re-tested segments' answers are
+ * then written into the host arrays by the device.  The
  * staging is shared by all handles of a device: concurrent host-buffer
  * queries on one device run one after the other.
  */
