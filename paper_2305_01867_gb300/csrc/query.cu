@@ -1362,8 +1362,8 @@ __global__ void __launch_bounds__(128) k_band_collect_threads(QueryArgs A, Batch
 // root unless the nearest mode needs the t of a certain hit; the count mode
 // computes it in step 3 where needed).  The pairs this test leaves undecided
 // are listed for step 2b, so that the long evaluation of the definition runs
-// apart: a few of them one warp each (k_band_classify_hard_warp, whose lanes
-// share the work of one pair), many of them one thread each.
+// apart (k_band_classify_hard): a few of them one warp each, whose lanes
+// share the work of one pair, many of them one thread each.
 constexpr int kHardWarpMax = 2048;   // undecided pairs up to which each gets a warp
 template <int MODE, bool BATCHED>
 __global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B, PairScratch P) {
@@ -1404,11 +1404,31 @@ __global__ void __launch_bounds__(256) k_band_classify(QueryArgs A, BatchArgs B,
 }
 
 // Step 2b: the definition itself (classify_fp64) for the undecided pairs:
-// one thread per pair for long lists, one warp per pair for short ones.
+// one warp per pair for short lists (the lanes share the pair's work), one
+// thread per pair for long ones.
 template <bool BATCHED>
-__global__ void __launch_bounds__(256) k_band_classify_hard(QueryArgs A, BatchArgs B, PairScratch P) {
+__global__ void __launch_bounds__(128) k_band_classify_hard(QueryArgs A, BatchArgs B, PairScratch P) {
     const int nh = *(volatile int*)&A.ctr->hard_count;
-    if (nh < kHardWarpMax) return;   // k_band_classify_hard_warp takes short lists
+    if (nh < kHardWarpMax) {
+        const int lane = threadIdx.x & 31;
+        const int warps = (gridDim.x * blockDim.x) >> 5;
+        for (int h = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < nh; h += warps) {
+            const int i = P.hard[h];
+            int64_t r;
+            const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[P.pair_seg[i]], r);
+            const D3 sd = {(double)Q.from[3 * r], (double)Q.from[3 * r + 1], (double)Q.from[3 * r + 2]};
+            const D3 ed = {(double)Q.to[3 * r], (double)Q.to[3 * r + 1], (double)Q.to[3 * r + 2]};
+            const Tri tr = load_tri(Q.tris, P.pair_leaf[i]);
+            double t = 0.0;
+            bool incl = false;
+            const int cls = classify_fp64_warp(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2), t, incl);
+            if (lane == 0) {
+                P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0));
+                P.pair_t[i] = t;
+            }
+        }
+        return;
+    }
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += gridDim.x * blockDim.x) {
         const int i = P.hard[h];
         int64_t r;
@@ -1421,29 +1441,6 @@ __global__ void __launch_bounds__(256) k_band_classify_hard(QueryArgs A, BatchAr
         const int cls = classify_fp64(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2), t, incl);
         P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0));
         P.pair_t[i] = t;
-    }
-}
-
-template <bool BATCHED>
-__global__ void __launch_bounds__(128) k_band_classify_hard_warp(QueryArgs A, BatchArgs B, PairScratch P) {
-    const int nh = *(volatile int*)&A.ctr->hard_count;
-    if (nh >= kHardWarpMax) return;   // k_band_classify_hard takes long lists
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int h = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < nh; h += warps) {
-        const int i = P.hard[h];
-        int64_t r;
-        const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[P.pair_seg[i]], r);
-        const D3 sd = {(double)Q.from[3 * r], (double)Q.from[3 * r + 1], (double)Q.from[3 * r + 2]};
-        const D3 ed = {(double)Q.to[3 * r], (double)Q.to[3 * r + 1], (double)Q.to[3 * r + 2]};
-        const Tri tr = load_tri(Q.tris, P.pair_leaf[i]);
-        double t = 0.0;
-        bool incl = false;
-        const int cls = classify_fp64_warp(sd, ed, d3of(tr.v0), d3of(tr.v1), d3of(tr.v2), t, incl);
-        if (lane == 0) {
-            P.pair_cls[i] = (uint8_t)(cls | (incl ? 4 : 0));
-            P.pair_t[i] = t;
-        }
     }
 }
 
@@ -1554,15 +1551,19 @@ __global__ void __launch_bounds__(128) k_band_crossings(QueryArgs A, BatchArgs B
         const int cnt = P.seg_cnt[k], off = P.seg_off[k];
         int64_t r;
         const QueryArgs Q = band_segment<BATCHED>(A, B, A.band_ids[k], r);
-        double ts[kCandMax];
+        // an inclusive crossing's t lies in [0, 1] (-0.0 included), where the
+        // order of the bit patterns as integers is the order of the values
+        // (-0.0 first, then equal to +0.0, which the merge below treats alike):
+        // the sort compares integers, not FP64 values
+        long long ts[kCandMax];
         int n_incl = 0, n_hit = 0;
         for (int i = 0; i < cnt; ++i) {
             const int c = P.pair_cls[off + i];
             n_hit += (c & 3) == kHit;
-            if (c & 4) ts[n_incl++] = P.pair_t[off + i];
+            if (c & 4) ts[n_incl++] = __double_as_longlong(P.pair_t[off + i]);
         }
         for (int i = 1; i < n_incl; ++i) {
-            const double x = ts[i];
+            const long long x = ts[i];
             int k2 = i - 1;
             while (k2 >= 0 && ts[k2] > x) {
                 ts[k2 + 1] = ts[k2];
@@ -1572,7 +1573,7 @@ __global__ void __launch_bounds__(128) k_band_crossings(QueryArgs A, BatchArgs B
         }
         int count = 0;
         for (int i = 0; i < n_incl; ++i)
-            if (i == 0 || __dsub_rn(ts[i], ts[i - 1]) > kTMerge) ++count;
+            if (i == 0 || __dsub_rn(__longlong_as_double(ts[i]), __longlong_as_double(ts[i - 1])) > kTMerge) ++count;
         atomicAdd(&A.ctr->ambiguous, 1ull);
         Q.count[r] = count;
         if (Q.hit) Q.hit[r] = (uint8_t)(count > 0);
@@ -2217,10 +2218,9 @@ void launch_fp64_pass(const QueryArgs& A, int height, const PairScratch* P0, cud
     else if (height < 64) k_band_collect_threads<64, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
     else k_band_collect_threads<128, BATCHED><<<cgrid, 128, 0, s>>>(A, B, *P);
     k_band_classify<MODE, BATCHED><<<device_sm_count() * 8, 256, 0, s>>>(A, B, *P);
-    k_band_classify_hard<BATCHED><<<device_sm_count() * 4, 256, 0, s>>>(A, B, *P);
-    k_band_classify_hard_warp<BATCHED><<<device_sm_count() * 4, 128, 0, s>>>(A, B, *P);
+    k_band_classify_hard<BATCHED><<<device_sm_count() * 8, 128, 0, s>>>(A, B, *P);
     k_band_reduce<MODE, BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
-    note_launches(6);
+    note_launches(5);
     if (MODE == RSI_COUNT) {   // the ambiguous segments' crossings
         k_band_tfix<BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
         k_band_crossings<BATCHED><<<grid, 128, 0, s>>>(A, B, *P);
